@@ -1,0 +1,87 @@
+"""Planted mistakes in the oracle must be caught by its pins (CPU only).
+
+Each case copies ``oracle.c``, plants one plausible mistake (a transposed
+operand, a dropped term, a wrong index, sign or inclusivity), compiles the
+copy into a temporary directory and runs the pins against it: at least one
+pin has to fail.  The library is not involved.
+"""
+import os
+import subprocess
+
+import pytest
+
+import oracle
+from tests import oracle_pins as pins
+
+SRC = os.path.join(os.path.dirname(oracle.__file__), "oracle.c")
+
+MUTANTS = {
+    "R_transposed": ("(double)R[3 * r] * x[0] + (double)R[3 * r + 1] * x[1] +\n"
+                     "               (double)R[3 * r + 2] * x[2]",
+                     "(double)R[r] * x[0] + (double)R[r + 3] * x[1] +\n"
+                     "               (double)R[r + 6] * x[2]"),
+    "t_dropped": (" + (double)vw->t[r];", ";"),
+    "fy_for_u": ("double u = (double)vw->fx * qx", "double u = (double)vw->fy * qx"),
+    "pixel_index_transposed": ("int64_t pix = (int64_t)iy * vw->W + ix;\n            if (pix_out)",
+                               "int64_t pix = (int64_t)ix * vw->H + iy;\n            if (pix_out)"),
+    "round_not_floor": ("*ix = (int)floor(u);", "*ix = (int)lround(u);"),
+    "closed_frame": ("u < (double)vw->W", "u <= (double)vw->W"),
+    "mask_dropped_from_W": ("Wsum += m * w;\n            Zsum += w;\n            if (i < 32)",
+                            "Wsum += w;\n            Zsum += w;\n            if (i < 32)"),
+    "depth_gate_exclusive": ("if (!(fabs(e) <= Delta)) continue;\n            double r = e / Delta;\n"
+                             "            double w = exp(-pr->alpha1 * r * r);\n            Wsum += m * w;"
+                             "\n            Zsum += w;\n            if (i < 32)",
+                             "if (!(fabs(e) < Delta)) continue;\n            double r = e / Delta;\n"
+                             "            double w = exp(-pr->alpha1 * r * r);\n            Wsum += m * w;"
+                             "\n            Zsum += w;\n            if (i < 32)"),
+    "weight_not_squared": ("double w = exp(-pr->alpha1 * r * r);\n            Wsum += m * w;"
+                           "\n            Zsum += w;\n            if (i < 32)",
+                           "double w = exp(-pr->alpha1 * fabs(r));\n            Wsum += m * w;"
+                           "\n            Zsum += w;\n            if (i < 32)"),
+    "gamma_ignored": ("double Delta = pr->gamma * hv;\n            double e",
+                      "double Delta = hv;\n            double e"),
+    "centre_offset": ("double c[3] = {origin[0] + (i + 0.5) * h",
+                      "double c[3] = {origin[0] + (i + 1.0) * h"),
+    "mask_gate_exclusive": ("*pass = *m >= pr->tau_m;\n    } else if",
+                            "*pass = *m > pr->tau_m;\n    } else if"),
+    "P_inverted": ("double P = Zsum > pr->eps ? Wsum / Zsum : 0.0;",
+                   "double P = Zsum > pr->eps ? Zsum / (Wsum + 1e-300) : 0.0;"),
+    "vmask_not_gated": ("vmask_out[a] = seg ? bits : 0u;", "vmask_out[a] = bits;"),
+    "consensus_exclusive": ("int seg = P >= pr->tau_cons;", "int seg = P > pr->tau_cons;"),
+    "view_bit_shifted": ("if (i < 32) bits |= 1u << i;", "if (i < 31) bits |= 1u << (i + 1);"),
+    "z_near_dropped": ("if (!(p[2] > z_near)) return 0;", ""),
+    "hv_linear_stretch": ("*hv = h / ((2.0 - rho) * (2.0 - rho));", "*hv = h / (2.0 - rho);"),
+    "uncontract_wrong": ("double s = 1.0 / (rho * (2.0 - rho));", "double s = 1.0 / (2.0 - rho);"),
+    "contract_wrong": ("double s = (2.0 - 1.0 / r) / r;", "double s = (2.0 - 1.0 / r);"),
+    "label_closed_bound": ("s < (double)g", "s <= (double)g"),
+    "grad_depth_sign": ("((mv[k] - P) / Zsum) * dwdD", "((P - mv[k]) / Zsum) * dwdD"),
+    "grad_sigmoid_dropped": ("mv[k] * (1.0 - mv[k]) : 1.0", "mv[k] : 1.0"),
+    "grad_Z_dropped": ("(wv[k] / Zsum) * dmdl", "wv[k] * dmdl"),
+    "grad_alpha_dropped": ("wv[k] * 2.0 * pr->alpha1 * ev[k]", "wv[k] * 2.0 * ev[k]"),
+}
+
+
+def _build(tmp_path, name, old, new):
+    src = open(SRC).read()
+    assert src.count(old) == 1, (name, src.count(old))
+    mut = src.replace(old, new)
+    c = tmp_path / f"{name}.c"
+    so = tmp_path / f"{name}.so"
+    c.write_text(mut)
+    subprocess.run(["gcc", "-O1", "-fopenmp", "-fPIC", "-shared", "-ffp-contract=off", str(c),
+                    "-o", str(so), "-lm"], check=True)
+    return str(so)
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_planted_mistake_is_caught(tmp_path, name):
+    old, new = MUTANTS[name]
+    orc = oracle.variant(_build(tmp_path, name, old, new))
+    caught = []
+    for pin in pins.ALL_PINS:
+        try:
+            pin(orc)
+        except AssertionError:
+            caught.append(pin.__name__)
+            break
+    assert caught, f"no pin caught the planted mistake {name}"
