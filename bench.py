@@ -1,0 +1,419 @@
+#!/usr/bin/env python
+"""Benchmark of the depth-weighted multi-view voxel fusion hot path.
+
+One step = one pass of the whole hot path over one synthetic scene shaped
+like the paper's forward-facing workload (LLFF-like, Sec. 4.1): 256^3 dense
+grid over [-1, 1]^3 (16.8M voxels), 8 anchor views of 1008x756 (FP32 planar
+depth, FP16 soft masks) ray-cast from 200 seeded ellipsoids and a back
+plane, a ~5 % surface-shell occupancy prior and 1M points to label:
+
+  A1  occupancy prior -> active list             (4 kernels)
+  A2-A6 project / gate / depth-weight / accumulate, 8 views in one launch
+  A7  normalise + consensus -> dense 256^3 score grid + seg bitfield
+  A8  Pass 1 labels of 1M points
+
+``value`` = nominal voxel-view updates/s = g^3 x views / step time, all
+inputs resident in HBM, L2 flushed between timed steps.  ``e2e`` = the same
+metric through the public API with pinned host buffers, host<->device copies
+inside the timed region.  ``--impl reference`` times the FP64 CPU oracle on a
+bounded sample of the same workload.  Under torchrun every rank runs an
+independent replica (the path has no exchange step): weak scaling.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = ("voxel-view updates/s and per-update fusion ms p50/p99 vs plain launch; "
+          "% HBM roofline")
+UNIT = "voxel-view updates/s"
+WORKLOADS = {
+    "forward-dense-256": "256^3 dense grid, 8 views 1008x756 FP32 depth + FP16 masks, "
+                         "200 ellipsoids + back plane, 1M points",
+    "unbounded-sparse-512": "contracted 512^3 grid, 12M sparse occupied voxels, 16 views "
+                            "1297x840, 1000 ellipsoids on a ground plane, 3M points",
+}
+
+
+def _env_int(k, d):
+    try:
+        return int(os.environ.get(k, d))
+    except ValueError:
+        return d
+
+
+def make_workload(name):
+    import synth
+    if name == "forward-dense-256":
+        return synth.config2()
+    if name == "unbounded-sparse-512":
+        return synth.config3()
+    raise SystemExit(f"unknown workload {name}")
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6400.0, "fallback"
+
+
+# --------------------------------------------------------------------------
+# clocks during the timed region
+# --------------------------------------------------------------------------
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-i", str(self.index), "-lms", "100"], stdout=open(self.path, "w"),
+                stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(smax)) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# --------------------------------------------------------------------------
+# CPU oracle baseline (bounded sample)
+# --------------------------------------------------------------------------
+def oracle_rate(wl, seconds: float, seed: int = 0):
+    """Time the FP64 oracle on a random sample of the active voxels (all views)
+    and of the points; returns the extrapolated full-step seconds and details."""
+    import oracle
+    cores = oracle.set_threads(0)
+    lin = wl.active_linear()
+    rng = np.random.Generator(np.random.PCG64(seed))
+    prm = oracle.Params()
+    pilot = rng.choice(len(lin), size=min(len(lin), 20000), replace=False)
+    t0 = time.perf_counter()
+    oracle.fuse(wl.grid, lin[pilot], wl.cams, wl.depth, wl.mask, wl.mask_type, prm)
+    t_pilot = time.perf_counter() - t0
+    n = int(min(len(lin), max(1000, len(pilot) * 0.8 * seconds / max(t_pilot, 1e-6))))
+    sample = rng.choice(len(lin), size=n, replace=False)
+    t0 = time.perf_counter()
+    out = oracle.fuse(wl.grid, lin[sample], wl.cams, wl.depth, wl.mask, wl.mask_type, prm)
+    t_fuse = time.perf_counter() - t0
+    npts = min(len(wl.points), 300_000)
+    seg = oracle.dense_seg(wl.grid, lin[sample], out["seg"])
+    t0 = time.perf_counter()
+    oracle.label(wl.grid, seg, wl.points[:npts])
+    t_lab = time.perf_counter() - t0
+    full = t_fuse * len(lin) / n + t_lab * len(wl.points) / npts
+    return full, {"cores": cores, "sample_voxels": n, "active_voxels": int(len(lin)),
+                  "sample_points": npts, "fuse_s": t_fuse, "label_s": t_lab}
+
+
+# --------------------------------------------------------------------------
+# our arm
+# --------------------------------------------------------------------------
+def algorithmic_bytes(wl, n_active):
+    """Bytes the method must move per step, per kernel (first touch only)."""
+    g3 = wl.n_voxels if wl.occ is not None else None
+    S = wl.n_views
+    view_bytes = sum(d.nbytes + m.nbytes for d, m in zip(wl.depth, wl.mask))
+    npts = len(wl.points)
+    if wl.occ is not None:
+        cells = int(wl.grid.g) ** 3
+        comp = cells + cells // 8 + 4 * n_active          # occ read, bits, active list
+        fin = cells // 8 + 8 * n_active + 4 * cells + cells // 8  # bits, W+Z, P, seg
+    else:
+        cells = int(wl.grid.g) ** 3
+        comp = 12 * len(wl.coords) + cells // 8 + 4 * n_active
+        fin = 8 * n_active + 4 * n_active + cells // 8
+    fuse = 4 * n_active + 12 * n_active + view_bytes        # index, W+Z+bits, rasters
+    lab = 13 * npts + cells // 8
+    return {"compaction": comp, "fuse": fuse, "finalize": fin, "label": lab}, view_bytes, S, g3
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+
+    from paper_2601_04860_b300 import FusionParams, VoxelFusion
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    wl = make_workload(args.workload)
+    occ = None if wl.occ is None else torch.from_numpy(wl.occ).to(dev)
+    coords = None if wl.coords is None else torch.from_numpy(wl.coords).to(dev)
+    depth = [torch.from_numpy(d).to(dev) for d in wl.depth]
+    if wl.mask_type == 1:
+        mask = [torch.from_numpy(m.view(np.float16)).to(dev) for m in wl.mask]
+    else:
+        mask = [torch.from_numpy(m).to(dev) for m in wl.mask]
+    pts = torch.from_numpy(np.ascontiguousarray(wl.points)).to(dev)
+    fu = VoxelFusion(wl.grid, occ=occ, coords=coords, params=FusionParams())
+    n_active = fu.n_active
+    dense = wl.occ is not None
+    score = torch.empty(fu.n_cells if dense else n_active, dtype=torch.float32, device=dev)
+    labels = torch.empty(len(wl.points), dtype=torch.uint8, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    S = wl.n_views
+    N = fu.n_cells if dense else n_active
+    launches_per_step = 4 + (0 if dense else 0) + math.ceil(S / 32) + 1 + 1
+
+    def step(ev=None):
+        fu.set_occupancy(occ=occ, coords=coords)
+        if ev:
+            ev[1].record(stream)
+        fu.add_views(wl.cams, depth, mask, mask_type=wl.mask_type)
+        if ev:
+            ev[2].record(stream)
+        fu.finalize(score=score)
+        if ev:
+            ev[3].record(stream)
+        fu.label_points(pts, out=labels)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
+    clocks = Clocks(local_rank)
+    clocks.start()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter()
+    for k in range(args.steps):
+        flush.zero_()
+        evs[k][0].record(stream)
+        step(evs[k])
+        evs[k][4].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    t_wall = time.perf_counter() - t_wall
+    clk = clocks.stop()
+    step_ms = np.array([e[0].elapsed_time(e[4]) for e in evs])
+    phase = {name: np.array([e[i].elapsed_time(e[i + 1]) for e in evs])
+             for i, name in enumerate(["compaction", "fuse", "finalize", "label"])}
+    ms = float(step_ms.mean())
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+
+    # per-update latency: one incremental view + finalize (the interactive update)
+    upd = []
+    for k in range(max(10, args.steps)):
+        fu.set_occupancy(occ=occ, coords=coords)
+        fu.add_views(wl.cams[:-1], depth[:-1], mask[:-1], mask_type=wl.mask_type)
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fu.add_view(wl.cams[-1], depth[-1], mask[-1], mask_type=wl.mask_type)
+        fu.finalize(score=score)
+        b.record(stream)
+        torch.cuda.synchronize()
+        upd.append(a.elapsed_time(b))
+    upd = np.array(upd)
+
+    # end to end through the public API with pinned host buffers
+    h_occ = None if occ is None else torch.from_numpy(wl.occ).pin_memory()
+    h_coords = None if coords is None else torch.from_numpy(wl.coords).pin_memory()
+    h_depth = [d.cpu().pin_memory() for d in depth]
+    h_mask = [m.cpu().pin_memory() for m in mask]
+    h_pts = pts.cpu().pin_memory()
+    h_score = torch.empty(score.shape, dtype=score.dtype).pin_memory()
+    h_labels = torch.empty(labels.shape, dtype=labels.dtype).pin_memory()
+    h2d = sum(t.numel() * t.element_size() for t in
+              [x for x in (h_occ, h_coords) if x is not None] + h_depth + h_mask + [h_pts])
+    d2h = h_score.numel() * 4 + h_labels.numel()
+
+    def e2e_step():
+        if occ is not None:
+            occ.copy_(h_occ, non_blocking=True)
+        if coords is not None:
+            coords.copy_(h_coords, non_blocking=True)
+        for a, b in zip(depth, h_depth):
+            a.copy_(b, non_blocking=True)
+        for a, b in zip(mask, h_mask):
+            a.copy_(b, non_blocking=True)
+        pts.copy_(h_pts, non_blocking=True)
+        step()
+        h_score.copy_(score, non_blocking=True)
+        h_labels.copy_(labels, non_blocking=True)
+    for _ in range(2):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_ms = []
+    for _ in range(max(3, args.steps // 2)):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        e2e_step()
+        b.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms.append(a.elapsed_time(b))
+    e2e_ms = float(np.mean(e2e_ms))
+    if world > 1:
+        t = torch.tensor([e2e_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+
+    algo, view_bytes, _, _ = algorithmic_bytes(wl, n_active)
+    peak, peak_kind = peaks()
+    pm = {k: float(v.mean()) for k, v in phase.items()}
+    dom = max(["fuse", "finalize", "label"], key=lambda k: pm[k])
+    achieved = algo[dom] / (pm[dom] * 1e-3) / 1e9
+    step_bytes = sum(algo.values())
+    res = {
+        "metric": METRIC, "value": world * N * S / (ms * 1e-3), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded ray-cast scene; no dataset)",
+        "config": {"workload": args.workload, "description": WORKLOADS[args.workload],
+                   "grid": int(wl.grid.g), "views": S, "active_voxels": int(n_active),
+                   "voxels_nominal": int(N), "points": int(len(wl.points)),
+                   "l2": "flushed between timed steps (256 MB write)",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
+                     "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                     "peak_kind": peak_kind,
+                     "algorithmic_bytes_per_launch": int(algo[dom])},
+        "step_roofline": {"algorithmic_bytes": int(step_bytes),
+                          "achieved_gbs": step_bytes / (ms * 1e-3) / 1e9,
+                          "frac": step_bytes / (ms * 1e-3) / 1e9 / peak},
+        "phase_ms": pm,
+        "per_update_ms": {"what": "add_view (1 view, incremental) + finalize, L2 flushed",
+                          "p50": float(np.percentile(upd, 50)),
+                          "p99": float(np.percentile(upd, 99))},
+        "active_updates_per_s": world * n_active * S / (ms * 1e-3),
+        "e2e": {"value": world * N * S / (e2e_ms * 1e-3), "unit": UNIT,
+                "ms_per_step": e2e_ms, "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": int(launches_per_step * args.steps),
+        "clocks": clk,
+        "wall_s_timed": t_wall,
+    }
+    fu.close()
+    return res, wl
+
+
+def run(args):
+    rank = _env_int("RANK", 0)
+    world = _env_int("WORLD_SIZE", 1)
+    local_rank = _env_int("LOCAL_RANK", 0)
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        return run_reference(args)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    res, wl = run_ours(args, rank, world, local_rank)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        full_s, det = oracle_rate(wl, args.cpu_seconds)
+        N = res["config"]["voxels_nominal"]
+        res["cpu_baseline"] = {
+            "value": N * wl.n_views / full_s, "unit": UNIT, "cores": det["cores"],
+            "kind": "oracle",
+            "sample": (f"{det['sample_voxels']} of {det['active_voxels']} active voxels x "
+                       f"{wl.n_views} views + {det['sample_points']} points, extrapolated "
+                       f"to the full step"),
+            "seconds": det["fuse_s"] + det["label_s"]}
+    if rank == 0:
+        print(json.dumps(res), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def run_reference(args):
+    wl = make_workload(args.workload)
+    per_step = max(1.0, min(10.0, 150.0 / max(1, args.steps + args.warmup)))
+    times, det = [], None
+    for k in range(args.warmup + args.steps):
+        full_s, det = oracle_rate(wl, per_step, seed=k)
+        if k >= args.warmup:
+            times.append(full_s)
+    N = wl.n_voxels
+    ms = float(np.mean(times)) * 1e3
+    v = N * wl.n_views / (ms * 1e-3)
+    sample = (f"each step: {det['sample_voxels']} of {det['active_voxels']} active voxels x "
+              f"{wl.n_views} views + {det['sample_points']} points, extrapolated to the full "
+              f"step")
+    res = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": 0,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic (seeded ray-cast scene; no dataset)",
+           "config": {"workload": args.workload, "description": WORKLOADS[args.workload]},
+           "cpu_baseline": {"value": v, "unit": UNIT, "cores": det["cores"], "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(res), flush=True)
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="forward-dense-256")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    args = ap.parse_args(argv)
+    args.warmup = max(3, args.warmup)  # at least 3 untimed warm-up steps
+    return run(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

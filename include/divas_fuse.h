@@ -1,0 +1,224 @@
+/*
+ * divas_fuse.h -- C ABI of the depth-weighted multi-view voxel fusion
+ * (DivAS, arXiv 2601.04860) on NVIDIA B300 (sm_103a).
+ *
+ * The operation (Sec. 3.5 "Shared voxel-voting concept"; Eq. compact-fusion,
+ * Eq. gs-depthweight, Eq. vmask; the thick-path algorithms of Appendix A.2
+ * "Thick-Structure Segmentation via Depth-Weighted Voxel Aggregation" and
+ * Appendix B.5 "Thick-Structure Segmentation for 2DGS"): for every voxel v
+ * of an occupied set (centre x_v, edge h_v) and every view i in order,
+ *
+ *   p = R_i x_v + t_i;  skip unless p_z > z_near
+ *   u = fx p_x/p_z + cx, v = fy p_y/p_z + cy; skip unless 0 <= u < W, 0 <= v < H
+ *   D = depth_i[floor v][floor u], m = mask_i[floor v][floor u]
+ *   skip unless D is finite and > 0, and m >= tau_mask
+ *   Delta = gamma h_v, e = p_z - D; skip unless |e| <= Delta
+ *   w = exp(-alpha1 (e/Delta)^2);  W += m w;  Z += w;  bits |= 1 << i
+ *
+ * then P = W/Z (Z > eps, else 0), seg = P >= tau_cons, vmask = seg ? bits : 0,
+ * and points are labelled by the seg bit of the voxel containing them
+ * (Eq. pass1).  Arithmetic is FP32 with a compensated depth residual; see
+ * the package documentation for the error analysis.
+ *
+ * Conventions
+ *   - Grid: voxel (i, j, k) centre = origin + (idx + 1/2) h; linear index
+ *     (k g + j) g + i (x fastest).  A contracted grid covers contracted space
+ *     [-2, 2]^3 (unbounded scenes): centres are uncontracted with
+ *     x = c / (|c| (2 - |c|)) for 1 < |c| < 2 (x = c inside the unit ball),
+ *     h_v = h / (2 - |c|)^2 there; voxels with |c| >= 2 never vote.  Points
+ *     are contracted with (2 - 1/|x|) x/|x| before lookup.
+ *   - Camera: OpenCV world->camera (x right, y down, z forward), R row-major;
+ *     pixel (i, j) covers [i, i+1) x [j, j+1); rasters are row-major H x W.
+ *   - Depth: planar camera-Z, float32; +inf, NaN or <= 0 means no surface.
+ *   - Views of one context are numbered 0, 1, 2, ... in the order they are
+ *     added; bit i of vmask is view i (views from 32 on vote but set no bit).
+ *
+ * Ownership and streams
+ *   Every pointer argument marked "device" is a CUDA device pointer owned by
+ *   the caller, which must keep it valid until the work queued on `stream`
+ *   has consumed it (the usual CUDA asynchronous contract).  Host structs
+ *   are copied during the call.  `stream` is a cudaStream_t (NULL = legacy
+ *   default stream).  The context owns its device state (accumulators,
+ *   active list, occupancy rank structure, seg bitfield).  Calls on one
+ *   context must not run concurrently from several host threads.
+ *
+ * Errors
+ *   Every call returns a divas_status and never aborts.  Invalid arguments
+ *   return DIVAS_E_INVALID before any work is queued; CUDA launch or
+ *   allocation failures return DIVAS_E_CUDA / DIVAS_E_OOM.  Conditions found
+ *   on the device (a sparse coordinate outside the grid, an occupied set
+ *   larger than the context's capacity) are recorded in a device status
+ *   word and returned by the next call that synchronises (divas_fuse_finalize
+ *   with a non-NULL n_seg_host, or divas_fuse_sync).  divas_last_error gives
+ *   a message for the last failing call on the context.
+ */
+#ifndef DIVAS_FUSE_H
+#define DIVAS_FUSE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct divas_ctx divas_ctx;
+
+typedef enum {
+    DIVAS_OK = 0,
+    DIVAS_E_INVALID = 1,  /* bad argument; nothing was queued */
+    DIVAS_E_OOM = 2,      /* device allocation failed */
+    DIVAS_E_CUDA = 3,     /* a CUDA call failed (message in divas_last_error) */
+    DIVAS_E_TIMEOUT = 4,  /* a bounded device-side wait expired */
+    DIVAS_E_STATE = 5,    /* call not valid in the context's current state */
+    DIVAS_E_CAPACITY = 6  /* occupied set larger than the context's capacity */
+} divas_status;
+
+typedef enum {
+    DIVAS_MASK_F32 = 0,      /* float32 probability in [0, 1] */
+    DIVAS_MASK_F16 = 1,      /* IEEE binary16 probability (widened exactly) */
+    DIVAS_MASK_LOGIT_F32 = 2 /* float32 logit l; m = 1/(1+exp(-l)); gate l >= logit(tau_mask) */
+} divas_mask_t;
+
+/* Constants of the thick path.  Defaults (divas_default_params): tau_mask 0.5
+ * (thick-path entry m >= 0.5, Algorithms A.2/B.5), gamma 1.0 and tau_cons 0.5
+ * (Table gs-hyperparams), alpha1 0.5 and eps 1e-12 (the paper gives no
+ * values), z_near 1e-6. */
+typedef struct {
+    float tau_mask, gamma, alpha1, tau_cons, eps, z_near;
+    uint32_t flags; /* reserved, 0 */
+} divas_params;
+
+typedef struct {
+    int32_t kind;       /* 0: dense prior (occ_dense), 1: sparse prior (coords) */
+    int32_t g;          /* voxels per side, 1 <= g <= 1024 */
+    float origin[3], h; /* voxel (i,j,k) centre = origin + (idx + 1/2) h, h > 0 */
+    int32_t contracted; /* 1: the grid lives in contracted space (see above) */
+} divas_grid;
+
+typedef struct {
+    int32_t W, H;       /* raster size, 1..65535 each */
+    float fx, fy, cx, cy;
+    float R[9], t[3];   /* world -> camera, row-major */
+} divas_camera;
+
+typedef struct {
+    divas_camera cam;
+    const float* depth; /* device, H x W float32 planar depth */
+    const void* mask;   /* device, H x W, element type from mask_type */
+    int32_t mask_type;  /* divas_mask_t */
+    int32_t reserved;
+} divas_view;
+
+/* Largest number of views one divas_fuse_add_views call accepts. */
+#define DIVAS_MAX_VIEWS_PER_CALL 32
+
+void divas_default_params(divas_params* out);
+
+/*
+ * Create a context for one occupied set and build its active list (the
+ * occupancy-prior gate and active-voxel list of Sec. 3.5 "Occupancy by
+ * Morton-scattered opacity" and Appendix B.1).
+ *   kind 0: occ_dense = device g^3 uint8 (x fastest), nonzero = occupied;
+ *           coords must be NULL.
+ *   kind 1: coords = device n_coords x 3 int32 (i, j, k); duplicates are
+ *           merged; occ_dense must be NULL.
+ * The active list is ordered by ascending linear index.  Allocates device
+ * memory and synchronises `stream` once (to size the active arrays).
+ */
+divas_status divas_fuse_init(divas_ctx** out, const divas_grid* grid, const uint8_t* occ_dense,
+                             const int32_t* coords, int64_t n_coords, const divas_params* params,
+                             void* stream);
+
+/* Rebuild the active list from a new prior of the same kind and grid, reusing
+ * the context's memory (no allocation, no synchronisation); resets W, Z, bits
+ * and the view count.  If the new occupied set exceeds the capacity sized at
+ * init, the excess voxels are dropped and DIVAS_E_CAPACITY is reported by the
+ * next synchronising call. */
+divas_status divas_fuse_set_occupancy(divas_ctx* ctx, const uint8_t* occ_dense,
+                                      const int32_t* coords, int64_t n_coords, void* stream);
+
+/* Fold one view into the accumulators (incremental update). */
+divas_status divas_fuse_add_view(divas_ctx* ctx, const divas_camera* cam, const float* depth,
+                                 const void* mask, int32_t mask_type, void* stream);
+
+/* Fold n_views (1..DIVAS_MAX_VIEWS_PER_CALL) views in index order in one
+ * launch.  The result is bitwise identical to n_views add_view calls. */
+divas_status divas_fuse_add_views(divas_ctx* ctx, const divas_view* views, int32_t n_views,
+                                  void* stream);
+
+/*
+ * Normalise and threshold (Eq. compact-fusion, V_seg = {P >= tau_cons}).
+ *   score_out    device float32: dense kind -> g^3 (0 for unoccupied voxels);
+ *                sparse kind -> n_active, in active-list order.  Nullable.
+ *   seg_bits_out device uint32, ceil(g^3 / 32) words, bit (lin & 31) of word
+ *                (lin >> 5) = seg of voxel lin (0 for unoccupied).  Nullable.
+ *   vmask_out    device uint32, n_active, in active-list order.  Nullable.
+ *   n_seg_host   host int64: number of segmented voxels.  Nullable; non-NULL
+ *                synchronises the stream and reports device-side errors.
+ * The context keeps its own seg bitfield for divas_label_points.
+ */
+divas_status divas_fuse_finalize(divas_ctx* ctx, float* score_out, uint32_t* seg_bits_out,
+                                 uint32_t* vmask_out, int64_t* n_seg_host, void* stream);
+
+/* Pass 1 labels (Eq. pass1): labels_out[i] = seg bit of the voxel containing
+ * point i (device n x 3 float32), 0 outside the grid (half-open box), for NaN,
+ * or for unoccupied voxels.  Uses the seg bitfield of the last finalize. */
+divas_status divas_label_points(divas_ctx* ctx, const float* xyz, int64_t n, uint8_t* labels_out,
+                                void* stream);
+
+/* W = Z = bits = 0 and view count 0 (the active list is kept). */
+divas_status divas_fuse_reset(divas_ctx* ctx, void* stream);
+
+/* Wait for the context's queued work and report device-side errors. */
+divas_status divas_fuse_sync(divas_ctx* ctx, void* stream);
+
+/* Number of active voxels (host value; exact after init, capacity-bounded after
+ * set_occupancy until the next synchronising call). */
+int64_t divas_fuse_n_active(const divas_ctx* ctx);
+
+/* Number of views folded in so far. */
+int32_t divas_fuse_n_views(const divas_ctx* ctx);
+
+/* Device n_active x 3 int32 (i, j, k) of the active list, in its order. */
+divas_status divas_fuse_active_coords(divas_ctx* ctx, int32_t* coords_out, void* stream);
+
+/* Export / import the accumulator state (checkpoint, eviction): device arrays
+ * of n_active float32 W, float32 Z and uint32 bits, in active-list order. */
+divas_status divas_fuse_export_state(divas_ctx* ctx, float* W_out, float* Z_out,
+                                     uint32_t* bits_out, void* stream);
+divas_status divas_fuse_import_state(divas_ctx* ctx, const float* W_in, const float* Z_in,
+                                     const uint32_t* bits_in, int32_t n_views, void* stream);
+
+/*
+ * Adjoint of the fusion for a voxel-space cotangent (derived from Eq.
+ * gs-depthweight and Eq. compact-fusion with the gates held fixed):
+ *   dP/dm = w/Z, dP/dw = (m - P)/Z, dw/dD = w 2 alpha1 e / Delta^2,
+ *   dm/dl = m (1 - m) for logit masks (1 for probability masks).
+ * grad_score: device float32 dL/dP, dense g^3 (dense kind) or n_active
+ * (sparse kind).  views: the same views, in the same order, that were folded
+ * in (view k of the call is view k of the context).  grad_mask[k] and
+ * grad_depth[k]: device float32 H x W rasters, accumulated into (atomic adds;
+ * the caller zeroes them); either array of pointers, or any entry, may be
+ * NULL to skip it.  Projections are recomputed per view; W and Z come from
+ * the context, so call after the views were folded in.
+ */
+divas_status divas_fuse_backward(divas_ctx* ctx, const divas_view* views, int32_t n_views,
+                                 const float* grad_score, float* const* grad_mask,
+                                 float* const* grad_depth, void* stream);
+
+/* Test hook: pixel index iy*W + ix that each active voxel projects to in a
+ * camera, or -1 when it is behind z_near or out of frame (device n_active int32). */
+divas_status divas_debug_project(divas_ctx* ctx, const divas_camera* cam, int32_t* pix_out,
+                                 void* stream);
+
+void divas_fuse_destroy(divas_ctx* ctx);
+
+/* Message of the last failing call on ctx (valid until the next call on ctx);
+ * with ctx == NULL, the last failure of divas_fuse_init on this thread. */
+const char* divas_last_error(const divas_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DIVAS_FUSE_H */

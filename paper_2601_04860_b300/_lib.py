@@ -1,0 +1,103 @@
+"""ctypes binding of ``libdivas_fuse.so`` (argument marshalling only).
+
+The structs mirror ``include/divas_fuse.h``.  Loading fails loudly when the
+library has not been built: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libdivas_fuse.so")
+
+DIVAS_OK = 0
+STATUS_NAMES = {0: "DIVAS_OK", 1: "DIVAS_E_INVALID", 2: "DIVAS_E_OOM", 3: "DIVAS_E_CUDA",
+                4: "DIVAS_E_TIMEOUT", 5: "DIVAS_E_STATE", 6: "DIVAS_E_CAPACITY"}
+MASK_F32 = 0
+MASK_F16 = 1
+MASK_LOGIT_F32 = 2
+MAX_VIEWS_PER_CALL = 32
+
+
+class DivasParams(ctypes.Structure):
+    _fields_ = [("tau_mask", ctypes.c_float), ("gamma", ctypes.c_float),
+                ("alpha1", ctypes.c_float), ("tau_cons", ctypes.c_float),
+                ("eps", ctypes.c_float), ("z_near", ctypes.c_float), ("flags", ctypes.c_uint32)]
+
+
+class DivasGrid(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("g", ctypes.c_int32), ("origin", ctypes.c_float * 3),
+                ("h", ctypes.c_float), ("contracted", ctypes.c_int32)]
+
+
+class DivasCamera(ctypes.Structure):
+    _fields_ = [("W", ctypes.c_int32), ("H", ctypes.c_int32), ("fx", ctypes.c_float),
+                ("fy", ctypes.c_float), ("cx", ctypes.c_float), ("cy", ctypes.c_float),
+                ("R", ctypes.c_float * 9), ("t", ctypes.c_float * 3)]
+
+
+class DivasView(ctypes.Structure):
+    _fields_ = [("cam", DivasCamera), ("depth", ctypes.c_void_p), ("mask", ctypes.c_void_p),
+                ("mask_type", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class DivasError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+# name -> (restype, argtypes)
+_P = ctypes.c_void_p
+_SIGS = {
+    "divas_default_params": (None, [ctypes.POINTER(DivasParams)]),
+    "divas_fuse_init": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.POINTER(DivasGrid), _P, _P,
+                                       ctypes.c_int64, ctypes.POINTER(DivasParams), _P]),
+    "divas_fuse_set_occupancy": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64, _P]),
+    "divas_fuse_add_view": (ctypes.c_int, [_P, ctypes.POINTER(DivasCamera), _P, _P,
+                                           ctypes.c_int32, _P]),
+    "divas_fuse_add_views": (ctypes.c_int, [_P, ctypes.POINTER(DivasView), ctypes.c_int32, _P]),
+    "divas_fuse_finalize": (ctypes.c_int, [_P, _P, _P, _P, ctypes.POINTER(ctypes.c_int64), _P]),
+    "divas_label_points": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, _P]),
+    "divas_fuse_reset": (ctypes.c_int, [_P, _P]),
+    "divas_fuse_sync": (ctypes.c_int, [_P, _P]),
+    "divas_fuse_n_active": (ctypes.c_int64, [_P]),
+    "divas_fuse_n_views": (ctypes.c_int32, [_P]),
+    "divas_fuse_active_coords": (ctypes.c_int, [_P, _P, _P]),
+    "divas_fuse_export_state": (ctypes.c_int, [_P, _P, _P, _P, _P]),
+    "divas_fuse_import_state": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int32, _P]),
+    "divas_fuse_backward": (ctypes.c_int, [_P, ctypes.POINTER(DivasView), ctypes.c_int32, _P,
+                                           ctypes.POINTER(_P), ctypes.POINTER(_P), _P]),
+    "divas_debug_project": (ctypes.c_int, [_P, ctypes.POINTER(DivasCamera), _P, _P]),
+    "divas_fuse_destroy": (None, [_P]),
+    "divas_last_error": (ctypes.c_char_p, [_P]),
+}
+
+EXPORTED = tuple(_SIGS)
+
+
+def load(path: str = LIB_PATH):
+    """Load the CUDA library once; raises if it is missing (no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(
+            f"{path} is missing: build the CUDA library first (python -c 'import "
+            "__graft_entry__ as g; g.build()'); there is no CPU fallback")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def check(status: int, ctx=None):
+    if status != DIVAS_OK:
+        msg = load().divas_last_error(ctx)
+        raise DivasError(status, msg.decode() if msg else "")

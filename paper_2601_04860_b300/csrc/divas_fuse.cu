@@ -1,0 +1,954 @@
+// divas_fuse.cu -- kernels and C ABI of the depth-weighted voxel fusion.
+//
+// Data layout in device memory (one context = one occupied set):
+//   occ_bits[ceil(g^3/32)]     occupancy prior as a bitfield, bit lin of the grid
+//   word_prefix[words]         exclusive prefix of popc(occ_bits): the rank structure
+//                              that maps a dense voxel to its active slot
+//   active[cap]                ascending linear indices of the occupied voxels
+//   W[cap], Z[cap], bits[cap]  accumulators of Eq. vmask, structure of arrays
+//   seg_bits[words]            segmentation bitfield B^seg of the last finalize
+//
+// Kernels: occupancy -> bits (dense) or scatter (sparse); per-block popcounts,
+// a one-block scan and an emit pass build the active list (the active-voxel list
+// of Sec. 3.5 / Appendix B.1); the fusion kernel walks the active list with a
+// grid-stride loop and folds up to 32 views per launch; finalize writes the
+// dense score grid with 128-bit stores (or the per-active scores), the seg
+// bitfield with warp-assembled words and the view masks; labels look points up
+// in the seg bitfield (Eq. pass1); the adjoint recomputes every vote and
+// scatters its derivatives into pixel rasters.
+#include "divas_fuse.h"
+
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "fuse_math.cuh"
+
+using namespace divas;
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kWordsPerThread = 4;                       // compaction
+constexpr int kWordsPerBlock = kThreads * kWordsPerThread;
+constexpr int32_t kStatusBadCoord = 1;
+constexpr int32_t kStatusCapacity = 2;
+
+struct BackPtrs {
+    float* gm[kMaxViews];
+    float* gd[kMaxViews];
+};
+
+// ---------------------------------------------------------------------------
+// compaction
+// ---------------------------------------------------------------------------
+// dense uint8 prior -> bitfield (one thread per 32-voxel word)
+__global__ void __launch_bounds__(kThreads) k_occ_bits(const uint8_t* __restrict__ occ,
+                                                       int64_t n_cells, int64_t n_words,
+                                                       uint32_t* __restrict__ bits) {
+    for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < n_words;
+         w += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t base = w * 32;
+        uint32_t word = 0;
+        if (base + 32 <= n_cells && ((reinterpret_cast<uintptr_t>(occ + base) & 15) == 0)) {
+            const uint4 a = __ldg(reinterpret_cast<const uint4*>(occ + base));
+            const uint4 b = __ldg(reinterpret_cast<const uint4*>(occ + base) + 1);
+            const uint32_t v[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+#pragma unroll
+                for (int s = 0; s < 4; ++s)
+                    word |= (((v[q] >> (8 * s)) & 0xffu) != 0u ? 1u : 0u) << (4 * q + s);
+        } else {
+            for (int s = 0; s < 32 && base + s < n_cells; ++s)
+                word |= (occ[base + s] != 0 ? 1u : 0u) << s;
+        }
+        bits[w] = word;
+    }
+}
+
+// sparse coordinates -> bitfield (atomic OR; duplicates merge)
+__global__ void __launch_bounds__(kThreads) k_scatter_coords(const int32_t* __restrict__ coords,
+                                                             int64_t n, int32_t g,
+                                                             uint32_t* __restrict__ bits,
+                                                             int32_t* __restrict__ status) {
+    for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < n;
+         a += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t i = __ldg(coords + 3 * a), j = __ldg(coords + 3 * a + 1),
+                      k = __ldg(coords + 3 * a + 2);
+        if (i < 0 || j < 0 || k < 0 || i >= g || j >= g || k >= g) {
+            atomicOr(status, kStatusBadCoord);
+            continue;
+        }
+        const int64_t lin = ((int64_t)k * g + j) * g + i;
+        atomicOr(bits + (lin >> 5), 1u << (lin & 31));
+    }
+}
+
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* total) {
+    __shared__ uint32_t warp_sums[kThreads / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_sums[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t s = lane < kThreads / 32 ? warp_sums[lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += y;
+        }
+        if (lane < kThreads / 32) warp_sums[lane] = s;
+    }
+    __syncthreads();
+    const uint32_t warp_off = warp > 0 ? warp_sums[warp - 1] : 0u;
+    if (total) *total = warp_sums[kThreads / 32 - 1];
+    __syncthreads();
+    return warp_off + x - v;
+}
+
+// per-block popcount of kWordsPerBlock words
+__global__ void __launch_bounds__(kThreads) k_block_popc(const uint32_t* __restrict__ bits,
+                                                         int64_t n_words,
+                                                         uint32_t* __restrict__ block_sums) {
+    const int64_t base = (int64_t)blockIdx.x * kWordsPerBlock + threadIdx.x * kWordsPerThread;
+    uint32_t c = 0;
+#pragma unroll
+    for (int q = 0; q < kWordsPerThread; ++q)
+        if (base + q < n_words) c += __popc(__ldg(bits + base + q));
+    uint32_t total;
+    block_exclusive_scan(c, &total);
+    if (threadIdx.x == 0) block_sums[blockIdx.x] = total;
+}
+
+// one block: exclusive scan of the block sums; d_n = min(total, cap)
+__global__ void __launch_bounds__(kThreads) k_scan_blocks(uint32_t* __restrict__ block_sums,
+                                                          int32_t n_blocks, int64_t cap,
+                                                          int64_t* __restrict__ d_total,
+                                                          int32_t* __restrict__ d_n,
+                                                          int32_t* __restrict__ status) {
+    uint32_t carry = 0;
+    for (int32_t base = 0; base < n_blocks; base += kThreads) {
+        const int32_t b = base + threadIdx.x;
+        const uint32_t v = b < n_blocks ? block_sums[b] : 0u;
+        uint32_t tot;
+        const uint32_t ex = block_exclusive_scan(v, &tot);
+        if (b < n_blocks) block_sums[b] = carry + ex;
+        carry += tot;
+    }
+    if (threadIdx.x == 0) {
+        *d_total = carry;
+        const int64_t n = carry < (uint64_t)cap ? (int64_t)carry : cap;
+        *d_n = (int32_t)n;
+        if ((int64_t)carry > cap) atomicOr(status, kStatusCapacity);
+    }
+}
+
+// rank structure and active list
+__global__ void __launch_bounds__(kThreads) k_emit(const uint32_t* __restrict__ bits,
+                                                   int64_t n_words,
+                                                   const uint32_t* __restrict__ block_off,
+                                                   int64_t cap, uint32_t* __restrict__ word_prefix,
+                                                   int32_t* __restrict__ active) {
+    const int64_t base = (int64_t)blockIdx.x * kWordsPerBlock + threadIdx.x * kWordsPerThread;
+    uint32_t w[kWordsPerThread];
+    uint32_t c = 0;
+#pragma unroll
+    for (int q = 0; q < kWordsPerThread; ++q) {
+        w[q] = base + q < n_words ? __ldg(bits + base + q) : 0u;
+        c += __popc(w[q]);
+    }
+    uint32_t off = block_off[blockIdx.x] + block_exclusive_scan(c, nullptr);
+#pragma unroll
+    for (int q = 0; q < kWordsPerThread; ++q) {
+        if (base + q >= n_words) break;
+        word_prefix[base + q] = off;
+        uint32_t m = w[q];
+        while (m) {
+            const int b = __ffs(m) - 1;
+            m &= m - 1;
+            if ((int64_t)off < cap) active[off] = (int32_t)((base + q) * 32 + b);
+            ++off;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// fusion
+// ---------------------------------------------------------------------------
+template <bool kAccumulate>
+__global__ void __launch_bounds__(kThreads) k_fuse(const int32_t* __restrict__ active,
+                                                   const int32_t* __restrict__ d_n, GridC G,
+                                                   FuseC F, const __grid_constant__ ViewBatch VB,
+                                                   float* __restrict__ W,
+                                                   float* __restrict__ Z,
+                                                   uint32_t* __restrict__ bits) {
+    const int32_t n = *d_n;
+    for (int32_t a = blockIdx.x * blockDim.x + threadIdx.x; a < n; a += gridDim.x * blockDim.x) {
+        const VoxelGeom vg = voxel_geom(__ldg(active + a), G, F.gamma);
+        float w = 0.f, z = 0.f;
+        uint32_t b = 0;
+        if (kAccumulate) {
+            w = W[a];
+            z = Z[a];
+            b = bits[a];
+        }
+        if (vg.ok)
+            for (int32_t v = 0; v < VB.n; ++v) vote(VB.v[v], vg, F, w, z, b);
+        W[a] = w;
+        Z[a] = z;
+        bits[a] = b;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// finalize
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float score_of(float w, float z, float eps) {
+    return z > eps ? __fdiv_rn(w, z) : 0.f;
+}
+
+// dense: 4 voxels per thread, 8 threads per occupancy word
+__global__ void __launch_bounds__(kThreads) k_finalize_dense(
+    const uint32_t* __restrict__ occ_bits, const uint32_t* __restrict__ word_prefix,
+    const int32_t* __restrict__ d_n, int64_t n_cells, const float* __restrict__ W,
+    const float* __restrict__ Z, const uint32_t* __restrict__ bits, float eps, float tau_cons,
+    float* __restrict__ score_out, uint32_t* __restrict__ seg_bits, uint32_t* __restrict__ seg_out,
+    uint32_t* __restrict__ vmask_out, unsigned long long* __restrict__ d_nseg) {
+    const int32_t n = *d_n;
+    const int64_t n_quads = (n_cells + 3) / 4;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    // whole warps iterate together so that the shuffles below stay converged
+    for (int64_t t0 = (int64_t)blockIdx.x * blockDim.x; t0 < n_quads; t0 += stride) {
+        const int64_t t = t0 + threadIdx.x;
+        const bool live = t < n_quads;
+        const int64_t v0 = 4 * t;
+        const int64_t wi = v0 >> 5;
+        const int b0 = (int)(v0 & 31);
+        uint32_t word = 0, pre = 0;
+        if (live) {
+            word = __ldg(occ_bits + wi);
+            pre = __ldg(word_prefix + wi);
+        }
+        float p[4] = {0.f, 0.f, 0.f, 0.f};
+        uint32_t nib = 0;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int b = b0 + q;
+            if (live && ((word >> b) & 1u)) {
+                const uint32_t slot = pre + __popc(word & ((1u << b) - 1u));
+                if ((int64_t)slot < n) {
+                    const float s = score_of(W[slot], Z[slot], eps);
+                    const bool seg = s >= tau_cons;
+                    p[q] = s;
+                    nib |= (seg ? 1u : 0u) << q;
+                    if (vmask_out) vmask_out[slot] = seg ? bits[slot] : 0u;
+                }
+            }
+        }
+        if (live && score_out) {
+            if (v0 + 4 <= n_cells && ((reinterpret_cast<uintptr_t>(score_out + v0) & 15) == 0)) {
+                __stcs(reinterpret_cast<float4*>(score_out + v0), make_float4(p[0], p[1], p[2], p[3]));
+            } else {
+                for (int q = 0; q < 4 && v0 + q < n_cells; ++q) score_out[v0 + q] = p[q];
+            }
+        }
+        uint32_t segw = nib << b0;
+        segw |= __shfl_xor_sync(0xffffffffu, segw, 1);
+        segw |= __shfl_xor_sync(0xffffffffu, segw, 2);
+        segw |= __shfl_xor_sync(0xffffffffu, segw, 4);
+        uint32_t cnt = 0;
+        if (live && (threadIdx.x & 7) == 0) {
+            seg_bits[wi] = segw;
+            if (seg_out) seg_out[wi] = segw;
+            cnt = __popc(segw);
+        }
+        if (d_nseg) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+            if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(d_nseg, (unsigned long long)cnt);
+        }
+    }
+}
+
+// sparse: one thread per active voxel; seg bitfields were zeroed before
+__global__ void __launch_bounds__(kThreads) k_finalize_sparse(
+    const int32_t* __restrict__ active, const int32_t* __restrict__ d_n,
+    const float* __restrict__ W, const float* __restrict__ Z, const uint32_t* __restrict__ bits,
+    float eps, float tau_cons, float* __restrict__ score_out, uint32_t* __restrict__ seg_bits,
+    uint32_t* __restrict__ seg_out, uint32_t* __restrict__ vmask_out,
+    unsigned long long* __restrict__ d_nseg) {
+    const int32_t n = *d_n;
+    for (int32_t a0 = blockIdx.x * blockDim.x; a0 < n; a0 += gridDim.x * blockDim.x) {
+        const int32_t a = a0 + threadIdx.x;
+        bool seg = false;
+        if (a < n) {
+            const float s = score_of(W[a], Z[a], eps);
+            seg = s >= tau_cons;
+            if (score_out) __stcs(score_out + a, s);
+            if (vmask_out) vmask_out[a] = seg ? bits[a] : 0u;
+            if (seg) {
+                const int32_t lin = __ldg(active + a);
+                atomicOr(seg_bits + (lin >> 5), 1u << (lin & 31));
+                if (seg_out) atomicOr(seg_out + (lin >> 5), 1u << (lin & 31));
+            }
+        }
+        if (d_nseg) {
+            const uint32_t cnt = __popc(__ballot_sync(0xffffffffu, seg));
+            if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(d_nseg, (unsigned long long)cnt);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// labels (Eq. pass1)
+// ---------------------------------------------------------------------------
+// floor of hi + lo (|lo| <= ulp(hi) / 2)
+__device__ __forceinline__ float floor_df(float hi, float lo) {
+    const float f = floorf(hi);
+    return (f == hi && lo < 0.f) ? f - 1.f : f;
+}
+
+__global__ void __launch_bounds__(kThreads) k_label(const float* __restrict__ xyz, int64_t n,
+                                                    GridC G, const uint32_t* __restrict__ seg_bits,
+                                                    uint8_t* __restrict__ labels) {
+    for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < n;
+         a += (int64_t)gridDim.x * blockDim.x) {
+        float xh[3] = {__ldg(xyz + 3 * a), __ldg(xyz + 3 * a + 1), __ldg(xyz + 3 * a + 2)};
+        float xl[3] = {0.f, 0.f, 0.f};
+        uint8_t lab = 0;
+        if (!(isnan(xh[0]) || isnan(xh[1]) || isnan(xh[2]))) {
+            if (G.contracted) {
+                // r^2 = |x|^2 as hi + lo
+                float s = 0.f, e = 0.f;
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    float p, pe, t;
+                    two_prod(xh[q], xh[q], p, pe);
+                    two_sum(s, p, s, t);
+                    e = __fadd_rn(e, __fadd_rn(t, pe));
+                }
+                float n2h, n2l;
+                two_sum(s, e, n2h, n2l);
+                if ((n2h > 1.f) || (n2h == 1.f && n2l > 0.f)) {
+                    if (n2h > 1e30f) {  // |x| beyond 1e15: contract(x) = 2 x / |x| in FP32
+                        const float inv = __frsqrt_rn(n2h);
+                        // not reached by finite scenes; keeps the arithmetic finite
+#pragma unroll
+                        for (int q = 0; q < 3; ++q) { xh[q] = 2.f * xh[q] * inv; xl[q] = 0.f; }
+                    } else {
+                        const float rh = __fsqrt_rn(n2h);
+                        const float rl =
+                            __fdiv_rn(__fadd_rn(__fmaf_rn(-rh, rh, n2h), n2l), __fmul_rn(2.f, rh));
+                        // ir = 1 / r
+                        const float ih = __frcp_rn(rh);
+                        const float il = __fmul_rn(
+                            ih, __fsub_rn(__fmaf_rn(-ih, rh, 1.f), __fmul_rn(ih, rl)));
+                        // tt = 2 - ir
+                        float th, tl;
+                        two_sum(2.f, -ih, th, tl);
+                        tl = __fsub_rn(tl, il);
+                        two_sum(th, tl, th, tl);
+                        // sc = tt * ir
+                        float sh, sl;
+                        two_prod(th, ih, sh, sl);
+                        sl = __fadd_rn(sl, __fadd_rn(__fmul_rn(th, il), __fmul_rn(tl, ih)));
+                        two_sum(sh, sl, sh, sl);
+#pragma unroll
+                        for (int q = 0; q < 3; ++q) {
+                            float qh, ql;
+                            two_prod(xh[q], sh, qh, ql);
+                            ql = __fadd_rn(ql, __fmul_rn(xh[q], sl));
+                            two_sum(qh, ql, xh[q], xl[q]);
+                        }
+                    }
+                }
+            }
+            bool inside = true;
+            int32_t idx[3];
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                // s = (x - origin) / h as hi + lo
+                float dh, dl;
+                two_sum(xh[q], -G.origin[q], dh, dl);
+                dl = __fadd_rn(dl, xl[q]);
+                const float sh = __fdiv_rn(dh, G.h);
+                const float sl = __fdiv_rn(__fadd_rn(__fmaf_rn(-sh, G.h, dh), dl), G.h);
+                const float f = floor_df(sh, sl);
+                if (!(f >= 0.f && f < (float)G.g)) inside = false;
+                idx[q] = inside ? (int32_t)f : 0;
+            }
+            if (inside) {
+                const int64_t lin = ((int64_t)idx[2] * G.g + idx[1]) * G.g + idx[0];
+                lab = (uint8_t)((__ldg(seg_bits + (lin >> 5)) >> (lin & 31)) & 1u);
+            }
+        }
+        labels[a] = lab;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// adjoint
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads) k_backward(
+    const int32_t* __restrict__ active, const int32_t* __restrict__ d_n, GridC G, FuseC F,
+    const __grid_constant__ ViewBatch VB, const __grid_constant__ BackPtrs BP,
+    const float* __restrict__ W, const float* __restrict__ Z,
+    const float* __restrict__ grad_score, int32_t dense) {
+    const int32_t n = *d_n;
+    for (int32_t a = blockIdx.x * blockDim.x + threadIdx.x; a < n; a += gridDim.x * blockDim.x) {
+        const int32_t lin = __ldg(active + a);
+        const float gP = __ldg(grad_score + (dense ? (int64_t)lin : (int64_t)a));
+        const float z = Z[a];
+        if (gP == 0.f || !(z > F.eps)) continue;
+        const float P = __fdiv_rn(W[a], z);
+        const VoxelGeom vg = voxel_geom(lin, G, F.gamma);
+        if (!vg.ok) continue;
+        const float gz = __fdiv_rn(gP, z);
+        const float k2 = __fmul_rn(__fmul_rn(2.f, F.alpha1), __fmul_rn(vg.invDelta, vg.invDelta));
+        for (int32_t v = 0; v < VB.n; ++v) {
+            Vote vt;
+            if (!eval_vote(VB.v[v], vg, F, vt)) continue;
+            if (BP.gm[v]) {
+                float dm = __fmul_rn(gz, vt.w);
+                if (VB.v[v].mask_type == kMaskLogit)
+                    dm = __fmul_rn(dm, __fmul_rn(vt.m, __fsub_rn(1.f, vt.m)));
+                atomicAdd(BP.gm[v] + vt.pix, dm);
+            }
+            if (BP.gd[v]) {
+                const float dw = __fmul_rn(__fmul_rn(vt.w, k2), vt.e);
+                atomicAdd(BP.gd[v] + vt.pix, __fmul_rn(__fmul_rn(gz, __fsub_rn(vt.m, P)), dw));
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// misc
+// ---------------------------------------------------------------------------
+__global__ void k_debug_project(const int32_t* __restrict__ active, const int32_t* __restrict__ d_n,
+                                GridC G, FuseC F, ViewC V, int32_t* __restrict__ pix_out) {
+    const int32_t n = *d_n;
+    for (int32_t a = blockIdx.x * blockDim.x + threadIdx.x; a < n; a += gridDim.x * blockDim.x) {
+        const VoxelGeom vg = voxel_geom(__ldg(active + a), G, F.gamma);
+        int32_t pix = -1;
+        float ph, pl;
+        if (!(vg.ok && project_voxel(V, vg, F.z_near, pix, ph, pl))) pix = -1;
+        pix_out[a] = pix;
+    }
+}
+
+__global__ void k_active_coords(const int32_t* __restrict__ active, const int32_t* __restrict__ d_n,
+                                int32_t g, int32_t* __restrict__ out) {
+    const int32_t n = *d_n;
+    for (int32_t a = blockIdx.x * blockDim.x + threadIdx.x; a < n; a += gridDim.x * blockDim.x) {
+        const int32_t lin = active[a];
+        out[3 * a] = lin % g;
+        out[3 * a + 1] = (lin / g) % g;
+        out[3 * a + 2] = lin / (g * g);
+    }
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+struct divas_ctx {
+    divas_grid grid;
+    divas_params params;
+    GridC G;
+    FuseC F;
+    int64_t n_cells = 0, n_words = 0;
+    int32_t n_cblocks = 0;  // compaction blocks
+    int64_t cap = 0;
+    int64_t n_active = 0;
+    int32_t n_views = 0;
+    int32_t sm_count = 148;
+    uint32_t* occ_bits = nullptr;
+    uint32_t* word_prefix = nullptr;
+    uint32_t* block_sums = nullptr;
+    uint32_t* seg_bits = nullptr;
+    int32_t* active = nullptr;
+    float* W = nullptr;
+    float* Z = nullptr;
+    uint32_t* bits = nullptr;
+    int32_t* d_n = nullptr;
+    int32_t* d_status = nullptr;
+    int64_t* d_total = nullptr;
+    unsigned long long* d_nseg = nullptr;
+    std::string err;
+};
+
+namespace {
+
+thread_local std::string g_init_error;
+
+divas_status fail(divas_ctx* c, divas_status st, const std::string& msg) {
+    if (c)
+        c->err = msg;
+    else
+        g_init_error = msg;
+    return st;
+}
+
+divas_status cuda_fail(divas_ctx* c, cudaError_t e, const char* where) {
+    return fail(c, e == cudaErrorMemoryAllocation ? DIVAS_E_OOM : DIVAS_E_CUDA,
+                std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define DIVAS_CUDA(ctx, call)                                   \
+    do {                                                        \
+        cudaError_t e_ = (call);                                \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
+    } while (0)
+
+#define DIVAS_LAUNCHED(ctx, what)                                  \
+    do {                                                           \
+        cudaError_t e_ = cudaGetLastError();                       \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, what);    \
+    } while (0)
+
+inline cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+int grid_for(int64_t items, int32_t sm_count, int per_sm = 16) {
+    int64_t b = (items + kThreads - 1) / kThreads;
+    const int64_t cap = (int64_t)sm_count * per_sm;
+    if (b > cap) b = cap;
+    if (b < 1) b = 1;
+    return (int)b;
+}
+
+bool finite_pos(float x) { return x > 0.f && x <= FLT_MAX; }
+
+divas_status check_camera(divas_ctx* c, const divas_camera* cam) {
+    if (!cam) return fail(c, DIVAS_E_INVALID, "camera is NULL");
+    if (cam->W <= 0 || cam->H <= 0 || cam->W > 65535 || cam->H > 65535 ||
+        (int64_t)cam->W * cam->H > INT32_MAX)
+        return fail(c, DIVAS_E_INVALID, "camera W/H must be in 1..65535 with W*H < 2^31");
+    for (int q = 0; q < 9; ++q)
+        if (!(fabsf(cam->R[q]) <= FLT_MAX)) return fail(c, DIVAS_E_INVALID, "camera R not finite");
+    for (int q = 0; q < 3; ++q)
+        if (!(fabsf(cam->t[q]) <= FLT_MAX)) return fail(c, DIVAS_E_INVALID, "camera t not finite");
+    if (!(fabsf(cam->fx) <= FLT_MAX && fabsf(cam->fy) <= FLT_MAX && fabsf(cam->cx) <= FLT_MAX &&
+          fabsf(cam->cy) <= FLT_MAX))
+        return fail(c, DIVAS_E_INVALID, "camera intrinsics not finite");
+    return DIVAS_OK;
+}
+
+ViewC make_view(const divas_camera& cam, const float* depth, const void* mask, int32_t mask_type,
+                int32_t index) {
+    ViewC v;
+    memcpy(v.R, cam.R, sizeof(v.R));
+    memcpy(v.t, cam.t, sizeof(v.t));
+    v.fx = cam.fx;
+    v.fy = cam.fy;
+    v.cx = cam.cx;
+    v.cy = cam.cy;
+    v.Wf = (float)cam.W;
+    v.Hf = (float)cam.H;
+    v.W = cam.W;
+    v.mask_type = mask_type;
+    v.bit = index < 32 ? (1u << index) : 0u;
+    v.pad = 0;
+    v.depth = depth;
+    v.mask = mask;
+    return v;
+}
+
+float logit_threshold(float tau) {
+    if (!(tau > 0.f)) return -INFINITY;
+    if (!(tau < 1.f)) return INFINITY;
+    return (float)log((double)tau / (1.0 - (double)tau));
+}
+
+// occupancy -> bits -> rank structure -> active list (no allocation)
+divas_status build_active(divas_ctx* c, const uint8_t* occ, const int32_t* coords, int64_t n_coords,
+                          cudaStream_t s) {
+    if (c->grid.kind == 0) {
+        k_occ_bits<<<grid_for(c->n_words, c->sm_count, 32), kThreads, 0, s>>>(occ, c->n_cells,
+                                                                             c->n_words, c->occ_bits);
+        DIVAS_LAUNCHED(c, "k_occ_bits");
+    } else {
+        DIVAS_CUDA(c, cudaMemsetAsync(c->occ_bits, 0, c->n_words * 4, s));
+        if (n_coords > 0) {
+            k_scatter_coords<<<grid_for(n_coords, c->sm_count, 32), kThreads, 0, s>>>(
+                coords, n_coords, c->grid.g, c->occ_bits, c->d_status);
+            DIVAS_LAUNCHED(c, "k_scatter_coords");
+        }
+    }
+    k_block_popc<<<c->n_cblocks, kThreads, 0, s>>>(c->occ_bits, c->n_words, c->block_sums);
+    DIVAS_LAUNCHED(c, "k_block_popc");
+    k_scan_blocks<<<1, kThreads, 0, s>>>(c->block_sums, c->n_cblocks, c->cap, c->d_total, c->d_n,
+                                         c->d_status);
+    DIVAS_LAUNCHED(c, "k_scan_blocks");
+    return DIVAS_OK;
+}
+
+divas_status emit_active(divas_ctx* c, cudaStream_t s) {
+    k_emit<<<c->n_cblocks, kThreads, 0, s>>>(c->occ_bits, c->n_words, c->block_sums, c->cap,
+                                             c->word_prefix, c->active);
+    DIVAS_LAUNCHED(c, "k_emit");
+    return DIVAS_OK;
+}
+
+divas_status read_status(divas_ctx* c, cudaStream_t s) {
+    int32_t st = 0;
+    int32_t n = 0;
+    DIVAS_CUDA(c, cudaMemcpyAsync(&st, c->d_status, 4, cudaMemcpyDeviceToHost, s));
+    DIVAS_CUDA(c, cudaMemcpyAsync(&n, c->d_n, 4, cudaMemcpyDeviceToHost, s));
+    DIVAS_CUDA(c, cudaStreamSynchronize(s));
+    c->n_active = n;
+    if (st) {
+        DIVAS_CUDA(c, cudaMemsetAsync(c->d_status, 0, 4, s));
+        if (st & kStatusBadCoord)
+            return fail(c, DIVAS_E_INVALID, "a sparse coordinate lies outside the grid (skipped)");
+        if (st & kStatusCapacity)
+            return fail(c, DIVAS_E_CAPACITY, "occupied set exceeds the context capacity (truncated)");
+    }
+    return DIVAS_OK;
+}
+
+void free_all(divas_ctx* c) {
+    void* ptrs[] = {c->occ_bits, c->word_prefix, c->block_sums, c->seg_bits, c->active, c->W,
+                    c->Z,        c->bits,        c->d_n,        c->d_status, c->d_total, c->d_nseg};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+}
+
+}  // namespace
+
+extern "C" {
+
+void divas_default_params(divas_params* out) {
+    if (!out) return;
+    out->tau_mask = 0.5f;
+    out->gamma = 1.0f;
+    out->alpha1 = 0.5f;
+    out->tau_cons = 0.5f;
+    out->eps = 1e-12f;
+    out->z_near = 1e-6f;
+    out->flags = 0;
+}
+
+divas_status divas_fuse_init(divas_ctx** out, const divas_grid* grid, const uint8_t* occ_dense,
+                             const int32_t* coords, int64_t n_coords, const divas_params* params,
+                             void* stream) {
+    if (!out) return fail(nullptr, DIVAS_E_INVALID, "out is NULL");
+    *out = nullptr;
+    if (!grid || !params) return fail(nullptr, DIVAS_E_INVALID, "grid or params is NULL");
+    if (grid->g < 1 || grid->g > 1024) return fail(nullptr, DIVAS_E_INVALID, "g must be in 1..1024");
+    if (!finite_pos(grid->h)) return fail(nullptr, DIVAS_E_INVALID, "h must be finite and > 0");
+    for (int q = 0; q < 3; ++q)
+        if (!(fabsf(grid->origin[q]) <= FLT_MAX))
+            return fail(nullptr, DIVAS_E_INVALID, "origin not finite");
+    if (grid->kind == 0) {
+        if (!occ_dense || coords) return fail(nullptr, DIVAS_E_INVALID, "dense kind needs occ_dense only");
+    } else if (grid->kind == 1) {
+        if (occ_dense || n_coords < 0 || (n_coords > 0 && !coords))
+            return fail(nullptr, DIVAS_E_INVALID, "sparse kind needs coords only");
+    } else {
+        return fail(nullptr, DIVAS_E_INVALID, "kind must be 0 (dense) or 1 (sparse)");
+    }
+    if (!(params->gamma > 0.f && params->gamma <= FLT_MAX) || !(params->alpha1 >= 0.f) ||
+        !(params->alpha1 <= FLT_MAX) || !(params->eps >= 0.f) || !(params->tau_mask == params->tau_mask) ||
+        !(params->tau_cons == params->tau_cons) || !(params->z_near == params->z_near))
+        return fail(nullptr, DIVAS_E_INVALID, "params out of range");
+
+    divas_ctx* c = new (std::nothrow) divas_ctx();
+    if (!c) return fail(nullptr, DIVAS_E_OOM, "host allocation failed");
+    c->grid = *grid;
+    c->params = *params;
+    c->G.origin[0] = grid->origin[0];
+    c->G.origin[1] = grid->origin[1];
+    c->G.origin[2] = grid->origin[2];
+    c->G.h = grid->h;
+    c->G.g = grid->g;
+    c->G.contracted = grid->contracted ? 1 : 0;
+    c->F.gamma = params->gamma;
+    c->F.alpha1 = params->alpha1;
+    c->F.tau_m = params->tau_mask;
+    c->F.logit_tau = logit_threshold(params->tau_mask);
+    c->F.z_near = params->z_near;
+    c->F.eps = params->eps;
+    c->F.tau_cons = params->tau_cons;
+    c->F.pad = 0;
+    c->n_cells = (int64_t)grid->g * grid->g * grid->g;
+    c->n_words = (c->n_cells + 31) / 32;
+    c->n_cblocks = (int32_t)((c->n_words + kWordsPerBlock - 1) / kWordsPerBlock);
+    cudaStream_t s = S(stream);
+    int dev = 0;
+    divas_status st = DIVAS_OK;
+    auto bail = [&](divas_status e) {
+        g_init_error = c->err;
+        free_all(c);
+        delete c;
+        return e;
+    };
+#define INIT_CUDA(call)                                                 \
+    do {                                                                \
+        cudaError_t e_ = (call);                                        \
+        if (e_ != cudaSuccess) return bail(cuda_fail(c, e_, #call));    \
+    } while (0)
+    INIT_CUDA(cudaGetDevice(&dev));
+    INIT_CUDA(cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, dev));
+    INIT_CUDA(cudaMalloc(&c->occ_bits, c->n_words * 4));
+    INIT_CUDA(cudaMalloc(&c->word_prefix, c->n_words * 4));
+    INIT_CUDA(cudaMalloc(&c->seg_bits, c->n_words * 4));
+    INIT_CUDA(cudaMalloc(&c->block_sums, ((int64_t)c->n_cblocks + 1) * 4));
+    INIT_CUDA(cudaMalloc(&c->d_n, 4));
+    INIT_CUDA(cudaMalloc(&c->d_status, 4));
+    INIT_CUDA(cudaMalloc(&c->d_total, 8));
+    INIT_CUDA(cudaMalloc(&c->d_nseg, 8));
+    INIT_CUDA(cudaMemsetAsync(c->d_status, 0, 4, s));
+    INIT_CUDA(cudaMemsetAsync(c->seg_bits, 0, c->n_words * 4, s));
+    c->cap = INT32_MAX;  // first pass only counts
+    st = build_active(c, occ_dense, coords, n_coords, s);
+    if (st != DIVAS_OK) return bail(st);
+    int64_t total = 0;
+    INIT_CUDA(cudaMemcpyAsync(&total, c->d_total, 8, cudaMemcpyDeviceToHost, s));
+    int32_t dst = 0;
+    INIT_CUDA(cudaMemcpyAsync(&dst, c->d_status, 4, cudaMemcpyDeviceToHost, s));
+    INIT_CUDA(cudaStreamSynchronize(s));
+    if (dst & kStatusBadCoord) {
+        c->err = "a sparse coordinate lies outside the grid";
+        return bail(DIVAS_E_INVALID);
+    }
+    if (total > INT32_MAX - 1) {
+        c->err = "occupied set too large";
+        return bail(DIVAS_E_INVALID);
+    }
+    c->n_active = total;
+    c->cap = total > 0 ? total : 1;
+    INIT_CUDA(cudaMalloc(&c->active, c->cap * 4));
+    INIT_CUDA(cudaMalloc(&c->W, c->cap * 4));
+    INIT_CUDA(cudaMalloc(&c->Z, c->cap * 4));
+    INIT_CUDA(cudaMalloc(&c->bits, c->cap * 4));
+    st = emit_active(c, s);
+    if (st != DIVAS_OK) return bail(st);
+    INIT_CUDA(cudaMemsetAsync(c->W, 0, c->cap * 4, s));
+    INIT_CUDA(cudaMemsetAsync(c->Z, 0, c->cap * 4, s));
+    INIT_CUDA(cudaMemsetAsync(c->bits, 0, c->cap * 4, s));
+#undef INIT_CUDA
+    *out = c;
+    return DIVAS_OK;
+}
+
+divas_status divas_fuse_set_occupancy(divas_ctx* c, const uint8_t* occ_dense, const int32_t* coords,
+                                      int64_t n_coords, void* stream) {
+    if (!c) return fail(nullptr, DIVAS_E_INVALID, "ctx is NULL");
+    if (c->grid.kind == 0 && (!occ_dense || coords))
+        return fail(c, DIVAS_E_INVALID, "dense context needs occ_dense only");
+    if (c->grid.kind == 1 && (occ_dense || n_coords < 0 || (n_coords > 0 && !coords)))
+        return fail(c, DIVAS_E_INVALID, "sparse context needs coords only");
+    cudaStream_t s = S(stream);
+    divas_status st = build_active(c, occ_dense, coords, n_coords, s);
+    if (st != DIVAS_OK) return st;
+    st = emit_active(c, s);
+    if (st != DIVAS_OK) return st;
+    c->n_views = 0;
+    c->n_active = c->cap;  // upper bound until the next synchronising call
+    return DIVAS_OK;
+}
+
+static divas_status launch_fuse(divas_ctx* c, const ViewBatch& vb, cudaStream_t s) {
+    const int blocks = grid_for(c->cap, c->sm_count);
+    if (c->n_views == 0)
+        k_fuse<false><<<blocks, kThreads, 0, s>>>(c->active, c->d_n, c->G, c->F, vb, c->W, c->Z,
+                                                  c->bits);
+    else
+        k_fuse<true><<<blocks, kThreads, 0, s>>>(c->active, c->d_n, c->G, c->F, vb, c->W, c->Z,
+                                                 c->bits);
+    DIVAS_LAUNCHED(c, "k_fuse");
+    c->n_views += vb.n;
+    return DIVAS_OK;
+}
+
+divas_status divas_fuse_add_view(divas_ctx* c, const divas_camera* cam, const float* depth,
+                                 const void* mask, int32_t mask_type, void* stream) {
+    if (!c) return fail(nullptr, DIVAS_E_INVALID, "ctx is NULL");
+    divas_status st = check_camera(c, cam);
+    if (st != DIVAS_OK) return st;
+    if (!depth || !mask) return fail(c, DIVAS_E_INVALID, "depth or mask is NULL");
+    if (mask_type < 0 || mask_type > 2) return fail(c, DIVAS_E_INVALID, "bad mask_type");
+    ViewBatch vb;
+    memset(&vb, 0, sizeof(vb));
+    vb.n = 1;
+    vb.v[0] = make_view(*cam, depth, mask, mask_type, c->n_views);
+    return launch_fuse(c, vb, S(stream));
+}
+
+divas_status divas_fuse_add_views(divas_ctx* c, const divas_view* views, int32_t n_views,
+                                  void* stream) {
+    if (!c) return fail(nullptr, DIVAS_E_INVALID, "ctx is NULL");
+    if (!views || n_views < 1 || n_views > kMaxViews)
+        return fail(c, DIVAS_E_INVALID, "n_views must be in 1..32 and views non-NULL");
+    ViewBatch vb;
+    memset(&vb, 0, sizeof(vb));
+    vb.n = n_views;
+    for (int32_t k = 0; k < n_views; ++k) {
+        divas_status st = check_camera(c, &views[k].cam);
+        if (st != DIVAS_OK) return st;
+        if (!views[k].depth || !views[k].mask) return fail(c, DIVAS_E_INVALID, "depth or mask is NULL");
+        if (views[k].mask_type < 0 || views[k].mask_type > 2)
+            return fail(c, DIVAS_E_INVALID, "bad mask_type");
+        vb.v[k] = make_view(views[k].cam, views[k].depth, views[k].mask, views[k].mask_type,
+                            c->n_views + k);
+    }
+    return launch_fuse(c, vb, S(stream));
+}
+
+divas_status divas_fuse_finalize(divas_ctx* c, float* score_out, uint32_t* seg_bits_out,
+                                 uint32_t* vmask_out, int64_t* n_seg_host, void* stream) {
+    if (!c) return fail(nullptr, DIVAS_E_INVALID, "ctx is NULL");
+    cudaStream_t s = S(stream);
+    unsigned long long* nseg = n_seg_host ? c->d_nseg : nullptr;
+    if (nseg) DIVAS_CUDA(c, cudaMemsetAsync(c->d_nseg, 0, 8, s));
+    if (c->n_views == 0) {
+        // no view folded in yet: W = Z = 0 (after init/reset), scores are all 0
+    }
+    if (c->grid.kind == 0) {
+        const int64_t quads = (c->n_cells + 3) / 4;
+        k_finalize_dense<<<grid_for(quads, c->sm_count, 32), kThreads, 0, s>>>(
+            c->occ_bits, c->word_prefix, c->d_n, c->n_cells, c->W, c->Z, c->bits, c->F.eps,
+            c->F.tau_cons, score_out, c->seg_bits, seg_bits_out, vmask_out, nseg);
+        DIVAS_LAUNCHED(c, "k_finalize_dense");
+    } else {
+        DIVAS_CUDA(c, cudaMemsetAsync(c->seg_bits, 0, c->n_words * 4, s));
+        if (seg_bits_out) DIVAS_CUDA(c, cudaMemsetAsync(seg_bits_out, 0, c->n_words * 4, s));
+        k_finalize_sparse<<<grid_for(c->cap, c->sm_count, 16), kThreads, 0, s>>>(
+            c->active, c->d_n, c->W, c->Z, c->bits, c->F.eps, c->F.tau_cons, score_out,
+            c->seg_bits, seg_bits_out, vmask_out, nseg);
+        DIVAS_LAUNCHED(c, "k_finalize_sparse");
+    }
+    if (n_seg_host) {
+        unsigned long long v = 0;
+        DIVAS_CUDA(c, cudaMemcpyAsync(&v, c->d_nseg, 8, cudaMemcpyDeviceToHost, s));
+        divas_status st = read_status(c, s);  // synchronises
+        *n_seg_host = (int64_t)v;
+        if (st != DIVAS_OK) return st;
+    }
+    return DIVAS_OK;
+}
+
+divas_status divas_label_points(divas_ctx* c, const float* xyz, int64_t n, uint8_t* labels_out,
+                                void* stream) {
+    if (!c) return fail(nullptr, DIVAS_E_INVALID, "ctx is NULL");
+    if (n < 0 || (n > 0 && (!xyz || !labels_out)))
+        return fail(c, DIVAS_E_INVALID, "bad point arguments");
+    if (n == 0) return DIVAS_OK;
+    k_label<<<grid_for(n, c->sm_count, 32), kThreads, 0, S(stream)>>>(xyz, n, c->G, c->seg_bits,
+                                                                       labels_out);
+    DIVAS_LAUNCHED(c, "k_label");
+    return DIVAS_OK;
+}
+
+divas_status divas_fuse_reset(divas_ctx* c, void* stream) {
+    if (!c) return fail(nullptr, DIVAS_E_INVALID, "ctx is NULL");
+    cudaStream_t s = S(stream);
+    DIVAS_CUDA(c, cudaMemsetAsync(c->W, 0, c->cap * 4, s));
+    DIVAS_CUDA(c, cudaMemsetAsync(c->Z, 0, c->cap * 4, s));
+    DIVAS_CUDA(c, cudaMemsetAsync(c->bits, 0, c->cap * 4, s));
+    c->n_views = 0;
+    return DIVAS_OK;
+}
+
+divas_status divas_fuse_sync(divas_ctx* c, void* stream) {
+    if (!c) return fail(nullptr, DIVAS_E_INVALID, "ctx is NULL");
+    return read_status(c, S(stream));
+}
+
+int64_t divas_fuse_n_active(const divas_ctx* c) { return c ? c->n_active : -1; }
+
+int32_t divas_fuse_n_views(const divas_ctx* c) { return c ? c->n_views : -1; }
+
+divas_status divas_fuse_active_coords(divas_ctx* c, int32_t* coords_out, void* stream) {
+    if (!c || !coords_out) return fail(c, DIVAS_E_INVALID, "NULL argument");
+    k_active_coords<<<grid_for(c->cap, c->sm_count), kThreads, 0, S(stream)>>>(c->active, c->d_n,
+                                                                             c->grid.g, coords_out);
+    DIVAS_LAUNCHED(c, "k_active_coords");
+    return DIVAS_OK;
+}
+
+divas_status divas_fuse_export_state(divas_ctx* c, float* W_out, float* Z_out, uint32_t* bits_out,
+                                     void* stream) {
+    if (!c || !W_out || !Z_out || !bits_out) return fail(c, DIVAS_E_INVALID, "NULL argument");
+    cudaStream_t s = S(stream);
+    DIVAS_CUDA(c, cudaMemcpyAsync(W_out, c->W, c->cap * 4, cudaMemcpyDeviceToDevice, s));
+    DIVAS_CUDA(c, cudaMemcpyAsync(Z_out, c->Z, c->cap * 4, cudaMemcpyDeviceToDevice, s));
+    DIVAS_CUDA(c, cudaMemcpyAsync(bits_out, c->bits, c->cap * 4, cudaMemcpyDeviceToDevice, s));
+    return DIVAS_OK;
+}
+
+divas_status divas_fuse_import_state(divas_ctx* c, const float* W_in, const float* Z_in,
+                                     const uint32_t* bits_in, int32_t n_views, void* stream) {
+    if (!c || !W_in || !Z_in || !bits_in || n_views < 0)
+        return fail(c, DIVAS_E_INVALID, "bad argument");
+    cudaStream_t s = S(stream);
+    DIVAS_CUDA(c, cudaMemcpyAsync(c->W, W_in, c->cap * 4, cudaMemcpyDeviceToDevice, s));
+    DIVAS_CUDA(c, cudaMemcpyAsync(c->Z, Z_in, c->cap * 4, cudaMemcpyDeviceToDevice, s));
+    DIVAS_CUDA(c, cudaMemcpyAsync(c->bits, bits_in, c->cap * 4, cudaMemcpyDeviceToDevice, s));
+    c->n_views = n_views;
+    return DIVAS_OK;
+}
+
+divas_status divas_fuse_backward(divas_ctx* c, const divas_view* views, int32_t n_views,
+                                 const float* grad_score, float* const* grad_mask,
+                                 float* const* grad_depth, void* stream) {
+    if (!c) return fail(nullptr, DIVAS_E_INVALID, "ctx is NULL");
+    if (!views || n_views < 1 || n_views > kMaxViews || !grad_score)
+        return fail(c, DIVAS_E_INVALID, "bad backward arguments");
+    ViewBatch vb;
+    memset(&vb, 0, sizeof(vb));
+    BackPtrs bp;
+    memset(&bp, 0, sizeof(bp));
+    vb.n = n_views;
+    for (int32_t k = 0; k < n_views; ++k) {
+        divas_status st = check_camera(c, &views[k].cam);
+        if (st != DIVAS_OK) return st;
+        if (!views[k].depth || !views[k].mask) return fail(c, DIVAS_E_INVALID, "depth or mask is NULL");
+        if (views[k].mask_type < 0 || views[k].mask_type > 2)
+            return fail(c, DIVAS_E_INVALID, "bad mask_type");
+        vb.v[k] = make_view(views[k].cam, views[k].depth, views[k].mask, views[k].mask_type, k);
+        bp.gm[k] = grad_mask ? grad_mask[k] : nullptr;
+        bp.gd[k] = grad_depth ? grad_depth[k] : nullptr;
+    }
+    k_backward<<<grid_for(c->cap, c->sm_count), kThreads, 0, S(stream)>>>(
+        c->active, c->d_n, c->G, c->F, vb, bp, c->W, c->Z, grad_score, c->grid.kind == 0 ? 1 : 0);
+    DIVAS_LAUNCHED(c, "k_backward");
+    return DIVAS_OK;
+}
+
+divas_status divas_debug_project(divas_ctx* c, const divas_camera* cam, int32_t* pix_out,
+                                 void* stream) {
+    if (!c) return fail(nullptr, DIVAS_E_INVALID, "ctx is NULL");
+    divas_status st = check_camera(c, cam);
+    if (st != DIVAS_OK) return st;
+    if (!pix_out) return fail(c, DIVAS_E_INVALID, "pix_out is NULL");
+    ViewC v = make_view(*cam, nullptr, nullptr, 0, 0);
+    k_debug_project<<<grid_for(c->cap, c->sm_count), kThreads, 0, S(stream)>>>(c->active, c->d_n,
+                                                                             c->G, c->F, v, pix_out);
+    DIVAS_LAUNCHED(c, "k_debug_project");
+    return DIVAS_OK;
+}
+
+void divas_fuse_destroy(divas_ctx* c) {
+    if (!c) return;
+    free_all(c);
+    delete c;
+}
+
+const char* divas_last_error(const divas_ctx* c) {
+    return c ? c->err.c_str() : g_init_error.c_str();
+}
+
+}  // extern "C"

@@ -1,0 +1,300 @@
+"""Python face of the fusion library: one ``VoxelFusion`` per occupied set.
+
+Argument marshalling only -- every step runs in the CUDA kernels of
+``libdivas_fuse.so`` (the C ABI in ``include/divas_fuse.h``).  PyTorch
+supplies device memory and the current stream.
+
+Notation follows the paper: W and Z are the weighted-vote and weight
+accumulators of Eq. vmask, P = W / Z the fused probability of Eq.
+compact-fusion, seg the consensus set {P >= tau_cons}, vmask the per-voxel
+view-coverage bitmask.
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+
+import torch
+
+from . import _lib as L
+
+
+@dataclass
+class FusionParams:
+    """Thick-path constants (defaults: tau_mask 0.5 = the thick-path entry gate of
+    Algorithms A.2 / B.5; gamma 1.0 and tau_cons 0.5 from Table gs-hyperparams;
+    alpha1 0.5 and eps 1e-12, for which the paper gives no value)."""
+
+    tau_mask: float = 0.5
+    gamma: float = 1.0
+    alpha1: float = 0.5
+    tau_cons: float = 0.5
+    eps: float = 1e-12
+    z_near: float = 1e-6
+
+    def c(self) -> L.DivasParams:
+        return L.DivasParams(self.tau_mask, self.gamma, self.alpha1, self.tau_cons, self.eps,
+                             self.z_near, 0)
+
+
+def _stream(stream=None) -> ctypes.c_void_p:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("tensor must be on a CUDA device")
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def camera_c(cam) -> L.DivasCamera:
+    """Any object with R (3x3), t (3), fx, fy, cx, cy, W, H -> divas_camera."""
+    c = L.DivasCamera()
+    c.W, c.H = int(cam.W), int(cam.H)
+    c.fx, c.fy, c.cx, c.cy = float(cam.fx), float(cam.fy), float(cam.cx), float(cam.cy)
+    R = [float(v) for row in _rows(cam.R) for v in row]
+    for k in range(9):
+        c.R[k] = R[k]
+    t = [float(v) for v in _flat(cam.t)]
+    for k in range(3):
+        c.t[k] = t[k]
+    return c
+
+
+def _rows(R):
+    try:
+        return [list(r) for r in R]
+    except TypeError:
+        return [list(R[3 * i:3 * i + 3]) for i in range(3)]
+
+
+def _flat(x):
+    try:
+        return [float(v) for v in x.reshape(-1)]
+    except AttributeError:
+        return [float(v) for v in x]
+
+
+def mask_type_of(mask: torch.Tensor, logits: bool = False) -> int:
+    if mask.dtype == torch.float16:
+        return L.MASK_F16
+    if mask.dtype == torch.float32:
+        return L.MASK_LOGIT_F32 if logits else L.MASK_F32
+    raise ValueError(f"unsupported mask dtype {mask.dtype}")
+
+
+def view_c(cam, depth: torch.Tensor, mask: torch.Tensor, mask_type: int | None = None,
+           logits: bool = False) -> L.DivasView:
+    if depth.dtype != torch.float32:
+        raise ValueError("depth must be float32")
+    if tuple(depth.shape[-2:]) != (int(cam.H), int(cam.W)) or mask.shape != depth.shape:
+        raise ValueError("depth and mask must be H x W")
+    v = L.DivasView()
+    v.cam = camera_c(cam)
+    v.depth = _ptr(depth)
+    v.mask = _ptr(mask)
+    v.mask_type = mask_type if mask_type is not None else mask_type_of(mask, logits)
+    return v
+
+
+class VoxelFusion:
+    """Device-resident fusion state for one occupied set (dense prior or sparse set).
+
+    ``grid``: object with g, origin (3), h, contracted.  Exactly one of
+    ``occ`` (uint8 g^3, x fastest) and ``coords`` ((n, 3) int32) is given,
+    both CUDA tensors."""
+
+    def __init__(self, grid, occ: torch.Tensor | None = None,
+                 coords: torch.Tensor | None = None, params: FusionParams | None = None,
+                 stream=None):
+        self.lib = L.load()
+        self.params = params or FusionParams()
+        g = L.DivasGrid()
+        g.kind = 0 if occ is not None else 1
+        g.g = int(grid.g)
+        for k in range(3):
+            g.origin[k] = float(grid.origin[k])
+        g.h = float(grid.h)
+        g.contracted = 1 if getattr(grid, "contracted", False) else 0
+        self.grid_c = g
+        self.g = int(grid.g)
+        self.dense = occ is not None
+        if occ is not None:
+            occ = occ.contiguous()
+            if occ.dtype != torch.uint8 or occ.numel() != self.g ** 3:
+                raise ValueError("occ must be uint8 with g^3 elements")
+        if coords is not None:
+            coords = coords.contiguous()
+            if coords.dtype != torch.int32 or coords.dim() != 2 or coords.shape[1] != 3:
+                raise ValueError("coords must be (n, 3) int32")
+        self._h = ctypes.c_void_p()
+        n = 0 if coords is None else coords.shape[0]
+        st = self.lib.divas_fuse_init(ctypes.byref(self._h), ctypes.byref(g), _ptr(occ),
+                                      _ptr(coords), n, ctypes.byref(self.params.c()),
+                                      _stream(stream))
+        L.check(st, None)
+
+    # -- lifecycle ---------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            self.lib.divas_fuse_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st):
+        L.check(st, self._h)
+
+    @property
+    def handle(self) -> ctypes.c_void_p:
+        return self._h
+
+    @property
+    def n_active(self) -> int:
+        return int(self.lib.divas_fuse_n_active(self._h))
+
+    @property
+    def n_views(self) -> int:
+        return int(self.lib.divas_fuse_n_views(self._h))
+
+    @property
+    def n_cells(self) -> int:
+        return self.g ** 3
+
+    # -- the hot path ------------------------------------------------------
+    def set_occupancy(self, occ=None, coords=None, stream=None):
+        n = 0 if coords is None else coords.shape[0]
+        self._check(self.lib.divas_fuse_set_occupancy(self._h, _ptr(occ), _ptr(coords), n,
+                                                      _stream(stream)))
+
+    def add_view(self, cam, depth, mask, mask_type: int | None = None, logits=False,
+                 stream=None):
+        mt = mask_type if mask_type is not None else mask_type_of(mask, logits)
+        c = camera_c(cam)
+        self._check(self.lib.divas_fuse_add_view(self._h, ctypes.byref(c), _ptr(depth),
+                                                 _ptr(mask), mt, _stream(stream)))
+
+    def add_views(self, cams, depths, masks, mask_type: int | None = None, logits=False,
+                  stream=None):
+        """Fold views in index order, up to 32 per launch."""
+        n = len(cams)
+        for s0 in range(0, n, L.MAX_VIEWS_PER_CALL):
+            s1 = min(n, s0 + L.MAX_VIEWS_PER_CALL)
+            arr = (L.DivasView * (s1 - s0))()
+            for k in range(s0, s1):
+                arr[k - s0] = view_c(cams[k], depths[k], masks[k], mask_type, logits)
+            self._check(self.lib.divas_fuse_add_views(self._h, arr, s1 - s0, _stream(stream)))
+
+    def finalize(self, score: bool | torch.Tensor = True, seg_bits: bool | torch.Tensor = False,
+                 vmask: bool | torch.Tensor = False, count: bool = False, stream=None) -> dict:
+        """Outputs as CUDA tensors: score (float32, g^3 dense or n_active sparse),
+        seg_bits (int32 view of ceil(g^3/32) uint32 words), vmask (int32 view of
+        n_active uint32), and n_seg (int, synchronises) when ``count``."""
+        dev = torch.device("cuda")
+        out = {}
+
+        def _buf(flag, n, dtype):
+            if isinstance(flag, torch.Tensor):
+                return flag
+            if flag:
+                return torch.empty(n, dtype=dtype, device=dev)
+            return None
+        n_score = self.n_cells if self.dense else self.n_active
+        out["score"] = _buf(score, n_score, torch.float32)
+        out["seg_bits"] = _buf(seg_bits, (self.n_cells + 31) // 32, torch.int32)
+        out["vmask"] = _buf(vmask, self.n_active, torch.int32)
+        nseg = ctypes.c_int64(0)
+        self._check(self.lib.divas_fuse_finalize(
+            self._h, _ptr(out["score"]), _ptr(out["seg_bits"]), _ptr(out["vmask"]),
+            ctypes.byref(nseg) if count else None, _stream(stream)))
+        if count:
+            out["n_seg"] = int(nseg.value)
+        return {k: v for k, v in out.items() if v is not None}
+
+    def label_points(self, xyz: torch.Tensor, out: torch.Tensor | None = None,
+                     stream=None) -> torch.Tensor:
+        """Pass 1 labels (uint8) of (n, 3) float32 points."""
+        xyz = xyz.contiguous()
+        if xyz.dtype != torch.float32 or xyz.dim() != 2 or xyz.shape[1] != 3:
+            raise ValueError("xyz must be (n, 3) float32")
+        n = xyz.shape[0]
+        if out is None:
+            out = torch.empty(n, dtype=torch.uint8, device=xyz.device)
+        self._check(self.lib.divas_label_points(self._h, _ptr(xyz), n, _ptr(out),
+                                                _stream(stream)))
+        return out
+
+    # -- state -------------------------------------------------------------
+    def reset(self, stream=None):
+        self._check(self.lib.divas_fuse_reset(self._h, _stream(stream)))
+
+    def sync(self, stream=None):
+        self._check(self.lib.divas_fuse_sync(self._h, _stream(stream)))
+
+    def active_coords(self, stream=None) -> torch.Tensor:
+        out = torch.empty((self.n_active, 3), dtype=torch.int32, device="cuda")
+        if out.numel() == 0:
+            return out
+        self._check(self.lib.divas_fuse_active_coords(self._h, _ptr(out), _stream(stream)))
+        return out
+
+    def export_state(self, stream=None) -> dict:
+        n = self.n_active
+        W = torch.empty(n, dtype=torch.float32, device="cuda")
+        Z = torch.empty(n, dtype=torch.float32, device="cuda")
+        b = torch.empty(n, dtype=torch.int32, device="cuda")
+        if n == 0:
+            return {"W": W, "Z": Z, "bits": b, "n_views": self.n_views}
+        self._check(self.lib.divas_fuse_export_state(self._h, _ptr(W), _ptr(Z), _ptr(b),
+                                                     _stream(stream)))
+        return {"W": W, "Z": Z, "bits": b, "n_views": self.n_views}
+
+    def import_state(self, state: dict, stream=None):
+        if state["W"].numel() == 0:
+            return
+        self._check(self.lib.divas_fuse_import_state(
+            self._h, _ptr(state["W"]), _ptr(state["Z"]), _ptr(state["bits"]),
+            int(state["n_views"]), _stream(stream)))
+
+    # -- adjoint and test hooks ---------------------------------------------
+    def backward(self, cams, depths, masks, grad_score: torch.Tensor, grad_mask=None,
+                 grad_depth=None, mask_type: int | None = None, logits=False, stream=None):
+        """Accumulate dL/dmask and dL/ddepth rasters for the cotangent grad_score."""
+        n = len(cams)
+        if n > L.MAX_VIEWS_PER_CALL:
+            raise ValueError("backward supports up to 32 views per call")
+        arr = (L.DivasView * n)()
+        for k in range(n):
+            arr[k] = view_c(cams[k], depths[k], masks[k], mask_type, logits)
+        gm = (ctypes.c_void_p * n)(*[(_ptr(t).value if t is not None else None)
+                                     for t in (grad_mask or [None] * n)])
+        gd = (ctypes.c_void_p * n)(*[(_ptr(t).value if t is not None else None)
+                                     for t in (grad_depth or [None] * n)])
+        self._check(self.lib.divas_fuse_backward(self._h, arr, n, _ptr(grad_score.contiguous()),
+                                                 gm, gd, _stream(stream)))
+
+    def debug_project(self, cam, stream=None) -> torch.Tensor:
+        out = torch.empty(self.n_active, dtype=torch.int32, device="cuda")
+        if out.numel() == 0:
+            return out
+        c = camera_c(cam)
+        self._check(self.lib.divas_debug_project(self._h, ctypes.byref(c), _ptr(out),
+                                                 _stream(stream)))
+        return out
+
+
+def seg_bits_to_bool(seg_bits: torch.Tensor, n_cells: int) -> torch.Tensor:
+    """Unpack an int32 view of the uint32 seg words into a bool tensor of n_cells."""
+    w = seg_bits.to(torch.int64) & 0xFFFFFFFF
+    shifts = torch.arange(32, device=w.device, dtype=torch.int64)
+    bits = (w[:, None] >> shifts[None, :]) & 1
+    return bits.reshape(-1)[:n_cells].to(torch.bool)
