@@ -179,7 +179,7 @@ def algorithmic_bytes(wl, n_active):
 def run_ours(args, rank, world, local_rank):
     import torch
 
-    from paper_2601_04860_b300 import FusionParams, VoxelFusion
+    from paper_2601_04860_b300 import FusionParams, PreparedViews, VoxelFusion
 
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
@@ -198,68 +198,129 @@ def run_ours(args, rank, world, local_rank):
     score = torch.empty(fu.n_cells if dense else n_active, dtype=torch.float32, device=dev)
     labels = torch.empty(len(wl.points), dtype=torch.uint8, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-    stream = torch.cuda.current_stream()
     S = wl.n_views
     N = fu.n_cells if dense else n_active
-    launches_per_step = 4 + (0 if dense else 0) + math.ceil(S / 32) + 1 + 1
+    pv = PreparedViews(wl.cams, depth, mask, wl.mask_type)
+    phases = ["compaction", "fuse", "finalize", "label"]
+    kernels_per_phase = {"compaction": 3 if dense else 4, "fuse": math.ceil(S / 32),
+                         "finalize": 1, "label": 1}
 
     def step(ev=None):
+        if ev:
+            ev[0].record()
         fu.set_occupancy(occ=occ, coords=coords)
         if ev:
-            ev[1].record(stream)
-        fu.add_views(wl.cams, depth, mask, mask_type=wl.mask_type)
+            ev[1].record()
+        fu.add_views(pv)
         if ev:
-            ev[2].record(stream)
+            ev[2].record()
         fu.finalize(score=score)
         if ev:
-            ev[3].record(stream)
+            ev[3].record()
         fu.label_points(pts, out=labels)
+        if ev:
+            ev[4].record()
 
+    # eager warm-up on a side stream, then capture one step in a CUDA graph whose
+    # event-record nodes time each phase on the device
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        for _ in range(3):
+            step()
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True, external=True) for _ in range(5)]
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        step(ev)
     for _ in range(args.warmup):
         flush.zero_()
-        step()
+        graph.replay()
     torch.cuda.synchronize()
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
+
     clocks = Clocks(local_rank)
     clocks.start()
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
     t_wall = time.perf_counter()
+    step_ms, phase = [], {k: [] for k in phases}
     for k in range(args.steps):
-        flush.zero_()
-        evs[k][0].record(stream)
-        step(evs[k])
-        evs[k][4].record(stream)
+        flush.zero_()  # L2 flush between timed steps (not inside the graph's events)
+        graph.replay()
+        torch.cuda.synchronize()
+        step_ms.append(ev[0].elapsed_time(ev[4]))
+        for i, name in enumerate(phases):
+            phase[name].append(ev[i].elapsed_time(ev[i + 1]))
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
     t_wall = time.perf_counter() - t_wall
     clk = clocks.stop()
-    step_ms = np.array([e[0].elapsed_time(e[4]) for e in evs])
-    phase = {name: np.array([e[i].elapsed_time(e[i + 1]) for e in evs])
-             for i, name in enumerate(["compaction", "fuse", "finalize", "label"])}
+    step_ms = np.array(step_ms)
     ms = float(step_ms.mean())
     if world > 1:
         t = torch.tensor([ms], device=dev)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         ms = float(t.item())
 
-    # per-update latency: one incremental view + finalize (the interactive update)
-    upd = []
-    for k in range(max(10, args.steps)):
-        fu.set_occupancy(occ=occ, coords=coords)
-        fu.add_views(wl.cams[:-1], depth[:-1], mask[:-1], mask_type=wl.mask_type)
+    if args.quick:  # timed graph steps only (profiling runs)
+        res = {"metric": METRIC, "value": world * N * S / (ms * 1e-3), "unit": UNIT,
+               "ms_per_step": ms, "phase_ms": {k: float(np.mean(v)) for k, v in phase.items()},
+               "quick": True}
+        fu.close()
+        return res, wl
+
+    # the same step launched eagerly through the Python API (host launch cost included)
+    eager = []
+    for _ in range(max(5, args.steps // 2)):
         flush.zero_()
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        fu.add_view(wl.cams[-1], depth[-1], mask[-1], mask_type=wl.mask_type)
-        fu.finalize(score=score)
-        b.record(stream)
+        a.record()
+        step()
+        b.record()
         torch.cuda.synchronize()
-        upd.append(a.elapsed_time(b))
+        eager.append(a.elapsed_time(b))
+
+    # per-update latency: one more view folded into a session holding S-1 views,
+    # then finalize -- eager API calls, and the same update replayed as a graph
+    upd, upd_g = [], []
+    pv_last = PreparedViews(wl.cams[-1:], depth[-1:], mask[-1:], wl.mask_type)
+    pv_first = PreparedViews(wl.cams[:-1], depth[:-1], mask[:-1], wl.mask_type)
+    ug = None
+    for k in range(max(20, args.steps)):
+        fu.set_occupancy(occ=occ, coords=coords)
+        fu.add_views(pv_first)
+        flush.zero_()
+        if ug is None:
+            torch.cuda.synchronize()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            fu.add_views(pv_last)
+            fu.finalize(score=score)
+            b.record()
+            torch.cuda.synchronize()
+            upd.append(a.elapsed_time(b))
+            if k == max(20, args.steps) // 2:
+                ue = [torch.cuda.Event(enable_timing=True, external=True) for _ in range(2)]
+                ug = torch.cuda.CUDAGraph()
+                fu.set_occupancy(occ=occ, coords=coords)
+                fu.add_views(pv_first)
+                torch.cuda.synchronize()
+                with torch.cuda.graph(ug):
+                    ue[0].record()
+                    fu.add_views(pv_last)
+                    fu.finalize(score=score)
+                    ue[1].record()
+        else:
+            ug.replay()
+            torch.cuda.synchronize()
+            upd_g.append(ue[0].elapsed_time(ue[1]))
     upd = np.array(upd)
+    upd_g = np.array(upd_g)
 
     # end to end through the public API with pinned host buffers
     h_occ = None if occ is None else torch.from_numpy(wl.occ).pin_memory()
@@ -283,7 +344,10 @@ def run_ours(args, rank, world, local_rank):
         for a, b in zip(mask, h_mask):
             a.copy_(b, non_blocking=True)
         pts.copy_(h_pts, non_blocking=True)
-        step()
+        fu.set_occupancy(occ=occ, coords=coords)
+        fu.add_views(wl.cams, depth, mask, mask_type=wl.mask_type)
+        fu.finalize(score=score)
+        fu.label_points(pts, out=labels)
         h_score.copy_(score, non_blocking=True)
         h_labels.copy_(labels, non_blocking=True)
     for _ in range(2):
@@ -293,9 +357,9 @@ def run_ours(args, rank, world, local_rank):
     for _ in range(max(3, args.steps // 2)):
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
-        a.record(stream)
+        a.record()
         e2e_step()
-        b.record(stream)
+        b.record()
         torch.cuda.synchronize()
         e2e_ms.append(a.elapsed_time(b))
     e2e_ms = float(np.mean(e2e_ms))
@@ -306,8 +370,9 @@ def run_ours(args, rank, world, local_rank):
 
     algo, view_bytes, _, _ = algorithmic_bytes(wl, n_active)
     peak, peak_kind = peaks()
-    pm = {k: float(v.mean()) for k, v in phase.items()}
-    dom = max(["fuse", "finalize", "label"], key=lambda k: pm[k])
+    pm = {k: float(np.mean(v)) for k, v in phase.items()}
+    single = [k for k in phases if kernels_per_phase[k] == 1]
+    dom = max(single, key=lambda k: pm[k])
     achieved = algo[dom] / (pm[dom] * 1e-3) / 1e9
     step_bytes = sum(algo.values())
     res = {
@@ -318,7 +383,8 @@ def run_ours(args, rank, world, local_rank):
         "config": {"workload": args.workload, "description": WORKLOADS[args.workload],
                    "grid": int(wl.grid.g), "views": S, "active_voxels": int(n_active),
                    "voxels_nominal": int(N), "points": int(len(wl.points)),
-                   "l2": "flushed between timed steps (256 MB write)",
+                   "l2": "flushed between timed steps (256 MB write, outside the timed events)",
+                   "launch": "one CUDA graph replay per step (device time from in-graph events)",
                    "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak, "traffic": None,
@@ -328,14 +394,18 @@ def run_ours(args, rank, world, local_rank):
                           "achieved_gbs": step_bytes / (ms * 1e-3) / 1e9,
                           "frac": step_bytes / (ms * 1e-3) / 1e9 / peak},
         "phase_ms": pm,
-        "per_update_ms": {"what": "add_view (1 view, incremental) + finalize, L2 flushed",
+        "phase_bytes": {k: int(v) for k, v in algo.items()},
+        "eager_ms_per_step": float(np.mean(eager)),
+        "per_update_ms": {"what": "fold 1 view into a session of S-1 views + finalize, L2 flushed",
                           "p50": float(np.percentile(upd, 50)),
-                          "p99": float(np.percentile(upd, 99))},
+                          "p99": float(np.percentile(upd, 99)),
+                          "graph_p50": float(np.percentile(upd_g, 50)) if len(upd_g) else None,
+                          "graph_p99": float(np.percentile(upd_g, 99)) if len(upd_g) else None},
         "active_updates_per_s": world * n_active * S / (ms * 1e-3),
         "e2e": {"value": world * N * S / (e2e_ms * 1e-3), "unit": UNIT,
                 "ms_per_step": e2e_ms, "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},
-        "gpu_launches": int(launches_per_step * args.steps),
+        "gpu_launches": int(sum(kernels_per_phase.values()) * args.steps),
         "clocks": clk,
         "wall_s_timed": t_wall,
     }
@@ -357,7 +427,7 @@ def run(args):
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     res, wl = run_ours(args, rank, world, local_rank)
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.quick:
         full_s, det = oracle_rate(wl, args.cpu_seconds)
         N = res["config"]["voxels_nominal"]
         res["cpu_baseline"] = {
@@ -410,6 +480,8 @@ def main(argv=None):
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="forward-dense-256")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--quick", action="store_true",
+                    help="timed graph steps only: no eager, per-update, e2e or CPU legs")
     args = ap.parse_args(argv)
     args.warmup = max(3, args.warmup)  # at least 3 untimed warm-up steps
     return run(args)

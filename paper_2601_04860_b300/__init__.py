@@ -13,4 +13,4 @@ from ._lib import (  # noqa: F401
     DivasError,
     load,
 )
-from .fusion import FusionParams, VoxelFusion, seg_bits_to_bool  # noqa: F401
+from .fusion import FusionParams, PreparedViews, VoxelFusion, seg_bits_to_bool  # noqa: F401

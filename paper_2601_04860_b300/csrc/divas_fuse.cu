@@ -21,6 +21,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstddef>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -33,7 +34,7 @@ using namespace divas;
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kWordsPerThread = 4;                       // compaction
+constexpr int kWordsPerThread = 1;                       // compaction
 constexpr int kWordsPerBlock = kThreads * kWordsPerThread;
 constexpr int32_t kStatusBadCoord = 1;
 constexpr int32_t kStatusCapacity = 2;
@@ -46,17 +47,20 @@ struct BackPtrs {
 // ---------------------------------------------------------------------------
 // compaction
 // ---------------------------------------------------------------------------
-// dense uint8 prior -> bitfield (one thread per 32-voxel word)
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* total);
+
+// dense uint8 prior -> bitfield words and per-block popcounts (one word per thread)
 __global__ void __launch_bounds__(kThreads) k_occ_bits(const uint8_t* __restrict__ occ,
                                                        int64_t n_cells, int64_t n_words,
-                                                       uint32_t* __restrict__ bits) {
-    for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < n_words;
-         w += (int64_t)gridDim.x * blockDim.x) {
+                                                       uint32_t* __restrict__ bits,
+                                                       uint32_t* __restrict__ block_sums) {
+    const int64_t w = blockIdx.x * (int64_t)kThreads + threadIdx.x;
+    uint32_t word = 0;
+    if (w < n_words) {
         const int64_t base = w * 32;
-        uint32_t word = 0;
         if (base + 32 <= n_cells && ((reinterpret_cast<uintptr_t>(occ + base) & 15) == 0)) {
-            const uint4 a = __ldg(reinterpret_cast<const uint4*>(occ + base));
-            const uint4 b = __ldg(reinterpret_cast<const uint4*>(occ + base) + 1);
+            const uint4 a = __ldcs(reinterpret_cast<const uint4*>(occ + base));
+            const uint4 b = __ldcs(reinterpret_cast<const uint4*>(occ + base) + 1);
             const uint32_t v[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
 #pragma unroll
             for (int q = 0; q < 8; ++q)
@@ -69,6 +73,9 @@ __global__ void __launch_bounds__(kThreads) k_occ_bits(const uint8_t* __restrict
         }
         bits[w] = word;
     }
+    uint32_t total;
+    block_exclusive_scan(__popc(word), &total);
+    if (threadIdx.x == 0) block_sums[blockIdx.x] = total;
 }
 
 // sparse coordinates -> bitfield (atomic OR; duplicates merge)
@@ -130,54 +137,57 @@ __global__ void __launch_bounds__(kThreads) k_block_popc(const uint32_t* __restr
     if (threadIdx.x == 0) block_sums[blockIdx.x] = total;
 }
 
-// one block: exclusive scan of the block sums; d_n = min(total, cap)
+// one block: exclusive scan of the block sums (each thread a contiguous run);
+// d_n = min(total, cap)
 __global__ void __launch_bounds__(kThreads) k_scan_blocks(uint32_t* __restrict__ block_sums,
                                                           int32_t n_blocks, int64_t cap,
                                                           int64_t* __restrict__ d_total,
                                                           int32_t* __restrict__ d_n,
                                                           int32_t* __restrict__ status) {
-    uint32_t carry = 0;
-    for (int32_t base = 0; base < n_blocks; base += kThreads) {
-        const int32_t b = base + threadIdx.x;
-        const uint32_t v = b < n_blocks ? block_sums[b] : 0u;
-        uint32_t tot;
-        const uint32_t ex = block_exclusive_scan(v, &tot);
-        if (b < n_blocks) block_sums[b] = carry + ex;
-        carry += tot;
+    const int32_t per = (n_blocks + kThreads - 1) / kThreads;
+    const int32_t beg = threadIdx.x * per;
+    const int32_t end = min(beg + per, n_blocks);
+    uint32_t s = 0;
+#pragma unroll 8
+    for (int32_t i = beg; i < end; ++i) s += block_sums[i];
+    uint32_t total;
+    uint32_t ex = block_exclusive_scan(s, &total);
+    for (int32_t i = beg; i < end; ++i) {
+        const uint32_t v = block_sums[i];
+        block_sums[i] = ex;
+        ex += v;
     }
     if (threadIdx.x == 0) {
-        *d_total = carry;
-        const int64_t n = carry < (uint64_t)cap ? (int64_t)carry : cap;
+        *d_total = total;
+        const int64_t n = (int64_t)total < cap ? (int64_t)total : cap;
         *d_n = (int32_t)n;
-        if ((int64_t)carry > cap) atomicOr(status, kStatusCapacity);
+        if ((int64_t)total > cap) atomicOr(status, kStatusCapacity);
     }
 }
 
-// rank structure and active list
+// rank structure and active list: one word per thread for the ranks; the
+// active list is written warp-cooperatively (word after word, one lane per
+// bit), so that every store instruction writes consecutive slots
 __global__ void __launch_bounds__(kThreads) k_emit(const uint32_t* __restrict__ bits,
                                                    int64_t n_words,
                                                    const uint32_t* __restrict__ block_off,
                                                    int64_t cap, uint32_t* __restrict__ word_prefix,
                                                    int32_t* __restrict__ active) {
-    const int64_t base = (int64_t)blockIdx.x * kWordsPerBlock + threadIdx.x * kWordsPerThread;
-    uint32_t w[kWordsPerThread];
-    uint32_t c = 0;
-#pragma unroll
-    for (int q = 0; q < kWordsPerThread; ++q) {
-        w[q] = base + q < n_words ? __ldg(bits + base + q) : 0u;
-        c += __popc(w[q]);
-    }
-    uint32_t off = block_off[blockIdx.x] + block_exclusive_scan(c, nullptr);
-#pragma unroll
-    for (int q = 0; q < kWordsPerThread; ++q) {
-        if (base + q >= n_words) break;
-        word_prefix[base + q] = off;
-        uint32_t m = w[q];
-        while (m) {
-            const int b = __ffs(m) - 1;
-            m &= m - 1;
-            if ((int64_t)off < cap) active[off] = (int32_t)((base + q) * 32 + b);
-            ++off;
+    const int64_t w = blockIdx.x * (int64_t)kThreads + threadIdx.x;
+    const uint32_t word = w < n_words ? __ldg(bits + w) : 0u;
+    const uint32_t off = block_off[blockIdx.x] + block_exclusive_scan(__popc(word), nullptr);
+    if (w < n_words) word_prefix[w] = off;
+    const int lane = threadIdx.x & 31;
+    const uint32_t lt = (1u << lane) - 1u;
+    const int64_t wbase = w - lane;  // word index of lane 0
+#pragma unroll 4
+    for (int i = 0; i < 32; ++i) {
+        const uint32_t wi = __shfl_sync(0xffffffffu, word, i);
+        const uint32_t oi = __shfl_sync(0xffffffffu, off, i);
+        if (wi == 0u) continue;  // warp-uniform
+        if ((wi >> lane) & 1u) {
+            const int64_t slot = (int64_t)oi + __popc(wi & lt);
+            if (slot < cap) active[slot] = (int32_t)((wbase + i) * 32 + lane);
         }
     }
 }
@@ -185,7 +195,7 @@ __global__ void __launch_bounds__(kThreads) k_emit(const uint32_t* __restrict__ 
 // ---------------------------------------------------------------------------
 // fusion
 // ---------------------------------------------------------------------------
-template <bool kAccumulate>
+template <bool kAccumulate, bool kContracted, int kChunks>
 __global__ void __launch_bounds__(kThreads) k_fuse(const int32_t* __restrict__ active,
                                                    const int32_t* __restrict__ d_n, GridC G,
                                                    FuseC F, const __grid_constant__ ViewBatch VB,
@@ -194,7 +204,7 @@ __global__ void __launch_bounds__(kThreads) k_fuse(const int32_t* __restrict__ a
                                                    uint32_t* __restrict__ bits) {
     const int32_t n = *d_n;
     for (int32_t a = blockIdx.x * blockDim.x + threadIdx.x; a < n; a += gridDim.x * blockDim.x) {
-        const VoxelGeom vg = voxel_geom(__ldg(active + a), G, F.gamma);
+        const VoxelGeom vg = voxel_geom<kContracted>(__ldg(active + a), G, F.gamma);
         float w = 0.f, z = 0.f;
         uint32_t b = 0;
         if (kAccumulate) {
@@ -202,12 +212,26 @@ __global__ void __launch_bounds__(kThreads) k_fuse(const int32_t* __restrict__ a
             z = Z[a];
             b = bits[a];
         }
-        if (vg.ok)
-            for (int32_t v = 0; v < VB.n; ++v) vote(VB.v[v], vg, F, w, z, b);
+        if (vg.ok) fold_views<kContracted, kChunks>(VB, vg, F, w, z, b);
         W[a] = w;
         Z[a] = z;
         bits[a] = b;
     }
+}
+
+// launch k_fuse with the chunk count as a compile-time constant
+template <bool kAccumulate, bool kContracted, int kChunks = 1>
+cudaError_t launch_fuse_chunks(int chunks, int blocks, cudaStream_t s, const int32_t* active,
+                               const int32_t* d_n, const GridC& G, const FuseC& F,
+                               const ViewBatch& vb, float* W, float* Z, uint32_t* bits) {
+    if constexpr (kChunks < kMaxViews / kViewChunk) {
+        if (chunks > kChunks)
+            return launch_fuse_chunks<kAccumulate, kContracted, kChunks + 1>(
+                chunks, blocks, s, active, d_n, G, F, vb, W, Z, bits);
+    }
+    k_fuse<kAccumulate, kContracted, kChunks><<<blocks, kThreads, 0, s>>>(active, d_n, G, F, vb,
+                                                                          W, Z, bits);
+    return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
@@ -217,66 +241,93 @@ __device__ __forceinline__ float score_of(float w, float z, float eps) {
     return z > eps ? __fdiv_rn(w, z) : 0.f;
 }
 
-// dense: 4 voxels per thread, 8 threads per occupancy word
+// dense: one occupancy word (32 voxels) per thread.  Each warp owns 1024
+// consecutive voxels: it zeroes a 4 KB shared tile, each lane drops the scores
+// of its word's occupied voxels into the tile (W / Z loads of up to four
+// voxels in flight at once), and the warp streams the tile out with coalesced
+// 128-bit stores.  The seg word and the view masks are written directly.
+constexpr int kFinWarps = kThreads / 32;
+
 __global__ void __launch_bounds__(kThreads) k_finalize_dense(
     const uint32_t* __restrict__ occ_bits, const uint32_t* __restrict__ word_prefix,
     const int32_t* __restrict__ d_n, int64_t n_cells, const float* __restrict__ W,
     const float* __restrict__ Z, const uint32_t* __restrict__ bits, float eps, float tau_cons,
     float* __restrict__ score_out, uint32_t* __restrict__ seg_bits, uint32_t* __restrict__ seg_out,
     uint32_t* __restrict__ vmask_out, unsigned long long* __restrict__ d_nseg) {
-    const int32_t n = *d_n;
-    const int64_t n_quads = (n_cells + 3) / 4;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    // whole warps iterate together so that the shuffles below stay converged
-    for (int64_t t0 = (int64_t)blockIdx.x * blockDim.x; t0 < n_quads; t0 += stride) {
-        const int64_t t = t0 + threadIdx.x;
-        const bool live = t < n_quads;
-        const int64_t v0 = 4 * t;
-        const int64_t wi = v0 >> 5;
-        const int b0 = (int)(v0 & 31);
-        uint32_t word = 0, pre = 0;
-        if (live) {
-            word = __ldg(occ_bits + wi);
-            pre = __ldg(word_prefix + wi);
-        }
-        float p[4] = {0.f, 0.f, 0.f, 0.f};
-        uint32_t nib = 0;
+    __shared__ float4 tile[kFinWarps][256];
+    const uint32_t n = (uint32_t)*d_n;
+    const int64_t n_words = (n_cells + 31) / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t w = blockIdx.x * (int64_t)kThreads + threadIdx.x;
+    const bool live = w < n_words;
+    uint32_t word = 0, pre = 0;
+    if (live) {
+        word = __ldg(occ_bits + w);
+        pre = __ldg(word_prefix + w);
+    }
+    float4* t4 = tile[warp];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) t4[lane + 32 * i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    __syncwarp();
+    float* t1 = reinterpret_cast<float*>(t4) + lane * 32;
+    uint32_t segw = 0;
+    uint32_t m = word;
+    uint32_t r = pre;
+    while (m) {  // up to four occupied voxels per round, their loads issued together
+        int b[4];
+        uint32_t sl[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            const int b = b0 + q;
-            if (live && ((word >> b) & 1u)) {
-                const uint32_t slot = pre + __popc(word & ((1u << b) - 1u));
-                if ((int64_t)slot < n) {
-                    const float s = score_of(W[slot], Z[slot], eps);
-                    const bool seg = s >= tau_cons;
-                    p[q] = s;
-                    nib |= (seg ? 1u : 0u) << q;
-                    if (vmask_out) vmask_out[slot] = seg ? bits[slot] : 0u;
-                }
+            b[q] = m ? __ffs(m) - 1 : -1;
+            sl[q] = (b[q] >= 0 && r < n) ? r : 0xffffffffu;
+            if (b[q] >= 0) {
+                m &= m - 1;
+                ++r;
             }
         }
-        if (live && score_out) {
-            if (v0 + 4 <= n_cells && ((reinterpret_cast<uintptr_t>(score_out + v0) & 15) == 0)) {
-                __stcs(reinterpret_cast<float4*>(score_out + v0), make_float4(p[0], p[1], p[2], p[3]));
-            } else {
-                for (int q = 0; q < 4 && v0 + q < n_cells; ++q) score_out[v0 + q] = p[q];
-            }
-        }
-        uint32_t segw = nib << b0;
-        segw |= __shfl_xor_sync(0xffffffffu, segw, 1);
-        segw |= __shfl_xor_sync(0xffffffffu, segw, 2);
-        segw |= __shfl_xor_sync(0xffffffffu, segw, 4);
-        uint32_t cnt = 0;
-        if (live && (threadIdx.x & 7) == 0) {
-            seg_bits[wi] = segw;
-            if (seg_out) seg_out[wi] = segw;
-            cnt = __popc(segw);
-        }
-        if (d_nseg) {
+        float wv[4], zv[4];
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
-            if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(d_nseg, (unsigned long long)cnt);
+        for (int q = 0; q < 4; ++q) {
+            const uint32_t s0 = sl[q] != 0xffffffffu ? sl[q] : 0u;
+            wv[q] = __ldcs(W + s0);
+            zv[q] = __ldcs(Z + s0);
         }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if (sl[q] == 0xffffffffu) continue;
+            const float p = zv[q] > eps ? __fdiv_rn(wv[q], zv[q]) : 0.f;
+            const bool sg = p >= tau_cons;
+            t1[b[q]] = p;
+            segw |= (sg ? 1u : 0u) << b[q];
+            if (vmask_out) vmask_out[sl[q]] = sg ? bits[sl[q]] : 0u;
+        }
+    }
+    __syncwarp();
+    // stream the warp's 1024 scores out: 8 coalesced float4 stores per lane
+    const int64_t v_warp = (w - lane) * 32;  // first voxel of the warp
+    if (score_out) {
+        const bool vec = ((reinterpret_cast<uintptr_t>(score_out) & 15) == 0) &&
+                         v_warp + 1024 <= n_cells;
+        if (vec) {
+            float4* dst = reinterpret_cast<float4*>(score_out + v_warp);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) __stcs(dst + lane + 32 * i, t4[lane + 32 * i]);
+        } else {
+            const float* src = reinterpret_cast<const float*>(t4);
+            for (int i = lane; i < 1024; i += 32)
+                if (v_warp + i < n_cells) score_out[v_warp + i] = src[i];
+        }
+    }
+    uint32_t cnt = 0;
+    if (live) {
+        seg_bits[w] = segw;
+        if (seg_out) seg_out[w] = segw;
+        cnt = __popc(segw);
+    }
+    if (d_nseg) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+        if (lane == 0 && cnt) atomicAdd(d_nseg, (unsigned long long)cnt);
     }
 }
 
@@ -381,8 +432,14 @@ __global__ void __launch_bounds__(kThreads) k_label(const float* __restrict__ xy
                 float dh, dl;
                 two_sum(xh[q], -G.origin[q], dh, dl);
                 dl = __fadd_rn(dl, xl[q]);
-                const float sh = __fdiv_rn(dh, G.h);
-                const float sl = __fdiv_rn(__fadd_rn(__fmaf_rn(-sh, G.h, dh), dl), G.h);
+                float sh, sl;
+                if (G.inv_h != 0.f) {  // power-of-two edge: scaling is exact
+                    sh = __fmul_rn(dh, G.inv_h);
+                    sl = __fmul_rn(dl, G.inv_h);
+                } else {
+                    sh = __fdiv_rn(dh, G.h);
+                    sl = __fdiv_rn(__fadd_rn(__fmaf_rn(-sh, G.h, dh), dl), G.h);
+                }
                 const float f = floor_df(sh, sl);
                 if (!(f >= 0.f && f < (float)G.g)) inside = false;
                 idx[q] = inside ? (int32_t)f : 0;
@@ -399,6 +456,7 @@ __global__ void __launch_bounds__(kThreads) k_label(const float* __restrict__ xy
 // ---------------------------------------------------------------------------
 // adjoint
 // ---------------------------------------------------------------------------
+template <bool kContracted, int kChunks>
 __global__ void __launch_bounds__(kThreads) k_backward(
     const int32_t* __restrict__ active, const int32_t* __restrict__ d_n, GridC G, FuseC F,
     const __grid_constant__ ViewBatch VB, const __grid_constant__ BackPtrs BP,
@@ -411,13 +469,15 @@ __global__ void __launch_bounds__(kThreads) k_backward(
         const float z = Z[a];
         if (gP == 0.f || !(z > F.eps)) continue;
         const float P = __fdiv_rn(W[a], z);
-        const VoxelGeom vg = voxel_geom(lin, G, F.gamma);
+        const VoxelGeom vg = voxel_geom<kContracted>(lin, G, F.gamma);
         if (!vg.ok) continue;
         const float gz = __fdiv_rn(gP, z);
         const float k2 = __fmul_rn(__fmul_rn(2.f, F.alpha1), __fmul_rn(vg.invDelta, vg.invDelta));
-        for (int32_t v = 0; v < VB.n; ++v) {
+#pragma unroll
+        for (int v = 0; v < kChunks * kViewChunk; ++v) {
+            if (v >= VB.n) break;
             Vote vt;
-            if (!eval_vote(VB.v[v], vg, F, vt)) continue;
+            if (!eval_vote<kContracted>(VB.v[v], vg, F, vt)) continue;
             if (BP.gm[v]) {
                 float dm = __fmul_rn(gz, vt.w);
                 if (VB.v[v].mask_type == kMaskLogit)
@@ -432,18 +492,32 @@ __global__ void __launch_bounds__(kThreads) k_backward(
     }
 }
 
+template <bool kContracted, int kChunks = 1>
+cudaError_t launch_backward_chunks(int chunks, int blocks, cudaStream_t s, const int32_t* active,
+                                   const int32_t* d_n, const GridC& G, const FuseC& F,
+                                   const ViewBatch& vb, const BackPtrs& bp, const float* W,
+                                   const float* Z, const float* grad_score, int32_t dense) {
+    if constexpr (kChunks < kMaxViews / kViewChunk) {
+        if (chunks > kChunks)
+            return launch_backward_chunks<kContracted, kChunks + 1>(
+                chunks, blocks, s, active, d_n, G, F, vb, bp, W, Z, grad_score, dense);
+    }
+    k_backward<kContracted, kChunks><<<blocks, kThreads, 0, s>>>(active, d_n, G, F, vb, bp, W, Z,
+                                                                 grad_score, dense);
+    return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------------------
 // misc
 // ---------------------------------------------------------------------------
+template <bool kContracted>
 __global__ void k_debug_project(const int32_t* __restrict__ active, const int32_t* __restrict__ d_n,
                                 GridC G, FuseC F, ViewC V, int32_t* __restrict__ pix_out) {
     const int32_t n = *d_n;
     for (int32_t a = blockIdx.x * blockDim.x + threadIdx.x; a < n; a += gridDim.x * blockDim.x) {
-        const VoxelGeom vg = voxel_geom(__ldg(active + a), G, F.gamma);
-        int32_t pix = -1;
+        const VoxelGeom vg = voxel_geom<kContracted>(__ldg(active + a), G, F.gamma);
         float ph, pl;
-        if (!(vg.ok && project_voxel(V, vg, F.z_near, pix, ph, pl))) pix = -1;
-        pix_out[a] = pix;
+        pix_out[a] = vg.ok ? project<kContracted>(V, vg, F.z_near, ph, pl) : -1;
     }
 }
 
@@ -545,11 +619,43 @@ divas_status check_camera(divas_ctx* c, const divas_camera* cam) {
     return DIVAS_OK;
 }
 
-ViewC make_view(const divas_camera& cam, const float* depth, const void* mask, int32_t mask_type,
-                int32_t index) {
+// Per-view constants.  Plain grids: lattice form p = T + M n, n = 2 idx + 1,
+// T = R o + t, M = (h/2) R, each split into an exact hi part (multiples of a
+// power of two 2^q with |T| + sum |M| (2g - 1) < 2^(q+24), so that the device
+// FMA chain over hi parts is exact) and a lo remainder.
+ViewC make_view(const divas_camera& cam, const GridC& G, const float* depth, const void* mask,
+                int32_t mask_type, int32_t index) {
     ViewC v;
-    memcpy(v.R, cam.R, sizeof(v.R));
-    memcpy(v.t, cam.t, sizeof(v.t));
+    memset(&v, 0, sizeof(v));
+    if (G.contracted) {
+        memcpy(v.A, cam.R, sizeof(cam.R));
+        memcpy(v.C, cam.t, sizeof(cam.t));
+    } else {
+        const double hh = 0.5 * (double)G.h;
+        const double nmax = 2.0 * G.g - 1.0;
+        for (int r = 0; r < 3; ++r) {
+            double T = (double)cam.t[r];
+            double M[3];
+            double bmax = 0.0;
+            for (int j = 0; j < 3; ++j) {
+                T += (double)cam.R[3 * r + j] * (double)G.origin[j];
+                M[j] = hh * (double)cam.R[3 * r + j];
+                bmax += fabs(M[j]) * nmax;
+            }
+            bmax += fabs(T);
+            int ex = 0;
+            frexp(bmax * 1.001 + 1e-300, &ex);  // bmax * 1.001 < 2^ex
+            const double quantum = ldexp(1.0, ex - 24);
+            for (int j = 0; j < 3; ++j) {
+                const double hi = rint(M[j] / quantum) * quantum;
+                v.A[3 * r + j] = (float)hi;
+                v.B[3 * r + j] = (float)(M[j] - hi);
+            }
+            const double thi = rint(T / quantum) * quantum;
+            v.C[r] = (float)thi;
+            v.E[r] = (float)(T - thi);
+        }
+    }
     v.fx = cam.fx;
     v.fy = cam.fy;
     v.cx = cam.cx;
@@ -575,8 +681,8 @@ float logit_threshold(float tau) {
 divas_status build_active(divas_ctx* c, const uint8_t* occ, const int32_t* coords, int64_t n_coords,
                           cudaStream_t s) {
     if (c->grid.kind == 0) {
-        k_occ_bits<<<grid_for(c->n_words, c->sm_count, 32), kThreads, 0, s>>>(occ, c->n_cells,
-                                                                             c->n_words, c->occ_bits);
+        k_occ_bits<<<c->n_cblocks, kThreads, 0, s>>>(occ, c->n_cells, c->n_words, c->occ_bits,
+                                                     c->block_sums);
         DIVAS_LAUNCHED(c, "k_occ_bits");
     } else {
         DIVAS_CUDA(c, cudaMemsetAsync(c->occ_bits, 0, c->n_words * 4, s));
@@ -585,9 +691,9 @@ divas_status build_active(divas_ctx* c, const uint8_t* occ, const int32_t* coord
                 coords, n_coords, c->grid.g, c->occ_bits, c->d_status);
             DIVAS_LAUNCHED(c, "k_scatter_coords");
         }
+        k_block_popc<<<c->n_cblocks, kThreads, 0, s>>>(c->occ_bits, c->n_words, c->block_sums);
+        DIVAS_LAUNCHED(c, "k_block_popc");
     }
-    k_block_popc<<<c->n_cblocks, kThreads, 0, s>>>(c->occ_bits, c->n_words, c->block_sums);
-    DIVAS_LAUNCHED(c, "k_block_popc");
     k_scan_blocks<<<1, kThreads, 0, s>>>(c->block_sums, c->n_cblocks, c->cap, c->d_total, c->d_n,
                                          c->d_status);
     DIVAS_LAUNCHED(c, "k_scan_blocks");
@@ -674,6 +780,12 @@ divas_status divas_fuse_init(divas_ctx** out, const divas_grid* grid, const uint
     c->G.h = grid->h;
     c->G.g = grid->g;
     c->G.contracted = grid->contracted ? 1 : 0;
+    {
+        int ex = 0;
+        const double fr = frexp((double)grid->h, &ex);
+        c->G.inv_h = fr == 0.5 ? (float)ldexp(1.0, 1 - ex) : 0.f;
+        c->G.pad = 0;
+    }
     c->F.gamma = params->gamma;
     c->F.alpha1 = params->alpha1;
     c->F.tau_m = params->tau_mask;
@@ -762,12 +874,20 @@ divas_status divas_fuse_set_occupancy(divas_ctx* c, const uint8_t* occ_dense, co
 
 static divas_status launch_fuse(divas_ctx* c, const ViewBatch& vb, cudaStream_t s) {
     const int blocks = grid_for(c->cap, c->sm_count);
-    if (c->n_views == 0)
-        k_fuse<false><<<blocks, kThreads, 0, s>>>(c->active, c->d_n, c->G, c->F, vb, c->W, c->Z,
-                                                  c->bits);
+    const bool acc = c->n_views > 0;
+    const int chunks = (vb.n + kViewChunk - 1) / kViewChunk;
+    cudaError_t e;
+    if (c->G.contracted)
+        e = acc ? launch_fuse_chunks<true, true>(chunks, blocks, s, c->active, c->d_n, c->G, c->F,
+                                                 vb, c->W, c->Z, c->bits)
+                : launch_fuse_chunks<false, true>(chunks, blocks, s, c->active, c->d_n, c->G,
+                                                  c->F, vb, c->W, c->Z, c->bits);
     else
-        k_fuse<true><<<blocks, kThreads, 0, s>>>(c->active, c->d_n, c->G, c->F, vb, c->W, c->Z,
-                                                 c->bits);
+        e = acc ? launch_fuse_chunks<true, false>(chunks, blocks, s, c->active, c->d_n, c->G,
+                                                  c->F, vb, c->W, c->Z, c->bits)
+                : launch_fuse_chunks<false, false>(chunks, blocks, s, c->active, c->d_n, c->G,
+                                                   c->F, vb, c->W, c->Z, c->bits);
+    if (e != cudaSuccess) return cuda_fail(c, e, "k_fuse");
     DIVAS_LAUNCHED(c, "k_fuse");
     c->n_views += vb.n;
     return DIVAS_OK;
@@ -783,7 +903,7 @@ divas_status divas_fuse_add_view(divas_ctx* c, const divas_camera* cam, const fl
     ViewBatch vb;
     memset(&vb, 0, sizeof(vb));
     vb.n = 1;
-    vb.v[0] = make_view(*cam, depth, mask, mask_type, c->n_views);
+    vb.v[0] = make_view(*cam, c->G, depth, mask, mask_type, c->n_views);
     return launch_fuse(c, vb, S(stream));
 }
 
@@ -801,8 +921,8 @@ divas_status divas_fuse_add_views(divas_ctx* c, const divas_view* views, int32_t
         if (!views[k].depth || !views[k].mask) return fail(c, DIVAS_E_INVALID, "depth or mask is NULL");
         if (views[k].mask_type < 0 || views[k].mask_type > 2)
             return fail(c, DIVAS_E_INVALID, "bad mask_type");
-        vb.v[k] = make_view(views[k].cam, views[k].depth, views[k].mask, views[k].mask_type,
-                            c->n_views + k);
+        vb.v[k] = make_view(views[k].cam, c->G, views[k].depth, views[k].mask,
+                            views[k].mask_type, c->n_views + k);
     }
     return launch_fuse(c, vb, S(stream));
 }
@@ -817,8 +937,7 @@ divas_status divas_fuse_finalize(divas_ctx* c, float* score_out, uint32_t* seg_b
         // no view folded in yet: W = Z = 0 (after init/reset), scores are all 0
     }
     if (c->grid.kind == 0) {
-        const int64_t quads = (c->n_cells + 3) / 4;
-        k_finalize_dense<<<grid_for(quads, c->sm_count, 32), kThreads, 0, s>>>(
+        k_finalize_dense<<<(unsigned)((c->n_words + kThreads - 1) / kThreads), kThreads, 0, s>>>(
             c->occ_bits, c->word_prefix, c->d_n, c->n_cells, c->W, c->Z, c->bits, c->F.eps,
             c->F.tau_cons, score_out, c->seg_bits, seg_bits_out, vmask_out, nseg);
         DIVAS_LAUNCHED(c, "k_finalize_dense");
@@ -846,7 +965,7 @@ divas_status divas_label_points(divas_ctx* c, const float* xyz, int64_t n, uint8
     if (n < 0 || (n > 0 && (!xyz || !labels_out)))
         return fail(c, DIVAS_E_INVALID, "bad point arguments");
     if (n == 0) return DIVAS_OK;
-    k_label<<<grid_for(n, c->sm_count, 32), kThreads, 0, S(stream)>>>(xyz, n, c->G, c->seg_bits,
+    k_label<<<grid_for(n, c->sm_count, 64), kThreads, 0, S(stream)>>>(xyz, n, c->G, c->seg_bits,
                                                                        labels_out);
     DIVAS_LAUNCHED(c, "k_label");
     return DIVAS_OK;
@@ -918,12 +1037,21 @@ divas_status divas_fuse_backward(divas_ctx* c, const divas_view* views, int32_t 
         if (!views[k].depth || !views[k].mask) return fail(c, DIVAS_E_INVALID, "depth or mask is NULL");
         if (views[k].mask_type < 0 || views[k].mask_type > 2)
             return fail(c, DIVAS_E_INVALID, "bad mask_type");
-        vb.v[k] = make_view(views[k].cam, views[k].depth, views[k].mask, views[k].mask_type, k);
+        vb.v[k] = make_view(views[k].cam, c->G, views[k].depth, views[k].mask,
+                            views[k].mask_type, k);
         bp.gm[k] = grad_mask ? grad_mask[k] : nullptr;
         bp.gd[k] = grad_depth ? grad_depth[k] : nullptr;
     }
-    k_backward<<<grid_for(c->cap, c->sm_count), kThreads, 0, S(stream)>>>(
-        c->active, c->d_n, c->G, c->F, vb, bp, c->W, c->Z, grad_score, c->grid.kind == 0 ? 1 : 0);
+    const int blocks = grid_for(c->cap, c->sm_count);
+    const int32_t dense = c->grid.kind == 0 ? 1 : 0;
+    const int chunks = (n_views + kViewChunk - 1) / kViewChunk;
+    cudaError_t e =
+        c->G.contracted
+            ? launch_backward_chunks<true>(chunks, blocks, S(stream), c->active, c->d_n, c->G,
+                                           c->F, vb, bp, c->W, c->Z, grad_score, dense)
+            : launch_backward_chunks<false>(chunks, blocks, S(stream), c->active, c->d_n, c->G,
+                                            c->F, vb, bp, c->W, c->Z, grad_score, dense);
+    if (e != cudaSuccess) return cuda_fail(c, e, "k_backward");
     DIVAS_LAUNCHED(c, "k_backward");
     return DIVAS_OK;
 }
@@ -934,9 +1062,14 @@ divas_status divas_debug_project(divas_ctx* c, const divas_camera* cam, int32_t*
     divas_status st = check_camera(c, cam);
     if (st != DIVAS_OK) return st;
     if (!pix_out) return fail(c, DIVAS_E_INVALID, "pix_out is NULL");
-    ViewC v = make_view(*cam, nullptr, nullptr, 0, 0);
-    k_debug_project<<<grid_for(c->cap, c->sm_count), kThreads, 0, S(stream)>>>(c->active, c->d_n,
-                                                                             c->G, c->F, v, pix_out);
+    ViewC v = make_view(*cam, c->G, nullptr, nullptr, 0, 0);
+    const int blocks = grid_for(c->cap, c->sm_count);
+    if (c->G.contracted)
+        k_debug_project<true><<<blocks, kThreads, 0, S(stream)>>>(c->active, c->d_n, c->G, c->F,
+                                                                  v, pix_out);
+    else
+        k_debug_project<false><<<blocks, kThreads, 0, S(stream)>>>(c->active, c->d_n, c->G, c->F,
+                                                                   v, pix_out);
     DIVAS_LAUNCHED(c, "k_debug_project");
     return DIVAS_OK;
 }

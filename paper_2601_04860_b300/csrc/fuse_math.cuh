@@ -1,26 +1,39 @@
 // fuse_math.cuh -- per-voxel, per-view arithmetic of the thick-path fusion.
 //
-// One __device__ function (`vote`) evaluates one (voxel, view) pair exactly
-// as Algorithms A.2 / B.5 state the thick path (Sec. 3.5): project the voxel
-// centre, read depth and mask at the pixel, gate on the mask (m >= tau) and
-// on depth consistency (|p_z - D| <= gamma h_v), and add the Gaussian depth
-// weight w = exp(-alpha1 (e / Delta)^2) (Eq. gs-depthweight with the depth
-// band [D - Delta, D + Delta]) to W and Z (Eq. vmask).  Every kernel that
-// folds views in (single view, many views, batched sessions, the adjoint)
-// calls these functions, and the library is compiled with -fmad=false, so
-// all of them produce bitwise identical results.
+// One (voxel, view) pair is evaluated exactly as Algorithms A.2 / B.5 state
+// the thick path (Sec. 3.5): project the voxel centre, read depth and mask at
+// the pixel, gate on the mask (m >= tau) and on depth consistency
+// (|p_z - D| <= gamma h_v), and add the Gaussian depth weight
+// w = exp(-alpha1 (e / Delta)^2) (Eq. gs-depthweight with the depth band
+// [D - Delta, D + Delta]) to W and Z (Eq. vmask).  The evaluation is split in
+// three steps -- project(), load_raster(), decide() -- so that the fusion
+// kernel can issue the raster loads of several views back to back while
+// every kernel (single view, many views, adjoint, projection hook) still runs
+// the very same arithmetic.  The library is compiled with -fmad=false, so
+// only the explicit __fmaf_rn below are fused and all kernels round alike.
 //
-// Precision.  The decisions (pixel index, gates) and the weights must agree
-// with a double-precision evaluation.  Plain FP32 would not do: p_z ~ 2.5 is
-// rounded to ~2.4e-7 while the depth residual e = p_z - D is compared with
-// Delta ~ 8e-3, so e / Delta would carry ~4e-5 relative error.  The camera
-// coordinates are therefore evaluated as unevaluated sums hi + lo of two
-// floats (error-free products via FMA and error-free sums, i.e. the
-// compensated dot product of Ogita, Rump and Oishi, "Accurate sum and dot
-// product", SIAM J. Sci. Comput. 2005), and e is formed as (p_z,hi - D) +
-// p_z,lo, where p_z,hi - D is exact by Sterbenz's lemma whenever the gate can
-// pass.  Voxel centres are likewise kept as hi + lo pairs, including the
-// inverse scene contraction of contracted grids.
+// Precision.  Decisions (pixel index, gates) and weights must agree with a
+// double-precision evaluation.  Plain FP32 would not do: p_z ~ 2.5 carries
+// ~2.4e-7 rounding while e = p_z - D is compared with Delta ~ 8e-3, so e /
+// Delta would be off by ~4e-5.  Two exact schemes are used:
+//
+//  * Plain grids (lattice projection).  Voxel centres are x = o + (h/2) n
+//    with n = 2 idx + 1 an odd integer (|n| < 2^11), so camera coordinates
+//    are p = T + M n with T = R o + t and M = (h/2) R, formed on the host in
+//    double.  Each is split into a "hi" part rounded to a multiple of a
+//    power of two 2^q -- chosen per row so that |T| + sum |M| (2g - 1) <
+//    2^(q+24) -- and a small "lo" remainder.  Every partial sum of
+//    T_hi + M_hi n is then a multiple of 2^q below 2^(q+24): the FMA chain
+//    is exact in FP32.  The lo chain adds a term of relative size 2^-36.
+//    p = hi + lo costs 6 FMA per coordinate.
+//
+//  * Contracted grids.  Centres are uncontracted in hi + lo pairs and
+//    projected with a compensated dot product (error-free products via FMA
+//    and error-free sums: Ogita, Rump and Oishi, "Accurate sum and dot
+//    product", SIAM J. Sci. Comput. 2005).
+//
+// In both, e = (p_z,hi - D) + p_z,lo, where p_z,hi - D is exact by
+// Sterbenz's lemma whenever the depth gate can pass.
 #pragma once
 
 #include <cfloat>
@@ -30,6 +43,7 @@
 namespace divas {
 
 constexpr int kMaxViews = 32;
+constexpr int kViewChunk = 4;  // views whose raster loads are issued together
 
 // ---------------------------------------------------------------------------
 // error-free transformations (round-to-nearest FP32, no contraction)
@@ -64,9 +78,14 @@ __device__ __forceinline__ void dot3c(float a0, float a1, float a2, const float*
 // ---------------------------------------------------------------------------
 // constants
 // ---------------------------------------------------------------------------
-struct ViewC {  // one view, passed by value inside kernel parameters
-    float R[9];
-    float t[3];
+// One view, passed by value inside kernel parameters.
+//   plain grid:      A = M_hi, B = M_lo (row-major 3x3), C = T_hi, E = T_lo
+//   contracted grid: A = R, C = t (B, E unused)
+struct ViewC {
+    float A[9];
+    float B[9];
+    float C[3];
+    float E[3];
     float fx, fy, cx, cy;
     float Wf, Hf;    // raster size as floats (frame test)
     int32_t W;       // row pitch in elements
@@ -88,6 +107,8 @@ struct GridC {
     float h;
     int32_t g;
     int32_t contracted;
+    float inv_h;  // 1/h when h is a power of two (exact), else 0
+    int32_t pad;
 };
 
 struct FuseC {
@@ -98,14 +119,15 @@ struct FuseC {
 enum : int32_t { kMaskF32 = 0, kMaskF16 = 1, kMaskLogit = 2 };
 
 // ---------------------------------------------------------------------------
-// voxel centre (hi + lo per axis) and its depth tolerance Delta = gamma h_v
+// voxel centre and its depth tolerance Delta = gamma h_v
 // ---------------------------------------------------------------------------
 struct VoxelGeom {
-    float xh[3], xl[3];
+    float xh[3], xl[3];  // plain grid: xh = n = 2 idx + 1, xl unused
     float Delta, invDelta;
     bool ok;  // false: contracted centre with |c| >= 2 (no world position)
 };
 
+template <bool kContracted>
 __device__ __forceinline__ VoxelGeom voxel_geom(int32_t lin, const GridC& G, float gamma) {
     VoxelGeom vg;
     const int32_t g = G.g;
@@ -113,6 +135,16 @@ __device__ __forceinline__ VoxelGeom voxel_geom(int32_t lin, const GridC& G, flo
     const int32_t r = lin / g;
     const int32_t j = r % g;
     const int32_t k = r / g;
+    vg.ok = true;
+    if (!kContracted) {
+        vg.xh[0] = (float)(2 * i + 1);
+        vg.xh[1] = (float)(2 * j + 1);
+        vg.xh[2] = (float)(2 * k + 1);
+        vg.xl[0] = vg.xl[1] = vg.xl[2] = 0.f;
+        vg.Delta = __fmul_rn(gamma, G.h);
+        vg.invDelta = __frcp_rn(vg.Delta);
+        return vg;
+    }
     const float idx[3] = {(float)i, (float)j, (float)k};
     float ch[3], cl[3];
 #pragma unroll
@@ -124,58 +156,49 @@ __device__ __forceinline__ VoxelGeom voxel_geom(int32_t lin, const GridC& G, flo
         cl[a] = __fadd_rn(se, pe);
     }
     float hv = G.h;
-    vg.ok = true;
-    if (!G.contracted) {
+    // n2 = |c|^2 as hi + lo
+    float s = 0.f, e = 0.f;
 #pragma unroll
-        for (int a = 0; a < 3; ++a) { vg.xh[a] = ch[a]; vg.xl[a] = cl[a]; }
-    } else {
-        // n2 = |c|^2 as hi + lo
-        float s = 0.f, e = 0.f;
+    for (int a = 0; a < 3; ++a) {
+        float p, pe, t;
+        two_prod(ch[a], ch[a], p, pe);
+        two_sum(s, p, s, t);
+        e = __fadd_rn(e, __fadd_rn(__fadd_rn(t, pe), __fmul_rn(2.f, __fmul_rn(ch[a], cl[a]))));
+    }
+    float n2h, n2l;
+    two_sum(s, e, n2h, n2l);
+    const bool outside = (n2h > 4.f) || (n2h == 4.f && n2l >= 0.f);
+    const bool inner = (n2h < 1.f) || (n2h == 1.f && n2l <= 0.f);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) { vg.xh[a] = ch[a]; vg.xl[a] = cl[a]; }
+    if (outside) {
+        vg.ok = false;
+    } else if (!inner) {
+        // rho = sqrt(n2) as hi + lo
+        const float rh = __fsqrt_rn(n2h);
+        const float rl = __fdiv_rn(__fadd_rn(__fmaf_rn(-rh, rh, n2h), n2l), __fmul_rn(2.f, rh));
+        // d = 2 - rho (2 - rh is exact for rh in [1, 2])
+        float dh, dl;
+        two_sum(__fsub_rn(2.f, rh), -rl, dh, dl);
+        // den = rho d
+        float qh, ql;
+        two_prod(rh, dh, qh, ql);
+        ql = __fadd_rn(ql, __fadd_rn(__fmul_rn(rh, dl), __fmul_rn(rl, dh)));
+        two_sum(qh, ql, qh, ql);
+        // sc = 1 / den
+        const float sh = __frcp_rn(qh);
+        const float res = __fsub_rn(__fmaf_rn(-sh, qh, 1.f), __fmul_rn(sh, ql));
+        const float sl = __fmul_rn(sh, res);
+        // x = c sc
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            float p, pe, t;
-            two_prod(ch[a], ch[a], p, pe);
-            two_sum(s, p, s, t);
-            e = __fadd_rn(e, __fadd_rn(__fadd_rn(t, pe), __fmul_rn(2.f, __fmul_rn(ch[a], cl[a]))));
+            float xh, xe;
+            two_prod(ch[a], sh, xh, xe);
+            xe = __fadd_rn(xe, __fadd_rn(__fmul_rn(ch[a], sl), __fmul_rn(cl[a], sh)));
+            two_sum(xh, xe, vg.xh[a], vg.xl[a]);
         }
-        float n2h, n2l;
-        two_sum(s, e, n2h, n2l);
-        const bool outside = (n2h > 4.f) || (n2h == 4.f && n2l >= 0.f);
-        const bool inner = (n2h < 1.f) || (n2h == 1.f && n2l <= 0.f);
-        if (outside) {
-            vg.ok = false;
-#pragma unroll
-            for (int a = 0; a < 3; ++a) { vg.xh[a] = ch[a]; vg.xl[a] = cl[a]; }
-        } else if (inner) {
-#pragma unroll
-            for (int a = 0; a < 3; ++a) { vg.xh[a] = ch[a]; vg.xl[a] = cl[a]; }
-        } else {
-            // rho = sqrt(n2) as hi + lo
-            const float rh = __fsqrt_rn(n2h);
-            const float rl = __fdiv_rn(__fadd_rn(__fmaf_rn(-rh, rh, n2h), n2l), __fmul_rn(2.f, rh));
-            // d = 2 - rho (2 - rh is exact for rh in [1, 2])
-            float dh, dl;
-            two_sum(__fsub_rn(2.f, rh), -rl, dh, dl);
-            // den = rho d
-            float qh, ql;
-            two_prod(rh, dh, qh, ql);
-            ql = __fadd_rn(ql, __fadd_rn(__fmul_rn(rh, dl), __fmul_rn(rl, dh)));
-            two_sum(qh, ql, qh, ql);
-            // sc = 1 / den
-            const float sh = __frcp_rn(qh);
-            const float res = __fsub_rn(__fmaf_rn(-sh, qh, 1.f), __fmul_rn(sh, ql));
-            const float sl = __fmul_rn(sh, res);
-            // x = c sc
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                float xh, xe;
-                two_prod(ch[a], sh, xh, xe);
-                xe = __fadd_rn(xe, __fadd_rn(__fmul_rn(ch[a], sl), __fmul_rn(cl[a], sh)));
-                two_sum(xh, xe, vg.xh[a], vg.xl[a]);
-            }
-            const float d = __fadd_rn(dh, dl);
-            hv = __fdiv_rn(G.h, __fmul_rn(d, d));  // largest stretch of the inverse contraction
-        }
+        const float d = __fadd_rn(dh, dl);
+        hv = __fdiv_rn(G.h, __fmul_rn(d, d));  // largest stretch of the inverse contraction
     }
     vg.Delta = __fmul_rn(gamma, hv);
     vg.invDelta = __frcp_rn(vg.Delta);
@@ -183,37 +206,76 @@ __device__ __forceinline__ VoxelGeom voxel_geom(int32_t lin, const GridC& G, flo
 }
 
 // ---------------------------------------------------------------------------
-// projection: pixel index, and camera depth p_z as hi + lo
+// step 1: projection -> pixel index (or -1) and camera depth p_z = hi + lo
+// (branch-free: every quantity is computed, validity is a predicate)
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ bool project_voxel(const ViewC& V, const VoxelGeom& vg, float z_near,
-                                              int32_t& pix, float& pzh, float& pzl) {
-    dot3c(V.R[6], V.R[7], V.R[8], vg.xh, vg.xl, V.t[2], pzh, pzl);
-    if (!(pzh > z_near)) return false;
-    float pxh, pxl, pyh, pyl;
-    dot3c(V.R[0], V.R[1], V.R[2], vg.xh, vg.xl, V.t[0], pxh, pxl);
-    dot3c(V.R[3], V.R[4], V.R[5], vg.xh, vg.xl, V.t[1], pyh, pyl);
-    const float inv = __frcp_rn(pzh);
-    const float u = __fmaf_rn(V.fx, __fmul_rn(pxh, inv), V.cx);
-    const float v = __fmaf_rn(V.fy, __fmul_rn(pyh, inv), V.cy);
-    if (!(u >= 0.f && u < V.Wf && v >= 0.f && v < V.Hf)) return false;
-    pix = (int32_t)v * V.W + (int32_t)u;  // u, v >= 0: truncation is floor
-    return true;
+__device__ __forceinline__ void lattice_row(const float* Mh, const float* Ml, float Th, float Tl,
+                                            const float* n, float& hi, float& lo) {
+    hi = __fmaf_rn(Mh[0], n[0], __fmaf_rn(Mh[1], n[1], __fmaf_rn(Mh[2], n[2], Th)));  // exact
+    lo = __fmaf_rn(Ml[0], n[0], __fmaf_rn(Ml[1], n[1], __fmaf_rn(Ml[2], n[2], Tl)));
 }
 
-// mask probability m at pix and whether it passes the thick-path gate
-__device__ __forceinline__ bool read_mask(const ViewC& V, int32_t pix, const FuseC& F, float& m) {
-    if (V.mask_type == kMaskF16) {
-        const unsigned short b = __ldg(reinterpret_cast<const unsigned short*>(V.mask) + pix);
-        m = __half2float(__ushort_as_half(b));
-        return m >= F.tau_m;
+template <bool kContracted>
+__device__ __forceinline__ int32_t project(const ViewC& V, const VoxelGeom& vg, float z_near,
+                                           float& pzh, float& pzl) {
+    float px, py, pz;
+    if (!kContracted) {
+        float h, l;
+        lattice_row(V.A + 6, V.B + 6, V.C[2], V.E[2], vg.xh, pzh, pzl);
+        lattice_row(V.A, V.B, V.C[0], V.E[0], vg.xh, h, l);
+        px = __fadd_rn(h, l);
+        lattice_row(V.A + 3, V.B + 3, V.C[1], V.E[1], vg.xh, h, l);
+        py = __fadd_rn(h, l);
+        pz = __fadd_rn(pzh, pzl);
+    } else {
+        float h, l;
+        dot3c(V.A[6], V.A[7], V.A[8], vg.xh, vg.xl, V.C[2], pzh, pzl);
+        dot3c(V.A[0], V.A[1], V.A[2], vg.xh, vg.xl, V.C[0], h, l);
+        px = h;
+        dot3c(V.A[3], V.A[4], V.A[5], vg.xh, vg.xl, V.C[1], h, l);
+        py = h;
+        pz = pzh;
     }
-    const float raw = __ldg(reinterpret_cast<const float*>(V.mask) + pix);
-    if (V.mask_type == kMaskLogit) {
-        m = __frcp_rn(__fadd_rn(1.f, expf(-raw)));
-        return raw >= F.logit_tau;
-    }
-    m = raw;
-    return m >= F.tau_m;
+    const bool front = pz > z_near;
+    const float inv = __frcp_rn(front ? pz : 1.f);
+    const float u = __fmaf_rn(V.fx, __fmul_rn(px, inv), V.cx);
+    const float v = __fmaf_rn(V.fy, __fmul_rn(py, inv), V.cy);
+    const bool in = front && u >= 0.f && u < V.Wf && v >= 0.f && v < V.Hf;
+    // u, v >= 0 inside the frame: truncation is floor
+    return in ? (int32_t)v * V.W + (int32_t)u : -1;
+}
+
+// ---------------------------------------------------------------------------
+// step 2: raster reads (depth and the mask's raw value, widened to float);
+// an invalid pixel reads pixel 0 (always in bounds) and is discarded later
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void load_raster(const ViewC& V, int32_t pix, float& D, float& raw) {
+    const int32_t p = pix >= 0 ? pix : 0;
+    D = __ldg(V.depth + p);
+    if (V.mask_type == kMaskF16)
+        raw = __half2float(
+            __ushort_as_half(__ldg(reinterpret_cast<const unsigned short*>(V.mask) + p)));
+    else
+        raw = __ldg(reinterpret_cast<const float*>(V.mask) + p);
+}
+
+// ---------------------------------------------------------------------------
+// step 3: gates (predicates) and, for an accepted vote, the weight
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool gates(const ViewC& V, const VoxelGeom& vg, const FuseC& F,
+                                      int32_t pix, float pzh, float pzl, float D, float raw,
+                                      float& e) {
+    e = __fadd_rn(__fsub_rn(pzh, D), pzl);
+    const float thr = V.mask_type == kMaskLogit ? F.logit_tau : F.tau_m;
+    // +inf, NaN or <= 0 depth: no surface; mask gate; depth gate
+    return pix >= 0 && D > 0.f && D <= FLT_MAX && raw >= thr && fabsf(e) <= vg.Delta;
+}
+
+__device__ __forceinline__ void weight(const ViewC& V, const VoxelGeom& vg, const FuseC& F,
+                                       float raw, float e, float& m, float& w) {
+    m = V.mask_type == kMaskLogit ? __frcp_rn(__fadd_rn(1.f, expf(-raw))) : raw;
+    const float r = __fmul_rn(e, vg.invDelta);
+    w = expf(-__fmul_rn(F.alpha1, __fmul_rn(r, r)));
 }
 
 // One accepted thick-path vote: everything the adjoint needs.
@@ -222,32 +284,54 @@ struct Vote {
     float m, w, e;
 };
 
+template <bool kContracted>
 __device__ __forceinline__ bool eval_vote(const ViewC& V, const VoxelGeom& vg, const FuseC& F,
                                           Vote& out) {
-    int32_t pix;
-    float pzh, pzl;
-    if (!project_voxel(V, vg, F.z_near, pix, pzh, pzl)) return false;
-    const float D = __ldg(V.depth + pix);
-    if (!(D > 0.f && D <= FLT_MAX)) return false;  // +inf, NaN, <= 0: no surface
-    float m;
-    if (!read_mask(V, pix, F, m)) return false;
-    const float e = __fadd_rn(__fsub_rn(pzh, D), pzl);
-    if (!(fabsf(e) <= vg.Delta)) return false;
-    const float r = __fmul_rn(e, vg.invDelta);
+    float pzh, pzl, D, raw;
+    const int32_t pix = project<kContracted>(V, vg, F.z_near, pzh, pzl);
+    load_raster(V, pix, D, raw);
+    if (!gates(V, vg, F, pix, pzh, pzl, D, raw, out.e)) return false;
+    weight(V, vg, F, raw, out.e, out.m, out.w);
     out.pix = pix;
-    out.m = m;
-    out.e = e;
-    out.w = expf(-__fmul_rn(F.alpha1, __fmul_rn(r, r)));
     return true;
 }
 
-__device__ __forceinline__ void vote(const ViewC& V, const VoxelGeom& vg, const FuseC& F,
-                                     float& W, float& Z, uint32_t& bits) {
-    Vote vt;
-    if (!eval_vote(V, vg, F, vt)) return;
-    W = __fmaf_rn(vt.m, vt.w, W);
-    Z = __fadd_rn(Z, vt.w);
-    bits |= V.bit;
+// Fold views [0, VB.n) of a batch into (W, Z, bits), in view order, for
+// VB.n <= 4 kChunks.  The view loop is unrolled at compile time so that every
+// view constant is an immediate constant-bank operand (a runtime view index
+// would turn each of them into a register-indexed constant load); the raster
+// loads of kViewChunk views are issued before any of them is consumed, and
+// only accepted votes (a few percent) branch into the weight computation.
+template <bool kContracted, int kChunks>
+__device__ __forceinline__ void fold_views(const ViewBatch& VB, const VoxelGeom& vg,
+                                           const FuseC& F, float& W, float& Z, uint32_t& bits) {
+#pragma unroll
+    for (int c = 0; c < kChunks; ++c) {
+        int32_t pix[kViewChunk];
+        float pzh[kViewChunk], pzl[kViewChunk], D[kViewChunk], raw[kViewChunk];
+#pragma unroll
+        for (int q = 0; q < kViewChunk; ++q) {
+            pix[q] = -1;
+            if (c * kViewChunk + q < VB.n)
+                pix[q] = project<kContracted>(VB.v[c * kViewChunk + q], vg, F.z_near, pzh[q], pzl[q]);
+        }
+#pragma unroll
+        for (int q = 0; q < kViewChunk; ++q)
+            if (c * kViewChunk + q < VB.n) load_raster(VB.v[c * kViewChunk + q], pix[q], D[q], raw[q]);
+#pragma unroll
+        for (int q = 0; q < kViewChunk; ++q) {
+            if (c * kViewChunk + q >= VB.n) break;
+            const ViewC& V = VB.v[c * kViewChunk + q];
+            float e;
+            if (gates(V, vg, F, pix[q], pzh[q], pzl[q], D[q], raw[q], e)) {
+                float m, w;
+                weight(V, vg, F, raw[q], e, m, w);
+                W = __fmaf_rn(m, w, W);
+                Z = __fadd_rn(Z, w);
+                bits |= V.bit;
+            }
+        }
+    }
 }
 
 }  // namespace divas

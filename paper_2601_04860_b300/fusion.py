@@ -102,6 +102,23 @@ def view_c(cam, depth: torch.Tensor, mask: torch.Tensor, mask_type: int | None =
     return v
 
 
+class PreparedViews:
+    """Views marshalled once into ``divas_view`` structs (chunks of up to 32), so
+    that repeated launches skip the per-call Python marshalling.  Keeps the
+    rasters alive."""
+
+    def __init__(self, cams, depths, masks, mask_type: int | None = None, logits=False):
+        self.n = len(cams)
+        self._keep = (list(depths), list(masks))
+        self.chunks = []
+        for s0 in range(0, self.n, L.MAX_VIEWS_PER_CALL):
+            s1 = min(self.n, s0 + L.MAX_VIEWS_PER_CALL)
+            arr = (L.DivasView * (s1 - s0))()
+            for k in range(s0, s1):
+                arr[k - s0] = view_c(cams[k], depths[k], masks[k], mask_type, logits)
+            self.chunks.append((arr, s1 - s0))
+
+
 class VoxelFusion:
     """Device-resident fusion state for one occupied set (dense prior or sparse set).
 
@@ -183,16 +200,15 @@ class VoxelFusion:
         self._check(self.lib.divas_fuse_add_view(self._h, ctypes.byref(c), _ptr(depth),
                                                  _ptr(mask), mt, _stream(stream)))
 
-    def add_views(self, cams, depths, masks, mask_type: int | None = None, logits=False,
-                  stream=None):
-        """Fold views in index order, up to 32 per launch."""
-        n = len(cams)
-        for s0 in range(0, n, L.MAX_VIEWS_PER_CALL):
-            s1 = min(n, s0 + L.MAX_VIEWS_PER_CALL)
-            arr = (L.DivasView * (s1 - s0))()
-            for k in range(s0, s1):
-                arr[k - s0] = view_c(cams[k], depths[k], masks[k], mask_type, logits)
-            self._check(self.lib.divas_fuse_add_views(self._h, arr, s1 - s0, _stream(stream)))
+    def add_views(self, cams, depths=None, masks=None, mask_type: int | None = None,
+                  logits=False, stream=None):
+        """Fold views in index order, up to 32 per launch.  ``cams`` may be a
+        ``PreparedViews`` (then depths / masks are not given)."""
+        pv = cams if isinstance(cams, PreparedViews) else PreparedViews(
+            cams, depths, masks, mask_type, logits)
+        s = _stream(stream)
+        for arr, n in pv.chunks:
+            self._check(self.lib.divas_fuse_add_views(self._h, arr, n, s))
 
     def finalize(self, score: bool | torch.Tensor = True, seg_bits: bool | torch.Tensor = False,
                  vmask: bool | torch.Tensor = False, count: bool = False, stream=None) -> dict:
