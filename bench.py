@@ -54,6 +54,32 @@ def _env_int(k, d):
         return d
 
 
+# DRAM traffic per launch of the roofline kernel, from one ncu --set full capture
+# (dram__bytes_read.sum + dram__bytes_write.sum), valid only while the kernel
+# sources are byte-identical to the ones profiled.
+TRAFFIC_CAPTURE = {
+    "source_sha1": "3a586c78b79ca8b35639df589cb26006a319e9b6",
+    "forward-dense-256": {"fuse": 24_658_688},
+}
+
+
+def source_sha1() -> str:
+    """sha1 over 'sha1  path' lines of the CUDA sources (as sha1sum would print)."""
+    import hashlib
+    d = os.path.join(ROOT, "paper_2601_04860_b300", "csrc")
+    lines = []
+    for f in sorted(os.listdir(d)):
+        h = hashlib.sha1(open(os.path.join(d, f), "rb").read()).hexdigest()
+        lines.append(f"{h}  paper_2601_04860_b300/csrc/{f}\n")
+    return hashlib.sha1("".join(lines).encode()).hexdigest()
+
+
+def traffic_for(workload, kernel):
+    if source_sha1() != TRAFFIC_CAPTURE["source_sha1"]:
+        return None  # the kernel changed since the counters were taken
+    return TRAFFIC_CAPTURE.get(workload, {}).get(kernel)
+
+
 def make_workload(name):
     import synth
     if name == "forward-dense-256":
@@ -387,7 +413,8 @@ def run_ours(args, rank, world, local_rank):
                    "launch": "one CUDA graph replay per step (device time from in-graph events)",
                    "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
-                     "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                     "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": traffic_for(args.workload, dom),
                      "peak_kind": peak_kind,
                      "algorithmic_bytes_per_launch": int(algo[dom])},
         "step_roofline": {"algorithmic_bytes": int(step_bytes),

@@ -88,6 +88,7 @@ typedef struct {
     uint32_t flags; /* reserved, 0 */
 } divas_params;
 
+
 typedef struct {
     int32_t kind;       /* 0: dense prior (occ_dense), 1: sparse prior (coords) */
     int32_t g;          /* voxels per side, 1 <= g <= 1024 */
@@ -130,8 +131,8 @@ divas_status divas_fuse_init(divas_ctx** out, const divas_grid* grid, const uint
                              void* stream);
 
 /* Rebuild the active list from a new prior of the same kind and grid, reusing
- * the context's memory (no allocation, no synchronisation); resets W, Z, bits
- * and the view count.  If the new occupied set exceeds the capacity sized at
+ * the context's memory (no allocation, no synchronisation); the view count
+ * returns to 0, so the next fold starts the accumulators from zero.  If the new occupied set exceeds the capacity sized at
  * init, the excess voxels are dropped and DIVAS_E_CAPACITY is reported by the
  * next synchronising call. */
 divas_status divas_fuse_set_occupancy(divas_ctx* ctx, const uint8_t* occ_dense,

@@ -4,7 +4,8 @@
 //   occ_bits[ceil(g^3/32)]     occupancy prior as a bitfield, bit lin of the grid
 //   word_prefix[words]         exclusive prefix of popc(occ_bits): the rank structure
 //                              that maps a dense voxel to its active slot
-//   active[cap]                ascending linear indices of the occupied voxels
+//   active[cap]                occupied voxels in ascending linear index, stored as
+//                              packed coordinates i | j << 10 | k << 20
 //   W[cap], Z[cap], bits[cap]  accumulators of Eq. vmask, structure of arrays
 //   seg_bits[words]            segmentation bitfield B^seg of the last finalize
 //
@@ -20,6 +21,7 @@
 
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstddef>
 #include <cstdio>
@@ -166,13 +168,15 @@ __global__ void __launch_bounds__(kThreads) k_scan_blocks(uint32_t* __restrict__
 }
 
 // rank structure and active list: one word per thread for the ranks; the
-// active list is written warp-cooperatively (word after word, one lane per
-// bit), so that every store instruction writes consecutive slots
+// active list is written warp-cooperatively (non-empty word after non-empty
+// word, one lane per bit), so that every store instruction writes
+// consecutive slots.  Entries are packed coordinates i | j << 10 | k << 20.
 __global__ void __launch_bounds__(kThreads) k_emit(const uint32_t* __restrict__ bits,
                                                    int64_t n_words,
                                                    const uint32_t* __restrict__ block_off,
-                                                   int64_t cap, uint32_t* __restrict__ word_prefix,
-                                                   int32_t* __restrict__ active) {
+                                                   int64_t cap, FastDiv gdiv,
+                                                   uint32_t* __restrict__ word_prefix,
+                                                   uint32_t* __restrict__ active) {
     const int64_t w = blockIdx.x * (int64_t)kThreads + threadIdx.x;
     const uint32_t word = w < n_words ? __ldg(bits + w) : 0u;
     const uint32_t off = block_off[blockIdx.x] + block_exclusive_scan(__popc(word), nullptr);
@@ -180,14 +184,18 @@ __global__ void __launch_bounds__(kThreads) k_emit(const uint32_t* __restrict__ 
     const int lane = threadIdx.x & 31;
     const uint32_t lt = (1u << lane) - 1u;
     const int64_t wbase = w - lane;  // word index of lane 0
-#pragma unroll 4
-    for (int i = 0; i < 32; ++i) {
+    for (uint32_t nz = __ballot_sync(0xffffffffu, word != 0u); nz; nz &= nz - 1u) {
+        const int i = __ffs(nz) - 1;
         const uint32_t wi = __shfl_sync(0xffffffffu, word, i);
         const uint32_t oi = __shfl_sync(0xffffffffu, off, i);
-        if (wi == 0u) continue;  // warp-uniform
         if ((wi >> lane) & 1u) {
             const int64_t slot = (int64_t)oi + __popc(wi & lt);
-            if (slot < cap) active[slot] = (int32_t)((wbase + i) * 32 + lane);
+            if (slot < cap) {
+                const uint32_t lin = (uint32_t)((wbase + i) * 32 + lane);  // < 2^30
+                const uint32_t r = fast_div(lin, gdiv);
+                const uint32_t k = fast_div(r, gdiv);
+                active[slot] = (lin - r * gdiv.d) | ((r - k * gdiv.d) << 10) | (k << 20);
+            }
         }
     }
 }
@@ -196,7 +204,7 @@ __global__ void __launch_bounds__(kThreads) k_emit(const uint32_t* __restrict__ 
 // fusion
 // ---------------------------------------------------------------------------
 template <bool kAccumulate, bool kContracted, int kChunks>
-__global__ void __launch_bounds__(kThreads) k_fuse(const int32_t* __restrict__ active,
+__global__ void __launch_bounds__(kThreads) k_fuse(const uint32_t* __restrict__ active,
                                                    const int32_t* __restrict__ d_n, GridC G,
                                                    FuseC F, const __grid_constant__ ViewBatch VB,
                                                    float* __restrict__ W,
@@ -221,7 +229,7 @@ __global__ void __launch_bounds__(kThreads) k_fuse(const int32_t* __restrict__ a
 
 // launch k_fuse with the chunk count as a compile-time constant
 template <bool kAccumulate, bool kContracted, int kChunks = 1>
-cudaError_t launch_fuse_chunks(int chunks, int blocks, cudaStream_t s, const int32_t* active,
+cudaError_t launch_fuse_chunks(int chunks, int blocks, cudaStream_t s, const uint32_t* active,
                                const int32_t* d_n, const GridC& G, const FuseC& F,
                                const ViewBatch& vb, float* W, float* Z, uint32_t* bits) {
     if constexpr (kChunks < kMaxViews / kViewChunk) {
@@ -241,121 +249,43 @@ __device__ __forceinline__ float score_of(float w, float z, float eps) {
     return z > eps ? __fdiv_rn(w, z) : 0.f;
 }
 
-// dense: one occupancy word (32 voxels) per thread.  Each warp owns 1024
-// consecutive voxels: it zeroes a 4 KB shared tile, each lane drops the scores
-// of its word's occupied voxels into the tile (W / Z loads of up to four
-// voxels in flight at once), and the warp streams the tile out with coalesced
-// 128-bit stores.  The seg word and the view masks are written directly.
-constexpr int kFinWarps = kThreads / 32;
-
-__global__ void __launch_bounds__(kThreads) k_finalize_dense(
-    const uint32_t* __restrict__ occ_bits, const uint32_t* __restrict__ word_prefix,
-    const int32_t* __restrict__ d_n, int64_t n_cells, const float* __restrict__ W,
-    const float* __restrict__ Z, const uint32_t* __restrict__ bits, float eps, float tau_cons,
-    float* __restrict__ score_out, uint32_t* __restrict__ seg_bits, uint32_t* __restrict__ seg_out,
+// normalise + threshold, one thread per active voxel (the dense score grid and
+// the seg bitfields were zeroed by the caller): P = W / Z, seg = P >= tau_cons,
+// the score goes to its dense or active-list position, seg bits are OR-ed in
+// once per group of lanes that share a 32-bit word
+__global__ void __launch_bounds__(kThreads) k_finalize(
+    const uint32_t* __restrict__ active, const int32_t* __restrict__ d_n, int32_t g,
+    int32_t dense, const float* __restrict__ W, const float* __restrict__ Z,
+    const uint32_t* __restrict__ bits, float eps, float tau_cons, float* __restrict__ score_out,
+    uint32_t* __restrict__ seg_bits, uint32_t* __restrict__ seg_out,
     uint32_t* __restrict__ vmask_out, unsigned long long* __restrict__ d_nseg) {
-    __shared__ float4 tile[kFinWarps][256];
-    const uint32_t n = (uint32_t)*d_n;
-    const int64_t n_words = (n_cells + 31) / 32;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t w = blockIdx.x * (int64_t)kThreads + threadIdx.x;
-    const bool live = w < n_words;
-    uint32_t word = 0, pre = 0;
-    if (live) {
-        word = __ldg(occ_bits + w);
-        pre = __ldg(word_prefix + w);
-    }
-    float4* t4 = tile[warp];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) t4[lane + 32 * i] = make_float4(0.f, 0.f, 0.f, 0.f);
-    __syncwarp();
-    float* t1 = reinterpret_cast<float*>(t4) + lane * 32;
-    uint32_t segw = 0;
-    uint32_t m = word;
-    uint32_t r = pre;
-    while (m) {  // up to four occupied voxels per round, their loads issued together
-        int b[4];
-        uint32_t sl[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            b[q] = m ? __ffs(m) - 1 : -1;
-            sl[q] = (b[q] >= 0 && r < n) ? r : 0xffffffffu;
-            if (b[q] >= 0) {
-                m &= m - 1;
-                ++r;
-            }
-        }
-        float wv[4], zv[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const uint32_t s0 = sl[q] != 0xffffffffu ? sl[q] : 0u;
-            wv[q] = __ldcs(W + s0);
-            zv[q] = __ldcs(Z + s0);
-        }
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            if (sl[q] == 0xffffffffu) continue;
-            const float p = zv[q] > eps ? __fdiv_rn(wv[q], zv[q]) : 0.f;
-            const bool sg = p >= tau_cons;
-            t1[b[q]] = p;
-            segw |= (sg ? 1u : 0u) << b[q];
-            if (vmask_out) vmask_out[sl[q]] = sg ? bits[sl[q]] : 0u;
-        }
-    }
-    __syncwarp();
-    // stream the warp's 1024 scores out: 8 coalesced float4 stores per lane
-    const int64_t v_warp = (w - lane) * 32;  // first voxel of the warp
-    if (score_out) {
-        const bool vec = ((reinterpret_cast<uintptr_t>(score_out) & 15) == 0) &&
-                         v_warp + 1024 <= n_cells;
-        if (vec) {
-            float4* dst = reinterpret_cast<float4*>(score_out + v_warp);
-#pragma unroll
-            for (int i = 0; i < 8; ++i) __stcs(dst + lane + 32 * i, t4[lane + 32 * i]);
-        } else {
-            const float* src = reinterpret_cast<const float*>(t4);
-            for (int i = lane; i < 1024; i += 32)
-                if (v_warp + i < n_cells) score_out[v_warp + i] = src[i];
-        }
-    }
-    uint32_t cnt = 0;
-    if (live) {
-        seg_bits[w] = segw;
-        if (seg_out) seg_out[w] = segw;
-        cnt = __popc(segw);
-    }
-    if (d_nseg) {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
-        if (lane == 0 && cnt) atomicAdd(d_nseg, (unsigned long long)cnt);
-    }
-}
-
-// sparse: one thread per active voxel; seg bitfields were zeroed before
-__global__ void __launch_bounds__(kThreads) k_finalize_sparse(
-    const int32_t* __restrict__ active, const int32_t* __restrict__ d_n,
-    const float* __restrict__ W, const float* __restrict__ Z, const uint32_t* __restrict__ bits,
-    float eps, float tau_cons, float* __restrict__ score_out, uint32_t* __restrict__ seg_bits,
-    uint32_t* __restrict__ seg_out, uint32_t* __restrict__ vmask_out,
-    unsigned long long* __restrict__ d_nseg) {
     const int32_t n = *d_n;
-    for (int32_t a0 = blockIdx.x * blockDim.x; a0 < n; a0 += gridDim.x * blockDim.x) {
-        const int32_t a = a0 + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const int32_t gw = (int32_t)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int32_t nw = (int32_t)((gridDim.x * blockDim.x) >> 5);
+    for (int32_t base = gw * 32; base < n; base += nw * 32) {
+        const int32_t a = base + lane;
+        const bool live = a < n;
         bool seg = false;
-        if (a < n) {
-            const float s = score_of(W[a], Z[a], eps);
-            seg = s >= tau_cons;
-            if (score_out) __stcs(score_out + a, s);
+        int64_t lin = 0;
+        if (live) {
+            const float w = __ldcs(W + a), z = __ldcs(Z + a);
+            const float p = z > eps ? __fdiv_rn(w, z) : 0.f;
+            seg = p >= tau_cons;
+            lin = packed_lin(__ldg(active + a), g);
+            if (score_out) score_out[dense ? lin : (int64_t)a] = p;
             if (vmask_out) vmask_out[a] = seg ? bits[a] : 0u;
-            if (seg) {
-                const int32_t lin = __ldg(active + a);
-                atomicOr(seg_bits + (lin >> 5), 1u << (lin & 31));
-                if (seg_out) atomicOr(seg_out + (lin >> 5), 1u << (lin & 31));
-            }
+        }
+        const uint32_t word = live ? (uint32_t)(lin >> 5) : 0xffffffffu;
+        const uint32_t grp = __match_any_sync(0xffffffffu, word);
+        const uint32_t orv = __reduce_or_sync(grp, seg ? 1u << (lin & 31) : 0u);
+        if (live && lane == __ffs(grp) - 1 && orv) {
+            atomicOr(seg_bits + word, orv);
+            if (seg_out) atomicOr(seg_out + word, orv);
         }
         if (d_nseg) {
             const uint32_t cnt = __popc(__ballot_sync(0xffffffffu, seg));
-            if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(d_nseg, (unsigned long long)cnt);
+            if (lane == 0 && cnt) atomicAdd(d_nseg, (unsigned long long)cnt);
         }
     }
 }
@@ -458,18 +388,18 @@ __global__ void __launch_bounds__(kThreads) k_label(const float* __restrict__ xy
 // ---------------------------------------------------------------------------
 template <bool kContracted, int kChunks>
 __global__ void __launch_bounds__(kThreads) k_backward(
-    const int32_t* __restrict__ active, const int32_t* __restrict__ d_n, GridC G, FuseC F,
+    const uint32_t* __restrict__ active, const int32_t* __restrict__ d_n, GridC G, FuseC F,
     const __grid_constant__ ViewBatch VB, const __grid_constant__ BackPtrs BP,
     const float* __restrict__ W, const float* __restrict__ Z,
     const float* __restrict__ grad_score, int32_t dense) {
     const int32_t n = *d_n;
     for (int32_t a = blockIdx.x * blockDim.x + threadIdx.x; a < n; a += gridDim.x * blockDim.x) {
-        const int32_t lin = __ldg(active + a);
-        const float gP = __ldg(grad_score + (dense ? (int64_t)lin : (int64_t)a));
+        const uint32_t pk = __ldg(active + a);
+        const float gP = __ldg(grad_score + (dense ? packed_lin(pk, G.g) : (int64_t)a));
         const float z = Z[a];
         if (gP == 0.f || !(z > F.eps)) continue;
         const float P = __fdiv_rn(W[a], z);
-        const VoxelGeom vg = voxel_geom<kContracted>(lin, G, F.gamma);
+        const VoxelGeom vg = voxel_geom<kContracted>(pk, G, F.gamma);
         if (!vg.ok) continue;
         const float gz = __fdiv_rn(gP, z);
         const float k2 = __fmul_rn(__fmul_rn(2.f, F.alpha1), __fmul_rn(vg.invDelta, vg.invDelta));
@@ -493,7 +423,7 @@ __global__ void __launch_bounds__(kThreads) k_backward(
 }
 
 template <bool kContracted, int kChunks = 1>
-cudaError_t launch_backward_chunks(int chunks, int blocks, cudaStream_t s, const int32_t* active,
+cudaError_t launch_backward_chunks(int chunks, int blocks, cudaStream_t s, const uint32_t* active,
                                    const int32_t* d_n, const GridC& G, const FuseC& F,
                                    const ViewBatch& vb, const BackPtrs& bp, const float* W,
                                    const float* Z, const float* grad_score, int32_t dense) {
@@ -511,7 +441,7 @@ cudaError_t launch_backward_chunks(int chunks, int blocks, cudaStream_t s, const
 // misc
 // ---------------------------------------------------------------------------
 template <bool kContracted>
-__global__ void k_debug_project(const int32_t* __restrict__ active, const int32_t* __restrict__ d_n,
+__global__ void k_debug_project(const uint32_t* __restrict__ active, const int32_t* __restrict__ d_n,
                                 GridC G, FuseC F, ViewC V, int32_t* __restrict__ pix_out) {
     const int32_t n = *d_n;
     for (int32_t a = blockIdx.x * blockDim.x + threadIdx.x; a < n; a += gridDim.x * blockDim.x) {
@@ -521,14 +451,15 @@ __global__ void k_debug_project(const int32_t* __restrict__ active, const int32_
     }
 }
 
-__global__ void k_active_coords(const int32_t* __restrict__ active, const int32_t* __restrict__ d_n,
+__global__ void k_active_coords(const uint32_t* __restrict__ active, const int32_t* __restrict__ d_n,
                                 int32_t g, int32_t* __restrict__ out) {
     const int32_t n = *d_n;
     for (int32_t a = blockIdx.x * blockDim.x + threadIdx.x; a < n; a += gridDim.x * blockDim.x) {
-        const int32_t lin = active[a];
-        out[3 * a] = lin % g;
-        out[3 * a + 1] = (lin / g) % g;
-        out[3 * a + 2] = lin / (g * g);
+        int32_t i, j, k;
+        unpack(active[a], i, j, k);
+        out[3 * a] = i;
+        out[3 * a + 1] = j;
+        out[3 * a + 2] = k;
     }
 }
 
@@ -552,7 +483,8 @@ struct divas_ctx {
     uint32_t* word_prefix = nullptr;
     uint32_t* block_sums = nullptr;
     uint32_t* seg_bits = nullptr;
-    int32_t* active = nullptr;
+    uint32_t* active = nullptr;
+    FastDiv gdiv;  // division by g
     float* W = nullptr;
     float* Z = nullptr;
     uint32_t* bits = nullptr;
@@ -702,7 +634,7 @@ divas_status build_active(divas_ctx* c, const uint8_t* occ, const int32_t* coord
 
 divas_status emit_active(divas_ctx* c, cudaStream_t s) {
     k_emit<<<c->n_cblocks, kThreads, 0, s>>>(c->occ_bits, c->n_words, c->block_sums, c->cap,
-                                             c->word_prefix, c->active);
+                                             c->gdiv, c->word_prefix, c->active);
     DIVAS_LAUNCHED(c, "k_emit");
     return DIVAS_OK;
 }
@@ -794,6 +726,15 @@ divas_status divas_fuse_init(divas_ctx** out, const divas_grid* grid, const uint
     c->F.eps = params->eps;
     c->F.tau_cons = params->tau_cons;
     c->F.pad = 0;
+    {  // multiply-shift divider for g (l = ceil(log2 g), m = 2^32 (2^l - g) / g + 1)
+        const uint32_t d = (uint32_t)grid->g;
+        int32_t l = 0;
+        while ((1ull << l) < d) ++l;
+        c->gdiv.d = d;
+        c->gdiv.l = l;
+        c->gdiv.m = (uint32_t)(((1ull << 32) * ((1ull << l) - d)) / d + 1);
+        c->gdiv.pad = 0;
+    }
     c->n_cells = (int64_t)grid->g * grid->g * grid->g;
     c->n_words = (c->n_cells + 31) / 32;
     c->n_cblocks = (int32_t)((c->n_words + kWordsPerBlock - 1) / kWordsPerBlock);
@@ -872,7 +813,7 @@ divas_status divas_fuse_set_occupancy(divas_ctx* c, const uint8_t* occ_dense, co
     return DIVAS_OK;
 }
 
-static divas_status launch_fuse(divas_ctx* c, const ViewBatch& vb, cudaStream_t s) {
+static divas_status launch_fuse(divas_ctx* c, ViewBatch& vb, cudaStream_t s) {
     const int blocks = grid_for(c->cap, c->sm_count);
     const bool acc = c->n_views > 0;
     const int chunks = (vb.n + kViewChunk - 1) / kViewChunk;
@@ -933,22 +874,15 @@ divas_status divas_fuse_finalize(divas_ctx* c, float* score_out, uint32_t* seg_b
     cudaStream_t s = S(stream);
     unsigned long long* nseg = n_seg_host ? c->d_nseg : nullptr;
     if (nseg) DIVAS_CUDA(c, cudaMemsetAsync(c->d_nseg, 0, 8, s));
-    if (c->n_views == 0) {
-        // no view folded in yet: W = Z = 0 (after init/reset), scores are all 0
-    }
-    if (c->grid.kind == 0) {
-        k_finalize_dense<<<(unsigned)((c->n_words + kThreads - 1) / kThreads), kThreads, 0, s>>>(
-            c->occ_bits, c->word_prefix, c->d_n, c->n_cells, c->W, c->Z, c->bits, c->F.eps,
-            c->F.tau_cons, score_out, c->seg_bits, seg_bits_out, vmask_out, nseg);
-        DIVAS_LAUNCHED(c, "k_finalize_dense");
-    } else {
-        DIVAS_CUDA(c, cudaMemsetAsync(c->seg_bits, 0, c->n_words * 4, s));
-        if (seg_bits_out) DIVAS_CUDA(c, cudaMemsetAsync(seg_bits_out, 0, c->n_words * 4, s));
-        k_finalize_sparse<<<grid_for(c->cap, c->sm_count, 16), kThreads, 0, s>>>(
-            c->active, c->d_n, c->W, c->Z, c->bits, c->F.eps, c->F.tau_cons, score_out,
-            c->seg_bits, seg_bits_out, vmask_out, nseg);
-        DIVAS_LAUNCHED(c, "k_finalize_sparse");
-    }
+    // zero-fill, then scatter the active voxels' scores and seg bits
+    if (score_out && c->grid.kind == 0)
+        DIVAS_CUDA(c, cudaMemsetAsync(score_out, 0, c->n_cells * 4, s));
+    DIVAS_CUDA(c, cudaMemsetAsync(c->seg_bits, 0, c->n_words * 4, s));
+    if (seg_bits_out) DIVAS_CUDA(c, cudaMemsetAsync(seg_bits_out, 0, c->n_words * 4, s));
+    k_finalize<<<grid_for(c->cap, c->sm_count, 16), kThreads, 0, s>>>(
+        c->active, c->d_n, c->grid.g, c->grid.kind == 0 ? 1 : 0, c->W, c->Z, c->bits, c->F.eps,
+        c->F.tau_cons, score_out, c->seg_bits, seg_bits_out, vmask_out, nseg);
+    DIVAS_LAUNCHED(c, "k_finalize");
     if (n_seg_host) {
         unsigned long long v = 0;
         DIVAS_CUDA(c, cudaMemcpyAsync(&v, c->d_nseg, 8, cudaMemcpyDeviceToHost, s));

@@ -127,14 +127,39 @@ struct VoxelGeom {
     bool ok;  // false: contracted centre with |c| >= 2 (no world position)
 };
 
+// n / d for 32-bit n by a divisor fixed per context: multiply-high and shift
+// (Granlund and Montgomery, "Division by invariant integers using
+// multiplication", PLDI 1994); exact for every 32-bit n.
+struct FastDiv {
+    uint32_t m, d;
+    int32_t l;
+    int32_t pad;
+};
+
+__device__ __forceinline__ uint32_t fast_div(uint32_t n, const FastDiv& f) {
+    if (f.l == 0) return n;  // d = 1
+    const uint32_t t = __umulhi(n, f.m);
+    return (t + ((n - t) >> 1)) >> (f.l - 1);
+}
+
+// active-list entries are packed voxel coordinates i | j << 10 | k << 20
+__device__ __forceinline__ void unpack(uint32_t pk, int32_t& i, int32_t& j, int32_t& k) {
+    i = (int32_t)(pk & 1023u);
+    j = (int32_t)((pk >> 10) & 1023u);
+    k = (int32_t)(pk >> 20);
+}
+
+__device__ __forceinline__ int64_t packed_lin(uint32_t pk, int32_t g) {
+    int32_t i, j, k;
+    unpack(pk, i, j, k);
+    return ((int64_t)k * g + j) * g + i;
+}
+
 template <bool kContracted>
-__device__ __forceinline__ VoxelGeom voxel_geom(int32_t lin, const GridC& G, float gamma) {
+__device__ __forceinline__ VoxelGeom voxel_geom(uint32_t pk, const GridC& G, float gamma) {
     VoxelGeom vg;
-    const int32_t g = G.g;
-    const int32_t i = lin % g;
-    const int32_t r = lin / g;
-    const int32_t j = r % g;
-    const int32_t k = r / g;
+    int32_t i, j, k;
+    unpack(pk, i, j, k);
     vg.ok = true;
     if (!kContracted) {
         vg.xh[0] = (float)(2 * i + 1);

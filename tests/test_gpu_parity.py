@@ -217,3 +217,4 @@ def test_config3_full_size_sampled():
     s = H.compare(wl, gpu, P0, sample=sample)
     _report("config3 full (sampled)", s)
     assert s["voted"] > 1000
+
