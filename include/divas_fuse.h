@@ -212,6 +212,31 @@ divas_status divas_fuse_backward(divas_ctx* ctx, const divas_view* views, int32_
 divas_status divas_debug_project(divas_ctx* ctx, const divas_camera* cam, int32_t* pix_out,
                                  void* stream);
 
+/*
+ * Allocation-free one-shot fusion of a dense prior: occupancy gate and active
+ * list, all views, normalisation and consensus, in one call that allocates
+ * nothing.  The paper has no counterpart: this exists for callers that must
+ * not allocate device memory while they run, such as a per-frame plug-in
+ * inside a host application that owns all GPU memory, where a cudaMalloc would
+ * synchronise the device and stall the frame.
+ *   grid: kind 0, not contracted, at most 64^3 cells (larger -> DIVAS_E_INVALID).
+ *   occ_dense, views: as for divas_fuse_init / divas_fuse_add_views (1..32 views).
+ *   score_out: device float32 g^3 (dense scores, 0 for unoccupied); nullable.
+ *   seg_bits_out: device uint32 ceil(g^3/32) words; nullable.
+ * Results equal divas_fuse_init + divas_fuse_add_views + divas_fuse_finalize.
+ * Scratch lives in one device array of the library (about 4.3 MB, reserved on
+ * every GPU that loads the library until exit) shared by all calls: calls that
+ * overlap on the GPU race.  The first call on a device looks up that array's
+ * address (once per device, with the device current); make it before any
+ * stream capture.  Errors: DIVAS_E_INVALID / DIVAS_E_CUDA, message from
+ * divas_noalloc_last_error.
+ */
+divas_status divas_fuse_dense_noalloc(const divas_grid* grid, const uint8_t* occ_dense,
+                                      const divas_view* views, int32_t n_views,
+                                      const divas_params* params, float* score_out,
+                                      uint32_t* seg_bits_out, void* stream);
+const char* divas_noalloc_last_error(void);
+
 void divas_fuse_destroy(divas_ctx* ctx);
 
 /* Message of the last failing call on ctx (valid until the next call on ctx);

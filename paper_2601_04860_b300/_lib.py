@@ -72,6 +72,10 @@ _SIGS = {
     "divas_fuse_backward": (ctypes.c_int, [_P, ctypes.POINTER(DivasView), ctypes.c_int32, _P,
                                            ctypes.POINTER(_P), ctypes.POINTER(_P), _P]),
     "divas_debug_project": (ctypes.c_int, [_P, ctypes.POINTER(DivasCamera), _P, _P]),
+    "divas_fuse_dense_noalloc": (ctypes.c_int, [ctypes.POINTER(DivasGrid), _P,
+                                                ctypes.POINTER(DivasView), ctypes.c_int32,
+                                                ctypes.POINTER(DivasParams), _P, _P, _P]),
+    "divas_noalloc_last_error": (ctypes.c_char_p, []),
     "divas_fuse_destroy": (None, [_P]),
     "divas_last_error": (ctypes.c_char_p, [_P]),
 }

@@ -26,6 +26,7 @@
 #include <cstddef>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 
@@ -1019,3 +1020,188 @@ const char* divas_last_error(const divas_ctx* c) {
 }
 
 }  // extern "C"
+
+// ===========================================================================
+// Allocation-free one-shot fusion (no counterpart in the paper)
+//
+// Some callers must not allocate device memory while they run: a plug-in
+// invoked once per frame inside a host application that owns all GPU memory
+// (where cudaMalloc would synchronise the device and stall the frame), or code
+// running under a strict no-allocation policy between frames.  For them,
+// divas_fuse_dense_noalloc runs the whole dense pipeline -- occupancy gate and
+// active list, fusion of the views, normalisation and consensus -- with its
+// scratch in one file-scope device array instead of context memory.
+//
+// The array holds grids of up to 64^3 cells and is reserved on every GPU that
+// loads this library until the process exits (about 4.3 MB).  All calls share
+// it and it keeps the previous call's contents, so every part that must start
+// at zero is cleared by the call itself; calls that overlap on the GPU (two
+// streams, or two host threads) race on it.  The first call on a device looks
+// up the array's device address with cudaGetSymbolAddress, once per device and
+// with that device current; make that first call before any stream capture.
+// ===========================================================================
+namespace {
+
+constexpr int64_t kNoAllocMaxCells = 1 << 18;  // 64^3
+constexpr int64_t kNoAllocWords = kNoAllocMaxCells / 32;
+constexpr int64_t kNoAllocBlocks = (kNoAllocWords + kWordsPerBlock - 1) / kWordsPerBlock;
+
+constexpr int64_t na_align(int64_t x) { return (x + 255) / 256 * 256; }
+constexpr int64_t kNaOccBits = 0;
+constexpr int64_t kNaPrefix = kNaOccBits + na_align(kNoAllocWords * 4);
+constexpr int64_t kNaSeg = kNaPrefix + na_align(kNoAllocWords * 4);
+constexpr int64_t kNaBlocks = kNaSeg + na_align(kNoAllocWords * 4);
+constexpr int64_t kNaActive = kNaBlocks + na_align((kNoAllocBlocks + 1) * 4);
+constexpr int64_t kNaW = kNaActive + na_align(kNoAllocMaxCells * 4);
+constexpr int64_t kNaZ = kNaW + na_align(kNoAllocMaxCells * 4);
+constexpr int64_t kNaBits = kNaZ + na_align(kNoAllocMaxCells * 4);
+constexpr int64_t kNaN = kNaBits + na_align(kNoAllocMaxCells * 4);
+constexpr int64_t kNaStatus = kNaN + 256;
+constexpr int64_t kNaTotal = kNaStatus + 256;
+constexpr int64_t kNoAllocBytes = kNaTotal + 256;
+
+}  // namespace
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+namespace {
+
+std::mutex g_noalloc_mu;
+void* g_noalloc_dev_ptr[256] = {nullptr};
+std::string g_noalloc_error;
+
+divas_status noalloc_fail(divas_status st, const std::string& msg) {
+    g_noalloc_error = msg;
+    return st;
+}
+
+}  // namespace
+
+extern "C" divas_status divas_fuse_dense_noalloc(const divas_grid* grid, const uint8_t* occ_dense,
+                                                 const divas_view* views, int32_t n_views,
+                                                 const divas_params* params, float* score_out,
+                                                 uint32_t* seg_bits_out, void* stream) {
+    if (!grid || !params || !occ_dense || !views)
+        return noalloc_fail(DIVAS_E_INVALID, "NULL argument");
+    if (grid->kind != 0 || grid->contracted)
+        return noalloc_fail(DIVAS_E_INVALID, "only plain dense grids (kind 0, not contracted)");
+    if (grid->g < 1 || (int64_t)grid->g * grid->g * grid->g > kNoAllocMaxCells)
+        return noalloc_fail(DIVAS_E_INVALID,
+                            "grid too large for the allocation-free path (at most 64^3 cells)");
+    if (!finite_pos(grid->h)) return noalloc_fail(DIVAS_E_INVALID, "h must be finite and > 0");
+    if (n_views < 1 || n_views > kMaxViews)
+        return noalloc_fail(DIVAS_E_INVALID, "n_views must be in 1..32");
+    if (!(params->gamma > 0.f && params->gamma <= FLT_MAX) || !(params->alpha1 >= 0.f) ||
+        !(params->eps >= 0.f))
+        return noalloc_fail(DIVAS_E_INVALID, "params out of range");
+    cudaStream_t s = S(stream);
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess || dev < 0 || dev >= 256)
+        return noalloc_fail(DIVAS_E_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+    unsigned char* base = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_noalloc_mu);
+        if (!g_noalloc_dev_ptr[dev]) {
+            void* p = nullptr;
+            e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+            if (e != cudaSuccess || !p)
+                return noalloc_fail(DIVAS_E_CUDA,
+                                    std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+            g_noalloc_dev_ptr[dev] = p;
+        }
+        base = static_cast<unsigned char*>(g_noalloc_dev_ptr[dev]);
+    }
+    uint32_t* occ_bits = reinterpret_cast<uint32_t*>(base + kNaOccBits);
+    uint32_t* word_prefix = reinterpret_cast<uint32_t*>(base + kNaPrefix);
+    uint32_t* seg_bits = reinterpret_cast<uint32_t*>(base + kNaSeg);
+    uint32_t* block_sums = reinterpret_cast<uint32_t*>(base + kNaBlocks);
+    uint32_t* active = reinterpret_cast<uint32_t*>(base + kNaActive);
+    float* W = reinterpret_cast<float*>(base + kNaW);
+    float* Z = reinterpret_cast<float*>(base + kNaZ);
+    uint32_t* bits = reinterpret_cast<uint32_t*>(base + kNaBits);
+    int32_t* d_n = reinterpret_cast<int32_t*>(base + kNaN);
+    int32_t* d_status = reinterpret_cast<int32_t*>(base + kNaStatus);
+    int64_t* d_total = reinterpret_cast<int64_t*>(base + kNaTotal);
+
+    GridC G;
+    for (int q = 0; q < 3; ++q) G.origin[q] = grid->origin[q];
+    G.h = grid->h;
+    G.g = grid->g;
+    G.contracted = 0;
+    {
+        int ex = 0;
+        const double fr = frexp((double)grid->h, &ex);
+        G.inv_h = fr == 0.5 ? (float)ldexp(1.0, 1 - ex) : 0.f;
+        G.pad = 0;
+    }
+    FuseC F;
+    F.gamma = params->gamma;
+    F.alpha1 = params->alpha1;
+    F.tau_m = params->tau_mask;
+    F.logit_tau = logit_threshold(params->tau_mask);
+    F.z_near = params->z_near;
+    F.eps = params->eps;
+    F.tau_cons = params->tau_cons;
+    F.pad = 0;
+    FastDiv gdiv;
+    {
+        const uint32_t d = (uint32_t)grid->g;
+        int32_t l = 0;
+        while ((1ull << l) < d) ++l;
+        gdiv.d = d;
+        gdiv.l = l;
+        gdiv.m = (uint32_t)(((1ull << 32) * ((1ull << l) - d)) / d + 1);
+        gdiv.pad = 0;
+    }
+    ViewBatch vb;
+    memset(&vb, 0, sizeof(vb));
+    vb.n = n_views;
+    for (int32_t k = 0; k < n_views; ++k) {
+        const divas_camera& cam = views[k].cam;
+        if (cam.W <= 0 || cam.H <= 0 || cam.W > 65535 || cam.H > 65535 ||
+            (int64_t)cam.W * cam.H > INT32_MAX || !views[k].depth || !views[k].mask ||
+            views[k].mask_type < 0 || views[k].mask_type > 2)
+            return noalloc_fail(DIVAS_E_INVALID, "bad view");
+        vb.v[k] = make_view(cam, G, views[k].depth, views[k].mask, views[k].mask_type, k);
+    }
+    const int64_t n_cells = (int64_t)grid->g * grid->g * grid->g;
+    const int64_t n_words = (n_cells + 31) / 32;
+    const int32_t n_blocks = (int32_t)((n_words + kWordsPerBlock - 1) / kWordsPerBlock);
+    const int64_t cap = kNoAllocMaxCells;
+    int sm_count = 148;
+    cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, dev);
+#define NA_CHECK(what)                                                                \
+    do {                                                                              \
+        cudaError_t e_ = cudaGetLastError();                                          \
+        if (e_ != cudaSuccess)                                                        \
+            return noalloc_fail(DIVAS_E_CUDA, std::string(what) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+    // state that must start at zero on every call
+    e = cudaMemsetAsync(d_status, 0, 4, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(seg_bits, 0, n_words * 4, s);
+    if (e == cudaSuccess && score_out) e = cudaMemsetAsync(score_out, 0, n_cells * 4, s);
+    if (e == cudaSuccess && seg_bits_out) e = cudaMemsetAsync(seg_bits_out, 0, n_words * 4, s);
+    if (e != cudaSuccess)
+        return noalloc_fail(DIVAS_E_CUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
+    k_occ_bits<<<n_blocks, kThreads, 0, s>>>(occ_dense, n_cells, n_words, occ_bits, block_sums);
+    NA_CHECK("k_occ_bits");
+    k_scan_blocks<<<1, kThreads, 0, s>>>(block_sums, n_blocks, cap, d_total, d_n, d_status);
+    NA_CHECK("k_scan_blocks");
+    k_emit<<<n_blocks, kThreads, 0, s>>>(occ_bits, n_words, block_sums, cap, gdiv, word_prefix,
+                                         active);
+    NA_CHECK("k_emit");
+    const int blocks = grid_for(n_cells, sm_count);
+    e = launch_fuse_chunks<false, false>((n_views + kViewChunk - 1) / kViewChunk, blocks, s,
+                                         active, d_n, G, F, vb, W, Z, bits);
+    if (e != cudaSuccess)
+        return noalloc_fail(DIVAS_E_CUDA, std::string("k_fuse: ") + cudaGetErrorString(e));
+    k_finalize<<<grid_for(n_cells, sm_count, 16), kThreads, 0, s>>>(
+        active, d_n, grid->g, 1, W, Z, bits, F.eps, F.tau_cons, score_out, seg_bits, seg_bits_out,
+        nullptr, nullptr);
+    NA_CHECK("k_finalize");
+#undef NA_CHECK
+    return DIVAS_OK;
+}
+
+extern "C" const char* divas_noalloc_last_error(void) { return g_noalloc_error.c_str(); }
