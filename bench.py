@@ -440,6 +440,48 @@ def run_ours(args, rank, world, local_rank):
     return res, wl
 
 
+def measure_adjoint(dev, steps: int):
+    """Config 4: forward + hand-written backward through the autograd Function on
+    the 256^3 forward-facing scene with FP32 logits and depth as leaves."""
+    import torch
+
+    import synth
+    from paper_2601_04860_b300 import MASK_LOGIT_F32, FusionParams, VoxelFusion, fuse
+    wl = synth.config4()
+    occ = torch.from_numpy(wl.occ).to(dev)
+    logits = [torch.from_numpy(m).to(dev).requires_grad_(True) for m in wl.mask]
+    depths = [torch.from_numpy(d).to(dev).requires_grad_(True) for d in wl.depth]
+    fu = VoxelFusion(wl.grid, occ=occ, params=FusionParams())
+    lin = torch.from_numpy(wl.active_linear()).to(dev)
+    y = (torch.rand(len(lin), device=dev) < 0.1).float()  # any fixed target works for timing
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    fwd, bwd = [], []
+    for k in range(3 + steps):
+        for t in logits + depths:
+            t.grad = None
+        flush.zero_()
+        a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        a.record()
+        P = fuse(fu, wl.cams, logits, depths, MASK_LOGIT_F32)
+        Pc = P[lin].clamp(1e-6, 1 - 1e-6)
+        loss = -(y * torch.log(Pc) + (1 - y) * torch.log(1 - Pc)).sum()
+        b.record()
+        loss.backward()
+        c.record()
+        torch.cuda.synchronize()
+        if k >= 3:
+            fwd.append(a.elapsed_time(b))
+            bwd.append(b.elapsed_time(c))
+    n = fu.n_cells
+    fu.close()
+    S = wl.n_views
+    return {"workload": "differentiable-256 (config-2 scene, FP32 logits + depth as leaves)",
+            "fwd_ms": float(np.mean(fwd)), "bwd_ms": float(np.mean(bwd)),
+            "fwd_bwd_updates_per_s": n * S / ((np.mean(fwd) + np.mean(bwd)) * 1e-3),
+            "what": "eager autograd: fuse() + BCE on active voxels, then loss.backward() "
+                    "(adjoint kernel + gradient raster zero-fill); L2 flushed per step"}
+
+
 def run(args):
     rank = _env_int("RANK", 0)
     world = _env_int("WORLD_SIZE", 1)
@@ -454,6 +496,9 @@ def run(args):
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     res, wl = run_ours(args, rank, world, local_rank)
+    if not args.quick and not args.no_adjoint:
+        import torch
+        res["adjoint"] = measure_adjoint(torch.device("cuda", local_rank), max(5, args.steps // 2))
     if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.quick:
         full_s, det = oracle_rate(wl, args.cpu_seconds)
         N = res["config"]["voxels_nominal"]
@@ -507,6 +552,7 @@ def main(argv=None):
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="forward-dense-256")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the forward+backward leg")
     ap.add_argument("--quick", action="store_true",
                     help="timed graph steps only: no eager, per-update, e2e or CPU legs")
     args = ap.parse_args(argv)

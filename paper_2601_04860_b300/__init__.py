@@ -14,3 +14,4 @@ from ._lib import (  # noqa: F401
     load,
 )
 from .fusion import FusionParams, PreparedViews, VoxelFusion, seg_bits_to_bool  # noqa: F401
+from .autograd import DivasFuseFunction, fuse  # noqa: F401,E402

@@ -291,6 +291,10 @@ class VoxelFusion:
         arr = (L.DivasView * n)()
         for k in range(n):
             arr[k] = view_c(cams[k], depths[k], masks[k], mask_type, logits)
+        for name, grads in (("grad_mask", grad_mask), ("grad_depth", grad_depth)):
+            for k, t in enumerate(grads or []):
+                if t is not None and (t.dtype != torch.float32 or t.shape != depths[k].shape):
+                    raise ValueError(f"{name}[{k}] must be a float32 H x W raster")
         gm = (ctypes.c_void_p * n)(*[(_ptr(t).value if t is not None else None)
                                      for t in (grad_mask or [None] * n)])
         gd = (ctypes.c_void_p * n)(*[(_ptr(t).value if t is not None else None)
