@@ -213,6 +213,47 @@ divas_status divas_debug_project(divas_ctx* ctx, const divas_camera* cam, int32_
                                  void* stream);
 
 /*
+ * Batched sessions: fold the views of many contexts (uneven grid sizes, kinds
+ * and view counts) in ONE persistent launch, then finalize and label all of
+ * them in one launch each.  Work items are (context, tile of its active
+ * list), taken dynamically by the CTAs; each context's result is bitwise
+ * identical to what its own add_views + finalize + label_points would give.
+ *
+ * Usage per batch: divas_batch_queue for each context (at most once per
+ * batch, 1..32 views each), divas_batch_fuse, divas_batch_finalize (which
+ * clears the queue).  A dry run (dry_run != 0) computes into batch scratch
+ * and leaves the contexts untouched: it exists to time schedules (autotuning);
+ * its first use allocates that scratch.  The batch stages descriptors in
+ * pinned host memory (double-buffered) and copies them with one
+ * cudaMemcpyAsync per call, so a fused-and-finalized batch can be captured in
+ * a CUDA graph.  The contexts of one batch must not be used by other calls
+ * between queue and finalize.
+ */
+typedef struct divas_batch divas_batch;
+
+typedef struct {
+    int32_t threads;           /* 64, 128 or 256 per CTA */
+    int32_t voxels_per_thread; /* 1, 2 or 4 voxels folded together per thread */
+    int32_t ctas_per_sm;       /* persistent grid = SMs x ctas_per_sm (1..32) */
+    int32_t tile;              /* voxels per work item, a multiple of threads x voxels_per_thread */
+} divas_schedule;
+
+divas_status divas_batch_create(divas_batch** out, int32_t max_sessions, int32_t max_views);
+divas_status divas_batch_queue(divas_batch* b, divas_ctx* ctx, const divas_view* views,
+                               int32_t n_views);
+divas_status divas_batch_fuse(divas_batch* b, const divas_schedule* sched, int32_t dry_run,
+                              void* stream);
+/* score_out[k] / xyz[k] / n_pts[k] / labels_out[k] for the k-th queued context
+ * (arrays and entries nullable): as divas_fuse_finalize's score_out and
+ * divas_label_points. */
+divas_status divas_batch_finalize(divas_batch* b, float* const* score_out, const float* const* xyz,
+                                  const int64_t* n_pts, uint8_t* const* labels_out, void* stream);
+divas_status divas_batch_clear(divas_batch* b);
+int32_t divas_batch_size(const divas_batch* b);
+const char* divas_batch_last_error(const divas_batch* b);
+void divas_batch_destroy(divas_batch* b);
+
+/*
  * Allocation-free one-shot fusion of a dense prior: occupancy gate and active
  * list, all views, normalisation and consensus, in one call that allocates
  * nothing.  The paper has no counterpart: this exists for callers that must

@@ -80,7 +80,10 @@ _SIGS = {
     "divas_last_error": (ctypes.c_char_p, [_P]),
 }
 
-EXPORTED = tuple(_SIGS)
+# batched sessions (bound in batch.py)
+EXPORTED = tuple(_SIGS) + ("divas_batch_create", "divas_batch_queue", "divas_batch_fuse",
+                           "divas_batch_finalize", "divas_batch_clear", "divas_batch_size",
+                           "divas_batch_last_error", "divas_batch_destroy")
 
 
 def load(path: str = LIB_PATH):

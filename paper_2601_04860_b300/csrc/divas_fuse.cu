@@ -29,6 +29,7 @@
 #include <mutex>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "fuse_math.cuh"
 
@@ -300,88 +301,94 @@ __device__ __forceinline__ float floor_df(float hi, float lo) {
     return (f == hi && lo < 0.f) ? f - 1.f : f;
 }
 
+// label of one point (x, y, z) against a seg bitfield
+__device__ __forceinline__ uint8_t label_one(const float* __restrict__ xyz, int64_t a,
+                                             const GridC& G,
+                                             const uint32_t* __restrict__ seg_bits) {
+    float xh[3] = {__ldg(xyz + 3 * a), __ldg(xyz + 3 * a + 1), __ldg(xyz + 3 * a + 2)};
+    float xl[3] = {0.f, 0.f, 0.f};
+    uint8_t lab = 0;
+    if (!(isnan(xh[0]) || isnan(xh[1]) || isnan(xh[2]))) {
+        if (G.contracted) {
+            // r^2 = |x|^2 as hi + lo
+            float s = 0.f, e = 0.f;
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                float p, pe, t;
+                two_prod(xh[q], xh[q], p, pe);
+                two_sum(s, p, s, t);
+                e = __fadd_rn(e, __fadd_rn(t, pe));
+            }
+            float n2h, n2l;
+            two_sum(s, e, n2h, n2l);
+            if ((n2h > 1.f) || (n2h == 1.f && n2l > 0.f)) {
+                if (n2h > 1e30f) {  // |x| beyond 1e15: contract(x) = 2 x / |x| in FP32
+                    const float inv = __frsqrt_rn(n2h);
+                    // not reached by finite scenes; keeps the arithmetic finite
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) { xh[q] = 2.f * xh[q] * inv; xl[q] = 0.f; }
+                } else {
+                    const float rh = __fsqrt_rn(n2h);
+                    const float rl =
+                        __fdiv_rn(__fadd_rn(__fmaf_rn(-rh, rh, n2h), n2l), __fmul_rn(2.f, rh));
+                    // ir = 1 / r
+                    const float ih = __frcp_rn(rh);
+                    const float il = __fmul_rn(
+                        ih, __fsub_rn(__fmaf_rn(-ih, rh, 1.f), __fmul_rn(ih, rl)));
+                    // tt = 2 - ir
+                    float th, tl;
+                    two_sum(2.f, -ih, th, tl);
+                    tl = __fsub_rn(tl, il);
+                    two_sum(th, tl, th, tl);
+                    // sc = tt * ir
+                    float sh, sl;
+                    two_prod(th, ih, sh, sl);
+                    sl = __fadd_rn(sl, __fadd_rn(__fmul_rn(th, il), __fmul_rn(tl, ih)));
+                    two_sum(sh, sl, sh, sl);
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) {
+                        float qh, ql;
+                        two_prod(xh[q], sh, qh, ql);
+                        ql = __fadd_rn(ql, __fmul_rn(xh[q], sl));
+                        two_sum(qh, ql, xh[q], xl[q]);
+                    }
+                }
+            }
+        }
+        bool inside = true;
+        int32_t idx[3];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            // s = (x - origin) / h as hi + lo
+            float dh, dl;
+            two_sum(xh[q], -G.origin[q], dh, dl);
+            dl = __fadd_rn(dl, xl[q]);
+            float sh, sl;
+            if (G.inv_h != 0.f) {  // power-of-two edge: scaling is exact
+                sh = __fmul_rn(dh, G.inv_h);
+                sl = __fmul_rn(dl, G.inv_h);
+            } else {
+                sh = __fdiv_rn(dh, G.h);
+                sl = __fdiv_rn(__fadd_rn(__fmaf_rn(-sh, G.h, dh), dl), G.h);
+            }
+            const float f = floor_df(sh, sl);
+            if (!(f >= 0.f && f < (float)G.g)) inside = false;
+            idx[q] = inside ? (int32_t)f : 0;
+        }
+        if (inside) {
+            const int64_t lin = ((int64_t)idx[2] * G.g + idx[1]) * G.g + idx[0];
+            lab = (uint8_t)((__ldg(seg_bits + (lin >> 5)) >> (lin & 31)) & 1u);
+        }
+    }
+    return lab;
+}
+
 __global__ void __launch_bounds__(kThreads) k_label(const float* __restrict__ xyz, int64_t n,
                                                     GridC G, const uint32_t* __restrict__ seg_bits,
                                                     uint8_t* __restrict__ labels) {
     for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < n;
-         a += (int64_t)gridDim.x * blockDim.x) {
-        float xh[3] = {__ldg(xyz + 3 * a), __ldg(xyz + 3 * a + 1), __ldg(xyz + 3 * a + 2)};
-        float xl[3] = {0.f, 0.f, 0.f};
-        uint8_t lab = 0;
-        if (!(isnan(xh[0]) || isnan(xh[1]) || isnan(xh[2]))) {
-            if (G.contracted) {
-                // r^2 = |x|^2 as hi + lo
-                float s = 0.f, e = 0.f;
-#pragma unroll
-                for (int q = 0; q < 3; ++q) {
-                    float p, pe, t;
-                    two_prod(xh[q], xh[q], p, pe);
-                    two_sum(s, p, s, t);
-                    e = __fadd_rn(e, __fadd_rn(t, pe));
-                }
-                float n2h, n2l;
-                two_sum(s, e, n2h, n2l);
-                if ((n2h > 1.f) || (n2h == 1.f && n2l > 0.f)) {
-                    if (n2h > 1e30f) {  // |x| beyond 1e15: contract(x) = 2 x / |x| in FP32
-                        const float inv = __frsqrt_rn(n2h);
-                        // not reached by finite scenes; keeps the arithmetic finite
-#pragma unroll
-                        for (int q = 0; q < 3; ++q) { xh[q] = 2.f * xh[q] * inv; xl[q] = 0.f; }
-                    } else {
-                        const float rh = __fsqrt_rn(n2h);
-                        const float rl =
-                            __fdiv_rn(__fadd_rn(__fmaf_rn(-rh, rh, n2h), n2l), __fmul_rn(2.f, rh));
-                        // ir = 1 / r
-                        const float ih = __frcp_rn(rh);
-                        const float il = __fmul_rn(
-                            ih, __fsub_rn(__fmaf_rn(-ih, rh, 1.f), __fmul_rn(ih, rl)));
-                        // tt = 2 - ir
-                        float th, tl;
-                        two_sum(2.f, -ih, th, tl);
-                        tl = __fsub_rn(tl, il);
-                        two_sum(th, tl, th, tl);
-                        // sc = tt * ir
-                        float sh, sl;
-                        two_prod(th, ih, sh, sl);
-                        sl = __fadd_rn(sl, __fadd_rn(__fmul_rn(th, il), __fmul_rn(tl, ih)));
-                        two_sum(sh, sl, sh, sl);
-#pragma unroll
-                        for (int q = 0; q < 3; ++q) {
-                            float qh, ql;
-                            two_prod(xh[q], sh, qh, ql);
-                            ql = __fadd_rn(ql, __fmul_rn(xh[q], sl));
-                            two_sum(qh, ql, xh[q], xl[q]);
-                        }
-                    }
-                }
-            }
-            bool inside = true;
-            int32_t idx[3];
-#pragma unroll
-            for (int q = 0; q < 3; ++q) {
-                // s = (x - origin) / h as hi + lo
-                float dh, dl;
-                two_sum(xh[q], -G.origin[q], dh, dl);
-                dl = __fadd_rn(dl, xl[q]);
-                float sh, sl;
-                if (G.inv_h != 0.f) {  // power-of-two edge: scaling is exact
-                    sh = __fmul_rn(dh, G.inv_h);
-                    sl = __fmul_rn(dl, G.inv_h);
-                } else {
-                    sh = __fdiv_rn(dh, G.h);
-                    sl = __fdiv_rn(__fadd_rn(__fmaf_rn(-sh, G.h, dh), dl), G.h);
-                }
-                const float f = floor_df(sh, sl);
-                if (!(f >= 0.f && f < (float)G.g)) inside = false;
-                idx[q] = inside ? (int32_t)f : 0;
-            }
-            if (inside) {
-                const int64_t lin = ((int64_t)idx[2] * G.g + idx[1]) * G.g + idx[0];
-                lab = (uint8_t)((__ldg(seg_bits + (lin >> 5)) >> (lin & 31)) & 1u);
-            }
-        }
-        labels[a] = lab;
-    }
+         a += (int64_t)gridDim.x * blockDim.x)
+        labels[a] = label_one(xyz, a, G, seg_bits);
 }
 
 // ---------------------------------------------------------------------------
@@ -1017,6 +1024,458 @@ void divas_fuse_destroy(divas_ctx* c) {
 
 const char* divas_last_error(const divas_ctx* c) {
     return c ? c->err.c_str() : g_init_error.c_str();
+}
+
+}  // extern "C"
+
+// ===========================================================================
+// Batched sessions: many contexts of uneven sizes and view counts in one
+// persistent launch.  Work items are (session, tile of its active list);
+// CTAs take items from a global counter (dynamic scheduling), stage the
+// session's views in shared memory and fold them into kVPT voxels per thread.
+// The per-vote arithmetic and the view order are those of the single-context
+// kernels, so a session's result is bitwise the same alone or in a batch.
+// ===========================================================================
+namespace {
+
+struct SessionDesc {
+    const uint32_t* active;
+    const int32_t* d_n;
+    const float* W_in;
+    const float* Z_in;
+    const uint32_t* bits_in;
+    float* W_out;
+    float* Z_out;
+    uint32_t* bits_out;
+    GridC G;
+    FuseC F;
+    int32_t view_off, n_views, accumulate, dense;
+    // finalize / labels (filled at finalize time)
+    float* score_out;
+    uint32_t* seg_bits;
+    const float* xyz;
+    uint8_t* labels;
+    int64_t n_pts;
+};
+
+// largest s with prefix[s] <= it (prefix[0] = 0, prefix[n] = total > it)
+__device__ __forceinline__ int32_t find_session(const uint32_t* prefix, int32_t n, uint32_t it) {
+    int32_t lo = 0, hi = n;
+    while (hi - lo > 1) {
+        const int32_t mid = (lo + hi) >> 1;
+        if (__ldg(prefix + mid) <= it) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+// one CTA-wide work item: returns false when the work is exhausted
+__device__ __forceinline__ bool next_item(int32_t* counter, const uint32_t* prefix, int32_t n,
+                                          uint32_t& it, int32_t& sess) {
+    __shared__ uint32_t s_it;
+    __shared__ int32_t s_sess;
+    __syncthreads();  // the previous item is done with shared state
+    if (threadIdx.x == 0) {
+        const uint32_t i = (uint32_t)atomicAdd(counter, 1);
+        s_it = i;
+        s_sess = i < __ldg(prefix + n) ? find_session(prefix, n, i) : -1;
+    }
+    __syncthreads();
+    it = s_it;
+    sess = s_sess;
+    return sess >= 0;
+}
+
+template <bool kContracted, int kVPT>
+__device__ __forceinline__ void batch_fuse_item(const SessionDesc& D, const ViewC* sv,
+                                                int32_t a0, int32_t a1) {
+    for (int32_t base = a0; base < a1; base += (int32_t)blockDim.x * kVPT) {
+        VoxelGeom vg[kVPT];
+        bool live[kVPT];
+        float W[kVPT], Z[kVPT];
+        uint32_t bits[kVPT];
+#pragma unroll
+        for (int j = 0; j < kVPT; ++j) {
+            const int32_t a = base + j * (int32_t)blockDim.x + (int32_t)threadIdx.x;
+            live[j] = a < a1;
+            const int32_t as = live[j] ? a : a0;
+            vg[j] = voxel_geom<kContracted>(__ldg(D.active + as), D.G, D.F.gamma);
+            W[j] = Z[j] = 0.f;
+            bits[j] = 0u;
+            if (D.accumulate && live[j]) {
+                W[j] = D.W_in[a];
+                Z[j] = D.Z_in[a];
+                bits[j] = D.bits_in[a];
+            }
+        }
+        fold_views_multi<kContracted, kVPT>(sv, D.n_views, vg, live, D.F, W, Z, bits);
+#pragma unroll
+        for (int j = 0; j < kVPT; ++j) {
+            const int32_t a = base + j * (int32_t)blockDim.x + (int32_t)threadIdx.x;
+            if (live[j]) {
+                D.W_out[a] = W[j];
+                D.Z_out[a] = Z[j];
+                D.bits_out[a] = bits[j];
+            }
+        }
+    }
+}
+
+template <int kVPT>
+__global__ void __launch_bounds__(kThreads) k_batch_fuse(const SessionDesc* __restrict__ S, int32_t n_sessions,
+                             const uint32_t* __restrict__ prefix, const ViewC* __restrict__ views,
+                             int32_t tile, int32_t* __restrict__ counter) {
+    __shared__ ViewC sv[kMaxViews];
+    uint32_t it;
+    int32_t s;
+    while (next_item(counter, prefix, n_sessions, it, s)) {
+        const SessionDesc& D = S[s];
+        const int32_t nv = D.n_views;
+        {
+            const uint32_t* src = reinterpret_cast<const uint32_t*>(views + D.view_off);
+            uint32_t* dst = reinterpret_cast<uint32_t*>(sv);
+            const int32_t words = nv * (int32_t)(sizeof(ViewC) / 4);
+            for (int32_t i = threadIdx.x; i < words; i += blockDim.x) dst[i] = __ldg(src + i);
+        }
+        __syncthreads();
+        const int32_t n = *D.d_n;
+        const int32_t a0 = (int32_t)(it - __ldg(prefix + s)) * tile;
+        const int32_t a1 = min(a0 + tile, n);
+        if (a0 < a1) {
+            if (D.G.contracted)
+                batch_fuse_item<true, kVPT>(D, sv, a0, a1);
+            else
+                batch_fuse_item<false, kVPT>(D, sv, a0, a1);
+        }
+    }
+}
+
+// normalise + threshold for all sessions (score grids and seg bits zeroed before)
+__global__ void __launch_bounds__(kThreads) k_batch_finalize(const SessionDesc* __restrict__ S,
+                                                             int32_t n_sessions,
+                                                             const uint32_t* __restrict__ prefix,
+                                                             int32_t tile,
+                                                             int32_t* __restrict__ counter) {
+    uint32_t it;
+    int32_t s;
+    const int lane = threadIdx.x & 31;
+    while (next_item(counter, prefix, n_sessions, it, s)) {
+        const SessionDesc& D = S[s];
+        const int32_t n = *D.d_n;
+        const int32_t a0 = (int32_t)(it - __ldg(prefix + s)) * tile;
+        const int32_t a1 = min(a0 + tile, n);
+        for (int32_t base = a0 + (int32_t)(threadIdx.x & ~31u); base < a1;
+             base += (int32_t)blockDim.x) {
+            const int32_t a = base + lane;
+            const bool live = a < a1;
+            bool seg = false;
+            int64_t lin = 0;
+            if (live) {
+                const float w = D.W_out[a], z = D.Z_out[a];
+                const float p = z > D.F.eps ? __fdiv_rn(w, z) : 0.f;
+                seg = p >= D.F.tau_cons;
+                lin = packed_lin(__ldg(D.active + a), D.G.g);
+                if (D.score_out) D.score_out[D.dense ? lin : (int64_t)a] = p;
+            }
+            const uint32_t word = live ? (uint32_t)(lin >> 5) : 0xffffffffu;
+            const uint32_t grp = __match_any_sync(0xffffffffu, word);
+            const uint32_t orv = __reduce_or_sync(grp, seg ? 1u << (lin & 31) : 0u);
+            if (live && lane == __ffs(grp) - 1 && orv) atomicOr(D.seg_bits + word, orv);
+        }
+    }
+}
+
+// Pass 1 labels for all sessions (items over points)
+__global__ void __launch_bounds__(kThreads) k_batch_label(const SessionDesc* __restrict__ S,
+                                                          int32_t n_sessions,
+                                                          const uint32_t* __restrict__ prefix,
+                                                          int32_t tile,
+                                                          int32_t* __restrict__ counter) {
+    uint32_t it;
+    int32_t s;
+    while (next_item(counter, prefix, n_sessions, it, s)) {
+        const SessionDesc& D = S[s];
+        const int64_t p0 = (int64_t)(it - __ldg(prefix + s)) * tile;
+        const int64_t p1 = min(p0 + tile, D.n_pts);
+        for (int64_t a = p0 + threadIdx.x; a < p1; a += blockDim.x)
+            D.labels[a] = label_one(D.xyz, a, D.G, D.seg_bits);
+    }
+}
+
+}  // namespace
+
+struct divas_batch {
+    int32_t max_sessions = 0, max_views = 0;
+    int32_t sm_count = 148;
+    // double-buffered pinned staging: [sessions | views | 3 prefix arrays]
+    unsigned char* h_stage[2] = {nullptr, nullptr};
+    cudaEvent_t stage_done[2] = {nullptr, nullptr};
+    int32_t cur = 0;
+    size_t stage_bytes = 0, off_views = 0, off_prefix = 0;
+    unsigned char* d_stage = nullptr;
+    int32_t* d_counter = nullptr;
+    // queue
+    std::vector<divas_ctx*> ctxs;
+    std::vector<int32_t> nq;
+    int32_t views_used = 0;
+    bool fused = false;
+    // dry-run outputs
+    float* dW = nullptr;
+    float* dZ = nullptr;
+    uint32_t* dbits = nullptr;
+    int64_t dcap = 0;
+    std::string err;
+};
+
+namespace {
+
+divas_status bfail(divas_batch* b, divas_status st, const std::string& m) {
+    if (b) b->err = m;
+    return st;
+}
+
+SessionDesc* stage_sessions(divas_batch* b) {
+    return reinterpret_cast<SessionDesc*>(b->h_stage[b->cur]);
+}
+ViewC* stage_views(divas_batch* b) {
+    return reinterpret_cast<ViewC*>(b->h_stage[b->cur] + b->off_views);
+}
+uint32_t* stage_prefix(divas_batch* b, int which) {
+    return reinterpret_cast<uint32_t*>(b->h_stage[b->cur] + b->off_prefix) +
+           (size_t)which * (b->max_sessions + 1);
+}
+
+}  // namespace
+
+extern "C" {
+
+divas_status divas_batch_create(divas_batch** out, int32_t max_sessions, int32_t max_views) {
+    if (!out || max_sessions < 1 || max_views < 1 || max_sessions > (1 << 20) ||
+        max_views > (1 << 20))
+        return fail(nullptr, DIVAS_E_INVALID, "bad batch limits");
+    *out = nullptr;
+    divas_batch* b = new (std::nothrow) divas_batch();
+    if (!b) return fail(nullptr, DIVAS_E_OOM, "host allocation failed");
+    b->max_sessions = max_sessions;
+    b->max_views = max_views;
+    auto align = [](size_t x) { return (x + 255) / 256 * 256; };
+    b->off_views = align(sizeof(SessionDesc) * max_sessions);
+    b->off_prefix = b->off_views + align(sizeof(ViewC) * max_views);
+    b->stage_bytes = b->off_prefix + align(sizeof(uint32_t) * 3 * (max_sessions + 1));
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->sm_count, cudaDevAttrMultiProcessorCount, dev);
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+        e = cudaHostAlloc(reinterpret_cast<void**>(&b->h_stage[k]), b->stage_bytes, cudaHostAllocDefault);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->stage_done[k], cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_stage, b->stage_bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_counter, 16);
+    if (e != cudaSuccess) {
+        divas_batch_destroy(b);
+        return cuda_fail(nullptr, e, "divas_batch_create");
+    }
+    b->ctxs.reserve(max_sessions);
+    b->nq.reserve(max_sessions);
+    *out = b;
+    return DIVAS_OK;
+}
+
+divas_status divas_batch_queue(divas_batch* b, divas_ctx* c, const divas_view* views,
+                               int32_t n_views) {
+    if (!b || !c) return bfail(b, DIVAS_E_INVALID, "NULL batch or context");
+    if (b->fused) return bfail(b, DIVAS_E_STATE, "finalize or clear the fused batch first");
+    if (!views || n_views < 1 || n_views > kMaxViews)
+        return bfail(b, DIVAS_E_INVALID, "n_views must be in 1..32");
+    if ((int32_t)b->ctxs.size() >= b->max_sessions) return bfail(b, DIVAS_E_CAPACITY, "batch full");
+    if (b->views_used + n_views > b->max_views) return bfail(b, DIVAS_E_CAPACITY, "too many views");
+    for (divas_ctx* q : b->ctxs)
+        if (q == c) return bfail(b, DIVAS_E_INVALID, "a context may appear once per batch");
+    if (b->ctxs.empty()) {  // first entry: the staging buffer must be free again
+        cudaError_t e = cudaEventSynchronize(b->stage_done[b->cur]);
+        if (e != cudaSuccess) return bfail(b, DIVAS_E_CUDA, cudaGetErrorString(e));
+    }
+    ViewC* hv = stage_views(b) + b->views_used;
+    for (int32_t k = 0; k < n_views; ++k) {
+        divas_status st = check_camera(c, &views[k].cam);
+        if (st != DIVAS_OK) return bfail(b, st, c->err);
+        if (!views[k].depth || !views[k].mask || views[k].mask_type < 0 || views[k].mask_type > 2)
+            return bfail(b, DIVAS_E_INVALID, "bad view");
+        hv[k] = make_view(views[k].cam, c->G, views[k].depth, views[k].mask, views[k].mask_type,
+                          c->n_views + k);
+    }
+    SessionDesc& D = stage_sessions(b)[b->ctxs.size()];
+    memset(&D, 0, sizeof(D));
+    D.active = c->active;
+    D.d_n = c->d_n;
+    D.W_in = D.W_out = c->W;
+    D.Z_in = D.Z_out = c->Z;
+    D.bits_in = D.bits_out = c->bits;
+    D.G = c->G;
+    D.F = c->F;
+    D.view_off = b->views_used;
+    D.n_views = n_views;
+    D.accumulate = c->n_views > 0 ? 1 : 0;
+    D.dense = c->grid.kind == 0 ? 1 : 0;
+    D.seg_bits = c->seg_bits;
+    b->ctxs.push_back(c);
+    b->nq.push_back(n_views);
+    b->views_used += n_views;
+    return DIVAS_OK;
+}
+
+divas_status divas_batch_fuse(divas_batch* b, const divas_schedule* sched, int32_t dry_run,
+                              void* stream) {
+    if (!b || !sched) return bfail(b, DIVAS_E_INVALID, "NULL argument");
+    if (b->fused) return bfail(b, DIVAS_E_STATE, "batch already fused");
+    const int32_t ns = (int32_t)b->ctxs.size();
+    if (ns == 0) return DIVAS_OK;
+    const int vpt = sched->voxels_per_thread;
+    if (!(sched->threads == 64 || sched->threads == 128 || sched->threads == 256) ||
+        !(vpt == 1 || vpt == 2 || vpt == 4) || sched->ctas_per_sm < 1 || sched->ctas_per_sm > 32 ||
+        sched->tile < sched->threads * vpt || sched->tile % (sched->threads * vpt) != 0)
+        return bfail(b, DIVAS_E_INVALID, "bad schedule");
+    cudaStream_t s = S(stream);
+    SessionDesc* hs = stage_sessions(b);
+    // tile prefix over capacities (the device count bounds the real work)
+    uint32_t* pf = stage_prefix(b, 0);
+    pf[0] = 0;
+    int64_t total_cap = 0;
+    for (int32_t k = 0; k < ns; ++k) {
+        const int64_t cap = b->ctxs[k]->cap;
+        pf[k + 1] = pf[k] + (uint32_t)((cap + sched->tile - 1) / sched->tile);
+        total_cap += cap;
+    }
+    if (dry_run) {  // outputs go to scratch: the contexts are left untouched
+        if (total_cap > b->dcap) {
+            if (b->dW) cudaFree(b->dW);
+            if (b->dZ) cudaFree(b->dZ);
+            if (b->dbits) cudaFree(b->dbits);
+            b->dW = b->dZ = nullptr;
+            b->dbits = nullptr;
+            b->dcap = 0;
+            cudaError_t e = cudaMalloc(&b->dW, total_cap * 4);
+            if (e == cudaSuccess) e = cudaMalloc(&b->dZ, total_cap * 4);
+            if (e == cudaSuccess) e = cudaMalloc(&b->dbits, total_cap * 4);
+            if (e != cudaSuccess) return bfail(b, DIVAS_E_OOM, cudaGetErrorString(e));
+            b->dcap = total_cap;
+        }
+        int64_t off = 0;
+        for (int32_t k = 0; k < ns; ++k) {
+            hs[k].W_out = b->dW + off;
+            hs[k].Z_out = b->dZ + off;
+            hs[k].bits_out = b->dbits + off;
+            off += b->ctxs[k]->cap;
+        }
+    } else {
+        for (int32_t k = 0; k < ns; ++k) {
+            hs[k].W_out = b->ctxs[k]->W;
+            hs[k].Z_out = b->ctxs[k]->Z;
+            hs[k].bits_out = b->ctxs[k]->bits;
+        }
+    }
+    cudaError_t e = cudaMemcpyAsync(b->d_stage, b->h_stage[b->cur], b->stage_bytes,
+                                    cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaEventRecord(b->stage_done[b->cur], s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_counter, 0, 4, s);
+    if (e != cudaSuccess) return bfail(b, DIVAS_E_CUDA, cudaGetErrorString(e));
+    const SessionDesc* dS = reinterpret_cast<const SessionDesc*>(b->d_stage);
+    const ViewC* dV = reinterpret_cast<const ViewC*>(b->d_stage + b->off_views);
+    const uint32_t* dP = reinterpret_cast<const uint32_t*>(b->d_stage + b->off_prefix);
+    const int grid = std::max(1, std::min<int>(b->sm_count * sched->ctas_per_sm, (int)pf[ns]));
+    switch (vpt) {
+        case 1: k_batch_fuse<1><<<grid, sched->threads, 0, s>>>(dS, ns, dP, dV, sched->tile, b->d_counter); break;
+        case 2: k_batch_fuse<2><<<grid, sched->threads, 0, s>>>(dS, ns, dP, dV, sched->tile, b->d_counter); break;
+        default: k_batch_fuse<4><<<grid, sched->threads, 0, s>>>(dS, ns, dP, dV, sched->tile, b->d_counter); break;
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return bfail(b, DIVAS_E_CUDA, std::string("k_batch_fuse: ") + cudaGetErrorString(e));
+    if (!dry_run) {
+        for (int32_t k = 0; k < ns; ++k) b->ctxs[k]->n_views += b->nq[k];
+        b->fused = true;
+    }
+    return DIVAS_OK;
+}
+
+divas_status divas_batch_finalize(divas_batch* b, float* const* score_out, const float* const* xyz,
+                                  const int64_t* n_pts, uint8_t* const* labels_out, void* stream) {
+    if (!b) return bfail(b, DIVAS_E_INVALID, "NULL batch");
+    const int32_t ns = (int32_t)b->ctxs.size();
+    if (ns == 0) return DIVAS_OK;
+    if (!b->fused) return bfail(b, DIVAS_E_STATE, "fuse the batch first (dry runs do not count)");
+    cudaStream_t s = S(stream);
+    SessionDesc* hs = stage_sessions(b);
+    uint32_t* pf = stage_prefix(b, 1);
+    uint32_t* pl = stage_prefix(b, 2);
+    const int32_t tile = 4096;
+    pf[0] = pl[0] = 0;
+    bool any_pts = false;
+    for (int32_t k = 0; k < ns; ++k) {
+        divas_ctx* c = b->ctxs[k];
+        hs[k].score_out = score_out ? score_out[k] : nullptr;
+        hs[k].xyz = xyz ? xyz[k] : nullptr;
+        hs[k].labels = labels_out ? labels_out[k] : nullptr;
+        hs[k].n_pts = (xyz && n_pts && labels_out && xyz[k] && labels_out[k]) ? n_pts[k] : 0;
+        if (hs[k].n_pts < 0) return bfail(b, DIVAS_E_INVALID, "negative point count");
+        any_pts |= hs[k].n_pts > 0;
+        pf[k + 1] = pf[k] + (uint32_t)((c->cap + tile - 1) / tile);
+        pl[k + 1] = pl[k] + (uint32_t)((hs[k].n_pts + tile - 1) / tile);
+        cudaError_t e = cudaSuccess;
+        if (hs[k].score_out && c->grid.kind == 0)
+            e = cudaMemsetAsync(hs[k].score_out, 0, c->n_cells * 4, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(c->seg_bits, 0, c->n_words * 4, s);
+        if (e != cudaSuccess) return bfail(b, DIVAS_E_CUDA, cudaGetErrorString(e));
+    }
+    // the staging buffer is the one of the fuse call; the copy orders after it on the stream
+    cudaError_t e = cudaMemcpyAsync(b->d_stage, b->h_stage[b->cur], b->stage_bytes,
+                                    cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaEventRecord(b->stage_done[b->cur], s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_counter, 0, 16, s);
+    if (e != cudaSuccess) return bfail(b, DIVAS_E_CUDA, cudaGetErrorString(e));
+    const SessionDesc* dS = reinterpret_cast<const SessionDesc*>(b->d_stage);
+    const uint32_t* dPf = reinterpret_cast<const uint32_t*>(b->d_stage + b->off_prefix) +
+                          (size_t)(b->max_sessions + 1);
+    const uint32_t* dPl = dPf + (size_t)(b->max_sessions + 1);
+    int grid = std::max(1, std::min<int>(b->sm_count * 8, (int)pf[ns]));
+    k_batch_finalize<<<grid, kThreads, 0, s>>>(dS, ns, dPf, tile, b->d_counter + 1);
+    e = cudaGetLastError();
+    if (e == cudaSuccess && any_pts) {
+        grid = std::max(1, std::min<int>(b->sm_count * 8, (int)pl[ns]));
+        k_batch_label<<<grid, kThreads, 0, s>>>(dS, ns, dPl, tile, b->d_counter + 2);
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) return bfail(b, DIVAS_E_CUDA, cudaGetErrorString(e));
+    return divas_batch_clear(b);
+}
+
+divas_status divas_batch_clear(divas_batch* b) {
+    if (!b) return DIVAS_E_INVALID;
+    b->ctxs.clear();
+    b->nq.clear();
+    b->views_used = 0;
+    b->fused = false;
+    b->cur ^= 1;  // the next batch stages into the other buffer
+    return DIVAS_OK;
+}
+
+int32_t divas_batch_size(const divas_batch* b) { return b ? (int32_t)b->ctxs.size() : -1; }
+
+const char* divas_batch_last_error(const divas_batch* b) { return b ? b->err.c_str() : ""; }
+
+void divas_batch_destroy(divas_batch* b) {
+    if (!b) return;
+    for (int k = 0; k < 2; ++k) {
+        if (b->stage_done[k]) {
+            cudaEventSynchronize(b->stage_done[k]);
+            cudaEventDestroy(b->stage_done[k]);
+        }
+        if (b->h_stage[k]) cudaFreeHost(b->h_stage[k]);
+    }
+    if (b->d_stage) cudaFree(b->d_stage);
+    if (b->d_counter) cudaFree(b->d_counter);
+    if (b->dW) cudaFree(b->dW);
+    if (b->dZ) cudaFree(b->dZ);
+    if (b->dbits) cudaFree(b->dbits);
+    delete b;
 }
 
 }  // extern "C"

@@ -359,4 +359,50 @@ __device__ __forceinline__ void fold_views(const ViewBatch& VB, const VoxelGeom&
     }
 }
 
+
+// Fold the views sv[0, n) (a runtime count, e.g. a session's views staged in
+// shared memory) into kVPT independent voxels at once: the same per-view
+// arithmetic and the same view order as fold_views, so the results are
+// bitwise identical.  kVPT voxels x (4 / kVPT) views of projections and raster
+// loads are in flight together.
+template <bool kContracted, int kVPT>
+__device__ __forceinline__ void fold_views_multi(const ViewC* sv, int32_t n, const VoxelGeom* vg,
+                                                 const bool* live, const FuseC& F, float* W,
+                                                 float* Z, uint32_t* bits) {
+    constexpr int kC = kViewChunk / kVPT > 0 ? kViewChunk / kVPT : 1;
+    for (int32_t v0 = 0; v0 < n; v0 += kC) {
+        int32_t pix[kVPT][kC];
+        float pzh[kVPT][kC], pzl[kVPT][kC], D[kVPT][kC], raw[kVPT][kC];
+#pragma unroll
+        for (int j = 0; j < kVPT; ++j)
+#pragma unroll
+            for (int q = 0; q < kC; ++q) {
+                pix[j][q] = -1;
+                pzh[j][q] = pzl[j][q] = 0.f;
+                if (v0 + q < n && live[j] && vg[j].ok)
+                    pix[j][q] = project<kContracted>(sv[v0 + q], vg[j], F.z_near, pzh[j][q], pzl[j][q]);
+            }
+#pragma unroll
+        for (int j = 0; j < kVPT; ++j)
+#pragma unroll
+            for (int q = 0; q < kC; ++q)
+                if (v0 + q < n) load_raster(sv[v0 + q], pix[j][q], D[j][q], raw[j][q]);
+#pragma unroll
+        for (int j = 0; j < kVPT; ++j)
+#pragma unroll
+            for (int q = 0; q < kC; ++q) {
+                if (v0 + q >= n) break;
+                const ViewC& V = sv[v0 + q];
+                float e;
+                if (gates(V, vg[j], F, pix[j][q], pzh[j][q], pzl[j][q], D[j][q], raw[j][q], e)) {
+                    float m, w;
+                    weight(V, vg[j], F, raw[j][q], e, m, w);
+                    W[j] = __fmaf_rn(m, w, W[j]);
+                    Z[j] = __fadd_rn(Z[j], w);
+                    bits[j] |= V.bit;
+                }
+            }
+    }
+}
+
 }  // namespace divas
