@@ -482,6 +482,117 @@ def measure_adjoint(dev, steps: int):
                     "(adjoint kernel + gradient raster zero-fill); L2 flushed per step"}
 
 
+def measure_sessions(dev, scale: float, n_sessions: int, rates, budget_frac: float = 1.0):
+    """Config 5: many uneven sessions.  (a) Batched: every session's views in ONE
+    persistent fuse launch + one finalize + one label launch, autotuned and
+    replayed from a CUDA graph, vs the plain per-session launches.  (b) Served:
+    Poisson requests (one new view each) through the continuous-batching server
+    vs the paper-style re-fusion and the incremental one-request-at-a-time
+    baselines."""
+    import torch
+
+    import synth
+    from paper_2601_04860_b300 import Autotuner, Batch, Schedule
+    from paper_2601_04860_b300.serve import (Server, Session, latency_summary,
+                                             poisson_requests, serve_plain, session_data_from)
+    t_gen = time.perf_counter()
+    recipes = synth.session_mix(n_sessions=n_sessions, scale=scale)
+    data = [session_data_from(synth.session_workload(r), i) for i, r in enumerate(recipes)]
+    t_gen = time.perf_counter() - t_gen
+    nominal = sum((int(d.grid.g) ** 3 if d.occ is not None else len(d.coords)) * d.n_views
+                  for d in data)
+    out = {"sessions": n_sessions, "scale": scale, "generation_s": t_gen,
+           "dense": sum(d.occ is not None for d in data),
+           "views_total": sum(d.n_views for d in data),
+           "voxel_views_nominal": int(nominal)}
+    # (a) batched vs plain, all views of every session
+    sess = [Session(d, dev) for d in data]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def plain_pass():
+        for s in sess:
+            s.fusion.reset()
+            s.fusion.add_views(s.data.cams, s.depth, s.mask, mask_type=s.data.mask_type)
+            s.fusion.finalize(score=s.score)
+            s.fusion.label_points(s.points, out=s.labels)
+    for _ in range(2):
+        plain_pass()
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(5):
+        flush.zero_()
+        a, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        plain_pass()
+        b_.record()
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b_))
+    out["plain_ms"] = float(np.mean(ms))
+    batch = Batch(max_sessions=n_sessions, max_views=sum(d.n_views for d in data))
+    for s in sess:
+        s.fusion.reset()
+        batch.queue(s.fusion, s.data.cams, s.depth, s.mask, mask_type=s.data.mask_type)
+    tuner = Autotuner(reps=2)
+    cands = [Schedule(t, v, c, tile) for t in (128, 256) for v in (1, 2) for c in (4, 8)
+             for tile in (t * v * 16, t * v * 64)]
+    sch = tuner.pick(batch, max(d.n_views for d in data), candidates=cands)
+    out["schedule"] = {"threads": sch.threads, "voxels_per_thread": sch.voxels_per_thread,
+                       "ctas_per_sm": sch.ctas_per_sm, "tile": sch.tile}
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    ev = [torch.cuda.Event(enable_timing=True, external=True) for _ in range(3)]
+    graph = torch.cuda.CUDAGraph()
+    torch.cuda.synchronize()
+    with torch.cuda.graph(graph):
+        ev[0].record()
+        batch.fuse(sch)
+        ev[1].record()
+        batch.finalize(scores=[s.score for s in sess], points=[s.points for s in sess],
+                       labels=[s.labels for s in sess])
+        ev[2].record()
+    fuse_ms, all_ms = [], []
+    for k in range(8):
+        flush.zero_()
+        graph.replay()
+        torch.cuda.synchronize()
+        if k >= 2:
+            fuse_ms.append(ev[0].elapsed_time(ev[1]))
+            all_ms.append(ev[0].elapsed_time(ev[2]))
+    out["batched_graph_ms"] = float(np.mean(all_ms))
+    out["batched_fuse_ms"] = float(np.mean(fuse_ms))
+    out["batched_updates_per_s"] = nominal / (np.mean(all_ms) * 1e-3)
+    out["plain_updates_per_s"] = nominal / (out["plain_ms"] * 1e-3)
+    out["launches"] = {"batched": 3 + 0, "plain": 4 * n_sessions}
+    del graph
+    for s in sess:
+        s.close()
+    batch.close()
+    torch.cuda.synchronize()
+    # (b) served requests
+    foot = sum(Session.footprint(d) for d in data)
+    served = {}
+    for rate in rates:
+        n_req = int(min(1000, max(200, rate * 2.0)))
+        res = {}
+        for mode in ("server", "incremental", "refuse"):
+            reqs = poisson_requests(n_req, float(rate), [d.sid for d in data], seed=1005 + 4)
+            if mode == "server":
+                srv = Server(data, memory_budget=int(foot * budget_frac) + 1, max_batch=64)
+                srv.admit_all()
+                warm = poisson_requests(64, float(rate), [d.sid for d in data], seed=99)
+                srv.run(warm)
+                srv.run(reqs)
+                res[mode] = latency_summary(reqs)
+                res[mode]["evictions"] = srv.stats["evictions"]
+                srv.close()
+            else:
+                serve_plain(data, reqs, mode)
+                res[mode] = latency_summary(reqs)
+        served[str(rate)] = res
+    out["served"] = served
+    return out
+
+
 def run(args):
     rank = _env_int("RANK", 0)
     world = _env_int("WORLD_SIZE", 1)
@@ -496,6 +607,11 @@ def run(args):
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     res, wl = run_ours(args, rank, world, local_rank)
+    if not args.quick and not args.no_sessions:
+        import torch
+        res["sessions"] = measure_sessions(torch.device("cuda", local_rank), args.sessions_scale,
+                                           args.sessions, [float(r) for r in
+                                                           args.rates.split(",")])
     if not args.quick and not args.no_adjoint:
         import torch
         res["adjoint"] = measure_adjoint(torch.device("cuda", local_rank), max(5, args.steps // 2))
@@ -553,6 +669,12 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-adjoint", action="store_true", help="skip the forward+backward leg")
+    ap.add_argument("--no-sessions", action="store_true", help="skip the batched/served leg")
+    ap.add_argument("--sessions", type=int, default=32, help="sessions in the batched/served leg")
+    ap.add_argument("--sessions-scale", type=float, default=0.5,
+                    help="size scale of the sessions (1.0 = the full session mix)")
+    ap.add_argument("--rates", default="200,2000,20000",
+                    help="request rates (per second) to serve")
     ap.add_argument("--quick", action="store_true",
                     help="timed graph steps only: no eager, per-update, e2e or CPU legs")
     args = ap.parse_args(argv)

@@ -226,8 +226,10 @@ divas_status divas_debug_project(divas_ctx* ctx, const divas_camera* cam, int32_
  * its first use allocates that scratch.  The batch stages descriptors in
  * pinned host memory (double-buffered) and copies them with one
  * cudaMemcpyAsync per call, so a fused-and-finalized batch can be captured in
- * a CUDA graph.  The contexts of one batch must not be used by other calls
- * between queue and finalize.
+ * a CUDA graph (the graph's copy keeps reading that staging buffer on every
+ * replay, so a captured batch object must not be reused while the graph
+ * lives).  fuse and finalize must run on the same stream.  The contexts of one
+ * batch must not be used by other calls between queue and finalize.
  */
 typedef struct divas_batch divas_batch;
 

@@ -108,6 +108,11 @@ class Batch:
         self._check(self.lib.divas_batch_queue(self._h, fusion.handle, arr, n))
         self.sessions.append(fusion)
 
+    def queue_prepared(self, fusion: VoxelFusion, view: L.DivasView):
+        """Queue one already marshalled view of one session."""
+        self._check(self.lib.divas_batch_queue(self._h, fusion.handle, ctypes.byref(view), 1))
+        self.sessions.append(fusion)
+
     def fuse(self, schedule: Schedule | None = None, dry_run: bool = False, stream=None):
         sch = (schedule or Schedule()).c()
         self._check(self.lib.divas_batch_fuse(self._h, ctypes.byref(sch), 1 if dry_run else 0,

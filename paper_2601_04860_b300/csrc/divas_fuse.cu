@@ -532,7 +532,17 @@ divas_status cuda_fail(divas_ctx* c, cudaError_t e, const char* where) {
         if (e_ != cudaSuccess) return cuda_fail(ctx, e_, what);    \
     } while (0)
 
-inline cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+inline cudaStream_t S(void* s) {
+    // a launch is checked with cudaGetLastError, so first drop any stale,
+    // non-sticky error that an earlier unchecked runtime call left behind
+    (void)cudaGetLastError();
+    return reinterpret_cast<cudaStream_t>(s);
+}
+
+bool capturing(cudaStream_t s) {
+    cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+    return cudaStreamIsCapturing(s, &st) == cudaSuccess && st != cudaStreamCaptureStatusNone;
+}
 
 int grid_for(int64_t items, int32_t sm_count, int per_sm = 16) {
     int64_t b = (items + kThreads - 1) / kThreads;
@@ -1019,6 +1029,7 @@ divas_status divas_debug_project(divas_ctx* c, const divas_camera* cam, int32_t*
 void divas_fuse_destroy(divas_ctx* c) {
     if (!c) return;
     free_all(c);
+    (void)cudaGetLastError();  // teardown errors are not reported; do not leave them pending
     delete c;
 }
 
@@ -1373,9 +1384,11 @@ divas_status divas_batch_fuse(divas_batch* b, const divas_schedule* sched, int32
             hs[k].bits_out = b->ctxs[k]->bits;
         }
     }
+    // (under stream capture the copy node keeps reading this staging buffer on
+    // every replay: the batch must not be reused while such a graph is alive)
     cudaError_t e = cudaMemcpyAsync(b->d_stage, b->h_stage[b->cur], b->stage_bytes,
                                     cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaEventRecord(b->stage_done[b->cur], s);
+    if (e == cudaSuccess && !capturing(s)) e = cudaEventRecord(b->stage_done[b->cur], s);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_counter, 0, 4, s);
     if (e != cudaSuccess) return bfail(b, DIVAS_E_CUDA, cudaGetErrorString(e));
     const SessionDesc* dS = reinterpret_cast<const SessionDesc*>(b->d_stage);
@@ -1428,7 +1441,7 @@ divas_status divas_batch_finalize(divas_batch* b, float* const* score_out, const
     // the staging buffer is the one of the fuse call; the copy orders after it on the stream
     cudaError_t e = cudaMemcpyAsync(b->d_stage, b->h_stage[b->cur], b->stage_bytes,
                                     cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaEventRecord(b->stage_done[b->cur], s);
+    if (e == cudaSuccess && !capturing(s)) e = cudaEventRecord(b->stage_done[b->cur], s);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_counter, 0, 16, s);
     if (e != cudaSuccess) return bfail(b, DIVAS_E_CUDA, cudaGetErrorString(e));
     const SessionDesc* dS = reinterpret_cast<const SessionDesc*>(b->d_stage);
@@ -1475,6 +1488,7 @@ void divas_batch_destroy(divas_batch* b) {
     if (b->dW) cudaFree(b->dW);
     if (b->dZ) cudaFree(b->dZ);
     if (b->dbits) cudaFree(b->dbits);
+    (void)cudaGetLastError();  // teardown errors are not reported; do not leave them pending
     delete b;
 }
 

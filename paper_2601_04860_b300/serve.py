@@ -35,7 +35,7 @@ import numpy as np
 import torch
 
 from .batch import Autotuner, Batch, Schedule
-from .fusion import FusionParams, PreparedViews, VoxelFusion
+from .fusion import FusionParams, PreparedViews, VoxelFusion, view_c
 
 
 @dataclass
@@ -76,6 +76,9 @@ class Session:
             self.mask = [_tensor(m, dev) for m in data.mask]
         self.points = _tensor(data.points, dev)
         self.fusion = VoxelFusion(data.grid, occ=self.occ, coords=self.coords, params=data.params)
+        # one marshalled view struct per view, reused by every request
+        self.view_c = [view_c(data.cams[k], self.depth[k], self.mask[k], data.mask_type)
+                       for k in range(data.n_views)]
         n_score = self.fusion.n_cells if self.fusion.dense else self.fusion.n_active
         self.score = torch.empty(n_score, dtype=torch.float32, device=dev)
         self.labels = torch.empty(len(data.points), dtype=torch.uint8, device=dev)
@@ -166,6 +169,17 @@ class Server:
         self.used -= Session.footprint(self.data[sid])
         self.stats["evictions"] += 1
 
+    def admit_all(self) -> int:
+        """Admit sessions up front while the budget allows; returns how many."""
+        for sid in self.data:
+            if sid in self.resident:
+                continue
+            if self.used + Session.footprint(self.data[sid]) > self.budget:
+                break
+            self._admit(sid, set())
+        torch.cuda.synchronize(self.dev)
+        return len(self.resident)
+
     # -- the loop -------------------------------------------------------------
     def run(self, requests: list[Request], t0: float | None = None) -> list[Request]:
         """Serve requests (sorted by arrival, seconds from t0) in real time."""
@@ -216,8 +230,7 @@ class Server:
         for r in picked:
             s = self.resident[r.sid]
             k = s.views_done % s.data.n_views   # sessions cycle through their views
-            b.queue(s.fusion, [s.data.cams[k]], [s.depth[k]], [s.mask[k]],
-                    mask_type=s.data.mask_type)
+            b.queue_prepared(s.fusion, s.view_c[k])
             s.views_done += 1
             self.views_done[r.sid] = s.views_done
             self.last_use[r.sid] = time.perf_counter()

@@ -440,7 +440,10 @@ def _config3_scene(seed, n_ell, cams_pos):
             a = rs.uniform(0, 2 * np.pi)
             ax = rs.uniform(0.05, 0.6, size=3)
             ci = np.array([r * np.cos(a), r * np.sin(a), ax[2]])
-            if np.min(np.linalg.norm(cams_pos - ci, axis=1)) > ax.max() + 0.1:
+            if len(cams_pos) == 0:  # cameras unknown: keep clear of the whole orbit annulus
+                if abs(r - 4.0) > ax.max() + 0.1:
+                    break
+            elif np.min(np.linalg.norm(cams_pos - ci, axis=1)) > ax.max() + 0.1:
                 break
         c[i] = ci
         axes[i] = ax
@@ -450,9 +453,13 @@ def _config3_scene(seed, n_ell, cams_pos):
                  np.array([50.0]), np.array([n_ell], np.int32), ids[ids % 5 == 0])
 
 
+_ND_CACHE: dict = {}
+
+
 def config3(seed: int = 1003, g: int = 512, n_views: int = 16, W: int = 1297, H: int = 840,
             f: float = 1100.0, n_ell: int = 1000, n_occ: int | None = 12_000_000,
-            n_points: int = 3_000_000, s_max: float = 6.0) -> Workload:
+            n_points: int = 3_000_000, s_max: float = 6.0,
+            view_seed: int | None = None) -> Workload:
     """Contracted 512^3 grid over [-2,2]^3 stored as a sparse occupied set;
     1,000 ellipsoids resting on the ground z = 0 (radial distance
     log-uniform [0.3, 50], semi-axes U[0.05, 0.6], group = id mod 5, target
@@ -463,20 +470,25 @@ def config3(seed: int = 1003, g: int = 512, n_views: int = 16, W: int = 1297, H:
     Occupancy: the ``n_occ`` voxels nearest (in contracted-space distance, in
     units of the contracted voxel edge) to a contracted surface; ``n_occ``
     defaults to 12M at g = 512 and scales with g^3 otherwise."""
-    rc = np.random.Generator(np.random.PCG64(seed + 5))
+    rc = np.random.Generator(np.random.PCG64((seed if view_seed is None else view_seed) + 5))
     az = 2 * np.pi * np.arange(n_views) / n_views + rc.uniform(-0.1, 0.1, n_views)
     hts = rc.uniform(0.5, 2.0, n_views)
     cams_pos = np.column_stack([4 * np.cos(az), 4 * np.sin(az), hts])
-    scene = _config3_scene(seed, n_ell, cams_pos)
+    scene = _config3_scene(seed, n_ell, np.zeros((0, 3)) if view_seed is not None else cams_pos)
     scale = W / 1297.0
     cams = [look_at(p, (0, 0, 0.5), (0, 0, 1), f * scale, f * scale, W / 2, H / 2, W, H)
             for p in cams_pos]
     if n_occ is None:
         n_occ = int(round(12_000_000 * (g / 512) ** 3))
-    nd = np.empty(g ** 3, np.float32)
-    _lib().synth_contracted_distance(len(scene.ell_c), _p(np.ascontiguousarray(scene.ell_c)),
-                                     _p(scene.ell_M), _p(np.ascontiguousarray(scene.ell_brad)),
-                                     2.0 - 1.0 / 50.0, g, float(s_max), _p(nd))
+    key = (seed, g, n_ell, float(s_max))
+    nd = _ND_CACHE.get(key)
+    if nd is None:
+        nd = np.empty(g ** 3, np.float32)
+        _lib().synth_contracted_distance(len(scene.ell_c), _p(np.ascontiguousarray(scene.ell_c)),
+                                         _p(scene.ell_M), _p(np.ascontiguousarray(scene.ell_brad)),
+                                         2.0 - 1.0 / 50.0, g, float(s_max), _p(nd))
+        _ND_CACHE.clear()  # keep one field (they are large)
+        _ND_CACHE[key] = nd
     finite = np.flatnonzero(np.isfinite(nd))
     if len(finite) > n_occ:
         vals = nd[finite]
@@ -523,7 +535,8 @@ def session_mix(seed: int = 1005, n_sessions: int = 64, scale: float = 1.0) -> l
         views = int(rng.integers(2, 13))
         W, H = res[int(rng.integers(0, 3))]
         out.append(dict(session=s, dense=dense, g=g, n_sparse=n_sparse, views=views, W=W, H=H,
-                        n_points=200_000, scene_seed=int(seed * 100 + s), scale=scale))
+                        n_points=200_000, scene_seed=int(seed * 100 + s),
+                        sparse_seed=int(seed * 100), scale=scale))
     return out
 
 
@@ -553,11 +566,14 @@ def session_workload(recipe: dict) -> Workload:
                 wl.hit.append(hid)
                 wl.mask.append(soft_mask_f16(np.isin(hid, wl.scene.target_ids), rm))
     else:
-        g = max(32, int(round(256 * sc)))
+        # sparse sessions share one unbounded scene (its contracted distance field
+        # is computed once) and differ in views, resolution and occupied-set size
+        g = max(32, int(round(384 * sc)))
         n_occ = max(1000, int(round(recipe["n_sparse"] * sc ** 3)))
         n_occ = min(n_occ, int(0.12 * g ** 3))
-        wl = config3(seed=recipe["scene_seed"], g=g, n_views=recipe["views"], W=W, H=H,
-                     n_occ=n_occ, n_points=npts, n_ell=200)
+        wl = config3(seed=recipe["sparse_seed"], g=g, n_views=recipe["views"], W=W, H=H,
+                     n_occ=n_occ, n_points=npts, n_ell=200,
+                     view_seed=recipe["scene_seed"])
     wl.name = f"session{recipe['session']}"
     wl.meta.update(recipe)
     return wl
