@@ -80,6 +80,23 @@ def traffic_for(workload, kernel):
     return TRAFFIC_CAPTURE.get(workload, {}).get(kernel)
 
 
+def max_over_ranks(x: float, world: int, device=None) -> float:
+    """Largest value of x over the ranks (the slowest rank times the job)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64,
+                     device=device if dist.get_backend() == "nccl" else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank: float, world: int, ms_max: float) -> float:
+    """Whole-job rate: the units all ranks processed / the slowest rank's time."""
+    return world * units_per_rank / (ms_max * 1e-3)
+
+
 def make_workload(name):
     import synth
     if name == "forward-dense-256":
@@ -285,14 +302,10 @@ def run_ours(args, rank, world, local_rank):
     t_wall = time.perf_counter() - t_wall
     clk = clocks.stop()
     step_ms = np.array(step_ms)
-    ms = float(step_ms.mean())
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(float(step_ms.mean()), world, dev)
 
     if args.quick:  # timed graph steps only (profiling runs)
-        res = {"metric": METRIC, "value": world * N * S / (ms * 1e-3), "unit": UNIT,
+        res = {"metric": METRIC, "value": job_throughput(N * S, world, ms), "unit": UNIT,
                "ms_per_step": ms, "phase_ms": {k: float(np.mean(v)) for k, v in phase.items()},
                "quick": True}
         fu.close()
@@ -388,11 +401,7 @@ def run_ours(args, rank, world, local_rank):
         b.record()
         torch.cuda.synchronize()
         e2e_ms.append(a.elapsed_time(b))
-    e2e_ms = float(np.mean(e2e_ms))
-    if world > 1:
-        t = torch.tensor([e2e_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks(float(np.mean(e2e_ms)), world, dev)
 
     algo, view_bytes, _, _ = algorithmic_bytes(wl, n_active)
     peak, peak_kind = peaks()
@@ -402,7 +411,8 @@ def run_ours(args, rank, world, local_rank):
     achieved = algo[dom] / (pm[dom] * 1e-3) / 1e9
     step_bytes = sum(algo.values())
     res = {
-        "metric": METRIC, "value": world * N * S / (ms * 1e-3), "unit": UNIT, "n_gpus": world,
+        "metric": METRIC, "value": job_throughput(N * S, world, ms), "unit": UNIT,
+        "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (seeded ray-cast scene; no dataset)",
@@ -429,7 +439,7 @@ def run_ours(args, rank, world, local_rank):
                           "graph_p50": float(np.percentile(upd_g, 50)) if len(upd_g) else None,
                           "graph_p99": float(np.percentile(upd_g, 99)) if len(upd_g) else None},
         "active_updates_per_s": world * n_active * S / (ms * 1e-3),
-        "e2e": {"value": world * N * S / (e2e_ms * 1e-3), "unit": UNIT,
+        "e2e": {"value": job_throughput(N * S, world, e2e_ms), "unit": UNIT,
                 "ms_per_step": e2e_ms, "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(sum(kernels_per_phase.values()) * args.steps),

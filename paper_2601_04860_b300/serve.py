@@ -118,8 +118,11 @@ class Server:
 
     def __init__(self, sessions: list[SessionData], memory_budget: int, device=None,
                  max_batch: int = 64, max_inflight: int = 2, autotune: bool = False,
-                 schedule: Schedule | None = None):
+                 schedule: Schedule | None = None, session_factory=None, footprint=None):
         self.dev = torch.device(device or "cuda")
+        # how sessions are created and sized (replaceable for host-side tests)
+        self.session_factory = session_factory or Session
+        self.footprint = footprint or Session.footprint
         self.data = {s.sid: s for s in sessions}
         self.budget = int(memory_budget)
         self.max_batch = max_batch
@@ -129,9 +132,11 @@ class Server:
         self.views_done: dict[int, int] = {s.sid: 0 for s in sessions}
         self.used = 0
         self.last_use: dict[int, float] = {}
-        self.streams = [torch.cuda.Stream(device=self.dev) for _ in range(max_inflight)]
-        self.batches = [Batch(max_sessions=max_batch, max_views=max_batch)
-                        for _ in range(max_inflight)]
+        self.streams, self.batches = [], []
+        if session_factory is None:  # a real server launches batches on its own streams
+            self.streams = [torch.cuda.Stream(device=self.dev) for _ in range(max_inflight)]
+            self.batches = [Batch(max_sessions=max_batch, max_views=max_batch)
+                            for _ in range(max_inflight)]
         self.tuner = Autotuner() if autotune else None
         self.schedule = schedule or Schedule()
         self.stats = {"batches": 0, "evictions": 0, "admissions": 0, "batch_sizes": []}
@@ -140,7 +145,7 @@ class Server:
     def _admit(self, sid: int, busy: set) -> bool:
         if sid in self.resident:
             return True
-        need = Session.footprint(self.data[sid])
+        need = self.footprint(self.data[sid])
         if need > self.budget:
             raise ValueError(f"session {sid} needs {need} bytes, above the whole budget")
         # evict idle sessions, least recently used first
@@ -150,7 +155,7 @@ class Server:
                 return False
             victim = min(idle, key=lambda s: self.last_use.get(s, -1.0))
             self._evict(victim)
-        sess = Session(self.data[sid], self.dev)
+        sess = self.session_factory(self.data[sid], self.dev)
         if sid in self.evicted:
             st = self.evicted.pop(sid)
             sess.fusion.import_state({k: (v.to(self.dev) if isinstance(v, torch.Tensor) else v)
@@ -163,10 +168,11 @@ class Server:
 
     def _evict(self, sid: int):
         sess = self.resident.pop(sid)
-        torch.cuda.synchronize(self.dev)
+        if self.dev.type == "cuda" and torch.cuda.is_available():
+            torch.cuda.synchronize(self.dev)
         self.evicted[sid] = sess.export()
         sess.close()
-        self.used -= Session.footprint(self.data[sid])
+        self.used -= self.footprint(self.data[sid])
         self.stats["evictions"] += 1
 
     def admit_all(self) -> int:
@@ -174,10 +180,11 @@ class Server:
         for sid in self.data:
             if sid in self.resident:
                 continue
-            if self.used + Session.footprint(self.data[sid]) > self.budget:
+            if self.used + self.footprint(self.data[sid]) > self.budget:
                 break
             self._admit(sid, set())
-        torch.cuda.synchronize(self.dev)
+        if self.dev.type == "cuda" and torch.cuda.is_available():
+            torch.cuda.synchronize(self.dev)
         return len(self.resident)
 
     # -- the loop -------------------------------------------------------------
@@ -253,7 +260,8 @@ class Server:
         return ev, b, picked, si
 
     def close(self):
-        torch.cuda.synchronize(self.dev)
+        if self.dev.type == "cuda" and torch.cuda.is_available():
+            torch.cuda.synchronize(self.dev)
         for s in self.resident.values():
             s.close()
         self.resident.clear()
