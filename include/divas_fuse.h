@@ -161,6 +161,20 @@ divas_status divas_fuse_add_views(divas_ctx* ctx, const divas_view* views, int32
 divas_status divas_fuse_finalize(divas_ctx* ctx, float* score_out, uint32_t* seg_bits_out,
                                  uint32_t* vmask_out, int64_t* n_seg_host, void* stream);
 
+/*
+ * The whole hot path in one call: divas_fuse_set_occupancy (A1), then
+ * divas_fuse_add_views (views folded into fresh accumulators), then finalize
+ * (score_out, seg_bits_out as in divas_fuse_finalize) and, when n_pts > 0,
+ * divas_label_points.  The zero-fill of the outputs runs on a helper stream of
+ * the context, in parallel with the occupancy compaction and the fusion (fork
+ * and join through events, so the call can be captured in a CUDA graph).
+ * Results equal the separate calls.
+ */
+divas_status divas_fuse_step(divas_ctx* ctx, const uint8_t* occ_dense, const int32_t* coords,
+                             int64_t n_coords, const divas_view* views, int32_t n_views,
+                             float* score_out, uint32_t* seg_bits_out, const float* xyz,
+                             int64_t n_pts, uint8_t* labels_out, void* stream);
+
 /* Pass 1 labels (Eq. pass1): labels_out[i] = seg bit of the voxel containing
  * point i (device n x 3 float32), 0 outside the grid (half-open box), for NaN,
  * or for unoccupied voxels.  Uses the seg bitfield of the last finalize. */
@@ -206,6 +220,12 @@ divas_status divas_fuse_import_state(divas_ctx* ctx, const float* W_in, const fl
 divas_status divas_fuse_backward(divas_ctx* ctx, const divas_view* views, int32_t n_views,
                                  const float* grad_score, float* const* grad_mask,
                                  float* const* grad_depth, void* stream);
+
+/* Test hook: out_nr[i] = the projection's reciprocal of x[i] (hardware
+ * approximation + one Newton-Raphson step), out_ieee[i] = the correctly
+ * rounded reciprocal (device n floats each). */
+divas_status divas_debug_rcp(const float* x, int64_t n, float* out_nr, float* out_ieee,
+                             void* stream);
 
 /* Test hook: pixel index iy*W + ix that each active voxel projects to in a
  * camera, or -1 when it is behind z_near or out of frame (device n_active int32). */

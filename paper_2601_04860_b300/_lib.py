@@ -72,6 +72,9 @@ _SIGS = {
     "divas_fuse_backward": (ctypes.c_int, [_P, ctypes.POINTER(DivasView), ctypes.c_int32, _P,
                                            ctypes.POINTER(_P), ctypes.POINTER(_P), _P]),
     "divas_debug_project": (ctypes.c_int, [_P, ctypes.POINTER(DivasCamera), _P, _P]),
+    "divas_debug_rcp": (ctypes.c_int, [_P, ctypes.c_int64, _P, _P, _P]),
+    "divas_fuse_step": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64, ctypes.POINTER(DivasView),
+                                       ctypes.c_int32, _P, _P, _P, ctypes.c_int64, _P, _P]),
     "divas_fuse_dense_noalloc": (ctypes.c_int, [ctypes.POINTER(DivasGrid), _P,
                                                 ctypes.POINTER(DivasView), ctypes.c_int32,
                                                 ctypes.POINTER(DivasParams), _P, _P, _P]),

@@ -305,7 +305,7 @@ __device__ __forceinline__ float floor_df(float hi, float lo) {
 __device__ __forceinline__ uint8_t label_one(const float* __restrict__ xyz, int64_t a,
                                              const GridC& G,
                                              const uint32_t* __restrict__ seg_bits) {
-    float xh[3] = {__ldg(xyz + 3 * a), __ldg(xyz + 3 * a + 1), __ldg(xyz + 3 * a + 2)};
+    float xh[3] = {xyz[3 * a], xyz[3 * a + 1], xyz[3 * a + 2]};
     float xl[3] = {0.f, 0.f, 0.f};
     uint8_t lab = 0;
     if (!(isnan(xh[0]) || isnan(xh[1]) || isnan(xh[2]))) {
@@ -383,12 +383,30 @@ __device__ __forceinline__ uint8_t label_one(const float* __restrict__ xyz, int6
     return lab;
 }
 
+// four points per thread: their 48 bytes come in three 128-bit loads (when the
+// array is 16-byte aligned) so that every thread has all its loads in flight
 __global__ void __launch_bounds__(kThreads) k_label(const float* __restrict__ xyz, int64_t n,
                                                     GridC G, const uint32_t* __restrict__ seg_bits,
                                                     uint8_t* __restrict__ labels) {
-    for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < n;
-         a += (int64_t)gridDim.x * blockDim.x)
-        labels[a] = label_one(xyz, a, G, seg_bits);
+    const bool vec = (reinterpret_cast<uintptr_t>(xyz) & 15) == 0 &&
+                     (reinterpret_cast<uintptr_t>(labels) & 3) == 0;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; 4 * q < n;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t a = 4 * q;
+        if (vec && a + 4 <= n) {
+            const float4* p4 = reinterpret_cast<const float4*>(xyz + 3 * a);
+            const float4 f0 = __ldcs(p4), f1 = __ldcs(p4 + 1), f2 = __ldcs(p4 + 2);
+            const float pts[12] = {f0.x, f0.y, f0.z, f0.w, f1.x, f1.y,
+                                   f1.z, f1.w, f2.x, f2.y, f2.z, f2.w};
+            uint32_t packed = 0;
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                packed |= (uint32_t)label_one(pts + 3 * k, 0, G, seg_bits) << (8 * k);
+            *reinterpret_cast<uint32_t*>(labels + a) = packed;
+        } else {
+            for (int64_t b = a; b < a + 4 && b < n; ++b) labels[b] = label_one(xyz, b, G, seg_bits);
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -459,6 +477,15 @@ __global__ void k_debug_project(const uint32_t* __restrict__ active, const int32
     }
 }
 
+__global__ void k_debug_rcp(const float* __restrict__ x, int64_t n, float* __restrict__ nr,
+                            float* __restrict__ ieee) {
+    for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < n;
+         a += (int64_t)gridDim.x * blockDim.x) {
+        nr[a] = rcp_nr(x[a]);
+        ieee[a] = __frcp_rn(x[a]);
+    }
+}
+
 __global__ void k_active_coords(const uint32_t* __restrict__ active, const int32_t* __restrict__ d_n,
                                 int32_t g, int32_t* __restrict__ out) {
     const int32_t n = *d_n;
@@ -493,6 +520,10 @@ struct divas_ctx {
     uint32_t* seg_bits = nullptr;
     uint32_t* active = nullptr;
     FastDiv gdiv;  // division by g
+    // divas_fuse_step: a helper stream zero-fills the outputs while the main
+    // stream compacts and fuses (fork / join through two events)
+    cudaStream_t helper = nullptr;
+    cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
     float* W = nullptr;
     float* Z = nullptr;
     uint32_t* bits = nullptr;
@@ -675,6 +706,9 @@ divas_status read_status(divas_ctx* c, cudaStream_t s) {
 }
 
 void free_all(divas_ctx* c) {
+    if (c->helper) cudaStreamDestroy(c->helper);
+    if (c->fork_ev) cudaEventDestroy(c->fork_ev);
+    if (c->join_ev) cudaEventDestroy(c->join_ev);
     void* ptrs[] = {c->occ_bits, c->word_prefix, c->block_sums, c->seg_bits, c->active, c->W,
                     c->Z,        c->bits,        c->d_n,        c->d_status, c->d_total, c->d_nseg};
     for (void* p : ptrs)
@@ -772,6 +806,9 @@ divas_status divas_fuse_init(divas_ctx** out, const divas_grid* grid, const uint
     } while (0)
     INIT_CUDA(cudaGetDevice(&dev));
     INIT_CUDA(cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, dev));
+    INIT_CUDA(cudaStreamCreateWithFlags(&c->helper, cudaStreamNonBlocking));
+    INIT_CUDA(cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming));
+    INIT_CUDA(cudaEventCreateWithFlags(&c->join_ev, cudaEventDisableTiming));
     INIT_CUDA(cudaMalloc(&c->occ_bits, c->n_words * 4));
     INIT_CUDA(cudaMalloc(&c->word_prefix, c->n_words * 4));
     INIT_CUDA(cudaMalloc(&c->seg_bits, c->n_words * 4));
@@ -886,28 +923,80 @@ divas_status divas_fuse_add_views(divas_ctx* c, const divas_view* views, int32_t
     return launch_fuse(c, vb, S(stream));
 }
 
+}  // extern "C"
+
+namespace {
+
+// zero-fill what the scatter below ORs or writes into
+divas_status finalize_zero(divas_ctx* c, float* score_out, uint32_t* seg_bits_out, cudaStream_t s) {
+    if (score_out && c->grid.kind == 0)
+        DIVAS_CUDA(c, cudaMemsetAsync(score_out, 0, c->n_cells * 4, s));
+    DIVAS_CUDA(c, cudaMemsetAsync(c->seg_bits, 0, c->n_words * 4, s));
+    if (seg_bits_out) DIVAS_CUDA(c, cudaMemsetAsync(seg_bits_out, 0, c->n_words * 4, s));
+    return DIVAS_OK;
+}
+
+divas_status finalize_scatter(divas_ctx* c, float* score_out, uint32_t* seg_bits_out,
+                              uint32_t* vmask_out, unsigned long long* nseg, cudaStream_t s) {
+    k_finalize<<<grid_for(c->cap, c->sm_count, 16), kThreads, 0, s>>>(
+        c->active, c->d_n, c->grid.g, c->grid.kind == 0 ? 1 : 0, c->W, c->Z, c->bits, c->F.eps,
+        c->F.tau_cons, score_out, c->seg_bits, seg_bits_out, vmask_out, nseg);
+    DIVAS_LAUNCHED(c, "k_finalize");
+    return DIVAS_OK;
+}
+
+divas_status finalize_count(divas_ctx* c, int64_t* n_seg_host, cudaStream_t s) {
+    unsigned long long v = 0;
+    DIVAS_CUDA(c, cudaMemcpyAsync(&v, c->d_nseg, 8, cudaMemcpyDeviceToHost, s));
+    divas_status st = read_status(c, s);  // synchronises
+    *n_seg_host = (int64_t)v;
+    return st;
+}
+
+}  // namespace
+
+extern "C" {
+
 divas_status divas_fuse_finalize(divas_ctx* c, float* score_out, uint32_t* seg_bits_out,
                                  uint32_t* vmask_out, int64_t* n_seg_host, void* stream) {
     if (!c) return fail(nullptr, DIVAS_E_INVALID, "ctx is NULL");
     cudaStream_t s = S(stream);
     unsigned long long* nseg = n_seg_host ? c->d_nseg : nullptr;
     if (nseg) DIVAS_CUDA(c, cudaMemsetAsync(c->d_nseg, 0, 8, s));
-    // zero-fill, then scatter the active voxels' scores and seg bits
-    if (score_out && c->grid.kind == 0)
-        DIVAS_CUDA(c, cudaMemsetAsync(score_out, 0, c->n_cells * 4, s));
-    DIVAS_CUDA(c, cudaMemsetAsync(c->seg_bits, 0, c->n_words * 4, s));
-    if (seg_bits_out) DIVAS_CUDA(c, cudaMemsetAsync(seg_bits_out, 0, c->n_words * 4, s));
-    k_finalize<<<grid_for(c->cap, c->sm_count, 16), kThreads, 0, s>>>(
-        c->active, c->d_n, c->grid.g, c->grid.kind == 0 ? 1 : 0, c->W, c->Z, c->bits, c->F.eps,
-        c->F.tau_cons, score_out, c->seg_bits, seg_bits_out, vmask_out, nseg);
-    DIVAS_LAUNCHED(c, "k_finalize");
-    if (n_seg_host) {
-        unsigned long long v = 0;
-        DIVAS_CUDA(c, cudaMemcpyAsync(&v, c->d_nseg, 8, cudaMemcpyDeviceToHost, s));
-        divas_status st = read_status(c, s);  // synchronises
-        *n_seg_host = (int64_t)v;
-        if (st != DIVAS_OK) return st;
-    }
+    divas_status st = finalize_zero(c, score_out, seg_bits_out, s);
+    if (st != DIVAS_OK) return st;
+    st = finalize_scatter(c, score_out, seg_bits_out, vmask_out, nseg, s);
+    if (st != DIVAS_OK) return st;
+    if (n_seg_host) return finalize_count(c, n_seg_host, s);
+    return DIVAS_OK;
+}
+
+divas_status divas_fuse_step(divas_ctx* c, const uint8_t* occ_dense, const int32_t* coords,
+                             int64_t n_coords, const divas_view* views, int32_t n_views,
+                             float* score_out, uint32_t* seg_bits_out, const float* xyz, int64_t n_pts,
+                             uint8_t* labels_out, void* stream) {
+    if (!c) return fail(nullptr, DIVAS_E_INVALID, "ctx is NULL");
+    if (!views || n_views < 1 || n_views > kMaxViews)
+        return fail(c, DIVAS_E_INVALID, "n_views must be in 1..32 and views non-NULL");
+    if (n_pts < 0 || (n_pts > 0 && (!xyz || !labels_out)))
+        return fail(c, DIVAS_E_INVALID, "bad point arguments");
+    cudaStream_t s = S(stream);
+    // fork: the helper stream zero-fills the outputs in parallel
+    DIVAS_CUDA(c, cudaEventRecord(c->fork_ev, s));
+    DIVAS_CUDA(c, cudaStreamWaitEvent(c->helper, c->fork_ev, 0));
+    divas_status st = finalize_zero(c, score_out, seg_bits_out, c->helper);
+    if (st != DIVAS_OK) return st;
+    DIVAS_CUDA(c, cudaEventRecord(c->join_ev, c->helper));
+    // main: occupancy gate + active list, then the views
+    st = divas_fuse_set_occupancy(c, occ_dense, coords, n_coords, stream);
+    if (st != DIVAS_OK) return st;
+    st = divas_fuse_add_views(c, views, n_views, stream);
+    if (st != DIVAS_OK) return st;
+    // join, then normalise + threshold and label
+    DIVAS_CUDA(c, cudaStreamWaitEvent(s, c->join_ev, 0));
+    st = finalize_scatter(c, score_out, seg_bits_out, nullptr, nullptr, s);
+    if (st != DIVAS_OK) return st;
+    if (n_pts > 0) return divas_label_points(c, xyz, n_pts, labels_out, stream);
     return DIVAS_OK;
 }
 
@@ -917,8 +1006,8 @@ divas_status divas_label_points(divas_ctx* c, const float* xyz, int64_t n, uint8
     if (n < 0 || (n > 0 && (!xyz || !labels_out)))
         return fail(c, DIVAS_E_INVALID, "bad point arguments");
     if (n == 0) return DIVAS_OK;
-    k_label<<<grid_for(n, c->sm_count, 64), kThreads, 0, S(stream)>>>(xyz, n, c->G, c->seg_bits,
-                                                                       labels_out);
+    k_label<<<grid_for((n + 3) / 4, c->sm_count, 64), kThreads, 0, S(stream)>>>(
+        xyz, n, c->G, c->seg_bits, labels_out);
     DIVAS_LAUNCHED(c, "k_label");
     return DIVAS_OK;
 }
@@ -1024,6 +1113,15 @@ divas_status divas_debug_project(divas_ctx* c, const divas_camera* cam, int32_t*
                                                                    v, pix_out);
     DIVAS_LAUNCHED(c, "k_debug_project");
     return DIVAS_OK;
+}
+
+divas_status divas_debug_rcp(const float* x, int64_t n, float* out_nr, float* out_ieee,
+                             void* stream) {
+    if (n < 0 || (n > 0 && (!x || !out_nr || !out_ieee))) return DIVAS_E_INVALID;
+    if (n == 0) return DIVAS_OK;
+    k_debug_rcp<<<(unsigned)std::min<int64_t>((n + kThreads - 1) / kThreads, 4096), kThreads, 0,
+                  S(stream)>>>(x, n, out_nr, out_ieee);
+    return cudaGetLastError() == cudaSuccess ? DIVAS_OK : DIVAS_E_CUDA;
 }
 
 void divas_fuse_destroy(divas_ctx* c) {

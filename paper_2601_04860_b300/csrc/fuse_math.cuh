@@ -231,6 +231,17 @@ __device__ __forceinline__ VoxelGeom voxel_geom(uint32_t pk, const GridC& G, flo
 }
 
 // ---------------------------------------------------------------------------
+// reciprocal of a normal, positive float: the hardware approximation (relative
+// error below 2^-22) refined by one Newton-Raphson step r' = r + r (1 - x r),
+// which squares the error; the result is within one ulp of 1/x.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float rcp_nr(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return __fmaf_rn(r, __fmaf_rn(-x, r, 1.f), r);
+}
+
+// ---------------------------------------------------------------------------
 // step 1: projection -> pixel index (or -1) and camera depth p_z = hi + lo
 // (branch-free: every quantity is computed, validity is a predicate)
 // ---------------------------------------------------------------------------
@@ -261,8 +272,8 @@ __device__ __forceinline__ int32_t project(const ViewC& V, const VoxelGeom& vg, 
         py = h;
         pz = pzh;
     }
-    const bool front = pz > z_near;
-    const float inv = __frcp_rn(front ? pz : 1.f);
+    const bool front = pz > z_near && pz <= FLT_MAX;
+    const float inv = rcp_nr(front ? pz : 1.f);
     const float u = __fmaf_rn(V.fx, __fmul_rn(px, inv), V.cx);
     const float v = __fmaf_rn(V.fy, __fmul_rn(py, inv), V.cy);
     const bool in = front && u >= 0.f && u < V.Wf && v >= 0.f && v < V.Hf;

@@ -236,6 +236,19 @@ class VoxelFusion:
             out["n_seg"] = int(nseg.value)
         return {k: v for k, v in out.items() if v is not None}
 
+    def step(self, views: "PreparedViews", occ=None, coords=None, score=None, seg_bits=None,
+             xyz=None, labels=None, stream=None):
+        """The whole hot path in one call (occupancy gate, views, finalize,
+        labels), with the output zero-fill overlapped on a helper stream."""
+        if len(views.chunks) != 1:
+            raise ValueError("step() takes up to 32 views")
+        arr, n = views.chunks[0]
+        n_c = 0 if coords is None else coords.shape[0]
+        n_p = 0 if xyz is None else xyz.shape[0]
+        self._check(self.lib.divas_fuse_step(self._h, _ptr(occ), _ptr(coords), n_c, arr, n,
+                                             _ptr(score), _ptr(seg_bits), _ptr(xyz), n_p,
+                                             _ptr(labels), _stream(stream)))
+
     def label_points(self, xyz: torch.Tensor, out: torch.Tensor | None = None,
                      stream=None) -> torch.Tensor:
         """Pass 1 labels (uint8) of (n, 3) float32 points."""
