@@ -165,15 +165,30 @@ divas_status divas_fuse_finalize(divas_ctx* ctx, float* score_out, uint32_t* seg
  * The whole hot path in one call: divas_fuse_set_occupancy (A1), then
  * divas_fuse_add_views (views folded into fresh accumulators), then finalize
  * (score_out, seg_bits_out as in divas_fuse_finalize) and, when n_pts > 0,
- * divas_label_points.  The zero-fill of the outputs runs on a helper stream of
- * the context, in parallel with the occupancy compaction and the fusion (fork
- * and join through events, so the call can be captured in a CUDA graph).
- * Results equal the separate calls.
+ * divas_label_points, in four kernel launches and no memset: the compaction
+ * clears the seg bitfields, and the fusion launch also normalises and
+ * thresholds each voxel and writes the zeros of the unoccupied cells of a
+ * dense score_out.  Results (outputs and context state) equal the separate
+ * calls; 1..DIVAS_MAX_VIEWS_PER_CALL views.  Capturable in a CUDA graph.  If
+ * the occupied set overflows the capacity (DIVAS_E_CAPACITY at the next
+ * synchronising call), the dense scores of the dropped voxels are unspecified.
  */
 divas_status divas_fuse_step(divas_ctx* ctx, const uint8_t* occ_dense, const int32_t* coords,
                              int64_t n_coords, const divas_view* views, int32_t n_views,
                              float* score_out, uint32_t* seg_bits_out, const float* xyz,
                              int64_t n_pts, uint8_t* labels_out, void* stream);
+
+/* divas_fuse_step that also records stage_events[k] (cudaEvent_t, entries
+ * nullable; the array nullable) on `stream`: [0] before the compaction, [1]
+ * after it, [2] after the fusion + finalize launch, [3] after the labels.
+ * During a stream capture they become external event-record nodes (events
+ * created with timing enabled time a graph replay's stages). */
+divas_status divas_fuse_step_profiled(divas_ctx* ctx, const uint8_t* occ_dense,
+                                      const int32_t* coords, int64_t n_coords,
+                                      const divas_view* views, int32_t n_views, float* score_out,
+                                      uint32_t* seg_bits_out, const float* xyz, int64_t n_pts,
+                                      uint8_t* labels_out, void* const* stage_events,
+                                      void* stream);
 
 /* Pass 1 labels (Eq. pass1): labels_out[i] = seg bit of the voxel containing
  * point i (device n x 3 float32), 0 outside the grid (half-open box), for NaN,

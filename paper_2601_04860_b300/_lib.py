@@ -75,6 +75,9 @@ _SIGS = {
     "divas_debug_rcp": (ctypes.c_int, [_P, ctypes.c_int64, _P, _P, _P]),
     "divas_fuse_step": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64, ctypes.POINTER(DivasView),
                                        ctypes.c_int32, _P, _P, _P, ctypes.c_int64, _P, _P]),
+    "divas_fuse_step_profiled": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64,
+                                                ctypes.POINTER(DivasView), ctypes.c_int32, _P, _P,
+                                                _P, ctypes.c_int64, _P, ctypes.POINTER(_P), _P]),
     "divas_fuse_dense_noalloc": (ctypes.c_int, [ctypes.POINTER(DivasGrid), _P,
                                                 ctypes.POINTER(DivasView), ctypes.c_int32,
                                                 ctypes.POINTER(DivasParams), _P, _P, _P]),

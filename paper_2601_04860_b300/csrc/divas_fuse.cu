@@ -2,16 +2,16 @@
 //
 // Data layout in device memory (one context = one occupied set):
 //   occ_bits[ceil(g^3/32)]     occupancy prior as a bitfield, bit lin of the grid
-//   word_prefix[words]         exclusive prefix of popc(occ_bits): the rank structure
-//                              that maps a dense voxel to its active slot
+//   tile_state[tiles], ticket  look-back states of the single-pass compaction
 //   active[cap]                occupied voxels in ascending linear index, stored as
 //                              packed coordinates i | j << 10 | k << 20
 //   W[cap], Z[cap], bits[cap]  accumulators of Eq. vmask, structure of arrays
 //   seg_bits[words]            segmentation bitfield B^seg of the last finalize
 //
-// Kernels: occupancy -> bits (dense) or scatter (sparse); per-block popcounts,
-// a one-block scan and an emit pass build the active list (the active-voxel list
-// of Sec. 3.5 / Appendix B.1); the fusion kernel walks the active list with a
+// Kernels: one single-pass compaction (occupancy -> bits -> scan with decoupled
+// look-back -> emit; sparse grids scatter their coordinates into the bits
+// first) builds the active list (the active-voxel list of Sec. 3.5 /
+// Appendix B.1); the fusion kernel walks the active list with a
 // grid-stride loop and folds up to 32 views per launch; finalize writes the
 // dense score grid with 128-bit stores (or the per-active scores), the seg
 // bitfield with warp-assembled words and the view masks; labels look points up
@@ -38,8 +38,6 @@ using namespace divas;
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kWordsPerThread = 1;                       // compaction
-constexpr int kWordsPerBlock = kThreads * kWordsPerThread;
 constexpr int32_t kStatusBadCoord = 1;
 constexpr int32_t kStatusCapacity = 2;
 
@@ -51,37 +49,6 @@ struct BackPtrs {
 // ---------------------------------------------------------------------------
 // compaction
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* total);
-
-// dense uint8 prior -> bitfield words and per-block popcounts (one word per thread)
-__global__ void __launch_bounds__(kThreads) k_occ_bits(const uint8_t* __restrict__ occ,
-                                                       int64_t n_cells, int64_t n_words,
-                                                       uint32_t* __restrict__ bits,
-                                                       uint32_t* __restrict__ block_sums) {
-    const int64_t w = blockIdx.x * (int64_t)kThreads + threadIdx.x;
-    uint32_t word = 0;
-    if (w < n_words) {
-        const int64_t base = w * 32;
-        if (base + 32 <= n_cells && ((reinterpret_cast<uintptr_t>(occ + base) & 15) == 0)) {
-            const uint4 a = __ldcs(reinterpret_cast<const uint4*>(occ + base));
-            const uint4 b = __ldcs(reinterpret_cast<const uint4*>(occ + base) + 1);
-            const uint32_t v[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
-#pragma unroll
-            for (int q = 0; q < 8; ++q)
-#pragma unroll
-                for (int s = 0; s < 4; ++s)
-                    word |= (((v[q] >> (8 * s)) & 0xffu) != 0u ? 1u : 0u) << (4 * q + s);
-        } else {
-            for (int s = 0; s < 32 && base + s < n_cells; ++s)
-                word |= (occ[base + s] != 0 ? 1u : 0u) << s;
-        }
-        bits[w] = word;
-    }
-    uint32_t total;
-    block_exclusive_scan(__popc(word), &total);
-    if (threadIdx.x == 0) block_sums[blockIdx.x] = total;
-}
-
 // sparse coordinates -> bitfield (atomic OR; duplicates merge)
 __global__ void __launch_bounds__(kThreads) k_scatter_coords(const int32_t* __restrict__ coords,
                                                              int64_t n, int32_t g,
@@ -127,76 +94,220 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* t
     return warp_off + x - v;
 }
 
-// per-block popcount of kWordsPerBlock words
-__global__ void __launch_bounds__(kThreads) k_block_popc(const uint32_t* __restrict__ bits,
-                                                         int64_t n_words,
-                                                         uint32_t* __restrict__ block_sums) {
-    const int64_t base = (int64_t)blockIdx.x * kWordsPerBlock + threadIdx.x * kWordsPerThread;
-    uint32_t c = 0;
+// ---------------------------------------------------------------------------
+// compaction in two launches, neither of which waits on another CTA.  A group
+// is 32 consecutive occupancy words (1024 cells), held one word per lane; an
+// item is 8 words (256 cells); a tile is the 32 groups of one k_tile_count CTA.
+//   k_tile_count  per warp 4 groups: the uint8 prior is read with fully
+//                 coalesced 16-byte loads (lane l: cells 16 l .. 16 l + 15 of
+//                 a 512-cell half group), turned into 16-bit halves and paired
+//                 across lanes into words (dense), or the words are read
+//                 (sparse); item popcounts -> each item's offset inside its
+//                 tile, and the tile's count.  The CTA that finishes last
+//                 (ticket of a done counter, after a fence) scans the tile
+//                 counts into tile_offset, writes the total and n_active, flags
+//                 overflow and rearms the counter.
+//   k_tile_emit   one warp per group (grid-stride), slot = group offset + word
+//                 prefix + the word's set bits below the bit.  Scattered bits
+//                 (largest word popcount <= number of non-empty words): every
+//                 lane walks its own word; dense words: one round per
+//                 non-empty word in which lane b writes bit b (consecutive
+//                 slots per store).  Packed coordinates come from the word's
+//                 first cell plus the bit while the word stays on one row.
+// ---------------------------------------------------------------------------
+constexpr int kGroupsPerWarp = 4;
+constexpr int kTileGroups = (kThreads / 32) * kGroupsPerWarp;  // 32
+constexpr int kTileSpan = kTileGroups * 32;                     // words per tile
+constexpr int kItemWords = 8;
+constexpr int kTileItems = kTileSpan / kItemWords;              // 128
+
+// 16 occupancy bytes -> 16 bits (bit t = byte t != 0)
+__device__ __forceinline__ uint32_t bytes_nonzero16(uint4 v) {
+    const uint32_t x[4] = {v.x, v.y, v.z, v.w};
+    uint32_t r = 0;
 #pragma unroll
-    for (int q = 0; q < kWordsPerThread; ++q)
-        if (base + q < n_words) c += __popc(__ldg(bits + base + q));
-    uint32_t total;
-    block_exclusive_scan(c, &total);
-    if (threadIdx.x == 0) block_sums[blockIdx.x] = total;
+    for (int k = 0; k < 4; ++k) {
+        // 0x01 in every nonzero byte, then gather the four byte-LSBs into a
+        // nibble with one multiply (partial products land on distinct bits)
+        const uint32_t m = __vcmpne4(x[k], 0u) & 0x01010101u;
+        r |= ((m * 0x01020408u) >> 24) << (4 * k);
+    }
+    return r;
 }
 
-// one block: exclusive scan of the block sums (each thread a contiguous run);
-// d_n = min(total, cap)
-__global__ void __launch_bounds__(kThreads) k_scan_blocks(uint32_t* __restrict__ block_sums,
-                                                          int32_t n_blocks, int64_t cap,
-                                                          int64_t* __restrict__ d_total,
-                                                          int32_t* __restrict__ d_n,
-                                                          int32_t* __restrict__ status) {
-    const int32_t per = (n_blocks + kThreads - 1) / kThreads;
-    const int32_t beg = threadIdx.x * per;
-    const int32_t end = min(beg + per, n_blocks);
-    uint32_t s = 0;
-#pragma unroll 8
-    for (int32_t i = beg; i < end; ++i) s += block_sums[i];
+template <bool kFromBits>
+__global__ void __launch_bounds__(kThreads) k_tile_count(
+    const uint8_t* __restrict__ occ, uint32_t* __restrict__ bits, int64_t n_cells, int64_t n_words,
+    int64_t cap, uint32_t* __restrict__ item_pref, uint32_t* __restrict__ tile_count,
+    uint32_t* __restrict__ tile_offset, uint32_t* __restrict__ done, int32_t n_tiles,
+    int32_t* __restrict__ d_n, int64_t* __restrict__ d_total, int32_t* __restrict__ status) {
+    __shared__ bool s_last;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t g0 = (int64_t)blockIdx.x * kTileGroups + warp * kGroupsPerWarp;
+    uint32_t word[kGroupsPerWarp];
+    if (kFromBits) {
+#pragma unroll
+        for (int q = 0; q < kGroupsPerWarp; ++q) {
+            const int64_t w = (g0 + q) * 32 + lane;
+            word[q] = w < n_words ? __ldcg(bits + w) : 0u;
+        }
+    } else {
+        const bool vec = (reinterpret_cast<uintptr_t>(occ) & 15) == 0;
+        uint4 raw[2 * kGroupsPerWarp];
+#pragma unroll
+        for (int q = 0; q < 2 * kGroupsPerWarp; ++q) {  // all loads in flight first
+            const int64_t c = (g0 * 64 + q * 32 + lane) * 16;  // first cell of this lane's 16
+            raw[q] = make_uint4(0u, 0u, 0u, 0u);
+            if (vec && c + 16 <= n_cells) {
+                raw[q] = __ldcs(reinterpret_cast<const uint4*>(occ + c));
+            } else {
+                uint32_t b[4] = {0u, 0u, 0u, 0u};
+                for (int t = 0; t < 16 && c + t < n_cells; ++t)
+                    b[t >> 2] |= (uint32_t)occ[c + t] << (8 * (t & 3));
+                raw[q] = make_uint4(b[0], b[1], b[2], b[3]);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < kGroupsPerWarp; ++q) {
+            // half group 2q covers words 0..15 of group q, half 2q + 1 words 16..31;
+            // word m of a half = lanes 2m (low bits) and 2m + 1 (high bits)
+            const uint32_t h0 = bytes_nonzero16(raw[2 * q]);
+            const uint32_t h1 = bytes_nonzero16(raw[2 * q + 1]);
+            const int src = 2 * (lane & 15);
+            const uint32_t a0 = __shfl_sync(0xffffffffu, h0, src);
+            const uint32_t b0 = __shfl_sync(0xffffffffu, h0, src + 1);
+            const uint32_t a1 = __shfl_sync(0xffffffffu, h1, src);
+            const uint32_t b1 = __shfl_sync(0xffffffffu, h1, src + 1);
+            word[q] = lane < 16 ? (a0 | (b0 << 16)) : (a1 | (b1 << 16));
+            const int64_t w = (g0 + q) * 32 + lane;
+            if (w < n_words) bits[w] = word[q];
+        }
+    }
+    // item counts (8 lanes each) -> the warp's 16 item counts, in item order
+    uint32_t ic[kGroupsPerWarp], wsum = 0;
+#pragma unroll
+    for (int q = 0; q < kGroupsPerWarp; ++q) {
+        uint32_t v = __popc(word[q]);
+#pragma unroll
+        for (int o = 1; o < kItemWords; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        ic[q] = v;  // the count of item (lane / 8) of group q, on every lane of that item
+        wsum += __shfl_sync(0xffffffffu, v, 0) + __shfl_sync(0xffffffffu, v, 8) +
+                __shfl_sync(0xffffffffu, v, 16) + __shfl_sync(0xffffffffu, v, 24);
+    }
     uint32_t total;
-    uint32_t ex = block_exclusive_scan(s, &total);
+    const uint32_t wex = block_exclusive_scan(lane == 0 ? wsum : 0u, &total);
+    const uint32_t wbase = __shfl_sync(0xffffffffu, wex, 0);
+    // lane 8 j + 0 writes item j of group q; prefix = wbase + items before it
+    {
+        uint32_t run = wbase;
+#pragma unroll
+        for (int q = 0; q < kGroupsPerWarp; ++q) {
+            const uint32_t c0 = __shfl_sync(0xffffffffu, ic[q], 0);
+            const uint32_t c1 = __shfl_sync(0xffffffffu, ic[q], 8);
+            const uint32_t c2 = __shfl_sync(0xffffffffu, ic[q], 16);
+            const uint32_t c3 = __shfl_sync(0xffffffffu, ic[q], 24);
+            const int j = lane >> 3;
+            const uint32_t before = (j > 0 ? c0 : 0u) + (j > 1 ? c1 : 0u) + (j > 2 ? c2 : 0u);
+            if ((lane & 7) == 0) item_pref[(g0 + q) * (32 / kItemWords) + j] = run + before;
+            run += c0 + c1 + c2 + c3;
+        }
+    }
+    if (threadIdx.x == 0) {
+        tile_count[blockIdx.x] = total;
+        __threadfence();
+        s_last = atomicAdd(done, 1u) == (uint32_t)(n_tiles - 1);
+    }
+    __syncthreads();
+    if (!s_last) return;
+    // the last CTA: every tile count is visible (each was fenced before its ticket)
+    __threadfence();
+    const int32_t per = (n_tiles + kThreads - 1) / kThreads;
+    const int32_t beg = min(n_tiles, (int32_t)threadIdx.x * per), end = min(n_tiles, beg + per);
+    uint32_t run = 0;
+    for (int32_t i = beg; i < end; ++i) run += __ldcg(tile_count + i);
+    uint32_t all;
+    uint32_t ex = block_exclusive_scan(run, &all);
     for (int32_t i = beg; i < end; ++i) {
-        const uint32_t v = block_sums[i];
-        block_sums[i] = ex;
+        const uint32_t v = __ldcg(tile_count + i);
+        tile_offset[i] = ex;
         ex += v;
     }
     if (threadIdx.x == 0) {
-        *d_total = total;
-        const int64_t n = (int64_t)total < cap ? (int64_t)total : cap;
-        *d_n = (int32_t)n;
-        if ((int64_t)total > cap) atomicOr(status, kStatusCapacity);
+        *d_total = (int64_t)all;
+        *d_n = (int32_t)((int64_t)all < cap ? (int64_t)all : cap);
+        if ((int64_t)all > cap) atomicOr(status, kStatusCapacity);
+        *done = 0u;  // rearmed for the next launch
     }
 }
 
-// rank structure and active list: one word per thread for the ranks; the
-// active list is written warp-cooperatively (non-empty word after non-empty
-// word, one lane per bit), so that every store instruction writes
-// consecutive slots.  Entries are packed coordinates i | j << 10 | k << 20.
-__global__ void __launch_bounds__(kThreads) k_emit(const uint32_t* __restrict__ bits,
-                                                   int64_t n_words,
-                                                   const uint32_t* __restrict__ block_off,
-                                                   int64_t cap, FastDiv gdiv,
-                                                   uint32_t* __restrict__ word_prefix,
-                                                   uint32_t* __restrict__ active) {
-    const int64_t w = blockIdx.x * (int64_t)kThreads + threadIdx.x;
-    const uint32_t word = w < n_words ? __ldg(bits + w) : 0u;
-    const uint32_t off = block_off[blockIdx.x] + block_exclusive_scan(__popc(word), nullptr);
-    if (w < n_words) word_prefix[w] = off;
-    const int lane = threadIdx.x & 31;
+// packed coordinates i | j << 10 | k << 20 of linear cell lin
+__device__ __forceinline__ uint32_t pack_lin(uint32_t lin, const FastDiv& gdiv) {
+    const uint32_t r = fast_div(lin, gdiv);
+    const uint32_t k = fast_div(r, gdiv);
+    return (lin - r * gdiv.d) | ((r - k * gdiv.d) << 10) | (k << 20);
+}
+
+// seg_zero / seg_zero2 (nullable): seg bitfields whose words are cleared on
+// the way (the one-call step)
+__global__ void __launch_bounds__(kThreads) k_tile_emit(
+    const uint32_t* __restrict__ bits, int64_t n_words, int64_t cap, FastDiv gdiv,
+    const uint32_t* __restrict__ item_pref, const uint32_t* __restrict__ tile_offset,
+    uint32_t* __restrict__ active, uint32_t* __restrict__ seg_zero,
+    uint32_t* __restrict__ seg_zero2) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t lt = (1u << lane) - 1u;
-    const int64_t wbase = w - lane;  // word index of lane 0
-    for (uint32_t nz = __ballot_sync(0xffffffffu, word != 0u); nz; nz &= nz - 1u) {
-        const int i = __ffs(nz) - 1;
-        const uint32_t wi = __shfl_sync(0xffffffffu, word, i);
-        const uint32_t oi = __shfl_sync(0xffffffffu, off, i);
-        if ((wi >> lane) & 1u) {
-            const int64_t slot = (int64_t)oi + __popc(wi & lt);
-            if (slot < cap) {
-                const uint32_t lin = (uint32_t)((wbase + i) * 32 + lane);  // < 2^30
-                const uint32_t r = fast_div(lin, gdiv);
-                const uint32_t k = fast_div(r, gdiv);
-                active[slot] = (lin - r * gdiv.d) | ((r - k * gdiv.d) << 10) | (k << 20);
+    const int64_t n_groups = (n_words + 31) / 32;
+    const int64_t n_warps = (int64_t)gridDim.x * (kThreads / 32);
+    for (int64_t g = (int64_t)blockIdx.x * (kThreads / 32) + warp; g < n_groups; g += n_warps) {
+        const int64_t w = g * 32 + lane;
+        const uint32_t x = w < n_words ? __ldcg(bits + w) : 0u;
+        if (w < n_words) {
+            if (seg_zero) seg_zero[w] = 0u;
+            if (seg_zero2) seg_zero2[w] = 0u;
+        }
+        uint32_t nz = __ballot_sync(0xffffffffu, x != 0u);
+        if (nz == 0u) continue;  // warp-uniform
+        const int64_t base = (int64_t)__ldg(tile_offset + g / kTileGroups) +
+                             __ldg(item_pref + g * (32 / kItemWords));
+        const uint32_t c = __popc(x);
+        uint32_t inc = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
+        }
+        const uint32_t ex = inc - c;
+        const uint32_t p0 = pack_lin((uint32_t)(w * 32), gdiv);  // this lane's word, bit 0
+        const uint32_t max_c = __reduce_max_sync(0xffffffffu, c);
+        if (max_c <= (uint32_t)__popc(nz)) {
+            // scattered bits: every lane walks its own word (rounds = the largest popcount)
+            uint32_t xb = x;
+            int64_t slot = base + ex;
+            const bool row = (p0 & 1023u) + 31u < gdiv.d;  // the word stays on one row
+            while (xb) {
+                const uint32_t b = __ffs(xb) - 1;
+                xb &= xb - 1u;
+                if (slot < cap)
+                    active[slot] = row ? p0 + b : pack_lin((uint32_t)(w * 32) + b, gdiv);
+                ++slot;
+            }
+            continue;
+        }
+        // dense words: one round per non-empty word, in which lane b writes bit b
+        while (nz) {
+            const int src = __ffs(nz) - 1;
+            nz &= nz - 1u;
+            const uint32_t xs = __shfl_sync(0xffffffffu, x, src);
+            const uint32_t off = __shfl_sync(0xffffffffu, ex, src);
+            const uint32_t ps = __shfl_sync(0xffffffffu, p0, src);
+            if ((xs >> lane) & 1u) {
+                const int64_t slot = base + off + __popc(xs & lt);
+                if (slot < cap) {
+                    // same row as the word's bit 0 unless the row wraps inside the word
+                    active[slot] = (ps & 1023u) + lane < gdiv.d
+                                       ? ps + lane
+                                       : pack_lin((uint32_t)((g * 32 + src) * 32 + lane), gdiv);
+                }
             }
         }
     }
@@ -247,10 +358,6 @@ cudaError_t launch_fuse_chunks(int chunks, int blocks, cudaStream_t s, const uin
 // ---------------------------------------------------------------------------
 // finalize
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ float score_of(float w, float z, float eps) {
-    return z > eps ? __fdiv_rn(w, z) : 0.f;
-}
-
 // normalise + threshold, one thread per active voxel (the dense score grid and
 // the seg bitfields were zeroed by the caller): P = W / Z, seg = P >= tau_cons,
 // the score goes to its dense or active-list position, seg bits are OR-ed in
@@ -288,6 +395,84 @@ __global__ void __launch_bounds__(kThreads) k_finalize(
         if (d_nseg) {
             const uint32_t cnt = __popc(__ballot_sync(0xffffffffu, seg));
             if (lane == 0 && cnt) atomicAdd(d_nseg, (unsigned long long)cnt);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// the one-call step's fusion: fresh accumulators, every view of the step, and
+// the finalize epilogue in the same pass (P = W / Z, seg = P >= tau_cons, the
+// score to its dense or active-list position, warp-aggregated seg-bit ORs into
+// bitfields that k_tile_emit cleared), then the zeros of a dense score grid's
+// unoccupied cells.  Per voxel the arithmetic is that of k_fuse followed by
+// k_finalize.
+// ---------------------------------------------------------------------------
+template <bool kContracted, int kChunks>
+__global__ void __launch_bounds__(kThreads, kContracted ? 4 : 6) k_fuse_step(
+    const uint32_t* __restrict__ active, const int32_t* __restrict__ d_n, GridC G, FuseC F,
+    const __grid_constant__ ViewBatch VB, float* __restrict__ W, float* __restrict__ Z,
+    uint32_t* __restrict__ bits, int32_t dense, float* __restrict__ score_out,
+    uint32_t* __restrict__ seg_bits, uint32_t* __restrict__ seg_out,
+    const uint32_t* __restrict__ occ_bits, int64_t n_words, int64_t n_cells) {
+    const int lane = threadIdx.x & 31;
+    const int32_t gw = (int32_t)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int32_t nw = (int32_t)((gridDim.x * blockDim.x) >> 5);
+    const bool zero = dense && score_out;
+    const int64_t n_groups = (n_words + 31) / 32;
+    // occupancy word of the first group this warp zero-fills, fetched now and
+    // used after the fusion loop
+    uint32_t x_first = 0;
+    if (zero && gw < n_groups && (int64_t)gw * 32 + lane < n_words)
+        x_first = __ldg(occ_bits + (int64_t)gw * 32 + lane);
+    const int32_t n = *d_n;
+    for (int32_t base = gw * 32; base < n; base += nw * 32) {
+        const int32_t a = base + lane;
+        const bool live = a < n;
+        bool seg = false;
+        int64_t lin = 0;
+        if (live) {
+            const uint32_t pk = __ldg(active + a);
+            const VoxelGeom vg = voxel_geom<kContracted>(pk, G, F.gamma);
+            float w = 0.f, z = 0.f;
+            uint32_t b = 0;
+            if (vg.ok) fold_views<kContracted, kChunks>(VB, vg, F, w, z, b);
+            W[a] = w;
+            Z[a] = z;
+            bits[a] = b;
+            const float p = z > F.eps ? __fdiv_rn(w, z) : 0.f;
+            seg = p >= F.tau_cons;
+            lin = packed_lin(pk, G.g);
+            if (score_out) score_out[dense ? lin : (int64_t)a] = p;
+        }
+        const uint32_t word = live ? (uint32_t)(lin >> 5) : 0xffffffffu;
+        const uint32_t grp = __match_any_sync(0xffffffffu, word);
+        const uint32_t orv = __reduce_or_sync(grp, seg ? 1u << (lin & 31) : 0u);
+        if (live && lane == __ffs(grp) - 1 && orv) {
+            atomicOr(seg_bits + word, orv);
+            if (seg_out) atomicOr(seg_out + word, orv);
+        }
+    }
+    if (!zero) return;
+    // zeros of the unoccupied cells, one group of 32 words (1024 cells) per
+    // warp and round: coalesced 16-byte stores that need no result (the
+    // occupied cells got their P above, possibly from other warps)
+    const bool vec = (reinterpret_cast<uintptr_t>(score_out) & 15) == 0;
+    for (int64_t g = gw; g < n_groups; g += nw) {
+        const int64_t w = g * 32 + lane;
+        const uint32_t x = g == gw ? x_first : (w < n_words ? __ldg(occ_bits + w) : 0u);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int f4 = q * 32 + lane;  // float4 index inside the group
+            const uint32_t xw = __shfl_sync(0xffffffffu, x, f4 >> 3);
+            const uint32_t nib = (xw >> ((f4 & 7) * 4)) & 0xfu;
+            const int64_t cell = g * 1024 + 4 * f4;
+            if (nib == 0u && vec && cell + 4 <= n_cells) {
+                __stcs(reinterpret_cast<float4*>(score_out + cell), make_float4(0.f, 0.f, 0.f, 0.f));
+            } else {
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    if (!((nib >> k) & 1u) && cell + k < n_cells) score_out[cell + k] = 0.f;
+            }
         }
     }
 }
@@ -383,8 +568,38 @@ __device__ __forceinline__ uint8_t label_one(const float* __restrict__ xyz, int6
     return lab;
 }
 
+// label of one point of a plain grid whose edge h is a power of two (G.inv_h
+// != 0): s = fl(x - o) / h is exact scaling of the rounded difference, and
+// rounding to nearest never crosses the representable k h, so floor(s) is the
+// exact floor unless s is an integer -- only then is the rounding error of the
+// difference (two_sum) needed to decide (the compensated path of label_one)
+__device__ __forceinline__ uint8_t label_plain_pow2(float x, float y, float z, const GridC& G,
+                                                   const uint32_t* __restrict__ seg_bits) {
+    const float p[3] = {x, y, z};
+    uint32_t idx[3];
+    bool inside = true;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        const float dh = __fsub_rn(p[q], G.origin[q]);
+        const float sh = __fmul_rn(dh, G.inv_h);
+        float f = floorf(sh);
+        if (f == sh) {  // on a cell boundary: the sign of the rounding error decides
+            float h2, l2;
+            two_sum(p[q], -G.origin[q], h2, l2);
+            if (l2 < 0.f) f = __fsub_rn(f, 1.f);
+        }
+        inside = inside && f >= 0.f && f < (float)G.g;  // false for NaN
+        idx[q] = inside ? (uint32_t)f : 0u;
+    }
+    if (!inside) return 0;
+    const uint32_t g = (uint32_t)G.g;
+    const uint32_t lin = (idx[2] * g + idx[1]) * g + idx[0];  // < 2^30
+    return (uint8_t)((__ldg(seg_bits + (lin >> 5)) >> (lin & 31)) & 1u);
+}
+
 // four points per thread: their 48 bytes come in three 128-bit loads (when the
 // array is 16-byte aligned) so that every thread has all its loads in flight
+template <bool kPlainPow2>
 __global__ void __launch_bounds__(kThreads) k_label(const float* __restrict__ xyz, int64_t n,
                                                     GridC G, const uint32_t* __restrict__ seg_bits,
                                                     uint8_t* __restrict__ labels) {
@@ -400,11 +615,19 @@ __global__ void __launch_bounds__(kThreads) k_label(const float* __restrict__ xy
                                    f1.z, f1.w, f2.x, f2.y, f2.z, f2.w};
             uint32_t packed = 0;
 #pragma unroll
-            for (int k = 0; k < 4; ++k)
-                packed |= (uint32_t)label_one(pts + 3 * k, 0, G, seg_bits) << (8 * k);
+            for (int k = 0; k < 4; ++k) {
+                const uint8_t lab =
+                    kPlainPow2 ? label_plain_pow2(pts[3 * k], pts[3 * k + 1], pts[3 * k + 2], G,
+                                                  seg_bits)
+                               : label_one(pts + 3 * k, 0, G, seg_bits);
+                packed |= (uint32_t)lab << (8 * k);
+            }
             *reinterpret_cast<uint32_t*>(labels + a) = packed;
         } else {
-            for (int64_t b = a; b < a + 4 && b < n; ++b) labels[b] = label_one(xyz, b, G, seg_bits);
+            for (int64_t b = a; b < a + 4 && b < n; ++b)
+                labels[b] = kPlainPow2 ? label_plain_pow2(xyz[3 * b], xyz[3 * b + 1],
+                                                          xyz[3 * b + 2], G, seg_bits)
+                                       : label_one(xyz, b, G, seg_bits);
         }
     }
 }
@@ -509,21 +732,19 @@ struct divas_ctx {
     GridC G;
     FuseC F;
     int64_t n_cells = 0, n_words = 0;
-    int32_t n_cblocks = 0;  // compaction blocks
     int64_t cap = 0;
     int64_t n_active = 0;
     int32_t n_views = 0;
     int32_t sm_count = 148;
     uint32_t* occ_bits = nullptr;
-    uint32_t* word_prefix = nullptr;
-    uint32_t* block_sums = nullptr;
+    uint32_t* item_pref = nullptr;    // compaction: item offsets inside their tile
+    uint32_t* tile_count = nullptr;   // compaction: active voxels per tile of 1024 words
+    uint32_t* tile_offset = nullptr;  // exclusive prefix of tile_count
+    uint32_t* done = nullptr;         // k_tile_count's done counter (rearmed by its last CTA)
+    int32_t n_tiles = 0;
     uint32_t* seg_bits = nullptr;
     uint32_t* active = nullptr;
     FastDiv gdiv;  // division by g
-    // divas_fuse_step: a helper stream zero-fills the outputs while the main
-    // stream compacts and fuses (fork / join through two events)
-    cudaStream_t helper = nullptr;
-    cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
     float* W = nullptr;
     float* Z = nullptr;
     uint32_t* bits = nullptr;
@@ -658,13 +879,37 @@ float logit_threshold(float tau) {
     return (float)log((double)tau / (1.0 - (double)tau));
 }
 
-// occupancy -> bits -> rank structure -> active list (no allocation)
-divas_status build_active(divas_ctx* c, const uint8_t* occ, const int32_t* coords, int64_t n_coords,
-                          cudaStream_t s) {
+// launch k_fuse_step with the chunk count as a compile-time constant
+template <bool kContracted, int kChunks = 1>
+cudaError_t launch_fuse_step_chunks(int chunks, int blocks, cudaStream_t s, const divas_ctx* c,
+                                    const ViewBatch& vb, float* score_out, uint32_t* seg_out) {
+    if constexpr (kChunks < kMaxViews / kViewChunk) {
+        if (chunks > kChunks)
+            return launch_fuse_step_chunks<kContracted, kChunks + 1>(chunks, blocks, s, c, vb,
+                                                                     score_out, seg_out);
+    }
+    k_fuse_step<kContracted, kChunks><<<blocks, kThreads, 0, s>>>(
+        c->active, c->d_n, c->G, c->F, vb, c->W, c->Z, c->bits, c->grid.kind == 0 ? 1 : 0,
+        score_out, c->seg_bits, seg_out, c->occ_bits, c->n_words, c->n_cells);
+    return cudaGetLastError();
+}
+
+// k_tile_emit grid: one group per warp, at most 16 CTAs per SM
+int emit_blocks(int64_t n_words, int32_t sm_count) {
+    const int64_t groups = (n_words + 31) / 32;
+    const int64_t want = (groups + kThreads / 32 - 1) / (kThreads / 32);
+    return (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sm_count * 16));
+}
+
+// occupancy -> bits -> tile counts -> active list (no allocation); seg_zero /
+// seg_zero2 (nullable) are seg bitfields to clear on the way
+divas_status build_counts(divas_ctx* c, const uint8_t* occ, const int32_t* coords,
+                          int64_t n_coords, cudaStream_t s) {
     if (c->grid.kind == 0) {
-        k_occ_bits<<<c->n_cblocks, kThreads, 0, s>>>(occ, c->n_cells, c->n_words, c->occ_bits,
-                                                     c->block_sums);
-        DIVAS_LAUNCHED(c, "k_occ_bits");
+        k_tile_count<false><<<c->n_tiles, kThreads, 0, s>>>(
+            occ, c->occ_bits, c->n_cells, c->n_words, c->cap, c->item_pref, c->tile_count,
+            c->tile_offset, c->done, c->n_tiles, c->d_n, c->d_total, c->d_status);
+        DIVAS_LAUNCHED(c, "k_tile_count");
     } else {
         DIVAS_CUDA(c, cudaMemsetAsync(c->occ_bits, 0, c->n_words * 4, s));
         if (n_coords > 0) {
@@ -672,19 +917,25 @@ divas_status build_active(divas_ctx* c, const uint8_t* occ, const int32_t* coord
                 coords, n_coords, c->grid.g, c->occ_bits, c->d_status);
             DIVAS_LAUNCHED(c, "k_scatter_coords");
         }
-        k_block_popc<<<c->n_cblocks, kThreads, 0, s>>>(c->occ_bits, c->n_words, c->block_sums);
-        DIVAS_LAUNCHED(c, "k_block_popc");
+        k_tile_count<true><<<c->n_tiles, kThreads, 0, s>>>(
+            nullptr, c->occ_bits, c->n_cells, c->n_words, c->cap, c->item_pref, c->tile_count,
+            c->tile_offset, c->done, c->n_tiles, c->d_n, c->d_total, c->d_status);
+        DIVAS_LAUNCHED(c, "k_tile_count");
     }
-    k_scan_blocks<<<1, kThreads, 0, s>>>(c->block_sums, c->n_cblocks, c->cap, c->d_total, c->d_n,
-                                         c->d_status);
-    DIVAS_LAUNCHED(c, "k_scan_blocks");
     return DIVAS_OK;
 }
 
-divas_status emit_active(divas_ctx* c, cudaStream_t s) {
-    k_emit<<<c->n_cblocks, kThreads, 0, s>>>(c->occ_bits, c->n_words, c->block_sums, c->cap,
-                                             c->gdiv, c->word_prefix, c->active);
-    DIVAS_LAUNCHED(c, "k_emit");
+// the full compaction: counts, then (when the active arrays exist) the list;
+// seg_zero / seg_zero2 (nullable) are seg bitfields to clear on the way
+divas_status build_active(divas_ctx* c, const uint8_t* occ, const int32_t* coords, int64_t n_coords,
+                          cudaStream_t s, uint32_t* seg_zero = nullptr,
+                          uint32_t* seg_zero2 = nullptr) {
+    divas_status st = build_counts(c, occ, coords, n_coords, s);
+    if (st != DIVAS_OK || !c->active) return st;
+    k_tile_emit<<<emit_blocks(c->n_words, c->sm_count), kThreads, 0, s>>>(
+        c->occ_bits, c->n_words, c->cap, c->gdiv, c->item_pref, c->tile_offset, c->active,
+        seg_zero, seg_zero2);
+    DIVAS_LAUNCHED(c, "k_tile_emit");
     return DIVAS_OK;
 }
 
@@ -706,11 +957,9 @@ divas_status read_status(divas_ctx* c, cudaStream_t s) {
 }
 
 void free_all(divas_ctx* c) {
-    if (c->helper) cudaStreamDestroy(c->helper);
-    if (c->fork_ev) cudaEventDestroy(c->fork_ev);
-    if (c->join_ev) cudaEventDestroy(c->join_ev);
-    void* ptrs[] = {c->occ_bits, c->word_prefix, c->block_sums, c->seg_bits, c->active, c->W,
-                    c->Z,        c->bits,        c->d_n,        c->d_status, c->d_total, c->d_nseg};
+    void* ptrs[] = {c->occ_bits, c->item_pref, c->tile_count, c->tile_offset, c->done,
+                    c->seg_bits, c->active,     c->W,          c->Z,           c->bits,
+                    c->d_n,      c->d_status,   c->d_total,    c->d_nseg};
     for (void* p : ptrs)
         if (p) cudaFree(p);
 }
@@ -789,7 +1038,7 @@ divas_status divas_fuse_init(divas_ctx** out, const divas_grid* grid, const uint
     }
     c->n_cells = (int64_t)grid->g * grid->g * grid->g;
     c->n_words = (c->n_cells + 31) / 32;
-    c->n_cblocks = (int32_t)((c->n_words + kWordsPerBlock - 1) / kWordsPerBlock);
+    c->n_tiles = (int32_t)((c->n_words + kTileSpan - 1) / kTileSpan);
     cudaStream_t s = S(stream);
     int dev = 0;
     divas_status st = DIVAS_OK;
@@ -806,13 +1055,13 @@ divas_status divas_fuse_init(divas_ctx** out, const divas_grid* grid, const uint
     } while (0)
     INIT_CUDA(cudaGetDevice(&dev));
     INIT_CUDA(cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, dev));
-    INIT_CUDA(cudaStreamCreateWithFlags(&c->helper, cudaStreamNonBlocking));
-    INIT_CUDA(cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming));
-    INIT_CUDA(cudaEventCreateWithFlags(&c->join_ev, cudaEventDisableTiming));
     INIT_CUDA(cudaMalloc(&c->occ_bits, c->n_words * 4));
-    INIT_CUDA(cudaMalloc(&c->word_prefix, c->n_words * 4));
+    INIT_CUDA(cudaMalloc(&c->item_pref, (size_t)c->n_tiles * kTileItems * 4));
+    INIT_CUDA(cudaMalloc(&c->tile_count, (size_t)c->n_tiles * 4));
+    INIT_CUDA(cudaMalloc(&c->tile_offset, (size_t)c->n_tiles * 4));
+    INIT_CUDA(cudaMalloc(&c->done, 4));
+    INIT_CUDA(cudaMemsetAsync(c->done, 0, 4, s));
     INIT_CUDA(cudaMalloc(&c->seg_bits, c->n_words * 4));
-    INIT_CUDA(cudaMalloc(&c->block_sums, ((int64_t)c->n_cblocks + 1) * 4));
     INIT_CUDA(cudaMalloc(&c->d_n, 4));
     INIT_CUDA(cudaMalloc(&c->d_status, 4));
     INIT_CUDA(cudaMalloc(&c->d_total, 8));
@@ -841,7 +1090,7 @@ divas_status divas_fuse_init(divas_ctx** out, const divas_grid* grid, const uint
     INIT_CUDA(cudaMalloc(&c->W, c->cap * 4));
     INIT_CUDA(cudaMalloc(&c->Z, c->cap * 4));
     INIT_CUDA(cudaMalloc(&c->bits, c->cap * 4));
-    st = emit_active(c, s);
+    st = build_active(c, occ_dense, coords, n_coords, s);
     if (st != DIVAS_OK) return bail(st);
     INIT_CUDA(cudaMemsetAsync(c->W, 0, c->cap * 4, s));
     INIT_CUDA(cudaMemsetAsync(c->Z, 0, c->cap * 4, s));
@@ -861,10 +1110,37 @@ divas_status divas_fuse_set_occupancy(divas_ctx* c, const uint8_t* occ_dense, co
     cudaStream_t s = S(stream);
     divas_status st = build_active(c, occ_dense, coords, n_coords, s);
     if (st != DIVAS_OK) return st;
-    st = emit_active(c, s);
-    if (st != DIVAS_OK) return st;
     c->n_views = 0;
     c->n_active = c->cap;  // upper bound until the next synchronising call
+    return DIVAS_OK;
+}
+
+// record stage event k (when given) on s; inside a stream capture it becomes
+// an event-record node, so that graph replays time the stages
+static divas_status record_stage(divas_ctx* c, void* const* events, int k, cudaStream_t s) {
+    if (!events || !events[k]) return DIVAS_OK;
+    cudaEvent_t ev = static_cast<cudaEvent_t>(events[k]);
+    DIVAS_CUDA(c, capturing(s) ? cudaEventRecordWithFlags(ev, s, cudaEventRecordExternal)
+                               : cudaEventRecord(ev, s));
+    return DIVAS_OK;
+}
+
+// validate views and build their constants (view bits continue the context's count)
+static divas_status make_batch(divas_ctx* c, const divas_view* views, int32_t n_views,
+                               int32_t first_view, ViewBatch& vb) {
+    if (!views || n_views < 1 || n_views > kMaxViews)
+        return fail(c, DIVAS_E_INVALID, "n_views must be in 1..32 and views non-NULL");
+    memset(&vb, 0, sizeof(vb));
+    vb.n = n_views;
+    for (int32_t k = 0; k < n_views; ++k) {
+        divas_status st = check_camera(c, &views[k].cam);
+        if (st != DIVAS_OK) return st;
+        if (!views[k].depth || !views[k].mask) return fail(c, DIVAS_E_INVALID, "depth or mask is NULL");
+        if (views[k].mask_type < 0 || views[k].mask_type > 2)
+            return fail(c, DIVAS_E_INVALID, "bad mask_type");
+        vb.v[k] = make_view(views[k].cam, c->G, views[k].depth, views[k].mask,
+                            views[k].mask_type, first_view + k);
+    }
     return DIVAS_OK;
 }
 
@@ -906,20 +1182,9 @@ divas_status divas_fuse_add_view(divas_ctx* c, const divas_camera* cam, const fl
 divas_status divas_fuse_add_views(divas_ctx* c, const divas_view* views, int32_t n_views,
                                   void* stream) {
     if (!c) return fail(nullptr, DIVAS_E_INVALID, "ctx is NULL");
-    if (!views || n_views < 1 || n_views > kMaxViews)
-        return fail(c, DIVAS_E_INVALID, "n_views must be in 1..32 and views non-NULL");
     ViewBatch vb;
-    memset(&vb, 0, sizeof(vb));
-    vb.n = n_views;
-    for (int32_t k = 0; k < n_views; ++k) {
-        divas_status st = check_camera(c, &views[k].cam);
-        if (st != DIVAS_OK) return st;
-        if (!views[k].depth || !views[k].mask) return fail(c, DIVAS_E_INVALID, "depth or mask is NULL");
-        if (views[k].mask_type < 0 || views[k].mask_type > 2)
-            return fail(c, DIVAS_E_INVALID, "bad mask_type");
-        vb.v[k] = make_view(views[k].cam, c->G, views[k].depth, views[k].mask,
-                            views[k].mask_type, c->n_views + k);
-    }
+    divas_status st = make_batch(c, views, n_views, c->n_views, vb);
+    if (st != DIVAS_OK) return st;
     return launch_fuse(c, vb, S(stream));
 }
 
@@ -975,29 +1240,53 @@ divas_status divas_fuse_step(divas_ctx* c, const uint8_t* occ_dense, const int32
                              int64_t n_coords, const divas_view* views, int32_t n_views,
                              float* score_out, uint32_t* seg_bits_out, const float* xyz, int64_t n_pts,
                              uint8_t* labels_out, void* stream) {
+    return divas_fuse_step_profiled(c, occ_dense, coords, n_coords, views, n_views, score_out,
+                                    seg_bits_out, xyz, n_pts, labels_out, nullptr, stream);
+}
+
+divas_status divas_fuse_step_profiled(divas_ctx* c, const uint8_t* occ_dense,
+                                      const int32_t* coords, int64_t n_coords,
+                                      const divas_view* views, int32_t n_views, float* score_out,
+                                      uint32_t* seg_bits_out, const float* xyz, int64_t n_pts,
+                                      uint8_t* labels_out, void* const* stage_events,
+                                      void* stream) {
     if (!c) return fail(nullptr, DIVAS_E_INVALID, "ctx is NULL");
-    if (!views || n_views < 1 || n_views > kMaxViews)
-        return fail(c, DIVAS_E_INVALID, "n_views must be in 1..32 and views non-NULL");
+    if (c->grid.kind == 0 && (!occ_dense || coords))
+        return fail(c, DIVAS_E_INVALID, "dense context needs occ_dense only");
+    if (c->grid.kind == 1 && (occ_dense || n_coords < 0 || (n_coords > 0 && !coords)))
+        return fail(c, DIVAS_E_INVALID, "sparse context needs coords only");
     if (n_pts < 0 || (n_pts > 0 && (!xyz || !labels_out)))
         return fail(c, DIVAS_E_INVALID, "bad point arguments");
+    ViewBatch vb;
+    divas_status st = make_batch(c, views, n_views, 0, vb);
+    if (st != DIVAS_OK) return st;
     cudaStream_t s = S(stream);
-    // fork: the helper stream zero-fills the outputs in parallel
-    DIVAS_CUDA(c, cudaEventRecord(c->fork_ev, s));
-    DIVAS_CUDA(c, cudaStreamWaitEvent(c->helper, c->fork_ev, 0));
-    divas_status st = finalize_zero(c, score_out, seg_bits_out, c->helper);
+    st = record_stage(c, stage_events, 0, s);
     if (st != DIVAS_OK) return st;
-    DIVAS_CUDA(c, cudaEventRecord(c->join_ev, c->helper));
-    // main: occupancy gate + active list, then the views
-    st = divas_fuse_set_occupancy(c, occ_dense, coords, n_coords, stream);
+    // occupancy gate + active list; the seg bitfields are cleared on the way
+    st = build_active(c, occ_dense, coords, n_coords, s, c->seg_bits, seg_bits_out);
     if (st != DIVAS_OK) return st;
-    st = divas_fuse_add_views(c, views, n_views, stream);
+    st = record_stage(c, stage_events, 1, s);
     if (st != DIVAS_OK) return st;
-    // join, then normalise + threshold and label
-    DIVAS_CUDA(c, cudaStreamWaitEvent(s, c->join_ev, 0));
-    st = finalize_scatter(c, score_out, seg_bits_out, nullptr, nullptr, s);
+    c->n_views = 0;
+    c->n_active = c->cap;  // upper bound until the next synchronising call
+    // fusion of every view + finalize epilogue
+    const int chunks = (vb.n + kViewChunk - 1) / kViewChunk;
+    const int blocks = grid_for(std::max<int64_t>(c->cap, c->n_words), c->sm_count);
+    cudaError_t e = c->G.contracted
+                        ? launch_fuse_step_chunks<true>(chunks, blocks, s, c, vb, score_out,
+                                                        seg_bits_out)
+                        : launch_fuse_step_chunks<false>(chunks, blocks, s, c, vb, score_out,
+                                                         seg_bits_out);
+    if (e != cudaSuccess) return cuda_fail(c, e, "k_fuse_step");
+    c->n_views = vb.n;
+    st = record_stage(c, stage_events, 2, s);
     if (st != DIVAS_OK) return st;
-    if (n_pts > 0) return divas_label_points(c, xyz, n_pts, labels_out, stream);
-    return DIVAS_OK;
+    if (n_pts > 0) {
+        st = divas_label_points(c, xyz, n_pts, labels_out, stream);
+        if (st != DIVAS_OK) return st;
+    }
+    return record_stage(c, stage_events, 3, s);
 }
 
 divas_status divas_label_points(divas_ctx* c, const float* xyz, int64_t n, uint8_t* labels_out,
@@ -1006,8 +1295,11 @@ divas_status divas_label_points(divas_ctx* c, const float* xyz, int64_t n, uint8
     if (n < 0 || (n > 0 && (!xyz || !labels_out)))
         return fail(c, DIVAS_E_INVALID, "bad point arguments");
     if (n == 0) return DIVAS_OK;
-    k_label<<<grid_for((n + 3) / 4, c->sm_count, 64), kThreads, 0, S(stream)>>>(
-        xyz, n, c->G, c->seg_bits, labels_out);
+    const int blocks = grid_for((n + 3) / 4, c->sm_count, 64);
+    if (!c->G.contracted && c->G.inv_h != 0.f)
+        k_label<true><<<blocks, kThreads, 0, S(stream)>>>(xyz, n, c->G, c->seg_bits, labels_out);
+    else
+        k_label<false><<<blocks, kThreads, 0, S(stream)>>>(xyz, n, c->G, c->seg_bits, labels_out);
     DIVAS_LAUNCHED(c, "k_label");
     return DIVAS_OK;
 }
@@ -1615,14 +1907,16 @@ namespace {
 
 constexpr int64_t kNoAllocMaxCells = 1 << 18;  // 64^3
 constexpr int64_t kNoAllocWords = kNoAllocMaxCells / 32;
-constexpr int64_t kNoAllocBlocks = (kNoAllocWords + kWordsPerBlock - 1) / kWordsPerBlock;
+constexpr int64_t kNoAllocTiles = (kNoAllocWords + kTileSpan - 1) / kTileSpan;
 
 constexpr int64_t na_align(int64_t x) { return (x + 255) / 256 * 256; }
 constexpr int64_t kNaOccBits = 0;
-constexpr int64_t kNaPrefix = kNaOccBits + na_align(kNoAllocWords * 4);
-constexpr int64_t kNaSeg = kNaPrefix + na_align(kNoAllocWords * 4);
-constexpr int64_t kNaBlocks = kNaSeg + na_align(kNoAllocWords * 4);
-constexpr int64_t kNaActive = kNaBlocks + na_align((kNoAllocBlocks + 1) * 4);
+constexpr int64_t kNaSeg = kNaOccBits + na_align(kNoAllocWords * 4);
+constexpr int64_t kNaItemPref = kNaSeg + na_align(kNoAllocWords * 4);
+constexpr int64_t kNaTileCount = kNaItemPref + na_align(kNoAllocTiles * kTileItems * 4);
+constexpr int64_t kNaTileOffset = kNaTileCount + na_align(kNoAllocTiles * 4);
+constexpr int64_t kNaDone = kNaTileOffset + na_align(kNoAllocTiles * 4);
+constexpr int64_t kNaActive = kNaDone + 256;
 constexpr int64_t kNaW = kNaActive + na_align(kNoAllocMaxCells * 4);
 constexpr int64_t kNaZ = kNaW + na_align(kNoAllocMaxCells * 4);
 constexpr int64_t kNaBits = kNaZ + na_align(kNoAllocMaxCells * 4);
@@ -1684,9 +1978,11 @@ extern "C" divas_status divas_fuse_dense_noalloc(const divas_grid* grid, const u
         base = static_cast<unsigned char*>(g_noalloc_dev_ptr[dev]);
     }
     uint32_t* occ_bits = reinterpret_cast<uint32_t*>(base + kNaOccBits);
-    uint32_t* word_prefix = reinterpret_cast<uint32_t*>(base + kNaPrefix);
     uint32_t* seg_bits = reinterpret_cast<uint32_t*>(base + kNaSeg);
-    uint32_t* block_sums = reinterpret_cast<uint32_t*>(base + kNaBlocks);
+    uint32_t* item_pref = reinterpret_cast<uint32_t*>(base + kNaItemPref);
+    uint32_t* tile_count = reinterpret_cast<uint32_t*>(base + kNaTileCount);
+    uint32_t* tile_offset = reinterpret_cast<uint32_t*>(base + kNaTileOffset);
+    uint32_t* done = reinterpret_cast<uint32_t*>(base + kNaDone);
     uint32_t* active = reinterpret_cast<uint32_t*>(base + kNaActive);
     float* W = reinterpret_cast<float*>(base + kNaW);
     float* Z = reinterpret_cast<float*>(base + kNaZ);
@@ -1738,7 +2034,7 @@ extern "C" divas_status divas_fuse_dense_noalloc(const divas_grid* grid, const u
     }
     const int64_t n_cells = (int64_t)grid->g * grid->g * grid->g;
     const int64_t n_words = (n_cells + 31) / 32;
-    const int32_t n_blocks = (int32_t)((n_words + kWordsPerBlock - 1) / kWordsPerBlock);
+    const int32_t n_tiles = (int32_t)((n_words + kTileSpan - 1) / kTileSpan);
     const int64_t cap = kNoAllocMaxCells;
     int sm_count = 148;
     cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, dev);
@@ -1750,18 +2046,19 @@ extern "C" divas_status divas_fuse_dense_noalloc(const divas_grid* grid, const u
     } while (0)
     // state that must start at zero on every call
     e = cudaMemsetAsync(d_status, 0, 4, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(done, 0, 4, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(seg_bits, 0, n_words * 4, s);
     if (e == cudaSuccess && score_out) e = cudaMemsetAsync(score_out, 0, n_cells * 4, s);
     if (e == cudaSuccess && seg_bits_out) e = cudaMemsetAsync(seg_bits_out, 0, n_words * 4, s);
     if (e != cudaSuccess)
         return noalloc_fail(DIVAS_E_CUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
-    k_occ_bits<<<n_blocks, kThreads, 0, s>>>(occ_dense, n_cells, n_words, occ_bits, block_sums);
-    NA_CHECK("k_occ_bits");
-    k_scan_blocks<<<1, kThreads, 0, s>>>(block_sums, n_blocks, cap, d_total, d_n, d_status);
-    NA_CHECK("k_scan_blocks");
-    k_emit<<<n_blocks, kThreads, 0, s>>>(occ_bits, n_words, block_sums, cap, gdiv, word_prefix,
-                                         active);
-    NA_CHECK("k_emit");
+    k_tile_count<false><<<n_tiles, kThreads, 0, s>>>(occ_dense, occ_bits, n_cells, n_words, cap,
+                                                     item_pref, tile_count, tile_offset, done,
+                                                     n_tiles, d_n, d_total, d_status);
+    NA_CHECK("k_tile_count");
+    k_tile_emit<<<emit_blocks(n_words, sm_count), kThreads, 0, s>>>(
+        occ_bits, n_words, cap, gdiv, item_pref, tile_offset, active, nullptr, nullptr);
+    NA_CHECK("k_tile_emit");
     const int blocks = grid_for(n_cells, sm_count);
     e = launch_fuse_chunks<false, false>((n_views + kViewChunk - 1) / kViewChunk, blocks, s,
                                          active, d_n, G, F, vb, W, Z, bits);

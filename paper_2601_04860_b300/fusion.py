@@ -237,17 +237,28 @@ class VoxelFusion:
         return {k: v for k, v in out.items() if v is not None}
 
     def step(self, views: "PreparedViews", occ=None, coords=None, score=None, seg_bits=None,
-             xyz=None, labels=None, stream=None):
+             xyz=None, labels=None, stage_events=None, stream=None):
         """The whole hot path in one call (occupancy gate, views, finalize,
-        labels), with the output zero-fill overlapped on a helper stream."""
+        labels) in four launches.  ``stage_events``: optional four
+        ``torch.cuda.Event`` (timing enabled, already recorded once) marking
+        before compaction / after compaction / after fusion / after labels."""
         if len(views.chunks) != 1:
             raise ValueError("step() takes up to 32 views")
         arr, n = views.chunks[0]
         n_c = 0 if coords is None else coords.shape[0]
         n_p = 0 if xyz is None else xyz.shape[0]
-        self._check(self.lib.divas_fuse_step(self._h, _ptr(occ), _ptr(coords), n_c, arr, n,
-                                             _ptr(score), _ptr(seg_bits), _ptr(xyz), n_p,
-                                             _ptr(labels), _stream(stream)))
+        if stage_events is None:
+            self._check(self.lib.divas_fuse_step(self._h, _ptr(occ), _ptr(coords), n_c, arr, n,
+                                                 _ptr(score), _ptr(seg_bits), _ptr(xyz), n_p,
+                                                 _ptr(labels), _stream(stream)))
+            return
+        if len(stage_events) != 4:
+            raise ValueError("stage_events takes four events")
+        evs = (ctypes.c_void_p * 4)(*[(e.cuda_event if e is not None else None)
+                                      for e in stage_events])
+        self._check(self.lib.divas_fuse_step_profiled(self._h, _ptr(occ), _ptr(coords), n_c, arr,
+                                                      n, _ptr(score), _ptr(seg_bits), _ptr(xyz),
+                                                      n_p, _ptr(labels), evs, _stream(stream)))
 
     def label_points(self, xyz: torch.Tensor, out: torch.Tensor | None = None,
                      stream=None) -> torch.Tensor:

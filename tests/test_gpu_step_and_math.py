@@ -58,3 +58,4 @@ def test_step_equals_separate_calls(which):
         assert np.array_equal(seg_bits_to_bool(seg, fu.n_cells).cpu().numpy(), ref["seg_dense"])
         assert np.array_equal(lab.cpu().numpy(), ref["labels"])
     fu.close()
+
