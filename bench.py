@@ -58,8 +58,10 @@ def _env_int(k, d):
 # (dram__bytes_read.sum + dram__bytes_write.sum), valid only while the kernel
 # sources are byte-identical to the ones profiled.
 TRAFFIC_CAPTURE = {
-    "source_sha1": "3a586c78b79ca8b35639df589cb26006a319e9b6",
-    "forward-dense-256": {"fuse": 24_658_688},
+    "source_sha1": "c3490904e45c53734c0d84f9f51edfcef6ff8a39",
+    "forward-dense-256": {"k_fuse_step": 28_072_448 + 21_315_840,
+                          "k_tile_count": 16_799_744, "k_tile_emit": 2_296_832,
+                          "k_label": 13_339_904},
 }
 
 
@@ -303,16 +305,25 @@ def run_ours(args, rank, world, local_rank):
         torch.cuda.current_stream().wait_stream(side)
         torch.cuda.synchronize()
         fev = [torch.cuda.Event(enable_timing=True, external=True) for _ in range(4)]
-        for e in fev:
+        sev = [torch.cuda.Event(enable_timing=True, external=True) for _ in range(4)]
+        for e in fev + sev:
             e.record()  # creates the events (torch creates them on first record)
         torch.cuda.synchronize()
+        # the timed graph has events around the step only; a second graph of the
+        # same step also marks the stage boundaries
         fast = torch.cuda.CUDAGraph()
         with torch.cuda.graph(fast):
             fu.step(pv_all, occ=occ, coords=coords, score=score, xyz=pts, labels=labels,
-                    stage_events=fev)
+                    stage_events=[fev[0], None, None, fev[3]])
+        staged = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(staged):
+            fu.step(pv_all, occ=occ, coords=coords, score=score, xyz=pts, labels=labels,
+                    stage_events=sev)
         for _ in range(args.warmup):
             flush.zero_()
             fast.replay()
+            flush.zero_()
+            staged.replay()
         torch.cuda.synchronize()
 
     clocks = Clocks(local_rank)
@@ -329,8 +340,11 @@ def run_ours(args, rank, world, local_rank):
             fast.replay()
             torch.cuda.synchronize()
             step_ms.append(fev[0].elapsed_time(fev[3]))
+            flush.zero_()
+            staged.replay()
+            torch.cuda.synchronize()
             for i, name in enumerate(step_phases):
-                sphase[name].append(fev[i].elapsed_time(fev[i + 1]))
+                sphase[name].append(sev[i].elapsed_time(sev[i + 1]))
             flush.zero_()
         graph.replay()
         torch.cuda.synchronize()
@@ -457,7 +471,7 @@ def run_ours(args, rank, world, local_rank):
     if fast is not None:  # the dominant single-kernel stage of the timed step
         spm = {k: float(np.mean(v)) for k, v in sphase.items()}
         cand = {k: (spm[k], algo[k]) for k in step_phases if step_kernels[k] == 1}
-        launches = sum(step_kernels.values()) + sum(kernels_per_phase.values())
+        launches = 2 * sum(step_kernels.values()) + sum(kernels_per_phase.values())
     else:
         spm = None
         cand = {k: (pm[k], algo[k]) for k in phases if kernels_per_phase[k] == 1}
@@ -476,7 +490,9 @@ def run_ours(args, rank, world, local_rank):
                    "voxels_nominal": int(N), "points": int(len(wl.points)),
                    "l2": "flushed between timed steps (256 MB write, outside the timed events)",
                    "launch": "one CUDA graph replay of divas_fuse_step per step (device time "
-                             "from in-graph events); phases from a graph of the separate calls",
+                             "from in-graph events around it); stage times from a second graph "
+                             "of the same step with events between its launches; "
+                             "separate_calls_* from a graph of the separate API calls",
                    "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "hbm", "kernel": KERNEL_OF[dom], "achieved": achieved,
                      "peak": peak,
@@ -663,6 +679,37 @@ def measure_sessions(dev, scale: float, n_sessions: int, rates, budget_frac: flo
     return out
 
 
+def profile_steps(args):
+    """Profiling target: init (3 launches: count, count, emit) then N eager
+    one-call steps (4 launches each: k_tile_count, k_tile_emit, k_fuse_step,
+    k_label on a dense workload) and nothing else."""
+    import torch
+
+    from paper_2601_04860_b300 import FusionParams, PreparedViews, VoxelFusion
+
+    dev = torch.device("cuda")
+    wl = make_workload(args.workload)
+    occ = None if wl.occ is None else torch.from_numpy(wl.occ).to(dev)
+    coords = None if wl.coords is None else torch.from_numpy(wl.coords).to(dev)
+    depth = [torch.from_numpy(d).to(dev) for d in wl.depth]
+    mask = [torch.from_numpy(m.view(np.float16) if wl.mask_type == 1 else m).to(dev)
+            for m in wl.mask]
+    pts = torch.from_numpy(np.ascontiguousarray(wl.points)).to(dev)
+    fu = VoxelFusion(wl.grid, occ=occ, coords=coords, params=FusionParams())
+    score = torch.empty(fu.n_cells if occ is not None else fu.n_active, dtype=torch.float32,
+                        device=dev)
+    labels = torch.empty(len(wl.points), dtype=torch.uint8, device=dev)
+    pv = PreparedViews(wl.cams, depth, mask, wl.mask_type)
+    for _ in range(args.profile_steps):
+        fu.step(pv, occ=occ, coords=coords, score=score, xyz=pts, labels=labels)
+    torch.cuda.synchronize()
+    fu.sync()
+    print(json.dumps({"profile_steps": args.profile_steps, "workload": args.workload,
+                      "active_voxels": fu.n_active}))
+    fu.close()
+    return 0
+
+
 def run(args):
     rank = _env_int("RANK", 0)
     world = _env_int("WORLD_SIZE", 1)
@@ -671,6 +718,8 @@ def run(args):
         if rank != 0:
             return 0
         return run_reference(args)
+    if args.profile_steps:
+        return profile_steps(args)
     if world > 1:
         import torch
         import torch.distributed as dist
@@ -747,6 +796,8 @@ def main(argv=None):
                     help="request rates (per second) to serve")
     ap.add_argument("--quick", action="store_true",
                     help="timed graph steps only: no eager, per-update, e2e or CPU legs")
+    ap.add_argument("--profile-steps", type=int, default=0,
+                    help="profiling target: run N eager one-call steps and exit")
     args = ap.parse_args(argv)
     args.warmup = max(3, args.warmup)  # at least 3 untimed warm-up steps
     return run(args)

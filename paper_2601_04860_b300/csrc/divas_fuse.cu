@@ -833,30 +833,40 @@ ViewC make_view(const divas_camera& cam, const GridC& G, const float* depth, con
         memcpy(v.A, cam.R, sizeof(cam.R));
         memcpy(v.C, cam.t, sizeof(cam.t));
     } else {
+        // camera coordinates of the lattice point n: p = T + M n, T = R o + t,
+        // M = (h / 2) R (in double)
         const double hh = 0.5 * (double)G.h;
         const double nmax = 2.0 * G.g - 1.0;
+        double T[3], M[3][3];
         for (int r = 0; r < 3; ++r) {
-            double T = (double)cam.t[r];
-            double M[3];
-            double bmax = 0.0;
+            T[r] = (double)cam.t[r];
             for (int j = 0; j < 3; ++j) {
-                T += (double)cam.R[3 * r + j] * (double)G.origin[j];
-                M[j] = hh * (double)cam.R[3 * r + j];
-                bmax += fabs(M[j]) * nmax;
+                T[r] += (double)cam.R[3 * r + j] * (double)G.origin[j];
+                M[r][j] = hh * (double)cam.R[3 * r + j];
             }
-            bmax += fabs(T);
-            int ex = 0;
-            frexp(bmax * 1.001 + 1e-300, &ex);  // bmax * 1.001 < 2^ex
-            const double quantum = ldexp(1.0, ex - 24);
-            for (int j = 0; j < 3; ++j) {
-                const double hi = rint(M[j] / quantum) * quantum;
-                v.A[3 * r + j] = (float)hi;
-                v.B[3 * r + j] = (float)(M[j] - hi);
-            }
-            const double thi = rint(T / quantum) * quantum;
-            v.C[r] = (float)thi;
-            v.E[r] = (float)(T - thi);
         }
+        // depth row: hi parts on a power-of-two quantum, so that the FMA chain
+        // over them is exact, plus the lo remainders
+        double bmax = fabs(T[2]);
+        for (int j = 0; j < 3; ++j) bmax += fabs(M[2][j]) * nmax;
+        int ex = 0;
+        frexp(bmax * 1.001 + 1e-300, &ex);  // bmax * 1.001 < 2^ex
+        const double quantum = ldexp(1.0, ex - 24);
+        for (int j = 0; j < 3; ++j) {
+            const double hi = rint(M[2][j] / quantum) * quantum;
+            v.A[6 + j] = (float)hi;
+            v.B[6 + j] = (float)(M[2][j] - hi);
+        }
+        const double thi = rint(T[2] / quantum) * quantum;
+        v.C[2] = (float)thi;
+        v.E[2] = (float)(T[2] - thi);
+        // pixel rows: u p_z = (fx M_0 + cx M_2) n + (fx T_0 + cx T_2), likewise v
+        for (int j = 0; j < 3; ++j) {
+            v.A[j] = (float)((double)cam.fx * M[0][j] + (double)cam.cx * M[2][j]);
+            v.A[3 + j] = (float)((double)cam.fy * M[1][j] + (double)cam.cy * M[2][j]);
+        }
+        v.C[0] = (float)((double)cam.fx * T[0] + (double)cam.cx * T[2]);
+        v.C[1] = (float)((double)cam.fy * T[1] + (double)cam.cy * T[2]);
     }
     v.fx = cam.fx;
     v.fy = cam.fy;

@@ -13,19 +13,24 @@
 // only the explicit __fmaf_rn below are fused and all kernels round alike.
 //
 // Precision.  Decisions (pixel index, gates) and weights must agree with a
-// double-precision evaluation.  Plain FP32 would not do: p_z ~ 2.5 carries
-// ~2.4e-7 rounding while e = p_z - D is compared with Delta ~ 8e-3, so e /
-// Delta would be off by ~4e-5.  Two exact schemes are used:
+// double-precision evaluation.  Plain FP32 would not do for the depth: p_z ~
+// 2.5 carries ~2.4e-7 rounding while e = p_z - D is compared with Delta ~
+// 8e-3, so e / Delta would be off by ~4e-5.  Two schemes are used:
 //
 //  * Plain grids (lattice projection).  Voxel centres are x = o + (h/2) n
 //    with n = 2 idx + 1 an odd integer (|n| < 2^11), so camera coordinates
 //    are p = T + M n with T = R o + t and M = (h/2) R, formed on the host in
-//    double.  Each is split into a "hi" part rounded to a multiple of a
-//    power of two 2^q -- chosen per row so that |T| + sum |M| (2g - 1) <
+//    double.  The depth row is split into a "hi" part rounded to a multiple
+//    of a power of two 2^q -- chosen so that |T_z| + sum |M_z| (2g - 1) <
 //    2^(q+24) -- and a small "lo" remainder.  Every partial sum of
 //    T_hi + M_hi n is then a multiple of 2^q below 2^(q+24): the FMA chain
-//    is exact in FP32.  The lo chain adds a term of relative size 2^-36.
-//    p = hi + lo costs 6 FMA per coordinate.
+//    is exact in FP32, and the lo chain adds a term of relative size 2^-36
+//    (6 FMA).  The pixel coordinates only decide which pixel is read, so
+//    they take the intrinsics-folded rows u p_z = (fx M_x + cx M_z) n +
+//    (fx T_x + cx T_z) (and likewise v) in one plain 3-FMA chain each and a
+//    multiply by 1 / p_z: a few ulp of |Ku n| + |Tu|, i.e. about 1e-4 pixel
+//    for the benchmark cameras, well inside the 1e-6-relative band within
+//    which a pixel decision counts as a tie.
 //
 //  * Contracted grids.  Centres are uncontracted in hi + lo pairs and
 //    projected with a compensated dot product (error-free products via FMA
@@ -254,16 +259,27 @@ __device__ __forceinline__ void lattice_row(const float* Mh, const float* Ml, fl
 template <bool kContracted>
 __device__ __forceinline__ int32_t project(const ViewC& V, const VoxelGeom& vg, float z_near,
                                            float& pzh, float& pzl) {
-    float px, py, pz;
+    float pz, u, v;
     if (!kContracted) {
-        float h, l;
+        // depth exactly (hi + lo); the pixel rows u p_z = Ku n + Tu and
+        // v p_z = Kv n + Tv in plain FMA chains (a few ulp of |Ku n| + |Tu|:
+        // about 1e-4 pixel on the benchmark cameras)
         lattice_row(V.A + 6, V.B + 6, V.C[2], V.E[2], vg.xh, pzh, pzl);
-        lattice_row(V.A, V.B, V.C[0], V.E[0], vg.xh, h, l);
-        px = __fadd_rn(h, l);
-        lattice_row(V.A + 3, V.B + 3, V.C[1], V.E[1], vg.xh, h, l);
-        py = __fadd_rn(h, l);
         pz = __fadd_rn(pzh, pzl);
-    } else {
+        const float pu = __fmaf_rn(V.A[0], vg.xh[0],
+                                   __fmaf_rn(V.A[1], vg.xh[1], __fmaf_rn(V.A[2], vg.xh[2], V.C[0])));
+        const float pv = __fmaf_rn(V.A[3], vg.xh[0],
+                                   __fmaf_rn(V.A[4], vg.xh[1], __fmaf_rn(V.A[5], vg.xh[2], V.C[1])));
+        const bool front = pz > z_near && pz <= FLT_MAX;
+        const float inv = rcp_nr(front ? pz : 1.f);
+        u = __fmul_rn(pu, inv);
+        v = __fmul_rn(pv, inv);
+        const bool in = front && u >= 0.f && u < V.Wf && v >= 0.f && v < V.Hf;
+        // u, v >= 0 inside the frame: truncation is floor
+        return in ? (int32_t)v * V.W + (int32_t)u : -1;
+    }
+    float px, py;
+    {
         float h, l;
         dot3c(V.A[6], V.A[7], V.A[8], vg.xh, vg.xl, V.C[2], pzh, pzl);
         dot3c(V.A[0], V.A[1], V.A[2], vg.xh, vg.xl, V.C[0], h, l);
@@ -274,8 +290,8 @@ __device__ __forceinline__ int32_t project(const ViewC& V, const VoxelGeom& vg, 
     }
     const bool front = pz > z_near && pz <= FLT_MAX;
     const float inv = rcp_nr(front ? pz : 1.f);
-    const float u = __fmaf_rn(V.fx, __fmul_rn(px, inv), V.cx);
-    const float v = __fmaf_rn(V.fy, __fmul_rn(py, inv), V.cy);
+    u = __fmaf_rn(V.fx, __fmul_rn(px, inv), V.cx);
+    v = __fmaf_rn(V.fy, __fmul_rn(py, inv), V.cy);
     const bool in = front && u >= 0.f && u < V.Wf && v >= 0.f && v < V.Hf;
     // u, v >= 0 inside the frame: truncation is floor
     return in ? (int32_t)v * V.W + (int32_t)u : -1;
