@@ -203,7 +203,7 @@ def oracle_rate(wl, seconds: float, seed: int = 0):
 # our arm
 # --------------------------------------------------------------------------
 KERNEL_OF = {"compaction": "k_tile_count+k_tile_emit", "fuse": "k_fuse",
-             "finalize": "k_finalize", "label": "k_label", "fuse_finalize": "k_fuse_step"}
+             "finalize": "k_finalize", "label": "k_label", "fuse_finalize": "k_fuse_fin"}
 
 
 def algorithmic_bytes(wl, n_active):
@@ -213,19 +213,20 @@ def algorithmic_bytes(wl, n_active):
     view_bytes = sum(d.nbytes + m.nbytes for d, m in zip(wl.depth, wl.mask))
     npts = len(wl.points)
     cells = int(wl.grid.g) ** 3
+    zeros = 0
     if wl.occ is not None:
         comp = cells + cells // 8 + 4 * n_active          # occ read, bits, active list
         fin = cells // 8 + 8 * n_active + 4 * cells + cells // 8  # bits, W+Z, P, seg
-        score = 4 * cells + cells // 8                    # dense P (every cell), bits read
+        zeros = 4 * (cells - n_active) + cells // 8       # unoccupied score cells, bits read
     else:
         comp = 12 * len(wl.coords) + cells // 8 + 4 * n_active
         fin = 8 * n_active + 4 * n_active + cells // 8
-        score = 4 * n_active
     fuse = 4 * n_active + 12 * n_active + view_bytes        # index, W+Z+bits, rasters
     lab = 13 * npts + cells // 8
     algo = {"compaction": comp + cells // 8,                # + the seg clear (step)
             "fuse": fuse, "finalize": fin, "label": lab,
-            "fuse_finalize": fuse + score + cells // 8}     # + seg bits
+            # + P of the active voxels, seg bits, zeros of the unoccupied cells
+            "fuse_finalize": fuse + 4 * n_active + cells // 8 + zeros}
     return algo, view_bytes, S, g3
 
 
@@ -257,7 +258,8 @@ def run_ours(args, rank, world, local_rank):
     phases = ["compaction", "fuse", "finalize", "label"]
     kernels_per_phase = {"compaction": 2 if dense else 3, "fuse": math.ceil(S / 32),
                          "finalize": 1, "label": 1}
-    # the one-call step: compaction (2 or 3 kernels), fusion + finalize (1), labels (1)
+    # the one-call step: compaction (2 or 3 kernels), fusion + finalize (1, which on a
+    # dense grid also writes the zeros of the unoccupied score cells), labels (1)
     step_phases = ["compaction", "fuse_finalize", "label"]
     step_kernels = {"compaction": 2 if dense else 3, "fuse_finalize": 1, "label": 1}
 
@@ -382,43 +384,56 @@ def run_ours(args, rank, world, local_rank):
         torch.cuda.synchronize()
         eager.append(a.elapsed_time(b))
 
-    # per-update latency: one more view folded into a session holding S-1 views,
-    # then finalize -- eager API calls, and the same update replayed as a graph
-    upd, upd_g = [], []
+    # per-update latency: one more view folded into a session holding S-1 views
+    # and finalized, through divas_fuse_update (one fusion launch; the score
+    # buffer holds this context's earlier result, so only active voxels are
+    # written) -- eager API calls, and the same update replayed as a graph; the
+    # separate add_views + finalize calls as a graph for reference
+    upd, upd_g, upd_sep = [], [], []
     pv_last = PreparedViews(wl.cams[-1:], depth[-1:], mask[-1:], wl.mask_type)
     pv_first = PreparedViews(wl.cams[:-1], depth[:-1], mask[:-1], wl.mask_type)
-    ug = None
-    for k in range(max(20, args.steps)):
+    n_upd = max(20, args.steps)
+    for k in range(n_upd):
         fu.set_occupancy(occ=occ, coords=coords)
         fu.add_views(pv_first)
         flush.zero_()
-        if ug is None:
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        fu.update(pv_last, score=score, keep_zeros=True)
+        b.record()
+        torch.cuda.synchronize()
+        upd.append(a.elapsed_time(b))
+    graphs = {}
+    for name in ("update", "separate"):
+        fu.set_occupancy(occ=occ, coords=coords)
+        fu.add_views(pv_first)
+        torch.cuda.synchronize()
+        ue = [torch.cuda.Event(enable_timing=True, external=True) for _ in range(2)]
+        ug = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(ug):
+            ue[0].record()
+            if name == "update":
+                fu.update(pv_last, score=score, keep_zeros=True)
+            else:
+                fu.add_views(pv_last)
+                fu.finalize(score=score)
+            ue[1].record()
+        graphs[name] = (ug, ue)
+    for k in range(n_upd):
+        for name, out in (("update", upd_g), ("separate", upd_sep)):
+            ug, ue = graphs[name]
+            fu.set_occupancy(occ=occ, coords=coords)
+            fu.add_views(pv_first)
+            flush.zero_()
             torch.cuda.synchronize()
-            a = torch.cuda.Event(enable_timing=True)
-            b = torch.cuda.Event(enable_timing=True)
-            a.record()
-            fu.add_views(pv_last)
-            fu.finalize(score=score)
-            b.record()
-            torch.cuda.synchronize()
-            upd.append(a.elapsed_time(b))
-            if k == max(20, args.steps) // 2:
-                ue = [torch.cuda.Event(enable_timing=True, external=True) for _ in range(2)]
-                ug = torch.cuda.CUDAGraph()
-                fu.set_occupancy(occ=occ, coords=coords)
-                fu.add_views(pv_first)
-                torch.cuda.synchronize()
-                with torch.cuda.graph(ug):
-                    ue[0].record()
-                    fu.add_views(pv_last)
-                    fu.finalize(score=score)
-                    ue[1].record()
-        else:
             ug.replay()
             torch.cuda.synchronize()
-            upd_g.append(ue[0].elapsed_time(ue[1]))
+            out.append(ue[0].elapsed_time(ue[1]))
     upd = np.array(upd)
     upd_g = np.array(upd_g)
+    upd_sep = np.array(upd_sep)
 
     # end to end through the public API with pinned host buffers
     h_occ = None if occ is None else torch.from_numpy(wl.occ).pin_memory()
@@ -509,11 +524,14 @@ def run_ours(args, rank, world, local_rank):
         "separate_calls_ms_per_step": float(np.mean(sep_ms)),
         "phase_bytes": {k: int(v) for k, v in algo.items()},
         "eager_ms_per_step": float(np.mean(eager)),
-        "per_update_ms": {"what": "fold 1 view into a session of S-1 views + finalize, L2 flushed",
+        "per_update_ms": {"what": "fold 1 view into a session of S-1 views + finalize "
+                                  "(divas_fuse_update, one fusion launch), L2 flushed",
                           "p50": float(np.percentile(upd, 50)),
                           "p99": float(np.percentile(upd, 99)),
-                          "graph_p50": float(np.percentile(upd_g, 50)) if len(upd_g) else None,
-                          "graph_p99": float(np.percentile(upd_g, 99)) if len(upd_g) else None},
+                          "graph_p50": float(np.percentile(upd_g, 50)),
+                          "graph_p99": float(np.percentile(upd_g, 99)),
+                          "separate_calls_graph_p50": float(np.percentile(upd_sep, 50)),
+                          "separate_calls_graph_p99": float(np.percentile(upd_sep, 99))},
         "active_updates_per_s": world * n_active * S / (ms * 1e-3),
         "e2e": {"value": job_throughput(N * S, world, e2e_ms), "unit": UNIT,
                 "ms_per_step": e2e_ms, "h2d_bytes_per_step": int(h2d),
@@ -681,7 +699,7 @@ def measure_sessions(dev, scale: float, n_sessions: int, rates, budget_frac: flo
 
 def profile_steps(args):
     """Profiling target: init (3 launches: count, count, emit) then N eager
-    one-call steps (4 launches each: k_tile_count, k_tile_emit, k_fuse_step,
+    one-call steps (4 launches each: k_tile_count, k_tile_emit, k_fuse_fin,
     k_label on a dense workload) and nothing else."""
     import torch
 

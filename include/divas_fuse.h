@@ -68,7 +68,7 @@ typedef enum {
     DIVAS_E_INVALID = 1,  /* bad argument; nothing was queued */
     DIVAS_E_OOM = 2,      /* device allocation failed */
     DIVAS_E_CUDA = 3,     /* a CUDA call failed (message in divas_last_error) */
-    DIVAS_E_TIMEOUT = 4,  /* a bounded device-side wait expired */
+    DIVAS_E_TIMEOUT = 4,  /* reserved: no kernel of this library waits on another CTA */
     DIVAS_E_STATE = 5,    /* call not valid in the context's current state */
     DIVAS_E_CAPACITY = 6  /* occupied set larger than the context's capacity */
 } divas_status;
@@ -132,9 +132,11 @@ divas_status divas_fuse_init(divas_ctx** out, const divas_grid* grid, const uint
 
 /* Rebuild the active list from a new prior of the same kind and grid, reusing
  * the context's memory (no allocation, no synchronisation); the view count
- * returns to 0, so the next fold starts the accumulators from zero.  If the new occupied set exceeds the capacity sized at
- * init, the excess voxels are dropped and DIVAS_E_CAPACITY is reported by the
- * next synchronising call. */
+ * returns to 0, so the next fold starts the accumulators from zero, and the
+ * context's seg bitfield is cleared (labels read 0 until the next finalize).
+ * If the new occupied set exceeds the capacity sized at init, the excess
+ * voxels are dropped and DIVAS_E_CAPACITY is reported by the next
+ * synchronising call. */
 divas_status divas_fuse_set_occupancy(divas_ctx* ctx, const uint8_t* occ_dense,
                                       const int32_t* coords, int64_t n_coords, void* stream);
 
@@ -161,17 +163,37 @@ divas_status divas_fuse_add_views(divas_ctx* ctx, const divas_view* views, int32
 divas_status divas_fuse_finalize(divas_ctx* ctx, float* score_out, uint32_t* seg_bits_out,
                                  uint32_t* vmask_out, int64_t* n_seg_host, void* stream);
 
+/* flags of divas_fuse_update and divas_batch_finalize */
+#define DIVAS_KEEP_ZEROS 1u /* score_out / seg_bits_out already hold 0 for every unoccupied
+                               voxel (e.g. an earlier result of this context for the same
+                               occupied set): only the active voxels' entries are written */
+
+/*
+ * Incremental update (Sec. 3.7: a new view arrives and the 3D mask is shown
+ * again): fold n_views (1..DIVAS_MAX_VIEWS_PER_CALL) views onto the stored
+ * accumulators and finalize, in one fusion launch.  Results equal
+ * divas_fuse_add_views followed by divas_fuse_finalize (score_out and
+ * seg_bits_out as there, nullable; no vmask, no count).  Without
+ * DIVAS_KEEP_ZEROS a dense score_out also gets its unoccupied zeros (in the
+ * same launch) and seg_bits_out is cleared first; with it, only active
+ * entries are written and bits are set and cleared in place.
+ */
+divas_status divas_fuse_update(divas_ctx* ctx, const divas_view* views, int32_t n_views,
+                               float* score_out, uint32_t* seg_bits_out, uint32_t flags,
+                               void* stream);
+
 /*
  * The whole hot path in one call: divas_fuse_set_occupancy (A1), then
  * divas_fuse_add_views (views folded into fresh accumulators), then finalize
  * (score_out, seg_bits_out as in divas_fuse_finalize) and, when n_pts > 0,
- * divas_label_points, in four kernel launches and no memset: the compaction
- * clears the seg bitfields, and the fusion launch also normalises and
- * thresholds each voxel and writes the zeros of the unoccupied cells of a
- * dense score_out.  Results (outputs and context state) equal the separate
- * calls; 1..DIVAS_MAX_VIEWS_PER_CALL views.  Capturable in a CUDA graph.  If
- * the occupied set overflows the capacity (DIVAS_E_CAPACITY at the next
- * synchronising call), the dense scores of the dropped voxels are unspecified.
+ * divas_label_points, in four launches and no memset: the compaction clears
+ * the seg bitfields, and the fusion launch also normalises and thresholds
+ * each voxel and then writes the zeros of a dense score_out's unoccupied
+ * cells.  Results (outputs and
+ * context state) equal the separate calls; 1..DIVAS_MAX_VIEWS_PER_CALL views.
+ * Capturable in a CUDA graph.  If the occupied set overflows the capacity
+ * (DIVAS_E_CAPACITY at the next synchronising call), the dense scores of the
+ * dropped voxels are unspecified.
  */
 divas_status divas_fuse_step(divas_ctx* ctx, const uint8_t* occ_dense, const int32_t* coords,
                              int64_t n_coords, const divas_view* views, int32_t n_views,
@@ -282,9 +304,11 @@ divas_status divas_batch_fuse(divas_batch* b, const divas_schedule* sched, int32
                               void* stream);
 /* score_out[k] / xyz[k] / n_pts[k] / labels_out[k] for the k-th queued context
  * (arrays and entries nullable): as divas_fuse_finalize's score_out and
- * divas_label_points. */
+ * divas_label_points.  flags: 0 or DIVAS_KEEP_ZEROS (the dense score_out
+ * buffers already hold zeros for their unoccupied voxels: not refilled). */
 divas_status divas_batch_finalize(divas_batch* b, float* const* score_out, const float* const* xyz,
-                                  const int64_t* n_pts, uint8_t* const* labels_out, void* stream);
+                                  const int64_t* n_pts, uint8_t* const* labels_out, uint32_t flags,
+                                  void* stream);
 divas_status divas_batch_clear(divas_batch* b);
 int32_t divas_batch_size(const divas_batch* b);
 const char* divas_batch_last_error(const divas_batch* b);

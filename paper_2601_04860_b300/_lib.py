@@ -18,6 +18,7 @@ MASK_F32 = 0
 MASK_F16 = 1
 MASK_LOGIT_F32 = 2
 MAX_VIEWS_PER_CALL = 32
+KEEP_ZEROS = 1
 
 
 class DivasParams(ctypes.Structure):
@@ -75,6 +76,8 @@ _SIGS = {
     "divas_debug_rcp": (ctypes.c_int, [_P, ctypes.c_int64, _P, _P, _P]),
     "divas_fuse_step": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64, ctypes.POINTER(DivasView),
                                        ctypes.c_int32, _P, _P, _P, ctypes.c_int64, _P, _P]),
+    "divas_fuse_update": (ctypes.c_int, [_P, ctypes.POINTER(DivasView), ctypes.c_int32, _P, _P,
+                                         ctypes.c_uint32, _P]),
     "divas_fuse_step_profiled": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64,
                                                 ctypes.POINTER(DivasView), ctypes.c_int32, _P, _P,
                                                 _P, ctypes.c_int64, _P, ctypes.POINTER(_P), _P]),

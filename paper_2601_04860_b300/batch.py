@@ -38,7 +38,7 @@ _BATCH_SIGS = {
     "divas_batch_fuse": (ctypes.c_int, [_P, ctypes.POINTER(DivasSchedule), ctypes.c_int32, _P]),
     "divas_batch_finalize": (ctypes.c_int, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P),
                                             ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(_P),
-                                            _P]),
+                                            ctypes.c_uint32, _P]),
     "divas_batch_clear": (ctypes.c_int, [_P]),
     "divas_batch_size": (ctypes.c_int32, [_P]),
     "divas_batch_last_error": (ctypes.c_char_p, [_P]),
@@ -118,8 +118,11 @@ class Batch:
         self._check(self.lib.divas_batch_fuse(self._h, ctypes.byref(sch), 1 if dry_run else 0,
                                               _stream(stream)))
 
-    def finalize(self, scores=None, points=None, labels=None, stream=None):
-        """scores / points / labels: per queued session, tensors or None."""
+    def finalize(self, scores=None, points=None, labels=None, keep_zeros=False, stream=None):
+        """scores / points / labels: per queued session, tensors or None.
+        ``keep_zeros``: the dense score tensors already hold zeros for their
+        unoccupied voxels (e.g. zero-initialised and only ever written by this
+        session), so only the active voxels' scores are written."""
         n = len(self.sessions)
         sc = (_P * n)(*[(_ptr(t).value if t is not None else None)
                         for t in (scores or [None] * n)])
@@ -129,7 +132,9 @@ class Batch:
                                       for t in (points or [None] * n)])
         lab = (_P * n)(*[(_ptr(t).value if t is not None else None)
                          for t in (labels or [None] * n)])
-        self._check(self.lib.divas_batch_finalize(self._h, sc, pts, npts, lab, _stream(stream)))
+        self._check(self.lib.divas_batch_finalize(self._h, sc, pts, npts, lab,
+                                                  L.KEEP_ZEROS if keep_zeros else 0,
+                                                  _stream(stream)))
         self.sessions = []
         self._keep = []
 

@@ -358,10 +358,34 @@ cudaError_t launch_fuse_chunks(int chunks, int blocks, cudaStream_t s, const uin
 // ---------------------------------------------------------------------------
 // finalize
 // ---------------------------------------------------------------------------
-// normalise + threshold, one thread per active voxel (the dense score grid and
-// the seg bitfields were zeroed by the caller): P = W / Z, seg = P >= tau_cons,
-// the score goes to its dense or active-list position, seg bits are OR-ed in
-// once per group of lanes that share a 32-bit word
+// seg bits of one warp's 32 voxels (active slots base .. base + 31): lanes
+// that share a 32-bit word are grouped, their set bits OR-ed in and -- for a
+// bitfield that may hold an earlier seg of the same voxels -- their unset bits
+// AND-ed out, one atomic per group and bitfield.  Every bit belongs to exactly
+// one voxel, so the result does not depend on the order of the atomics.
+__device__ __forceinline__ void seg_epilogue(bool live, bool seg, int64_t lin,
+                                             uint32_t* __restrict__ seg_bits, bool clear_bits,
+                                             uint32_t* __restrict__ seg_out, bool clear_out) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t word = live ? (uint32_t)(lin >> 5) : 0xffffffffu;
+    const uint32_t bit = live ? 1u << (lin & 31) : 0u;
+    const uint32_t grp = __match_any_sync(0xffffffffu, word);
+    const uint32_t set = __reduce_or_sync(grp, seg ? bit : 0u);
+    const uint32_t clr = __reduce_or_sync(grp, seg ? 0u : bit);
+    if (!live || lane != __ffs(grp) - 1) return;
+    if (set) atomicOr(seg_bits + word, set);
+    if (clr && clear_bits) atomicAnd(seg_bits + word, ~clr);
+    if (seg_out) {
+        if (set) atomicOr(seg_out + word, set);
+        if (clr && clear_out) atomicAnd(seg_out + word, ~clr);
+    }
+}
+
+// normalise + threshold, one thread per active voxel: P = W / Z, seg = P >=
+// tau_cons; the score goes to its dense or active-list position (the caller
+// zeroed a dense grid's other cells).  The context's seg bitfield holds no bit
+// of an unoccupied voxel (set_occupancy clears it), so its bits are set and
+// cleared in place; seg_out (zeroed by the caller) only gets its set bits.
 __global__ void __launch_bounds__(kThreads) k_finalize(
     const uint32_t* __restrict__ active, const int32_t* __restrict__ d_n, int32_t g,
     int32_t dense, const float* __restrict__ W, const float* __restrict__ Z,
@@ -385,13 +409,7 @@ __global__ void __launch_bounds__(kThreads) k_finalize(
             if (score_out) score_out[dense ? lin : (int64_t)a] = p;
             if (vmask_out) vmask_out[a] = seg ? bits[a] : 0u;
         }
-        const uint32_t word = live ? (uint32_t)(lin >> 5) : 0xffffffffu;
-        const uint32_t grp = __match_any_sync(0xffffffffu, word);
-        const uint32_t orv = __reduce_or_sync(grp, seg ? 1u << (lin & 31) : 0u);
-        if (live && lane == __ffs(grp) - 1 && orv) {
-            atomicOr(seg_bits + word, orv);
-            if (seg_out) atomicOr(seg_out + word, orv);
-        }
+        seg_epilogue(live, seg, lin, seg_bits, true, seg_out, false);
         if (d_nseg) {
             const uint32_t cnt = __popc(__ballot_sync(0xffffffffu, seg));
             if (lane == 0 && cnt) atomicAdd(d_nseg, (unsigned long long)cnt);
@@ -400,29 +418,31 @@ __global__ void __launch_bounds__(kThreads) k_finalize(
 }
 
 // ---------------------------------------------------------------------------
-// the one-call step's fusion: fresh accumulators, every view of the step, and
-// the finalize epilogue in the same pass (P = W / Z, seg = P >= tau_cons, the
-// score to its dense or active-list position, warp-aggregated seg-bit ORs into
-// bitfields that k_tile_emit cleared), then the zeros of a dense score grid's
-// unoccupied cells.  Per voxel the arithmetic is that of k_fuse followed by
-// k_finalize.
+// fusion + finalize in one pass (the one-call step and the incremental
+// update): fold the batch's views (into fresh accumulators, or onto the
+// stored ones with kAccumulate), store W, Z, bits, then P = W / Z, seg =
+// P >= tau_cons, the score to its dense or active-list position and the seg
+// bits (seg_epilogue; clear_bits / clear_out when the bitfield may hold an
+// earlier seg of these voxels); with zero_unoccupied, a dense score grid then
+// gets the zeros of its unoccupied cells.  Per voxel the arithmetic is that of
+// k_fuse followed by k_finalize.
 // ---------------------------------------------------------------------------
-template <bool kContracted, int kChunks>
-__global__ void __launch_bounds__(kThreads, kContracted ? 4 : 6) k_fuse_step(
+template <bool kAccumulate, bool kContracted, int kChunks>
+__global__ void __launch_bounds__(kThreads, kContracted ? 4 : 6) k_fuse_fin(
     const uint32_t* __restrict__ active, const int32_t* __restrict__ d_n, GridC G, FuseC F,
     const __grid_constant__ ViewBatch VB, float* __restrict__ W, float* __restrict__ Z,
     uint32_t* __restrict__ bits, int32_t dense, float* __restrict__ score_out,
-    uint32_t* __restrict__ seg_bits, uint32_t* __restrict__ seg_out,
-    const uint32_t* __restrict__ occ_bits, int64_t n_words, int64_t n_cells) {
+    uint32_t* __restrict__ seg_bits, int32_t clear_bits, uint32_t* __restrict__ seg_out,
+    int32_t clear_out, const uint32_t* __restrict__ occ_bits, int64_t n_words, int64_t n_cells,
+    int32_t zero_unoccupied) {
     const int lane = threadIdx.x & 31;
     const int32_t gw = (int32_t)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int32_t nw = (int32_t)((gridDim.x * blockDim.x) >> 5);
-    const bool zero = dense && score_out;
     const int64_t n_groups = (n_words + 31) / 32;
     // occupancy word of the first group this warp zero-fills, fetched now and
     // used after the fusion loop
     uint32_t x_first = 0;
-    if (zero && gw < n_groups && (int64_t)gw * 32 + lane < n_words)
+    if (zero_unoccupied && gw < n_groups && (int64_t)gw * 32 + lane < n_words)
         x_first = __ldg(occ_bits + (int64_t)gw * 32 + lane);
     const int32_t n = *d_n;
     for (int32_t base = gw * 32; base < n; base += nw * 32) {
@@ -435,6 +455,11 @@ __global__ void __launch_bounds__(kThreads, kContracted ? 4 : 6) k_fuse_step(
             const VoxelGeom vg = voxel_geom<kContracted>(pk, G, F.gamma);
             float w = 0.f, z = 0.f;
             uint32_t b = 0;
+            if (kAccumulate) {
+                w = W[a];
+                z = Z[a];
+                b = bits[a];
+            }
             if (vg.ok) fold_views<kContracted, kChunks>(VB, vg, F, w, z, b);
             W[a] = w;
             Z[a] = z;
@@ -444,18 +469,12 @@ __global__ void __launch_bounds__(kThreads, kContracted ? 4 : 6) k_fuse_step(
             lin = packed_lin(pk, G.g);
             if (score_out) score_out[dense ? lin : (int64_t)a] = p;
         }
-        const uint32_t word = live ? (uint32_t)(lin >> 5) : 0xffffffffu;
-        const uint32_t grp = __match_any_sync(0xffffffffu, word);
-        const uint32_t orv = __reduce_or_sync(grp, seg ? 1u << (lin & 31) : 0u);
-        if (live && lane == __ffs(grp) - 1 && orv) {
-            atomicOr(seg_bits + word, orv);
-            if (seg_out) atomicOr(seg_out + word, orv);
-        }
+        seg_epilogue(live, seg, lin, seg_bits, clear_bits != 0, seg_out, clear_out != 0);
     }
-    if (!zero) return;
-    // zeros of the unoccupied cells, one group of 32 words (1024 cells) per
-    // warp and round: coalesced 16-byte stores that need no result (the
-    // occupied cells got their P above, possibly from other warps)
+    if (!zero_unoccupied) return;
+    // zeros of a dense score grid's unoccupied cells, one group of 32 words
+    // (1024 cells) per warp and round: coalesced 16-byte stores that need no
+    // result (the occupied cells got their P above, possibly from other warps)
     const bool vec = (reinterpret_cast<uintptr_t>(score_out) & 15) == 0;
     for (int64_t g = gw; g < n_groups; g += nw) {
         const int64_t w = g * 32 + lane;
@@ -855,11 +874,11 @@ ViewC make_view(const divas_camera& cam, const GridC& G, const float* depth, con
         for (int j = 0; j < 3; ++j) {
             const double hi = rint(M[2][j] / quantum) * quantum;
             v.A[6 + j] = (float)hi;
-            v.B[6 + j] = (float)(M[2][j] - hi);
+            v.B[j] = (float)(M[2][j] - hi);
         }
         const double thi = rint(T[2] / quantum) * quantum;
         v.C[2] = (float)thi;
-        v.E[2] = (float)(T[2] - thi);
+        v.E = (float)(T[2] - thi);
         // pixel rows: u p_z = (fx M_0 + cx M_2) n + (fx T_0 + cx T_2), likewise v
         for (int j = 0; j < 3; ++j) {
             v.A[j] = (float)((double)cam.fx * M[0][j] + (double)cam.cx * M[2][j]);
@@ -868,10 +887,10 @@ ViewC make_view(const divas_camera& cam, const GridC& G, const float* depth, con
         v.C[0] = (float)((double)cam.fx * T[0] + (double)cam.cx * T[2]);
         v.C[1] = (float)((double)cam.fy * T[1] + (double)cam.cy * T[2]);
     }
-    v.fx = cam.fx;
-    v.fy = cam.fy;
-    v.cx = cam.cx;
-    v.cy = cam.cy;
+    v.K[0] = cam.fx;
+    v.K[1] = cam.fy;
+    v.K[2] = cam.cx;
+    v.K[3] = cam.cy;
     v.Wf = (float)cam.W;
     v.Hf = (float)cam.H;
     v.W = cam.W;
@@ -889,19 +908,39 @@ float logit_threshold(float tau) {
     return (float)log((double)tau / (1.0 - (double)tau));
 }
 
-// launch k_fuse_step with the chunk count as a compile-time constant
-template <bool kContracted, int kChunks = 1>
-cudaError_t launch_fuse_step_chunks(int chunks, int blocks, cudaStream_t s, const divas_ctx* c,
-                                    const ViewBatch& vb, float* score_out, uint32_t* seg_out) {
+// launch k_fuse_fin with the chunk count as a compile-time constant
+template <bool kAccumulate, bool kContracted, int kChunks = 1>
+cudaError_t launch_fuse_fin_chunks(int chunks, int blocks, cudaStream_t s, const divas_ctx* c,
+                                   const ViewBatch& vb, float* score_out, bool clear_bits,
+                                   uint32_t* seg_out, bool clear_out, bool zero) {
     if constexpr (kChunks < kMaxViews / kViewChunk) {
         if (chunks > kChunks)
-            return launch_fuse_step_chunks<kContracted, kChunks + 1>(chunks, blocks, s, c, vb,
-                                                                     score_out, seg_out);
+            return launch_fuse_fin_chunks<kAccumulate, kContracted, kChunks + 1>(
+                chunks, blocks, s, c, vb, score_out, clear_bits, seg_out, clear_out, zero);
     }
-    k_fuse_step<kContracted, kChunks><<<blocks, kThreads, 0, s>>>(
+    k_fuse_fin<kAccumulate, kContracted, kChunks><<<blocks, kThreads, 0, s>>>(
         c->active, c->d_n, c->G, c->F, vb, c->W, c->Z, c->bits, c->grid.kind == 0 ? 1 : 0,
-        score_out, c->seg_bits, seg_out, c->occ_bits, c->n_words, c->n_cells);
+        score_out, c->seg_bits, clear_bits ? 1 : 0, seg_out, clear_out ? 1 : 0, c->occ_bits,
+        c->n_words, c->n_cells, zero ? 1 : 0);
     return cudaGetLastError();
+}
+
+// zero: also write the zeros of a dense score_out's unoccupied cells
+cudaError_t launch_fuse_fin(const divas_ctx* c, bool accumulate, const ViewBatch& vb,
+                            cudaStream_t s, float* score_out, bool clear_bits, uint32_t* seg_out,
+                            bool clear_out, bool zero) {
+    const int chunks = (vb.n + kViewChunk - 1) / kViewChunk;
+    const int blocks = grid_for(zero ? std::max<int64_t>(c->cap, c->n_words) : c->cap, c->sm_count);
+    if (c->G.contracted)
+        return accumulate ? launch_fuse_fin_chunks<true, true>(chunks, blocks, s, c, vb, score_out,
+                                                               clear_bits, seg_out, clear_out, zero)
+                          : launch_fuse_fin_chunks<false, true>(chunks, blocks, s, c, vb,
+                                                                score_out, clear_bits, seg_out,
+                                                                clear_out, zero);
+    return accumulate ? launch_fuse_fin_chunks<true, false>(chunks, blocks, s, c, vb, score_out,
+                                                            clear_bits, seg_out, clear_out, zero)
+                      : launch_fuse_fin_chunks<false, false>(chunks, blocks, s, c, vb, score_out,
+                                                             clear_bits, seg_out, clear_out, zero);
 }
 
 // k_tile_emit grid: one group per warp, at most 16 CTAs per SM
@@ -1118,7 +1157,9 @@ divas_status divas_fuse_set_occupancy(divas_ctx* c, const uint8_t* occ_dense, co
     if (c->grid.kind == 1 && (occ_dense || n_coords < 0 || (n_coords > 0 && !coords)))
         return fail(c, DIVAS_E_INVALID, "sparse context needs coords only");
     cudaStream_t s = S(stream);
-    divas_status st = build_active(c, occ_dense, coords, n_coords, s);
+    // the seg bitfield is cleared on the way: it never holds a bit of a voxel
+    // outside the current occupied set
+    divas_status st = build_active(c, occ_dense, coords, n_coords, s, c->seg_bits);
     if (st != DIVAS_OK) return st;
     c->n_views = 0;
     c->n_active = c->cap;  // upper bound until the next synchronising call
@@ -1203,10 +1244,11 @@ divas_status divas_fuse_add_views(divas_ctx* c, const divas_view* views, int32_t
 namespace {
 
 // zero-fill what the scatter below ORs or writes into
+// the caller's outputs start at zero (the context's own seg bitfield needs no
+// clearing: it never holds a bit of an unoccupied voxel)
 divas_status finalize_zero(divas_ctx* c, float* score_out, uint32_t* seg_bits_out, cudaStream_t s) {
     if (score_out && c->grid.kind == 0)
         DIVAS_CUDA(c, cudaMemsetAsync(score_out, 0, c->n_cells * 4, s));
-    DIVAS_CUDA(c, cudaMemsetAsync(c->seg_bits, 0, c->n_words * 4, s));
     if (seg_bits_out) DIVAS_CUDA(c, cudaMemsetAsync(seg_bits_out, 0, c->n_words * 4, s));
     return DIVAS_OK;
 }
@@ -1280,15 +1322,11 @@ divas_status divas_fuse_step_profiled(divas_ctx* c, const uint8_t* occ_dense,
     if (st != DIVAS_OK) return st;
     c->n_views = 0;
     c->n_active = c->cap;  // upper bound until the next synchronising call
-    // fusion of every view + finalize epilogue
-    const int chunks = (vb.n + kViewChunk - 1) / kViewChunk;
-    const int blocks = grid_for(std::max<int64_t>(c->cap, c->n_words), c->sm_count);
-    cudaError_t e = c->G.contracted
-                        ? launch_fuse_step_chunks<true>(chunks, blocks, s, c, vb, score_out,
-                                                        seg_bits_out)
-                        : launch_fuse_step_chunks<false>(chunks, blocks, s, c, vb, score_out,
-                                                         seg_bits_out);
-    if (e != cudaSuccess) return cuda_fail(c, e, "k_fuse_step");
+    const bool zero = score_out && c->grid.kind == 0;
+    // fusion of every view + finalize epilogue (both seg bitfields were
+    // cleared) + the zeros of a dense score grid's unoccupied cells
+    cudaError_t e = launch_fuse_fin(c, false, vb, s, score_out, false, seg_bits_out, false, zero);
+    if (e != cudaSuccess) return cuda_fail(c, e, "k_fuse_fin");
     c->n_views = vb.n;
     st = record_stage(c, stage_events, 2, s);
     if (st != DIVAS_OK) return st;
@@ -1297,6 +1335,27 @@ divas_status divas_fuse_step_profiled(divas_ctx* c, const uint8_t* occ_dense,
         if (st != DIVAS_OK) return st;
     }
     return record_stage(c, stage_events, 3, s);
+}
+
+divas_status divas_fuse_update(divas_ctx* c, const divas_view* views, int32_t n_views,
+                               float* score_out, uint32_t* seg_bits_out, uint32_t flags,
+                               void* stream) {
+    if (!c) return fail(nullptr, DIVAS_E_INVALID, "ctx is NULL");
+    if (flags & ~(uint32_t)DIVAS_KEEP_ZEROS) return fail(c, DIVAS_E_INVALID, "unknown flags");
+    ViewBatch vb;
+    divas_status st = make_batch(c, views, n_views, c->n_views, vb);
+    if (st != DIVAS_OK) return st;
+    cudaStream_t s = S(stream);
+    const bool keep = (flags & DIVAS_KEEP_ZEROS) != 0;
+    const bool zero = !keep && score_out && c->grid.kind == 0;
+    if (!keep && seg_bits_out) DIVAS_CUDA(c, cudaMemsetAsync(seg_bits_out, 0, c->n_words * 4, s));
+    // the context's seg bitfield holds this occupied set's previous seg (or
+    // zeros): set and clear in place; seg_bits_out likewise when kept
+    cudaError_t e = launch_fuse_fin(c, c->n_views > 0, vb, s, score_out, true, seg_bits_out, keep,
+                                    zero);
+    if (e != cudaSuccess) return cuda_fail(c, e, "k_fuse_fin");
+    c->n_views += vb.n;
+    return DIVAS_OK;
 }
 
 divas_status divas_label_points(divas_ctx* c, const float* xyz, int64_t n, uint8_t* labels_out,
@@ -1587,10 +1646,7 @@ __global__ void __launch_bounds__(kThreads) k_batch_finalize(const SessionDesc* 
                 lin = packed_lin(__ldg(D.active + a), D.G.g);
                 if (D.score_out) D.score_out[D.dense ? lin : (int64_t)a] = p;
             }
-            const uint32_t word = live ? (uint32_t)(lin >> 5) : 0xffffffffu;
-            const uint32_t grp = __match_any_sync(0xffffffffu, word);
-            const uint32_t orv = __reduce_or_sync(grp, seg ? 1u << (lin & 31) : 0u);
-            if (live && lane == __ffs(grp) - 1 && orv) atomicOr(D.seg_bits + word, orv);
+            seg_epilogue(live, seg, lin, D.seg_bits, true, nullptr, false);
         }
     }
 }
@@ -1810,8 +1866,11 @@ divas_status divas_batch_fuse(divas_batch* b, const divas_schedule* sched, int32
 }
 
 divas_status divas_batch_finalize(divas_batch* b, float* const* score_out, const float* const* xyz,
-                                  const int64_t* n_pts, uint8_t* const* labels_out, void* stream) {
+                                  const int64_t* n_pts, uint8_t* const* labels_out, uint32_t flags,
+                                  void* stream) {
     if (!b) return bfail(b, DIVAS_E_INVALID, "NULL batch");
+    if (flags & ~(uint32_t)DIVAS_KEEP_ZEROS) return bfail(b, DIVAS_E_INVALID, "unknown flags");
+    const bool keep = (flags & DIVAS_KEEP_ZEROS) != 0;
     const int32_t ns = (int32_t)b->ctxs.size();
     if (ns == 0) return DIVAS_OK;
     if (!b->fused) return bfail(b, DIVAS_E_STATE, "fuse the batch first (dry runs do not count)");
@@ -1832,11 +1891,13 @@ divas_status divas_batch_finalize(divas_batch* b, float* const* score_out, const
         any_pts |= hs[k].n_pts > 0;
         pf[k + 1] = pf[k] + (uint32_t)((c->cap + tile - 1) / tile);
         pl[k + 1] = pl[k] + (uint32_t)((hs[k].n_pts + tile - 1) / tile);
-        cudaError_t e = cudaSuccess;
-        if (hs[k].score_out && c->grid.kind == 0)
-            e = cudaMemsetAsync(hs[k].score_out, 0, c->n_cells * 4, s);
-        if (e == cudaSuccess) e = cudaMemsetAsync(c->seg_bits, 0, c->n_words * 4, s);
-        if (e != cudaSuccess) return bfail(b, DIVAS_E_CUDA, cudaGetErrorString(e));
+        // the session's seg bitfield is set and cleared in place (it never
+        // holds a bit of an unoccupied voxel); a dense score grid is zeroed
+        // unless the caller keeps its zeros
+        if (hs[k].score_out && c->grid.kind == 0 && !keep) {
+            const cudaError_t e = cudaMemsetAsync(hs[k].score_out, 0, c->n_cells * 4, s);
+            if (e != cudaSuccess) return bfail(b, DIVAS_E_CUDA, cudaGetErrorString(e));
+        }
     }
     // the staging buffer is the one of the fuse call; the copy orders after it on the stream
     cudaError_t e = cudaMemcpyAsync(b->d_stage, b->h_stage[b->cur], b->stage_bytes,

@@ -24,10 +24,10 @@
 //    of a power of two 2^q -- chosen so that |T_z| + sum |M_z| (2g - 1) <
 //    2^(q+24) -- and a small "lo" remainder.  Every partial sum of
 //    T_hi + M_hi n is then a multiple of 2^q below 2^(q+24): the FMA chain
-//    is exact in FP32, and the lo chain adds a term of relative size 2^-36
-//    (6 FMA).  The pixel coordinates only decide which pixel is read, so
-//    they take the intrinsics-folded rows u p_z = (fx M_x + cx M_z) n +
-//    (fx T_x + cx T_z) (and likewise v) in one plain 3-FMA chain each and a
+//    is exact in FP32, and the lo chain adds a term of
+//    relative size 2^-36.  The pixel coordinates only decide which pixel is
+//    read, so they take the intrinsics-folded rows u p_z = (fx M_x + cx M_z) n
+//    + (fx T_x + cx T_z) (and likewise v) in one plain chain each and a
 //    multiply by 1 / p_z: a few ulp of |Ku n| + |Tu|, i.e. about 1e-4 pixel
 //    for the benchmark cameras, well inside the 1e-6-relative band within
 //    which a pixel decision counts as a tie.
@@ -86,12 +86,16 @@ __device__ __forceinline__ void dot3c(float a0, float a1, float a2, const float*
 // One view, passed by value inside kernel parameters.
 //   plain grid:      A = M_hi, B = M_lo (row-major 3x3), C = T_hi, E = T_lo
 //   contracted grid: A = R, C = t (B, E unused)
+// Per-view constants (120 bytes, so that a batch of 32 views stays within the
+// classic 4 KB kernel-parameter space).  Plain grids: A = (Ku, Kv, M_z hi),
+// B = M_z lo, C = (Tu, Tv, T_z hi), E = T_z lo.  Contracted grids: A = R,
+// C = t, K = (fx, fy, cx, cy); B and E are unused.
 struct ViewC {
     float A[9];
-    float B[9];
+    float B[3];
     float C[3];
-    float E[3];
-    float fx, fy, cx, cy;
+    float E;
+    float K[4];
     float Wf, Hf;    // raster size as floats (frame test)
     int32_t W;       // row pitch in elements
     int32_t mask_type;
@@ -100,12 +104,14 @@ struct ViewC {
     const float* depth;
     const void* mask;
 };
+static_assert(sizeof(ViewC) == 120, "ViewC layout");
 
 struct ViewBatch {
     int32_t n;
     int32_t pad;
     ViewC v[kMaxViews];
 };
+static_assert(sizeof(ViewBatch) <= 3900, "a view batch and the other kernel arguments fit 4 KB");
 
 struct GridC {
     float origin[3];
@@ -264,7 +270,7 @@ __device__ __forceinline__ int32_t project(const ViewC& V, const VoxelGeom& vg, 
         // depth exactly (hi + lo); the pixel rows u p_z = Ku n + Tu and
         // v p_z = Kv n + Tv in plain FMA chains (a few ulp of |Ku n| + |Tu|:
         // about 1e-4 pixel on the benchmark cameras)
-        lattice_row(V.A + 6, V.B + 6, V.C[2], V.E[2], vg.xh, pzh, pzl);
+        lattice_row(V.A + 6, V.B, V.C[2], V.E, vg.xh, pzh, pzl);
         pz = __fadd_rn(pzh, pzl);
         const float pu = __fmaf_rn(V.A[0], vg.xh[0],
                                    __fmaf_rn(V.A[1], vg.xh[1], __fmaf_rn(V.A[2], vg.xh[2], V.C[0])));
@@ -290,8 +296,8 @@ __device__ __forceinline__ int32_t project(const ViewC& V, const VoxelGeom& vg, 
     }
     const bool front = pz > z_near && pz <= FLT_MAX;
     const float inv = rcp_nr(front ? pz : 1.f);
-    u = __fmaf_rn(V.fx, __fmul_rn(px, inv), V.cx);
-    v = __fmaf_rn(V.fy, __fmul_rn(py, inv), V.cy);
+    u = __fmaf_rn(V.K[0], __fmul_rn(px, inv), V.K[2]);
+    v = __fmaf_rn(V.K[1], __fmul_rn(py, inv), V.K[3]);
     const bool in = front && u >= 0.f && u < V.Wf && v >= 0.f && v < V.Hf;
     // u, v >= 0 inside the frame: truncation is floor
     return in ? (int32_t)v * V.W + (int32_t)u : -1;

@@ -210,6 +210,26 @@ class VoxelFusion:
         for arr, n in pv.chunks:
             self._check(self.lib.divas_fuse_add_views(self._h, arr, n, s))
 
+    def update(self, views, score: torch.Tensor | None = None,
+               seg_bits: torch.Tensor | None = None, keep_zeros: bool = False, stream=None):
+        """Incremental update: fold ``views`` (a ``PreparedViews`` or one
+        ``DivasView``) onto the stored accumulators and finalize in one fusion
+        launch (``divas_fuse_update``).  ``keep_zeros``: ``score`` /
+        ``seg_bits`` already hold zeros for every unoccupied voxel (e.g. an
+        earlier result of this context for the same occupied set), so only the
+        active entries are written."""
+        flags = L.KEEP_ZEROS if keep_zeros else 0
+        s = _stream(stream)
+        if isinstance(views, L.DivasView):
+            chunks = [(ctypes.pointer(views), 1)]
+        else:
+            chunks = views.chunks
+        if len(chunks) != 1:
+            raise ValueError("update() takes up to 32 views")
+        arr, n = chunks[0]
+        self._check(self.lib.divas_fuse_update(self._h, arr, n, _ptr(score), _ptr(seg_bits), flags,
+                                               s))
+
     def finalize(self, score: bool | torch.Tensor = True, seg_bits: bool | torch.Tensor = False,
                  vmask: bool | torch.Tensor = False, count: bool = False, stream=None) -> dict:
         """Outputs as CUDA tensors: score (float32, g^3 dense or n_active sparse),
