@@ -32,10 +32,11 @@
 //    for the benchmark cameras, well inside the 1e-6-relative band within
 //    which a pixel decision counts as a tie.
 //
-//  * Contracted grids.  Centres are uncontracted in hi + lo pairs and
-//    projected with a compensated dot product (error-free products via FMA
-//    and error-free sums: Ogita, Rump and Oishi, "Accurate sum and dot
-//    product", SIAM J. Sci. Comput. 2005).
+//  * Contracted grids.  Centres are uncontracted in hi + lo pairs; the depth
+//    row is a compensated dot product (error-free products via FMA and
+//    error-free sums: Ogita, Rump and Oishi, "Accurate sum and dot product",
+//    SIAM J. Sci. Comput. 2005), the pixel rows plain FMA chains over the hi
+//    and lo parts (inside the same tie band as above).
 //
 // In both, e = (p_z,hi - D) + p_z,lo, where p_z,hi - D is exact by
 // Sterbenz's lemma whenever the depth gate can pass.
@@ -284,16 +285,17 @@ __device__ __forceinline__ int32_t project(const ViewC& V, const VoxelGeom& vg, 
         // u, v >= 0 inside the frame: truncation is floor
         return in ? (int32_t)v * V.W + (int32_t)u : -1;
     }
-    float px, py;
-    {
-        float h, l;
-        dot3c(V.A[6], V.A[7], V.A[8], vg.xh, vg.xl, V.C[2], pzh, pzl);
-        dot3c(V.A[0], V.A[1], V.A[2], vg.xh, vg.xl, V.C[0], h, l);
-        px = h;
-        dot3c(V.A[3], V.A[4], V.A[5], vg.xh, vg.xl, V.C[1], h, l);
-        py = h;
-        pz = pzh;
-    }
+    // depth compensated (hi + lo); the pixel rows in plain FMA chains over the
+    // centre's hi and lo parts: at most 6 ulp of sum |R_j x_j| + |t| (about
+    // 1e-4 at |x| = 256, i.e. < 5e-4 pixel for the benchmark cameras)
+    dot3c(V.A[6], V.A[7], V.A[8], vg.xh, vg.xl, V.C[2], pzh, pzl);
+    pz = pzh;
+    const float px = __fmaf_rn(V.A[0], vg.xh[0], __fmaf_rn(V.A[1], vg.xh[1], __fmaf_rn(
+        V.A[2], vg.xh[2], __fmaf_rn(V.A[0], vg.xl[0], __fmaf_rn(V.A[1], vg.xl[1], __fmaf_rn(
+        V.A[2], vg.xl[2], V.C[0]))))));
+    const float py = __fmaf_rn(V.A[3], vg.xh[0], __fmaf_rn(V.A[4], vg.xh[1], __fmaf_rn(
+        V.A[5], vg.xh[2], __fmaf_rn(V.A[3], vg.xl[0], __fmaf_rn(V.A[4], vg.xl[1], __fmaf_rn(
+        V.A[5], vg.xl[2], V.C[1]))))));
     const bool front = pz > z_near && pz <= FLT_MAX;
     const float inv = rcp_nr(front ? pz : 1.f);
     u = __fmaf_rn(V.K[0], __fmul_rn(px, inv), V.K[2]);
