@@ -500,9 +500,7 @@ def run_ours(args, rank, world, local_rank):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (seeded ray-cast scene; no dataset)",
-        "config": {"workload": args.workload, "description": WORKLOADS[args.workload],
-                   "grid": int(wl.grid.g), "views": S, "active_voxels": int(n_active),
-                   "voxels_nominal": int(N), "points": int(len(wl.points)),
+        "config": {**workload_config(args.workload, wl),
                    "l2": "flushed between timed steps (256 MB write, outside the timed events)",
                    "launch": "one CUDA graph replay of divas_fuse_step per step (device time "
                              "from in-graph events around it); stage times from a second graph "
@@ -770,6 +768,13 @@ def run(args):
     return 0
 
 
+def workload_config(name, wl):
+    """The config keys both arms report for a workload."""
+    return {"workload": name, "description": WORKLOADS[name], "grid": int(wl.grid.g),
+            "views": int(wl.n_views), "active_voxels": int(len(wl.active_linear())),
+            "voxels_nominal": int(wl.n_voxels), "points": int(len(wl.points))}
+
+
 def run_reference(args):
     wl = make_workload(args.workload)
     per_step = max(1.0, min(10.0, 150.0 / max(1, args.steps + args.warmup)))
@@ -784,11 +789,12 @@ def run_reference(args):
     sample = (f"each step: {det['sample_voxels']} of {det['active_voxels']} active voxels x "
               f"{wl.n_views} views + {det['sample_points']} points, extrapolated to the full "
               f"step")
-    res = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": 0,
+    res = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic (seeded ray-cast scene; no dataset)",
-           "config": {"workload": args.workload, "description": WORKLOADS[args.workload]},
+           "config": {**workload_config(args.workload, wl),
+                      "parallelism": f"oracle on {det['cores']} host cores"},
            "cpu_baseline": {"value": v, "unit": UNIT, "cores": det["cores"], "kind": "oracle",
                             "sample": sample},
            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}

@@ -49,21 +49,34 @@ struct BackPtrs {
 // ---------------------------------------------------------------------------
 // compaction
 // ---------------------------------------------------------------------------
-// sparse coordinates -> bitfield (atomic OR; duplicates merge)
+// sparse coordinates -> bitfield (atomic OR; duplicates merge).  Lanes take
+// consecutive coordinates and those that fall in the same 32-bit word OR their
+// bits together first, so a sorted (or spatially coherent) set costs one
+// atomic per word and warp instead of one per coordinate.
 __global__ void __launch_bounds__(kThreads) k_scatter_coords(const int32_t* __restrict__ coords,
                                                              int64_t n, int32_t g,
                                                              uint32_t* __restrict__ bits,
                                                              int32_t* __restrict__ status) {
-    for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < n;
-         a += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t i = __ldg(coords + 3 * a), j = __ldg(coords + 3 * a + 1),
-                      k = __ldg(coords + 3 * a + 2);
-        if (i < 0 || j < 0 || k < 0 || i >= g || j >= g || k >= g) {
-            atomicOr(status, kStatusBadCoord);
-            continue;
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) & ~(int64_t)31; base < n;
+         base += stride) {
+        const int64_t a = base + lane;
+        uint32_t word = 0xffffffffu, bit = 0u;
+        if (a < n) {
+            const int32_t i = __ldg(coords + 3 * a), j = __ldg(coords + 3 * a + 1),
+                          k = __ldg(coords + 3 * a + 2);
+            if (i < 0 || j < 0 || k < 0 || i >= g || j >= g || k >= g) {
+                atomicOr(status, kStatusBadCoord);
+            } else {
+                const int64_t lin = ((int64_t)k * g + j) * g + i;
+                word = (uint32_t)(lin >> 5);
+                bit = 1u << (lin & 31);
+            }
         }
-        const int64_t lin = ((int64_t)k * g + j) * g + i;
-        atomicOr(bits + (lin >> 5), 1u << (lin & 31));
+        const uint32_t grp = __match_any_sync(0xffffffffu, word);
+        const uint32_t orv = __reduce_or_sync(grp, bit);
+        if (word != 0xffffffffu && lane == __ffs(grp) - 1) atomicOr(bits + word, orv);
     }
 }
 

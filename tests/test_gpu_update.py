@@ -105,3 +105,19 @@ def test_batch_finalize_keep_zeros():
     b.close()
     for f in fus:
         f.close()
+
+
+def test_update_rejects_unknown_flags_and_bad_views():
+    import ctypes
+    from paper_2601_04860_b300 import _lib as L
+    from paper_2601_04860_b300.fusion import view_c
+    wl = synth.config1(g=32, n_points=100)
+    d = H.upload(wl)
+    fu = VoxelFusion(wl.grid, occ=d["occ"], params=H.to_params(oracle.Params()))
+    v = view_c(wl.cams[0], d["depth"][0], d["mask"][0], wl.mask_type)
+    lib = L.load()
+    assert lib.divas_fuse_update(fu.handle, ctypes.byref(v), 1, None, None, 2, None) == 1
+    assert lib.divas_fuse_update(fu.handle, ctypes.byref(v), 0, None, None, 0, None) == 1
+    assert lib.divas_fuse_update(fu.handle, None, 1, None, None, 0, None) == 1
+    assert fu.n_views == 0  # nothing was folded
+    fu.close()
