@@ -368,6 +368,39 @@ cudaError_t launch_fuse_chunks(int chunks, int blocks, cudaStream_t s, const uin
     return cudaGetLastError();
 }
 
+// zeros of a dense score grid's unoccupied cells for the groups of 32
+// occupancy words (1024 cells) g = gw, gw + nw, ...: one coalesced pass of
+// 16-byte stores per group and warp (x_first: the first group's word, already
+// loaded by this lane, or ~0u to load it here)
+__device__ __forceinline__ void zero_unoccupied_groups(const uint32_t* __restrict__ occ_bits,
+                                                       int64_t n_words, int64_t n_cells,
+                                                       float* __restrict__ score_out, int64_t gw,
+                                                       int64_t nw, uint32_t x_first,
+                                                       bool have_first) {
+    const int lane = threadIdx.x & 31;
+    const int64_t n_groups = (n_words + 31) / 32;
+    const bool vec = (reinterpret_cast<uintptr_t>(score_out) & 15) == 0;
+    for (int64_t g = gw; g < n_groups; g += nw) {
+        const int64_t w = g * 32 + lane;
+        const uint32_t x = (g == gw && have_first) ? x_first
+                                                   : (w < n_words ? __ldg(occ_bits + w) : 0u);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int f4 = q * 32 + lane;  // float4 index inside the group
+            const uint32_t xw = __shfl_sync(0xffffffffu, x, f4 >> 3);
+            const uint32_t nib = (xw >> ((f4 & 7) * 4)) & 0xfu;
+            const int64_t cell = g * 1024 + 4 * f4;
+            if (nib == 0u && vec && cell + 4 <= n_cells) {
+                __stcs(reinterpret_cast<float4*>(score_out + cell), make_float4(0.f, 0.f, 0.f, 0.f));
+            } else {
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    if (!((nib >> k) & 1u) && cell + k < n_cells) score_out[cell + k] = 0.f;
+            }
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // finalize
 // ---------------------------------------------------------------------------
@@ -484,29 +517,8 @@ __global__ void __launch_bounds__(kThreads, kContracted ? 4 : 6) k_fuse_fin(
         }
         seg_epilogue(live, seg, lin, seg_bits, clear_bits != 0, seg_out, clear_out != 0);
     }
-    if (!zero_unoccupied) return;
-    // zeros of a dense score grid's unoccupied cells, one group of 32 words
-    // (1024 cells) per warp and round: coalesced 16-byte stores that need no
-    // result (the occupied cells got their P above, possibly from other warps)
-    const bool vec = (reinterpret_cast<uintptr_t>(score_out) & 15) == 0;
-    for (int64_t g = gw; g < n_groups; g += nw) {
-        const int64_t w = g * 32 + lane;
-        const uint32_t x = g == gw ? x_first : (w < n_words ? __ldg(occ_bits + w) : 0u);
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const int f4 = q * 32 + lane;  // float4 index inside the group
-            const uint32_t xw = __shfl_sync(0xffffffffu, x, f4 >> 3);
-            const uint32_t nib = (xw >> ((f4 & 7) * 4)) & 0xfu;
-            const int64_t cell = g * 1024 + 4 * f4;
-            if (nib == 0u && vec && cell + 4 <= n_cells) {
-                __stcs(reinterpret_cast<float4*>(score_out + cell), make_float4(0.f, 0.f, 0.f, 0.f));
-            } else {
-#pragma unroll
-                for (int k = 0; k < 4; ++k)
-                    if (!((nib >> k) & 1u) && cell + k < n_cells) score_out[cell + k] = 0.f;
-            }
-        }
-    }
+    if (zero_unoccupied)
+        zero_unoccupied_groups(occ_bits, n_words, n_cells, score_out, gw, nw, x_first, true);
 }
 
 // ---------------------------------------------------------------------------
@@ -904,12 +916,10 @@ ViewC make_view(const divas_camera& cam, const GridC& G, const float* depth, con
     v.K[1] = cam.fy;
     v.K[2] = cam.cx;
     v.K[3] = cam.cy;
-    v.Wf = (float)cam.W;
-    v.Hf = (float)cam.H;
     v.W = cam.W;
+    v.H = cam.H;
     v.mask_type = mask_type;
     v.bit = index < 32 ? (1u << index) : 0u;
-    v.pad = 0;
     v.depth = depth;
     v.mask = mask;
     return v;
@@ -1189,6 +1199,18 @@ static divas_status record_stage(divas_ctx* c, void* const* events, int k, cudaS
     return DIVAS_OK;
 }
 
+// labels of n > 0 points
+static divas_status launch_label(divas_ctx* c, const float* xyz, int64_t n, uint8_t* labels_out,
+                                 cudaStream_t s) {
+    const int blocks = grid_for((n + 3) / 4, c->sm_count, 64);
+    if (!c->G.contracted && c->G.inv_h != 0.f)
+        k_label<true><<<blocks, kThreads, 0, s>>>(xyz, n, c->G, c->seg_bits, labels_out);
+    else
+        k_label<false><<<blocks, kThreads, 0, s>>>(xyz, n, c->G, c->seg_bits, labels_out);
+    DIVAS_LAUNCHED(c, "k_label");
+    return DIVAS_OK;
+}
+
 // validate views and build their constants (view bits continue the context's count)
 static divas_status make_batch(divas_ctx* c, const divas_view* views, int32_t n_views,
                                int32_t first_view, ViewBatch& vb) {
@@ -1344,7 +1366,7 @@ divas_status divas_fuse_step_profiled(divas_ctx* c, const uint8_t* occ_dense,
     st = record_stage(c, stage_events, 2, s);
     if (st != DIVAS_OK) return st;
     if (n_pts > 0) {
-        st = divas_label_points(c, xyz, n_pts, labels_out, stream);
+        st = launch_label(c, xyz, n_pts, labels_out, s);
         if (st != DIVAS_OK) return st;
     }
     return record_stage(c, stage_events, 3, s);
@@ -1377,13 +1399,7 @@ divas_status divas_label_points(divas_ctx* c, const float* xyz, int64_t n, uint8
     if (n < 0 || (n > 0 && (!xyz || !labels_out)))
         return fail(c, DIVAS_E_INVALID, "bad point arguments");
     if (n == 0) return DIVAS_OK;
-    const int blocks = grid_for((n + 3) / 4, c->sm_count, 64);
-    if (!c->G.contracted && c->G.inv_h != 0.f)
-        k_label<true><<<blocks, kThreads, 0, S(stream)>>>(xyz, n, c->G, c->seg_bits, labels_out);
-    else
-        k_label<false><<<blocks, kThreads, 0, S(stream)>>>(xyz, n, c->G, c->seg_bits, labels_out);
-    DIVAS_LAUNCHED(c, "k_label");
-    return DIVAS_OK;
+    return launch_label(c, xyz, n, labels_out, S(stream));
 }
 
 divas_status divas_fuse_reset(divas_ctx* c, void* stream) {

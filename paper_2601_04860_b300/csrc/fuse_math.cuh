@@ -87,7 +87,7 @@ __device__ __forceinline__ void dot3c(float a0, float a1, float a2, const float*
 // One view, passed by value inside kernel parameters.
 //   plain grid:      A = M_hi, B = M_lo (row-major 3x3), C = T_hi, E = T_lo
 //   contracted grid: A = R, C = t (B, E unused)
-// Per-view constants (120 bytes, so that a batch of 32 views stays within the
+// Per-view constants (112 bytes, so that a batch of 32 views stays within the
 // classic 4 KB kernel-parameter space).  Plain grids: A = (Ku, Kv, M_z hi),
 // B = M_z lo, C = (Tu, Tv, T_z hi), E = T_z lo.  Contracted grids: A = R,
 // C = t, K = (fx, fy, cx, cy); B and E are unused.
@@ -97,15 +97,23 @@ struct ViewC {
     float C[3];
     float E;
     float K[4];
-    float Wf, Hf;    // raster size as floats (frame test)
-    int32_t W;       // row pitch in elements
+    int32_t W, H;    // raster size (W is the row pitch in elements)
     int32_t mask_type;
     uint32_t bit;    // 1 << view index, 0 from view 32 on
-    int32_t pad;
     const float* depth;
     const void* mask;
 };
-static_assert(sizeof(ViewC) == 120, "ViewC layout");
+static_assert(sizeof(ViewC) == 112, "ViewC layout");
+
+// pixel index of (u, v) -- finite, as they are in front of the camera -- or -1
+// outside the half-open frame [0, W) x [0, H): floor(u) in [0, W) iff
+// 0 <= u < W, so one unsigned compare per axis on the floor conversions that
+// the index needs anyway (saturated conversions of huge values fall outside)
+__device__ __forceinline__ int32_t pixel_index(const ViewC& V, bool front, float u, float v) {
+    const int32_t iu = __float2int_rd(u), iv = __float2int_rd(v);
+    const bool in = front && (uint32_t)iu < (uint32_t)V.W && (uint32_t)iv < (uint32_t)V.H;
+    return in ? iv * V.W + iu : -1;
+}
 
 struct ViewBatch {
     int32_t n;
@@ -281,9 +289,7 @@ __device__ __forceinline__ int32_t project(const ViewC& V, const VoxelGeom& vg, 
         const float inv = rcp_nr(front ? pz : 1.f);
         u = __fmul_rn(pu, inv);
         v = __fmul_rn(pv, inv);
-        const bool in = front && u >= 0.f && u < V.Wf && v >= 0.f && v < V.Hf;
-        // u, v >= 0 inside the frame: truncation is floor
-        return in ? (int32_t)v * V.W + (int32_t)u : -1;
+        return pixel_index(V, front, u, v);
     }
     // depth compensated (hi + lo); the pixel rows in plain FMA chains over the
     // centre's hi and lo parts: at most 6 ulp of sum |R_j x_j| + |t| (about
@@ -300,9 +306,7 @@ __device__ __forceinline__ int32_t project(const ViewC& V, const VoxelGeom& vg, 
     const float inv = rcp_nr(front ? pz : 1.f);
     u = __fmaf_rn(V.K[0], __fmul_rn(px, inv), V.K[2]);
     v = __fmaf_rn(V.K[1], __fmul_rn(py, inv), V.K[3]);
-    const bool in = front && u >= 0.f && u < V.Wf && v >= 0.f && v < V.Hf;
-    // u, v >= 0 inside the frame: truncation is floor
-    return in ? (int32_t)v * V.W + (int32_t)u : -1;
+    return pixel_index(V, front, u, v);
 }
 
 // ---------------------------------------------------------------------------
