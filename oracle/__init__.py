@@ -65,6 +65,21 @@ class _Params(ctypes.Structure):
                 ("tau_m", "gamma", "alpha1", "tau_cons", "eps", "z_near", "logit_tau")]
 
 
+class _TView(ctypes.Structure):
+    _fields_ = [("R", ctypes.c_float * 9), ("t", ctypes.c_float * 3), ("fx", ctypes.c_float),
+                ("fy", ctypes.c_float), ("cx", ctypes.c_float), ("cy", ctypes.c_float),
+                ("W", ctypes.c_int32), ("H", ctypes.c_int32), ("d_min", ctypes.c_void_p),
+                ("d_med", ctypes.c_void_p), ("d_max", ctypes.c_void_p),
+                ("n_samp", ctypes.c_void_p), ("mask", ctypes.c_void_p),
+                ("d_cam", ctypes.c_double)]
+
+
+class _TParams(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in
+                ("beta", "gamma_st", "tau_thin", "rho_cover", "rho_occ", "n_abs", "dist_gate",
+                 "behind_margin", "k_dg", "rho_thin")]
+
+
 def _configure(lib):
     P = ctypes.c_void_p
     I = ctypes.c_int
@@ -80,6 +95,8 @@ def _configure(lib):
     lib.oracle_project.restype = None
     lib.oracle_set_threads.argtypes = [I]
     lib.oracle_set_threads.restype = I
+    lib.oracle_fuse_tuple.argtypes = [I, P, D, I, L, P, P, I, P, I, P, P, P, P, P, P, P, P, P, P]
+    lib.oracle_fuse_tuple.restype = None
     return lib
 
 
@@ -129,6 +146,59 @@ class Params:
     def _c(self) -> _Params:
         return _Params(self.tau_m, self.gamma, self.alpha1, self.tau_cons, self.eps, self.z_near,
                        self.logit_tau())
+
+
+@dataclass
+class TupleParams:
+    """Depth-tuple-mode constants (Table gs-hyperparams: beta 0.05, gamma_st
+    1.5, tau_thin 0.6, rho_cover 0.5, rho_occ 0.1, n_abs 25, the 1.5 h_v
+    distance gate and the 2 h_v behind margin).  k_dg (the depth-gradient
+    factor's decay, App. D, "k > 0" without a value) and rho_thin (the thin
+    path's density floor, no 2DGS value) are readings: k_dg = 0 (pi_dg = 1)
+    and rho_thin = 1 (every voxel of a binary prior is eligible)."""
+
+    beta: float = 0.05
+    gamma_st: float = 1.5
+    tau_thin: float = 0.6
+    rho_cover: float = 0.5
+    rho_occ: float = 0.1
+    n_abs: float = 25.0
+    dist_gate: float = 1.5
+    behind_margin: float = 2.0
+    k_dg: float = 0.0
+    rho_thin: float = 1.0
+
+    def f32(self) -> "TupleParams":
+        return TupleParams(*[float(np.float32(getattr(self, f))) for f in
+                             self.__dataclass_fields__])
+
+    def _c(self) -> _TParams:
+        return _TParams(*[float(getattr(self, f)) for f in self.__dataclass_fields__])
+
+
+def _tviews(cams, tup, masks):
+    arr = (_TView * len(cams))()
+    keep = []
+    for i, cam in enumerate(cams):
+        ras = [np.ascontiguousarray(tup[k][i], np.float32) for k in ("d_min", "d_med", "d_max")]
+        n = np.ascontiguousarray(tup["n_samp"][i], np.uint16)
+        m = np.ascontiguousarray(masks[i])
+        keep += ras + [n, m]
+        v = arr[i]
+        R = np.asarray(cam.R, np.float32).reshape(-1)
+        for k in range(9):
+            v.R[k] = float(R[k])
+        for k in range(3):
+            v.t[k] = float(np.asarray(cam.t, np.float32)[k])
+        v.fx, v.fy, v.cx, v.cy = cam.fx, cam.fy, cam.cx, cam.cy
+        v.W, v.H = cam.W, cam.H
+        for r in ras + [n, m]:
+            assert r.shape == (cam.H, cam.W)
+        v.d_min, v.d_med, v.d_max = (r.ctypes.data for r in ras)
+        v.n_samp = n.ctypes.data
+        v.mask = m.ctypes.data
+        v.d_cam = float(np.float32(tup["d_cam"][i]))
+    return arr, keep
 
 
 def _views(cams, depths, masks):
@@ -186,6 +256,33 @@ class OracleApi:
         del keep
         if want_pix:
             out["pix"] = pix
+        return out
+
+    def fuse_tuple(self, grid, lin, cams, tup, masks, mask_type, params: Params | None = None,
+                   tparams: TupleParams | None = None, rho=None) -> dict:
+        """Depth-tuple-mode fusion (thick path with the tuple gates + thin path)
+        of views with rasters ``tup`` (dict of per-view lists d_min, d_med,
+        d_max, n_samp and per-view d_cam) into the voxels ``lin``.  Returns
+        float64 W, Z, P; uint8 seg; uint32 bits, flags; uint8 kind (n_vox x
+        n_views: 0 no vote, 1 thick, 2 thin); float64 thin (thin score t)."""
+        params = params or Params()
+        tparams = tparams or TupleParams()
+        lin = np.ascontiguousarray(lin, np.int64)
+        n = len(lin)
+        g, origin, h, contracted = _grid_args(grid)
+        views, keep = _tviews(cams, tup, masks)
+        rho = None if rho is None else np.ascontiguousarray(rho, np.float64)
+        out = dict(W=np.empty(n), Z=np.empty(n), P=np.empty(n), seg=np.empty(n, np.uint8),
+                   bits=np.empty(n, np.uint32), flags=np.empty(n, np.uint32),
+                   kind=np.empty((n, len(cams)), np.uint8), thin=np.empty((n, len(cams))))
+        pr = params._c()
+        tp = tparams._c()
+        self.lib.oracle_fuse_tuple(g, _p(origin), h, contracted, n, _p(lin), _p(rho), len(cams),
+                                   views, int(mask_type), ctypes.byref(pr), ctypes.byref(tp),
+                                   _p(out["W"]), _p(out["Z"]), _p(out["P"]), _p(out["seg"]),
+                                   _p(out["bits"]), _p(out["flags"]), _p(out["kind"]),
+                                   _p(out["thin"]))
+        del keep
         return out
 
     def fuse_grad(self, grid, lin, cams, depths, masks, mask_type, gP, params: Params | None = None):
@@ -258,6 +355,10 @@ def fuse(*a, **k):
 
 def fuse_grad(*a, **k):
     return _api().fuse_grad(*a, **k)
+
+
+def fuse_tuple(*a, **k):
+    return _api().fuse_tuple(*a, **k)
 
 
 def label(*a, **k):

@@ -163,3 +163,156 @@ def label(grid, seg_dense, xyz):
         i, j, k = (int(np.floor(c)) for c in s)
         out[a] = seg_dense[(k * g + j) * g + i]
     return out
+
+
+def _mask_prob(mask, mask_type):
+    """Per-pixel probability and the strict half test, as float64 arrays."""
+    if mask_type == 1:    # binary16 bits
+        m = mask.view(np.float16).astype(np.float64) if mask.dtype != np.float16 \
+            else mask.astype(np.float64)
+        return m, m > 0.5
+    if mask_type == 2:    # logits
+        lg = mask.astype(np.float64)
+        return 1.0 / (1.0 + np.exp(-lg)), lg > 0.0
+    m = mask.astype(np.float64)
+    return m, m > 0.5
+
+
+def fuse_tuple(grid, lin, cams, tup, masks, mask_type, tau_m=0.5, gamma=1.0, alpha1=0.5,
+               tau_cons=0.5, eps=1e-12, z_near=1e-6, beta=0.05, gamma_st=1.5, tau_thin=0.6,
+               rho_cover=0.5, rho_occ=0.1, n_abs=25.0, dist_gate=1.5, behind_margin=2.0,
+               k_dg=0.0, rho_thin=1.0, rho=None):
+    """Depth-tuple-mode fusion written out per voxel and view with NumPy
+    slices (Sec. 3.5, Algorithms "Thick-Structure Segmentation for 2DGS" and
+    "Thin-Structure Segmentation for 2DGS", App. B.5): footprint statistics
+    by summing the footprint slice (no integral image), the layered test as
+    n > mean + std in float64, the ray geometry through explicit vectors
+    (camera centre, unit ray direction, closest clamped point), unprojection
+    through the inverse intrinsics.  Small inputs only (a Python loop).
+
+    Returns W, Z, P, seg, bits, kind (n x views: 0 / 1 thick / 2 thin)."""
+    x, hvs, ok = voxel_centres(grid, lin)
+    n_v = len(cams)
+    N = len(lin)
+    W = np.zeros(N)
+    Z = np.zeros(N)
+    bits = np.zeros(N, np.uint32)
+    kind = np.zeros((N, n_v), np.uint8)
+    logit_tau = -np.inf if tau_m <= 0 else (np.inf if tau_m >= 1 else
+                                            float(np.float32(np.log(tau_m / (1 - tau_m)))))
+    per_view = []
+    for i, cam in enumerate(cams):
+        R = np.asarray(cam.R, np.float32).astype(np.float64).reshape(3, 3)
+        t = np.asarray(cam.t, np.float32).astype(np.float64)
+        o = -R.T @ t
+        mprob, mhalf = _mask_prob(np.asarray(masks[i]), mask_type)
+        raw = np.asarray(masks[i])
+        if mask_type == 1:
+            gate = mprob >= tau_m
+        elif mask_type == 2:
+            gate = raw.astype(np.float64) >= logit_tau
+        else:
+            gate = mprob >= tau_m
+        dmin = tup["d_min"][i].astype(np.float64)
+        dmax = tup["d_max"][i].astype(np.float64)
+        cen = 0.5 * (dmin + dmax)
+        cp = np.pad(cen, 1, mode="edge")
+        gx = cp[1:-1, 2:] - cp[1:-1, :-2]
+        gy = cp[2:, 1:-1] - cp[:-2, 1:-1]
+        fin = np.isfinite(cp[1:-1, 2:]) & np.isfinite(cp[1:-1, :-2]) & \
+            np.isfinite(cp[2:, 1:-1]) & np.isfinite(cp[:-2, 1:-1])
+        with np.errstate(invalid="ignore", over="ignore"):
+            pig = np.where(fin, np.exp(-k_dg * (gx * gx + gy * gy)), 0.0) if k_dg else \
+                np.ones_like(cen)
+        per_view.append((R, t, o, mprob, mhalf, gate, dmin, tup["d_med"][i].astype(np.float64),
+                         dmax, tup["n_samp"][i].astype(np.int64), pig,
+                         float(np.float32(tup["d_cam"][i]))))
+    signs = np.array([[sx, sy, sz] for sz in (-0.5, 0.5) for sy in (-0.5, 0.5)
+                      for sx in (-0.5, 0.5)])
+    for a in range(N):
+        if not ok[a]:
+            continue
+        hv = hvs[a]
+        xc = x[a]
+        rv = 1.0 if rho is None else float(rho[a])
+        for i, cam in enumerate(cams):
+            R, t, o, mprob, mhalf, gate, dmin, dmed, dmax, ns, pig, dcam = per_view[i]
+            fx, fy, cx, cy = (float(np.float32(v)) for v in (cam.fx, cam.fy, cam.cx, cam.cy))
+            pc = R @ xc + t
+            corners = R @ (xc[None, :] + signs * hv).T + t[:, None]
+            if pc[2] <= z_near or np.any(corners[2] <= z_near):
+                continue
+            u = fx * pc[0] / pc[2] + cx
+            v = fy * pc[1] / pc[2] + cy
+            if not (0 <= u < cam.W and 0 <= v < cam.H):
+                continue
+            cu = fx * corners[0] / corners[2] + cx
+            cv = fy * corners[1] / corners[2] + cy
+            i0, i1 = max(int(np.floor(cu.min())), 0), min(int(np.floor(cu.max())), cam.W - 1)
+            j0, j1 = max(int(np.floor(cv.min())), 0), min(int(np.floor(cv.max())), cam.H - 1)
+            area = (min(cu.max(), cam.W) - max(cu.min(), 0.0)) * \
+                (min(cv.max(), cam.H) - max(cv.min(), 0.0))
+            fp = ns[j0:j1 + 1, i0:i1 + 1].astype(np.float64)
+            mean = fp.mean()
+            std = np.sqrt(max((fp * fp).mean() - mean * mean, 0.0))
+            ix, iy = int(np.floor(u)), int(np.floor(v))
+            d_lo, d_me, d_hi, n_c = dmin[iy, ix], dmed[iy, ix], dmax[iy, ix], ns[iy, ix]
+            trusted = d_lo <= d_me
+            seethru = d_me > gamma_st * dcam
+            front = (n_c > mean + std or seethru) and trusted
+            xd = pc[2]
+            dist = np.linalg.norm(xc - o)
+            dhat = (xc - o) / dist
+            cos = float(R[2] @ dhat)
+            voted = False
+            if gate[iy, ix] and trusted and all(np.isfinite([d_lo, d_me, d_hi])) and \
+                    min(d_lo, d_me, d_hi) > 0:
+                ref = d_lo if front else d_me
+                th = min(max(dist, d_lo / cos), ref / cos)
+                closest = o + th * dhat
+                tdep = gamma * hv / (1.0 + beta * max(n_c - mean, 0.0))
+                ok_d = (xd - d_lo <= tdep) if front else (abs(xd - d_me) <= tdep)
+                if np.linalg.norm(xc - closest) <= hv * pig[iy, ix] and ok_d:
+                    ctr = 0.5 * (d_lo + d_hi) / cos
+                    hw = max(0.5 * (d_hi - d_lo) / cos, eps)
+                    w = np.exp(-alpha1 * ((th - ctr) / hw) ** 2)
+                    W[a] += mprob[iy, ix] * w
+                    Z[a] += w
+                    bits[a] |= np.uint32(1 << i) if i < 32 else np.uint32(0)
+                    kind[a, i] = 1
+                    voted = True
+            surf = d_lo if (trusted and seethru) else d_me
+            if voted or xd > surf + behind_margin * hv or not (rv >= rho_thin):
+                continue
+            n_depth = n_md = 0
+            m_max = 0.0
+            d2 = np.inf
+            Kinv = np.array([[1 / fx, 0, -cx / fx], [0, 1 / fy, -cy / fy], [0, 0, 1]])
+            for yy in range(j0, j1 + 1):
+                for xx in range(i0, i1 + 1):
+                    q_lo, q_me, nq = dmin[yy, xx], dmed[yy, xx], ns[yy, xx]
+                    if q_me < eps:
+                        continue
+                    tq = gamma * hv / (1.0 + beta * max(nq - mean, 0.0))
+                    fq = (nq > mean + std or q_me > gamma_st * dcam) and q_lo <= q_me
+                    ok_q = (xd - q_lo <= tq) if fq else (abs(xd - q_me) <= tq)
+                    if not ok_q:
+                        continue
+                    n_depth += 1
+                    if not mhalf[yy, xx]:
+                        continue
+                    n_md += 1
+                    m_max = max(m_max, mprob[yy, xx])
+                    dq = q_lo if fq else q_me
+                    pcam = Kinv @ np.array([xx + 0.5, yy + 0.5, 1.0]) * dq
+                    pw = R.T @ (pcam - t)
+                    d2 = min(d2, float(np.sum((pw - xc) ** 2)))
+            tt = m_max if (n_depth >= max(n_abs, np.ceil(rho_occ * area)) and
+                           n_md >= rho_cover * n_depth and d2 <= (dist_gate * hv) ** 2) else 0.0
+            if tt >= tau_thin:
+                W[a] += tt
+                Z[a] += 1.0
+                bits[a] |= np.uint32(1 << i) if i < 32 else np.uint32(0)
+                kind[a, i] = 2
+    P = np.where(Z > eps, W / np.where(Z > eps, Z, 1.0), 0.0)
+    return dict(W=W, Z=Z, P=P, seg=(P >= tau_cons).astype(np.uint8), bits=bits, kind=kind)

@@ -359,3 +359,297 @@ int oracle_set_threads(int n) {
     return 1;
 #endif
 }
+
+/* ==========================================================================
+ * Depth-tuple mode (Sec. 3.5 "Footprint statistics" .. "Thin-structure
+ * path"; Algorithm "Thick-Structure Segmentation for 2DGS" and Algorithm
+ * "Thin-Structure Segmentation for 2DGS" in Appendix B.5).
+ *
+ * Per voxel v (centre x, edge h_v, density rho_v) and view i in index order,
+ * with o_i the camera centre, x_d = p_z the voxel's planar depth, t* = |x - o_i|
+ * its distance along the ray through its own projection (the ray direction
+ * d_hat runs through the projected point, so x lies on it and the planar-to-ray
+ * factor is 1 / cos(theta) = t* / x_d):
+ *
+ *   skip unless the centre and all 8 corners x +- h_v/2 are in front
+ *   (p_z > z_near) and the centre projects in frame;
+ *   footprint B = pixels floor(u_min)..floor(u_max) x floor(v_min)..floor(v_max)
+ *     of the corners' projections, clipped to the image; A = |B|,
+ *     S1 = sum n_samp, S2 = sum n_samp^2 over B (the four-corner integral-image
+ *     query); A_B = (u_max - u_min)(v_max - v_min) of the box clipped to
+ *     [0, W] x [0, H];
+ *   layered(n) = n > mean + sigma (mean = S1/A, sigma^2 = S2/A - mean^2), decided
+ *     exactly on integers: n A - S1 > 0 and (n A - S1)^2 > A S2 - S1^2;
+ *   E(n) = max(n - mean, 0);  t_depth(n) = gamma h_v / (1 + beta E(n))  (Eq. tightening)
+ *   at the centre pixel: trusted = d_min <= d_med, seethru = d_med > gamma_st d_cam,
+ *     front = (layered(n) or seethru) and trusted              (Eq. seethrough)
+ *   thick path (m >= tau_m, trusted, all three depths finite and > 0):
+ *     d_ref = front ? d_min : d_med;  t_hat = clip(t*, d_min^ray, d_ref^ray);
+ *     spatial: |t* - t_hat| <= h_v pi_dg   (Eq. gs-spatial; |x - (o + t_hat d_hat)|)
+ *     depth:   front ? x_d - d_min <= t_depth : |x_d - d_med| <= t_depth  (Eq. asym-gate)
+ *     vote:    w = exp(-alpha1 ((t_hat - d_ctr) / d_hw)^2), d_ctr = (d_min^ray + d_max^ray)/2,
+ *              d_hw = max((d_max^ray - d_min^ray)/2, eps)         (Eq. gs-depthweight)
+ *              W += m w, Z += w, bits |= 1 << i                   (Eq. vmask)
+ *   behind: d_surf = (trusted and seethru) ? d_min : d_med;
+ *           behind_fail = x_d > d_surf + behind_margin h_v        (Eq. behind-gate)
+ *   thin path (no thick vote, not behind_fail, rho_v >= rho_thin):
+ *     per pixel q of B with not (d_med(q) < eps): front(q) as above with q's own
+ *     values; valid = front(q) ? x_d - d_min(q) <= t_depth(n(q)) : |x_d - d_med(q)|
+ *     <= t_depth(n(q)); valid -> n_depth += 1; valid and m(q) > 1/2 -> n_md += 1,
+ *     m_max = max(m_max, m(q)), d2 = min(d2, |unproject(q, front(q) ? d_min(q) :
+ *     d_med(q)) - x|^2) (pixel centre, planar depth)         (Eq. thin-d2min)
+ *     t = m_max if n_depth >= max(n_abs, ceil(rho_occ A_B)), n_md >= rho_cover n_depth
+ *         and d2 <= (dist_gate h_v)^2, else 0        (Eqs. thin-nmin, gs-coverage, thin-tthin-gs)
+ *     t >= tau_thin -> W += t, Z += 1, bits |= 1 << i         (Eq. compact-fusion)
+ *   pi_dg at pixel (x, y) = exp(-k G), G = g_x^2 + g_y^2 of c = (d_min + d_max)/2 by
+ *   central differences, clamped at the border; G = inf (pi = 0) when a used c is
+ *   not finite; pi = 1 when k = 0 (App. D).
+ *
+ * parity: pinned by the tuple-mode tests (closed-form single-voxel cases of
+ * every gate, exact integer footprint statistics, an independent NumPy
+ * statement on small scenes).
+ * ========================================================================== */
+
+enum { FLAG_TUPLE = 32 }; /* a tuple-mode gate (spatial, depth, behind, thin, footprint) near flipping */
+
+typedef struct {
+    float R[9], t[3], fx, fy, cx, cy;
+    int32_t W, H;
+    const float* d_min;
+    const float* d_med;
+    const float* d_max;
+    const uint16_t* n_samp;
+    const void* mask;
+    double d_cam;
+} oracle_tview;
+
+typedef struct {
+    double beta, gamma_st, tau_thin, rho_cover, rho_occ, n_abs, dist_gate, behind_margin, k_dg,
+        rho_thin;
+} oracle_tparams;
+
+/* mask probability at p (and the thick-entry gate m >= tau_m) */
+static void tmask_at(const oracle_tview* vw, int mask_type, int64_t p, const oracle_params* pr,
+                     double* m, int* pass, int* half) {
+    if (mask_type == MASK_F16) {
+        *m = half_to_double(((const uint16_t*)vw->mask)[p]);
+        *pass = *m >= pr->tau_m;
+        *half = *m > 0.5;
+    } else if (mask_type == MASK_LOGIT_F32) {
+        double l = ((const float*)vw->mask)[p];
+        *m = 1.0 / (1.0 + exp(-l));
+        *pass = l >= pr->logit_tau;
+        *half = l > 0.0; /* sigmoid(l) > 1/2 exactly when l > 0 */
+    } else {
+        *m = ((const float*)vw->mask)[p];
+        *pass = *m >= pr->tau_m;
+        *half = *m > 0.5;
+    }
+}
+
+static double centre_depth(const oracle_tview* vw, int x, int y) {
+    if (x < 0) x = 0;
+    if (x > vw->W - 1) x = vw->W - 1;
+    if (y < 0) y = 0;
+    if (y > vw->H - 1) y = vw->H - 1;
+    int64_t q = (int64_t)y * vw->W + x;
+    return 0.5 * ((double)vw->d_min[q] + (double)vw->d_max[q]);
+}
+
+static double pi_dg(const oracle_tview* vw, int x, int y, double k) {
+    if (k == 0.0) return 1.0;
+    double a = centre_depth(vw, x + 1, y), b = centre_depth(vw, x - 1, y);
+    double c = centre_depth(vw, x, y + 1), d = centre_depth(vw, x, y - 1);
+    if (!(isfinite(a) && isfinite(b) && isfinite(c) && isfinite(d))) return 0.0;
+    double gx = a - b, gy = c - d;
+    return exp(-k * (gx * gx + gy * gy));
+}
+
+/* n > mean + sigma over a footprint of A pixels with sums S1, S2, exactly */
+static int layered_exact(int64_t n, int64_t A, int64_t S1, int64_t S2) {
+    int64_t d = n * A - S1;
+    if (d <= 0) return 0;
+    return (__int128)d * d > (__int128)A * S2 - (__int128)S1 * S1;
+}
+
+static void near_flag(double lhs, double rhs, double scale, uint32_t* flags) {
+    if (fabs(lhs - rhs) < ORACLE_MARGIN * (scale + 1e-30)) *flags |= FLAG_TUPLE;
+}
+
+void oracle_fuse_tuple(int g, const double* origin, double h, int contracted, int64_t n_vox,
+                       const int64_t* lin, const double* rho, int n_views,
+                       const oracle_tview* views, int mask_type, const oracle_params* pr,
+                       const oracle_tparams* tp, double* W_out, double* Z_out, double* P_out,
+                       uint8_t* seg_out, uint32_t* bits_out, uint32_t* flags_out,
+                       uint8_t* kind_out, double* thin_out) {
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t a = 0; a < n_vox; ++a) {
+        uint32_t flags = 0, bits = 0;
+        double Wsum = 0.0, Zsum = 0.0;
+        double x[3], hv;
+        int ok = voxel_centre(lin[a], g, origin, h, contracted, x, &hv, &flags);
+        double rho_v = rho ? rho[a] : 1.0;
+        for (int i = 0; i < n_views; ++i) {
+            if (kind_out) kind_out[a * n_views + i] = 0;
+            if (thin_out) thin_out[a * n_views + i] = 0.0;
+            if (!ok) continue;
+            const oracle_tview* vw = &views[i];
+            const float* R = vw->R;
+            /* centre: camera coordinates and pixel */
+            double p[3];
+            int ix, iy;
+            oracle_view pv = {{0}, {0}, vw->fx, vw->fy, vw->cx, vw->cy, vw->W, vw->H, NULL, NULL};
+            memcpy(pv.R, vw->R, sizeof(pv.R));
+            memcpy(pv.t, vw->t, sizeof(pv.t));
+            int in = project(&pv, x, pr->z_near, p, &ix, &iy, &flags);
+            /* corners: all in front, the footprint box of their projections */
+            double umin = INFINITY, umax = -INFINITY, vmin = INFINITY, vmax = -INFINITY;
+            int corners_ok = 1;
+            for (int c = 0; c < 8; ++c) {
+                double xc[3] = {x[0] + ((c & 1) ? 0.5 : -0.5) * hv,
+                                x[1] + ((c & 2) ? 0.5 : -0.5) * hv,
+                                x[2] + ((c & 4) ? 0.5 : -0.5) * hv};
+                double q[3];
+                for (int r = 0; r < 3; ++r)
+                    q[r] = (double)R[3 * r] * xc[0] + (double)R[3 * r + 1] * xc[1] +
+                           (double)R[3 * r + 2] * xc[2] + vw->t[r];
+                near_flag(q[2], pr->z_near, fabs(q[2]) + 1.0, &flags);
+                if (!(q[2] > pr->z_near)) { corners_ok = 0; break; }
+                double u = (double)vw->fx * q[0] / q[2] + (double)vw->cx;
+                double v = (double)vw->fy * q[1] / q[2] + (double)vw->cy;
+                double su = 1.0 + fabs((double)vw->cx) + fabs(u - (double)vw->cx);
+                double sv = 1.0 + fabs((double)vw->cy) + fabs(v - (double)vw->cy);
+                if (dist_to_int(u) < ORACLE_MARGIN * su || dist_to_int(v) < ORACLE_MARGIN * sv)
+                    flags |= FLAG_TUPLE;
+                umin = fmin(umin, u); umax = fmax(umax, u);
+                vmin = fmin(vmin, v); vmax = fmax(vmax, v);
+            }
+            if (!in || !corners_ok) continue;
+            double cu0 = fmax(umin, 0.0), cu1 = fmin(umax, (double)vw->W);
+            double cv0 = fmax(vmin, 0.0), cv1 = fmin(vmax, (double)vw->H);
+            int i0 = (int)fmax(floor(umin), 0.0), i1 = (int)fmin(floor(umax), vw->W - 1.0);
+            int j0 = (int)fmax(floor(vmin), 0.0), j1 = (int)fmin(floor(vmax), vw->H - 1.0);
+            int64_t A = (int64_t)(i1 - i0 + 1) * (j1 - j0 + 1), S1 = 0, S2 = 0;
+            for (int yy = j0; yy <= j1; ++yy)
+                for (int xx = i0; xx <= i1; ++xx) {
+                    int64_t nn = vw->n_samp[(int64_t)yy * vw->W + xx];
+                    S1 += nn;
+                    S2 += nn * nn;
+                }
+            double mean = (double)S1 / (double)A;
+            double A_B = (cu1 - cu0) * (cv1 - cv0);
+            /* centre pixel */
+            int64_t pix = (int64_t)iy * vw->W + ix;
+            double dmin = vw->d_min[pix], dmed = vw->d_med[pix], dmax = vw->d_max[pix];
+            int64_t n = vw->n_samp[pix];
+            double m;
+            int pass, half;
+            tmask_at(vw, mask_type, pix, pr, &m, &pass, &half);
+            double xd = p[2];
+            double oc[3];
+            for (int r = 0; r < 3; ++r)  /* o = -R^T t */
+                oc[r] = -((double)R[r] * vw->t[0] + (double)R[3 + r] * vw->t[1] +
+                          (double)R[6 + r] * vw->t[2]);
+            double tstar = sqrt((x[0] - oc[0]) * (x[0] - oc[0]) + (x[1] - oc[1]) * (x[1] - oc[1]) +
+                                (x[2] - oc[2]) * (x[2] - oc[2]));
+            double ray = tstar / xd; /* 1 / cos(theta) */
+            int trusted = dmin <= dmed;
+            int seethru = dmed > tp->gamma_st * vw->d_cam;
+            near_flag(dmed, tp->gamma_st * vw->d_cam, fabs(dmed), &flags);
+            int layered = layered_exact(n, A, S1, S2);
+            int front = (layered || seethru) && trusted;
+            int check_thin = 1;
+            if (pass && trusted && isfinite(dmin) && isfinite(dmed) && isfinite(dmax) &&
+                dmin > 0.0 && dmed > 0.0 && dmax > 0.0) {
+                double dref = front ? dmin : dmed;
+                double lo = dmin * ray, hi = dref * ray;
+                double that = tstar < lo ? lo : (tstar > hi ? hi : tstar);
+                double delta = fabs(tstar - that);
+                double tau_sp = hv * pi_dg(vw, ix, iy, tp->k_dg);
+                double E = fmax((double)n - mean, 0.0);
+                double tdep = pr->gamma * hv / (1.0 + tp->beta * E);
+                double lhs = front ? xd - dmin : fabs(xd - dmed);
+                near_flag(delta, tau_sp, tstar, &flags);
+                near_flag(lhs, tdep, fabs(xd), &flags);
+                if (delta <= tau_sp && lhs <= tdep) {
+                    double dctr = 0.5 * (dmin + dmax) * ray;
+                    double dhw = fmax(0.5 * (dmax - dmin) * ray, pr->eps);
+                    double r = (that - dctr) / dhw;
+                    double w = exp(-pr->alpha1 * r * r);
+                    Wsum += m * w;
+                    Zsum += w;
+                    bits |= i < 32 ? 1u << i : 0u;
+                    check_thin = 0;
+                    if (kind_out) kind_out[a * n_views + i] = 1;
+                }
+            }
+            double dsurf = (trusted && seethru) ? dmin : dmed;
+            near_flag(xd, dsurf + tp->behind_margin * hv, fabs(xd), &flags);
+            int behind_fail = xd > dsurf + tp->behind_margin * hv;
+            if (!check_thin || behind_fail || !(rho_v >= tp->rho_thin)) continue;
+            /* thin path over the footprint */
+            int64_t n_depth = 0, n_md = 0;
+            double m_max = 0.0, d2 = INFINITY;
+            for (int yy = j0; yy <= j1; ++yy)
+                for (int xx = i0; xx <= i1; ++xx) {
+                    int64_t q = (int64_t)yy * vw->W + xx;
+                    double qmin = vw->d_min[q], qmed = vw->d_med[q];
+                    if (qmed < pr->eps) continue;
+                    int64_t nq = vw->n_samp[q];
+                    double Eq = fmax((double)nq - mean, 0.0);
+                    double tq = pr->gamma * hv / (1.0 + tp->beta * Eq);
+                    int tr_q = qmin <= qmed;
+                    int st_q = qmed > tp->gamma_st * vw->d_cam;
+                    int fr_q = (layered_exact(nq, A, S1, S2) || st_q) && tr_q;
+                    double lhs = fr_q ? xd - qmin : fabs(xd - qmed);
+                    near_flag(lhs, tq, fabs(xd), &flags);
+                    near_flag(qmed, tp->gamma_st * vw->d_cam, fabs(qmed), &flags);
+                    if (!(lhs <= tq)) continue;
+                    ++n_depth;
+                    double mq;
+                    int pq, hq;
+                    tmask_at(vw, mask_type, q, pr, &mq, &pq, &hq);
+                    if (!hq) continue;
+                    ++n_md;
+                    if (mq > m_max) m_max = mq;
+                    double dq = fr_q ? qmin : qmed;
+                    double pc[3] = {((double)xx + 0.5 - (double)vw->cx) / (double)vw->fx * dq,
+                                    ((double)yy + 0.5 - (double)vw->cy) / (double)vw->fy * dq, dq};
+                    double pw[3];
+                    for (int r = 0; r < 3; ++r)  /* world = R^T (pc - t) */
+                        pw[r] = (double)R[r] * (pc[0] - vw->t[0]) +
+                                (double)R[3 + r] * (pc[1] - vw->t[1]) +
+                                (double)R[6 + r] * (pc[2] - vw->t[2]);
+                    double dd = (pw[0] - x[0]) * (pw[0] - x[0]) + (pw[1] - x[1]) * (pw[1] - x[1]) +
+                                (pw[2] - x[2]) * (pw[2] - x[2]);
+                    if (dd < d2) d2 = dd;
+                }
+            double n_min = fmax(tp->n_abs, ceil(tp->rho_occ * A_B));
+            double gate = tp->dist_gate * hv;
+            near_flag(d2, gate * gate, gate * gate, &flags);
+            if (fabs(tp->rho_occ * A_B - round(tp->rho_occ * A_B)) < ORACLE_MARGIN * (A_B + 1.0))
+                flags |= FLAG_TUPLE; /* ceil near an integer step */
+            double t = ((double)n_depth >= n_min && (double)n_md >= tp->rho_cover * (double)n_depth &&
+                        d2 <= gate * gate)
+                           ? m_max
+                           : 0.0;
+            if (thin_out) thin_out[a * n_views + i] = t;
+            near_flag(t, tp->tau_thin, 1.0, &flags);
+            if (t >= tp->tau_thin) {
+                Wsum += t;
+                Zsum += 1.0;
+                bits |= i < 32 ? 1u << i : 0u;
+                if (kind_out) kind_out[a * n_views + i] = 2;
+            }
+        }
+        double P = (Zsum > pr->eps) ? Wsum / Zsum : 0.0;
+        if (Zsum > pr->eps && fabs(P - pr->tau_cons) < ORACLE_MARGIN) flags |= FLAG_CONS;
+        int seg = (P >= pr->tau_cons);
+        if (W_out) W_out[a] = Wsum;
+        if (Z_out) Z_out[a] = Zsum;
+        if (P_out) P_out[a] = P;
+        if (seg_out) seg_out[a] = (uint8_t)seg;
+        if (bits_out) bits_out[a] = bits;
+        if (flags_out) flags_out[a] = flags;
+    }
+}

@@ -24,6 +24,8 @@ from .scenes import (  # noqa: F401
     config3,
     config4,
     look_at,
+    render_tuple,
     session_mix,
     session_workload,
+    with_tuple,
 )

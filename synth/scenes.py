@@ -48,6 +48,9 @@ def _lib():
         D = ctypes.c_double
         lib.synth_render.argtypes = [I, P, P, P, P, I, P, P, P, P, P, P, D, D, D, D, I, I, P, P]
         lib.synth_render.restype = None
+        lib.synth_render_tuple.argtypes = [I, P, P, P, P, I, P, P, P, P, P, P, D, D, D, D, I, I,
+                                           P, P, P, P]
+        lib.synth_render_tuple.restype = None
         lib.synth_occ_sphere_band.argtypes = [I, P, P, D, I, P, D, P]
         lib.synth_occ_sphere_band.restype = None
         lib.synth_occ_corner_sign.argtypes = [I, P, P, P, I, P, P, I, P, D, P]
@@ -142,6 +145,9 @@ class Workload:
     points: np.ndarray            # (n, 3) float32
     scene: Scene
     meta: dict = field(default_factory=dict)
+    # depth-tuple mode (per view): d_min / d_med / d_max float32 (H, W) planar,
+    # +inf = miss; n_samp uint16 (H, W); d_cam float (camera-target distance)
+    tuple: dict | None = None
 
     @property
     def n_views(self) -> int:
@@ -228,6 +234,63 @@ def render(scene: Scene, cam: Camera):
                      _p(pl_n), _p(pl_d), _p(pl_rad), _p(pl_id), _p(R), _p(t), cam.fx, cam.fy,
                      cam.cx, cam.cy, cam.W, cam.H, _p(depth), _p(hit))
     return depth, hit
+
+
+def render_tuple(scene: Scene, cam: Camera):
+    """Front-hit depth, exit depth of that primitive, surface crossings along
+    the whole ray, and hit id (float32, float32, int32, int32; (H, W))."""
+    lib = _lib()
+    front = np.empty((cam.H, cam.W), np.float32)
+    back = np.empty((cam.H, cam.W), np.float32)
+    cross = np.empty((cam.H, cam.W), np.int32)
+    hit = np.empty((cam.H, cam.W), np.int32)
+    ell_c = np.ascontiguousarray(scene.ell_c, np.float64)
+    brad = np.ascontiguousarray(scene.ell_brad, np.float64)
+    ell_id = np.ascontiguousarray(scene.ell_id, np.int32)
+    pl_n = np.ascontiguousarray(scene.pl_n, np.float64).reshape(-1)
+    pl_d = np.ascontiguousarray(scene.pl_d, np.float64)
+    pl_rad = np.ascontiguousarray(scene.pl_rad, np.float64)
+    pl_id = np.ascontiguousarray(scene.pl_id, np.int32)
+    R = np.ascontiguousarray(cam.R, np.float64).reshape(-1)
+    t = np.ascontiguousarray(cam.t, np.float64)
+    lib.synth_render_tuple(len(ell_c), _p(ell_c), _p(scene.ell_M), _p(brad), _p(ell_id),
+                           len(pl_d), _p(pl_n), _p(pl_d), _p(pl_rad), _p(pl_id), _p(R), _p(t),
+                           cam.fx, cam.fy, cam.cx, cam.cy, cam.W, cam.H, _p(front), _p(back),
+                           _p(cross), _p(hit))
+    return front, back, cross, hit
+
+
+def with_tuple(wl: "Workload", seed: int = 1100, band: float = 2.0, untrusted: float = 0.03,
+               d_cam_scale: float = 0.8, target=(0.0, 0.0, 0.0)) -> "Workload":
+    """The workload plus depth-tuple rasters for its cameras (depth-tuple mode,
+    Sec. 3.5), the way a 2DGS renderer would report them for opaque surfaces:
+    d_min = front hit; d_max = d_min + band h (1 + U[0, 1/2]) (the splat band,
+    h the grid's voxel edge); d_med = d_min + U[0, 1/2] (d_max - d_min), except
+    for a fraction ``untrusted`` of hit pixels where d_med = d_min - U[0.1, 1] h
+    (a tilted-surfel anomaly, d_min > d_med); n_samp = 3 x (surfaces the ray
+    crosses) + U{0, 1, 2}; misses are +inf.  d_cam = d_cam_scale x the camera
+    centre's distance to ``target``."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    h = float(wl.grid.h)
+    t = {"d_min": [], "d_med": [], "d_max": [], "n_samp": [], "d_cam": []}
+    for cam in wl.cams:
+        front, _back, cross, _hit = render_tuple(wl.scene, cam)
+        hitm = np.isfinite(front)
+        d_max = front.astype(np.float64) + band * h * (1.0 + 0.5 * rng.uniform(0, 1, front.shape))
+        d_med = front + 0.5 * rng.uniform(0, 1, front.shape) * (d_max - front)
+        anom = hitm & (rng.uniform(0, 1, front.shape) < untrusted)
+        d_med = np.where(anom, front - rng.uniform(0.1, 1.0, front.shape) * h, d_med)
+        inf = np.float32(np.inf)
+        t["d_min"].append(np.where(hitm, front, inf).astype(np.float32))
+        t["d_med"].append(np.where(hitm, d_med, inf).astype(np.float32))
+        t["d_max"].append(np.where(hitm, d_max, inf).astype(np.float32))
+        t["n_samp"].append((3 * cross + rng.integers(0, 3, cross.shape)).astype(np.uint16))
+        C = -np.asarray(cam.R, np.float64).T @ np.asarray(cam.t, np.float64)
+        t["d_cam"].append(float(d_cam_scale * np.linalg.norm(C - np.asarray(target))))
+    out = Workload(**{k: getattr(wl, k) for k in wl.__dataclass_fields__ if k != "tuple"})
+    out.tuple = t
+    out.name = wl.name + "-tuple"
+    return out
 
 
 def soft_mask_f16(indicator: np.ndarray, rng, sigma=2.0, radius=6, noise_std=0.05) -> np.ndarray:

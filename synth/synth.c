@@ -55,6 +55,28 @@ static inline double hit_ellipsoid(const double* c, const double* M,
     return t > 0.0 ? t : INFINITY;
 }
 
+/* Both positive ray parameters of |M(o + t d - c)| = 1 (entry t0, exit t1);
+ * returns 0 when the ray misses or the object lies behind the origin. */
+static inline int hit_ellipsoid2(const double* c, const double* M, const double* o,
+                                 const double* d, double* t0, double* t1) {
+    double oc[3] = {o[0] - c[0], o[1] - c[1], o[2] - c[2]};
+    double op[3], dp[3];
+    matvec3(M, oc, op);
+    matvec3(M, d, dp);
+    double a = dot3(dp, dp);
+    double b = 2.0 * dot3(op, dp);
+    double q = dot3(op, op) - 1.0;
+    if (q <= 0.0 || b >= 0.0) return 0;
+    double disc = b * b - 4.0 * a * q;
+    if (disc < 0.0) return 0;
+    double sq = sqrt(disc);
+    double qq = -0.5 * (b - sq); /* b < 0: no cancellation */
+    double r0 = q / qq, r1 = qq / a;
+    *t0 = fmin(r0, r1);
+    *t1 = fmax(r0, r1);
+    return *t0 > 0.0;
+}
+
 /* Conservative pixel bounding box of a sphere (camera-space centre cc, radius r). */
 static void sphere_bbox(const double* cc, double r, double fx, double fy, double cx,
                         double cy, int W, int H, int* box) {
@@ -412,4 +434,87 @@ void synth_contracted_distance(int n_ell, const double* ell_c, const double* ell
                     if (d <= s_max && d < nd[v]) nd[v] = (float)d;
                 }
     }
+}
+
+/*
+ * Depth tuple of one view (the per-pixel outputs a 2DGS / NeRF renderer hands
+ * to the fusion stage in depth-tuple mode, Sec. 3.5): planar depth of the
+ * nearest hit (front), planar depth where the ray leaves that primitive
+ * (back; = front for planes), number of primitive surfaces the ray crosses
+ * over its whole length (2 per ellipsoid it passes through, 1 per plane it
+ * hits), and the id of the nearest primitive.  Same scene arguments as
+ * synth_render; front/back: H*W float32 (+inf on a miss), cross: H*W int32.
+ */
+void synth_render_tuple(int n_ell, const double* ell_c, const double* ell_M,
+                        const double* ell_brad, const int32_t* ell_id, int n_pl,
+                        const double* pl_n, const double* pl_d, const double* pl_rad,
+                        const int32_t* pl_id, const double* R, const double* t, double fx,
+                        double fy, double cx, double cy, int W, int H, float* front,
+                        float* back, int32_t* cross, int32_t* hit) {
+    double C[3] = {-(R[0] * t[0] + R[3] * t[1] + R[6] * t[2]),
+                   -(R[1] * t[0] + R[4] * t[1] + R[7] * t[2]),
+                   -(R[2] * t[0] + R[5] * t[1] + R[8] * t[2])};
+    int* box = (int*)malloc(sizeof(int) * 4 * (size_t)(n_ell > 0 ? n_ell : 1));
+    for (int e = 0; e < n_ell; ++e) {
+        double cc[3];
+        matvec3(R, ell_c + 3 * e, cc);
+        cc[0] += t[0]; cc[1] += t[1]; cc[2] += t[2];
+        sphere_bbox(cc, ell_brad[e], fx, fy, cx, cy, W, H, box + 4 * e);
+    }
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int j = 0; j < H; ++j) {
+        double* best = (double*)malloc(sizeof(double) * W);
+        double* bexit = (double*)malloc(sizeof(double) * W);
+        int32_t* nc = cross + (size_t)j * W;
+        int32_t* bid = hit + (size_t)j * W;
+        for (int i = 0; i < W; ++i) {
+            best[i] = INFINITY;
+            bexit[i] = INFINITY;
+            nc[i] = 0;
+            bid[i] = -1;
+        }
+        double yc = ((double)j + 0.5 - cy) / fy;
+        for (int e = 0; e < n_ell; ++e) {
+            const int* b = box + 4 * e;
+            if (j < b[2] || j > b[3] || b[0] > b[1]) continue;
+            for (int i = b[0]; i <= b[1]; ++i) {
+                double dc[3] = {((double)i + 0.5 - cx) / fx, yc, 1.0};
+                double d[3] = {R[0] * dc[0] + R[3] * dc[1] + R[6] * dc[2],
+                               R[1] * dc[0] + R[4] * dc[1] + R[7] * dc[2],
+                               R[2] * dc[0] + R[5] * dc[1] + R[8] * dc[2]};
+                double t0, t1;
+                if (!hit_ellipsoid2(ell_c + 3 * e, ell_M + 9 * e, C, d, &t0, &t1)) continue;
+                nc[i] += 2;
+                if (t0 < best[i]) { best[i] = t0; bexit[i] = t1; bid[i] = ell_id[e]; }
+            }
+        }
+        for (int p = 0; p < n_pl; ++p) {
+            const double* n = pl_n + 3 * p;
+            for (int i = 0; i < W; ++i) {
+                double dc[3] = {((double)i + 0.5 - cx) / fx, yc, 1.0};
+                double d[3] = {R[0] * dc[0] + R[3] * dc[1] + R[6] * dc[2],
+                               R[1] * dc[0] + R[4] * dc[1] + R[7] * dc[2],
+                               R[2] * dc[0] + R[5] * dc[1] + R[8] * dc[2]};
+                double nd = dot3(n, d);
+                if (nd == 0.0) continue;
+                double th = (pl_d[p] - dot3(n, C)) / nd;
+                if (!(th > 0.0)) continue;
+                if (pl_rad[p] > 0.0) {
+                    double x[3] = {C[0] + th * d[0], C[1] + th * d[1], C[2] + th * d[2]};
+                    double off = dot3(n, x);
+                    double r2 = dot3(x, x) - off * off;
+                    if (r2 > pl_rad[p] * pl_rad[p]) continue;
+                }
+                nc[i] += 1;
+                if (th < best[i]) { best[i] = th; bexit[i] = th; bid[i] = pl_id[p]; }
+            }
+        }
+        for (int i = 0; i < W; ++i) {
+            front[(size_t)j * W + i] = (float)best[i];
+            back[(size_t)j * W + i] = (float)bexit[i];
+        }
+        free(best);
+        free(bexit);
+    }
+    free(box);
 }

@@ -455,5 +455,139 @@ def pin_gradient_fd(orc):
     fd_check(orc, wl, oracle.MASK_F32, n_per_view=30, n_random=10)
 
 
+# --------------------------------------------------------------------------
+# depth-tuple mode (Sec. 3.5 "Footprint statistics" .. "Thin-structure path";
+# Algorithms "Thick-/Thin-Structure Segmentation for 2DGS", App. B.5)
+# --------------------------------------------------------------------------
+def _tuple_setup():
+    """Grid 8^3 over [-1,1]^3 (h = 1/4), voxel (3, 4, 5) at x = (-1/8, 1/8, 3/8)
+    seen on-axis (the ray through its projection is the optical axis, so
+    t* = x_d = 2.375 and the planar-to-ray factor is 1) by a camera R = I,
+    f = 100, principal point (50.25, 40.75), 100 x 80: the voxel projects to
+    pixel (50, 40) and its corners to u in [44.69, 55.81], v in [35.19, 46.31]
+    -> footprint pixels 44..55 x 35..46 (A = 144), clipped box area 123.5."""
+    grid = synth.Grid(8, (-1.0, -1.0, -1.0), 0.25, False)
+    cam = synth.Camera(np.eye(3, dtype=np.float32), np.array([0.125, -0.125, 2.0], np.float32),
+                       100.0, 100.0, 50.25, 40.75, 100, 80)
+    lin = np.array([(5 * 8 + 4) * 8 + 3], np.int64)
+    return grid, cam, lin, 2.375
+
+
+def _tuple_run(orc, d_min, d_med, d_max, n=5, mask=1.0, d_cam=3.0, tparams=None, params=None):
+    grid, cam, lin, xd = _tuple_setup()
+
+    def ras(v, dtype=np.float32):
+        return np.broadcast_to(np.asarray(v, dtype), (cam.H, cam.W)).copy()
+    tup = {"d_min": [ras(d_min)], "d_med": [ras(d_med)], "d_max": [ras(d_max)],
+           "n_samp": [ras(n, np.uint16)], "d_cam": [d_cam]}
+    r = orc.fuse_tuple(grid, lin, [cam], tup, [ras(mask)], oracle.MASK_F32,
+                       params=params or P_DEFAULT, tparams=tparams or oracle.TupleParams())
+    return r, tup
+
+
+def _w(lo, hi, t_hat, alpha1=0.5):
+    lo, hi = float(np.float32(lo)), float(np.float32(hi))
+    return math.exp(-alpha1 * ((t_hat - 0.5 * (lo + hi)) / (0.5 * (hi - lo))) ** 2)
+
+
+def pin_tuple_closed_form(orc):
+    xd = 2.375
+    # base: d_med at the voxel, median reference, t_hat = t* -> w at the band offset
+    r, _ = _tuple_run(orc, 2.275, 2.375, 2.575)
+    assert r["kind"][0, 0] == 1
+    assert math.isclose(r["W"][0], _w(2.275, 2.575, xd), rel_tol=1e-12)
+    assert math.isclose(r["Z"][0], r["W"][0], rel_tol=1e-15) and r["P"][0] == 1.0
+    # see-through (d_med > gamma_st d_cam): front surface reference, one-sided gate,
+    # t_hat clamped to d_min
+    r, _ = _tuple_run(orc, 2.275, 2.375, 2.575, d_cam=1.0)
+    assert r["kind"][0, 0] == 1
+    assert math.isclose(r["W"][0], _w(2.275, 2.575, float(np.float32(2.275))), rel_tol=1e-12)
+    # layered centre pixel: front reference and a tightened tolerance
+    # 0.25 / (1 + 0.05 E), E = 60 - 775/144, rejects x_d - d_min = 0.1; the
+    # thin path then certifies the footprint: t = m_max = 1, W = Z = 1
+    n = np.full((80, 100), 5, np.uint16)
+    n[40, 50] = 60
+    r, _ = _tuple_run(orc, 2.275, 2.375, 2.575, n=n)
+    assert r["kind"][0, 0] == 2 and r["W"][0] == 1.0 and r["Z"][0] == 1.0
+    # the same with the centre count just below mean + sigma is not layered
+    # (but still tightened): median reference, thick vote
+    n[40, 50] = 6
+    r, _ = _tuple_run(orc, 2.275, 2.375, 2.575, n=n)
+    assert r["kind"][0, 0] == 1
+    # one-sided gate: voxel 0.2 in front of d_min (see-through), tolerance
+    # tightened to 0.25 / 1.3 < 0.2 by a centre count 16 over a 0/20 checkerboard
+    # (mean 10, sigma 10: not layered): x_d - d_min = -0.2 passes, |.| would not
+    n = np.where((np.add.outer(np.arange(80), np.arange(100)) % 2) == 0, 0, 20).astype(np.uint16)
+    n[40, 50] = 16
+    r, _ = _tuple_run(orc, 2.575, 2.675, 2.775, n=n, d_cam=1.0)
+    assert r["kind"][0, 0] == 1
+    assert math.isclose(r["W"][0], _w(2.575, 2.775, float(np.float32(2.575))), rel_tol=1e-12)
+    # untrusted (d_min > d_med) everywhere: no thick vote, the thin path
+    # (median reference per pixel) votes
+    r, _ = _tuple_run(orc, 2.475, 2.375, 2.575)
+    assert r["kind"][0, 0] == 2 and r["W"][0] == 1.0
+    # behind the surface by 0.6 > 2 h_v: neither path
+    r, _ = _tuple_run(orc, 1.775, 1.775, 1.975)
+    assert r["kind"][0, 0] == 0 and r["Z"][0] == 0.0
+    # 0.1 behind the median with a centre mask below tau_m: the behind gate lets
+    # it through (0.1 <= 2 h_v) and the footprint certifies it (thin vote)
+    m = np.ones((80, 100), np.float32)
+    m[40, 50] = 0.3
+    r, _ = _tuple_run(orc, 2.175, 2.275, 2.475, mask=m)
+    assert r["kind"][0, 0] == 2 and r["W"][0] == 1.0
+    # depth-gradient factor: a step of 0.05 in (d_min + d_max)/2 across the
+    # centre pixel's neighbours; see-through reference (|t* - t_hat| = 0.1):
+    # k = 1000 -> pi = exp(-2.5) -> 0.25 pi < 0.1 rejects; k = 0 accepts
+    lo = np.full((80, 100), 2.275, np.float32)
+    lo[:, 51:] += np.float32(0.05)
+    hi = lo + np.float32(0.3)
+    r, _ = _tuple_run(orc, lo, 2.375, hi, d_cam=1.0, tparams=oracle.TupleParams(k_dg=1000.0))
+    assert r["kind"][0, 0] != 1
+    r, _ = _tuple_run(orc, lo, 2.375, hi, d_cam=1.0, tparams=oracle.TupleParams(k_dg=0.0))
+    assert r["kind"][0, 0] == 1
+    # thin floors: support below n_min, coverage below rho_cover
+    r, _ = _tuple_run(orc, 2.475, 2.375, 2.575, tparams=oracle.TupleParams(n_abs=145.0))
+    assert r["kind"][0, 0] == 0
+    m = np.zeros((80, 100), np.float32)
+    m[35:40, 44:56] = 1.0  # 60 of 144 depth-valid pixels mask-positive: 0.42 < 0.5
+    r, _ = _tuple_run(orc, 2.475, 2.375, 2.575, mask=m)
+    assert r["kind"][0, 0] == 0
+    m[40, 44:56] = 1.0     # 72 of 144: exactly 0.5 (inclusive)
+    r, _ = _tuple_run(orc, 2.475, 2.375, 2.575, mask=m)
+    assert r["kind"][0, 0] == 2
+    # distance gate (1.5 h_v): with an 8 x 8 mask hole around the centre (80 of
+    # 144 pixels positive) the nearest mask-positive unprojection lies 0.101
+    # from the centre: inside 1.5 h_v = 0.375, outside 0.3 h_v = 0.075
+    m = np.ones((80, 100), np.float32)
+    m[37:45, 46:54] = 0.0
+    r, _ = _tuple_run(orc, 2.475, 2.375, 2.575, mask=m)
+    assert r["kind"][0, 0] == 2
+    r, _ = _tuple_run(orc, 2.475, 2.375, 2.575, mask=m,
+                      tparams=oracle.TupleParams(dist_gate=0.3))
+    assert r["kind"][0, 0] == 0
+
+
+def pin_tuple_bruteforce(orc):
+    wl = synth.config2(g=40, W=140, H=105, n_ell=40, n_points=500)
+    tw = synth.with_tuple(wl)
+    lin = wl.active_linear()
+    for tp, prm in [(oracle.TupleParams(n_abs=4.0, k_dg=30.0), P_DEFAULT),
+                    (oracle.TupleParams(n_abs=2.0, rho_cover=0.3, tau_thin=0.3),
+                     oracle.Params(tau_m=0.3, alpha1=1.0))]:
+        r = orc.fuse_tuple(wl.grid, lin, wl.cams, tw.tuple, wl.mask, wl.mask_type, params=prm,
+                           tparams=tp)
+        b = brute.fuse_tuple(wl.grid, lin, wl.cams, tw.tuple, wl.mask, wl.mask_type,
+                             tau_m=prm.tau_m, alpha1=prm.alpha1, **{
+                                 k: getattr(tp, k) for k in tp.__dataclass_fields__})
+        ok = r["flags"] == 0
+        assert ok.mean() > 0.95
+        assert (b["kind"] == 1).sum() > 50 and (b["kind"] == 2).sum() > 50
+        assert np.array_equal(r["kind"][ok], b["kind"][ok])
+        assert np.array_equal(r["bits"][ok], b["bits"][ok])
+        assert np.allclose(r["W"][ok], b["W"][ok], rtol=1e-12, atol=1e-300)
+        assert np.allclose(r["Z"][ok], b["Z"][ok], rtol=1e-12, atol=1e-300)
+
+
 ALL_PINS = [pin_single_view_closed_form, pin_pixel_convention, pin_alpha0_mean, pin_invariants,
-            pin_scale_invariance, pin_sphere_scene, pin_bruteforce, pin_labels, pin_gradient_fd]
+            pin_scale_invariance, pin_sphere_scene, pin_bruteforce, pin_labels, pin_gradient_fd,
+            pin_tuple_closed_form, pin_tuple_bruteforce]

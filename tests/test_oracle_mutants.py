@@ -58,6 +58,30 @@ MUTANTS = {
     "grad_sigmoid_dropped": ("mv[k] * (1.0 - mv[k]) : 1.0", "mv[k] : 1.0"),
     "grad_Z_dropped": ("(wv[k] / Zsum) * dmdl", "wv[k] * dmdl"),
     "grad_alpha_dropped": ("wv[k] * 2.0 * pr->alpha1 * ev[k]", "wv[k] * 2.0 * ev[k]"),
+    # depth-tuple mode
+    "tuple_one_sided_abs": ("double lhs = front ? xd - dmin : fabs(xd - dmed);",
+                            "double lhs = front ? fabs(xd - dmin) : fabs(xd - dmed);"),
+    "tuple_no_tightening": ("double tdep = pr->gamma * hv / (1.0 + tp->beta * E);",
+                            "double tdep = pr->gamma * hv;"),
+    "tuple_layered_inclusive": ("if (d <= 0) return 0;\n    return (__int128)d * d > ",
+                                "if (d < 0) return 0;\n    return (__int128)d * d >= "),
+    "tuple_behind_margin_dropped": ("int behind_fail = xd > dsurf + tp->behind_margin * hv;",
+                                    "int behind_fail = xd > dsurf;"),
+    "tuple_coverage_over_area": ("(double)n_md >= tp->rho_cover * (double)n_depth",
+                                 "(double)n_md >= tp->rho_cover * (double)A"),
+    "tuple_ray_factor_dropped": ("double lo = dmin * ray, hi = dref * ray;",
+                                 "double lo = dmin, hi = dref;"),
+    "tuple_seethru_flipped": ("int seethru = dmed > tp->gamma_st * vw->d_cam;",
+                              "int seethru = dmed < tp->gamma_st * vw->d_cam;"),
+    "tuple_hw_not_halved": ("double dhw = fmax(0.5 * (dmax - dmin) * ray, pr->eps);",
+                            "double dhw = fmax((dmax - dmin) * ray, pr->eps);"),
+    "tuple_thin_denominator_t": ("Wsum += t;\n                Zsum += 1.0;",
+                                 "Wsum += t;\n                Zsum += t;"),
+    "tuple_dist_gate_dropped": (" &&\n                        d2 <= gate * gate)", ")"),
+    "tuple_pi_ignored": ("double tau_sp = hv * pi_dg(vw, ix, iy, tp->k_dg);",
+                         "double tau_sp = hv;"),
+    "tuple_thin_trusted_dropped": ("int fr_q = (layered_exact(nq, A, S1, S2) || st_q) && tr_q;",
+                                   "int fr_q = (layered_exact(nq, A, S1, S2) || st_q);"),
 }
 
 
