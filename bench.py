@@ -542,6 +542,65 @@ def run_ours(args, rank, world, local_rank):
     return res, wl
 
 
+def measure_tuple(dev, steps: int):
+    """Depth-tuple mode on the 256^3 forward-facing scene (8 views 1008x756 with
+    d_min / d_med / d_max / n_samp rasters): one step = occupancy gate + the
+    tuple views (integral images, thick gates, thin footprint path) + finalize
+    + labels, replayed from a CUDA graph, L2 flushed between steps."""
+    import torch
+
+    import synth
+    from paper_2601_04860_b300 import FusionParams, TupleParams, VoxelFusion
+    tw = synth.with_tuple(synth.config2())
+    occ = torch.from_numpy(tw.occ).to(dev)
+    T = tw.tuple
+    ras = {k: [torch.from_numpy(a).to(dev) for a in T[k]] for k in ("d_min", "d_med", "d_max")}
+    ns = [torch.from_numpy(a.view(np.int16)).to(dev) for a in T["n_samp"]]
+    mask = [torch.from_numpy(m.view(np.float16)).to(dev) for m in tw.mask]
+    pts = torch.from_numpy(np.ascontiguousarray(tw.points)).to(dev)
+    fu = VoxelFusion(tw.grid, occ=occ, params=FusionParams())
+    score = torch.empty(fu.n_cells, dtype=torch.float32, device=dev)
+    labels = torch.empty(len(tw.points), dtype=torch.uint8, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    tp = TupleParams()
+
+    def step():
+        fu.set_occupancy(occ=occ)
+        fu.add_views_tuple(tw.cams, ras["d_min"], ras["d_med"], ras["d_max"], ns, mask,
+                           T["d_cam"], tw.mask_type, tparams=tp)
+        fu.finalize(score=score)
+        fu.label_points(pts, out=labels)
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        for _ in range(3):
+            step()
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True, external=True) for _ in range(2)]
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        ev[0].record()
+        step()
+        ev[1].record()
+    ms = []
+    for k in range(3 + steps):
+        flush.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        if k >= 3:
+            ms.append(ev[0].elapsed_time(ev[1]))
+    n, S, na = fu.n_cells, tw.n_views, fu.n_active
+    fu.close()
+    m = float(np.mean(ms))
+    return {"workload": "forward-dense-256-tuple (config-2 scene, depth tuple per view, paper "
+                        "defaults: thick gates + thin footprint path)",
+            "ms_per_step": m, "updates_per_s": n * S / (m * 1e-3),
+            "active_updates_per_s": na * S / (m * 1e-3),
+            "what": "graph replay of set_occupancy + add_views_tuple (8 views) + finalize + "
+                    "label_points; L2 flushed per step"}
+
+
 def measure_adjoint(dev, steps: int):
     """Config 4: forward + hand-written backward through the autograd Function on
     the 256^3 forward-facing scene with FP32 logits and depth as leaves."""
@@ -750,6 +809,9 @@ def run(args):
     if not args.quick and not args.no_adjoint:
         import torch
         res["adjoint"] = measure_adjoint(torch.device("cuda", local_rank), max(5, args.steps // 2))
+    if not args.quick and not args.no_tuple and args.workload == "forward-dense-256":
+        import torch
+        res["tuple"] = measure_tuple(torch.device("cuda", local_rank), max(5, args.steps // 2))
     if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.quick:
         full_s, det = oracle_rate(wl, args.cpu_seconds)
         N = res["config"]["voxels_nominal"]
@@ -813,6 +875,7 @@ def main(argv=None):
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-adjoint", action="store_true", help="skip the forward+backward leg")
     ap.add_argument("--no-sessions", action="store_true", help="skip the batched/served leg")
+    ap.add_argument("--no-tuple", action="store_true", help="skip the depth-tuple-mode leg")
     ap.add_argument("--sessions", type=int, default=32, help="sessions in the batched/served leg")
     ap.add_argument("--sessions-scale", type=float, default=0.5,
                     help="size scale of the sessions (1.0 = the full session mix)")

@@ -212,6 +212,57 @@ divas_status divas_fuse_step_profiled(divas_ctx* ctx, const uint8_t* occ_dense,
                                       uint8_t* labels_out, void* const* stage_events,
                                       void* stream);
 
+/*
+ * Depth-tuple mode (Sec. 3.5 "Planar-to-ray depth correction" .. "Thin-
+ * structure path"; Algorithms "Thick-Structure Segmentation for 2DGS" and
+ * "Thin-Structure Segmentation for 2DGS", Appendix B.5).  Each view carries
+ * the renderer's depth tuple instead of one depth: the thick path takes the
+ * footprint statistics of n_samp (integral images), the layered / see-through
+ * / trust tests, the asymmetric depth gate with the count-tightened tolerance
+ * gamma h_v / (1 + beta E), the ray-space spatial gate with the depth-gradient
+ * factor and the depth-band weight; a view that casts no thick vote and passes
+ * the behind-surface gate goes through the thin path over the voxel's
+ * projected footprint (two counters, coverage, peak mask, distance gate) and
+ * adds its score t to W and 1 to Z when t >= tau_thin.  The occupied set is
+ * binary (density 1 per active voxel).
+ */
+typedef struct {
+    divas_camera cam;
+    const float* d_min;      /* device H x W planar depths (front hit, median, back); */
+    const float* d_med;      /* +inf, NaN or <= 0: no surface                           */
+    const float* d_max;
+    const uint16_t* n_samp;  /* device H x W splat-traversal count                       */
+    const void* mask;        /* device H x W, as in divas_view                           */
+    int32_t mask_type;
+    float d_cam;             /* camera-target distance (see-through test)                */
+} divas_tuple_view;
+
+typedef struct {
+    float beta;          /* count tightening (0.05)                                       */
+    float gamma_st;      /* see-through threshold as a multiple of d_cam (1.5)             */
+    float tau_thin;      /* thin-path acceptance (0.6)                                    */
+    float rho_cover;     /* coverage n_md / n_depth (0.5)                                 */
+    float rho_occ;       /* fractional support floor of the footprint area (0.1)           */
+    float n_abs;         /* absolute support floor (25)                                   */
+    float dist_gate;     /* unprojection distance gate in units of h_v (1.5)               */
+    float behind_margin; /* behind-surface margin in units of h_v (2)                      */
+    float k_dg;          /* depth-gradient decay (0: factor 1)                             */
+    float rho_thin;      /* thin-path density floor (1: every active voxel is eligible)    */
+} divas_tuple_params;
+
+/* The constants above (Table gs-hyperparams; k_dg and rho_thin are readings). */
+divas_tuple_params divas_default_tuple_params(void);
+
+/* Fold n_views (1..DIVAS_MAX_VIEWS_PER_CALL) tuple views in index order onto
+ * the accumulators (view bits continue the context's count); finalize as
+ * usual.  Builds per-view integral images in context scratch that grows on
+ * demand (the first call with larger views allocates and synchronises; such a
+ * call inside a stream capture returns DIVAS_E_STATE).  Footprints must stay
+ * below 2^16 pixels for the integral-image sums to be exact. */
+divas_status divas_fuse_add_views_tuple(divas_ctx* ctx, const divas_tuple_view* views,
+                                        int32_t n_views, const divas_tuple_params* tp,
+                                        void* stream);
+
 /* Pass 1 labels (Eq. pass1): labels_out[i] = seg bit of the voxel containing
  * point i (device n x 3 float32), 0 outside the grid (half-open box), for NaN,
  * or for unoccupied voxels.  Uses the seg bitfield of the last finalize. */

@@ -517,14 +517,23 @@ void oracle_fuse_tuple(int g, const double* origin, double h, int contracted, in
                 if (!(q[2] > pr->z_near)) { corners_ok = 0; break; }
                 double u = (double)vw->fx * q[0] / q[2] + (double)vw->cx;
                 double v = (double)vw->fy * q[1] / q[2] + (double)vw->cy;
-                double su = 1.0 + fabs((double)vw->cx) + fabs(u - (double)vw->cx);
-                double sv = 1.0 + fabs((double)vw->cy) + fabs(v - (double)vw->cy);
-                if (dist_to_int(u) < ORACLE_MARGIN * su || dist_to_int(v) < ORACLE_MARGIN * sv)
-                    flags |= FLAG_TUPLE;
                 umin = fmin(umin, u); umax = fmax(umax, u);
                 vmin = fmin(vmin, v); vmax = fmax(vmax, v);
             }
             if (!in || !corners_ok) continue;
+            /* the box edges decide which pixel rows and columns it covers: only
+               an edge near an integer inside the frame (the floor is clamped to
+               the frame outside it) can flip that */
+            {
+                const double ext[4] = {umin, umax, vmin, vmax};
+                for (int e = 0; e < 4; ++e) {
+                    double lim = e < 2 ? (double)vw->W : (double)vw->H;
+                    double c = e < 2 ? (double)vw->cx : (double)vw->cy;
+                    double s = 1.0 + fabs(c) + fabs(ext[e] - c);
+                    if (ext[e] > -0.5 && ext[e] < lim + 0.5 && dist_to_int(ext[e]) < ORACLE_MARGIN * s)
+                        flags |= FLAG_TUPLE;
+                }
+            }
             double cu0 = fmax(umin, 0.0), cu1 = fmin(umax, (double)vw->W);
             double cv0 = fmax(vmin, 0.0), cv1 = fmin(vmax, (double)vw->H);
             int i0 = (int)fmax(floor(umin), 0.0), i1 = (int)fmin(floor(umax), vw->W - 1.0);
@@ -627,8 +636,13 @@ void oracle_fuse_tuple(int g, const double* origin, double h, int contracted, in
             double n_min = fmax(tp->n_abs, ceil(tp->rho_occ * A_B));
             double gate = tp->dist_gate * hv;
             near_flag(d2, gate * gate, gate * gate, &flags);
-            if (fabs(tp->rho_occ * A_B - round(tp->rho_occ * A_B)) < ORACLE_MARGIN * (A_B + 1.0))
-                flags |= FLAG_TUPLE; /* ceil near an integer step */
+            {   /* ceil near an integer step: flag when the two candidate counts
+                   would decide this voxel differently */
+                double k = round(tp->rho_occ * A_B);
+                if (fabs(tp->rho_occ * A_B - k) < ORACLE_MARGIN * (A_B + 1.0) &&
+                    ((double)n_depth >= fmax(tp->n_abs, k)) != ((double)n_depth >= fmax(tp->n_abs, k + 1.0)))
+                    flags |= FLAG_TUPLE;
+            }
             double t = ((double)n_depth >= n_min && (double)n_md >= tp->rho_cover * (double)n_depth &&
                         d2 <= gate * gate)
                            ? m_max

@@ -13,7 +13,13 @@ from ._lib import (  # noqa: F401
     DivasError,
     load,
 )
-from .fusion import FusionParams, PreparedViews, VoxelFusion, seg_bits_to_bool  # noqa: F401
+from .fusion import (  # noqa: F401
+    FusionParams,
+    PreparedViews,
+    TupleParams,
+    VoxelFusion,
+    seg_bits_to_bool,
+)
 from .autograd import DivasFuseFunction, fuse  # noqa: F401,E402
 from .batch import Autotuner, Batch, Schedule  # noqa: F401,E402
 from .serve import Server, latency_summary, poisson_requests, serve_plain  # noqa: F401,E402

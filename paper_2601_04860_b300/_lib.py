@@ -43,6 +43,19 @@ class DivasView(ctypes.Structure):
                 ("mask_type", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
+class DivasTupleView(ctypes.Structure):
+    _fields_ = [("cam", DivasCamera), ("d_min", ctypes.c_void_p), ("d_med", ctypes.c_void_p),
+                ("d_max", ctypes.c_void_p), ("n_samp", ctypes.c_void_p),
+                ("mask", ctypes.c_void_p), ("mask_type", ctypes.c_int32),
+                ("d_cam", ctypes.c_float)]
+
+
+class DivasTupleParams(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_float) for n in
+                ("beta", "gamma_st", "tau_thin", "rho_cover", "rho_occ", "n_abs", "dist_gate",
+                 "behind_margin", "k_dg", "rho_thin")]
+
+
 class DivasError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
@@ -76,6 +89,10 @@ _SIGS = {
     "divas_debug_rcp": (ctypes.c_int, [_P, ctypes.c_int64, _P, _P, _P]),
     "divas_fuse_step": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64, ctypes.POINTER(DivasView),
                                        ctypes.c_int32, _P, _P, _P, ctypes.c_int64, _P, _P]),
+    "divas_default_tuple_params": (DivasTupleParams, []),
+    "divas_fuse_add_views_tuple": (ctypes.c_int, [_P, ctypes.POINTER(DivasTupleView),
+                                                  ctypes.c_int32,
+                                                  ctypes.POINTER(DivasTupleParams), _P]),
     "divas_fuse_update": (ctypes.c_int, [_P, ctypes.POINTER(DivasView), ctypes.c_int32, _P, _P,
                                          ctypes.c_uint32, _P]),
     "divas_fuse_step_profiled": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64,

@@ -789,6 +789,8 @@ struct divas_ctx {
     uint32_t* seg_bits = nullptr;
     uint32_t* active = nullptr;
     FastDiv gdiv;  // division by g
+    void* sat = nullptr;   // tuple mode: integral-image scratch, grown on demand
+    size_t sat_bytes = 0;
     float* W = nullptr;
     float* Z = nullptr;
     uint32_t* bits = nullptr;
@@ -880,7 +882,7 @@ ViewC make_view(const divas_camera& cam, const GridC& G, const float* depth, con
         // camera coordinates of the lattice point n: p = T + M n, T = R o + t,
         // M = (h / 2) R (in double)
         const double hh = 0.5 * (double)G.h;
-        const double nmax = 2.0 * G.g - 1.0;
+        const double nmax = 2.0 * G.g;  // centres n <= 2g - 1, corners n + 1 <= 2g
         double T[3], M[3][3];
         for (int r = 0; r < 3; ++r) {
             T[r] = (double)cam.t[r];
@@ -1029,6 +1031,7 @@ divas_status read_status(divas_ctx* c, cudaStream_t s) {
 }
 
 void free_all(divas_ctx* c) {
+    if (c->sat) cudaFree(c->sat);
     void* ptrs[] = {c->occ_bits, c->item_pref, c->tile_count, c->tile_offset, c->done,
                     c->seg_bits, c->active,     c->W,          c->Z,           c->bits,
                     c->d_n,      c->d_status,   c->d_total,    c->d_nseg};
@@ -1983,6 +1986,9 @@ void divas_batch_destroy(divas_batch* b) {
 }
 
 }  // extern "C"
+
+// depth-tuple mode (thick gates on the depth tuple + thin footprint path)
+#include "tuple_mode.cuh"
 
 // ===========================================================================
 // Allocation-free one-shot fusion (no counterpart in the paper)

@@ -144,6 +144,7 @@ enum : int32_t { kMaskF32 = 0, kMaskF16 = 1, kMaskLogit = 2 };
 struct VoxelGeom {
     float xh[3], xl[3];  // plain grid: xh = n = 2 idx + 1, xl unused
     float Delta, invDelta;
+    float hv;            // world edge h_v
     bool ok;  // false: contracted centre with |c| >= 2 (no world position)
 };
 
@@ -186,6 +187,7 @@ __device__ __forceinline__ VoxelGeom voxel_geom(uint32_t pk, const GridC& G, flo
         vg.xh[1] = (float)(2 * j + 1);
         vg.xh[2] = (float)(2 * k + 1);
         vg.xl[0] = vg.xl[1] = vg.xl[2] = 0.f;
+        vg.hv = G.h;
         vg.Delta = __fmul_rn(gamma, G.h);
         vg.invDelta = __frcp_rn(vg.Delta);
         return vg;
@@ -245,6 +247,7 @@ __device__ __forceinline__ VoxelGeom voxel_geom(uint32_t pk, const GridC& G, flo
         const float d = __fadd_rn(dh, dl);
         hv = __fdiv_rn(G.h, __fmul_rn(d, d));  // largest stretch of the inverse contraction
     }
+    vg.hv = hv;
     vg.Delta = __fmul_rn(gamma, hv);
     vg.invDelta = __frcp_rn(vg.Delta);
     return vg;

@@ -102,6 +102,45 @@ def view_c(cam, depth: torch.Tensor, mask: torch.Tensor, mask_type: int | None =
     return v
 
 
+@dataclass
+class TupleParams:
+    """Depth-tuple-mode constants (``divas_tuple_params``; defaults of Table
+    gs-hyperparams, k_dg = 0 and rho_thin = 1)."""
+    beta: float = 0.05
+    gamma_st: float = 1.5
+    tau_thin: float = 0.6
+    rho_cover: float = 0.5
+    rho_occ: float = 0.1
+    n_abs: float = 25.0
+    dist_gate: float = 1.5
+    behind_margin: float = 2.0
+    k_dg: float = 0.0
+    rho_thin: float = 1.0
+
+    def c(self) -> L.DivasTupleParams:
+        return L.DivasTupleParams(*[float(getattr(self, f)) for f in self.__dataclass_fields__])
+
+
+def tuple_views_c(cams, d_min, d_med, d_max, n_samp, masks, d_cams, mask_type: int):
+    """Marshal tuple views (device tensors: float32 depths, uint16-compatible
+    n_samp as torch.int16 / uint16 storage, masks as for ``view_c``)."""
+    arr = (L.DivasTupleView * len(cams))()
+    for k, cam in enumerate(cams):
+        for nm, ten in (("d_min", d_min[k]), ("d_med", d_med[k]), ("d_max", d_max[k])):
+            if ten.dtype != torch.float32 or tuple(ten.shape) != (int(cam.H), int(cam.W)):
+                raise ValueError(f"{nm} must be float32 H x W")
+        if n_samp[k].element_size() != 2 or tuple(n_samp[k].shape) != (int(cam.H), int(cam.W)):
+            raise ValueError("n_samp must be 16-bit H x W")
+        v = arr[k]
+        v.cam = camera_c(cam)
+        v.d_min, v.d_med, v.d_max = _ptr(d_min[k]), _ptr(d_med[k]), _ptr(d_max[k])
+        v.n_samp = _ptr(n_samp[k])
+        v.mask = _ptr(masks[k])
+        v.mask_type = int(mask_type)
+        v.d_cam = float(d_cams[k])
+    return arr
+
+
 class PreparedViews:
     """Views marshalled once into ``divas_view`` structs (chunks of up to 32), so
     that repeated launches skip the per-call Python marshalling.  Keeps the
@@ -209,6 +248,16 @@ class VoxelFusion:
         s = _stream(stream)
         for arr, n in pv.chunks:
             self._check(self.lib.divas_fuse_add_views(self._h, arr, n, s))
+
+    def add_views_tuple(self, cams, d_min, d_med, d_max, n_samp, masks, d_cams, mask_type: int,
+                        tparams: "TupleParams | None" = None, stream=None):
+        """Fold depth-tuple views (``divas_fuse_add_views_tuple``), up to 32."""
+        if len(cams) > L.MAX_VIEWS_PER_CALL:
+            raise ValueError("add_views_tuple() takes up to 32 views")
+        arr = tuple_views_c(cams, d_min, d_med, d_max, n_samp, masks, d_cams, mask_type)
+        tp = (tparams or TupleParams()).c()
+        self._check(self.lib.divas_fuse_add_views_tuple(self._h, arr, len(cams), ctypes.byref(tp),
+                                                        _stream(stream)))
 
     def update(self, views, score: torch.Tensor | None = None,
                seg_bits: torch.Tensor | None = None, keep_zeros: bool = False, stream=None):

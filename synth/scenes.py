@@ -277,7 +277,8 @@ def with_tuple(wl: "Workload", seed: int = 1100, band: float = 2.0, untrusted: f
         front, _back, cross, _hit = render_tuple(wl.scene, cam)
         hitm = np.isfinite(front)
         d_max = front.astype(np.float64) + band * h * (1.0 + 0.5 * rng.uniform(0, 1, front.shape))
-        d_med = front + 0.5 * rng.uniform(0, 1, front.shape) * (d_max - front)
+        with np.errstate(invalid="ignore"):  # misses: inf - inf, replaced by +inf below
+            d_med = front + 0.5 * rng.uniform(0, 1, front.shape) * (d_max - front)
         anom = hitm & (rng.uniform(0, 1, front.shape) < untrusted)
         d_med = np.where(anom, front - rng.uniform(0.1, 1.0, front.shape) * h, d_med)
         inf = np.float32(np.inf)

@@ -39,3 +39,20 @@ def test_default_params_match_paper_constants():
     assert p.tau_mask == c["mask_gate"]["value"]
     assert p.tau_cons == c["tau_cons"]["value"]
     assert p.gamma == c["gamma_gs"]["value"]
+
+
+def test_default_tuple_params_match_paper_constants():
+    import json
+    import math
+    p = L.load().divas_default_tuple_params()
+    c = json.load(open(os.path.join(ROOT, "tests", "golden", "paper_constants.json")))
+    f32 = lambda v: float(__import__("numpy").float32(v))  # noqa: E731
+    assert p.beta == f32(c["beta_gs"]["value"])
+    assert p.gamma_st == f32(c["gamma_st"]["value"])
+    assert p.tau_thin == f32(c["tau_thin"]["value"])
+    assert p.rho_cover == f32(c["rho_cover"]["value"])
+    assert p.rho_occ == f32(c["rho_occ"]["value"])
+    assert p.n_abs == c["n_abs"]["value"]
+    assert p.dist_gate == c["dist_gate_hv"]["value"]
+    assert p.behind_margin == c["behind_margin_hv"]["value"]
+    assert p.k_dg == 0.0 and p.rho_thin == 1.0 and not math.isnan(p.beta)

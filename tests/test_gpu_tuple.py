@@ -1,0 +1,133 @@
+"""Depth-tuple mode (thick gates on the depth tuple + thin footprint path) on
+the GPU against the FP64 oracle: W, Z and view bits per active voxel, with
+the oracle's near-boundary voxels excluded from exact checks (GPU)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from paper_2601_04860_b300 import TupleParams, VoxelFusion
+from tests import gpu_helpers as H
+
+pytestmark = pytest.mark.gpu
+
+
+def _upload_tuple(tw):
+    dev = torch.device("cuda")
+    t = tw.tuple
+    up = {k: [torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in t[k]]
+          for k in ("d_min", "d_med", "d_max")}
+    up["n_samp"] = [torch.from_numpy(np.ascontiguousarray(a).view(np.int16)).to(dev)
+                    for a in t["n_samp"]]
+    if tw.mask_type == oracle.MASK_F16:
+        up["mask"] = [torch.from_numpy(m.view(np.float16)).to(dev) for m in tw.mask]
+    else:
+        up["mask"] = [torch.from_numpy(m).to(dev) for m in tw.mask]
+    up["occ"] = None if tw.occ is None else torch.from_numpy(tw.occ).to(dev)
+    up["coords"] = None if tw.coords is None else torch.from_numpy(tw.coords).to(dev)
+    return up
+
+
+def _gpu(tw, prm, tp, splits=None):
+    up = _upload_tuple(tw)
+    fu = VoxelFusion(tw.grid, occ=up["occ"], coords=up["coords"], params=H.to_params(prm))
+    n = tw.n_views
+    cuts = [0] + (splits or []) + [n]
+    for a, b in zip(cuts[:-1], cuts[1:]):
+        fu.add_views_tuple(tw.cams[a:b], up["d_min"][a:b], up["d_med"][a:b], up["d_max"][a:b],
+                           up["n_samp"][a:b], up["mask"][a:b], tw.tuple["d_cam"][a:b],
+                           tw.mask_type, tparams=TupleParams(**tp.__dict__))
+    st = fu.export_state()
+    out = {"W": st["W"].cpu().numpy(), "Z": st["Z"].cpu().numpy(),
+           "bits": st["bits"].cpu().numpy().view(np.uint32),
+           "active": fu.active_coords().cpu().numpy()}
+    fin = fu.finalize(score=True)
+    out["score"] = fin["score"].cpu().numpy()
+    torch.cuda.synchronize()
+    fu.close()
+    return out
+
+
+def _compare(tw, got, prm, tp):
+    lin = tw.active_linear()
+    g = tw.grid.g
+    act = got["active"].astype(np.int64)
+    assert np.array_equal((act[:, 2] * g + act[:, 1]) * g + act[:, 0], lin)
+    ref = oracle.fuse_tuple(tw.grid, lin, tw.cams, tw.tuple, tw.mask, tw.mask_type,
+                            params=prm.f32(), tparams=tp.f32())
+    ok = ref["flags"] == 0
+    assert ok.mean() > 0.9, ok.mean()
+    assert np.array_equal(got["bits"][ok], ref["bits"][ok]), "view bits differ"
+    assert np.allclose(got["W"][ok], ref["W"][ok], rtol=H.RTOL, atol=1e-30), "W differs"
+    assert np.allclose(got["Z"][ok], ref["Z"][ok], rtol=H.RTOL, atol=1e-30), "Z differs"
+    thick = int((ref["kind"][ok] == 1).sum())
+    thin = int((ref["kind"][ok] == 2).sum())
+    return thick, thin
+
+
+def _dense(**kw):
+    wl = synth.config2(g=64, W=224, H=168, n_ell=50, n_points=100)
+    return synth.with_tuple(wl, **kw)
+
+
+@pytest.mark.parametrize("case", ["thin_on", "paper_defaults", "soft_consensus", "gradient"])
+def test_tuple_dense_matches_oracle(case):
+    tw = _dense()
+    prm, tp = oracle.Params(), oracle.TupleParams(n_abs=4.0)
+    if case == "paper_defaults":
+        tp = oracle.TupleParams()
+    elif case == "soft_consensus":
+        prm, tp = oracle.Params(tau_m=0.3, alpha1=1.0), oracle.TupleParams(n_abs=2.0, tau_thin=0.3)
+    elif case == "gradient":
+        tp = oracle.TupleParams(n_abs=4.0, k_dg=30.0)
+    thick, thin = _compare(tw, _gpu(tw, prm, tp), prm, tp)
+    assert thick > 100
+    if case != "paper_defaults":
+        assert thin > 50
+
+
+def test_tuple_logit_and_f32_masks():
+    tw = _dense()
+    logits = []
+    for m in tw.mask:
+        p = np.clip(m.view(np.float16).astype(np.float64), 1e-4, 1 - 1e-4)
+        logits.append(np.log(p / (1 - p)).astype(np.float32))
+    probs = [m.view(np.float16).astype(np.float32) for m in tw.mask]
+    for masks, mt in ((logits, oracle.MASK_LOGIT_F32), (probs, oracle.MASK_F32)):
+        tw.mask, tw.mask_type = masks, mt
+        thick, thin = _compare(tw, _gpu(tw, oracle.Params(), oracle.TupleParams(n_abs=4.0)),
+                               oracle.Params(), oracle.TupleParams(n_abs=4.0))
+        assert thick > 100 and thin > 50
+
+
+def test_tuple_contracted_and_many_views():
+    wl = synth.config3(g=48, n_views=20, W=162, H=105, n_ell=80, n_occ=None, n_points=100)
+    tw = synth.with_tuple(wl, target=(0.0, 0.0, 0.5))
+    prm, tp = oracle.Params(), oracle.TupleParams(n_abs=2.0)
+    one = _gpu(tw, prm, tp)                 # 20 views: two launches of <= 16
+    thick, _ = _compare(tw, one, prm, tp)
+    assert thick > 100
+    split = _gpu(tw, prm, tp, splits=[7, 13])
+    for k in ("W", "Z", "bits", "score"):
+        assert np.array_equal(one[k], split[k]), f"{k}: split calls differ from one call"
+
+
+def test_tuple_rejects_bad_arguments():
+    import ctypes
+    from paper_2601_04860_b300 import _lib as L
+    from paper_2601_04860_b300.fusion import tuple_views_c
+    tw = synth.with_tuple(synth.config1(g=16, n_points=10))
+    up = _upload_tuple(tw)
+    fu = VoxelFusion(tw.grid, occ=up["occ"], params=H.to_params(oracle.Params()))
+    arr = tuple_views_c(tw.cams[:1], up["d_min"], up["d_med"], up["d_max"], up["n_samp"],
+                        up["mask"], tw.tuple["d_cam"], tw.mask_type)
+    lib = L.load()
+    tp = TupleParams().c()
+    assert lib.divas_fuse_add_views_tuple(fu.handle, arr, 0, ctypes.byref(tp), None) == 1
+    bad = TupleParams(beta=-1.0).c()
+    assert lib.divas_fuse_add_views_tuple(fu.handle, arr, 1, ctypes.byref(bad), None) == 1
+    arr[0].d_med = None
+    assert lib.divas_fuse_add_views_tuple(fu.handle, arr, 1, ctypes.byref(tp), None) == 1
+    assert fu.n_views == 0
+    fu.close()
