@@ -54,9 +54,13 @@ def _env_int(k, d):
         return d
 
 
-# DRAM traffic per launch of the roofline kernel, from one ncu --set full capture
-# (dram__bytes_read.sum + dram__bytes_write.sum), valid only while the kernel
-# sources are byte-identical to the ones profiled.
+# DRAM traffic per launch of the one-call step's kernels, from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum), valid only while the sources
+# those kernels are compiled from are byte-identical to the ones profiled.  The
+# depth-tuple kernels live in their own file (included after the step kernels,
+# in its own functions), so it is not part of the hash.
+STEP_SOURCES = ("include/divas_fuse.h", "paper_2601_04860_b300/csrc/divas_fuse.cu",
+                "paper_2601_04860_b300/csrc/fuse_math.cuh")
 TRAFFIC_CAPTURE = {
     "source_sha1": "c3490904e45c53734c0d84f9f51edfcef6ff8a39",
     "forward-dense-256": {"k_fuse_step": 28_072_448 + 21_315_840,
@@ -66,13 +70,13 @@ TRAFFIC_CAPTURE = {
 
 
 def source_sha1() -> str:
-    """sha1 over 'sha1  path' lines of the CUDA sources (as sha1sum would print)."""
+    """sha1 over 'sha1  path' lines of the step kernels' sources (as sha1sum
+    would print them)."""
     import hashlib
-    d = os.path.join(ROOT, "paper_2601_04860_b300", "csrc")
     lines = []
-    for f in sorted(os.listdir(d)):
-        h = hashlib.sha1(open(os.path.join(d, f), "rb").read()).hexdigest()
-        lines.append(f"{h}  paper_2601_04860_b300/csrc/{f}\n")
+    for f in STEP_SOURCES:
+        h = hashlib.sha1(open(os.path.join(ROOT, f), "rb").read()).hexdigest()
+        lines.append(f"{h}  {f}\n")
     return hashlib.sha1("".join(lines).encode()).hexdigest()
 
 
@@ -542,11 +546,11 @@ def run_ours(args, rank, world, local_rank):
     return res, wl
 
 
-def measure_tuple(dev, steps: int):
+def _tuple_step(dev):
     """Depth-tuple mode on the 256^3 forward-facing scene (8 views 1008x756 with
-    d_min / d_med / d_max / n_samp rasters): one step = occupancy gate + the
-    tuple views (integral images, thick gates, thin footprint path) + finalize
-    + labels, replayed from a CUDA graph, L2 flushed between steps."""
+    d_min / d_med / d_max / n_samp rasters, paper defaults: thick gates + thin
+    footprint path): the context and one step = occupancy gate + the tuple
+    views (integral images, fusion) + finalize + labels."""
     import torch
 
     import synth
@@ -561,7 +565,6 @@ def measure_tuple(dev, steps: int):
     fu = VoxelFusion(tw.grid, occ=occ, params=FusionParams())
     score = torch.empty(fu.n_cells, dtype=torch.float32, device=dev)
     labels = torch.empty(len(tw.points), dtype=torch.uint8, device=dev)
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     tp = TupleParams()
 
     def step():
@@ -570,6 +573,14 @@ def measure_tuple(dev, steps: int):
                            T["d_cam"], tw.mask_type, tparams=tp)
         fu.finalize(score=score)
         fu.label_points(pts, out=labels)
+    return fu, step, tw
+
+
+def measure_tuple(dev, steps: int):
+    """The depth-tuple step replayed from a CUDA graph, L2 flushed between steps."""
+    import torch
+    fu, step, tw = _tuple_step(dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     side = torch.cuda.Stream()
     side.wait_stream(torch.cuda.current_stream())
     with torch.cuda.stream(side):
@@ -599,6 +610,23 @@ def measure_tuple(dev, steps: int):
             "active_updates_per_s": na * S / (m * 1e-3),
             "what": "graph replay of set_occupancy + add_views_tuple (8 views) + finalize + "
                     "label_points; L2 flushed per step"}
+
+
+def profile_tuple_steps(args):
+    """Profiling target of the depth-tuple step: N eager steps (per step:
+    k_tile_count, k_tile_emit, k_mask_tile_max, k_tuple_scan, k_tuple_heavy,
+    k_finalize, k_label on the 256^3 scene, whose footprints are summed
+    directly) and nothing else."""
+    import torch
+    fu, step, _ = _tuple_step(torch.device("cuda"))
+    for _ in range(args.profile_tuple_steps):
+        step()
+    torch.cuda.synchronize()
+    fu.sync()
+    print(json.dumps({"profile_tuple_steps": args.profile_tuple_steps,
+                      "workload": "forward-dense-256-tuple", "active_voxels": fu.n_active}))
+    fu.close()
+    return 0
 
 
 def measure_adjoint(dev, steps: int):
@@ -795,6 +823,8 @@ def run(args):
         return run_reference(args)
     if args.profile_steps:
         return profile_steps(args)
+    if args.profile_tuple_steps:
+        return profile_tuple_steps(args)
     if world > 1:
         import torch
         import torch.distributed as dist
@@ -885,6 +915,8 @@ def main(argv=None):
                     help="timed graph steps only: no eager, per-update, e2e or CPU legs")
     ap.add_argument("--profile-steps", type=int, default=0,
                     help="profiling target: run N eager one-call steps and exit")
+    ap.add_argument("--profile-tuple-steps", type=int, default=0,
+                    help="profiling target: run N eager depth-tuple steps and exit")
     args = ap.parse_args(argv)
     args.warmup = max(3, args.warmup)  # at least 3 untimed warm-up steps
     return run(args)

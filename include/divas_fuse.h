@@ -240,7 +240,7 @@ typedef struct {
 typedef struct {
     float beta;          /* count tightening (0.05)                                       */
     float gamma_st;      /* see-through threshold as a multiple of d_cam (1.5)             */
-    float tau_thin;      /* thin-path acceptance (0.6)                                    */
+    float tau_thin;      /* thin-path acceptance (0.6); must be > 0                       */
     float rho_cover;     /* coverage n_md / n_depth (0.5)                                 */
     float rho_occ;       /* fractional support floor of the footprint area (0.1)           */
     float n_abs;         /* absolute support floor (25)                                   */
@@ -255,10 +255,14 @@ divas_tuple_params divas_default_tuple_params(void);
 
 /* Fold n_views (1..DIVAS_MAX_VIEWS_PER_CALL) tuple views in index order onto
  * the accumulators (view bits continue the context's count); finalize as
- * usual.  Builds per-view integral images in context scratch that grows on
- * demand (the first call with larger views allocates and synchronises; such a
- * call inside a stream capture returns DIVAS_E_STATE).  Footprints must stay
- * below 2^16 pixels for the integral-image sums to be exact. */
+ * usual.  Footprint sums of n_samp come straight from the raster when the
+ * grid's geometry bounds every footprint of a view to at most 256 pixels,
+ * else from per-view integral images built in context scratch that grows on
+ * demand (the first call that needs more allocates and synchronises; such a
+ * call inside a stream capture returns DIVAS_E_STATE).  Integral-image sums
+ * are exact for footprints below 2^16 pixels.  DIVAS_E_INVALID: NULL or
+ * out-of-range arguments (including tau_thin <= 0, where a view without thin
+ * evidence would add a zero vote), before any launch. */
 divas_status divas_fuse_add_views_tuple(divas_ctx* ctx, const divas_tuple_view* views,
                                         int32_t n_views, const divas_tuple_params* tp,
                                         void* stream);
@@ -314,6 +318,14 @@ divas_status divas_fuse_backward(divas_ctx* ctx, const divas_view* views, int32_
  * rounded reciprocal (device n floats each). */
 divas_status divas_debug_rcp(const float* x, int64_t n, float* out_nr, float* out_ieee,
                              void* stream);
+
+/* Test hook: the two integral images the depth-tuple mode builds per view, of
+ * one W x H uint16 raster n_samp (device, row-major) into caller buffers s1
+ * (uint32) and s2 (uint64), each (H + 1) x (W + 1) row-major with a zero
+ * first row and column: s1[y][x] = sum of n over rows < y and columns < x
+ * (mod 2^32), s2 the same of n^2 (mod 2^64).  Synchronises the stream. */
+divas_status divas_debug_integral_images(const uint16_t* n_samp, int32_t W, int32_t H,
+                                         uint32_t* s1, uint64_t* s2, void* stream);
 
 /* Test hook: pixel index iy*W + ix that each active voxel projects to in a
  * camera, or -1 when it is behind z_near or out of frame (device n_active int32). */

@@ -635,7 +635,13 @@ void oracle_fuse_tuple(int g, const double* origin, double h, int contracted, in
                 }
             double n_min = fmax(tp->n_abs, ceil(tp->rho_occ * A_B));
             double gate = tp->dist_gate * hv;
-            near_flag(d2, gate * gate, gate * gate, &flags);
+            {   /* the distance gate compares a distance formed from differences of
+                   coordinates of size |x| + |o|: near it when within 4e-6 of that
+                   size (the 1e-6 margin times 4), not of the gate itself */
+                double xn = sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
+                double on = sqrt(oc[0] * oc[0] + oc[1] * oc[1] + oc[2] * oc[2]);
+                near_flag(sqrt(d2), gate, 4.0 * (1.0 + xn + on), &flags);
+            }
             {   /* ceil near an integer step: flag when the two candidate counts
                    would decide this voxel differently */
                 double k = round(tp->rho_occ * A_B);

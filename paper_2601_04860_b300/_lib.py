@@ -87,6 +87,8 @@ _SIGS = {
                                            ctypes.POINTER(_P), ctypes.POINTER(_P), _P]),
     "divas_debug_project": (ctypes.c_int, [_P, ctypes.POINTER(DivasCamera), _P, _P]),
     "divas_debug_rcp": (ctypes.c_int, [_P, ctypes.c_int64, _P, _P, _P]),
+    "divas_debug_integral_images": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, _P, _P,
+                                                    _P]),
     "divas_fuse_step": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64, ctypes.POINTER(DivasView),
                                        ctypes.c_int32, _P, _P, _P, ctypes.c_int64, _P, _P]),
     "divas_default_tuple_params": (DivasTupleParams, []),

@@ -125,9 +125,34 @@ def test_tuple_rejects_bad_arguments():
     lib = L.load()
     tp = TupleParams().c()
     assert lib.divas_fuse_add_views_tuple(fu.handle, arr, 0, ctypes.byref(tp), None) == 1
-    bad = TupleParams(beta=-1.0).c()
-    assert lib.divas_fuse_add_views_tuple(fu.handle, arr, 1, ctypes.byref(bad), None) == 1
+    for bad in (TupleParams(beta=-1.0).c(), TupleParams(tau_thin=0.0).c()):
+        assert lib.divas_fuse_add_views_tuple(fu.handle, arr, 1, ctypes.byref(bad), None) == 1
     arr[0].d_med = None
     assert lib.divas_fuse_add_views_tuple(fu.handle, arr, 1, ctypes.byref(tp), None) == 1
     assert fu.n_views == 0
     fu.close()
+
+
+@pytest.mark.parametrize("W,H,hi", [(1, 1, 9), (33, 65, 40), (1008, 77, 40), (2100, 40, 65535),
+                                    (1297, 131, 65535)])
+def test_integral_images_exact(W, H, hi):
+    """The per-view integral images of n_samp equal NumPy's exact cumulative
+    sums (uint32 and uint64, modular), ragged strips and column segments
+    included."""
+    from paper_2601_04860_b300 import _lib as L
+    rng = np.random.Generator(np.random.PCG64(W * 7919 + H))
+    n = rng.integers(0, hi + 1, size=(H, W), dtype=np.uint16)
+    dn = torch.from_numpy(n.view(np.int16)).cuda()
+    s1 = torch.empty((H + 1, W + 1), dtype=torch.int32, device="cuda")
+    s2 = torch.empty((H + 1, W + 1), dtype=torch.int64, device="cuda")
+    lib = L.load()
+    assert lib.divas_debug_integral_images(dn.data_ptr(), W, H, s1.data_ptr(), s2.data_ptr(),
+                                           None) == 0
+    n64 = n.astype(np.uint64)
+    e2 = np.zeros((H + 1, W + 1), np.uint64)
+    e2[1:, 1:] = (n64 * n64).cumsum(0).cumsum(1)        # wraps mod 2^64
+    e1 = np.zeros((H + 1, W + 1), np.uint64)
+    e1[1:, 1:] = n64.cumsum(0).cumsum(1)
+    e1 &= np.uint64(0xFFFFFFFF)
+    assert np.array_equal(s1.cpu().numpy().view(np.uint32).astype(np.uint64), e1)
+    assert np.array_equal(s2.cpu().numpy().view(np.uint64), e2)
