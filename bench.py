@@ -546,11 +546,11 @@ def run_ours(args, rank, world, local_rank):
     return res, wl
 
 
-def _tuple_step(dev):
+def _tuple_step(dev, n_abs: float | None = None):
     """Depth-tuple mode on the 256^3 forward-facing scene (8 views 1008x756 with
-    d_min / d_med / d_max / n_samp rasters, paper defaults: thick gates + thin
-    footprint path): the context and one step = occupancy gate + the tuple
-    views (integral images, fusion) + finalize + labels."""
+    d_min / d_med / d_max / n_samp rasters; paper defaults, or another n_abs):
+    the context and one step = occupancy gate + the tuple views (per-view maps,
+    candidate scan, heavy pass) + finalize + labels."""
     import torch
 
     import synth
@@ -565,51 +565,107 @@ def _tuple_step(dev):
     fu = VoxelFusion(tw.grid, occ=occ, params=FusionParams())
     score = torch.empty(fu.n_cells, dtype=torch.float32, device=dev)
     labels = torch.empty(len(tw.points), dtype=torch.uint8, device=dev)
-    tp = TupleParams()
+    tp = TupleParams() if n_abs is None else TupleParams(n_abs=n_abs)
 
-    def step():
+    def step(ev=None):
         fu.set_occupancy(occ=occ)
         fu.add_views_tuple(tw.cams, ras["d_min"], ras["d_med"], ras["d_max"], ns, mask,
-                           T["d_cam"], tw.mask_type, tparams=tp)
+                           T["d_cam"], tw.mask_type, tparams=tp, stage_events=ev)
         fu.finalize(score=score)
         fu.label_points(pts, out=labels)
-    return fu, step, tw
+    return fu, step, tw, tp
+
+
+def _tuple_scan_bytes(tw, n_active: int) -> int:
+    """Algorithmic bytes of one candidate-scan launch (first views of a
+    context): the active list (4 B per voxel) and the zeroed accumulators (12
+    B), plus each view's centre rasters read once (d_min and d_med FP32, the
+    mask)."""
+    mb = 2 if tw.mask_type == 1 else 4
+    return 16 * n_active + sum(c.W * c.H * (8 + mb) for c in tw.cams)
 
 
 def measure_tuple(dev, steps: int):
-    """The depth-tuple step replayed from a CUDA graph, L2 flushed between steps."""
+    """The depth-tuple step replayed from a CUDA graph (events around it only),
+    L2 flushed between steps, for the paper's defaults and with the thin path
+    voting (n_abs = 4); stage times from a second graph whose tuple call
+    records events between its launches; the candidate scan's roofline; the
+    oracle on the host as its CPU baseline."""
     import torch
-    fu, step, tw = _tuple_step(dev)
+    out = {"workload": "forward-dense-256-tuple (config-2 scene with a depth tuple per view: "
+                       "d_min / d_med / d_max FP32, n_samp uint16; 8 views 1008x756)",
+           "what": "graph replay of set_occupancy + add_views_tuple (8 views) + finalize + "
+                   "label_points; L2 flushed per step"}
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-    side = torch.cuda.Stream()
-    side.wait_stream(torch.cuda.current_stream())
-    with torch.cuda.stream(side):
-        for _ in range(3):
-            step()
-    torch.cuda.current_stream().wait_stream(side)
-    torch.cuda.synchronize()
-    ev = [torch.cuda.Event(enable_timing=True, external=True) for _ in range(2)]
-    g = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(g):
-        ev[0].record()
-        step()
-        ev[1].record()
-    ms = []
-    for k in range(3 + steps):
-        flush.zero_()
-        g.replay()
+    peak, peak_kind = peaks()
+    for name, n_abs in (("paper_defaults", None), ("thin_active_n_abs_4", 4.0)):
+        fu, step, tw, tp = _tuple_step(dev, n_abs)
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            for _ in range(3):
+                step()
+        torch.cuda.current_stream().wait_stream(side)
         torch.cuda.synchronize()
-        if k >= 3:
-            ms.append(ev[0].elapsed_time(ev[1]))
-    n, S, na = fu.n_cells, tw.n_views, fu.n_active
-    fu.close()
-    m = float(np.mean(ms))
-    return {"workload": "forward-dense-256-tuple (config-2 scene, depth tuple per view, paper "
-                        "defaults: thick gates + thin footprint path)",
-            "ms_per_step": m, "updates_per_s": n * S / (m * 1e-3),
-            "active_updates_per_s": na * S / (m * 1e-3),
-            "what": "graph replay of set_occupancy + add_views_tuple (8 views) + finalize + "
-                    "label_points; L2 flushed per step"}
+        ev = [torch.cuda.Event(enable_timing=True, external=True) for _ in range(2)]
+        sev = [torch.cuda.Event(enable_timing=True, external=True) for _ in range(4)]
+        for e in sev:
+            e.record()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            ev[0].record()
+            step()
+            ev[1].record()
+        gs = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(gs):
+            step(sev)
+        ms, st = [], {"maps": [], "scan": [], "heavy": []}
+        for k in range(3 + steps):
+            flush.zero_()
+            g.replay()
+            torch.cuda.synchronize()
+            flush.zero_()
+            gs.replay()
+            torch.cuda.synchronize()
+            if k >= 3:
+                ms.append(ev[0].elapsed_time(ev[1]))
+                st["maps"].append(sev[0].elapsed_time(sev[1]))
+                st["scan"].append(sev[1].elapsed_time(sev[2]))
+                st["heavy"].append(sev[2].elapsed_time(sev[3]))
+        n, S, na = fu.n_cells, tw.n_views, fu.n_active
+        m = float(np.mean(ms))
+        stm = {k: float(np.mean(v)) for k, v in st.items()}
+        scan_bytes = _tuple_scan_bytes(tw, na)
+        ach = scan_bytes / (stm["scan"] * 1e-3) / 1e9
+        out[name] = {"n_abs": tp.n_abs, "ms_per_step": m, "updates_per_s": n * S / (m * 1e-3),
+                     "active_updates_per_s": na * S / (m * 1e-3),
+                     "stage_ms": stm,
+                     "roofline": {"bound": "hbm", "kernel": "k_tuple_scan", "achieved": ach,
+                                  "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                                  "traffic": None, "peak_kind": peak_kind,
+                                  "algorithmic_bytes_per_launch": scan_bytes,
+                                  "ms_per_launch": stm["scan"]}}
+        fu.close()
+    out["cpu_baseline"] = tuple_cpu_baseline(tw)
+    return out
+
+
+def tuple_cpu_baseline(tw):
+    """The oracle's depth-tuple fusion (paper defaults) on the host cores over
+    every active voxel x 8 views of the 256^3 scene, as nominal voxel-view
+    updates/s (g^3 x views / time)."""
+    import oracle
+    cores = oracle.set_threads(0)
+    lin = tw.active_linear()
+    t0 = time.perf_counter()
+    oracle.fuse_tuple(tw.grid, lin, tw.cams, tw.tuple, tw.mask, tw.mask_type,
+                      params=oracle.Params().f32(), tparams=oracle.TupleParams().f32())
+    dt = time.perf_counter() - t0
+    g = tw.grid.g
+    return {"value": g ** 3 * tw.n_views / dt, "unit": UNIT, "cores": cores,
+            "kind": "oracle", "seconds": dt,
+            "sample": f"all {len(lin)} active voxels x {tw.n_views} views (fusion only, no "
+                      "finalize or labels)"}
 
 
 def profile_tuple_steps(args):
@@ -618,7 +674,7 @@ def profile_tuple_steps(args):
     k_finalize, k_label on the 256^3 scene, whose footprints are summed
     directly) and nothing else."""
     import torch
-    fu, step, _ = _tuple_step(torch.device("cuda"))
+    fu, step, _, _ = _tuple_step(torch.device("cuda"))
     for _ in range(args.profile_tuple_steps):
         step()
     torch.cuda.synchronize()

@@ -267,6 +267,15 @@ divas_status divas_fuse_add_views_tuple(divas_ctx* ctx, const divas_tuple_view* 
                                         int32_t n_views, const divas_tuple_params* tp,
                                         void* stream);
 
+/* divas_fuse_add_views_tuple that also records stage_events[k] (cudaEvent_t,
+ * entries nullable; the array nullable) on `stream`: [0] before the per-view
+ * maps (mask-tile maxima, integral images), [1] after them, [2] after the
+ * candidate scan of the last 16-view batch, [3] after its heavy pass.  Inside
+ * a stream capture they become external event-record nodes. */
+divas_status divas_fuse_add_views_tuple_profiled(divas_ctx* ctx, const divas_tuple_view* views,
+                                                 int32_t n_views, const divas_tuple_params* tp,
+                                                 void* const* stage_events, void* stream);
+
 /* Pass 1 labels (Eq. pass1): labels_out[i] = seg bit of the voxel containing
  * point i (device n x 3 float32), 0 outside the grid (half-open box), for NaN,
  * or for unoccupied voxels.  Uses the seg bitfield of the last finalize. */

@@ -95,6 +95,10 @@ _SIGS = {
     "divas_fuse_add_views_tuple": (ctypes.c_int, [_P, ctypes.POINTER(DivasTupleView),
                                                   ctypes.c_int32,
                                                   ctypes.POINTER(DivasTupleParams), _P]),
+    "divas_fuse_add_views_tuple_profiled": (ctypes.c_int, [_P, ctypes.POINTER(DivasTupleView),
+                                                           ctypes.c_int32,
+                                                           ctypes.POINTER(DivasTupleParams), _P,
+                                                           _P]),
     "divas_fuse_update": (ctypes.c_int, [_P, ctypes.POINTER(DivasView), ctypes.c_int32, _P, _P,
                                          ctypes.c_uint32, _P]),
     "divas_fuse_step_profiled": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64,

@@ -899,6 +899,12 @@ divas_tuple_params divas_default_tuple_params(void) {
 divas_status divas_fuse_add_views_tuple(divas_ctx* c, const divas_tuple_view* views,
                                         int32_t n_views, const divas_tuple_params* tp,
                                         void* stream) {
+    return divas_fuse_add_views_tuple_profiled(c, views, n_views, tp, nullptr, stream);
+}
+
+divas_status divas_fuse_add_views_tuple_profiled(divas_ctx* c, const divas_tuple_view* views,
+                                                 int32_t n_views, const divas_tuple_params* tp,
+                                                 void* const* stage_events, void* stream) {
     if (!c) return fail(nullptr, DIVAS_E_INVALID, "ctx is NULL");
     if (!views || !tp || n_views < 1 || n_views > kMaxViews)
         return fail(c, DIVAS_E_INVALID, "n_views must be in 1..32, views and tp non-NULL");
@@ -951,6 +957,8 @@ divas_status divas_fuse_add_views_tuple(divas_ctx* c, const divas_tuple_view* vi
     T.k_dg = tp->k_dg;
     T.thin_on = tp->rho_thin <= 1.f ? 1 : 0;
     T.pad = 0;
+    divas_status st = record_stage(c, stage_events, 0, s);
+    if (st != DIVAS_OK) return st;
     unsigned char* cur = static_cast<unsigned char*>(c->sat);
     int32_t* n_heavy = reinterpret_cast<int32_t*>(cur);
     uint2* heavy = reinterpret_cast<uint2*>(cur + 256);
@@ -1013,7 +1021,10 @@ divas_status divas_fuse_add_views_tuple(divas_ctx* c, const divas_tuple_view* vi
         k_sat_strip_fill<<<dim3(max_strips, jobs.n), kSatThreads, 0, s>>>(jobs);
         DIVAS_LAUNCHED(c, "k_sat_strip_fill");
     }
+    st = record_stage(c, stage_events, 1, s);
+    if (st != DIVAS_OK) return st;
     for (int32_t k0 = 0; k0 < n_views; k0 += kMaxTupleViews) {
+        const bool last = k0 + kMaxTupleViews >= n_views;
         TViewBatch tb;
         memset(&tb, 0, sizeof(tb));
         tb.n = std::min<int32_t>(kMaxTupleViews, n_views - k0);
@@ -1054,21 +1065,23 @@ divas_status divas_fuse_add_views_tuple(divas_ctx* c, const divas_tuple_view* vi
         const int32_t acc = c->n_views + k0 > 0 ? 1 : 0;
         DIVAS_CUDA(c, cudaMemsetAsync(n_heavy, 0, sizeof(int32_t), s));
         const int nv = tb.n;
-        if (c->G.contracted) {
-            const divas_status st = launch_tuple_scan<true>(nv, blocks, s, c, tb, T, acc, heavy, n_heavy);
+        st = c->G.contracted ? launch_tuple_scan<true>(nv, blocks, s, c, tb, T, acc, heavy, n_heavy)
+                             : launch_tuple_scan<false>(nv, blocks, s, c, tb, T, acc, heavy, n_heavy);
+        if (st != DIVAS_OK) return st;
+        if (last) {
+            st = record_stage(c, stage_events, 2, s);
             if (st != DIVAS_OK) return st;
+        }
+        if (c->G.contracted)
             k_tuple_heavy<true><<<blocks, kThreads, 0, s>>>(c->active, heavy, n_heavy, c->G, c->F, tb,
                                                             T, c->W, c->Z, c->bits);
-        } else {
-            const divas_status st = launch_tuple_scan<false>(nv, blocks, s, c, tb, T, acc, heavy, n_heavy);
-            if (st != DIVAS_OK) return st;
+        else
             k_tuple_heavy<false><<<blocks, kThreads, 0, s>>>(c->active, heavy, n_heavy, c->G, c->F, tb,
                                                              T, c->W, c->Z, c->bits);
-        }
         DIVAS_LAUNCHED(c, "k_tuple_heavy");
     }
     c->n_views += n_views;
-    return DIVAS_OK;
+    return record_stage(c, stage_events, 3, s);
 }
 
 divas_status divas_debug_integral_images(const uint16_t* n_samp, int32_t W, int32_t H,

@@ -250,14 +250,25 @@ class VoxelFusion:
             self._check(self.lib.divas_fuse_add_views(self._h, arr, n, s))
 
     def add_views_tuple(self, cams, d_min, d_med, d_max, n_samp, masks, d_cams, mask_type: int,
-                        tparams: "TupleParams | None" = None, stream=None):
-        """Fold depth-tuple views (``divas_fuse_add_views_tuple``), up to 32."""
+                        tparams: "TupleParams | None" = None, stage_events=None, stream=None):
+        """Fold depth-tuple views (``divas_fuse_add_views_tuple``), up to 32.
+        ``stage_events``: optional four ``torch.cuda.Event`` (timing enabled)
+        marking before the per-view maps / after them / after the candidate
+        scan / after the heavy pass (``divas_fuse_add_views_tuple_profiled``)."""
         if len(cams) > L.MAX_VIEWS_PER_CALL:
             raise ValueError("add_views_tuple() takes up to 32 views")
         arr = tuple_views_c(cams, d_min, d_med, d_max, n_samp, masks, d_cams, mask_type)
         tp = (tparams or TupleParams()).c()
-        self._check(self.lib.divas_fuse_add_views_tuple(self._h, arr, len(cams), ctypes.byref(tp),
-                                                        _stream(stream)))
+        if stage_events is None:
+            self._check(self.lib.divas_fuse_add_views_tuple(self._h, arr, len(cams),
+                                                            ctypes.byref(tp), _stream(stream)))
+            return
+        if len(stage_events) != 4:
+            raise ValueError("stage_events takes four events")
+        evs = (ctypes.c_void_p * 4)(*[(e.cuda_event if e is not None else None)
+                                      for e in stage_events])
+        self._check(self.lib.divas_fuse_add_views_tuple_profiled(
+            self._h, arr, len(cams), ctypes.byref(tp), evs, _stream(stream)))
 
     def update(self, views, score: torch.Tensor | None = None,
                seg_bits: torch.Tensor | None = None, keep_zeros: bool = False, stream=None):
