@@ -276,6 +276,46 @@ divas_status divas_fuse_add_views_tuple_profiled(divas_ctx* ctx, const divas_tup
                                                  int32_t n_views, const divas_tuple_params* tp,
                                                  void* const* stage_events, void* stream);
 
+/*
+ * Depth-weighted mask refinement (Sec. 3.4 "Depth-weighting: bounded
+ * normalization (NeRF) vs. band-pass (2DGS)"), a per-view pre-pass whose
+ * output is folded like any FP32 mask (add_views, add_views_tuple, update):
+ *   DIVAS_WEIGHT_NERF_MINMAX (Eq. nerf-depthweight): M~ = M (1 - Z^),
+ *     Z^ = (D - min D) / (max D - min D) over the view's depth raster D;
+ *   DIVAS_WEIGHT_GS_BAND (Eqs. depthband, gs-bandpass): [d_min, d_max] = the
+ *     range of D at the positive prompts and at the view centre pixel
+ *     (W / 2, H / 2) (integer halves), d_far = P98(D) (linear interpolation
+ *     between the order statistics of ranks floor(0.98 (n - 1)) and the next,
+ *     found exactly), M~ = M (1 - clip((max(d_min - D, 0) + max(D - d_max,
+ *     0)) / max(d_far - d_max, 1e-6), 0, 1)).
+ * M is the mask probability (binary16, FP32, or the sigmoid of FP32 logits).
+ * Non-finite depth means no surface: M~ = 0 there, and such pixels take no
+ * part in min, max or the percentile; prompts / the centre at non-finite
+ * depth are skipped; with none left (band) or max == min (min-max) the
+ * weight is 1 on finite pixels.
+ */
+#define DIVAS_MAX_PROMPTS 15
+enum { DIVAS_WEIGHT_NERF_MINMAX = 1, DIVAS_WEIGHT_GS_BAND = 2 };
+
+typedef struct {
+    const float* depth;   /* device H x W FP32 depth (D_exp or D_med), row-major          */
+    const void* mask;     /* device H x W mask of mask_type                               */
+    float* out;           /* device H x W FP32: the weighted mask (caller-owned)          */
+    int32_t mask_type;    /* DIVAS_MASK_*                                                 */
+    int32_t W, H;
+    int32_t n_prompts;    /* GS_BAND: 0..DIVAS_MAX_PROMPTS positive prompts               */
+    int32_t prompt_xy[2 * DIVAS_MAX_PROMPTS]; /* (x, y) pixel of each prompt, in frame    */
+} divas_weight_view;
+
+/* Weight n_views (1..DIVAS_MAX_VIEWS_PER_CALL) masks in `mode` on `stream`
+ * (one launch per pass for all views; scratch in the context grows on demand
+ * like the tuple scratch).  stats_out (device, nullable): n_views x 4 floats,
+ * (min D, max D, n_finite, 0) for NERF_MINMAX, (d_min, d_max, d_far,
+ * n_finite) for GS_BAND, NaN where undefined.  DIVAS_E_INVALID before any
+ * launch: NULL rasters, bad sizes or mask_type, prompts outside the view. */
+divas_status divas_depth_weight(divas_ctx* ctx, const divas_weight_view* views, int32_t n_views,
+                                int32_t mode, float* stats_out, void* stream);
+
 /* Pass 1 labels (Eq. pass1): labels_out[i] = seg bit of the voxel containing
  * point i (device n x 3 float32), 0 outside the grid (half-open box), for NaN,
  * or for unoccupied voxels.  Uses the seg bitfield of the last finalize. */

@@ -19,6 +19,9 @@ MASK_F16 = 1
 MASK_LOGIT_F32 = 2
 MAX_VIEWS_PER_CALL = 32
 KEEP_ZEROS = 1
+MAX_PROMPTS = 15
+WEIGHT_NERF_MINMAX = 1
+WEIGHT_GS_BAND = 2
 
 
 class DivasParams(ctypes.Structure):
@@ -54,6 +57,12 @@ class DivasTupleParams(ctypes.Structure):
     _fields_ = [(n, ctypes.c_float) for n in
                 ("beta", "gamma_st", "tau_thin", "rho_cover", "rho_occ", "n_abs", "dist_gate",
                  "behind_margin", "k_dg", "rho_thin")]
+
+
+class DivasWeightView(ctypes.Structure):
+    _fields_ = [("depth", ctypes.c_void_p), ("mask", ctypes.c_void_p), ("out", ctypes.c_void_p),
+                ("mask_type", ctypes.c_int32), ("W", ctypes.c_int32), ("H", ctypes.c_int32),
+                ("n_prompts", ctypes.c_int32), ("prompt_xy", ctypes.c_int32 * (2 * 15))]
 
 
 class DivasError(RuntimeError):
@@ -92,6 +101,8 @@ _SIGS = {
     "divas_fuse_step": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64, ctypes.POINTER(DivasView),
                                        ctypes.c_int32, _P, _P, _P, ctypes.c_int64, _P, _P]),
     "divas_default_tuple_params": (DivasTupleParams, []),
+    "divas_depth_weight": (ctypes.c_int, [_P, ctypes.POINTER(DivasWeightView), ctypes.c_int32,
+                                          ctypes.c_int32, _P, _P]),
     "divas_fuse_add_views_tuple": (ctypes.c_int, [_P, ctypes.POINTER(DivasTupleView),
                                                   ctypes.c_int32,
                                                   ctypes.POINTER(DivasTupleParams), _P]),

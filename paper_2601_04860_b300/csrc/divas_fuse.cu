@@ -791,6 +791,8 @@ struct divas_ctx {
     FastDiv gdiv;  // division by g
     void* sat = nullptr;   // tuple mode: integral-image scratch, grown on demand
     size_t sat_bytes = 0;
+    void* wt = nullptr;    // depth weighting: selection state and histograms, grown on demand
+    size_t wt_bytes = 0;
     float* W = nullptr;
     float* Z = nullptr;
     uint32_t* bits = nullptr;
@@ -1032,6 +1034,7 @@ divas_status read_status(divas_ctx* c, cudaStream_t s) {
 
 void free_all(divas_ctx* c) {
     if (c->sat) cudaFree(c->sat);
+    if (c->wt) cudaFree(c->wt);
     void* ptrs[] = {c->occ_bits, c->item_pref, c->tile_count, c->tile_offset, c->done,
                     c->seg_bits, c->active,     c->W,          c->Z,           c->bits,
                     c->d_n,      c->d_status,   c->d_total,    c->d_nseg};
@@ -1989,6 +1992,7 @@ void divas_batch_destroy(divas_batch* b) {
 
 // depth-tuple mode (thick gates on the depth tuple + thin footprint path)
 #include "tuple_mode.cuh"
+#include "weighting.cuh"
 
 // ===========================================================================
 // Allocation-free one-shot fusion (no counterpart in the paper)

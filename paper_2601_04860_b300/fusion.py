@@ -270,6 +270,43 @@ class VoxelFusion:
         self._check(self.lib.divas_fuse_add_views_tuple_profiled(
             self._h, arr, len(cams), ctypes.byref(tp), evs, _stream(stream)))
 
+    def depth_weight(self, depths, masks, mask_type: int, mode: str = "band", prompts=None,
+                     out=None, stats: bool = False, stream=None):
+        """Depth-weighted masks (``divas_depth_weight``) of up to 32 views:
+        ``mode`` "nerf" (Eq. nerf-depthweight: min-max-normalised depth) or
+        "band" (Eqs. depthband, gs-bandpass: the depth band of ``prompts``,
+        per view a list of (x, y) pixels, and the view centre, with the
+        98th-percentile far depth).  Returns the FP32 weighted masks (``out``
+        or new tensors) and, with ``stats``, an (n, 4) float32 tensor of the
+        per-view constants."""
+        n = len(depths)
+        if n < 1 or n > L.MAX_VIEWS_PER_CALL or len(masks) != n:
+            raise ValueError("depth_weight() takes 1..32 views with one mask each")
+        m = {"nerf": L.WEIGHT_NERF_MINMAX, "band": L.WEIGHT_GS_BAND}[mode]
+        prompts = prompts if prompts is not None else [[] for _ in range(n)]
+        if out is None:
+            out = [torch.empty(d.shape, dtype=torch.float32, device=d.device) for d in depths]
+        arr = (L.DivasWeightView * n)()
+        for k in range(n):
+            d, mk, o = depths[k], masks[k], out[k]
+            if d.dtype != torch.float32 or d.dim() != 2 or not d.is_contiguous():
+                raise ValueError("depth rasters must be contiguous (H, W) float32")
+            if o.shape != d.shape or o.dtype != torch.float32 or not o.is_contiguous():
+                raise ValueError("out rasters must be contiguous (H, W) float32")
+            if mk.shape != d.shape or not mk.is_contiguous():
+                raise ValueError("masks must be contiguous (H, W)")
+            pk = list(prompts[k])
+            if len(pk) > L.MAX_PROMPTS:
+                raise ValueError("at most 15 prompts per view")
+            arr[k].depth, arr[k].mask, arr[k].out = d.data_ptr(), mk.data_ptr(), o.data_ptr()
+            arr[k].mask_type, arr[k].H, arr[k].W = mask_type, d.shape[0], d.shape[1]
+            arr[k].n_prompts = len(pk)
+            for q, (x, y) in enumerate(pk):
+                arr[k].prompt_xy[2 * q], arr[k].prompt_xy[2 * q + 1] = int(x), int(y)
+        st = torch.empty((n, 4), dtype=torch.float32, device=depths[0].device) if stats else None
+        self._check(self.lib.divas_depth_weight(self._h, arr, n, m, _ptr(st), _stream(stream)))
+        return (out, st) if stats else out
+
     def update(self, views, score: torch.Tensor | None = None,
                seg_bits: torch.Tensor | None = None, keep_zeros: bool = False, stream=None):
         """Incremental update: fold ``views`` (a ``PreparedViews`` or one

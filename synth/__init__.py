@@ -27,5 +27,6 @@ from .scenes import (  # noqa: F401
     render_tuple,
     session_mix,
     session_workload,
+    prompts,
     with_tuple,
 )

@@ -294,6 +294,25 @@ def with_tuple(wl: "Workload", seed: int = 1100, band: float = 2.0, untrusted: f
     return out
 
 
+def prompts(wl: "Workload", n: int = 3, seed: int = 1200, thresh: float = 0.9) -> list:
+    """Positive prompts per view, the clicks a user would place on the target:
+    up to n pixels (x, y) drawn (seeded, without replacement) from those whose
+    mask probability exceeds thresh."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for m in wl.mask:
+        if wl.mask_type == 1:
+            p = np.asarray(m).view(np.float16).astype(np.float64)
+        elif wl.mask_type == 2:
+            p = 1.0 / (1.0 + np.exp(-np.asarray(m, np.float64)))
+        else:
+            p = np.asarray(m, np.float64)
+        ys, xs = np.nonzero(p > thresh)
+        pick = rng.choice(len(xs), size=min(n, len(xs)), replace=False) if len(xs) else []
+        out.append([(int(xs[i]), int(ys[i])) for i in pick])
+    return out
+
+
 def soft_mask_f16(indicator: np.ndarray, rng, sigma=2.0, radius=6, noise_std=0.05) -> np.ndarray:
     """Indicator -> Gaussian blur (sigma px, clamp-to-edge) -> + N(0, noise_std)
     -> clamp [0, 1] -> binary16 bits (uint16)."""
