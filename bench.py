@@ -685,6 +685,125 @@ def profile_tuple_steps(args):
     return 0
 
 
+def _weight_step(dev, mode: str):
+    """Depth-weighted masks on the 256^3 forward-facing scene (8 views
+    1008x756, FP16 masks, 3 positive prompts per view on the target): the
+    context and one step = depth_weight (8 views) + occupancy gate + the
+    weighted views + finalize + labels."""
+    import torch
+
+    import synth
+    from paper_2601_04860_b300 import MASK_F32, FusionParams, VoxelFusion
+    wl = synth.config2()
+    pr = synth.prompts(wl)
+    occ = torch.from_numpy(wl.occ).to(dev)
+    depth = [torch.from_numpy(x).to(dev) for x in wl.depth]
+    mask = [torch.from_numpy(m.view(np.int16)).to(dev) for m in wl.mask]
+    wbuf = [torch.empty(x.shape, dtype=torch.float32, device=dev) for x in depth]
+    pts = torch.from_numpy(np.ascontiguousarray(wl.points)).to(dev)
+    fu = VoxelFusion(wl.grid, occ=occ, params=FusionParams())
+    score = torch.empty(fu.n_cells, dtype=torch.float32, device=dev)
+    labels = torch.empty(len(wl.points), dtype=torch.uint8, device=dev)
+
+    def step(ev=None):
+        if ev:
+            ev[0].record()
+        fu.depth_weight(depth, mask, wl.mask_type, mode=mode, prompts=pr, out=wbuf)
+        if ev:
+            ev[1].record()
+        fu.set_occupancy(occ=occ)
+        fu.add_views(wl.cams, depth, wbuf, mask_type=MASK_F32)
+        fu.finalize(score=score)
+        fu.label_points(pts, out=labels)
+    return fu, step, wl, pr
+
+
+def measure_weighting(dev, steps: int):
+    """The depth-weighted step replayed from a CUDA graph (events around it),
+    L2 flushed between steps, for the band-pass (with P98 selection) and the
+    min-max weighting; the weighting stage's time from events inside a
+    second graph, its roofline, and the oracle on the host."""
+    import torch
+    out = {"workload": "forward-dense-256-weighted (config-2 scene; 8 views 1008x756, FP16 "
+                       "masks, 3 positive prompts per view; weighted masks FP32)",
+           "what": "graph replay of depth_weight (8 views) + set_occupancy + add_views "
+                   "(weighted masks) + finalize + label_points; L2 flushed per step"}
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    peak, peak_kind = peaks()
+    for mode in ("band", "nerf"):
+        fu, step, wl, pr = _weight_step(dev, mode)
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            for _ in range(3):
+                step()
+        torch.cuda.current_stream().wait_stream(side)
+        torch.cuda.synchronize()
+        ev = [torch.cuda.Event(enable_timing=True, external=True) for _ in range(2)]
+        sev = [torch.cuda.Event(enable_timing=True, external=True) for _ in range(2)]
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            ev[0].record()
+            step()
+            ev[1].record()
+        gs = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(gs):
+            step(sev)
+        ms, wms = [], []
+        for k in range(3 + steps):
+            flush.zero_()
+            g.replay()
+            torch.cuda.synchronize()
+            flush.zero_()
+            gs.replay()
+            torch.cuda.synchronize()
+            if k >= 3:
+                ms.append(ev[0].elapsed_time(ev[1]))
+                wms.append(sev[0].elapsed_time(sev[1]))
+        m, w = float(np.mean(ms)), float(np.mean(wms))
+        algo = sum(c.W * c.H * (4 + 2 + 4) for c in wl.cams)  # depth, FP16 mask, FP32 out
+        ach = algo / (w * 1e-3) / 1e9
+        out[mode] = {"ms_per_step": m, "updates_per_s": fu.n_cells * wl.n_views / (m * 1e-3),
+                     "weighting_ms": w,
+                     "roofline": {"bound": "hbm", "kernel": "depth_weight (all passes)",
+                                  "achieved": ach, "peak": peak, "unit": "GB/s",
+                                  "frac": ach / peak, "traffic": None, "peak_kind": peak_kind,
+                                  "algorithmic_bytes_per_launch": algo, "ms_per_launch": w}}
+        fu.close()
+    out["cpu_baseline"] = weighting_cpu_baseline(wl, pr)
+    return out
+
+
+def weighting_cpu_baseline(wl, pr):
+    """The oracle's band-pass weighting (FP64 NumPy, one host thread) of the
+    8 views, as weighted pixels/s."""
+    import oracle.weighting as OW
+    t0 = time.perf_counter()
+    for k in range(wl.n_views):
+        OW.gs_band(wl.depth[k], wl.mask[k], wl.mask_type, pr[k])
+    dt = time.perf_counter() - t0
+    px = sum(c.W * c.H for c in wl.cams)
+    return {"value": px / dt, "unit": "weighted pixels/s", "cores": 1, "kind": "oracle",
+            "seconds": dt, "sample": f"all {wl.n_views} views (band-pass, with P98)"}
+
+
+def profile_weight_steps(args):
+    """Profiling target of the depth-weighted step (band-pass): N eager steps
+    (per step: k_weight_init, k_weight_pass1, k_weight_digit x2,
+    k_weight_final, k_weight_apply, then k_tile_count, k_tile_emit, k_fuse,
+    k_finalize, k_label) and nothing else."""
+    import torch
+    fu, step, _, _ = _weight_step(torch.device("cuda"), "band")
+    for _ in range(args.profile_weight_steps):
+        step()
+    torch.cuda.synchronize()
+    fu.sync()
+    print(json.dumps({"profile_weight_steps": args.profile_weight_steps,
+                      "workload": "forward-dense-256-weighted"}))
+    fu.close()
+    return 0
+
+
 def measure_adjoint(dev, steps: int):
     """Config 4: forward + hand-written backward through the autograd Function on
     the 256^3 forward-facing scene with FP32 logits and depth as leaves."""
@@ -881,6 +1000,8 @@ def run(args):
         return profile_steps(args)
     if args.profile_tuple_steps:
         return profile_tuple_steps(args)
+    if args.profile_weight_steps:
+        return profile_weight_steps(args)
     if world > 1:
         import torch
         import torch.distributed as dist
@@ -898,6 +1019,10 @@ def run(args):
     if not args.quick and not args.no_tuple and args.workload == "forward-dense-256":
         import torch
         res["tuple"] = measure_tuple(torch.device("cuda", local_rank), max(5, args.steps // 2))
+    if not args.quick and not args.no_weighting and args.workload == "forward-dense-256":
+        import torch
+        res["weighting"] = measure_weighting(torch.device("cuda", local_rank),
+                                             max(5, args.steps // 2))
     if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.quick:
         full_s, det = oracle_rate(wl, args.cpu_seconds)
         N = res["config"]["voxels_nominal"]
@@ -962,6 +1087,8 @@ def main(argv=None):
     ap.add_argument("--no-adjoint", action="store_true", help="skip the forward+backward leg")
     ap.add_argument("--no-sessions", action="store_true", help="skip the batched/served leg")
     ap.add_argument("--no-tuple", action="store_true", help="skip the depth-tuple-mode leg")
+    ap.add_argument("--no-weighting", action="store_true",
+                    help="skip the depth-weighted-mask leg")
     ap.add_argument("--sessions", type=int, default=32, help="sessions in the batched/served leg")
     ap.add_argument("--sessions-scale", type=float, default=0.5,
                     help="size scale of the sessions (1.0 = the full session mix)")
@@ -973,6 +1100,8 @@ def main(argv=None):
                     help="profiling target: run N eager one-call steps and exit")
     ap.add_argument("--profile-tuple-steps", type=int, default=0,
                     help="profiling target: run N eager depth-tuple steps and exit")
+    ap.add_argument("--profile-weight-steps", type=int, default=0,
+                    help="profiling target: run N eager depth-weighted steps and exit")
     args = ap.parse_args(argv)
     args.warmup = max(3, args.warmup)  # at least 3 untimed warm-up steps
     return run(args)

@@ -23,6 +23,7 @@ namespace {
 constexpr int kWeightPrompts = DIVAS_MAX_PROMPTS + 1;  // + the view centre
 constexpr int kRadixBins = 2048;                       // 11-bit digits
 constexpr int kWeightThreads = 256;
+constexpr int kUnroll = 4;                             // pixels per thread with loads in flight
 
 struct WJob {
     const float* depth;
@@ -154,19 +155,26 @@ __global__ void __launch_bounds__(kWeightThreads) k_weight_pass1(const __grid_co
     __syncthreads();
     const int32_t npix = jb.W * jb.H;
     uint32_t cnt = 0u, lo = 0xffffffffu, hi = 0u;
-    // warp-uniform loop (the histogram step shuffles)
-    for (int32_t base = (blockIdx.x * kWeightThreads + threadIdx.x) & ~31; base < npix;
-         base += gridDim.x * kWeightThreads) {
-        const int32_t i = base + (threadIdx.x & 31);
-        const float d = i < npix ? __ldg(jb.depth + i) : 0.f;
-        const bool fin = i < npix && finite_f(d);
-        const uint32_t key = fin ? float_key(d) : 0u;
-        cnt += fin ? 1u : 0u;
-        if (fin) {
-            lo = min(lo, key);
-            hi = max(hi, key);
+    const int32_t stride = gridDim.x * kWeightThreads;
+    // warp-uniform loop (the histogram step shuffles), kUnroll loads in flight
+    for (int32_t b0 = (blockIdx.x * kWeightThreads + threadIdx.x) & ~31; b0 < npix; b0 += kUnroll * stride) {
+        float d[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            const int32_t i = b0 + (threadIdx.x & 31) + u * stride;
+            d[u] = i < npix ? __ldg(jb.depth + i) : __int_as_float(0x7fc00000);
         }
-        if (band) hist_add(sh, fin, key >> 21);
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            const bool fin = finite_f(d[u]);
+            const uint32_t key = fin ? float_key(d[u]) : 0u;
+            cnt += fin ? 1u : 0u;
+            if (fin) {
+                lo = min(lo, key);
+                hi = max(hi, key);
+            }
+            if (band) hist_add(sh, fin, key >> 21);
+        }
     }
     // block reductions
     cnt = __reduce_add_sync(0xffffffffu, cnt);
@@ -228,14 +236,21 @@ __global__ void __launch_bounds__(kWeightThreads) k_weight_digit(const __grid_co
     const int sh_p = digit_shift(P);
     const uint32_t dmask = (1u << digit_width(P)) - 1u;
     const int32_t npix = jb.W * jb.H;
-    for (int32_t base = (blockIdx.x * kWeightThreads + threadIdx.x) & ~31; base < npix;
-         base += gridDim.x * kWeightThreads) {
-        const int32_t i = base + (threadIdx.x & 31);
-        const float d = i < npix ? __ldg(jb.depth + i) : 0.f;
-        const bool fin = i < npix && finite_f(d);
-        const uint32_t key = fin ? float_key(d) : 0u;
-        const bool match = fin && (key >> hi_shift) == (prefix >> hi_shift);
-        hist_add(sh, match, (key >> sh_p) & dmask);
+    const int32_t stride = gridDim.x * kWeightThreads;
+    for (int32_t b0 = (blockIdx.x * kWeightThreads + threadIdx.x) & ~31; b0 < npix; b0 += kUnroll * stride) {
+        float d[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            const int32_t i = b0 + (threadIdx.x & 31) + u * stride;
+            d[u] = i < npix ? __ldg(jb.depth + i) : __int_as_float(0x7fc00000);
+        }
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            const bool fin = finite_f(d[u]);
+            const uint32_t key = fin ? float_key(d[u]) : 0u;
+            const bool match = fin && (key >> hi_shift) == (prefix >> hi_shift);
+            hist_add(sh, match, (key >> sh_p) & dmask);
+        }
     }
     __syncthreads();
     hist_merge(sh, H + P * kRadixBins);
@@ -262,13 +277,21 @@ __global__ void __launch_bounds__(kWeightThreads) k_weight_final(const __grid_co
     __syncthreads();
     uint32_t le = 0u, gt = 0xffffffffu;
     const int32_t npix = jb.W * jb.H;
-    for (int32_t i = blockIdx.x * kWeightThreads + threadIdx.x; i < npix;
-         i += gridDim.x * kWeightThreads) {
-        const float d = __ldg(jb.depth + i);
-        if (!finite_f(d)) continue;
-        const uint32_t key = float_key(d);
-        if (key <= key_k) ++le;
-        else gt = min(gt, key);
+    const int32_t stride = gridDim.x * kWeightThreads;
+    for (int32_t b0 = blockIdx.x * kWeightThreads + threadIdx.x; b0 < npix; b0 += kUnroll * stride) {
+        float d[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            const int32_t i = b0 + u * stride;
+            d[u] = i < npix ? __ldg(jb.depth + i) : __int_as_float(0x7fc00000);
+        }
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            if (!finite_f(d[u])) continue;
+            const uint32_t key = float_key(d[u]);
+            if (key <= key_k) ++le;
+            else gt = min(gt, key);
+        }
     }
     le = __reduce_add_sync(0xffffffffu, le);
     gt = __reduce_min_sync(0xffffffffu, gt);
@@ -361,23 +384,32 @@ __global__ void __launch_bounds__(kWeightThreads) k_weight_apply(const __grid_co
     const float a = s_a, b = s_b, den = s_den;
     const int kind = s_kind;
     const int32_t npix = jb.W * jb.H;
-    for (int32_t i = blockIdx.x * kWeightThreads + threadIdx.x; i < npix;
-         i += gridDim.x * kWeightThreads) {
-        const float d = __ldg(jb.depth + i);
-        const float m = weight_mask(jb, i);
-        float w = 0.f;
-        if (finite_f(d)) {
-            if (kind == 1) {
-                w = __fsub_rn(1.f, __fdiv_rn(__fsub_rn(d, a), den));
-            } else if (kind == 2) {
-                const float dm = fmaxf(__fsub_rn(a, d), 0.f), dp = fmaxf(__fsub_rn(d, b), 0.f);
-                const float band = fminf(fmaxf(__fdiv_rn(__fadd_rn(dm, dp), den), 0.f), 1.f);
-                w = __fsub_rn(1.f, band);
-            } else {
-                w = 1.f;
-            }
+    const int32_t stride = gridDim.x * kWeightThreads;
+    for (int32_t b0 = blockIdx.x * kWeightThreads + threadIdx.x; b0 < npix; b0 += kUnroll * stride) {
+        float d[kUnroll], m[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            const int32_t i = b0 + u * stride;
+            d[u] = i < npix ? __ldg(jb.depth + i) : 0.f;
+            m[u] = i < npix ? weight_mask(jb, i) : 0.f;
         }
-        jb.out[i] = __fmul_rn(m, w);
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            const int32_t i = b0 + u * stride;
+            float w = 0.f;
+            if (finite_f(d[u])) {
+                if (kind == 1) {
+                    w = __fsub_rn(1.f, __fdiv_rn(__fsub_rn(d[u], a), den));
+                } else if (kind == 2) {
+                    const float dm = fmaxf(__fsub_rn(a, d[u]), 0.f), dp = fmaxf(__fsub_rn(d[u], b), 0.f);
+                    const float band = fminf(fmaxf(__fdiv_rn(__fadd_rn(dm, dp), den), 0.f), 1.f);
+                    w = __fsub_rn(1.f, band);
+                } else {
+                    w = 1.f;
+                }
+            }
+            if (i < npix) jb.out[i] = __fmul_rn(m[u], w);
+        }
     }
 }
 
@@ -442,8 +474,10 @@ divas_status divas_depth_weight(divas_ctx* c, const divas_weight_view* views, in
     k_weight_init<<<(unsigned)((hist_words + kWeightThreads - 1) / kWeightThreads), kWeightThreads, 0, s>>>(
         st, n_views, hist, hist_words);
     DIVAS_LAUNCHED(c, "k_weight_init");
-    const int per_view = (int)std::min<int64_t>((max_pix + kWeightThreads * 16 - 1) / (kWeightThreads * 16),
-                                                std::max(1, 2 * c->sm_count / n_views + 1));
+    // about 8 blocks per SM over all views, at least kUnroll pixels per thread
+    const int per_view = (int)std::max<int64_t>(1, std::min<int64_t>(
+        (max_pix + kWeightThreads * kUnroll - 1) / (kWeightThreads * kUnroll),
+        (8 * c->sm_count + n_views - 1) / n_views));
     const dim3 grid(per_view, n_views);
     k_weight_pass1<<<grid, kWeightThreads, 0, s>>>(J, st, hist);
     DIVAS_LAUNCHED(c, "k_weight_pass1");
