@@ -804,6 +804,129 @@ def profile_weight_steps(args):
     return 0
 
 
+def measure_occupancy(dev, steps: int):
+    """Occupancy construction from a surfel cloud of the 256^3 scene (its 1M
+    surface points as centres, 0.5% floaters, two scales and a dyadic opacity
+    each): the frame call (two exact selection rounds; synchronises) timed
+    with events around it; the occupancy call (density zeroed, opacity
+    scatter-add, tau_TF floor) replayed from a CUDA graph, with its roofline;
+    the fusion step on the constructed occupancy (8 views); the oracle on the
+    host."""
+    import torch
+
+    import synth
+    from paper_2601_04860_b300 import (FusionParams, PreparedViews, VoxelFusion, occupancy,
+                                       scene_frame)
+    wl = synth.config2()
+    mu, sc, al = synth.gaussians(wl)
+    dmu, dsc, dal = (torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in (mu, sc, al))
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    fms = []
+    for k in range(3 + steps):
+        ev[0].record()
+        f = scene_frame(dmu, dsc)
+        ev[1].record()
+        torch.cuda.synchronize()
+        if k >= 3:
+            fms.append(ev[0].elapsed_time(ev[1]))
+    n = f.g ** 3
+    density = torch.empty(n, dtype=torch.float32, device=dev)
+    occ = torch.empty(n, dtype=torch.uint8, device=dev)
+    for _ in range(3):
+        occupancy(dmu, dal, f, density=density, occ=occ)
+    torch.cuda.synchronize()
+    ge = [torch.cuda.Event(enable_timing=True, external=True) for _ in range(2)]
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        ge[0].record()
+        occupancy(dmu, dal, f, density=density, occ=occ)
+        ge[1].record()
+    oms = []
+    for k in range(3 + steps):
+        g.replay()
+        torch.cuda.synchronize()
+        if k >= 3:
+            oms.append(ge[0].elapsed_time(ge[1]))
+    om = float(np.mean(oms))
+    algo = len(mu) * 16 + n * (4 + 4 + 1)  # surfels read; density zeroed, read; occupancy written
+    peak, peak_kind = peaks()
+    ach = algo / (om * 1e-3) / 1e9
+    n_active = int(occ.sum().item())
+    # the fusion step on the constructed occupancy
+    grid = f.grid()
+    fu = VoxelFusion(grid, occ=occ, params=FusionParams())
+    depth = [torch.from_numpy(x).to(dev) for x in wl.depth]
+    mask = [torch.from_numpy(m.view(np.int16)).to(dev) for m in wl.mask]
+    pv = PreparedViews(wl.cams, depth, mask, wl.mask_type)
+    pts = torch.from_numpy(np.ascontiguousarray(wl.points)).to(dev)
+    score = torch.empty(n, dtype=torch.float32, device=dev)
+    labels = torch.empty(len(wl.points), dtype=torch.uint8, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    for _ in range(3):
+        fu.step(pv, occ=occ, score=score, xyz=pts, labels=labels)
+    torch.cuda.synchronize()
+    se = [torch.cuda.Event(enable_timing=True, external=True) for _ in range(2)]
+    gs = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(gs):
+        se[0].record()
+        fu.step(pv, occ=occ, score=score, xyz=pts, labels=labels)
+        se[1].record()
+    sms = []
+    for k in range(3 + steps):
+        flush.zero_()
+        gs.replay()
+        torch.cuda.synchronize()
+        if k >= 3:
+            sms.append(se[0].elapsed_time(se[1]))
+    sm = float(np.mean(sms))
+    fu.close()
+    out = {"workload": f"gaussians-from-forward-dense-256 ({len(mu)} surfels; frame -> g = {f.g}, "
+                       f"h = {f.h:.6g}, b = {f.b:g}; {n_active} occupied voxels)",
+           "frame_ms": float(np.mean(fms)), "occupancy_ms": om,
+           "surfels_per_s": len(mu) / ((float(np.mean(fms)) + om) * 1e-3),
+           "roofline": {"bound": "hbm", "kernel": "occupancy (memset + k_gauss_scatter + "
+                                                  "k_density_floor)",
+                        "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                        "traffic": None, "peak_kind": peak_kind,
+                        "algorithmic_bytes_per_launch": algo, "ms_per_launch": om},
+           "fusion_step_ms": sm,
+           "fusion_updates_per_s": n * wl.n_views / (sm * 1e-3)}
+    out["cpu_baseline"] = occupancy_cpu_baseline(mu, sc, al)
+    return out
+
+
+def occupancy_cpu_baseline(mu, sc, al):
+    """The oracle's frame and occupancy (FP64 NumPy, one host thread) on the
+    same cloud, as surfels/s."""
+    import oracle.occupancy as O
+    t0 = time.perf_counter()
+    f = O.scene_frame(mu, sc)
+    O.occupancy(mu, al, f)
+    dt = time.perf_counter() - t0
+    return {"value": len(mu) / dt, "unit": "surfels/s", "cores": 1, "kind": "oracle",
+            "seconds": dt, "sample": f"all {len(mu)} surfels (frame + occupancy, g = {f['g']})"}
+
+
+def profile_occupancy_steps(args):
+    """Profiling target of the occupancy construction: N frame + occupancy
+    calls on the 256^3 scene's surfel cloud (per call: k_gauss_smax, the
+    selection launches, k_gauss_dist, again the selection, k_gauss_frame,
+    then k_gauss_scatter and k_density_floor) and nothing else."""
+    import torch
+
+    import synth
+    from paper_2601_04860_b300 import occupancy, scene_frame
+    wl = synth.config2()
+    mu, sc, al = (torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in synth.gaussians(wl))
+    for _ in range(args.profile_occupancy_steps):
+        f = scene_frame(mu, sc)
+        occ, _ = occupancy(mu, al, f)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_occupancy_steps": args.profile_occupancy_steps, "g": f.g,
+                      "occupied": int(occ.sum().item())}))
+    return 0
+
+
 def measure_adjoint(dev, steps: int):
     """Config 4: forward + hand-written backward through the autograd Function on
     the 256^3 forward-facing scene with FP32 logits and depth as leaves."""
@@ -1002,6 +1125,8 @@ def run(args):
         return profile_tuple_steps(args)
     if args.profile_weight_steps:
         return profile_weight_steps(args)
+    if args.profile_occupancy_steps:
+        return profile_occupancy_steps(args)
     if world > 1:
         import torch
         import torch.distributed as dist
@@ -1022,6 +1147,10 @@ def run(args):
     if not args.quick and not args.no_weighting and args.workload == "forward-dense-256":
         import torch
         res["weighting"] = measure_weighting(torch.device("cuda", local_rank),
+                                             max(5, args.steps // 2))
+    if not args.quick and not args.no_occupancy and args.workload == "forward-dense-256":
+        import torch
+        res["occupancy"] = measure_occupancy(torch.device("cuda", local_rank),
                                              max(5, args.steps // 2))
     if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.quick:
         full_s, det = oracle_rate(wl, args.cpu_seconds)
@@ -1089,6 +1218,8 @@ def main(argv=None):
     ap.add_argument("--no-tuple", action="store_true", help="skip the depth-tuple-mode leg")
     ap.add_argument("--no-weighting", action="store_true",
                     help="skip the depth-weighted-mask leg")
+    ap.add_argument("--no-occupancy", action="store_true",
+                    help="skip the occupancy-construction leg")
     ap.add_argument("--sessions", type=int, default=32, help="sessions in the batched/served leg")
     ap.add_argument("--sessions-scale", type=float, default=0.5,
                     help="size scale of the sessions (1.0 = the full session mix)")
@@ -1102,6 +1233,8 @@ def main(argv=None):
                     help="profiling target: run N eager depth-tuple steps and exit")
     ap.add_argument("--profile-weight-steps", type=int, default=0,
                     help="profiling target: run N eager depth-weighted steps and exit")
+    ap.add_argument("--profile-occupancy-steps", type=int, default=0,
+                    help="profiling target: run N occupancy constructions and exit")
     args = ap.parse_args(argv)
     args.warmup = max(3, args.warmup)  # at least 3 untimed warm-up steps
     return run(args)

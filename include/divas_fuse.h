@@ -316,6 +316,60 @@ typedef struct {
 divas_status divas_depth_weight(divas_ctx* ctx, const divas_weight_view* views, int32_t n_views,
                                 int32_t mode, float* stats_out, void* stream);
 
+/*
+ * Occupancy construction from 2DGS surfels (Sec. 3.5 "Occupancy by Morton-
+ * scattered opacity"; Appendix "Occupancy grid construction"):
+ *   Eq. scene-norm:  c = coordinate-wise median of the centres mu,
+ *                    r_fg = P99(|mu - c|), b = max(ceil(pad r_fg), 1);
+ *   Eq. voxel-size:  h = max(alpha_v s_bar, beta_v r_fg / g0), s_bar = the
+ *                    median over surfels of their larger scale; g = the
+ *                    smallest power of two >= 2 b / h, capped at g_max (h
+ *                    raised to 2 b / g_max when the cap binds);
+ *   the surfels inside the half-open cube c +- b scatter-add their opacity
+ *   into voxel floor((mu - c + b) / h) of a g^3 density; occupied where
+ *   density >= tau_tf.
+ * Quantiles are the linear-interpolation ones of the finite values, found
+ * exactly; distances are formed in FP64 and kept as FP32; the rules and the
+ * voxel index are FP64.  The grid is linear (x fastest): origin = c - b,
+ * edge h, side g (the fusion's plain grid).
+ */
+typedef struct {
+    double alpha_v, beta_v; /* voxel-size weights (3, 1)                                   */
+    double pad;             /* cube margin (1.05)                                          */
+    int32_t g0, g_max;      /* reference and maximum grid side (256, 512; g_max a power of two <= 2048) */
+    float tau_tf;           /* occupancy floor (0.5)                                       */
+    int32_t reserved;
+} divas_occupancy_params;
+
+typedef struct {
+    double c[3];      /* coordinate-wise median centre                      */
+    double r_fg;      /* 99th-percentile radial distance                    */
+    double b;         /* cube half-extent                                   */
+    double s_bar;     /* median larger surfel scale                         */
+    double h;         /* voxel edge                                         */
+    double origin[3]; /* c - b: the grid's corner                           */
+    int32_t g;        /* grid side                                          */
+    int32_t pad;
+} divas_scene_frame;
+
+/* The paper's constants above (Table gs-hyperparams; g_max 512 as for LLFF). */
+divas_occupancy_params divas_default_occupancy_params(void);
+
+/* The frame from m surfels: mu (device m x 3 FP32 centres), scales (device
+ * m x 2 FP32).  Synchronises `stream` (the grid side decides allocations).
+ * DIVAS_E_INVALID: bad arguments or parameters, or no finite centre / scale. */
+divas_status divas_scene_frame_from_gaussians(const float* mu, const float* scales, int64_t m,
+                                              const divas_occupancy_params* params,
+                                              divas_scene_frame* frame_out, void* stream);
+
+/* The density (device g^3 FP32, 16-byte aligned, overwritten) and the dense
+ * occupancy prior occ_out (device g^3 uint8, 4-byte aligned: 1 where density
+ * >= tau_tf) of m surfels (mu as above, alpha device m FP32 opacities) in a
+ * frame, on `stream`.  Density sums are FP32 atomics (their order varies). */
+divas_status divas_occupancy_from_gaussians(const float* mu, const float* alpha, int64_t m,
+                                            const divas_scene_frame* frame, float tau_tf,
+                                            float* density, uint8_t* occ_out, void* stream);
+
 /* Pass 1 labels (Eq. pass1): labels_out[i] = seg bit of the voxel containing
  * point i (device n x 3 float32), 0 outside the grid (half-open box), for NaN,
  * or for unoccupied voxels.  Uses the seg bitfield of the last finalize. */

@@ -23,3 +23,4 @@ from .fusion import (  # noqa: F401
 from .autograd import DivasFuseFunction, fuse  # noqa: F401,E402
 from .batch import Autotuner, Batch, Schedule  # noqa: F401,E402
 from .serve import Server, latency_summary, poisson_requests, serve_plain  # noqa: F401,E402
+from .occupancy import OccupancyParams, SceneFrame, occupancy, scene_frame  # noqa: F401,E402

@@ -65,6 +65,18 @@ class DivasWeightView(ctypes.Structure):
                 ("n_prompts", ctypes.c_int32), ("prompt_xy", ctypes.c_int32 * (2 * 15))]
 
 
+class DivasOccupancyParams(ctypes.Structure):
+    _fields_ = [("alpha_v", ctypes.c_double), ("beta_v", ctypes.c_double), ("pad", ctypes.c_double),
+                ("g0", ctypes.c_int32), ("g_max", ctypes.c_int32), ("tau_tf", ctypes.c_float),
+                ("reserved", ctypes.c_int32)]
+
+
+class DivasSceneFrame(ctypes.Structure):
+    _fields_ = [("c", ctypes.c_double * 3), ("r_fg", ctypes.c_double), ("b", ctypes.c_double),
+                ("s_bar", ctypes.c_double), ("h", ctypes.c_double), ("origin", ctypes.c_double * 3),
+                ("g", ctypes.c_int32), ("pad", ctypes.c_int32)]
+
+
 class DivasError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
@@ -103,6 +115,13 @@ _SIGS = {
     "divas_default_tuple_params": (DivasTupleParams, []),
     "divas_depth_weight": (ctypes.c_int, [_P, ctypes.POINTER(DivasWeightView), ctypes.c_int32,
                                           ctypes.c_int32, _P, _P]),
+    "divas_default_occupancy_params": (DivasOccupancyParams, []),
+    "divas_scene_frame_from_gaussians": (ctypes.c_int, [_P, _P, ctypes.c_int64,
+                                                        ctypes.POINTER(DivasOccupancyParams),
+                                                        ctypes.POINTER(DivasSceneFrame), _P]),
+    "divas_occupancy_from_gaussians": (ctypes.c_int, [_P, _P, ctypes.c_int64,
+                                                      ctypes.POINTER(DivasSceneFrame),
+                                                      ctypes.c_float, _P, _P, _P]),
     "divas_fuse_add_views_tuple": (ctypes.c_int, [_P, ctypes.POINTER(DivasTupleView),
                                                   ctypes.c_int32,
                                                   ctypes.POINTER(DivasTupleParams), _P]),

@@ -1993,6 +1993,7 @@ void divas_batch_destroy(divas_batch* b) {
 // depth-tuple mode (thick gates on the depth tuple + thin footprint path)
 #include "tuple_mode.cuh"
 #include "weighting.cuh"
+#include "occupancy.cuh"
 
 // ===========================================================================
 // Allocation-free one-shot fusion (no counterpart in the paper)

@@ -23,6 +23,7 @@ from .scenes import (  # noqa: F401
     config2,
     config3,
     config4,
+    gaussians,
     look_at,
     render_tuple,
     session_mix,

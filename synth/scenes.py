@@ -294,6 +294,31 @@ def with_tuple(wl: "Workload", seed: int = 1100, band: float = 2.0, untrusted: f
     return out
 
 
+def gaussians(wl: "Workload", seed: int = 1300, floaters: float = 0.005, dyadic: bool = True):
+    """A 2DGS surfel cloud for the workload's scene (the input of the
+    occupancy construction, Sec. 3.5): centres = the workload's surface points
+    plus a fraction ``floaters`` scattered uniformly in a box 20x the scene's
+    (the outlier tail the P99 radius ignores); two scales per surfel U[0.5,
+    1.5] x h / 3 (h the workload's voxel edge, so that 3 s_bar is about h);
+    opacities U[0.05, 0.6], rounded to multiples of 1/64 when ``dyadic`` (FP32
+    sums of them are exact in any order).  Returns (mu (m, 3), scales (m, 2),
+    alpha (m,)), FP32."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    mu = np.asarray(wl.points, np.float32).copy()
+    m = len(mu)
+    nf = int(round(floaters * m))
+    lo, hi = mu.min(0), mu.max(0)
+    ctr, ext = 0.5 * (lo + hi), 10.0 * (hi - lo)
+    idx = rng.choice(m, size=nf, replace=False)
+    mu[idx] = (ctr + rng.uniform(-1.0, 1.0, size=(nf, 3)) * ext).astype(np.float32)
+    h = float(wl.grid.h)
+    scales = (rng.uniform(0.5, 1.5, size=(m, 2)) * h / 3.0).astype(np.float32)
+    alpha = rng.uniform(0.05, 0.6, size=m)
+    if dyadic:
+        alpha = np.round(alpha * 64.0) / 64.0
+    return mu, scales, alpha.astype(np.float32)
+
+
 def prompts(wl: "Workload", n: int = 3, seed: int = 1200, thresh: float = 0.9) -> list:
     """Positive prompts per view, the clicks a user would place on the target:
     up to n pixels (x, y) drawn (seeded, without replacement) from those whose
