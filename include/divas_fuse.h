@@ -370,6 +370,48 @@ divas_status divas_occupancy_from_gaussians(const float* mu, const float* alpha,
                                             const divas_scene_frame* frame, float tau_tf,
                                             float* density, uint8_t* occ_out, void* stream);
 
+/*
+ * Voxel-to-surfel mapping for 2DGS, Passes 1-3 (Sec. 3.6 "Voxel-to-Surfel
+ * Mapping and Aggregation"; Algorithm "Voxel-to-Surfel Mapping for 2DGS"):
+ *   Pass 1 (Eq. pass1): F1 = the seg bit of the cell holding the centre (the
+ *     context's seg bitfield of the last finalize, as divas_label_points);
+ *   Pass 2 (Eqs. aspect, needle, pass-needle): a = max(s1, s2) / (min(s1, s2)
+ *     + eps_aspect) (FP64, kept as FP32), tau_a = P99(a) found exactly,
+ *     F2 = F1 and a <= tau_a;
+ *   Pass 3 (Eqs. cov-atomics, kappa, final-F): in every view whose bit is set
+ *     in the voxel's view mask (the context's vote bits), the tangent
+ *     semi-axes t_k = s_k R[:, k] (k = 0, 1; R of the unit quaternion
+ *     (w, x, y, z)), alpha_k = (pi(mu + t_k) - pi(mu - t_k)) / 2, the pixels
+ *     whose centres lie in the 1-sigma box pi(mu) +- max(|alpha_0|, |alpha_1|)
+ *     and pass the 3-sigma Cramer test (u^2 + v^2 <= 9 in tangent
+ *     coordinates) count as visited, those with mask >= tau_m (logits:
+ *     l >= logit(tau_m)) as foreground; F = F2 and, for some view,
+ *     foreground >= tau_kappa max(visited, 1); kappa = the largest fraction.
+ * A view counts only when the centre and the four tips are in front of
+ * z_near.  Call after divas_fuse_finalize.
+ */
+typedef struct {
+    float tau_m;       /* Pass 3 mask threshold (0.5)                  */
+    float tau_kappa;   /* coverage threshold (0.5)                     */
+    float eps_aspect;  /* aspect denominator guard (1e-8)              */
+    int32_t reserved;
+} divas_surfel_params;
+
+/* The constants above (Table gs-hyperparams; eps_aspect is a reading). */
+divas_surfel_params divas_default_surfel_params(void);
+
+/* m surfels: mu (device m x 3), scales (device m x 2), quats (device m x 4,
+ * (w, x, y, z)) FP32; n_views (0..DIVAS_MAX_VIEWS_PER_CALL) host cameras and
+ * device masks of mask_type in the order of the views folded into the
+ * context (view s is bit s).  Outputs (device, m each): f_out (final uint8),
+ * f2_out (after Pass 2, nullable), kappa_out (FP32, nullable).  Scratch in
+ * the context grows on demand (outside a stream capture). */
+divas_status divas_surfel_labels(divas_ctx* ctx, const float* mu, const float* scales,
+                                 const float* quats, int64_t m, const divas_camera* cams,
+                                 const void* const* masks, int32_t mask_type, int32_t n_views,
+                                 const divas_surfel_params* params, uint8_t* f_out,
+                                 uint8_t* f2_out, float* kappa_out, void* stream);
+
 /* Pass 1 labels (Eq. pass1): labels_out[i] = seg bit of the voxel containing
  * point i (device n x 3 float32), 0 outside the grid (half-open box), for NaN,
  * or for unoccupied voxels.  Uses the seg bitfield of the last finalize. */

@@ -77,6 +77,11 @@ class DivasSceneFrame(ctypes.Structure):
                 ("g", ctypes.c_int32), ("pad", ctypes.c_int32)]
 
 
+class DivasSurfelParams(ctypes.Structure):
+    _fields_ = [("tau_m", ctypes.c_float), ("tau_kappa", ctypes.c_float),
+                ("eps_aspect", ctypes.c_float), ("reserved", ctypes.c_int32)]
+
+
 class DivasError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
@@ -116,6 +121,11 @@ _SIGS = {
     "divas_depth_weight": (ctypes.c_int, [_P, ctypes.POINTER(DivasWeightView), ctypes.c_int32,
                                           ctypes.c_int32, _P, _P]),
     "divas_default_occupancy_params": (DivasOccupancyParams, []),
+    "divas_default_surfel_params": (DivasSurfelParams, []),
+    "divas_surfel_labels": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int64,
+                                           ctypes.POINTER(DivasCamera), ctypes.POINTER(_P),
+                                           ctypes.c_int32, ctypes.c_int32,
+                                           ctypes.POINTER(DivasSurfelParams), _P, _P, _P, _P]),
     "divas_scene_frame_from_gaussians": (ctypes.c_int, [_P, _P, ctypes.c_int64,
                                                         ctypes.POINTER(DivasOccupancyParams),
                                                         ctypes.POINTER(DivasSceneFrame), _P]),

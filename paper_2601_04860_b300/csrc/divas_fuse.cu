@@ -531,12 +531,13 @@ __device__ __forceinline__ float floor_df(float hi, float lo) {
 }
 
 // label of one point (x, y, z) against a seg bitfield
-__device__ __forceinline__ uint8_t label_one(const float* __restrict__ xyz, int64_t a,
-                                             const GridC& G,
-                                             const uint32_t* __restrict__ seg_bits) {
+// the cell idx of point a (exact floor of (x - origin) / h, through the
+// contraction for contracted grids); false outside the grid or for NaN
+__device__ __forceinline__ bool point_cell(const float* __restrict__ xyz, int64_t a, const GridC& G,
+                                           int32_t (&idx)[3]) {
     float xh[3] = {xyz[3 * a], xyz[3 * a + 1], xyz[3 * a + 2]};
     float xl[3] = {0.f, 0.f, 0.f};
-    uint8_t lab = 0;
+    bool inside = false;
     if (!(isnan(xh[0]) || isnan(xh[1]) || isnan(xh[2]))) {
         if (G.contracted) {
             // r^2 = |x|^2 as hi + lo
@@ -584,8 +585,7 @@ __device__ __forceinline__ uint8_t label_one(const float* __restrict__ xyz, int6
                 }
             }
         }
-        bool inside = true;
-        int32_t idx[3];
+        inside = true;
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
             // s = (x - origin) / h as hi + lo
@@ -604,12 +604,17 @@ __device__ __forceinline__ uint8_t label_one(const float* __restrict__ xyz, int6
             if (!(f >= 0.f && f < (float)G.g)) inside = false;
             idx[q] = inside ? (int32_t)f : 0;
         }
-        if (inside) {
-            const int64_t lin = ((int64_t)idx[2] * G.g + idx[1]) * G.g + idx[0];
-            lab = (uint8_t)((__ldg(seg_bits + (lin >> 5)) >> (lin & 31)) & 1u);
-        }
     }
-    return lab;
+    return inside;
+}
+
+__device__ __forceinline__ uint8_t label_one(const float* __restrict__ xyz, int64_t a,
+                                             const GridC& G,
+                                             const uint32_t* __restrict__ seg_bits) {
+    int32_t idx[3];
+    if (!point_cell(xyz, a, G, idx)) return 0;
+    const int64_t lin = ((int64_t)idx[2] * G.g + idx[1]) * G.g + idx[0];
+    return (uint8_t)((__ldg(seg_bits + (lin >> 5)) >> (lin & 31)) & 1u);
 }
 
 // label of one point of a plain grid whose edge h is a power of two (G.inv_h
@@ -1994,6 +1999,7 @@ void divas_batch_destroy(divas_batch* b) {
 #include "tuple_mode.cuh"
 #include "weighting.cuh"
 #include "occupancy.cuh"
+#include "surfels.cuh"
 
 // ===========================================================================
 // Allocation-free one-shot fusion (no counterpart in the paper)

@@ -307,6 +307,32 @@ class VoxelFusion:
         self._check(self.lib.divas_depth_weight(self._h, arr, n, m, _ptr(st), _stream(stream)))
         return (out, st) if stats else out
 
+    def surfel_labels(self, mu: torch.Tensor, scales: torch.Tensor, quats: torch.Tensor, cams,
+                      masks, mask_type: int, tau_m: float = 0.5, tau_kappa: float = 0.5,
+                      eps_aspect: float = 1e-8, stream=None) -> dict:
+        """Voxel-to-surfel mapping, Passes 1-3 (``divas_surfel_labels``) of
+        m surfels (centres (m, 3), scales (m, 2), quaternions (m, 4) (w, x, y,
+        z), FP32 CUDA) against this context's last finalize; ``cams`` /
+        ``masks``: the views folded into it, in order.  Returns uint8 ``f``
+        (final) and ``f2`` (after the needle cull) and FP32 ``kappa``."""
+        m = mu.shape[0]
+        for x, c in ((mu, 3), (scales, 2), (quats, 4)):
+            if x.dtype != torch.float32 or x.shape != (m, c) or not x.is_contiguous():
+                raise ValueError("mu / scales / quats: contiguous float32 (m, 3) / (m, 2) / (m, 4)")
+        n = len(cams)
+        if n > L.MAX_VIEWS_PER_CALL or len(masks) != n:
+            raise ValueError("up to 32 views, one mask each")
+        cam_arr = (L.DivasCamera * max(n, 1))(*[camera_c(c) for c in cams])
+        mask_arr = (ctypes.c_void_p * max(n, 1))(*[mk.data_ptr() for mk in masks])
+        p = L.DivasSurfelParams(tau_m, tau_kappa, eps_aspect, 0)
+        f = torch.empty(m, dtype=torch.uint8, device=mu.device)
+        f2 = torch.empty(m, dtype=torch.uint8, device=mu.device)
+        kappa = torch.empty(m, dtype=torch.float32, device=mu.device)
+        self._check(self.lib.divas_surfel_labels(
+            self._h, _ptr(mu), _ptr(scales), _ptr(quats), m, cam_arr, mask_arr, mask_type, n,
+            ctypes.byref(p), _ptr(f), _ptr(f2), _ptr(kappa), _stream(stream)))
+        return {"f": f, "f2": f2, "kappa": kappa}
+
     def update(self, views, score: torch.Tensor | None = None,
                seg_bits: torch.Tensor | None = None, keep_zeros: bool = False, stream=None):
         """Incremental update: fold ``views`` (a ``PreparedViews`` or one

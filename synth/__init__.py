@@ -29,5 +29,6 @@ from .scenes import (  # noqa: F401
     session_mix,
     session_workload,
     prompts,
+    quaternions,
     with_tuple,
 )

@@ -319,6 +319,14 @@ def gaussians(wl: "Workload", seed: int = 1300, floaters: float = 0.005, dyadic:
     return mu, scales, alpha.astype(np.float32)
 
 
+def quaternions(m: int, seed: int = 1400) -> np.ndarray:
+    """m seeded uniform random unit quaternions (w, x, y, z), FP32 (the
+    surfels' orientations)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    q = rng.normal(size=(m, 4))
+    return (q / np.linalg.norm(q, axis=1, keepdims=True)).astype(np.float32)
+
+
 def prompts(wl: "Workload", n: int = 3, seed: int = 1200, thresh: float = 0.9) -> list:
     """Positive prompts per view, the clicks a user would place on the target:
     up to n pixels (x, y) drawn (seeded, without replacement) from those whose

@@ -1,0 +1,97 @@
+"""Voxel-to-surfel mapping (Passes 1-3) on the GPU against the FP64 oracle:
+the needle cull (exact P99 aspect threshold), the footprint-coverage cull
+with view gating, and the final indicator; surfels near a cell boundary, in
+a flagged voxel or with a near-boundary footprint are excluded and counted
+(GPU)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import oracle.surfels as S
+import synth
+from paper_2601_04860_b300 import VoxelFusion
+from tests import gpu_helpers as H
+
+pytestmark = pytest.mark.gpu
+
+
+def _setup(n_points=40_000, mask_type=oracle.MASK_F16, needles=True):
+    wl = synth.config2(g=64, W=224, H=168, n_ell=50, n_points=n_points)
+    mu, sc, _ = synth.gaussians(wl, floaters=0.0)
+    q = synth.quaternions(len(mu))
+    if needles:  # 2% needle-like surfels (aspect 100-1000)
+        rng = np.random.Generator(np.random.PCG64(21))
+        k = rng.choice(len(mu), len(mu) // 50, replace=False)
+        sc[k, 0] *= rng.uniform(100, 1000, size=len(k)).astype(np.float32)
+    if mask_type == oracle.MASK_F32:
+        wl.mask = [m.view(np.float16).astype(np.float32) for m in wl.mask]
+        wl.mask_type = oracle.MASK_F32
+    return wl, mu, sc, q
+
+
+def _run(wl, mu, sc, q, prm=oracle.Params()):
+    d = H.upload(wl)
+    fu = VoxelFusion(wl.grid, occ=d["occ"], params=H.to_params(prm))
+    fu.add_views(wl.cams, d["depth"], d["mask"], mask_type=wl.mask_type)
+    fu.finalize(score=True)
+    dm, ds, dq = (torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (mu, sc, q))
+    r = fu.surfel_labels(dm, ds, dq, wl.cams, d["mask"], wl.mask_type)
+    out = {k: v.cpu().numpy() for k, v in r.items()}
+    fu.close()
+    return out
+
+
+def _oracle(wl, mu, sc, q, prm=oracle.Params()):
+    lin = wl.active_linear()
+    o = oracle.fuse(wl.grid, lin, wl.cams, wl.depth, wl.mask, wl.mask_type, prm)
+    seg = oracle.dense_seg(wl.grid, lin, o["seg"])
+    F1, lflags = oracle.label(wl.grid, seg, mu)
+    # each surfel's voxel (the label's cell), its active index and view bits
+    g, h = wl.grid.g, np.float64(np.float32(wl.grid.h))
+    org = np.asarray(wl.grid.origin, np.float32).astype(np.float64)
+    idx = np.floor((mu.astype(np.float64) - org) / h).astype(np.int64)
+    inside = np.all((idx >= 0) & (idx < g), axis=1)
+    vlin = np.where(inside, (idx[:, 2] * g + idx[:, 1]) * g + idx[:, 0], -1)
+    pos = np.clip(np.searchsorted(lin, vlin), 0, len(lin) - 1)
+    found = inside & (lin[pos] == vlin)
+    vbits = np.where(found & (F1 > 0), o["bits"][pos], 0).astype(np.uint32)
+    vflag = found & (o["flags"][pos] != 0)
+    r = S.surfel_labels(mu, sc, q, F1 > 0, vbits, wl.cams, wl.mask, wl.mask_type)
+    r["excluded"] = (lflags != 0) | vflag | r["flags"]
+    r["F1"] = F1 > 0
+    return r
+
+
+@pytest.mark.parametrize("mask_type", [oracle.MASK_F16, oracle.MASK_F32])
+def test_surfel_labels_match_oracle(mask_type):
+    wl, mu, sc, q = _setup(mask_type=mask_type)
+    got = _run(wl, mu, sc, q)
+    ref = _oracle(wl, mu, sc, q)
+    ok = ~ref["excluded"]
+    assert ok.mean() > 0.9, ok.mean()
+    assert ref["F1"][ok].sum() > 500 and ref["F"][ok].sum() > 100
+    assert (ref["F2"][ok] < ref["F1"][ok]).sum() >= 3, "the needle cull removed nothing"
+    assert (ref["F"][ok] < ref["F2"][ok]).sum() >= 3, "the coverage cull removed nothing"
+    assert np.array_equal(got["f2"][ok].astype(bool), ref["F2"][ok]), "Pass 2 differs"
+    assert np.array_equal(got["f"][ok].astype(bool), ref["F"][ok]), "final indicator differs"
+    assert np.allclose(got["kappa"][ok], ref["kappa"][ok], rtol=0, atol=1e-6), "kappa differs"
+
+
+def test_surfels_outside_or_unsegmented():
+    """Surfels outside the grid, with NaN centres or in unsegmented voxels are
+    0 in every pass; no views: nothing passes Pass 3."""
+    wl, mu, sc, q = _setup(n_points=5_000, needles=False)
+    mu = mu.copy()
+    mu[:10] = np.float32(5.0)             # outside the grid
+    mu[10:20, 1] = np.nan
+    d = H.upload(wl)
+    fu = VoxelFusion(wl.grid, occ=d["occ"], params=H.to_params(oracle.Params()))
+    fu.add_views(wl.cams, d["depth"], d["mask"], mask_type=wl.mask_type)
+    fu.finalize(score=True)
+    dm, ds, dq = (torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (mu, sc, q))
+    r = fu.surfel_labels(dm, ds, dq, wl.cams, d["mask"], wl.mask_type)
+    assert not r["f2"][:20].any() and not r["f"][:20].any()
+    r0 = fu.surfel_labels(dm, ds, dq, [], [], wl.mask_type)
+    assert not r0["f"].any() and r0["f2"].any()
+    fu.close()
