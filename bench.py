@@ -927,6 +927,89 @@ def profile_occupancy_steps(args):
     return 0
 
 
+def measure_surfels(dev, steps: int):
+    """Voxel-to-surfel mapping on the 256^3 scene: its 1M surface points as
+    surfel centres (two scales, a random orientation, 2% needles) against the
+    finalized fusion of its 8 views; the call (aspects, the P99 selection,
+    the per-surfel pass) replayed from a CUDA graph, L2 flushed; its roofline
+    (surfel inputs and outputs once); the oracle on a sample on the host."""
+    import torch
+
+    import synth
+    from paper_2601_04860_b300 import FusionParams, VoxelFusion
+    wl = synth.config2()
+    mu, sc, _ = synth.gaussians(wl, floaters=0.0)
+    q = synth.quaternions(len(mu))
+    rng = np.random.Generator(np.random.PCG64(21))
+    k = rng.choice(len(mu), len(mu) // 50, replace=False)
+    sc[k, 0] *= rng.uniform(100, 1000, size=len(k)).astype(np.float32)
+    occ = torch.from_numpy(wl.occ).to(dev)
+    depth = [torch.from_numpy(x).to(dev) for x in wl.depth]
+    mask = [torch.from_numpy(m.view(np.int16)).to(dev) for m in wl.mask]
+    fu = VoxelFusion(wl.grid, occ=occ, params=FusionParams())
+    fu.add_views(wl.cams, depth, mask, mask_type=wl.mask_type)
+    fu.finalize(score=True)
+    dm, ds, dq = (torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in (mu, sc, q))
+    for _ in range(3):
+        r = fu.surfel_labels(dm, ds, dq, wl.cams, mask, wl.mask_type)
+    torch.cuda.synchronize()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    ev = [torch.cuda.Event(enable_timing=True, external=True) for _ in range(2)]
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        ev[0].record()
+        r = fu.surfel_labels(dm, ds, dq, wl.cams, mask, wl.mask_type)
+        ev[1].record()
+    ms = []
+    for k in range(3 + steps):
+        flush.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        if k >= 3:
+            ms.append(ev[0].elapsed_time(ev[1]))
+    m = float(np.mean(ms))
+    n = len(mu)
+    f1 = int(fu.label_points(dm).sum().item())
+    f2, f = int(r["f2"].sum().item()), int(r["f"].sum().item())
+    fu.close()
+    algo = n * (12 + 8 + 16 + 1 + 1 + 4)  # centres, scales, quaternions; f, f2, kappa
+    peak, peak_kind = peaks()
+    ach = algo / (m * 1e-3) / 1e9
+    return {"workload": f"surfels-on-forward-dense-256 ({n} surfels, 8 views; passes kept "
+                        f"{f1} / {f2} / {f})",
+            "ms": m, "surfels_per_s": n / (m * 1e-3),
+            "roofline": {"bound": "hbm", "kernel": "surfel_labels (k_surfel_aspect + selection + "
+                                                  "k_surfel_pass)",
+                         "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                         "traffic": None, "peak_kind": peak_kind,
+                         "algorithmic_bytes_per_launch": algo, "ms_per_launch": m},
+            "cpu_baseline": surfels_cpu_baseline(wl, mu, sc, q)}
+
+
+def surfels_cpu_baseline(wl, mu, sc, q, n_sample: int = 20_000):
+    """The oracle's Passes 2-3 (FP64 NumPy and Python loops, one thread) on a
+    sample of the surfels, given its own Pass 1 and view masks, as surfels/s."""
+    import oracle
+    import oracle.surfels as S
+    lin = wl.active_linear()
+    o = oracle.fuse(wl.grid, lin, wl.cams, wl.depth, wl.mask, wl.mask_type, oracle.Params())
+    seg = oracle.dense_seg(wl.grid, lin, o["seg"])
+    idx = np.arange(0, len(mu), max(1, len(mu) // n_sample))[:n_sample]
+    F1, _ = oracle.label(wl.grid, seg, mu[idx])
+    g, h = wl.grid.g, np.float64(np.float32(wl.grid.h))
+    org = np.asarray(wl.grid.origin, np.float32).astype(np.float64)
+    cell = np.floor((mu[idx].astype(np.float64) - org) / h).astype(np.int64)
+    vlin = (cell[:, 2] * g + cell[:, 1]) * g + cell[:, 0]
+    pos = np.clip(np.searchsorted(lin, vlin), 0, len(lin) - 1)
+    vbits = np.where((lin[pos] == vlin) & (F1 > 0), o["bits"][pos], 0).astype(np.uint32)
+    t0 = time.perf_counter()
+    S.surfel_labels(mu[idx], sc[idx], q[idx], F1 > 0, vbits, wl.cams, wl.mask, wl.mask_type)
+    dt = time.perf_counter() - t0
+    return {"value": len(idx) / dt, "unit": "surfels/s", "cores": 1, "kind": "oracle",
+            "seconds": dt, "sample": f"{len(idx)} of {len(mu)} surfels (every "
+                                     f"{len(mu) // len(idx)}th; Passes 2-3)"}
+
+
 def measure_adjoint(dev, steps: int):
     """Config 4: forward + hand-written backward through the autograd Function on
     the 256^3 forward-facing scene with FP32 logits and depth as leaves."""
@@ -1152,6 +1235,9 @@ def run(args):
         import torch
         res["occupancy"] = measure_occupancy(torch.device("cuda", local_rank),
                                              max(5, args.steps // 2))
+    if not args.quick and not args.no_surfels and args.workload == "forward-dense-256":
+        import torch
+        res["surfels"] = measure_surfels(torch.device("cuda", local_rank), max(5, args.steps // 2))
     if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.quick:
         full_s, det = oracle_rate(wl, args.cpu_seconds)
         N = res["config"]["voxels_nominal"]
@@ -1220,6 +1306,7 @@ def main(argv=None):
                     help="skip the depth-weighted-mask leg")
     ap.add_argument("--no-occupancy", action="store_true",
                     help="skip the occupancy-construction leg")
+    ap.add_argument("--no-surfels", action="store_true", help="skip the voxel-to-surfel leg")
     ap.add_argument("--sessions", type=int, default=32, help="sessions in the batched/served leg")
     ap.add_argument("--sessions-scale", type=float, default=0.5,
                     help="size scale of the sessions (1.0 = the full session mix)")

@@ -13,7 +13,9 @@
 // reaches tau_kappa.  One thread owns a surfel's counters and walks its box
 // in every view, so no atomics and no tile sort are needed (the paper's tile
 // sort is rasterizer scaffolding for ordered blending; coverage counting has
-// no order).
+// no order); a surfel whose box in some view holds more than kSurfelSmallBox
+// pixels (a large or elongated disc) is listed and counted by a whole block,
+// its box's pixels spread over the threads.
 #pragma once
 
 #include "select.cuh"
@@ -59,13 +61,20 @@ __device__ __forceinline__ bool surf_front(const SView& V, const float (&X)[3], 
     return true;
 }
 
-// (total, mask) of a surfel in one view; false when a point is behind
-__device__ bool surfel_view(const SView& V, const float (&m)[3], const float (&t0)[3],
-                            const float (&t1)[3], int32_t mask_type, float gate, float z_near,
-                            uint32_t& total, uint32_t& msk) {
-    total = msk = 0u;
-    float X[3], cu, cv, u0p, v0p, u0m, v0m, u1p, v1p, u1m, v1m;
-    bool ok = surf_front(V, m, z_near, cu, cv);
+// a surfel's footprint in one view: the centre, the projected tangent
+// vectors, 1 / det, the 1-sigma pixel box (clipped to the frame)
+struct SFoot {
+    float cu, cv, a0x, a0y, a1x, a1y, inv;
+    int x0, x1, y0, y1;
+    bool any;  // a pixel can be accepted (in front, not edge-on, box non-empty)
+};
+
+// false when the centre or a tip is behind the camera (the view is skipped)
+__device__ bool surfel_foot(const SView& V, const float (&m)[3], const float (&t0)[3],
+                            const float (&t1)[3], float z_near, SFoot& F) {
+    float X[3], u0p, v0p, u0m, v0m, u1p, v1p, u1m, v1m;
+    F.any = false;
+    bool ok = surf_front(V, m, z_near, F.cu, F.cv);
 #pragma unroll
     for (int q = 0; q < 3; ++q) X[q] = __fadd_rn(m[q], t0[q]);
     ok = ok && surf_front(V, X, z_near, u0p, v0p);
@@ -79,34 +88,70 @@ __device__ bool surfel_view(const SView& V, const float (&m)[3], const float (&t
     for (int q = 0; q < 3; ++q) X[q] = __fsub_rn(m[q], t1[q]);
     ok = ok && surf_front(V, X, z_near, u1m, v1m);
     if (!ok) return false;
-    const float a0x = __fmul_rn(0.5f, __fsub_rn(u0p, u0m)), a0y = __fmul_rn(0.5f, __fsub_rn(v0p, v0m));
-    const float a1x = __fmul_rn(0.5f, __fsub_rn(u1p, u1m)), a1y = __fmul_rn(0.5f, __fsub_rn(v1p, v1m));
-    const float det = __fsub_rn(__fmul_rn(a0x, a1y), __fmul_rn(a0y, a1x));
+    F.a0x = __fmul_rn(0.5f, __fsub_rn(u0p, u0m));
+    F.a0y = __fmul_rn(0.5f, __fsub_rn(v0p, v0m));
+    F.a1x = __fmul_rn(0.5f, __fsub_rn(u1p, u1m));
+    F.a1y = __fmul_rn(0.5f, __fsub_rn(v1p, v1m));
+    const float det = __fsub_rn(__fmul_rn(F.a0x, F.a1y), __fmul_rn(F.a0y, F.a1x));
     if (det == 0.f) return true;  // edge-on: no pixel
-    const float inv = __frcp_rn(det);
-    const float ex = fmaxf(fabsf(a0x), fabsf(a1x)), ey = fmaxf(fabsf(a0y), fabsf(a1y));
+    F.inv = __frcp_rn(det);
+    const float ex = fmaxf(fabsf(F.a0x), fabsf(F.a1x)), ey = fmaxf(fabsf(F.a0y), fabsf(F.a1y));
     // pixel centres x + 1/2 inside [cu - ex, cu + ex], clipped to the frame
-    const int x0 = (int)fmaxf(ceilf(__fsub_rn(__fsub_rn(cu, ex), 0.5f)), 0.f);
-    const int x1 = (int)fminf(floorf(__fsub_rn(__fadd_rn(cu, ex), 0.5f)), (float)(V.W - 1));
-    const int y0 = (int)fmaxf(ceilf(__fsub_rn(__fsub_rn(cv, ey), 0.5f)), 0.f);
-    const int y1 = (int)fminf(floorf(__fsub_rn(__fadd_rn(cv, ey), 0.5f)), (float)(V.H - 1));
-    for (int y = y0; y <= y1; ++y) {
-        const float dy = __fsub_rn(__fadd_rn((float)y, 0.5f), cv);
-        for (int x = x0; x <= x1; ++x) {
-            const float dx = __fsub_rn(__fadd_rn((float)x, 0.5f), cu);
-            const float uu = __fmul_rn(__fsub_rn(__fmul_rn(dx, a1y), __fmul_rn(dy, a1x)), inv);
-            const float vv = __fmul_rn(__fsub_rn(__fmul_rn(a0x, dy), __fmul_rn(a0y, dx)), inv);
-            if (__fadd_rn(__fmul_rn(uu, uu), __fmul_rn(vv, vv)) <= 9.f) {
-                ++total;
-                const int32_t q = y * V.W + x;
-                const float mv = mask_type == kMaskF16
-                    ? __half2float(__ushort_as_half(__ldg(reinterpret_cast<const unsigned short*>(V.mask) + q)))
-                    : __ldg(reinterpret_cast<const float*>(V.mask) + q);
-                msk += mv >= gate ? 1u : 0u;
-            }
-        }
-    }
+    F.x0 = (int)fmaxf(ceilf(__fsub_rn(__fsub_rn(F.cu, ex), 0.5f)), 0.f);
+    F.x1 = (int)fminf(floorf(__fsub_rn(__fadd_rn(F.cu, ex), 0.5f)), (float)(V.W - 1));
+    F.y0 = (int)fmaxf(ceilf(__fsub_rn(__fsub_rn(F.cv, ey), 0.5f)), 0.f);
+    F.y1 = (int)fminf(floorf(__fsub_rn(__fadd_rn(F.cv, ey), 0.5f)), (float)(V.H - 1));
+    F.any = F.x0 <= F.x1 && F.y0 <= F.y1;
     return true;
+}
+
+// the 3-sigma Cramer test and the mask at pixel (x, y): adds to (total, mask)
+__device__ __forceinline__ void surfel_pixel(const SView& V, const SFoot& F, int x, int y,
+                                             int32_t mask_type, float gate, uint32_t& total,
+                                             uint32_t& msk) {
+    const float dx = __fsub_rn(__fadd_rn((float)x, 0.5f), F.cu);
+    const float dy = __fsub_rn(__fadd_rn((float)y, 0.5f), F.cv);
+    const float uu = __fmul_rn(__fsub_rn(__fmul_rn(dx, F.a1y), __fmul_rn(dy, F.a1x)), F.inv);
+    const float vv = __fmul_rn(__fsub_rn(__fmul_rn(F.a0x, dy), __fmul_rn(F.a0y, dx)), F.inv);
+    if (__fadd_rn(__fmul_rn(uu, uu), __fmul_rn(vv, vv)) <= 9.f) {
+        ++total;
+        const int32_t q = y * V.W + x;
+        const float mv = mask_type == kMaskF16
+            ? __half2float(__ushort_as_half(__ldg(reinterpret_cast<const unsigned short*>(V.mask) + q)))
+            : __ldg(reinterpret_cast<const float*>(V.mask) + q);
+        msk += mv >= gate ? 1u : 0u;
+    }
+}
+
+// the box's pixel count (64-bit)
+__device__ __forceinline__ int64_t foot_area(const SFoot& F) {
+    return F.any ? (int64_t)(F.x1 - F.x0 + 1) * (F.y1 - F.y0 + 1) : 0;
+}
+
+constexpr int64_t kSurfelSmallBox = 1024;  // larger boxes go to the block-per-surfel pass
+
+// a surfel's tangent semi-axes and centre
+__device__ __forceinline__ void surfel_axes(const float* __restrict__ mu,
+                                            const float* __restrict__ scales,
+                                            const float* __restrict__ quats, int32_t i,
+                                            float (&mm)[3], float (&t0)[3], float (&t1)[3]) {
+    const float qw = __ldg(quats + 4 * (int64_t)i), qx = __ldg(quats + 4 * (int64_t)i + 1);
+    const float qy = __ldg(quats + 4 * (int64_t)i + 2), qz = __ldg(quats + 4 * (int64_t)i + 3);
+    const float rn = __frsqrt_rn(__fmaf_rn(qw, qw, __fmaf_rn(qx, qx, __fmaf_rn(qy, qy, __fmul_rn(qz, qz)))));
+    const float w = __fmul_rn(qw, rn), x = __fmul_rn(qx, rn), y = __fmul_rn(qy, rn), z = __fmul_rn(qz, rn);
+    const float s0 = __ldg(scales + 2 * (int64_t)i), s1 = __ldg(scales + 2 * (int64_t)i + 1);
+    const float c0[3] = {__fsub_rn(1.f, __fmul_rn(2.f, __fmaf_rn(y, y, __fmul_rn(z, z)))),
+                         __fmul_rn(2.f, __fmaf_rn(x, y, __fmul_rn(w, z))),
+                         __fmul_rn(2.f, __fsub_rn(__fmul_rn(x, z), __fmul_rn(w, y)))};
+    const float c1[3] = {__fmul_rn(2.f, __fsub_rn(__fmul_rn(x, y), __fmul_rn(w, z))),
+                         __fsub_rn(1.f, __fmul_rn(2.f, __fmaf_rn(x, x, __fmul_rn(z, z)))),
+                         __fmul_rn(2.f, __fmaf_rn(y, z, __fmul_rn(w, x)))};
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        mm[q] = __ldg(mu + 3 * (int64_t)i + q);
+        t0[q] = __fmul_rn(s0, c0[q]);
+        t1[q] = __fmul_rn(s1, c1[q]);
+    }
 }
 
 // the active-list index of packed cell pk (ascending list), or -1
@@ -121,63 +166,126 @@ __device__ __forceinline__ int32_t active_find(const uint32_t* __restrict__ acti
     return lo < n && __ldg(active + lo) == pk ? lo : -1;
 }
 
-// Passes 1-3 per surfel: f (final), f2 (after the needle cull), kappa
+// Passes 1-3 per surfel: f (final), f2 (after the needle cull), kappa.  A
+// surfel whose 1-sigma box in some scored view holds more than
+// kSurfelSmallBox pixels is appended to `big` (with its view bits) and left
+// to k_surfel_big.
 __global__ void __launch_bounds__(kSurfThreads) k_surfel_pass(
     const float* __restrict__ mu, const float* __restrict__ scales, const float* __restrict__ quats,
     const float* __restrict__ aspect, int32_t m, GridC G, const uint32_t* __restrict__ seg_bits,
     const uint32_t* __restrict__ active, const int32_t* __restrict__ d_n,
     const uint32_t* __restrict__ vbits, const SelState* __restrict__ st,
     const __grid_constant__ SViews SV, float tau_kappa, float z_near, uint8_t* __restrict__ f_out,
-    uint8_t* __restrict__ f2_out, float* __restrict__ kappa_out) {
+    uint8_t* __restrict__ f2_out, float* __restrict__ kappa_out, uint2* __restrict__ big,
+    int32_t* __restrict__ n_big) {
     const float tau_a = (float)sel_value(st[0], 0.99);
     const int32_t n_act = *d_n;
+    const float gate = SV.mask_type == kMaskLogit ? SV.logit_m : SV.tau_m;
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
         int32_t idx[3];
-        bool f2 = false, f = false;
+        bool f2 = false, f = false, large = false;
         float kappa = 0.f;
+        uint32_t vb = 0u;
         if (point_cell(mu, i, G, idx)) {
             const int64_t lin = ((int64_t)idx[2] * G.g + idx[1]) * G.g + idx[0];
             const bool f1 = (__ldg(seg_bits + (lin >> 5)) >> (lin & 31)) & 1u;
             f2 = f1 && __ldg(aspect + i) <= tau_a;
             const uint32_t pk = (uint32_t)idx[0] | ((uint32_t)idx[1] << 10) | ((uint32_t)idx[2] << 20);
             const int32_t ai = f2 ? active_find(active, n_act, pk) : -1;
-            const uint32_t vb = ai >= 0 ? __ldg(vbits + ai) : 0u;
+            vb = ai >= 0 ? __ldg(vbits + ai) : 0u;
             if (vb) {
-                // tangent semi-axes: the scales on the rotation's first two columns
-                const float qw = __ldg(quats + 4 * (int64_t)i), qx = __ldg(quats + 4 * (int64_t)i + 1);
-                const float qy = __ldg(quats + 4 * (int64_t)i + 2), qz = __ldg(quats + 4 * (int64_t)i + 3);
-                const float rn = __frsqrt_rn(__fmaf_rn(qw, qw, __fmaf_rn(qx, qx, __fmaf_rn(qy, qy, __fmul_rn(qz, qz)))));
-                const float w = __fmul_rn(qw, rn), x = __fmul_rn(qx, rn), y = __fmul_rn(qy, rn),
-                            z = __fmul_rn(qz, rn);
-                const float s0 = __ldg(scales + 2 * (int64_t)i), s1 = __ldg(scales + 2 * (int64_t)i + 1);
-                const float c0[3] = {__fsub_rn(1.f, __fmul_rn(2.f, __fmaf_rn(y, y, __fmul_rn(z, z)))),
-                                     __fmul_rn(2.f, __fmaf_rn(x, y, __fmul_rn(w, z))),
-                                     __fmul_rn(2.f, __fsub_rn(__fmul_rn(x, z), __fmul_rn(w, y)))};
-                const float c1[3] = {__fmul_rn(2.f, __fsub_rn(__fmul_rn(x, y), __fmul_rn(w, z))),
-                                     __fsub_rn(1.f, __fmul_rn(2.f, __fmaf_rn(x, x, __fmul_rn(z, z)))),
-                                     __fmul_rn(2.f, __fmaf_rn(y, z, __fmul_rn(w, x)))};
-                float t0[3], t1[3];
-                const float mm[3] = {__ldg(mu + 3 * (int64_t)i), __ldg(mu + 3 * (int64_t)i + 1),
-                                     __ldg(mu + 3 * (int64_t)i + 2)};
-#pragma unroll
-                for (int q = 0; q < 3; ++q) {
-                    t0[q] = __fmul_rn(s0, c0[q]);
-                    t1[q] = __fmul_rn(s1, c1[q]);
-                }
-                const float gate = SV.mask_type == kMaskLogit ? SV.logit_m : SV.tau_m;
-                for (int32_t s = 0; s < SV.n; ++s) {
+                float mm[3], t0[3], t1[3];
+                surfel_axes(mu, scales, quats, i, mm, t0, t1);
+                for (int32_t s = 0; s < SV.n && !large; ++s) {
                     if (!((vb >> s) & 1u)) continue;
-                    uint32_t tot, msk;
-                    if (!surfel_view(SV.v[s], mm, t0, t1, SV.mask_type, gate, z_near, tot, msk)) continue;
+                    SFoot F;
+                    if (!surfel_foot(SV.v[s], mm, t0, t1, z_near, F)) continue;
+                    if (foot_area(F) > kSurfelSmallBox) {
+                        large = true;
+                        break;
+                    }
+                    uint32_t tot = 0u, msk = 0u;
+                    if (F.any)
+                        for (int y = F.y0; y <= F.y1; ++y)
+                            for (int x = F.x0; x <= F.x1; ++x)
+                                surfel_pixel(SV.v[s], F, x, y, SV.mask_type, gate, tot, msk);
                     const uint32_t den = max(tot, 1u);
                     kappa = fmaxf(kappa, __fdiv_rn((float)msk, (float)den));
                     f = f || (double)msk >= (double)tau_kappa * (double)den;
                 }
             }
         }
-        f_out[i] = (uint8_t)(f2 && f);
         if (f2_out) f2_out[i] = (uint8_t)f2;
+        if (large) {
+            big[atomicAdd(n_big, 1)] = make_uint2((uint32_t)i, vb);  // at most m entries
+            continue;
+        }
+        f_out[i] = (uint8_t)(f2 && f);
         if (kappa_out) kappa_out[i] = kappa;
+    }
+}
+
+// The listed surfels: one block per (listed surfel, view) (blockIdx.y =
+// view); the footprint (one thread), then the box's pixels spread over the
+// block and the counts reduced; per surfel, the largest fraction (atomicMax
+// on its non-negative bits) and whether some view reached tau_kappa
+// (atomicOr) go to acc (zeroed).
+__global__ void __launch_bounds__(kSurfThreads) k_surfel_big(
+    const float* __restrict__ mu, const float* __restrict__ scales, const float* __restrict__ quats,
+    const uint2* __restrict__ big, const int32_t* __restrict__ n_big,
+    const __grid_constant__ SViews SV, float tau_kappa, float z_near, uint2* __restrict__ acc) {
+    __shared__ SFoot sF;
+    __shared__ bool s_ok;
+    __shared__ uint32_t s_tot, s_msk;
+    const float gate = SV.mask_type == kMaskLogit ? SV.logit_m : SV.tau_m;
+    const int32_t nb = *n_big;
+    const int32_t s = blockIdx.y;
+    for (int32_t e = blockIdx.x; e < nb; e += gridDim.x) {
+        const uint2 it = big[e];
+        if (!((it.y >> s) & 1u)) continue;  // block-uniform
+        const int32_t i = (int32_t)it.x;
+        if (threadIdx.x == 0) {
+            float mm[3], t0[3], t1[3];
+            surfel_axes(mu, scales, quats, i, mm, t0, t1);
+            s_ok = surfel_foot(SV.v[s], mm, t0, t1, z_near, sF);
+            s_tot = 0u;
+            s_msk = 0u;
+        }
+        __syncthreads();
+        if (s_ok) {
+            const SFoot F = sF;
+            uint32_t tot = 0u, msk = 0u;
+            const int64_t area = foot_area(F);
+            const int32_t bw = F.x1 - F.x0 + 1;
+            for (int64_t p = threadIdx.x; p < area; p += blockDim.x)
+                surfel_pixel(SV.v[s], F, F.x0 + (int)(p % bw), F.y0 + (int)(p / bw), SV.mask_type,
+                             gate, tot, msk);
+            tot = __reduce_add_sync(0xffffffffu, tot);
+            msk = __reduce_add_sync(0xffffffffu, msk);
+            if ((threadIdx.x & 31) == 0) {
+                atomicAdd(&s_tot, tot);
+                atomicAdd(&s_msk, msk);
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0 && s_ok) {
+            const uint32_t den = max(s_tot, 1u);
+            atomicMax(&acc[e].x, __float_as_uint(__fdiv_rn((float)s_msk, (float)den)));
+            if ((double)s_msk >= (double)tau_kappa * (double)den) atomicOr(&acc[e].y, 1u);
+        }
+        __syncthreads();
+    }
+}
+
+// the listed surfels' outputs from their accumulators
+__global__ void __launch_bounds__(kSurfThreads) k_surfel_big_out(
+    const uint2* __restrict__ big, const int32_t* __restrict__ n_big, const uint2* __restrict__ acc,
+    uint8_t* __restrict__ f_out, float* __restrict__ kappa_out) {
+    const int32_t nb = *n_big;
+    for (int32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < nb; e += gridDim.x * blockDim.x) {
+        const int32_t i = (int32_t)big[e].x;
+        f_out[i] = (uint8_t)(acc[e].y != 0u);  // listed surfels passed Pass 2
+        if (kappa_out) kappa_out[i] = __uint_as_float(acc[e].x);
     }
 }
 
@@ -228,10 +336,12 @@ divas_status divas_surfel_labels(divas_ctx* c, const float* mu, const float* sca
         v.H = cams[k].H;
         v.mask = masks[k];
     }
-    // scratch (the weighting's): aspects, then one selection job
+    // scratch (the weighting's): aspects, the large-footprint list and its
+    // count, then one selection job
     const int32_t n = (int32_t)m;
     const size_t arr = ((size_t)n * 4 + 255) / 256 * 256;
-    const size_t need = arr + sel_scratch_bytes(1);
+    const size_t lst = ((size_t)n * 16 + 256 + 255) / 256 * 256;  // list + accumulators
+    const size_t need = arr + lst + sel_scratch_bytes(1);
     cudaStream_t s = S(stream);
     if (need > c->wt_bytes) {
         if (capturing(s))
@@ -244,7 +354,12 @@ divas_status divas_surfel_labels(divas_ctx* c, const float* mu, const float* sca
         c->wt_bytes = need;
     }
     float* aspect = static_cast<float*>(c->wt);
-    void* sel = static_cast<unsigned char*>(c->wt) + arr;
+    int32_t* n_big = reinterpret_cast<int32_t*>(static_cast<unsigned char*>(c->wt) + arr);
+    uint2* big = reinterpret_cast<uint2*>(static_cast<unsigned char*>(c->wt) + arr + 256);
+    uint2* acc = big + n;
+    void* sel = static_cast<unsigned char*>(c->wt) + arr + lst;
+    DIVAS_CUDA(c, cudaMemsetAsync(n_big, 0, sizeof(int32_t), s));
+    DIVAS_CUDA(c, cudaMemsetAsync(acc, 0, (size_t)n * sizeof(uint2), s));
     const int blocks = (int)std::min<int64_t>((n + kSurfThreads - 1) / kSurfThreads, 16 * (int64_t)c->sm_count);
     k_surfel_aspect<<<blocks, kSurfThreads, 0, s>>>(scales, n, p->eps_aspect, aspect);
     DIVAS_LAUNCHED(c, "k_surfel_aspect");
@@ -256,8 +371,16 @@ divas_status divas_surfel_labels(divas_ctx* c, const float* mu, const float* sca
     k_surfel_pass<<<blocks, kSurfThreads, 0, s>>>(mu, scales, quats, aspect, n, c->G, c->seg_bits,
                                                   c->active, c->d_n, c->bits,
                                                   static_cast<const SelState*>(sel), SV, p->tau_kappa,
-                                                  c->F.z_near, f_out, f2_out, kappa_out);
+                                                  c->F.z_near, f_out, f2_out, kappa_out, big,
+                                                  n_big);
     DIVAS_LAUNCHED(c, "k_surfel_pass");
+    if (n_views > 0) {
+        k_surfel_big<<<dim3(std::max(1, 4 * c->sm_count / n_views), n_views), kSurfThreads, 0, s>>>(
+            mu, scales, quats, big, n_big, SV, p->tau_kappa, c->F.z_near, acc);
+        DIVAS_LAUNCHED(c, "k_surfel_big");
+        k_surfel_big_out<<<c->sm_count, kSurfThreads, 0, s>>>(big, n_big, acc, f_out, kappa_out);
+        DIVAS_LAUNCHED(c, "k_surfel_big_out");
+    }
     return DIVAS_OK;
 }
 
