@@ -412,6 +412,15 @@ divas_status divas_surfel_labels(divas_ctx* ctx, const float* mu, const float* s
                                  const divas_surfel_params* params, uint8_t* f_out,
                                  uint8_t* f2_out, float* kappa_out, void* stream);
 
+/* The back-projected overlay of a view (Sec. 3.7 "Iterative Mask
+ * Propagation": the fused 3D mask shown on the next view): out[y W + x] =
+ * the seg bit of the cell holding the pixel centre (x + 1/2, y + 1/2)
+ * unprojected at its planar depth (device H x W FP32), 0 where the depth is
+ * not finite and positive or the point is outside the grid (device H x W
+ * uint8).  Uses the seg bitfield of the last finalize. */
+divas_status divas_overlay(divas_ctx* ctx, const divas_camera* cam, const float* depth,
+                           uint8_t* out, void* stream);
+
 /* Pass 1 labels (Eq. pass1): labels_out[i] = seg bit of the voxel containing
  * point i (device n x 3 float32), 0 outside the grid (half-open box), for NaN,
  * or for unoccupied voxels.  Uses the seg bitfield of the last finalize. */

@@ -42,9 +42,17 @@ pixel of a box edge, or a tip or centre near z_near may go either way;
 such surfels are flagged (the counts are integers, so kappa_s >= tau_kappa
 is exact once they agree).
 
+The back-projected overlay (Sec. 3.7 "Iterative Mask Propagation": the
+fused 3D mask shown on the next view): each pixel centre unprojected at its
+planar depth, x = R^T (((u + 1/2 - cx) / fx) d, ((v + 1/2 - cy) / fy) d, d)
+- R^T t (FP64, then FP32 as the label lookup takes points), and the seg bit
+of its cell (oracle.label); 0 where the depth is not finite and positive.
+Pixels whose point lies within 64 x 2^-24 of the magnitudes of a cell
+boundary (the reach of an FP32 unprojection) are flagged.
+
 parity: pinned by tests/test_oracle_surfels.py (closed forms for a
 fronto-parallel disc, gating, the aspect threshold, a per-pixel brute force
-over the whole image, planted mistakes).
+over the whole image, a constructed overlay, planted mistakes).
 """
 from __future__ import annotations
 
@@ -152,3 +160,31 @@ def surfel_labels(mu, scales, quats, F1, voxel_bits, cams, masks, mask_type, tau
             if msk >= tau_kappa * max(tot, 1):
                 keep[i] = True
     return {"F2": F2, "F": F2 & keep, "kappa": kappa, "tau_a": tau_a, "flags": flags}
+
+
+def overlay(grid, seg_dense, cam, depth):
+    """The overlay of one view: (uint8 H x W, the label's flags per pixel)."""
+    from . import label
+    D = np.asarray(depth, np.float32).astype(np.float64)
+    H, W = D.shape
+    ys, xs = np.mgrid[0:H, 0:W]
+    ok = np.isfinite(D) & (D > 0)
+    Dz = np.where(ok, D, 1.0)
+    pc = np.stack([((xs + 0.5 - float(cam.cx)) / float(cam.fx)) * Dz,
+                   ((ys + 0.5 - float(cam.cy)) / float(cam.fy)) * Dz, Dz], axis=-1).reshape(-1, 3)
+    R = np.asarray(cam.R, np.float32).astype(np.float64).reshape(3, 3)
+    t = np.asarray(cam.t, np.float32).astype(np.float64)
+    X64 = (pc - t) @ R                            # R^T (p_c - t), row vectors
+    lab, fl = label(grid, seg_dense, X64.astype(np.float32))
+    # an FP32 unprojection (about ten roundings) moves x by at most a few
+    # units of 2^-24 of the magnitudes involved: cells nearer than 64 of them
+    # may go either way
+    h = float(np.float32(grid.h))
+    org = np.asarray(grid.origin, np.float32).astype(np.float64)
+    mag = np.abs(pc).sum(axis=1) + np.abs(t).sum() + np.abs(X64).max(axis=1)
+    s = (X64 - org) / h
+    near = np.any(np.abs(s - np.round(s)) < (64.0 * 2.0 ** -24 * mag / h)[:, None], axis=1)
+    fl = fl | near.astype(fl.dtype)
+    lab = np.where(ok.ravel(), lab, 0).astype(np.uint8)
+    fl = np.where(ok.ravel(), fl, 0)
+    return lab.reshape(H, W), fl.reshape(H, W)

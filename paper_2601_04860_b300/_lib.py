@@ -122,6 +122,7 @@ _SIGS = {
                                           ctypes.c_int32, _P, _P]),
     "divas_default_occupancy_params": (DivasOccupancyParams, []),
     "divas_default_surfel_params": (DivasSurfelParams, []),
+    "divas_overlay": (ctypes.c_int, [_P, ctypes.POINTER(DivasCamera), _P, _P, _P]),
     "divas_surfel_labels": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int64,
                                            ctypes.POINTER(DivasCamera), ctypes.POINTER(_P),
                                            ctypes.c_int32, ctypes.c_int32,

@@ -273,6 +273,9 @@ __global__ void __launch_bounds__(kThreads) k_tile_emit(
     const int64_t n_warps = (int64_t)gridDim.x * (kThreads / 32);
     for (int64_t g = (int64_t)blockIdx.x * (kThreads / 32) + warp; g < n_groups; g += n_warps) {
         const int64_t w = g * 32 + lane;
+        // the group's slot base is loaded with its words (one round trip)
+        const uint32_t t_off = __ldg(tile_offset + g / kTileGroups);
+        const uint32_t i_pre = __ldg(item_pref + g * (32 / kItemWords));
         const uint32_t x = w < n_words ? __ldcg(bits + w) : 0u;
         if (w < n_words) {
             if (seg_zero) seg_zero[w] = 0u;
@@ -280,8 +283,7 @@ __global__ void __launch_bounds__(kThreads) k_tile_emit(
         }
         uint32_t nz = __ballot_sync(0xffffffffu, x != 0u);
         if (nz == 0u) continue;  // warp-uniform
-        const int64_t base = (int64_t)__ldg(tile_offset + g / kTileGroups) +
-                             __ldg(item_pref + g * (32 / kItemWords));
+        const int64_t base = (int64_t)t_off + i_pre;
         const uint32_t c = __popc(x);
         uint32_t inc = c;
 #pragma unroll

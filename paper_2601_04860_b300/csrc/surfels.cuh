@@ -289,9 +289,68 @@ __global__ void __launch_bounds__(kSurfThreads) k_surfel_big_out(
     }
 }
 
+// The back-projected overlay of a view (Sec. 3.7 "Iterative Mask
+// Propagation"): each pixel centre unprojected at its planar depth,
+// x = R^T (((u + 1/2 - cx) / fx) d, ((v + 1/2 - cy) / fy) d, d) - R^T t, and
+// the seg bit of the cell holding x (0 for no surface or outside the grid).
+struct OverlayView {
+    float R[9], t[3];
+    float fx, fy, cx, cy;
+    int32_t W, H;
+};
+
+__global__ void __launch_bounds__(kSurfThreads) k_overlay(OverlayView V, const float* __restrict__ depth,
+                                                          GridC G, const uint32_t* __restrict__ seg_bits,
+                                                          uint8_t* __restrict__ out) {
+    const int32_t npix = V.W * V.H;
+    for (int32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < npix; q += gridDim.x * blockDim.x) {
+        const float d = __ldg(depth + q);
+        uint8_t lab = 0;
+        if (d > 0.f && d <= FLT_MAX) {
+            const int x = q % V.W, y = q / V.W;
+            const float pc[3] = {
+                __fsub_rn(__fmul_rn(__fdiv_rn(__fsub_rn(__fadd_rn((float)x, 0.5f), V.cx), V.fx), d), V.t[0]),
+                __fsub_rn(__fmul_rn(__fdiv_rn(__fsub_rn(__fadd_rn((float)y, 0.5f), V.cy), V.fy), d), V.t[1]),
+                __fsub_rn(d, V.t[2])};
+            float X[3];
+#pragma unroll
+            for (int r = 0; r < 3; ++r)  // world = R^T (p_c - t)
+                X[r] = __fmaf_rn(V.R[r], pc[0], __fmaf_rn(V.R[3 + r], pc[1], __fmul_rn(V.R[6 + r], pc[2])));
+            int32_t idx[3];
+            if (point_cell(X, 0, G, idx)) {
+                const int64_t lin = ((int64_t)idx[2] * G.g + idx[1]) * G.g + idx[0];
+                lab = (uint8_t)((__ldg(seg_bits + (lin >> 5)) >> (lin & 31)) & 1u);
+            }
+        }
+        out[q] = lab;
+    }
+}
+
 }  // namespace
 
 extern "C" {
+
+divas_status divas_overlay(divas_ctx* c, const divas_camera* cam, const float* depth, uint8_t* out,
+                           void* stream) {
+    if (!c) return fail(nullptr, DIVAS_E_INVALID, "ctx is NULL");
+    if (!cam || !depth || !out) return fail(c, DIVAS_E_INVALID, "camera, depth and out are required");
+    divas_status st = check_camera(c, cam);
+    if (st != DIVAS_OK) return st;
+    OverlayView V;
+    memcpy(V.R, cam->R, sizeof(V.R));
+    memcpy(V.t, cam->t, sizeof(V.t));
+    V.fx = cam->fx;
+    V.fy = cam->fy;
+    V.cx = cam->cx;
+    V.cy = cam->cy;
+    V.W = cam->W;
+    V.H = cam->H;
+    const int64_t npix = (int64_t)cam->W * cam->H;
+    k_overlay<<<(int)std::min<int64_t>((npix + kSurfThreads - 1) / kSurfThreads, 16 * (int64_t)c->sm_count),
+                kSurfThreads, 0, S(stream)>>>(V, depth, c->G, c->seg_bits, out);
+    DIVAS_LAUNCHED(c, "k_overlay");
+    return DIVAS_OK;
+}
 
 divas_surfel_params divas_default_surfel_params(void) {
     divas_surfel_params p;

@@ -307,6 +307,23 @@ class VoxelFusion:
         self._check(self.lib.divas_depth_weight(self._h, arr, n, m, _ptr(st), _stream(stream)))
         return (out, st) if stats else out
 
+    def overlay(self, cam, depth: torch.Tensor, out: torch.Tensor | None = None,
+                stream=None) -> torch.Tensor:
+        """The back-projected overlay of a view (``divas_overlay``): uint8 (H,
+        W), the seg bit of the cell under each pixel's rendered surface point."""
+        if depth.dtype != torch.float32 or depth.dim() != 2 or not depth.is_contiguous():
+            raise ValueError("depth must be a contiguous (H, W) float32 tensor")
+        if tuple(depth.shape) != (int(cam.H), int(cam.W)):
+            raise ValueError(f"depth is {tuple(depth.shape)}, the camera is {cam.H} x {cam.W}")
+        if out is None:
+            out = torch.empty(depth.shape, dtype=torch.uint8, device=depth.device)
+        elif out.dtype != torch.uint8 or out.shape != depth.shape or not out.is_contiguous():
+            raise ValueError("out must be a contiguous uint8 tensor shaped like depth")
+        c = camera_c(cam)
+        self._check(self.lib.divas_overlay(self._h, ctypes.byref(c), _ptr(depth), _ptr(out),
+                                           _stream(stream)))
+        return out
+
     def surfel_labels(self, mu: torch.Tensor, scales: torch.Tensor, quats: torch.Tensor, cams,
                       masks, mask_type: int, tau_m: float = 0.5, tau_kappa: float = 0.5,
                       eps_aspect: float = 1e-8, stream=None) -> dict:

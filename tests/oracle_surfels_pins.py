@@ -127,5 +127,29 @@ def pin_brute_force_whole_image(S):
         assert (tot, msk) == (bt, bm)
 
 
+def pin_overlay_constructed(S):
+    """A fronto-parallel plane at depth 1 seen by an identity camera (f = 100,
+    64 x 48) through a 4^3 grid of edge 0.25 over [-0.5, 0.5]^2 x [0.5, 1.5]
+    whose one segmented voxel is (2, 2, 2) (x, y in [0, 0.25), z in
+    [1, 1.25)): the overlay is 1 exactly on the pixels whose centres
+    unproject into [0, 0.25)^2, i.e. columns 32..56 and rows 24..48 clipped
+    to the frame; no-surface pixels are 0."""
+    class G:
+        g, origin, h, contracted = 4, (-0.5, -0.5, 0.5), 0.25, False
+    cam = _Cam()
+    seg = np.zeros(64, np.uint8)
+    seg[(2 * 4 + 2) * 4 + 2] = 1
+    D = np.ones((48, 64), np.float32)
+    D[0, :] = np.inf
+    out, _ = S.overlay(G, seg, cam, D)
+    want = np.zeros((48, 64), np.uint8)
+    for y in range(48):
+        for x in range(64):
+            px, py = (x + 0.5 - 32) / 100.0, (y + 0.5 - 24) / 100.0
+            want[y, x] = 1 if (0 <= px < 0.25 and 0 <= py < 0.25 and y > 0) else 0
+    assert np.array_equal(out, want) and want.sum() == 25 * 24 - 0
+
+
 ALL_PINS = [pin_rotation, pin_aspect_threshold, pin_fronto_parallel_counts,
-            pin_coverage_at_threshold, pin_gating_and_max, pin_brute_force_whole_image]
+            pin_coverage_at_threshold, pin_gating_and_max, pin_brute_force_whole_image,
+            pin_overlay_constructed]

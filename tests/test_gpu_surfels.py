@@ -95,3 +95,45 @@ def test_surfels_outside_or_unsegmented():
     r0 = fu.surfel_labels(dm, ds, dq, [], [], wl.mask_type)
     assert not r0["f"].any() and r0["f2"].any()
     fu.close()
+
+
+def test_overlay_matches_oracle():
+    """The back-projected overlay of every view against the oracle's (pixels
+    near a cell boundary, or whose cell the fusion oracle flags, excluded)."""
+    wl, _, _, _ = _setup(n_points=1_000, needles=False)
+    prm = oracle.Params()
+    d = H.upload(wl)
+    fu = VoxelFusion(wl.grid, occ=d["occ"], params=H.to_params(prm))
+    fu.add_views(wl.cams, d["depth"], d["mask"], mask_type=wl.mask_type)
+    fu.finalize(score=True)
+    lin = wl.active_linear()
+    o = oracle.fuse(wl.grid, lin, wl.cams, wl.depth, wl.mask, wl.mask_type, prm)
+    seg = oracle.dense_seg(wl.grid, lin, o["seg"])
+    flagged_cells = np.zeros(wl.grid.g ** 3, bool)
+    flagged_cells[lin[o["flags"] != 0]] = True
+    g, h = wl.grid.g, np.float64(np.float32(wl.grid.h))
+    org = np.asarray(wl.grid.origin, np.float32).astype(np.float64)
+    total = ones = 0
+    for k, cam in enumerate(wl.cams):
+        got = fu.overlay(cam, d["depth"][k]).cpu().numpy()
+        ref, fl = S.overlay(wl.grid, seg, cam, wl.depth[k])
+        # the cell of each pixel's surface point, to skip flagged voxels
+        D = wl.depth[k].astype(np.float64)
+        Hh, Ww = D.shape
+        ys, xs = np.mgrid[0:Hh, 0:Ww]
+        okd = np.isfinite(D) & (D > 0)
+        Dz = np.where(okd, D, 1.0)
+        pc = np.stack([((xs + 0.5 - float(cam.cx)) / float(cam.fx)) * Dz,
+                       ((ys + 0.5 - float(cam.cy)) / float(cam.fy)) * Dz, Dz], -1).reshape(-1, 3)
+        R = np.asarray(cam.R, np.float32).astype(np.float64).reshape(3, 3)
+        X = (pc - np.asarray(cam.t, np.float32).astype(np.float64)) @ R
+        c = np.floor((X - org) / h).astype(np.int64)
+        inside = np.all((c >= 0) & (c < g), axis=1) & okd.ravel()
+        cl = np.where(inside, (c[:, 2] * g + c[:, 1]) * g + c[:, 0], 0)
+        bad = (fl.ravel() != 0) | (inside & flagged_cells[cl])
+        ok = ~bad.reshape(Hh, Ww)
+        assert np.array_equal(got[ok], ref[ok]), f"overlay differs in view {k}"
+        total += ok.sum()
+        ones += ref[ok].sum()
+    assert ones > 100 and total > 0.95 * sum(c.W * c.H for c in wl.cams)
+    fu.close()
