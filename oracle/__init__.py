@@ -7,9 +7,12 @@ this package imports nothing from the library: the two share no code.
 
 ``oracle.c`` is the plain definition of the fusion rule (Sec. 3.5, Eq.
 compact-fusion, Eq. gs-depthweight, Eq. vmask, the thick-path algorithms of
-Appendices A.2 and B.5) and of the Pass 1 label lookup (Eq. pass1);
-``brute.py`` is an independent NumPy restatement that re-casts every pixel
-ray analytically instead of reading the stored depth map.
+Appendices A.2 and B.5), of the depth-tuple modes (the 2DGS thick and thin
+paths of Sec. 3.5 and the NeRF variant of the appendix "NeRF-Backbone 3D
+Fusion Details") and of the Pass 1 label lookup (Eq. pass1); ``brute.py`` is
+an independent NumPy restatement that re-casts every pixel ray analytically
+instead of reading the stored depth map, and states the tuple modes with
+explicit ray vectors.
 
 Parity status: every function here is pinned by tests against closed forms,
 invariants, an independent brute force or finite differences (see the tests
@@ -80,6 +83,12 @@ class _TParams(ctypes.Structure):
                  "behind_margin", "k_dg", "rho_thin")]
 
 
+class _NParams(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in
+                ("gamma", "beta", "b_max", "lambda_range", "rho_thin", "rho_cover", "tau_thin",
+                 "m_thin", "k_dg")]
+
+
 def _configure(lib):
     P = ctypes.c_void_p
     I = ctypes.c_int
@@ -97,6 +106,8 @@ def _configure(lib):
     lib.oracle_set_threads.restype = I
     lib.oracle_fuse_tuple.argtypes = [I, P, D, I, L, P, P, I, P, I, P, P, P, P, P, P, P, P, P, P]
     lib.oracle_fuse_tuple.restype = None
+    lib.oracle_fuse_nerf.argtypes = [I, P, D, I, L, P, P, I, P, I, P, P, P, P, P, P, P, P, P, P]
+    lib.oracle_fuse_nerf.restype = None
     return lib
 
 
@@ -176,6 +187,37 @@ class TupleParams:
         return _TParams(*[float(getattr(self, f)) for f in self.__dataclass_fields__])
 
 
+@dataclass
+class NerfParams:
+    """NeRF-variant constants (Table kernel_hyperparams, LLFF column: gamma
+    4.0, beta 0.2, b_max 10, lambda_range 0.05, rho_thin_thresh 50,
+    rho_cover 0.20, tau_thin 0.6; the thin path's eligibility m > 0.1 from
+    its three-criterion rule).  ``mip360()`` gives the Mip-NeRF 360 column.
+    k_dg (the depth-gradient decay, App. D gives no value) is a reading:
+    0, so pi_dg = 1."""
+
+    gamma: float = 4.0
+    beta: float = 0.2
+    b_max: float = 10.0
+    lambda_range: float = 0.05
+    rho_thin: float = 50.0
+    rho_cover: float = 0.2
+    tau_thin: float = 0.6
+    m_thin: float = 0.1
+    k_dg: float = 0.0
+
+    @staticmethod
+    def mip360() -> "NerfParams":
+        return NerfParams(gamma=0.5, b_max=1.0, lambda_range=5.0, rho_thin=30.0, rho_cover=0.3)
+
+    def f32(self) -> "NerfParams":
+        return NerfParams(*[float(np.float32(getattr(self, f))) for f in
+                            self.__dataclass_fields__])
+
+    def _c(self) -> _NParams:
+        return _NParams(*[float(getattr(self, f)) for f in self.__dataclass_fields__])
+
+
 def _tviews(cams, tup, masks):
     arr = (_TView * len(cams))()
     keep = []
@@ -197,7 +239,7 @@ def _tviews(cams, tup, masks):
         v.d_min, v.d_med, v.d_max = (r.ctypes.data for r in ras)
         v.n_samp = n.ctypes.data
         v.mask = m.ctypes.data
-        v.d_cam = float(np.float32(tup["d_cam"][i]))
+        v.d_cam = float(np.float32(tup["d_cam"][i])) if "d_cam" in tup else 0.0
     return arr, keep
 
 
@@ -285,6 +327,36 @@ class OracleApi:
         del keep
         return out
 
+    def fuse_nerf(self, grid, lin, cams, tup, masks, mask_type, params: Params | None = None,
+                  nparams: NerfParams | None = None, rho=None) -> dict:
+        """NeRF-variant fusion (thick path: ray-voxel alignment, distance and
+        depth tolerances, Gaussian band weight; thin path: footprint support
+        count and peak mask) of views with rasters ``tup`` (dict of per-view
+        lists d_min, d_exp, d_max, n_samp: planar depths and the sample
+        count) into the voxels ``lin`` with densities ``rho`` (None: 1 each).
+        Returns float64 W, Z, P; uint8 seg; uint32 bits, flags; uint8 kind
+        (n_vox x n_views: 0 no vote, 1 thick, 2 thin); float64 thin (t)."""
+        params = params or Params()
+        nparams = nparams or NerfParams()
+        lin = np.ascontiguousarray(lin, np.int64)
+        n = len(lin)
+        g, origin, h, contracted = _grid_args(grid)
+        views, keep = _tviews(cams, {"d_min": tup["d_min"], "d_med": tup["d_exp"],
+                                     "d_max": tup["d_max"], "n_samp": tup["n_samp"]}, masks)
+        rho = None if rho is None else np.ascontiguousarray(rho, np.float64)
+        out = dict(W=np.empty(n), Z=np.empty(n), P=np.empty(n), seg=np.empty(n, np.uint8),
+                   bits=np.empty(n, np.uint32), flags=np.empty(n, np.uint32),
+                   kind=np.empty((n, len(cams)), np.uint8), thin=np.empty((n, len(cams))))
+        pr = params._c()
+        npr = nparams._c()
+        self.lib.oracle_fuse_nerf(g, _p(origin), h, contracted, n, _p(lin), _p(rho), len(cams),
+                                  views, int(mask_type), ctypes.byref(pr), ctypes.byref(npr),
+                                  _p(out["W"]), _p(out["Z"]), _p(out["P"]), _p(out["seg"]),
+                                  _p(out["bits"]), _p(out["flags"]), _p(out["kind"]),
+                                  _p(out["thin"]))
+        del keep
+        return out
+
     def fuse_grad(self, grid, lin, cams, depths, masks, mask_type, gP, params: Params | None = None):
         """Adjoint of ``fuse``: per-view float64 rasters (gM, gD) for a cotangent gP on P."""
         params = params or Params()
@@ -359,6 +431,10 @@ def fuse_grad(*a, **k):
 
 def fuse_tuple(*a, **k):
     return _api().fuse_tuple(*a, **k)
+
+
+def fuse_nerf(*a, **k):
+    return _api().fuse_nerf(*a, **k)
 
 
 def label(*a, **k):

@@ -316,3 +316,118 @@ def fuse_tuple(grid, lin, cams, tup, masks, mask_type, tau_m=0.5, gamma=1.0, alp
                 kind[a, i] = 2
     P = np.where(Z > eps, W / np.where(Z > eps, Z, 1.0), 0.0)
     return dict(W=W, Z=Z, P=P, seg=(P >= tau_cons).astype(np.uint8), bits=bits, kind=kind)
+
+
+def fuse_nerf(grid, lin, cams, tup, masks, mask_type, rho=None, tau_m=0.5, alpha1=0.5,
+              tau_cons=0.5, eps=1e-12, z_near=1e-6, gamma=4.0, beta=0.2, b_max=10.0,
+              lambda_range=0.05, rho_thin=50.0, rho_cover=0.2, tau_thin=0.6, m_thin=0.1,
+              k_dg=0.0):
+    """NeRF-variant fusion written out per voxel and view in ray space
+    (appendix "NeRF-Backbone 3D Fusion Details", Algorithms "Thick-Structure
+    Segmentation via Depth-Weighted Voxel Aggregation" and "Thin-Structure
+    Segmentation via Footprint-Based Coverage Analysis"): the centre pixel's
+    ray as the camera centre o and a unit world direction d through the pixel
+    centre, the planar band [d_min, d_max] turned into the ray segment
+    [d_min, d_max] / cos theta, the projection t_proj = <x_c - o, d> clamped
+    to it, the closest point o + t_c d and its distance; the weight from the
+    ray-space mid-point and half-width; the thin path's footprint as a NumPy
+    slice of the box of the eight projected corners.  Small inputs only.
+
+    Returns W, Z, P, seg, bits, kind (n x views: 0 / 1 thick / 2 thin)."""
+    x, hvs, ok = voxel_centres(grid, lin)
+    n_v = len(cams)
+    N = len(lin)
+    W = np.zeros(N)
+    Z = np.zeros(N)
+    bits = np.zeros(N, np.uint32)
+    kind = np.zeros((N, n_v), np.uint8)
+
+    def logit32(p):
+        return -np.inf if p <= 0 else (np.inf if p >= 1 else
+                                       float(np.float32(np.log(p / (1 - p)))))
+    per_view = []
+    for i, cam in enumerate(cams):
+        R = np.asarray(cam.R, np.float32).astype(np.float64).reshape(3, 3)
+        t = np.asarray(cam.t, np.float32).astype(np.float64)
+        mprob, mhalf = _mask_prob(np.asarray(masks[i]), mask_type)
+        raw = np.asarray(masks[i]).astype(np.float64)
+        if mask_type == 2:
+            gate, elig = raw >= logit32(tau_m), raw > logit32(m_thin)
+        else:
+            gate, elig = mprob >= tau_m, mprob > m_thin
+        dmin = tup["d_min"][i].astype(np.float64)
+        dmax = tup["d_max"][i].astype(np.float64)
+        cen = 0.5 * (dmin + dmax)
+        cp = np.pad(cen, 1, mode="edge")
+        gx = cp[1:-1, 2:] - cp[1:-1, :-2]
+        gy = cp[2:, 1:-1] - cp[:-2, 1:-1]
+        fin = np.isfinite(cp[1:-1, 2:]) & np.isfinite(cp[1:-1, :-2]) & \
+            np.isfinite(cp[2:, 1:-1]) & np.isfinite(cp[:-2, 1:-1])
+        with np.errstate(invalid="ignore", over="ignore"):
+            pig = np.where(fin, np.exp(-k_dg * (gx * gx + gy * gy)), 0.0) if k_dg else \
+                np.ones_like(cen)
+        per_view.append((R, t, -R.T @ t, mprob, mhalf, gate, elig, dmin,
+                         tup["d_exp"][i].astype(np.float64), dmax,
+                         tup["n_samp"][i].astype(np.int64), pig))
+    signs = np.array([[sx, sy, sz] for sz in (-0.5, 0.5) for sy in (-0.5, 0.5)
+                      for sx in (-0.5, 0.5)])
+    for a in range(N):
+        if not ok[a]:
+            continue
+        hv = hvs[a]
+        xc = x[a]
+        rv = 1.0 if rho is None else float(rho[a])
+        for i, cam in enumerate(cams):
+            R, t, o, mprob, mhalf, gate, elig, dmin, dexp, dmax, ns, pig = per_view[i]
+            fx, fy, cx, cy = (float(np.float32(v)) for v in (cam.fx, cam.fy, cam.cx, cam.cy))
+            pc = R @ xc + t
+            if pc[2] <= z_near:
+                continue
+            u = fx * pc[0] / pc[2] + cx
+            v = fy * pc[1] / pc[2] + cy
+            if not (0 <= u < cam.W and 0 <= v < cam.H):
+                continue
+            ix, iy = int(np.floor(u)), int(np.floor(v))
+            xd = pc[2]
+            voted = False
+            lo, ex, hi, nc = dmin[iy, ix], dexp[iy, ix], dmax[iy, ix], ns[iy, ix]
+            if gate[iy, ix] and np.all(np.isfinite([lo, ex, hi])) and min(lo, ex, hi) > 0:
+                kcam = np.array([(ix + 0.5 - cx) / fx, (iy + 0.5 - cy) / fy, 1.0])
+                sec = np.linalg.norm(kcam)           # 1 / cos(theta)
+                d = R.T @ (kcam / sec)               # unit world direction
+                t_proj = float(np.dot(xc - o, d))
+                t_c = min(max(t_proj, lo * sec), hi * sec)
+                delta = np.linalg.norm(xc - (o + t_c * d))
+                tau_sp = hv * pig[iy, ix] + lambda_range * (hi - lo) * sec
+                b = min(beta * nc, b_max)
+                if delta <= tau_sp and abs(xd - ex) <= (gamma + b) * hv:
+                    mu = 0.5 * (lo + hi) * sec
+                    hd = max(0.5 * (hi - lo) * sec, eps * sec)
+                    w = np.exp(-alpha1 * ((t_c - mu) / hd) ** 2)
+                    W[a] += mprob[iy, ix] * w
+                    Z[a] += w
+                    bits[a] |= np.uint32(1 << i) if i < 32 else np.uint32(0)
+                    kind[a, i] = 1
+                    voted = True
+            if voted or not elig[iy, ix] or not (rv >= rho_thin):
+                continue
+            corners = R @ (xc[None, :] + signs * hv).T + t[:, None]
+            if np.any(corners[2] <= z_near):
+                continue
+            cu = fx * corners[0] / corners[2] + cx
+            cv = fy * corners[1] / corners[2] + cy
+            i0, i1 = max(int(np.floor(cu.min())), 0), min(int(np.floor(cu.max())), cam.W - 1)
+            j0, j1 = max(int(np.floor(cv.min())), 0), min(int(np.floor(cv.max())), cam.H - 1)
+            box = (slice(j0, j1 + 1), slice(i0, i1 + 1))
+            tol = (2.0 * gamma + np.minimum(beta * ns[box], b_max)) * hv
+            with np.errstate(invalid="ignore"):
+                support = mhalf[box] & (np.abs(xd - dexp[box]) <= tol)
+            m_max = float(mprob[box].max())
+            tt = m_max if support.sum() >= rho_cover * support.size else 0.0
+            if tt >= tau_thin:
+                W[a] += tt
+                Z[a] += 1.0
+                bits[a] |= np.uint32(1 << i) if i < 32 else np.uint32(0)
+                kind[a, i] = 2
+    P = np.where(Z > eps, W / np.where(Z > eps, Z, 1.0), 0.0)
+    return dict(W=W, Z=Z, P=P, seg=(P >= tau_cons).astype(np.uint8), bits=bits, kind=kind)

@@ -673,3 +673,193 @@ void oracle_fuse_tuple(int g, const double* origin, double h, int contracted, in
         if (flags_out) flags_out[a] = flags;
     }
 }
+
+/* ==========================================================================
+ * NeRF variant of the depth-tuple fusion (Appendix "NeRF-Backbone 3D Fusion
+ * Details": Eqs. distance_cond, dist_tol, depth_tol, nerf-accept, nerf-vote,
+ * nerf-thindepth, nerf-support, nerf-counters, nerf-coverage, nerf-thin;
+ * Algorithms "Thick-Structure Segmentation via Depth-Weighted Voxel
+ * Aggregation" and "Thin-Structure Segmentation via Footprint-Based Coverage
+ * Analysis"), per voxel x (centre x_c, edge Delta = h_v) and view i in order:
+ *
+ *   centre pixel (x_p, y_p) of the projection (in frame, in front of z_near);
+ *   m = mask probability there; check_thin = 1;
+ *   thick entry m >= tau_m (logits l >= logit(tau_m)) with d_min, d_exp,
+ *   d_max finite and positive (planar depths of the tuple at the centre
+ *   pixel), n = n_samp there:
+ *     the pixel's ray through its centre, camera-space direction
+ *     k = ((x_p + 1/2 - cx)/fx, (y_p + 1/2 - cy)/fy, 1), |k| = 1/cos theta;
+ *     a planar depth d on it is the point k d (ray distance |k| d);
+ *     closest point of the band: z_proj = <p, k> / |k|^2 (p = camera-space
+ *     x_c), z_c = clip(z_proj, d_min, d_max), delta = |p - k z_c|;
+ *     tau_spatial = Delta pi_dg + lambda_range |k| (d_max - d_min);
+ *     b = min(beta n, b_max), tau_depth = (gamma + b) Delta;
+ *     x_d = p_z; accept when delta <= tau_spatial and |x_d - d_exp| <=
+ *     tau_depth: mu = (d_min + d_max)/2, h_d = max((d_max - d_min)/2, eps),
+ *     r = |z_c - mu| / h_d (the ray-space ratio: |k| cancels),
+ *     w = exp(-alpha1 r^2), W += m w, Z += w, check_thin = 0;
+ *   thin fallback when check_thin, m > m_thin (logits l > logit(m_thin) in
+ *   FP32) and rho_x >= rho_thin: the 8 corners x_c +- Delta/2 (all in front
+ *   of z_near), the pixel box of their projections clipped to the frame (N
+ *   pixels); per box pixel q: b_q = min(beta n(q), b_max), support = m(q) >
+ *   1/2 and |x_d - d_exp(q)| <= (2 gamma + b_q) Delta; n_valid = the
+ *   supports, m_max = max of m(q) over the whole box; t = m_max when n_valid
+ *   >= rho_cover N, else 0; t >= tau_thin -> W += t, Z += 1.
+ *   P = W / Z if Z > eps else 0; seg = P >= tau_cons.
+ *
+ * Near-boundary flags as in the 2DGS variant: the spatial gate against 4e-6
+ * (1 + |x| + |o|) (a distance formed from coordinate differences), the depth
+ * gates against 1e-6 |x_d|, box edges near an integer, tau_thin, z_near.
+ *
+ * parity: pinned by the NeRF-variant tests (single-voxel closed forms of
+ * every gate and of the weight, an independent NumPy statement in ray space).
+ * ========================================================================== */
+
+typedef struct {
+    double gamma, beta, b_max, lambda_range, rho_thin, rho_cover, tau_thin, m_thin, k_dg;
+} oracle_nparams;
+
+void oracle_fuse_nerf(int g, const double* origin, double h, int contracted, int64_t n_vox,
+                      const int64_t* lin, const double* rho, int n_views,
+                      const oracle_tview* views, int mask_type, const oracle_params* pr,
+                      const oracle_nparams* np, double* W_out, double* Z_out, double* P_out,
+                      uint8_t* seg_out, uint32_t* bits_out, uint32_t* flags_out,
+                      uint8_t* kind_out, double* thin_out) {
+    /* the thin eligibility m > m_thin on logits: l > logit(m_thin), as FP32 */
+    double l_thin = (np->m_thin <= 0.0) ? -INFINITY
+                  : (np->m_thin >= 1.0) ? INFINITY
+                  : (double)(float)log(np->m_thin / (1.0 - np->m_thin));
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t a = 0; a < n_vox; ++a) {
+        uint32_t flags = 0, bits = 0;
+        double Wsum = 0.0, Zsum = 0.0;
+        double x[3], hv;
+        int ok = voxel_centre(lin[a], g, origin, h, contracted, x, &hv, &flags);
+        double rho_v = rho ? rho[a] : 1.0;
+        for (int i = 0; i < n_views; ++i) {
+            if (kind_out) kind_out[a * n_views + i] = 0;
+            if (thin_out) thin_out[a * n_views + i] = 0.0;
+            if (!ok) continue;
+            const oracle_tview* vw = &views[i];
+            const float* R = vw->R;
+            double p[3];
+            int ix, iy;
+            oracle_view pv = {{0}, {0}, vw->fx, vw->fy, vw->cx, vw->cy, vw->W, vw->H, NULL, NULL};
+            memcpy(pv.R, vw->R, sizeof(pv.R));
+            memcpy(pv.t, vw->t, sizeof(pv.t));
+            if (!project(&pv, x, pr->z_near, p, &ix, &iy, &flags)) continue;
+            int64_t pix = (int64_t)iy * vw->W + ix;
+            double m;
+            int pass, half;
+            tmask_at(vw, mask_type, pix, pr, &m, &pass, &half);
+            double xd = p[2];
+            double oc[3];
+            for (int r = 0; r < 3; ++r) /* camera centre o = -R^T t */
+                oc[r] = -((double)R[r] * vw->t[0] + (double)R[3 + r] * vw->t[1] +
+                          (double)R[6 + r] * vw->t[2]);
+            double xn = sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
+            double on = sqrt(oc[0] * oc[0] + oc[1] * oc[1] + oc[2] * oc[2]);
+            int check_thin = 1;
+            /* thick path (Eqs. distance_cond .. nerf-vote) */
+            double dmin = vw->d_min[pix], dexp = vw->d_med[pix], dmax = vw->d_max[pix];
+            int64_t n = vw->n_samp[pix];
+            if (pass && isfinite(dmin) && isfinite(dexp) && isfinite(dmax) && dmin > 0.0 &&
+                dexp > 0.0 && dmax > 0.0) {
+                double k[3] = {((double)ix + 0.5 - (double)vw->cx) / (double)vw->fx,
+                               ((double)iy + 0.5 - (double)vw->cy) / (double)vw->fy, 1.0};
+                double k2 = k[0] * k[0] + k[1] * k[1] + 1.0;
+                double zproj = (p[0] * k[0] + p[1] * k[1] + p[2]) / k2;
+                double zc = zproj < dmin ? dmin : (zproj > dmax ? dmax : zproj);
+                double e0 = p[0] - k[0] * zc, e1 = p[1] - k[1] * zc, e2 = p[2] - zc;
+                double delta = sqrt(e0 * e0 + e1 * e1 + e2 * e2);
+                double tau_sp = hv * pi_dg(vw, ix, iy, np->k_dg) +
+                                np->lambda_range * sqrt(k2) * (dmax - dmin);
+                double b = fmin(np->beta * (double)n, np->b_max);
+                double tau_d = (np->gamma + b) * hv;
+                near_flag(delta, tau_sp, 4.0 * (1.0 + xn + on), &flags);
+                near_flag(fabs(xd - dexp), tau_d, fabs(xd), &flags);
+                if (delta <= tau_sp && fabs(xd - dexp) <= tau_d) {
+                    double mu = 0.5 * (dmin + dmax);
+                    double hd = fmax(0.5 * (dmax - dmin), pr->eps);
+                    double r = fabs(zc - mu) / hd;
+                    double w = exp(-pr->alpha1 * r * r);
+                    Wsum += m * w;
+                    Zsum += w;
+                    bits |= i < 32 ? 1u << i : 0u;
+                    check_thin = 0;
+                    if (kind_out) kind_out[a * n_views + i] = 1;
+                }
+            }
+            /* thin fallback (Eqs. nerf-thindepth .. nerf-thin) */
+            int eligible;
+            if (mask_type == MASK_LOGIT_F32)
+                eligible = (double)((const float*)vw->mask)[pix] > l_thin;
+            else
+                eligible = m > np->m_thin;
+            if (!check_thin || !eligible || !(rho_v >= np->rho_thin)) continue;
+            double umin = INFINITY, umax = -INFINITY, vmin = INFINITY, vmax = -INFINITY;
+            int corners_ok = 1;
+            for (int c = 0; c < 8; ++c) {
+                double xc[3] = {x[0] + ((c & 1) ? 0.5 : -0.5) * hv,
+                                x[1] + ((c & 2) ? 0.5 : -0.5) * hv,
+                                x[2] + ((c & 4) ? 0.5 : -0.5) * hv};
+                double q[3];
+                for (int r = 0; r < 3; ++r)
+                    q[r] = (double)R[3 * r] * xc[0] + (double)R[3 * r + 1] * xc[1] +
+                           (double)R[3 * r + 2] * xc[2] + vw->t[r];
+                near_flag(q[2], pr->z_near, fabs(q[2]) + 1.0, &flags);
+                if (!(q[2] > pr->z_near)) { corners_ok = 0; break; }
+                double u = (double)vw->fx * q[0] / q[2] + (double)vw->cx;
+                double v = (double)vw->fy * q[1] / q[2] + (double)vw->cy;
+                umin = fmin(umin, u); umax = fmax(umax, u);
+                vmin = fmin(vmin, v); vmax = fmax(vmax, v);
+            }
+            if (!corners_ok) continue;
+            {
+                const double ext[4] = {umin, umax, vmin, vmax};
+                for (int e = 0; e < 4; ++e) {
+                    double lim = e < 2 ? (double)vw->W : (double)vw->H;
+                    double c = e < 2 ? (double)vw->cx : (double)vw->cy;
+                    double s = 1.0 + fabs(c) + fabs(ext[e] - c);
+                    if (ext[e] > -0.5 && ext[e] < lim + 0.5 && dist_to_int(ext[e]) < ORACLE_MARGIN * s)
+                        flags |= FLAG_TUPLE;
+                }
+            }
+            int i0 = (int)fmax(floor(umin), 0.0), i1 = (int)fmin(floor(umax), vw->W - 1.0);
+            int j0 = (int)fmax(floor(vmin), 0.0), j1 = (int)fmin(floor(vmax), vw->H - 1.0);
+            int64_t N = (int64_t)(i1 - i0 + 1) * (j1 - j0 + 1), n_valid = 0;
+            double m_max = 0.0;
+            for (int yy = j0; yy <= j1; ++yy)
+                for (int xx = i0; xx <= i1; ++xx) {
+                    int64_t q = (int64_t)yy * vw->W + xx;
+                    double mq;
+                    int pq, hq;
+                    tmask_at(vw, mask_type, q, pr, &mq, &pq, &hq);
+                    if (mq > m_max) m_max = mq;
+                    double bq = fmin(np->beta * (double)vw->n_samp[q], np->b_max);
+                    double tq = (2.0 * np->gamma + bq) * hv;
+                    double e = fabs(xd - (double)vw->d_med[q]);
+                    near_flag(e, tq, fabs(xd), &flags);
+                    if (hq && e <= tq) ++n_valid;
+                }
+            double t = ((double)n_valid >= np->rho_cover * (double)N) ? m_max : 0.0;
+            if (thin_out) thin_out[a * n_views + i] = t;
+            near_flag(t, np->tau_thin, 1.0, &flags);
+            if (t >= np->tau_thin) {
+                Wsum += t;
+                Zsum += 1.0;
+                bits |= i < 32 ? 1u << i : 0u;
+                if (kind_out) kind_out[a * n_views + i] = 2;
+            }
+        }
+        double P = (Zsum > pr->eps) ? Wsum / Zsum : 0.0;
+        if (Zsum > pr->eps && fabs(P - pr->tau_cons) < ORACLE_MARGIN) flags |= FLAG_CONS;
+        int seg = (P >= pr->tau_cons);
+        if (W_out) W_out[a] = Wsum;
+        if (Z_out) Z_out[a] = Zsum;
+        if (P_out) P_out[a] = P;
+        if (seg_out) seg_out[a] = (uint8_t)seg;
+        if (bits_out) bits_out[a] = bits;
+        if (flags_out) flags_out[a] = flags;
+    }
+}

@@ -24,6 +24,8 @@ from .scenes import (  # noqa: F401
     config3,
     config4,
     gaussians,
+    nerf_density,
+    with_nerf_tuple,
     look_at,
     render_tuple,
     session_mix,

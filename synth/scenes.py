@@ -294,6 +294,68 @@ def with_tuple(wl: "Workload", seed: int = 1100, band: float = 2.0, untrusted: f
     return out
 
 
+def with_nerf_tuple(wl: "Workload", seed: int = 1500, noisy: float = 0.05) -> "Workload":
+    """The workload plus the depth tuple a NeRF renderer reports (the NeRF
+    variant of the fusion): planar depths d_min = front hit - U[0, 1] h (the
+    first significant sample), d_exp = front hit + U[-1/4, 3/4] h (the
+    expected depth), d_max = min(exit of the hit primitive, front hit + U[1,
+    6] h) but at least d_exp (the cumulative-weight cut-off inside the
+    object's volume), n_samp = 4 + U{0..23} + 4 x (surfaces crossed) ray
+    samples; on a fraction ``noisy`` of hit pixels d_exp is off by U[-8, 8] h
+    (a depth outlier).  Misses are +inf with n_samp = 0.  Stored as
+    ``tuple`` with keys d_min, d_exp, d_max, n_samp."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    h = float(wl.grid.h)
+    t = {"d_min": [], "d_exp": [], "d_max": [], "n_samp": []}
+    for cam in wl.cams:
+        front, back, cross, _hit = render_tuple(wl.scene, cam)
+        hitm = np.isfinite(front)
+        f = np.where(hitm, front, 0.0).astype(np.float64)
+        shape = front.shape
+        d_min = f - rng.uniform(0.0, 1.0, shape) * h
+        d_exp = f + rng.uniform(-0.25, 0.75, shape) * h
+        out = hitm & (rng.uniform(0, 1, shape) < noisy)
+        d_exp = np.where(out, f + rng.uniform(-8.0, 8.0, shape) * h, d_exp)
+        cut = f + rng.uniform(1.0, 6.0, shape) * h
+        bk = np.where(np.isfinite(back) & (back > front), back, cut).astype(np.float64)
+        d_max = np.maximum(np.minimum(bk, cut), d_exp)
+        d_min = np.minimum(d_min, d_exp)
+        inf = np.float32(np.inf)
+        t["d_min"].append(np.where(hitm, d_min, inf).astype(np.float32))
+        t["d_exp"].append(np.where(hitm, d_exp, inf).astype(np.float32))
+        t["d_max"].append(np.where(hitm, d_max, inf).astype(np.float32))
+        ns = 4 + rng.integers(0, 24, shape) + 4 * cross
+        t["n_samp"].append(np.where(hitm, ns, 0).astype(np.uint16))
+    out_wl = Workload(**{k: getattr(wl, k) for k in wl.__dataclass_fields__ if k != "tuple"})
+    out_wl.tuple = t
+    out_wl.name = wl.name + "-nerf"
+    return out_wl
+
+
+def nerf_density(wl: "Workload", seed: int = 1600, haze: float = 0.01,
+                 lo: float = 10.0, hi: float = 200.0) -> np.ndarray:
+    """A dense g^3 FP32 density grid (x fastest) for the workload's occupied
+    voxels, the way a NeRF's density field sampled at voxel centres looks:
+    log-uniform in [lo, hi) on the occupied prior, U[0, lo) haze on a fraction
+    ``haze`` of the other cells, 0 elsewhere.  density >= lo gives back the
+    prior."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    g = int(wl.grid.g)
+    if wl.occ is not None:
+        occ = np.asarray(wl.occ, np.uint8).reshape(-1) != 0
+    else:
+        occ = np.zeros(g ** 3, bool)
+        occ[wl.active_linear()] = True
+    rho = np.zeros(g ** 3, np.float32)
+    k = int(occ.sum())
+    rho[occ] = np.exp(rng.uniform(np.log(lo), np.log(hi), k)).astype(np.float32)
+    rho[occ] = np.maximum(rho[occ], np.float32(lo))
+    free = np.nonzero(~occ)[0]
+    pick = rng.choice(len(free), size=int(haze * len(free)), replace=False)
+    rho[free[pick]] = np.minimum(rng.uniform(0.0, lo, len(pick)), np.nextafter(np.float32(lo), np.float32(0)))
+    return rho
+
+
 def gaussians(wl: "Workload", seed: int = 1300, floaters: float = 0.005, dyadic: bool = True):
     """A 2DGS surfel cloud for the workload's scene (the input of the
     occupancy construction, Sec. 3.5): centres = the workload's surface points

@@ -588,6 +588,145 @@ def pin_tuple_bruteforce(orc):
         assert np.allclose(r["Z"][ok], b["Z"][ok], rtol=1e-12, atol=1e-300)
 
 
-ALL_PINS = [pin_single_view_closed_form, pin_pixel_convention, pin_alpha0_mean, pin_invariants,
-            pin_scale_invariance, pin_sphere_scene, pin_bruteforce, pin_labels, pin_gradient_fd,
-            pin_tuple_closed_form, pin_tuple_bruteforce]
+# --------------------------------------------------------------------------
+# NeRF variant (appendix "NeRF-Backbone 3D Fusion Details"; Algorithms
+# "Thick-Structure Segmentation via Depth-Weighted Voxel Aggregation" and
+# "Thin-Structure Segmentation via Footprint-Based Coverage Analysis")
+# --------------------------------------------------------------------------
+def _nerf_run(orc, d_min, d_exp, d_max, n=5, mask=1.0, rho=None, nparams=None):
+    """The single-voxel setup of the 2DGS pins (x_d = 2.375, centre pixel
+    (50, 40) whose centre ray is k = (0.0025, -0.0025, 1), h_v = 1/4,
+    footprint pixels 44..55 x 35..46, N = 144)."""
+    grid, cam, lin, xd = _tuple_setup()
+
+    def ras(v, dtype=np.float32):
+        return np.broadcast_to(np.asarray(v, dtype), (cam.H, cam.W)).copy()
+    tup = {"d_min": [ras(d_min)], "d_exp": [ras(d_exp)], "d_max": [ras(d_max)],
+           "n_samp": [ras(n, np.uint16)]}
+    return orc.fuse_nerf(grid, lin, [cam], tup, [ras(mask)], oracle.MASK_F32, params=P_DEFAULT,
+                         nparams=nparams or oracle.NerfParams(),
+                         rho=None if rho is None else np.array([rho], np.float64))
+
+
+def pin_nerf_closed_form(orc):
+    f = lambda v: float(np.float32(v))  # noqa: E731  (raster values are FP32)
+    k = np.array([0.0025, -0.0025, 1.0])
+    p = np.array([0.0, 0.0, 2.375])
+    # base: the band contains the projection onto the centre ray, z_c =
+    # <p, k> / |k|^2; weight from |z_c - mid| / half-width
+    r = _nerf_run(orc, 2.275, 2.375, 2.575)
+    zc = p @ k / (k @ k)
+    w = math.exp(-0.5 * (abs(zc - 0.5 * (f(2.275) + f(2.575))) / (0.5 * (f(2.575) - f(2.275)))) ** 2)
+    assert r["kind"][0, 0] == 1 and math.isclose(r["W"][0], w, rel_tol=1e-12)
+    assert math.isclose(r["Z"][0], w, rel_tol=1e-12)
+    # a thick vote leaves no thin vote, density or not
+    r = _nerf_run(orc, 2.275, 2.375, 2.575, rho=100.0)
+    assert r["kind"][0, 0] == 1 and r["Z"][0] == r["W"][0]
+    # band beyond the voxel: z_c = d_min, delta = |p - k d_min| ~ 0.3 > tau_spatial =
+    # h_v + 0.05 |k| 0.1 (rejected); lambda_range = 1 widens it by |k| 0.1 (accepted,
+    # r = 1 exactly: w = exp(-1/2))
+    r = _nerf_run(orc, 2.675, 2.375, 2.775)
+    assert r["kind"][0, 0] == 0 and r["Z"][0] == 0.0
+    delta = np.linalg.norm(p - k * f(2.675))
+    assert 0.25 + 0.05 * np.linalg.norm(k) * 0.1 < delta < 0.25 + np.linalg.norm(k) * 0.1
+    r = _nerf_run(orc, 2.675, 2.375, 2.775, nparams=oracle.NerfParams(lambda_range=1.0))
+    assert r["kind"][0, 0] == 1 and math.isclose(r["W"][0], math.exp(-0.5), rel_tol=1e-9)
+    # depth tolerance (gamma + min(beta n, b_max)) h_v against |x_d - d_exp| = 1.2:
+    # n = 5 -> 1.25 (accepted), n = 3 -> 1.15, b_max = 0.5 -> 1.125 (rejected)
+    assert abs(2.375 - f(3.575)) > 1.15 + 1e-6 and abs(2.375 - f(3.575)) < 1.25 - 1e-6
+    assert _nerf_run(orc, 2.275, 3.575, 3.675)["kind"][0, 0] == 1
+    assert _nerf_run(orc, 2.275, 3.575, 3.675, n=3)["kind"][0, 0] == 0
+    assert _nerf_run(orc, 2.275, 3.575, 3.675,
+                     nparams=oracle.NerfParams(b_max=0.5))["kind"][0, 0] == 0
+    # thin path: centre mask 0.3 (no thick entry, > m_thin), density 100 >= 50,
+    # d_exp at the voxel everywhere; s supportive pixels (m = 1) of N = 144:
+    # vote iff s >= 0.2 N = 28.8
+    for s, want in ((28, 0), (29, 2)):
+        m = np.zeros((80, 100), np.float32)
+        m.reshape(-1)[np.ravel_multi_index((np.arange(35, 47).repeat(12)[:s],
+                                            np.tile(np.arange(44, 56), 12)[:s]), (80, 100))] = 1.0
+        m[40, 50] = 0.3
+        r = _nerf_run(orc, 2.275, 2.375, 2.575, mask=m, rho=100.0)
+        assert r["kind"][0, 0] == want, (s, r["kind"])
+        if want:
+            assert r["W"][0] == 1.0 and r["Z"][0] == 1.0
+    # coverage is inclusive: rho_cover = 1/4 of N = 144 is exactly 36
+    m = np.zeros((80, 100), np.float32)
+    m[35:38, 44:56] = 1.0
+    m[40, 50] = 0.3
+    r = _nerf_run(orc, 2.275, 2.375, 2.575, mask=m, rho=100.0,
+                  nparams=oracle.NerfParams(rho_cover=0.25))
+    assert r["kind"][0, 0] == 2
+    # m_max over the whole box: supportive pixels at 0.7, one unsupported
+    # pixel at 0.95 (its d_exp far off) -> t = 0.95
+    m = np.full((80, 100), 0.7, np.float32)
+    m[40, 50] = 0.3
+    m[36, 45] = 0.95
+    e = np.full((80, 100), 2.375, np.float32)
+    e[36, 45] = 9.0
+    r = _nerf_run(orc, 2.275, e, 9.5, mask=m, rho=100.0)
+    assert r["kind"][0, 0] == 2 and r["W"][0] == f(0.95) and r["thin"][0, 0] == f(0.95)
+    # the thin depth tolerance doubles gamma: (2 gamma + 1) h_v = 2.25 admits
+    # |x_d - d_exp| = 2.2; gamma h_v + 0.25 = 1.25 would not
+    m = np.ones((80, 100), np.float32)
+    m[40, 50] = 0.3
+    r = _nerf_run(orc, 2.275, 2.375 + 2.2, 5.0, mask=m, rho=100.0)
+    assert r["kind"][0, 0] == 2
+    r = _nerf_run(orc, 2.275, 2.375 + 2.3, 5.0, mask=m, rho=100.0)
+    assert r["kind"][0, 0] == 0
+    # thin eligibility: density below rho_thin, centre mask not above 0.1
+    assert _nerf_run(orc, 2.275, 2.375, 2.575, mask=m, rho=49.0)["kind"][0, 0] == 0
+    m[40, 50] = np.float32(0.1)
+    assert _nerf_run(orc, 2.275, 2.375, 2.575, mask=m, rho=100.0,
+                     nparams=oracle.NerfParams(m_thin=float(np.float32(0.1))))["kind"][0, 0] == 0
+    # clipped footprint: the camera shifted so the voxel projects to pixel
+    # (1, 40): its box covers pixels 0..6 (7 of 12 columns), N = 84; 17 of
+    # them supportive is enough (17 >= 16.8), 16 is not
+    grid, cam, lin, xd = _tuple_setup()
+    cam2 = synth.Camera(cam.R, cam.t, cam.fx, cam.fy, 1.25, cam.cy, cam.W, cam.H)
+    for s, want in ((16, 0), (17, 2)):
+        m = np.zeros((80, 100), np.float32)
+        rows = np.arange(35, 47).repeat(7)[:s]
+        cols = np.tile(np.arange(0, 7), 12)[:s]
+        m[rows, cols] = 1.0
+        m[40, 1] = 0.3  # (rows 35..37 hold the supportive pixels)
+        ras = lambda v, dt=np.float32: np.broadcast_to(np.asarray(v, dt), (80, 100)).copy()  # noqa: E731
+        tup = {"d_min": [ras(2.275)], "d_exp": [ras(2.375)], "d_max": [ras(2.575)],
+               "n_samp": [ras(5, np.uint16)]}
+        r = orc.fuse_nerf(grid, lin, [cam2], tup, [m], oracle.MASK_F32, params=P_DEFAULT,
+                          nparams=oracle.NerfParams(), rho=np.array([100.0]))
+        assert r["kind"][0, 0] == want, (s, r["kind"])
+
+
+def pin_nerf_bruteforce(orc):
+    wl = synth.config2(g=40, W=140, H=105, n_ell=40, n_points=500)
+    nw = synth.with_nerf_tuple(wl)
+    rho = synth.nerf_density(wl)
+    lin = wl.active_linear()
+    masks32 = [m.view(np.float16).astype(np.float32) if m.dtype == np.uint16 else m
+               for m in wl.mask]
+    mt = oracle.MASK_F32 if wl.mask_type == oracle.MASK_F16 else wl.mask_type
+    for npar, prm, masks, mtype in [
+            (oracle.NerfParams(), P_DEFAULT, wl.mask, wl.mask_type),
+            (oracle.NerfParams.mip360(), oracle.Params(tau_m=0.4, alpha1=1.0), masks32, mt),
+            (oracle.NerfParams(k_dg=30.0, rho_cover=0.4, tau_thin=0.3), P_DEFAULT,
+             [np.log(np.clip(m, 1e-6, 1 - 1e-6) / (1 - np.clip(m, 1e-6, 1 - 1e-6))).astype(np.float32)
+              for m in masks32], oracle.MASK_LOGIT_F32)]:
+        r = orc.fuse_nerf(wl.grid, lin, wl.cams, nw.tuple, masks, mtype, params=prm,
+                          nparams=npar, rho=rho[lin].astype(np.float64))
+        b = brute.fuse_nerf(wl.grid, lin, wl.cams, nw.tuple, masks, mtype, rho=rho[lin],
+                            tau_m=prm.tau_m, alpha1=prm.alpha1,
+                            **{k: getattr(npar, k) for k in npar.__dataclass_fields__})
+        ok = r["flags"] == 0
+        assert ok.mean() > 0.95
+        assert (b["kind"] == 1).sum() > 50 and (b["kind"] == 2).sum() > 20
+        assert np.array_equal(r["kind"][ok], b["kind"][ok])
+        assert np.array_equal(r["bits"][ok], b["bits"][ok])
+        assert np.allclose(r["W"][ok], b["W"][ok], rtol=1e-12, atol=1e-300)
+        assert np.allclose(r["Z"][ok], b["Z"][ok], rtol=1e-12, atol=1e-300)
+
+
+ALL_PINS = [pin_nerf_closed_form, pin_single_view_closed_form, pin_pixel_convention,
+            pin_alpha0_mean, pin_invariants, pin_scale_invariance, pin_sphere_scene,
+            pin_bruteforce, pin_labels, pin_gradient_fd, pin_tuple_closed_form,
+            pin_tuple_bruteforce, pin_nerf_bruteforce]

@@ -75,13 +75,43 @@ MUTANTS = {
                               "int seethru = dmed < tp->gamma_st * vw->d_cam;"),
     "tuple_hw_not_halved": ("double dhw = fmax(0.5 * (dmax - dmin) * ray, pr->eps);",
                             "double dhw = fmax((dmax - dmin) * ray, pr->eps);"),
-    "tuple_thin_denominator_t": ("Wsum += t;\n                Zsum += 1.0;",
-                                 "Wsum += t;\n                Zsum += t;"),
+    "tuple_thin_denominator_t": ("if (t >= tp->tau_thin) {\n                Wsum += t;\n                Zsum += 1.0;",
+                                 "if (t >= tp->tau_thin) {\n                Wsum += t;\n                Zsum += t;"),
     "tuple_dist_gate_dropped": (" &&\n                        d2 <= gate * gate)", ")"),
     "tuple_pi_ignored": ("double tau_sp = hv * pi_dg(vw, ix, iy, tp->k_dg);",
                          "double tau_sp = hv;"),
     "tuple_thin_trusted_dropped": ("int fr_q = (layered_exact(nq, A, S1, S2) || st_q) && tr_q;",
                                    "int fr_q = (layered_exact(nq, A, S1, S2) || st_q);"),
+    # NeRF variant
+    "nerf_lambda_range_dropped": ("double tau_sp = hv * pi_dg(vw, ix, iy, np->k_dg) +\n"
+                                  "                                np->lambda_range * sqrt(k2) * (dmax - dmin);",
+                                  "double tau_sp = hv * pi_dg(vw, ix, iy, np->k_dg);"),
+    "nerf_delta_unclamped": ("double zc = zproj < dmin ? dmin : (zproj > dmax ? dmax : zproj);",
+                             "double zc = zproj;"),
+    "nerf_bonus_uncapped": ("double b = fmin(np->beta * (double)n, np->b_max);",
+                            "double b = np->beta * (double)n;"),
+    "nerf_thin_gamma_not_doubled": ("double tq = (2.0 * np->gamma + bq) * hv;",
+                                    "double tq = (np->gamma + bq) * hv;"),
+    "nerf_mmax_supportive_only": (
+        "if (mq > m_max) m_max = mq;\n"
+        "                    double bq = fmin(np->beta * (double)vw->n_samp[q], np->b_max);\n"
+        "                    double tq = (2.0 * np->gamma + bq) * hv;\n"
+        "                    double e = fabs(xd - (double)vw->d_med[q]);\n"
+        "                    near_flag(e, tq, fabs(xd), &flags);\n"
+        "                    if (hq && e <= tq) ++n_valid;",
+        "double bq = fmin(np->beta * (double)vw->n_samp[q], np->b_max);\n"
+        "                    double tq = (2.0 * np->gamma + bq) * hv;\n"
+        "                    double e = fabs(xd - (double)vw->d_med[q]);\n"
+        "                    near_flag(e, tq, fabs(xd), &flags);\n"
+        "                    if (hq && e <= tq) { ++n_valid; if (mq > m_max) m_max = mq; }"),
+    "nerf_coverage_exclusive": ("((double)n_valid >= np->rho_cover * (double)N)",
+                                "((double)n_valid > np->rho_cover * (double)N)"),
+    "nerf_weight_full_width": ("double hd = fmax(0.5 * (dmax - dmin), pr->eps);",
+                               "double hd = fmax(dmax - dmin, pr->eps);"),
+    "nerf_density_ignored": ("if (!check_thin || !eligible || !(rho_v >= np->rho_thin)) continue;",
+                             "if (!check_thin || !eligible) continue;"),
+    "nerf_thin_after_thick": ("if (!check_thin || !eligible || !(rho_v >= np->rho_thin)) continue;",
+                              "if (!eligible || !(rho_v >= np->rho_thin)) continue;"),
 }
 
 
