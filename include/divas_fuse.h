@@ -277,6 +277,80 @@ divas_status divas_fuse_add_views_tuple_profiled(divas_ctx* ctx, const divas_tup
                                                  void* const* stage_events, void* stream);
 
 /*
+ * NeRF variant of the depth-tuple fusion (appendix "NeRF-Backbone 3D Fusion
+ * Details": Eqs. distance_cond, dist_tol, depth_tol, nerf-accept, nerf-vote,
+ * nerf-thindepth .. nerf-thin; Algorithms "Thick-Structure Segmentation via
+ * Depth-Weighted Voxel Aggregation" and "Thin-Structure Segmentation via
+ * Footprint-Based Coverage Analysis").  Views are divas_tuple_view with
+ * d_med holding the expected depth d_exp (d_min, d_exp, d_max planar; n_samp
+ * the ray-sample count; d_cam unused).  Per voxel (edge Delta) and view:
+ *   thick, at the centre pixel (x, y) when m >= tau_m and the three depths
+ *   are finite and positive: k = ((x + 1/2 - cx)/fx, (y + 1/2 - cy)/fy, 1)
+ *   (the pixel-centre ray; a planar depth d on it is the point k d), p the
+ *   camera-space voxel centre, z_c = clip(<p, k> / |k|^2, d_min, d_max)
+ *   (clip(z, a, b) = a if z < a, else b if z > b, else z; also for b < a),
+ *   delta = |p - k z_c| <= Delta pi_dg + lambda_range |k| (d_max - d_min) and
+ *   |p_z - d_exp| <= (gamma + min(beta n, b_max)) Delta: W += m w, Z += w,
+ *   w = exp(-alpha1 r^2), r = |z_c - (d_min + d_max)/2| / max((d_max -
+ *   d_min)/2, eps);
+ *   thin, when the thick path did not vote, m > m_thin (logits: l >
+ *   logit(m_thin) in FP32) and the voxel's density >= rho_thin: over the box
+ *   of the 8 projected corners clipped to the frame (N pixels), n_valid = #
+ *   {q: m(q) > 1/2 and |p_z - d_exp(q)| <= (2 gamma + min(beta n(q), b_max))
+ *   Delta}, m_max = max m(q); t = m_max if n_valid >= rho_cover N, else 0;
+ *   t >= tau_thin: W += t, Z += 1.
+ * gamma here replaces the context's gamma; alpha1, tau_m, eps and z_near
+ * are the context's.
+ */
+enum { DIVAS_NERF_LLFF = 0, DIVAS_NERF_MIP360 = 1 };
+
+typedef struct {
+    float gamma;         /* base tolerance multiplier (4.0 LLFF, 0.5 Mip-NeRF 360)          */
+    float beta;          /* per-sample bonus (0.2)                                         */
+    float b_max;         /* bonus cap (10, 1)                                              */
+    float lambda_range;  /* band slack of the spatial tolerance (0.05, 5.0)                */
+    float rho_thin;      /* thin-path density floor (50, 30)                               */
+    float rho_cover;     /* thin coverage threshold (0.20, 0.30)                           */
+    float tau_thin;      /* thin acceptance (0.6); must be > 0                             */
+    float m_thin;        /* thin eligibility of the centre mask (0.1), in [0, 1)           */
+    float k_dg;          /* depth-gradient decay (0: factor 1)                             */
+    int32_t reserved;
+} divas_nerf_params;
+
+/* Table kernel_hyperparams' column for DIVAS_NERF_LLFF or DIVAS_NERF_MIP360
+ * (any other value: LLFF); m_thin from the thin path's eligibility rule,
+ * k_dg = 0 a reading (no value given). */
+divas_nerf_params divas_default_nerf_params(int32_t preset);
+
+/* Fold n_views (1..32) NeRF tuple views in index order onto the
+ * accumulators; finalize as usual.  density: NULL (every active voxel has
+ * density 1) or device g^3 FP32 (x fastest, 4-byte aligned), read for the
+ * thin path's floor.  Scratch (the heavy list, mask-tile maxima) is the
+ * tuple mode's, grown on demand (outside a stream capture, else
+ * DIVAS_E_STATE).  DIVAS_E_INVALID: NULL or out-of-range arguments, before
+ * any launch. */
+divas_status divas_fuse_add_views_nerf(divas_ctx* ctx, const divas_tuple_view* views,
+                                       int32_t n_views, const divas_nerf_params* np,
+                                       const float* density, void* stream);
+
+/* The same, recording stage_events[k] (cudaEvent_t, nullable) on stream: [0]
+ * before the mask-tile maps, [1] after them, [2] after the scan of the last
+ * 16-view batch, [3] after its heavy pass. */
+divas_status divas_fuse_add_views_nerf_profiled(divas_ctx* ctx, const divas_tuple_view* views,
+                                                int32_t n_views, const divas_nerf_params* np,
+                                                const float* density, void* const* stage_events,
+                                                void* stream);
+
+/* The density floor of the NeRF occupancy (the empty-voxel skip of
+ * Algorithm "Thick-Structure Segmentation via Depth-Weighted Voxel
+ * Aggregation"): occ[i] = density[i] >= rho_thresh (1 / 0; NaN gives 0),
+ * the uint8 prior divas_fuse_set_occupancy takes.  density: device n FP32,
+ * 16-byte aligned; occ: device n uint8, 4-byte aligned; DIVAS_E_INVALID
+ * otherwise.  Asynchronous on stream. */
+divas_status divas_density_floor(const float* density, int64_t n, float rho_thresh, uint8_t* occ,
+                                 void* stream);
+
+/*
  * Depth-weighted mask refinement (Sec. 3.4 "Depth-weighting: bounded
  * normalization (NeRF) vs. band-pass (2DGS)"), a per-view pre-pass whose
  * output is folded like any FP32 mask (add_views, add_views_tuple, update):

@@ -15,9 +15,11 @@ from ._lib import (  # noqa: F401
 )
 from .fusion import (  # noqa: F401
     FusionParams,
+    NerfParams,
     PreparedViews,
     TupleParams,
     VoxelFusion,
+    density_floor,
     seg_bits_to_bool,
 )
 from .autograd import DivasFuseFunction, fuse  # noqa: F401,E402

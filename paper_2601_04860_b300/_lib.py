@@ -22,6 +22,8 @@ KEEP_ZEROS = 1
 MAX_PROMPTS = 15
 WEIGHT_NERF_MINMAX = 1
 WEIGHT_GS_BAND = 2
+NERF_LLFF = 0
+NERF_MIP360 = 1
 
 
 class DivasParams(ctypes.Structure):
@@ -57,6 +59,12 @@ class DivasTupleParams(ctypes.Structure):
     _fields_ = [(n, ctypes.c_float) for n in
                 ("beta", "gamma_st", "tau_thin", "rho_cover", "rho_occ", "n_abs", "dist_gate",
                  "behind_margin", "k_dg", "rho_thin")]
+
+
+class DivasNerfParams(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_float) for n in
+                ("gamma", "beta", "b_max", "lambda_range", "rho_thin", "rho_cover", "tau_thin",
+                 "m_thin", "k_dg")] + [("reserved", ctypes.c_int32)]
 
 
 class DivasWeightView(ctypes.Structure):
@@ -123,6 +131,14 @@ _SIGS = {
     "divas_default_occupancy_params": (DivasOccupancyParams, []),
     "divas_default_surfel_params": (DivasSurfelParams, []),
     "divas_overlay": (ctypes.c_int, [_P, ctypes.POINTER(DivasCamera), _P, _P, _P]),
+    "divas_default_nerf_params": (DivasNerfParams, [ctypes.c_int32]),
+    "divas_fuse_add_views_nerf": (ctypes.c_int, [_P, ctypes.POINTER(DivasTupleView), ctypes.c_int32,
+                                                 ctypes.POINTER(DivasNerfParams), _P, _P]),
+    "divas_fuse_add_views_nerf_profiled": (ctypes.c_int, [_P, ctypes.POINTER(DivasTupleView),
+                                                          ctypes.c_int32,
+                                                          ctypes.POINTER(DivasNerfParams), _P, _P,
+                                                          _P]),
+    "divas_density_floor": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_float, _P, _P]),
     "divas_surfel_labels": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int64,
                                            ctypes.POINTER(DivasCamera), ctypes.POINTER(_P),
                                            ctypes.c_int32, ctypes.c_int32,

@@ -2002,6 +2002,8 @@ void divas_batch_destroy(divas_batch* b) {
 #include "weighting.cuh"
 #include "occupancy.cuh"
 #include "surfels.cuh"
+// the NeRF variant of the depth-tuple mode
+#include "nerf_mode.cuh"
 
 // ===========================================================================
 // Allocation-free one-shot fusion (no counterpart in the paper)

@@ -184,6 +184,52 @@ __device__ __forceinline__ bool box_may_vote(const TViewC& T, int i0, int i1, in
 
 constexpr int kThinGroup = 4;  // footprint pixels whose loads are in flight together
 
+// The pixel-coordinate box of a voxel's 8 corners, each the centre's camera
+// rows plus or minus the three axis offsets (plain grids: lattice steps of
+// the folded pixel rows and of the depth; contracted grids: the rotation's
+// columns times h_v / 2); false when a corner is not in front of z_near.
+template <bool kContracted>
+__device__ __forceinline__ bool corner_box(const TViewC& T, float hv, float z_near, float pzh,
+                                           float pzl, float r0, float r1, float& umin, float& umax,
+                                           float& vmin, float& vmax) {
+    const ViewC& V = T.base;
+    umin = FLT_MAX; umax = -FLT_MAX; vmin = FLT_MAX; vmax = -FLT_MAX;
+    bool corners = true;
+    const float pz = kContracted ? pzh : __fadd_rn(pzh, pzl);
+    const float sc = kContracted ? __fmul_rn(0.5f, hv) : 1.f;
+    float d0[3], d1[3], d2[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        d0[q] = __fmul_rn(T.cd[q], sc);
+        d1[q] = __fmul_rn(T.cd[3 + q], sc);
+        d2[q] = __fmul_rn(T.cd[6 + q], sc);
+    }
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        float c0 = r0, c1 = r1, c2 = pz;
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            const bool up = (c >> q) & 1;
+            c0 = up ? __fadd_rn(c0, d0[q]) : __fsub_rn(c0, d0[q]);
+            c1 = up ? __fadd_rn(c1, d1[q]) : __fsub_rn(c1, d1[q]);
+            c2 = up ? __fadd_rn(c2, d2[q]) : __fsub_rn(c2, d2[q]);
+        }
+        corners = corners && c2 > z_near && c2 <= FLT_MAX;
+        const float inv = rcp_nr(c2 > z_near && c2 <= FLT_MAX ? c2 : 1.f);
+        float cu, cv;
+        if (kContracted) {
+            cu = __fmaf_rn(V.K[0], __fmul_rn(c0, inv), V.K[2]);
+            cv = __fmaf_rn(V.K[1], __fmul_rn(c1, inv), V.K[3]);
+        } else {
+            cu = __fmul_rn(c0, inv);
+            cv = __fmul_rn(c1, inv);
+        }
+        umin = fminf(umin, cu); umax = fmaxf(umax, cu);
+        vmin = fminf(vmin, cv); vmax = fmaxf(vmax, cv);
+    }
+    return corners;
+}
+
 // Whether view T can add a vote to the voxel (a thick or a thin candidate):
 // the centre pixel's d_min, d_med and mask decide (most voxels are behind the
 // visible surface and stop there); a thick candidate also needs a finite
@@ -261,45 +307,9 @@ __device__ __forceinline__ void tuple_view(const TViewC& T, const VoxelGeom& vg,
         thick_cand = dmax > 0.f && dmax <= FLT_MAX;
     }
     if (!thick_cand && !thin_cand) return;
-    // footprint: the pixel box of the 8 corners, each the centre's
-    // camera rows plus or minus the three axis offsets
-    float umin = FLT_MAX, umax = -FLT_MAX, vmin = FLT_MAX, vmax = -FLT_MAX;
-    bool corners = true;
-    {
-        const float pz = kContracted ? pzh : __fadd_rn(pzh, pzl);
-        const float sc = kContracted ? __fmul_rn(0.5f, hv) : 1.f;
-        float d0[3], d1[3], d2[3];
-#pragma unroll
-        for (int q = 0; q < 3; ++q) {
-            d0[q] = __fmul_rn(T.cd[q], sc);
-            d1[q] = __fmul_rn(T.cd[3 + q], sc);
-            d2[q] = __fmul_rn(T.cd[6 + q], sc);
-        }
-#pragma unroll
-        for (int c = 0; c < 8; ++c) {
-            float c0 = r0, c1 = r1, c2 = pz;
-#pragma unroll
-            for (int q = 0; q < 3; ++q) {
-                const bool up = (c >> q) & 1;
-                c0 = up ? __fadd_rn(c0, d0[q]) : __fsub_rn(c0, d0[q]);
-                c1 = up ? __fadd_rn(c1, d1[q]) : __fsub_rn(c1, d1[q]);
-                c2 = up ? __fadd_rn(c2, d2[q]) : __fsub_rn(c2, d2[q]);
-            }
-            corners = corners && c2 > F.z_near && c2 <= FLT_MAX;
-            const float inv = rcp_nr(c2 > F.z_near && c2 <= FLT_MAX ? c2 : 1.f);
-            float cu, cv;
-            if (kContracted) {
-                cu = __fmaf_rn(V.K[0], __fmul_rn(c0, inv), V.K[2]);
-                cv = __fmaf_rn(V.K[1], __fmul_rn(c1, inv), V.K[3]);
-            } else {
-                cu = __fmul_rn(c0, inv);
-                cv = __fmul_rn(c1, inv);
-            }
-            umin = fminf(umin, cu); umax = fmaxf(umax, cu);
-            vmin = fminf(vmin, cv); vmax = fmaxf(vmax, cv);
-        }
-    }
-    if (!corners) return;
+    // footprint: the pixel box of the 8 corners
+    float umin, umax, vmin, vmax;
+    if (!corner_box<kContracted>(T, hv, F.z_near, pzh, pzl, r0, r1, umin, umax, vmin, vmax)) return;
     const float Wf = (float)V.W, Hf = (float)V.H;
     // pixel box, clamped to the image before the integer conversions
     const int i0 = (int)fminf(fmaxf(floorf(umin), 0.f), Wf);
@@ -876,6 +886,39 @@ static size_t sat_bytes_of(int32_t W, int32_t H) {
     return (b + 255) / 256 * 256;
 }
 
+// The mask-key tile maxima of every view (k_mask_tiles, one launch), both
+// maps of view k at cur + the sum of the earlier views' tile_bytes_of; cur
+// is advanced past them.
+static divas_status launch_tile_maps(divas_ctx* c, const divas_tuple_view* views, int32_t n_views,
+                                     unsigned char*& cur, TileJobs& tj, cudaStream_t s) {
+    memset(&tj, 0, sizeof(tj));
+    tj.n = n_views;
+    int32_t max_tw = 0, max_th = 0;
+    for (int32_t k = 0; k < n_views; ++k) {
+        const divas_tuple_view& v = views[k];
+        TileJob& jb = tj.j[k];
+        jb.mask = v.mask;
+        jb.W = v.cam.W;
+        jb.H = v.cam.H;
+        jb.mask_type = v.mask_type;
+        jb.tiles_w = (v.cam.W + kMaskTile - 1) / kMaskTile;
+        const size_t row_bytes = (size_t)v.cam.W * (v.mask_type == kMaskF16 ? 2 : 4);
+        jb.vec = (reinterpret_cast<uintptr_t>(v.mask) % 16 == 0 && row_bytes % 16 == 0) ? 1 : 0;
+        const int32_t th = (v.cam.H + kMaskTile - 1) / kMaskTile;
+        const size_t half = tile_bytes_of(v.cam.W, v.cam.H) / 2;
+        jb.out = reinterpret_cast<float*>(cur);
+        jb.dil = reinterpret_cast<float*>(cur + half);
+        max_tw = std::max(max_tw, jb.tiles_w);
+        max_th = std::max(max_th, th);
+        cur += 2 * half;
+    }
+    k_mask_tiles<<<dim3((max_tw + kTileBlock - 1) / kTileBlock, (max_th + kTileBlock - 1) / kTileBlock,
+                        n_views),
+                   kTileBlock * kTileBlock, 0, s>>>(tj);
+    DIVAS_LAUNCHED(c, "k_mask_tiles");
+    return DIVAS_OK;
+}
+
 // ---------------------------------------------------------------------------
 // C ABI of the tuple mode
 // ---------------------------------------------------------------------------
@@ -965,31 +1008,8 @@ divas_status divas_fuse_add_views_tuple_profiled(divas_ctx* c, const divas_tuple
     cur += heavy_bytes;
     // the mask-key tile maxima of every view, in one launch
     TileJobs tj;
-    memset(&tj, 0, sizeof(tj));
-    tj.n = n_views;
-    int32_t max_tw = 0, max_th = 0;
-    for (int32_t k = 0; k < n_views; ++k) {
-        const divas_tuple_view& v = views[k];
-        TileJob& jb = tj.j[k];
-        jb.mask = v.mask;
-        jb.W = v.cam.W;
-        jb.H = v.cam.H;
-        jb.mask_type = v.mask_type;
-        jb.tiles_w = (v.cam.W + kMaskTile - 1) / kMaskTile;
-        const size_t row_bytes = (size_t)v.cam.W * (v.mask_type == kMaskF16 ? 2 : 4);
-        jb.vec = (reinterpret_cast<uintptr_t>(v.mask) % 16 == 0 && row_bytes % 16 == 0) ? 1 : 0;
-        const int32_t th = (v.cam.H + kMaskTile - 1) / kMaskTile;
-        const size_t half = tile_bytes_of(v.cam.W, v.cam.H) / 2;
-        jb.out = reinterpret_cast<float*>(cur);
-        jb.dil = reinterpret_cast<float*>(cur + half);
-        max_tw = std::max(max_tw, jb.tiles_w);
-        max_th = std::max(max_th, th);
-        cur += 2 * half;
-    }
-    k_mask_tiles<<<dim3((max_tw + kTileBlock - 1) / kTileBlock, (max_th + kTileBlock - 1) / kTileBlock,
-                        n_views),
-                   kTileBlock * kTileBlock, 0, s>>>(tj);
-    DIVAS_LAUNCHED(c, "k_mask_tiles");
+    st = launch_tile_maps(c, views, n_views, cur, tj, s);
+    if (st != DIVAS_OK) return st;
     // integral images of the views that need them, in two launches
     SatJobs jobs;
     memset(&jobs, 0, sizeof(jobs));

@@ -121,6 +121,48 @@ class TupleParams:
         return L.DivasTupleParams(*[float(getattr(self, f)) for f in self.__dataclass_fields__])
 
 
+@dataclass
+class NerfParams:
+    """NeRF-variant constants (``divas_nerf_params``; Table
+    kernel_hyperparams, LLFF column by default, ``mip360()`` for the other;
+    m_thin = 0.1, k_dg = 0)."""
+    gamma: float = 4.0
+    beta: float = 0.2
+    b_max: float = 10.0
+    lambda_range: float = 0.05
+    rho_thin: float = 50.0
+    rho_cover: float = 0.2
+    tau_thin: float = 0.6
+    m_thin: float = 0.1
+    k_dg: float = 0.0
+
+    @staticmethod
+    def mip360() -> "NerfParams":
+        return NerfParams(gamma=0.5, b_max=1.0, lambda_range=5.0, rho_thin=30.0, rho_cover=0.3)
+
+    def c(self) -> L.DivasNerfParams:
+        return L.DivasNerfParams(*[float(getattr(self, f)) for f in self.__dataclass_fields__], 0)
+
+
+def density_floor(density: torch.Tensor, rho_thresh: float, out: torch.Tensor | None = None,
+                  stream=None) -> torch.Tensor:
+    """The occupancy prior of a NeRF density grid (``divas_density_floor``):
+    uint8 ``density >= rho_thresh`` of a contiguous float32 tensor (16-byte
+    aligned; ``out`` 4-byte aligned)."""
+    if density.dtype != torch.float32 or not density.is_contiguous() or not density.is_cuda:
+        raise ValueError("density must be a contiguous float32 CUDA tensor")
+    if out is None:
+        out = torch.empty(density.shape, dtype=torch.uint8, device=density.device)
+    elif out.dtype != torch.uint8 or out.numel() != density.numel() or not out.is_contiguous():
+        raise ValueError("out must be a contiguous uint8 tensor of the density's size")
+    lib = L.load()
+    st = lib.divas_density_floor(_ptr(density), density.numel(), float(rho_thresh), _ptr(out),
+                                 _stream(stream))
+    if st != 0:
+        raise L.DivasError(f"divas_density_floor failed ({st}): check alignment and arguments")
+    return out
+
+
 def tuple_views_c(cams, d_min, d_med, d_max, n_samp, masks, d_cams, mask_type: int):
     """Marshal tuple views (device tensors: float32 depths, uint16-compatible
     n_samp as torch.int16 / uint16 storage, masks as for ``view_c``)."""
@@ -269,6 +311,32 @@ class VoxelFusion:
                                       for e in stage_events])
         self._check(self.lib.divas_fuse_add_views_tuple_profiled(
             self._h, arr, len(cams), ctypes.byref(tp), evs, _stream(stream)))
+
+    def add_views_nerf(self, cams, d_min, d_exp, d_max, n_samp, masks, mask_type: int,
+                       nparams: "NerfParams | None" = None, density: torch.Tensor | None = None,
+                       stage_events=None, stream=None):
+        """Fold NeRF depth-tuple views (``divas_fuse_add_views_nerf``), up to
+        32; ``density`` None (density 1 everywhere) or the g^3 float32 grid.
+        ``stage_events``: optional four ``torch.cuda.Event`` (before the
+        mask-tile maps / after them / after the scan / after the heavy pass)."""
+        if len(cams) > L.MAX_VIEWS_PER_CALL:
+            raise ValueError("add_views_nerf() takes up to 32 views")
+        if density is not None and (density.dtype != torch.float32 or not density.is_contiguous()
+                                    or density.numel() != self.n_cells):
+            raise ValueError("density must be a contiguous float32 tensor of g^3 cells")
+        arr = tuple_views_c(cams, d_min, d_exp, d_max, n_samp, masks, [0.0] * len(cams), mask_type)
+        npr = (nparams or NerfParams()).c()
+        if stage_events is None:
+            self._check(self.lib.divas_fuse_add_views_nerf(self._h, arr, len(cams),
+                                                           ctypes.byref(npr), _ptr(density),
+                                                           _stream(stream)))
+            return
+        if len(stage_events) != 4:
+            raise ValueError("stage_events takes four events")
+        evs = (ctypes.c_void_p * 4)(*[(e.cuda_event if e is not None else None)
+                                      for e in stage_events])
+        self._check(self.lib.divas_fuse_add_views_nerf_profiled(
+            self._h, arr, len(cams), ctypes.byref(npr), _ptr(density), evs, _stream(stream)))
 
     def depth_weight(self, depths, masks, mask_type: int, mode: str = "band", prompts=None,
                      out=None, stats: bool = False, stream=None):
