@@ -686,6 +686,148 @@ def profile_tuple_steps(args):
     return 0
 
 
+def _nerf_step(dev, preset: str = "llff"):
+    """The NeRF variant on the 256^3 forward-facing scene (8 views 1008x756
+    with d_min / d_exp / d_max / n_samp rasters and a 256^3 FP32 density
+    grid; Table kernel_hyperparams, LLFF or Mip-NeRF 360 column): the context
+    and one step = density floor (rho >= 10) + occupancy gate + the NeRF views
+    (mask-tile maps, scan, heavy pass) + finalize + labels."""
+    import torch
+
+    import synth
+    from paper_2601_04860_b300 import FusionParams, NerfParams, VoxelFusion, density_floor
+    wl = synth.config2()
+    nw, rho = synth.with_nerf_tuple(wl), synth.nerf_density(wl)
+    T = nw.tuple
+    ras = {k: [torch.from_numpy(a).to(dev) for a in T[k]] for k in ("d_min", "d_exp", "d_max")}
+    ns = [torch.from_numpy(a.view(np.int16)).to(dev) for a in T["n_samp"]]
+    mask = [torch.from_numpy(m.view(np.float16)).to(dev) for m in nw.mask]
+    pts = torch.from_numpy(np.ascontiguousarray(nw.points)).to(dev)
+    drho = torch.from_numpy(rho).to(dev)
+    occ = torch.empty(drho.numel(), dtype=torch.uint8, device=dev)
+    fu = VoxelFusion(nw.grid, occ=density_floor(drho, 10.0), params=FusionParams())
+    score = torch.empty(fu.n_cells, dtype=torch.float32, device=dev)
+    labels = torch.empty(len(nw.points), dtype=torch.uint8, device=dev)
+    npar = NerfParams() if preset == "llff" else NerfParams.mip360()
+
+    def step(ev=None):
+        density_floor(drho, 10.0, out=occ)
+        fu.set_occupancy(occ=occ)
+        fu.add_views_nerf(nw.cams, ras["d_min"], ras["d_exp"], ras["d_max"], ns, mask,
+                          nw.mask_type, nparams=npar, density=drho, stage_events=ev)
+        fu.finalize(score=score)
+        fu.label_points(pts, out=labels)
+    return fu, step, nw, rho, npar
+
+
+def _nerf_scan_bytes(nw, n_active: int) -> int:
+    """Algorithmic bytes of one NeRF scan launch (first views of a context):
+    the active list (4 B per voxel), each voxel's density (4 B) and its
+    written accumulators (12 B), plus each view's rasters read once (d_min,
+    d_exp, d_max FP32, n_samp 2 B, the mask)."""
+    mb = 2 if nw.mask_type == 1 else 4
+    return 20 * n_active + sum(c.W * c.H * (14 + mb) for c in nw.cams)
+
+
+def measure_nerf(dev, steps: int):
+    """The NeRF-variant step replayed from a CUDA graph (events around it
+    only), L2 flushed between steps, with the LLFF and the Mip-NeRF 360
+    constants; stage times from a second graph whose NeRF call records events
+    between its launches; the scan's roofline; the oracle on the host."""
+    import torch
+    out = {"workload": "forward-dense-256-nerf (config-2 scene with a NeRF depth tuple per view: "
+                       "d_min / d_exp / d_max FP32, n_samp uint16; 256^3 FP32 density; 8 views "
+                       "1008x756)",
+           "what": "graph replay of density_floor + set_occupancy + add_views_nerf (8 views) + "
+                   "finalize + label_points; L2 flushed per step"}
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    peak, peak_kind = peaks()
+    for preset in ("llff", "mip360"):
+        fu, step, nw, rho, npar = _nerf_step(dev, preset)
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            for _ in range(3):
+                step()
+        torch.cuda.current_stream().wait_stream(side)
+        torch.cuda.synchronize()
+        ev = [torch.cuda.Event(enable_timing=True, external=True) for _ in range(2)]
+        sev = [torch.cuda.Event(enable_timing=True, external=True) for _ in range(4)]
+        for e in sev:
+            e.record()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            ev[0].record()
+            step()
+            ev[1].record()
+        gs = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(gs):
+            step(sev)
+        ms, st = [], {"maps": [], "scan": [], "heavy": []}
+        for k in range(3 + steps):
+            flush.zero_()
+            g.replay()
+            torch.cuda.synchronize()
+            flush.zero_()
+            gs.replay()
+            torch.cuda.synchronize()
+            if k >= 3:
+                ms.append(ev[0].elapsed_time(ev[1]))
+                st["maps"].append(sev[0].elapsed_time(sev[1]))
+                st["scan"].append(sev[1].elapsed_time(sev[2]))
+                st["heavy"].append(sev[2].elapsed_time(sev[3]))
+        n, S, na = fu.n_cells, nw.n_views, fu.n_active
+        m = float(np.mean(ms))
+        stm = {k: float(np.mean(v)) for k, v in st.items()}
+        scan_bytes = _nerf_scan_bytes(nw, na)
+        ach = scan_bytes / (stm["scan"] * 1e-3) / 1e9
+        out[preset] = {"ms_per_step": m, "updates_per_s": n * S / (m * 1e-3),
+                       "active_updates_per_s": na * S / (m * 1e-3), "stage_ms": stm,
+                       "roofline": {"bound": "hbm", "kernel": "k_nerf_scan", "achieved": ach,
+                                    "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                                    "traffic": None, "peak_kind": peak_kind,
+                                    "algorithmic_bytes_per_launch": scan_bytes,
+                                    "ms_per_launch": stm["scan"]}}
+        fu.close()
+    out["cpu_baseline"] = nerf_cpu_baseline(nw, rho)
+    return out
+
+
+def nerf_cpu_baseline(nw, rho):
+    """The oracle's NeRF-variant fusion (LLFF constants) on the host cores over
+    every active voxel x 8 views of the 256^3 scene, as nominal voxel-view
+    updates/s (g^3 x views / time)."""
+    import oracle
+    cores = oracle.set_threads(0)
+    lin = nw.active_linear()
+    t0 = time.perf_counter()
+    oracle.fuse_nerf(nw.grid, lin, nw.cams, nw.tuple, nw.mask, nw.mask_type,
+                     params=oracle.Params().f32(), nparams=oracle.NerfParams().f32(),
+                     rho=rho[lin].astype(np.float64))
+    dt = time.perf_counter() - t0
+    g = nw.grid.g
+    return {"value": g ** 3 * nw.n_views / dt, "unit": UNIT, "cores": cores,
+            "kind": "oracle", "seconds": dt,
+            "sample": f"all {len(lin)} active voxels x {nw.n_views} views (fusion only, no "
+                      "finalize or labels)"}
+
+
+def profile_nerf_steps(args):
+    """Profiling target of the NeRF-variant step: N eager steps (per step:
+    k_density_floor, k_tile_count, k_tile_emit, k_mask_tiles, k_nerf_scan,
+    k_nerf_heavy, k_finalize, k_label on the 256^3 scene) and nothing else."""
+    import torch
+    fu, step, _, _, _ = _nerf_step(torch.device("cuda"))
+    for _ in range(args.profile_nerf_steps):
+        step()
+    torch.cuda.synchronize()
+    fu.sync()
+    print(json.dumps({"profile_nerf_steps": args.profile_nerf_steps,
+                      "workload": "forward-dense-256-nerf", "active_voxels": fu.n_active}))
+    fu.close()
+    return 0
+
+
 def _weight_step(dev, mode: str):
     """Depth-weighted masks on the 256^3 forward-facing scene (8 views
     1008x756, FP16 masks, 3 positive prompts per view on the target): the
@@ -1209,6 +1351,8 @@ def run(args):
         return profile_tuple_steps(args)
     if args.profile_weight_steps:
         return profile_weight_steps(args)
+    if args.profile_nerf_steps:
+        return profile_nerf_steps(args)
     if args.profile_occupancy_steps:
         return profile_occupancy_steps(args)
     if world > 1:
@@ -1228,6 +1372,9 @@ def run(args):
     if not args.quick and not args.no_tuple and args.workload == "forward-dense-256":
         import torch
         res["tuple"] = measure_tuple(torch.device("cuda", local_rank), max(5, args.steps // 2))
+    if not args.quick and not args.no_nerf and args.workload == "forward-dense-256":
+        import torch
+        res["nerf"] = measure_nerf(torch.device("cuda", local_rank), max(5, args.steps // 2))
     if not args.quick and not args.no_weighting and args.workload == "forward-dense-256":
         import torch
         res["weighting"] = measure_weighting(torch.device("cuda", local_rank),
@@ -1303,6 +1450,7 @@ def main(argv=None):
     ap.add_argument("--no-adjoint", action="store_true", help="skip the forward+backward leg")
     ap.add_argument("--no-sessions", action="store_true", help="skip the batched/served leg")
     ap.add_argument("--no-tuple", action="store_true", help="skip the depth-tuple-mode leg")
+    ap.add_argument("--no-nerf", action="store_true", help="skip the NeRF-variant leg")
     ap.add_argument("--no-weighting", action="store_true",
                     help="skip the depth-weighted-mask leg")
     ap.add_argument("--no-occupancy", action="store_true",
@@ -1319,6 +1467,8 @@ def main(argv=None):
                     help="profiling target: run N eager one-call steps and exit")
     ap.add_argument("--profile-tuple-steps", type=int, default=0,
                     help="profiling target: run N eager depth-tuple steps and exit")
+    ap.add_argument("--profile-nerf-steps", type=int, default=0,
+                    help="profiling target: run N eager NeRF-variant steps and exit")
     ap.add_argument("--profile-weight-steps", type=int, default=0,
                     help="profiling target: run N eager depth-weighted steps and exit")
     ap.add_argument("--profile-occupancy-steps", type=int, default=0,
