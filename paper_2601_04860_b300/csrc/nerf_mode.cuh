@@ -233,7 +233,7 @@ __device__ __forceinline__ float voxel_density(const float* __restrict__ rho, ui
 // their thick votes in view order here; the others go to the heavy list
 // (entry: voxel, views with a thick vote | thin candidates << 16).
 template <bool kC, int kN>
-__global__ void __launch_bounds__(kThreads) k_nerf_scan(
+__global__ void __launch_bounds__(kThreads, kC ? 4 : 6) k_nerf_scan(
     const uint32_t* __restrict__ active, const int32_t* __restrict__ d_n, GridC G, FuseC F,
     const __grid_constant__ TViewBatch TB, NerfC N, const float* __restrict__ density,
     int32_t accumulate, float* __restrict__ W, float* __restrict__ Z, uint32_t* __restrict__ bits,
