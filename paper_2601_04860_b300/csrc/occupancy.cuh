@@ -47,7 +47,7 @@ __global__ void __launch_bounds__(kOccThreads) k_gauss_dist(const float* __restr
     }
 }
 
-// the frame's selected values: c[0..2], s_bar (round 1), r_fg (round 2)
+// the frame's selected values: c[0..2] and s_bar (first selection), r_fg (second)
 __global__ void k_gauss_frame(const SelState* __restrict__ st1, const SelState* __restrict__ st2,
                               double* __restrict__ out) {
     const int t = threadIdx.x;

@@ -44,7 +44,7 @@ def test_batch_matches_sessions_alone(sched):
     fus = [VoxelFusion(wl.grid, occ=d["occ"], coords=d["coords"], params=H.to_params(P0))
            for wl, d in sess]
     b = Batch(max_sessions=16, max_views=256)
-    # two rounds: views split in two batches (accumulation across batches)
+    # two passes: views split in two batches (accumulation across batches)
     for lo, hi in ((0, 1), (1, None)):
         for (wl, d), fu in zip(sess, fus):
             h = max(1, wl.n_views // 2)
@@ -70,7 +70,7 @@ def test_batch_matches_sessions_alone(sched):
         assert np.array_equal(st["W"].cpu().numpy(), r["W"])
         assert np.array_equal(st["Z"].cpu().numpy(), r["Z"])
         assert np.array_equal(st["bits"].cpu().numpy(), r["bits"])
-    # the last finalize covered every session with views in round 2
+    # the last finalize covered every session with views in the second pass
     for f, sc, lab in zip(queued, scores, labs):
         i = fus.index(f)
         assert np.array_equal(sc.cpu().numpy(), ref[i]["score"])
