@@ -475,7 +475,7 @@ __global__ void __launch_bounds__(kThreads) k_finalize(
 // gets the zeros of its unoccupied cells.  Per voxel the arithmetic is that of
 // k_fuse followed by k_finalize.
 // ---------------------------------------------------------------------------
-template <bool kAccumulate, bool kContracted, int kChunks>
+template <bool kAccumulate, bool kContracted, int kChunks, bool kF16Full = false>
 __global__ void __launch_bounds__(kThreads, kContracted ? 4 : 6) k_fuse_fin(
     const uint32_t* __restrict__ active, const int32_t* __restrict__ d_n, GridC G, FuseC F,
     const __grid_constant__ ViewBatch VB, float* __restrict__ W, float* __restrict__ Z,
@@ -508,7 +508,7 @@ __global__ void __launch_bounds__(kThreads, kContracted ? 4 : 6) k_fuse_fin(
                 z = Z[a];
                 b = bits[a];
             }
-            if (vg.ok) fold_views<kContracted, kChunks>(VB, vg, F, w, z, b);
+            if (vg.ok) fold_views<kContracted, kChunks, kF16Full>(VB, vg, F, w, z, b);
             W[a] = w;
             Z[a] = z;
             bits[a] = b;
@@ -942,7 +942,9 @@ float logit_threshold(float tau) {
     return (float)log((double)tau / (1.0 - (double)tau));
 }
 
-// launch k_fuse_fin with the chunk count as a compile-time constant
+// launch k_fuse_fin with the chunk count as a compile-time constant; plain
+// grids whose views all carry binary16 masks and fill their chunks exactly take
+// the kF16Full instance
 template <bool kAccumulate, bool kContracted, int kChunks = 1>
 cudaError_t launch_fuse_fin_chunks(int chunks, int blocks, cudaStream_t s, const divas_ctx* c,
                                    const ViewBatch& vb, float* score_out, bool clear_bits,
@@ -952,10 +954,20 @@ cudaError_t launch_fuse_fin_chunks(int chunks, int blocks, cudaStream_t s, const
             return launch_fuse_fin_chunks<kAccumulate, kContracted, kChunks + 1>(
                 chunks, blocks, s, c, vb, score_out, clear_bits, seg_out, clear_out, zero);
     }
-    k_fuse_fin<kAccumulate, kContracted, kChunks><<<blocks, kThreads, 0, s>>>(
-        c->active, c->d_n, c->G, c->F, vb, c->W, c->Z, c->bits, c->grid.kind == 0 ? 1 : 0,
-        score_out, c->seg_bits, clear_bits ? 1 : 0, seg_out, clear_out ? 1 : 0, c->occ_bits,
-        c->n_words, c->n_cells, zero ? 1 : 0);
+    bool f16_full = !kContracted && vb.n == kChunks * kViewChunk;
+    for (int32_t i = 0; i < vb.n && f16_full; ++i) f16_full = vb.v[i].mask_type == kMaskF16;
+#define DIVAS_FUSE_FIN(F16)                                                                        \
+    k_fuse_fin<kAccumulate, kContracted, kChunks, F16><<<blocks, kThreads, 0, s>>>(                \
+        c->active, c->d_n, c->G, c->F, vb, c->W, c->Z, c->bits, c->grid.kind == 0 ? 1 : 0,         \
+        score_out, c->seg_bits, clear_bits ? 1 : 0, seg_out, clear_out ? 1 : 0, c->occ_bits,     \
+        c->n_words, c->n_cells, zero ? 1 : 0)
+    if constexpr (!kContracted) {
+        if (f16_full) DIVAS_FUSE_FIN(true);
+        else DIVAS_FUSE_FIN(false);
+    } else {
+        DIVAS_FUSE_FIN(false);
+    }
+#undef DIVAS_FUSE_FIN
     return cudaGetLastError();
 }
 

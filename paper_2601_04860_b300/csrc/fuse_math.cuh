@@ -316,10 +316,17 @@ __device__ __forceinline__ int32_t project(const ViewC& V, const VoxelGeom& vg, 
 // step 2: raster reads (depth and the mask's raw value, widened to float);
 // an invalid pixel reads pixel 0 (always in bounds) and is discarded later
 // ---------------------------------------------------------------------------
+// the view's mask type: kMT when it is fixed at compile time (kMT >= 0)
+template <int kMT>
+__device__ __forceinline__ int32_t mask_type_of(const ViewC& V) {
+    return kMT >= 0 ? kMT : V.mask_type;
+}
+
+template <int kMT = -1>
 __device__ __forceinline__ void load_raster(const ViewC& V, int32_t pix, float& D, float& raw) {
     const int32_t p = pix >= 0 ? pix : 0;
     D = __ldg(V.depth + p);
-    if (V.mask_type == kMaskF16)
+    if (mask_type_of<kMT>(V) == kMaskF16)
         raw = __half2float(
             __ushort_as_half(__ldg(reinterpret_cast<const unsigned short*>(V.mask) + p)));
     else
@@ -329,18 +336,20 @@ __device__ __forceinline__ void load_raster(const ViewC& V, int32_t pix, float& 
 // ---------------------------------------------------------------------------
 // step 3: gates (predicates) and, for an accepted vote, the weight
 // ---------------------------------------------------------------------------
+template <int kMT = -1>
 __device__ __forceinline__ bool gates(const ViewC& V, const VoxelGeom& vg, const FuseC& F,
                                       int32_t pix, float pzh, float pzl, float D, float raw,
                                       float& e) {
     e = __fadd_rn(__fsub_rn(pzh, D), pzl);
-    const float thr = V.mask_type == kMaskLogit ? F.logit_tau : F.tau_m;
+    const float thr = mask_type_of<kMT>(V) == kMaskLogit ? F.logit_tau : F.tau_m;
     // +inf, NaN or <= 0 depth: no surface; mask gate; depth gate
     return pix >= 0 && D > 0.f && D <= FLT_MAX && raw >= thr && fabsf(e) <= vg.Delta;
 }
 
+template <int kMT = -1>
 __device__ __forceinline__ void weight(const ViewC& V, const VoxelGeom& vg, const FuseC& F,
                                        float raw, float e, float& m, float& w) {
-    m = V.mask_type == kMaskLogit ? __frcp_rn(__fadd_rn(1.f, expf(-raw))) : raw;
+    m = mask_type_of<kMT>(V) == kMaskLogit ? __frcp_rn(__fadd_rn(1.f, expf(-raw))) : raw;
     const float r = __fmul_rn(e, vg.invDelta);
     w = expf(-__fmul_rn(F.alpha1, __fmul_rn(r, r)));
 }
@@ -369,9 +378,13 @@ __device__ __forceinline__ bool eval_vote(const ViewC& V, const VoxelGeom& vg, c
 // would turn each of them into a register-indexed constant load); the raster
 // loads of kViewChunk views are issued before any of them is consumed, and
 // only accepted votes (a few percent) branch into the weight computation.
-template <bool kContracted, int kChunks>
+// kF16Full: every view's mask is binary16 and VB.n == 4 kChunks, so the mask
+// type and the view count are compile-time constants (no per-view branches
+// on them); the arithmetic is the same.
+template <bool kContracted, int kChunks, bool kF16Full = false>
 __device__ __forceinline__ void fold_views(const ViewBatch& VB, const VoxelGeom& vg,
                                            const FuseC& F, float& W, float& Z, uint32_t& bits) {
+    constexpr int kMT = kF16Full ? kMaskF16 : -1;
 #pragma unroll
     for (int c = 0; c < kChunks; ++c) {
         int32_t pix[kViewChunk];
@@ -379,20 +392,21 @@ __device__ __forceinline__ void fold_views(const ViewBatch& VB, const VoxelGeom&
 #pragma unroll
         for (int q = 0; q < kViewChunk; ++q) {
             pix[q] = -1;
-            if (c * kViewChunk + q < VB.n)
+            if (kF16Full || c * kViewChunk + q < VB.n)
                 pix[q] = project<kContracted>(VB.v[c * kViewChunk + q], vg, F.z_near, pzh[q], pzl[q]);
         }
 #pragma unroll
         for (int q = 0; q < kViewChunk; ++q)
-            if (c * kViewChunk + q < VB.n) load_raster(VB.v[c * kViewChunk + q], pix[q], D[q], raw[q]);
+            if (kF16Full || c * kViewChunk + q < VB.n)
+                load_raster<kMT>(VB.v[c * kViewChunk + q], pix[q], D[q], raw[q]);
 #pragma unroll
         for (int q = 0; q < kViewChunk; ++q) {
-            if (c * kViewChunk + q >= VB.n) break;
+            if (!kF16Full && c * kViewChunk + q >= VB.n) break;
             const ViewC& V = VB.v[c * kViewChunk + q];
             float e;
-            if (gates(V, vg, F, pix[q], pzh[q], pzl[q], D[q], raw[q], e)) {
+            if (gates<kMT>(V, vg, F, pix[q], pzh[q], pzl[q], D[q], raw[q], e)) {
                 float m, w;
-                weight(V, vg, F, raw[q], e, m, w);
+                weight<kMT>(V, vg, F, raw[q], e, m, w);
                 W = __fmaf_rn(m, w, W);
                 Z = __fadd_rn(Z, w);
                 bits |= V.bit;
