@@ -34,10 +34,20 @@ def test_reciprocal_within_one_ulp():
     assert np.array_equal(b, ref)
 
 
-@pytest.mark.parametrize("which", ["dense", "sparse"])
+@pytest.mark.parametrize("which", ["dense", "dense4", "dense7", "dense12", "dense_f32", "sparse"])
 def test_step_equals_separate_calls(which):
-    if which == "dense":
-        wl = synth.config2(g=96, W=336, H=252, n_ell=60, n_points=20_000)
+    """Bitwise: the one-call step (its fusion kernel takes the binary16,
+    full-chunk instance for 4, 8 and 12 FP16 views, the generic one for 7
+    views or FP32 masks) against the separate calls' kernels."""
+    if which.startswith("dense"):
+        nv = {"dense4": 4, "dense7": 7}.get(which, 8)
+        wl = synth.config2(g=96, n_views=nv, W=336, H=252, n_ell=60, n_points=20_000)
+        if which == "dense12":  # the eight cameras and four of them again
+            wl.cams, wl.depth, wl.mask = (wl.cams + wl.cams[:4], wl.depth + wl.depth[:4],
+                                          wl.mask + wl.mask[:4])
+        if which == "dense_f32":
+            wl.mask = [m.view(np.float16).astype(np.float32) for m in wl.mask]
+            wl.mask_type = oracle.MASK_F32
     else:
         wl = synth.config3(g=96, n_views=8, W=324, H=210, n_ell=200, n_occ=None,
                            n_points=20_000)
