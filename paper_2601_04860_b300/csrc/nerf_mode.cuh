@@ -68,7 +68,7 @@ __device__ __forceinline__ float sub_pixel_offset(float f, float ph, float pl, f
 // vote (x = m, y = w), 2 = thin candidate (rho_v is the voxel's density; a
 // candidate also needs a mask key >= key_thr in the dilated tile map around
 // the centre when the view has one).
-template <bool kC>
+template <bool kC, int kMT = -1>
 __device__ __forceinline__ int nerf_centre(const TViewC& T, const VoxelGeom& vg, const FuseC& F,
                                            const NerfC& N, float rho_v, float& x, float& y,
                                            NerfCentre& c) {
@@ -77,10 +77,10 @@ __device__ __forceinline__ int nerf_centre(const TViewC& T, const VoxelGeom& vg,
     const int32_t pix = pixel_index(V, true, c.u, c.v);
     if (pix < 0) return 0;
     c.pix = pix;
-    const uint32_t mraw = mask_bits(V, pix);
+    const uint32_t mraw = mask_bits<kMT>(V, pix);
     bool half;
-    const float m = mask_from_bits(V, mraw, half);
-    const bool logit = V.mask_type == kMaskLogit;
+    const float m = mask_from_bits<kMT>(V, mraw, half);
+    const bool logit = mask_type_of<kMT>(V) == kMaskLogit;
     const float raw = logit ? __uint_as_float(mraw) : m;
     if (raw >= (logit ? F.logit_tau : F.tau_m)) {
         const float dmin = __ldg(V.depth + pix), dexp = __ldg(T.d_med + pix);
@@ -154,7 +154,7 @@ __device__ __forceinline__ int nerf_centre(const TViewC& T, const VoxelGeom& vg,
 // the peak mask key over it (kThinGroup pixels at a time, loads issued
 // together), stopping once n_valid can no longer reach rho_cover N.  Returns
 // t >= tau_thin (the vote t in x), else false.
-template <bool kC>
+template <bool kC, int kMT = -1>
 __device__ __forceinline__ bool nerf_thin(const TViewC& T, const VoxelGeom& vg, const FuseC& F,
                                           const NerfC& N, const NerfCentre& c, float& x) {
     const ViewC& V = T.base;
@@ -172,7 +172,7 @@ __device__ __forceinline__ bool nerf_thin(const TViewC& T, const VoxelGeom& vg, 
     if (!box_may_vote(T, i0, i1, j0, j1)) return false;  // m_max < tau_thin
     const float Af = (float)A;
     const float t2 = __fmul_rn(2.f, N.gamma);
-    const bool logit = V.mask_type == kMaskLogit;
+    const bool logit = mask_type_of<kMT>(V) == kMaskLogit;
     uint32_t n_valid = 0u;
     float mkey = -FLT_MAX;
     int xx = i0, yy = j0;
@@ -192,7 +192,7 @@ __device__ __forceinline__ bool nerf_thin(const TViewC& T, const VoxelGeom& vg, 
                 const int32_t q = yy * V.W + xx;
                 gexp[k] = __ldg(T.d_med + q);
                 gn[k] = __ldg(T.n_samp + q);
-                gm[k] = mask_bits(V, q);
+                gm[k] = mask_bits<kMT>(V, q);
             }
             if (++xx > i1) {
                 xx = i0;
@@ -203,7 +203,7 @@ __device__ __forceinline__ bool nerf_thin(const TViewC& T, const VoxelGeom& vg, 
         for (int k = 0; k < kThinGroup; ++k) {
             float key;
             bool hq;
-            if (V.mask_type == kMaskF16) {
+            if (mask_type_of<kMT>(V) == kMaskF16) {
                 key = __half2float(__ushort_as_half((unsigned short)gm[k]));
                 hq = key > 0.5f;
             } else {
@@ -232,7 +232,7 @@ __device__ __forceinline__ float voxel_density(const float* __restrict__ rho, ui
 // candidacy from the centre pixels.  Voxels without a thin candidate add
 // their thick votes in view order here; the others go to the heavy list
 // (entry: voxel, views with a thick vote | thin candidates << 16).
-template <bool kC, int kN>
+template <bool kC, int kN, int kMT = -1>
 __global__ void __launch_bounds__(kThreads, kC ? 4 : 6) k_nerf_scan(
     const uint32_t* __restrict__ active, const int32_t* __restrict__ d_n, GridC G, FuseC F,
     const __grid_constant__ TViewBatch TB, NerfC N, const float* __restrict__ density,
@@ -262,7 +262,7 @@ __global__ void __launch_bounds__(kThreads, kC ? 4 : 6) k_nerf_scan(
                     if (i >= TB.n) break;
                     float x = 0.f, y = 0.f;
                     NerfCentre c;
-                    const int kind = nerf_centre<kC>(TB.v[i], vg, F, N, rho_v, x, y, c);
+                    const int kind = nerf_centre<kC, kMT>(TB.v[i], vg, F, N, rho_v, x, y, c);
                     if (kind == 1) {
                         thick |= 1u << i;
                         Ws = __fmaf_rn(x, y, Ws);
@@ -298,7 +298,7 @@ __global__ void __launch_bounds__(kThreads, kC ? 4 : 6) k_nerf_scan(
 // Pass 2: a half-warp per listed voxel, lane i = view i: thick views
 // recomputed, thin candidates through the footprint loop; the half's first
 // lane adds the votes in view order (the scan's FMA and additions).
-template <bool kC>
+template <bool kC, int kMT = -1>
 __global__ void __launch_bounds__(kThreads) k_nerf_heavy(
     const uint32_t* __restrict__ active, const uint2* __restrict__ heavy,
     const int32_t* __restrict__ n_heavy, GridC G, FuseC F, const __grid_constant__ TViewBatch TB,
@@ -330,8 +330,8 @@ __global__ void __launch_bounds__(kThreads) k_nerf_heavy(
             NerfCentre c;
             // the scan's outcome for this view, recomputed (a thin candidate
             // passed the density test there)
-            kind = nerf_centre<kC>(T, vg, F, N, is_thin ? FLT_MAX : 0.f, x, y, c);
-            if (kind == 2) kind = nerf_thin<kC>(T, vg, F, N, c, x) ? 2 : 0;
+            kind = nerf_centre<kC, kMT>(T, vg, F, N, is_thin ? FLT_MAX : 0.f, x, y, c);
+            if (kind == 2) kind = nerf_thin<kC, kMT>(T, vg, F, N, c, x) ? 2 : 0;
         }
         float Ws = 0.f, Zs = 0.f;
         uint32_t b = 0u;
@@ -364,13 +364,14 @@ __global__ void __launch_bounds__(kThreads) k_nerf_heavy(
 
 }  // namespace
 
-template <bool kC>
+template <bool kC, int kMT>
 static divas_status launch_nerf_scan(int nv, int blocks, cudaStream_t s, divas_ctx* c,
                                      const TViewBatch& tb, const NerfC& N, const float* density,
                                      int32_t acc, uint2* heavy, int32_t* n_heavy) {
 #define DIVAS_NERF_SCAN(K)                                                                         \
-    k_nerf_scan<kC, K><<<blocks, kThreads, 0, s>>>(c->active, c->d_n, c->G, c->F, tb, N, density, \
-                                                  acc, c->W, c->Z, c->bits, heavy, n_heavy)
+    k_nerf_scan<kC, K, kMT><<<blocks, kThreads, 0, s>>>(c->active, c->d_n, c->G, c->F, tb, N,      \
+                                                       density, acc, c->W, c->Z, c->bits, heavy,  \
+                                                       n_heavy)
     if (nv <= 4) DIVAS_NERF_SCAN(4);
     else if (nv <= 8) DIVAS_NERF_SCAN(8);
     else DIVAS_NERF_SCAN(16);
@@ -504,20 +505,33 @@ divas_status divas_fuse_add_views_nerf_profiled(divas_ctx* c, const divas_tuple_
         const int blocks = grid_for(c->cap, c->sm_count);
         const int32_t acc = c->n_views + k0 > 0 ? 1 : 0;
         DIVAS_CUDA(c, cudaMemsetAsync(n_heavy, 0, sizeof(int32_t), s));
-        st = c->G.contracted
-                 ? launch_nerf_scan<true>(tb.n, blocks, s, c, tb, N, density, acc, heavy, n_heavy)
-                 : launch_nerf_scan<false>(tb.n, blocks, s, c, tb, N, density, acc, heavy, n_heavy);
+        const bool f16 = batch_all_f16(tb);
+        if (c->G.contracted)
+            st = f16 ? launch_nerf_scan<true, kMaskF16>(tb.n, blocks, s, c, tb, N, density, acc, heavy,
+                                                        n_heavy)
+                     : launch_nerf_scan<true, -1>(tb.n, blocks, s, c, tb, N, density, acc, heavy,
+                                                  n_heavy);
+        else
+            st = f16 ? launch_nerf_scan<false, kMaskF16>(tb.n, blocks, s, c, tb, N, density, acc, heavy,
+                                                         n_heavy)
+                     : launch_nerf_scan<false, -1>(tb.n, blocks, s, c, tb, N, density, acc, heavy,
+                                                   n_heavy);
         if (st != DIVAS_OK) return st;
         if (last) {
             st = record_stage(c, stage_events, 2, s);
             if (st != DIVAS_OK) return st;
         }
-        if (c->G.contracted)
-            k_nerf_heavy<true><<<blocks, kThreads, 0, s>>>(c->active, heavy, n_heavy, c->G, c->F, tb, N,
-                                                           c->W, c->Z, c->bits);
-        else
-            k_nerf_heavy<false><<<blocks, kThreads, 0, s>>>(c->active, heavy, n_heavy, c->G, c->F, tb, N,
-                                                            c->W, c->Z, c->bits);
+#define DIVAS_NERF_HEAVY(KC, MT)                                                                   \
+    k_nerf_heavy<KC, MT><<<blocks, kThreads, 0, s>>>(c->active, heavy, n_heavy, c->G, c->F, tb, N,   \
+                                                     c->W, c->Z, c->bits)
+        if (c->G.contracted) {
+            if (f16) DIVAS_NERF_HEAVY(true, kMaskF16);
+            else DIVAS_NERF_HEAVY(true, -1);
+        } else {
+            if (f16) DIVAS_NERF_HEAVY(false, kMaskF16);
+            else DIVAS_NERF_HEAVY(false, -1);
+        }
+#undef DIVAS_NERF_HEAVY
         DIVAS_LAUNCHED(c, "k_nerf_heavy");
     }
     c->n_views += n_views;

@@ -149,21 +149,23 @@ __device__ __forceinline__ bool layered_threshold(uint32_t A, unsigned long long
 }
 
 // mask bits at pixel q (binary16 or FP32 / logit bits), loaded ahead of use
+template <int kMT = -1>
 __device__ __forceinline__ uint32_t mask_bits(const ViewC& V, int32_t q) {
-    return V.mask_type == kMaskF16
+    return mask_type_of<kMT>(V) == kMaskF16
                ? (uint32_t)__ldg(reinterpret_cast<const unsigned short*>(V.mask) + q)
                : __ldg(reinterpret_cast<const uint32_t*>(V.mask) + q);
 }
 
 // probability and "mask positive" (m > 1/2; logit l > 0) of loaded mask bits
+template <int kMT = -1>
 __device__ __forceinline__ float mask_from_bits(const ViewC& V, uint32_t raw, bool& half) {
-    if (V.mask_type == kMaskF16) {
+    if (mask_type_of<kMT>(V) == kMaskF16) {
         const float m = __half2float(__ushort_as_half((unsigned short)raw));
         half = m > 0.5f;
         return m;
     }
     const float x = __uint_as_float(raw);
-    if (V.mask_type == kMaskLogit) {
+    if (mask_type_of<kMT>(V) == kMaskLogit) {
         half = x > 0.f;
         return __frcp_rn(__fadd_rn(1.f, expf(-x)));
     }
@@ -235,7 +237,7 @@ __device__ __forceinline__ bool corner_box(const TViewC& T, float hv, float z_ne
 // visible surface and stop there); a thick candidate also needs a finite
 // d_max, a thin-only candidate a mask key >= key_thr within one tile of its
 // centre's tile (when every footprint of the view stays there).
-template <bool kContracted>
+template <bool kContracted, int kMT = -1>
 __device__ __forceinline__ bool tuple_candidate(const TViewC& T, const VoxelGeom& vg, const FuseC& F,
                                                 const TupleC& TP) {
     const ViewC& V = T.base;
@@ -244,11 +246,12 @@ __device__ __forceinline__ bool tuple_candidate(const TViewC& T, const VoxelGeom
     const int32_t pix = pixel_index(V, true, u, v);
     if (pix < 0) return false;
     const float dmin = __ldg(V.depth + pix), dmed = __ldg(T.d_med + pix);
-    const uint32_t mraw = mask_bits(V, pix);
+    const uint32_t mraw = mask_bits<kMT>(V, pix);
     bool half;
-    const float m = mask_from_bits(V, mraw, half);
-    const float raw_gate = V.mask_type == kMaskLogit ? __uint_as_float(mraw) : m;
-    const bool pass = raw_gate >= (V.mask_type == kMaskLogit ? F.logit_tau : F.tau_m);
+    const float m = mask_from_bits<kMT>(V, mraw, half);
+    const int32_t mt = mask_type_of<kMT>(V);
+    const float raw_gate = mt == kMaskLogit ? __uint_as_float(mraw) : m;
+    const bool pass = raw_gate >= (mt == kMaskLogit ? F.logit_tau : F.tau_m);
     const bool trusted = dmin <= dmed;
     if (pass && trusted && dmin > 0.f && dmin <= FLT_MAX && dmed > 0.f && dmed <= FLT_MAX) {
         const float dmax = __ldg(T.d_max + pix);
@@ -272,7 +275,7 @@ __device__ __forceinline__ bool tuple_candidate(const TViewC& T, const VoxelGeom
 // a time with their loads issued together).  Adds the view's vote, if any.
 // The vote is returned, not added: kind 1 thick (x = m, y = w: W += m w,
 // Z += w), kind 2 thin (x = t: W += t, Z += 1), kind 0 none.
-template <bool kContracted>
+template <bool kContracted, int kMT = -1>
 __device__ __forceinline__ void tuple_view(const TViewC& T, const VoxelGeom& vg, const FuseC& F,
                                            const TupleC& TP, int& kind, float& x, float& y) {
     kind = 0;
@@ -285,11 +288,12 @@ __device__ __forceinline__ void tuple_view(const TViewC& T, const VoxelGeom& vg,
     if (pix < 0) return;
     // the centre pixel: d_min, d_med and the mask decide the candidates
     const float dmin = __ldg(V.depth + pix), dmed = __ldg(T.d_med + pix);
-    const uint32_t mraw = mask_bits(V, pix);
+    const uint32_t mraw = mask_bits<kMT>(V, pix);
     bool half;
-    const float m = mask_from_bits(V, mraw, half);
-    const float raw_gate = V.mask_type == kMaskLogit ? __uint_as_float(mraw) : m;
-    const bool pass = raw_gate >= (V.mask_type == kMaskLogit ? F.logit_tau : F.tau_m);
+    const float m = mask_from_bits<kMT>(V, mraw, half);
+    const int32_t mt = mask_type_of<kMT>(V);
+    const float raw_gate = mt == kMaskLogit ? __uint_as_float(mraw) : m;
+    const bool pass = raw_gate >= (mt == kMaskLogit ? F.logit_tau : F.tau_m);
     const bool trusted = dmin <= dmed;
     const bool seethru = dmed > T.st_thr;
     // behind-surface gate (it only blocks the thin path)
@@ -388,7 +392,7 @@ __device__ __forceinline__ void tuple_view(const TViewC& T, const VoxelGeom& vg,
     // at depth d to (((x + 1/2) - cx) d / fx, ((y + 1/2) - cy) d / fy, d).
     const float px = __fmul_rn(__fmul_rn(__fsub_rn(u, V.K[2]), T.inv_fx), __fadd_rn(pzh, pzl));
     const float py = __fmul_rn(__fmul_rn(__fsub_rn(v, V.K[3]), T.inv_fy), __fadd_rn(pzh, pzl));
-    const bool logit = V.mask_type == kMaskLogit;
+    const bool logit = mask_type_of<kMT>(V) == kMaskLogit;
     int n_depth = 0, n_md = 0;
     float mkey = -FLT_MAX;  // the peak mask of the valid mask-positive pixels, as its key
     float d2 = FLT_MAX;
@@ -416,7 +420,7 @@ __device__ __forceinline__ void tuple_view(const TViewC& T, const VoxelGeom& vg,
                 gmed[k] = __ldg(T.d_med + q);
                 gmin[k] = __ldg(V.depth + q);
                 gn[k] = __ldg(T.n_samp + q);
-                gm[k] = mask_bits(V, q);
+                gm[k] = mask_bits<kMT>(V, q);
             }
         }
 #pragma unroll
@@ -433,7 +437,7 @@ __device__ __forceinline__ void tuple_view(const TViewC& T, const VoxelGeom& vg,
             const bool valid = !(qmed < F.eps) && __fmul_rn(lhs, den) <= t_full;
             float key;
             bool hq;
-            if (V.mask_type == kMaskF16) {
+            if (mask_type_of<kMT>(V) == kMaskF16) {
                 key = __half2float(__ushort_as_half((unsigned short)gm[k]));
                 hq = key > 0.5f;
             } else {
@@ -471,7 +475,7 @@ __device__ __forceinline__ void tuple_view(const TViewC& T, const VoxelGeom& vg,
 // Zeroes the accumulators first when the context holds no views yet.  The
 // view loop is unrolled to kN (>= the batch's views) so that the views'
 // constants are addressed at compile time.
-template <bool kContracted, int kN>
+template <bool kContracted, int kN, int kMT = -1>
 __global__ void __launch_bounds__(kThreads) k_tuple_scan(
     const uint32_t* __restrict__ active, const int32_t* __restrict__ d_n, GridC G, FuseC F,
     const __grid_constant__ TViewBatch TB, TupleC TP, int32_t accumulate, float* __restrict__ W,
@@ -494,7 +498,7 @@ __global__ void __launch_bounds__(kThreads) k_tuple_scan(
             if (vg.ok) {
 #pragma unroll
                 for (int i = 0; i < kN; ++i)
-                    if (i < TB.n && tuple_candidate<kContracted>(TB.v[i], vg, F, TP)) cand |= 1u << i;
+                    if (i < TB.n && tuple_candidate<kContracted, kMT>(TB.v[i], vg, F, TP)) cand |= 1u << i;
             }
         }
         const unsigned hb = __ballot_sync(0xffffffffu, cand != 0u);
@@ -512,7 +516,7 @@ __global__ void __launch_bounds__(kThreads) k_tuple_scan(
 // computes view i's vote (views run in parallel), then the half's first lane
 // adds the votes in view order (every voxel still sums its votes in view
 // order, with the same FMA and additions).
-template <bool kContracted>
+template <bool kContracted, int kMT = -1>
 __global__ void __launch_bounds__(kThreads) k_tuple_heavy(
     const uint32_t* __restrict__ active, const uint2* __restrict__ heavy,
     const int32_t* __restrict__ n_heavy, GridC G, FuseC F, const __grid_constant__ TViewBatch TB,
@@ -544,8 +548,8 @@ __global__ void __launch_bounds__(kThreads) k_tuple_heavy(
         float x = 0.f, y = 0.f;
         if (live && ((h.y >> l) & 1u)) {
             const VoxelGeom vg = voxel_geom<kContracted>(__ldg(active + h.x), G, F.gamma);
-            tuple_view<kContracted>(*reinterpret_cast<const TViewC*>(sv + l * kWords), vg, F, TP,
-                                    kind, x, y);
+            tuple_view<kContracted, kMT>(*reinterpret_cast<const TViewC*>(sv + l * kWords), vg, F, TP,
+                                         kind, x, y);
         }
         float Ws = 0.f, Zs = 0.f;
         uint32_t b = 0u;
@@ -859,11 +863,19 @@ static float thin_key_threshold(int32_t mask_type, float tau_thin) {
     return (float)std::log(tp / (1.0 - tp));
 }
 
-template <bool kC>
+// every view of the batch has a binary16 mask: the kernels take the mask type
+// as a compile-time constant (no per-view or per-pixel branches on it)
+static bool batch_all_f16(const TViewBatch& tb) {
+    for (int32_t i = 0; i < tb.n; ++i)
+        if (tb.v[i].base.mask_type != kMaskF16) return false;
+    return true;
+}
+
+template <bool kC, int kMT>
 static divas_status launch_tuple_scan(int nv, int blocks, cudaStream_t s, divas_ctx* c, const TViewBatch& tb,
                               const TupleC& T, int32_t acc, uint2* heavy, int32_t* n_heavy) {
 #define DIVAS_TUPLE_SCAN(N)                                                                      \
-    k_tuple_scan<kC, N><<<blocks, kThreads, 0, s>>>(c->active, c->d_n, c->G, c->F, tb, T, acc, \
+    k_tuple_scan<kC, N, kMT><<<blocks, kThreads, 0, s>>>(c->active, c->d_n, c->G, c->F, tb, T, acc, \
                                                    c->W, c->Z, c->bits, heavy, n_heavy)
     if (nv <= 4) DIVAS_TUPLE_SCAN(4);
     else if (nv <= 8) DIVAS_TUPLE_SCAN(8);
@@ -1085,19 +1097,29 @@ divas_status divas_fuse_add_views_tuple_profiled(divas_ctx* c, const divas_tuple
         const int32_t acc = c->n_views + k0 > 0 ? 1 : 0;
         DIVAS_CUDA(c, cudaMemsetAsync(n_heavy, 0, sizeof(int32_t), s));
         const int nv = tb.n;
-        st = c->G.contracted ? launch_tuple_scan<true>(nv, blocks, s, c, tb, T, acc, heavy, n_heavy)
-                             : launch_tuple_scan<false>(nv, blocks, s, c, tb, T, acc, heavy, n_heavy);
+        const bool f16 = batch_all_f16(tb);
+        if (c->G.contracted)
+            st = f16 ? launch_tuple_scan<true, kMaskF16>(nv, blocks, s, c, tb, T, acc, heavy, n_heavy)
+                     : launch_tuple_scan<true, -1>(nv, blocks, s, c, tb, T, acc, heavy, n_heavy);
+        else
+            st = f16 ? launch_tuple_scan<false, kMaskF16>(nv, blocks, s, c, tb, T, acc, heavy, n_heavy)
+                     : launch_tuple_scan<false, -1>(nv, blocks, s, c, tb, T, acc, heavy, n_heavy);
         if (st != DIVAS_OK) return st;
         if (last) {
             st = record_stage(c, stage_events, 2, s);
             if (st != DIVAS_OK) return st;
         }
-        if (c->G.contracted)
-            k_tuple_heavy<true><<<blocks, kThreads, 0, s>>>(c->active, heavy, n_heavy, c->G, c->F, tb,
-                                                            T, c->W, c->Z, c->bits);
-        else
-            k_tuple_heavy<false><<<blocks, kThreads, 0, s>>>(c->active, heavy, n_heavy, c->G, c->F, tb,
-                                                             T, c->W, c->Z, c->bits);
+#define DIVAS_TUPLE_HEAVY(KC, MT)                                                                  \
+    k_tuple_heavy<KC, MT><<<blocks, kThreads, 0, s>>>(c->active, heavy, n_heavy, c->G, c->F, tb, T,  \
+                                                      c->W, c->Z, c->bits)
+        if (c->G.contracted) {
+            if (f16) DIVAS_TUPLE_HEAVY(true, kMaskF16);
+            else DIVAS_TUPLE_HEAVY(true, -1);
+        } else {
+            if (f16) DIVAS_TUPLE_HEAVY(false, kMaskF16);
+            else DIVAS_TUPLE_HEAVY(false, -1);
+        }
+#undef DIVAS_TUPLE_HEAVY
         DIVAS_LAUNCHED(c, "k_tuple_heavy");
     }
     c->n_views += n_views;
