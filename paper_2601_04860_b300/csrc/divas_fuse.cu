@@ -406,21 +406,30 @@ __device__ __forceinline__ void zero_unoccupied_groups(const uint32_t* __restric
 // ---------------------------------------------------------------------------
 // finalize
 // ---------------------------------------------------------------------------
-// seg bits of one warp's 32 voxels (active slots base .. base + 31): lanes
-// that share a 32-bit word are grouped, their set bits OR-ed in and -- for a
-// bitfield that may hold an earlier seg of the same voxels -- their unset bits
-// AND-ed out, one atomic per group and bitfield.  Every bit belongs to exactly
-// one voxel, so the result does not depend on the order of the atomics.
+// seg bits of one warp's 32 voxels (active slots base .. base + 31): runs of
+// consecutive lanes that share a 32-bit word (the active list is ascending, so
+// a word's voxels are one run) are grouped, their set bits OR-ed in and -- for
+// a bitfield that may hold an earlier seg of the same voxels -- their unset
+// bits AND-ed out, one atomic per run and bitfield.  Every bit belongs to
+// exactly one voxel, so the result does not depend on the order of the
+// atomics (nor on a word's voxels forming one run).
 __device__ __forceinline__ void seg_epilogue(bool live, bool seg, int64_t lin,
                                              uint32_t* __restrict__ seg_bits, bool clear_bits,
                                              uint32_t* __restrict__ seg_out, bool clear_out) {
     const int lane = threadIdx.x & 31;
     const uint32_t word = live ? (uint32_t)(lin >> 5) : 0xffffffffu;
     const uint32_t bit = live ? 1u << (lin & 31) : 0u;
-    const uint32_t grp = __match_any_sync(0xffffffffu, word);
+    const uint32_t prev = __shfl_up_sync(0xffffffffu, word, 1);
+    const uint32_t heads = __ballot_sync(0xffffffffu, lane == 0 || prev != word);
+    // this lane's run: from the last head at or below it to the next head
+    const uint32_t upto = heads & (0xffffffffu >> (31 - lane));
+    const int first = 31 - __clz(upto);
+    const uint32_t after = heads & ~(0xffffffffu >> (31 - lane));
+    const int end = after ? __ffs(after) - 1 : 32;
+    const uint32_t grp = (end == 32 ? 0xffffffffu : (1u << end) - 1u) & ~((1u << first) - 1u);
     const uint32_t set = __reduce_or_sync(grp, seg ? bit : 0u);
     const uint32_t clr = __reduce_or_sync(grp, seg ? 0u : bit);
-    if (!live || lane != __ffs(grp) - 1) return;
+    if (!live || lane != first) return;
     if (set) atomicOr(seg_bits + word, set);
     if (clr && clear_bits) atomicAnd(seg_bits + word, ~clr);
     if (seg_out) {
