@@ -1122,12 +1122,10 @@ def profile_occupancy_steps(args):
     return 0
 
 
-def measure_surfels(dev, steps: int):
-    """Voxel-to-surfel mapping on the 256^3 scene: its 1M surface points as
-    surfel centres (two scales, a random orientation, 2% needles) against the
-    finalized fusion of its 8 views; the call (aspects, the P99 selection,
-    the per-surfel pass) replayed from a CUDA graph, L2 flushed; its roofline
-    (surfel inputs and outputs once); the oracle on a sample on the host."""
+def _surfel_setup(dev):
+    """The surfel leg's inputs on the 256^3 scene: its 1M surface points as
+    surfel centres (two scales, a random orientation, 2% needles of aspect
+    100-1000) and a context holding the finalized fusion of its 8 views."""
     import torch
 
     import synth
@@ -1145,6 +1143,33 @@ def measure_surfels(dev, steps: int):
     fu.add_views(wl.cams, depth, mask, mask_type=wl.mask_type)
     fu.finalize(score=True)
     dm, ds, dq = (torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in (mu, sc, q))
+    return wl, fu, mask, (mu, sc, q), (dm, ds, dq)
+
+
+def profile_surfel_steps(args):
+    """Profiling target of the voxel-to-surfel mapping: the fusion set-up,
+    then N surfel_labels calls (k_surfel_aspect, the selection launches,
+    k_surfel_pass, k_surfel_big, k_surfel_big_out) and nothing else."""
+    import torch
+    dev = torch.device("cuda")
+    wl, fu, mask, _, (dm, ds, dq) = _surfel_setup(dev)
+    for _ in range(args.profile_surfel_steps):
+        fu.surfel_labels(dm, ds, dq, wl.cams, mask, wl.mask_type)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_surfel_steps": args.profile_surfel_steps,
+                      "workload": "surfels-on-forward-dense-256", "surfels": int(dm.shape[0])}))
+    fu.close()
+    return 0
+
+
+def measure_surfels(dev, steps: int):
+    """Voxel-to-surfel mapping on the 256^3 scene: its 1M surface points as
+    surfel centres (two scales, a random orientation, 2% needles) against the
+    finalized fusion of its 8 views; the call (aspects, the P99 selection,
+    the per-surfel pass) replayed from a CUDA graph, L2 flushed; its roofline
+    (surfel inputs and outputs once); the oracle on a sample on the host."""
+    import torch
+    wl, fu, mask, (mu, sc, q), (dm, ds, dq) = _surfel_setup(dev)
     for _ in range(3):
         r = fu.surfel_labels(dm, ds, dq, wl.cams, mask, wl.mask_type)
     torch.cuda.synchronize()
@@ -1405,6 +1430,8 @@ def run(args):
         return profile_weight_steps(args)
     if args.profile_nerf_steps:
         return profile_nerf_steps(args)
+    if args.profile_surfel_steps:
+        return profile_surfel_steps(args)
     if args.profile_occupancy_steps:
         return profile_occupancy_steps(args)
     if world > 1:
@@ -1521,6 +1548,8 @@ def main(argv=None):
                     help="profiling target: run N eager depth-tuple steps and exit")
     ap.add_argument("--profile-nerf-steps", type=int, default=0,
                     help="profiling target: run N eager NeRF-variant steps and exit")
+    ap.add_argument("--profile-surfel-steps", type=int, default=0,
+                    help="profiling target: run N voxel-to-surfel calls and exit")
     ap.add_argument("--profile-weight-steps", type=int, default=0,
                     help="profiling target: run N eager depth-weighted steps and exit")
     ap.add_argument("--profile-occupancy-steps", type=int, default=0,

@@ -128,7 +128,8 @@ __device__ __forceinline__ int64_t foot_area(const SFoot& F) {
     return F.any ? (int64_t)(F.x1 - F.x0 + 1) * (F.y1 - F.y0 + 1) : 0;
 }
 
-constexpr int64_t kSurfelSmallBox = 1024;  // larger boxes go to the block-per-surfel pass
+constexpr int64_t kSurfelSmallBox = 256;  // larger boxes go to the block-per-surfel pass
+constexpr int kSurfBigThreads = 512;       // threads of a block of that pass
 
 // a surfel's tangent semi-axes and centre
 __device__ __forceinline__ void surfel_axes(const float* __restrict__ mu,
@@ -230,7 +231,7 @@ __global__ void __launch_bounds__(kSurfThreads) k_surfel_pass(
 // block and the counts reduced; per surfel, the largest fraction (atomicMax
 // on its non-negative bits) and whether some view reached tau_kappa
 // (atomicOr) go to acc (zeroed).
-__global__ void __launch_bounds__(kSurfThreads) k_surfel_big(
+__global__ void __launch_bounds__(kSurfBigThreads) k_surfel_big(
     const float* __restrict__ mu, const float* __restrict__ scales, const float* __restrict__ quats,
     const uint2* __restrict__ big, const int32_t* __restrict__ n_big,
     const __grid_constant__ SViews SV, float tau_kappa, float z_near, uint2* __restrict__ acc) {
@@ -255,11 +256,12 @@ __global__ void __launch_bounds__(kSurfThreads) k_surfel_big(
         if (s_ok) {
             const SFoot F = sF;
             uint32_t tot = 0u, msk = 0u;
-            const int64_t area = foot_area(F);
-            const int32_t bw = F.x1 - F.x0 + 1;
-            for (int64_t p = threadIdx.x; p < area; p += blockDim.x)
-                surfel_pixel(SV.v[s], F, F.x0 + (int)(p % bw), F.y0 + (int)(p / bw), SV.mask_type,
-                             gate, tot, msk);
+            // warps take rows, lanes take columns (consecutive mask words)
+            const int nwarps = (int)(blockDim.x >> 5), lane = (int)(threadIdx.x & 31);
+            if (F.any)
+                for (int y = F.y0 + (int)(threadIdx.x >> 5); y <= F.y1; y += nwarps)
+                    for (int x = F.x0 + lane; x <= F.x1; x += 32)
+                        surfel_pixel(SV.v[s], F, x, y, SV.mask_type, gate, tot, msk);
             tot = __reduce_add_sync(0xffffffffu, tot);
             msk = __reduce_add_sync(0xffffffffu, msk);
             if ((threadIdx.x & 31) == 0) {
@@ -434,7 +436,7 @@ divas_status divas_surfel_labels(divas_ctx* c, const float* mu, const float* sca
                                                   n_big);
     DIVAS_LAUNCHED(c, "k_surfel_pass");
     if (n_views > 0) {
-        k_surfel_big<<<dim3(std::max(1, 4 * c->sm_count / n_views), n_views), kSurfThreads, 0, s>>>(
+        k_surfel_big<<<dim3(std::max(1, 4 * c->sm_count / n_views), n_views), kSurfBigThreads, 0, s>>>(
             mu, scales, quats, big, n_big, SV, p->tau_kappa, c->F.z_near, acc);
         DIVAS_LAUNCHED(c, "k_surfel_big");
         k_surfel_big_out<<<c->sm_count, kSurfThreads, 0, s>>>(big, n_big, acc, f_out, kappa_out);
