@@ -517,7 +517,7 @@ __global__ void __launch_bounds__(kThreads) k_tuple_scan(
 // adds the votes in view order (every voxel still sums its votes in view
 // order, with the same FMA and additions).
 template <bool kContracted, int kMT = -1>
-__global__ void __launch_bounds__(kThreads) k_tuple_heavy(
+__global__ void __launch_bounds__(kThreads, 4) k_tuple_heavy(
     const uint32_t* __restrict__ active, const uint2* __restrict__ heavy,
     const int32_t* __restrict__ n_heavy, GridC G, FuseC F, const __grid_constant__ TViewBatch TB,
     TupleC TP, float* __restrict__ W, float* __restrict__ Z, uint32_t* __restrict__ bits) {
