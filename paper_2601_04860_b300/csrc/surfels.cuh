@@ -171,7 +171,7 @@ __device__ __forceinline__ int32_t active_find(const uint32_t* __restrict__ acti
 // surfel whose 1-sigma box in some scored view holds more than
 // kSurfelSmallBox pixels is appended to `big` (with its view bits) and left
 // to k_surfel_big.
-__global__ void __launch_bounds__(kSurfThreads) k_surfel_pass(
+__global__ void __launch_bounds__(kSurfThreads, 6) k_surfel_pass(
     const float* __restrict__ mu, const float* __restrict__ scales, const float* __restrict__ quats,
     const float* __restrict__ aspect, int32_t m, GridC G, const uint32_t* __restrict__ seg_bits,
     const uint32_t* __restrict__ active, const int32_t* __restrict__ d_n,
