@@ -178,9 +178,10 @@ class Clocks:
 # --------------------------------------------------------------------------
 # CPU oracle baseline (bounded sample)
 # --------------------------------------------------------------------------
-def oracle_rate(wl, seconds: float, seed: int = 0):
+def oracle_rate(wl, seconds: float, seed: int = 0, repeats: int = 3):
     """Time the FP64 oracle on a random sample of the active voxels (all views)
-    and of the points; returns the extrapolated full-step seconds and details."""
+    and of the points; returns the extrapolated full-step seconds (the median
+    of `repeats` timed runs of the same sample) and details with the spread."""
     import oracle
     cores = oracle.set_threads(0)
     lin = wl.active_linear()
@@ -190,19 +191,28 @@ def oracle_rate(wl, seconds: float, seed: int = 0):
     t0 = time.perf_counter()
     oracle.fuse(wl.grid, lin[pilot], wl.cams, wl.depth, wl.mask, wl.mask_type, prm)
     t_pilot = time.perf_counter() - t0
-    n = int(min(len(lin), max(1000, len(pilot) * 0.8 * seconds / max(t_pilot, 1e-6))))
-    sample = rng.choice(len(lin), size=n, replace=False)
-    t0 = time.perf_counter()
-    out = oracle.fuse(wl.grid, lin[sample], wl.cams, wl.depth, wl.mask, wl.mask_type, prm)
-    t_fuse = time.perf_counter() - t0
+    per_run = seconds / max(1, repeats)
+    n = int(min(len(lin), max(1000, len(pilot) * 0.8 * per_run / max(t_pilot, 1e-6))))
+    sample = np.sort(rng.choice(len(lin), size=n, replace=False))
     npts = min(len(wl.points), 300_000)
-    seg = oracle.dense_seg(wl.grid, lin[sample], out["seg"])
-    t0 = time.perf_counter()
-    oracle.label(wl.grid, seg, wl.points[:npts])
-    t_lab = time.perf_counter() - t0
-    full = t_fuse * len(lin) / n + t_lab * len(wl.points) / npts
+    fulls, fuse_s, label_s = [], [], []
+    for _ in range(max(1, repeats)):
+        t0 = time.perf_counter()
+        out = oracle.fuse(wl.grid, lin[sample], wl.cams, wl.depth, wl.mask, wl.mask_type, prm)
+        t_fuse = time.perf_counter() - t0
+        seg = oracle.dense_seg(wl.grid, lin[sample], out["seg"])
+        t0 = time.perf_counter()
+        oracle.label(wl.grid, seg, wl.points[:npts])
+        t_lab = time.perf_counter() - t0
+        fulls.append(t_fuse * len(lin) / n + t_lab * len(wl.points) / npts)
+        fuse_s.append(t_fuse)
+        label_s.append(t_lab)
+    full = float(np.median(fulls))
     return full, {"cores": cores, "sample_voxels": n, "active_voxels": int(len(lin)),
-                  "sample_points": npts, "fuse_s": t_fuse, "label_s": t_lab}
+                  "sample_points": npts, "fuse_s": float(np.median(fuse_s)),
+                  "label_s": float(np.median(label_s)), "repeats": len(fulls),
+                  "full_s_min": float(min(fulls)), "full_s_max": float(max(fulls)),
+                  "sample_index": sample, "sample_out": out}
 
 
 # --------------------------------------------------------------------------
@@ -1473,8 +1483,10 @@ def run(args):
             "kind": "oracle",
             "sample": (f"{det['sample_voxels']} of {det['active_voxels']} active voxels x "
                        f"{wl.n_views} views + {det['sample_points']} points, extrapolated "
-                       f"to the full step"),
-            "seconds": det["fuse_s"] + det["label_s"]}
+                       f"to the full step; median of {det['repeats']} timed runs"),
+            "seconds": det["fuse_s"] + det["label_s"],
+            "repeats": det["repeats"],
+            "spread": [N * wl.n_views / det["full_s_max"], N * wl.n_views / det["full_s_min"]]}
     if rank == 0:
         print(json.dumps(res), flush=True)
     if world > 1:
@@ -1495,15 +1507,16 @@ def run_reference(args):
     per_step = max(1.0, min(10.0, 150.0 / max(1, args.steps + args.warmup)))
     times, det = [], None
     for k in range(args.warmup + args.steps):
-        full_s, det = oracle_rate(wl, per_step, seed=k)
+        full_s, det = oracle_rate(wl, per_step, seed=k, repeats=1)
         if k >= args.warmup:
             times.append(full_s)
     N = wl.n_voxels
-    ms = float(np.mean(times)) * 1e3
+    ms = float(np.median(times)) * 1e3
     v = N * wl.n_views / (ms * 1e-3)
     sample = (f"each step: {det['sample_voxels']} of {det['active_voxels']} active voxels x "
               f"{wl.n_views} views + {det['sample_points']} points, extrapolated to the full "
-              f"step")
+              f"step; the median over the {len(times)} timed steps (spread "
+              f"{1e3 * min(times):.1f}-{1e3 * max(times):.1f} ms)")
     res = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",

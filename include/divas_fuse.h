@@ -621,8 +621,13 @@ void divas_batch_destroy(divas_batch* b);
  * every GPU that loads the library until exit) shared by all calls: calls that
  * overlap on the GPU race.  The first call on a device looks up that array's
  * address (once per device, with the device current); make it before any
- * stream capture.  Errors: DIVAS_E_INVALID / DIVAS_E_CUDA, message from
- * divas_noalloc_last_error.
+ * stream capture.  Errors: DIVAS_E_INVALID before any launch for the same
+ * invalid grids, parameters and cameras that divas_fuse_init and
+ * divas_fuse_add_views reject (non-finite origin, intrinsics, R or t, NaN
+ * thresholds, ...), for a side beyond 64, other grid kinds and bad views;
+ * DIVAS_E_CUDA for a failed runtime call.  divas_noalloc_last_error returns
+ * the message of this host thread's last failed call (thread-local, valid
+ * until that thread's next call).
  */
 divas_status divas_fuse_dense_noalloc(const divas_grid* grid, const uint8_t* occ_dense,
                                       const divas_view* views, int32_t n_views,

@@ -870,18 +870,43 @@ int grid_for(int64_t items, int32_t sm_count, int per_sm = 16) {
 
 bool finite_pos(float x) { return x > 0.f && x <= FLT_MAX; }
 
-divas_status check_camera(divas_ctx* c, const divas_camera* cam) {
-    if (!cam) return fail(c, DIVAS_E_INVALID, "camera is NULL");
+// Argument checks shared by every entry point that takes a grid, fusion
+// parameters or a camera: nullptr when the argument is valid, else the reason.
+const char* grid_problem(const divas_grid* grid, int32_t g_max) {
+    if (!grid) return "grid is NULL";
+    if (grid->g < 1 || grid->g > g_max) return "g out of range";
+    if (!finite_pos(grid->h)) return "h must be finite and > 0";
+    for (int q = 0; q < 3; ++q)
+        if (!(fabsf(grid->origin[q]) <= FLT_MAX)) return "origin not finite";
+    return nullptr;
+}
+
+const char* params_problem(const divas_params* p) {
+    if (!p) return "params is NULL";
+    if (!(p->gamma > 0.f && p->gamma <= FLT_MAX) || !(p->alpha1 >= 0.f) ||
+        !(p->alpha1 <= FLT_MAX) || !(p->eps >= 0.f) || !(p->tau_mask == p->tau_mask) ||
+        !(p->tau_cons == p->tau_cons) || !(p->z_near == p->z_near))
+        return "params out of range";
+    return nullptr;
+}
+
+const char* camera_problem(const divas_camera* cam) {
+    if (!cam) return "camera is NULL";
     if (cam->W <= 0 || cam->H <= 0 || cam->W > 65535 || cam->H > 65535 ||
         (int64_t)cam->W * cam->H > INT32_MAX)
-        return fail(c, DIVAS_E_INVALID, "camera W/H must be in 1..65535 with W*H < 2^31");
+        return "camera W/H must be in 1..65535 with W*H < 2^31";
     for (int q = 0; q < 9; ++q)
-        if (!(fabsf(cam->R[q]) <= FLT_MAX)) return fail(c, DIVAS_E_INVALID, "camera R not finite");
+        if (!(fabsf(cam->R[q]) <= FLT_MAX)) return "camera R not finite";
     for (int q = 0; q < 3; ++q)
-        if (!(fabsf(cam->t[q]) <= FLT_MAX)) return fail(c, DIVAS_E_INVALID, "camera t not finite");
+        if (!(fabsf(cam->t[q]) <= FLT_MAX)) return "camera t not finite";
     if (!(fabsf(cam->fx) <= FLT_MAX && fabsf(cam->fy) <= FLT_MAX && fabsf(cam->cx) <= FLT_MAX &&
           fabsf(cam->cy) <= FLT_MAX))
-        return fail(c, DIVAS_E_INVALID, "camera intrinsics not finite");
+        return "camera intrinsics not finite";
+    return nullptr;
+}
+
+divas_status check_camera(divas_ctx* c, const divas_camera* cam) {
+    if (const char* why = camera_problem(cam)) return fail(c, DIVAS_E_INVALID, why);
     return DIVAS_OK;
 }
 
@@ -1092,10 +1117,7 @@ divas_status divas_fuse_init(divas_ctx** out, const divas_grid* grid, const uint
     *out = nullptr;
     if (!grid || !params) return fail(nullptr, DIVAS_E_INVALID, "grid or params is NULL");
     if (grid->g < 1 || grid->g > 1024) return fail(nullptr, DIVAS_E_INVALID, "g must be in 1..1024");
-    if (!finite_pos(grid->h)) return fail(nullptr, DIVAS_E_INVALID, "h must be finite and > 0");
-    for (int q = 0; q < 3; ++q)
-        if (!(fabsf(grid->origin[q]) <= FLT_MAX))
-            return fail(nullptr, DIVAS_E_INVALID, "origin not finite");
+    if (const char* why = grid_problem(grid, 1024)) return fail(nullptr, DIVAS_E_INVALID, why);
     if (grid->kind == 0) {
         if (!occ_dense || coords) return fail(nullptr, DIVAS_E_INVALID, "dense kind needs occ_dense only");
     } else if (grid->kind == 1) {
@@ -1104,10 +1126,7 @@ divas_status divas_fuse_init(divas_ctx** out, const divas_grid* grid, const uint
     } else {
         return fail(nullptr, DIVAS_E_INVALID, "kind must be 0 (dense) or 1 (sparse)");
     }
-    if (!(params->gamma > 0.f && params->gamma <= FLT_MAX) || !(params->alpha1 >= 0.f) ||
-        !(params->alpha1 <= FLT_MAX) || !(params->eps >= 0.f) || !(params->tau_mask == params->tau_mask) ||
-        !(params->tau_cons == params->tau_cons) || !(params->z_near == params->z_near))
-        return fail(nullptr, DIVAS_E_INVALID, "params out of range");
+    if (const char* why = params_problem(params)) return fail(nullptr, DIVAS_E_INVALID, why);
 
     divas_ctx* c = new (std::nothrow) divas_ctx();
     if (!c) return fail(nullptr, DIVAS_E_OOM, "host allocation failed");
@@ -2075,7 +2094,7 @@ namespace {
 
 std::mutex g_noalloc_mu;
 void* g_noalloc_dev_ptr[256] = {nullptr};
-std::string g_noalloc_error;
+thread_local std::string g_noalloc_error;  // per host thread, like the init error
 
 divas_status noalloc_fail(divas_status st, const std::string& msg) {
     g_noalloc_error = msg;
@@ -2092,15 +2111,20 @@ extern "C" divas_status divas_fuse_dense_noalloc(const divas_grid* grid, const u
         return noalloc_fail(DIVAS_E_INVALID, "NULL argument");
     if (grid->kind != 0 || grid->contracted)
         return noalloc_fail(DIVAS_E_INVALID, "only plain dense grids (kind 0, not contracted)");
-    if (grid->g < 1 || (int64_t)grid->g * grid->g * grid->g > kNoAllocMaxCells)
+    // the side is bounded before any product of it is formed
+    if (grid->g < 1 || grid->g > 64)
         return noalloc_fail(DIVAS_E_INVALID,
                             "grid too large for the allocation-free path (at most 64^3 cells)");
-    if (!finite_pos(grid->h)) return noalloc_fail(DIVAS_E_INVALID, "h must be finite and > 0");
+    if (const char* why = grid_problem(grid, 64)) return noalloc_fail(DIVAS_E_INVALID, why);
     if (n_views < 1 || n_views > kMaxViews)
         return noalloc_fail(DIVAS_E_INVALID, "n_views must be in 1..32");
-    if (!(params->gamma > 0.f && params->gamma <= FLT_MAX) || !(params->alpha1 >= 0.f) ||
-        !(params->eps >= 0.f))
-        return noalloc_fail(DIVAS_E_INVALID, "params out of range");
+    if (const char* why = params_problem(params)) return noalloc_fail(DIVAS_E_INVALID, why);
+    for (int32_t k = 0; k < n_views; ++k) {
+        if (const char* why = camera_problem(&views[k].cam))
+            return noalloc_fail(DIVAS_E_INVALID, why);
+        if (!views[k].depth || !views[k].mask || views[k].mask_type < 0 || views[k].mask_type > 2)
+            return noalloc_fail(DIVAS_E_INVALID, "bad view");
+    }
     cudaStream_t s = S(stream);
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -2166,14 +2190,8 @@ extern "C" divas_status divas_fuse_dense_noalloc(const divas_grid* grid, const u
     ViewBatch vb;
     memset(&vb, 0, sizeof(vb));
     vb.n = n_views;
-    for (int32_t k = 0; k < n_views; ++k) {
-        const divas_camera& cam = views[k].cam;
-        if (cam.W <= 0 || cam.H <= 0 || cam.W > 65535 || cam.H > 65535 ||
-            (int64_t)cam.W * cam.H > INT32_MAX || !views[k].depth || !views[k].mask ||
-            views[k].mask_type < 0 || views[k].mask_type > 2)
-            return noalloc_fail(DIVAS_E_INVALID, "bad view");
-        vb.v[k] = make_view(cam, G, views[k].depth, views[k].mask, views[k].mask_type, k);
-    }
+    for (int32_t k = 0; k < n_views; ++k)
+        vb.v[k] = make_view(views[k].cam, G, views[k].depth, views[k].mask, views[k].mask_type, k);
     const int64_t n_cells = (int64_t)grid->g * grid->g * grid->g;
     const int64_t n_words = (n_cells + 31) / 32;
     const int32_t n_tiles = (int32_t)((n_words + kTileSpan - 1) / kTileSpan);
