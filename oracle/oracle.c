@@ -635,13 +635,8 @@ void oracle_fuse_tuple(int g, const double* origin, double h, int contracted, in
                 }
             double n_min = fmax(tp->n_abs, ceil(tp->rho_occ * A_B));
             double gate = tp->dist_gate * hv;
-            {   /* the distance gate compares a distance formed from differences of
-                   coordinates of size |x| + |o|: near it when within 4e-6 of that
-                   size (the 1e-6 margin times 4), not of the gate itself */
-                double xn = sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
-                double on = sqrt(oc[0] * oc[0] + oc[1] * oc[1] + oc[2] * oc[2]);
-                near_flag(sqrt(d2), gate, 4.0 * (1.0 + xn + on), &flags);
-            }
+            /* the distance gate: near it within 1e-6 of the gate itself */
+            near_flag(sqrt(d2), gate, gate, &flags);
             {   /* ceil near an integer step: flag when the two candidate counts
                    would decide this voxel differently */
                 double k = round(tp->rho_occ * A_B);
@@ -707,9 +702,9 @@ void oracle_fuse_tuple(int g, const double* origin, double h, int contracted, in
  *   >= rho_cover N, else 0; t >= tau_thin -> W += t, Z += 1.
  *   P = W / Z if Z > eps else 0; seg = P >= tau_cons.
  *
- * Near-boundary flags as in the 2DGS variant: the spatial gate against 4e-6
- * (1 + |x| + |o|) (a distance formed from coordinate differences), the depth
- * gates against 1e-6 |x_d|, box edges near an integer, tau_thin, z_near.
+ * Near-boundary flags as in the 2DGS variant: the spatial gate within 1e-6
+ * of tau_spatial itself, the depth gates against 1e-6 |x_d|, box edges near
+ * an integer, tau_thin, z_near.
  *
  * parity: pinned by the NeRF-variant tests (single-voxel closed forms of
  * every gate and of the weight, an independent NumPy statement in ray space).
@@ -753,12 +748,6 @@ void oracle_fuse_nerf(int g, const double* origin, double h, int contracted, int
             int pass, half;
             tmask_at(vw, mask_type, pix, pr, &m, &pass, &half);
             double xd = p[2];
-            double oc[3];
-            for (int r = 0; r < 3; ++r) /* camera centre o = -R^T t */
-                oc[r] = -((double)R[r] * vw->t[0] + (double)R[3 + r] * vw->t[1] +
-                          (double)R[6 + r] * vw->t[2]);
-            double xn = sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
-            double on = sqrt(oc[0] * oc[0] + oc[1] * oc[1] + oc[2] * oc[2]);
             int check_thin = 1;
             /* thick path (Eqs. distance_cond .. nerf-vote) */
             double dmin = vw->d_min[pix], dexp = vw->d_med[pix], dmax = vw->d_max[pix];
@@ -776,7 +765,7 @@ void oracle_fuse_nerf(int g, const double* origin, double h, int contracted, int
                                 np->lambda_range * sqrt(k2) * (dmax - dmin);
                 double b = fmin(np->beta * (double)n, np->b_max);
                 double tau_d = (np->gamma + b) * hv;
-                near_flag(delta, tau_sp, 4.0 * (1.0 + xn + on), &flags);
+                near_flag(delta, tau_sp, tau_sp, &flags);
                 near_flag(fabs(xd - dexp), tau_d, fabs(xd), &flags);
                 if (delta <= tau_sp && fabs(xd - dexp) <= tau_d) {
                     double mu = 0.5 * (dmin + dmax);

@@ -45,10 +45,11 @@ is exact once they agree).
 The back-projected overlay (Sec. 3.7 "Iterative Mask Propagation": the
 fused 3D mask shown on the next view): each pixel centre unprojected at its
 planar depth, x = R^T (((u + 1/2 - cx) / fx) d, ((v + 1/2 - cy) / fy) d, d)
-- R^T t (FP64, then FP32 as the label lookup takes points), and the seg bit
-of its cell (oracle.label); 0 where the depth is not finite and positive.
-Pixels whose point lies within 64 x 2^-24 of the magnitudes of a cell
-boundary (the reach of an FP32 unprojection) are flagged.
+- R^T t in FP64, and the seg bit of its cell floor((q - origin) / h) (q = x,
+or contract(x) on a contracted grid; the Pass 1 lookup rule, taken on the
+FP64 point); 0 where the depth is not finite and positive or the point is
+outside the grid.  Pixels whose (q - origin) / h lies within 1e-6
+(relative, as for point labels) of an integer are flagged.
 
 parity: pinned by tests/test_oracle_surfels.py (closed forms for a
 fronto-parallel disc, gating, the aspect threshold, a per-pixel brute force
@@ -163,8 +164,7 @@ def surfel_labels(mu, scales, quats, F1, voxel_bits, cams, masks, mask_type, tau
 
 
 def overlay(grid, seg_dense, cam, depth):
-    """The overlay of one view: (uint8 H x W, the label's flags per pixel)."""
-    from . import label
+    """The overlay of one view: (uint8 H x W, the near-boundary flags per pixel)."""
     D = np.asarray(depth, np.float32).astype(np.float64)
     H, W = D.shape
     ys, xs = np.mgrid[0:H, 0:W]
@@ -174,17 +174,21 @@ def overlay(grid, seg_dense, cam, depth):
                    ((ys + 0.5 - float(cam.cy)) / float(cam.fy)) * Dz, Dz], axis=-1).reshape(-1, 3)
     R = np.asarray(cam.R, np.float32).astype(np.float64).reshape(3, 3)
     t = np.asarray(cam.t, np.float32).astype(np.float64)
-    X64 = (pc - t) @ R                            # R^T (p_c - t), row vectors
-    lab, fl = label(grid, seg_dense, X64.astype(np.float32))
-    # an FP32 unprojection (about ten roundings) moves x by at most a few
-    # units of 2^-24 of the magnitudes involved: cells nearer than 64 of them
-    # may go either way
+    X = (pc - t) @ R                              # R^T (p_c - t), row vectors
+    if getattr(grid, "contracted", False):        # contract(x) = (2 - 1/|x|) x / |x|
+        r = np.sqrt((X * X).sum(axis=1))
+        sc = np.where(r > 1.0, (2.0 - 1.0 / np.where(r > 1.0, r, 1.0)) / np.where(r > 1.0, r, 1.0),
+                      1.0)
+        X = X * sc[:, None]
+    g = int(grid.g)
     h = float(np.float32(grid.h))
     org = np.asarray(grid.origin, np.float32).astype(np.float64)
-    mag = np.abs(pc).sum(axis=1) + np.abs(t).sum() + np.abs(X64).max(axis=1)
-    s = (X64 - org) / h
-    near = np.any(np.abs(s - np.round(s)) < (64.0 * 2.0 ** -24 * mag / h)[:, None], axis=1)
-    fl = fl | near.astype(fl.dtype)
-    lab = np.where(ok.ravel(), lab, 0).astype(np.uint8)
-    fl = np.where(ok.ravel(), fl, 0)
+    s = (X - org) / h
+    f = s - np.floor(s)
+    near = np.any(np.minimum(f, 1.0 - f) < 1e-6 * np.maximum(1.0, np.abs(s)), axis=1)
+    inside = np.all((s >= 0.0) & (s < g), axis=1) & ok.ravel()
+    idx = np.where(inside[:, None], np.floor(s), 0).astype(np.int64)
+    seg = np.asarray(seg_dense, np.uint8).ravel()
+    lab = np.where(inside, seg[(idx[:, 2] * g + idx[:, 1]) * g + idx[:, 0]], 0).astype(np.uint8)
+    fl = np.where(ok.ravel(), near, False).astype(np.uint32)
     return lab.reshape(H, W), fl.reshape(H, W)

@@ -730,3 +730,81 @@ ALL_PINS = [pin_nerf_closed_form, pin_single_view_closed_form, pin_pixel_convent
             pin_alpha0_mean, pin_invariants, pin_scale_invariance, pin_sphere_scene,
             pin_bruteforce, pin_labels, pin_gradient_fd, pin_tuple_closed_form,
             pin_tuple_bruteforce, pin_nerf_bruteforce]
+
+
+# --------------------------------------------------------------------------
+# near-boundary flags: a decision within 1e-6 (relative to its own scale) of
+# flipping is flagged, one farther away is not
+# --------------------------------------------------------------------------
+FLAG_TUPLE = 32
+NEAR, FAR = 0.5e-6, 2e-6
+
+
+def _flag_probe(orc, cx=16.25, depth=None, mask=1.0):
+    grid, cam, lin, p_z = _probe_setup()
+    cam = synth.Camera(cam.R, cam.t, cam.fx, cam.fy, float(np.float32(cx)), cam.cy, cam.W, cam.H)
+    at = (12, int(math.floor(cx)))
+    D = _raster(cam, p_z if depth is None else depth, at)
+    M = _raster(cam, mask, at, fill=0.0)
+    return orc.fuse(grid, lin, [cam], [D], [M], oracle.MASK_F32, P_DEFAULT), p_z
+
+
+def pin_near_boundary_flags(orc):
+    # pixel: the voxel sits on the optical axis (p_x = 0), so u = cx; a
+    # principal point 16 + m (1 + |cx|) above the integer 16 puts u there
+    for m, want in ((NEAR, True), (FAR, False)):
+        cx = float(np.float32(16.0 + m * 17.0))
+        margin = (cx - 16.0) / (1.0 + cx)
+        assert (margin < 1e-6) == want
+        r, _ = _flag_probe(orc, cx=cx)
+        assert bool(r["flags"][0] & oracle.FLAG_PIX) == want, (m, r["flags"])
+        assert r["bits"][0] == 1  # the vote itself is unaffected
+    # depth gate |e| <= Delta = 1/4, margin ||e| - Delta| / max(p_z, D): the
+    # depth just inside and just outside the band, near and far from its edge
+    for side in (+1, -1):
+        for m, want in ((NEAR, True), (FAR, False)):
+            _, p_z = _flag_probe(orc)
+            D = float(np.float32(p_z - 0.25 + side * m * p_z))
+            margin = abs(abs(p_z - D) - 0.25) / max(p_z, D)
+            assert (margin < 1e-6) == want
+            r, _ = _flag_probe(orc, depth=D)
+            assert bool(r["flags"][0] & oracle.FLAG_DEPTH) == want, (side, m, r["flags"])
+            assert r["bits"][0] == (1 if side > 0 else 0)
+    # consensus P >= tau_cons: one view votes, so P = m exactly
+    for m, want in ((NEAR, True), (FAR, False)):
+        mk = float(np.float32(0.5 + m))
+        r, _ = _flag_probe(orc, mask=mk)
+        assert r["P"][0] == mk and bool(r["flags"][0] & oracle.FLAG_CONS) == want
+    # 2DGS thin path, distance gate dist_gate h_v against the nearest
+    # mask-positive unprojection (the 8 x 8 mask hole of pin_tuple_closed_form:
+    # untrusted everywhere, so every pixel unprojects at d_med = 2.375 and the
+    # distance is 2.375 |((x + 1/2 - cx) / fx, (y + 1/2 - cy) / fy)|)
+    grid, cam, lin, xd = _tuple_setup()
+    mk = np.ones((80, 100), np.float32)
+    mk[37:45, 46:54] = 0.0
+    d_med = float(np.float32(2.375))
+    best = min(d_med * math.hypot((x + 0.5 - 50.25) / 100.0, (y + 0.5 - 40.75) / 100.0)
+               for y in range(35, 47) for x in range(44, 56) if mk[y, x] > 0.5)
+    for m, want in ((NEAR, True), (FAR, False)):
+        for side, vote in ((+1, 2), (-1, 0)):
+            gate = best * (1.0 + side * m)
+            r, _ = _tuple_run(orc, 2.475, 2.375, 2.575, mask=mk,
+                              tparams=oracle.TupleParams(dist_gate=gate / 0.25))
+            assert bool(r["flags"][0] & FLAG_TUPLE) == want, (m, side, r["flags"])
+            assert r["kind"][0, 0] == vote
+    # NeRF thick path, spatial gate delta = |p - k d_min| (the band lies
+    # beyond the voxel, z_c = d_min) against tau = h_v + lambda |k| (d_max - d_min)
+    f = lambda v: float(np.float32(v))  # noqa: E731
+    k = np.array([0.0025, -0.0025, 1.0])
+    p = np.array([0.0, 0.0, 2.375])
+    delta = float(np.linalg.norm(p - k * f(2.675)))
+    band = f(2.775) - f(2.675)
+    for m, want in ((NEAR, True), (FAR, False)):
+        for side, vote in ((+1, 1), (-1, 0)):
+            lam = (delta * (1.0 + side * m) - 0.25) / (np.linalg.norm(k) * band)
+            r = _nerf_run(orc, 2.675, 2.375, 2.775, nparams=oracle.NerfParams(lambda_range=lam))
+            assert bool(r["flags"][0] & FLAG_TUPLE) == want, (m, side, r["flags"])
+            assert r["kind"][0, 0] == vote
+
+
+ALL_PINS.append(pin_near_boundary_flags)

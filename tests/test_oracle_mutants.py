@@ -112,6 +112,14 @@ MUTANTS = {
                              "if (!check_thin || !eligible) continue;"),
     "nerf_thin_after_thick": ("if (!check_thin || !eligible || !(rho_v >= np->rho_thin)) continue;",
                               "if (!eligible || !(rho_v >= np->rho_thin)) continue;"),
+    # near-boundary flags: bands wider than 1e-6 of the decision's scale, or none
+    "flag_margin_widened": ("#define ORACLE_MARGIN 1e-6", "#define ORACLE_MARGIN 4e-6"),
+    "flag_pixel_scale_dropped": ("dist_to_int(u) < ORACLE_MARGIN * su", "dist_to_int(u) < ORACLE_MARGIN"),
+    "flag_depth_missing": ("if (fabs(fabs(e) - Delta) < ORACLE_MARGIN * sc) flags |= FLAG_DEPTH;", ""),
+    "flag_tuple_distance_coordinate_scale": ("near_flag(sqrt(d2), gate, gate, &flags);",
+                                             "near_flag(sqrt(d2), gate, 4.0 * (1.0 + fabs(x[2])), &flags);"),
+    "flag_nerf_spatial_coordinate_scale": ("near_flag(delta, tau_sp, tau_sp, &flags);",
+                                           "near_flag(delta, tau_sp, 4.0 * (1.0 + fabs(xd)), &flags);"),
 }
 
 
