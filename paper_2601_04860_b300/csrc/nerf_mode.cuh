@@ -64,14 +64,48 @@ __device__ __forceinline__ float sub_pixel_offset(float f, float ph, float pl, f
     return __fdiv_rn(__fadd_rn(__fsub_rn(a, b), tail), __fmul_rn(f, __fadd_rn(zh, zl)));
 }
 
+// The thick path's spatial gate in FP64, with the operations of the FP64
+// definition: p = R x + t, k = the centre pixel's ray, z_c = clip(<p, k> /
+// |k|^2, d_min, d_max), delta = |p - k z_c| against h_v pi + lambda_range
+// |k| (d_max - d_min) (the re-evaluation of a decision near the gate).
+__device__ __noinline__ bool nerf_spatial_exact(const TViewC& T, const double* x, int ix, int iy,
+                                                float dmin, float dmax, float hv, float pi,
+                                                float lambda) {
+    const ViewC& V = T.base;
+    double p[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+        p[r] = __dadd_rn(__dadd_rn(__dadd_rn(__dmul_rn((double)T.R[3 * r], x[0]),
+                                             __dmul_rn((double)T.R[3 * r + 1], x[1])),
+                                   __dmul_rn((double)T.R[3 * r + 2], x[2])),
+                         (double)T.t[r]);
+    const double k0 = __ddiv_rn(__dsub_rn(__dadd_rn((double)ix, 0.5), (double)V.K[2]), (double)V.K[0]);
+    const double k1 = __ddiv_rn(__dsub_rn(__dadd_rn((double)iy, 0.5), (double)V.K[3]), (double)V.K[1]);
+    const double k2 = __dadd_rn(__dadd_rn(__dmul_rn(k0, k0), __dmul_rn(k1, k1)), 1.0);
+    const double zp = __ddiv_rn(__dadd_rn(__dadd_rn(__dmul_rn(p[0], k0), __dmul_rn(p[1], k1)), p[2]), k2);
+    const double lo = (double)dmin, hi = (double)dmax;
+    const double zc = zp < lo ? lo : (zp > hi ? hi : zp);
+    const double e0 = __dsub_rn(p[0], __dmul_rn(k0, zc)), e1 = __dsub_rn(p[1], __dmul_rn(k1, zc));
+    const double e2 = __dsub_rn(p[2], zc);
+    const double delta =
+        __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(e0, e0), __dmul_rn(e1, e1)), __dmul_rn(e2, e2)));
+    const double tau = __dadd_rn(__dmul_rn((double)hv, (double)pi),
+                                 __dmul_rn(__dmul_rn((double)lambda, __dsqrt_rn(k2)), __dsub_rn(hi, lo)));
+    return delta <= tau;
+}
+
 // View T at the voxel's centre pixel: 0 = neither path can vote, 1 = thick
 // vote (x = m, y = w), 2 = thin candidate (rho_v is the voxel's density; a
 // candidate also needs a mask key >= key_thr in the dilated tile map around
-// the centre when the view has one).
-template <bool kC, int kMT = -1>
-__device__ __forceinline__ int nerf_centre(const TViewC& T, const VoxelGeom& vg, const FuseC& F,
-                                           const NerfC& N, float rho_v, float& x, float& y,
-                                           NerfCentre& c) {
+// the centre when the view has one).  A spatial distance within the FP32
+// rounding bound of its gate is decided again in FP64 when kExact; otherwise
+// it counts as no thick vote and sets undecided (the caller hands the voxel
+// to the pass that decides it exactly).
+template <bool kC, int kMT = -1, bool kExact = true>
+__device__ __forceinline__ int nerf_centre(const TViewC& T, const VoxelGeom& vg, const GridC& G,
+                                           const FuseC& F, const NerfC& N, float rho_v, float& x,
+                                           float& y, NerfCentre& c, bool& undecided) {
+    undecided = false;
     const ViewC& V = T.base;
     if (!project_uv<kC>(V, vg.xh, vg.xl, F.z_near, c.pzh, c.pzl, c.r0, c.r1, c.u, c.v)) return 0;
     const int32_t pix = pixel_index(V, true, c.u, c.v);
@@ -121,9 +155,22 @@ __device__ __forceinline__ int nerf_centre(const TViewC& T, const VoxelGeom& vg,
                 const float dy = __fmaf_rn(-ky, s, __fmul_rn(pz, ey));
                 const float delta = __fsqrt_rn(__fmaf_rn(dx, dx, __fmaf_rn(dy, dy, __fmul_rn(s, s))));
                 const float band = __fsub_rn(dmax, dmin);
+                const float pi = pi_dg(T, ix, iy, N.k_dg);
                 const float tau_sp = __fmaf_rn(__fmul_rn(N.lambda_range, __fsqrt_rn(k2)), band,
-                                               __fmul_rn(hv, pi_dg(T, ix, iy, N.k_dg)));
-                if (delta <= tau_sp) {
+                                               __fmul_rn(hv, pi));
+                bool accept = delta <= tau_sp;
+                if (fabsf(__fsub_rn(delta, tau_sp)) <= recheck_band(T, vg, G, pz)) {
+                    if (kExact) {
+                        double xw[3];
+                        centre64(vg, G, xw);
+                        accept = nerf_spatial_exact(T, xw, ix, iy, dmin, dmax, hv, pi,
+                                                    N.lambda_range);
+                    } else {
+                        accept = false;
+                        undecided = true;
+                    }
+                }
+                if (accept) {
                     // z_c - mid: +-(d_max - d_min)/2 at a clamped end (from the
                     // depths themselves: lo and hi are rounded offsets when the
                     // band lies far from p_z), s - (lo + hi)/2 inside the band
@@ -245,6 +292,7 @@ __global__ void __launch_bounds__(kThreads, kC ? 4 : 6) k_nerf_scan(
     for (int32_t base = (blockIdx.x * blockDim.x + threadIdx.x) & ~31; base < n; base += stride) {
         const int32_t a = base + lane;
         uint32_t thick = 0u, thin = 0u;
+        bool heavy_only = false;
         if (a < n) {
             const uint32_t pk = __ldg(active + a);
             const VoxelGeom vg = voxel_geom<kC>(pk, G, F.gamma);
@@ -262,7 +310,9 @@ __global__ void __launch_bounds__(kThreads, kC ? 4 : 6) k_nerf_scan(
                     if (i >= TB.n) break;
                     float x = 0.f, y = 0.f;
                     NerfCentre c;
-                    const int kind = nerf_centre<kC, kMT>(TB.v[i], vg, F, N, rho_v, x, y, c);
+                    bool undecided;
+                    const int kind = nerf_centre<kC, kMT, false>(TB.v[i], vg, G, F, N, rho_v, x,
+                                                                 y, c, undecided);
                     if (kind == 1) {
                         thick |= 1u << i;
                         Ws = __fmaf_rn(x, y, Ws);
@@ -271,9 +321,15 @@ __global__ void __launch_bounds__(kThreads, kC ? 4 : 6) k_nerf_scan(
                     } else if (kind == 2) {
                         thin |= 1u << i;
                     }
+                    // a spatial decision near its gate: the heavy pass takes the view
+                    // again (thick bit) and decides it exactly
+                    if (undecided) {
+                        thick |= 1u << i;
+                        heavy_only = true;
+                    }
                 }
             }
-            if (!thin) {
+            if (!thin && !heavy_only) {
                 W[a] = Ws;
                 Z[a] = Zs;
                 bits[a] = b;
@@ -283,13 +339,14 @@ __global__ void __launch_bounds__(kThreads, kC ? 4 : 6) k_nerf_scan(
                 bits[a] = 0u;
             }
         }
-        const unsigned hb = __ballot_sync(0xffffffffu, thin != 0u);
+        const bool to_heavy = thin != 0u || heavy_only;
+        const unsigned hb = __ballot_sync(0xffffffffu, to_heavy);
         if (hb) {
             const int lead = __ffs(hb) - 1;
             int32_t slot = 0;
             if (lane == lead) slot = atomicAdd(n_heavy, __popc(hb));
             slot = __shfl_sync(0xffffffffu, slot, lead);
-            if (thin)
+            if (to_heavy)
                 heavy[slot + __popc(hb & ((1u << lane) - 1u))] = make_uint2((uint32_t)a, thick | (thin << 16));
         }
     }
@@ -330,7 +387,8 @@ __global__ void __launch_bounds__(kThreads) k_nerf_heavy(
             NerfCentre c;
             // the scan's outcome for this view, recomputed (a thin candidate
             // passed the density test there)
-            kind = nerf_centre<kC, kMT>(T, vg, F, N, is_thin ? FLT_MAX : 0.f, x, y, c);
+            bool undecided;
+            kind = nerf_centre<kC, kMT>(T, vg, G, F, N, is_thin ? FLT_MAX : 0.f, x, y, c, undecided);
             if (kind == 2) kind = nerf_thin<kC, kMT>(T, vg, F, N, c, x) ? 2 : 0;
         }
         float Ws = 0.f, Zs = 0.f;
@@ -478,6 +536,8 @@ divas_status divas_fuse_add_views_nerf_profiled(divas_ctx* c, const divas_tuple_
             const divas_tuple_view& v = views[k0 + j];
             TViewC& t = tb.v[j];
             t.base = make_view(v.cam, c->G, v.d_min, v.mask, v.mask_type, c->n_views + k0 + j);
+            memcpy(t.R, v.cam.R, sizeof(t.R));
+            memcpy(t.t, v.cam.t, sizeof(t.t));
             t.d_med = v.d_med;  // d_exp
             t.d_max = v.d_max;
             t.n_samp = v.n_samp;

@@ -295,11 +295,49 @@ __global__ void __launch_bounds__(kSurfThreads) k_surfel_big_out(
 // Propagation"): each pixel centre unprojected at its planar depth,
 // x = R^T (((u + 1/2 - cx) / fx) d, ((v + 1/2 - cy) / fy) d, d) - R^T t, and
 // the seg bit of the cell holding x (0 for no surface or outside the grid).
+// The point is formed in FP32; where its cell coordinate (q - origin) / h (q
+// = x, or contract(x)) lies within the FP32 rounding bound of an integer, the
+// pixel is evaluated again in FP64 with the operations of the FP64
+// definition, so that the cell agrees with it away from 1e-6 (relative) of a
+// boundary.
 struct OverlayView {
     float R[9], t[3];
     float fx, fy, cx, cy;
     int32_t W, H;
 };
+
+// the cell of pixel (x, y) at depth d in FP64; false outside the grid
+__device__ __noinline__ bool overlay_cell64(const OverlayView& V, const GridC& G, int x, int y,
+                                            float d, int32_t (&idx)[3]) {
+    const double dd = (double)d;
+    const double pc[3] = {
+        __dmul_rn(__ddiv_rn(__dsub_rn(__dadd_rn((double)x, 0.5), (double)V.cx), (double)V.fx), dd),
+        __dmul_rn(__ddiv_rn(__dsub_rn(__dadd_rn((double)y, 0.5), (double)V.cy), (double)V.fy), dd),
+        dd};
+    double X[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+        X[r] = __dadd_rn(__dadd_rn(__dmul_rn(__dsub_rn(pc[0], (double)V.t[0]), (double)V.R[r]),
+                                   __dmul_rn(__dsub_rn(pc[1], (double)V.t[1]), (double)V.R[3 + r])),
+                         __dmul_rn(__dsub_rn(pc[2], (double)V.t[2]), (double)V.R[6 + r]));
+    if (G.contracted) {  // contract(x) = (2 - 1/|x|) x / |x| beyond the unit ball
+        const double r = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(X[0], X[0]), __dmul_rn(X[1], X[1])),
+                                              __dmul_rn(X[2], X[2])));
+        if (r > 1.0) {
+            const double sc = __ddiv_rn(__dsub_rn(2.0, __ddiv_rn(1.0, r)), r);
+#pragma unroll
+            for (int q = 0; q < 3; ++q) X[q] = __dmul_rn(X[q], sc);
+        }
+    }
+    bool inside = true;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        const double s = __ddiv_rn(__dsub_rn(X[q], (double)G.origin[q]), (double)G.h);
+        inside = inside && s >= 0.0 && s < (double)G.g;
+        idx[q] = inside ? (int32_t)floor(s) : 0;
+    }
+    return inside;
+}
 
 __global__ void __launch_bounds__(kSurfThreads) k_overlay(OverlayView V, const float* __restrict__ depth,
                                                           GridC G, const uint32_t* __restrict__ seg_bits,
@@ -318,8 +356,28 @@ __global__ void __launch_bounds__(kSurfThreads) k_overlay(OverlayView V, const f
 #pragma unroll
             for (int r = 0; r < 3; ++r)  // world = R^T (p_c - t)
                 X[r] = __fmaf_rn(V.R[r], pc[0], __fmaf_rn(V.R[3 + r], pc[1], __fmul_rn(V.R[6 + r], pc[2])));
+            // the cell coordinate in FP32 and its distance to the nearest integer
+            float Q[3] = {X[0], X[1], X[2]};
+            float mag = fabsf(pc[0]) + fabsf(pc[1]) + fabsf(pc[2]) + fabsf(V.t[0]) +
+                        fabsf(V.t[1]) + fabsf(V.t[2]);
+            if (G.contracted) {
+                const float r = __fsqrt_rn(__fmaf_rn(X[0], X[0], __fmaf_rn(X[1], X[1], __fmul_rn(X[2], X[2]))));
+                if (r > 1.f) {
+                    const float sc = __fdiv_rn(__fsub_rn(2.f, __frcp_rn(r)), r);
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) Q[k] = __fmul_rn(X[k], sc);
+                }
+            }
+            bool near = false;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const float sk = __fdiv_rn(__fsub_rn(Q[k], G.origin[k]), G.h);
+                const float band = __fmul_rn(0x1p-15f, __fadd_rn(__fdiv_rn(mag, G.h), fabsf(sk)));
+                near = near || fabsf(__fsub_rn(sk, rintf(sk))) <= band;
+            }
             int32_t idx[3];
-            if (point_cell(X, 0, G, idx)) {
+            const bool in = near ? overlay_cell64(V, G, x, y, d, idx) : point_cell(X, 0, G, idx);
+            if (in) {
                 const int64_t lin = ((int64_t)idx[2] * G.g + idx[1]) * G.g + idx[0];
                 lab = (uint8_t)((__ldg(seg_bits + (lin >> 5)) >> (lin & 31)) & 1u);
             }

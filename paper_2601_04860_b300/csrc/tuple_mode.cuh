@@ -52,6 +52,8 @@ struct TViewC {
                                      // NULL: footprints may reach beyond it (no pre-check)
     int32_t tiles_w;                 // tiles per row
     float key_thr;                   // no thin vote unless some key in the footprint reaches it
+    float R[9], t[3];                // the camera as given (world -> camera, row-major): the
+                                     // exact re-evaluation of decisions near a gate
 };
 
 struct TViewBatch {
@@ -59,7 +61,8 @@ struct TViewBatch {
     int32_t pad;
     TViewC v[kMaxTupleViews];
 };
-static_assert(sizeof(TViewBatch) <= 3800, "a tuple view batch and the other arguments fit 4 KB");
+// (beyond the classic 4 KB: kernel parameters up to 32 KB, CUDA 12.1 and later)
+static_assert(sizeof(TViewBatch) <= 4600, "a tuple view batch and the other arguments");
 
 struct TupleC {
     float beta, tau_thin, rho_cover, rho_occ, n_abs, dist_gate, behind_margin, k_dg;
@@ -126,6 +129,63 @@ __device__ __forceinline__ bool layered_q(uint32_t n, uint32_t A, unsigned long 
                                           unsigned __int128 Q) {
     const long long d = (long long)n * (long long)A - (long long)S1;
     return d > 0 && (unsigned __int128)d * (unsigned __int128)d > Q;
+}
+
+// ---------------------------------------------------------------------------
+// Exact re-evaluation of distance decisions near their gates.  The FP32
+// distances of the kernels carry rounding of order 2^-24 of the coordinates'
+// magnitudes; when one lies within a bound of that size of its gate, the
+// decision is taken again in FP64, in world coordinates, with the same
+// operations as the FP64 definition (pixel centre unprojected at its depth,
+// x = R^T (p_c - t); camera point p = R x + t), so that the result agrees with
+// it wherever the distance is farther than 1e-6 of the gate from it.
+// ---------------------------------------------------------------------------
+// world centre of a voxel in FP64: plain grids o + n h / 2 (n = 2 idx + 1, so
+// (idx + 1/2) h exactly as one rounding), contracted grids hi + lo
+__device__ __forceinline__ void centre64(const VoxelGeom& vg, const GridC& G, double* x) {
+#pragma unroll
+    for (int q = 0; q < 3; ++q)
+        x[q] = G.contracted ? __dadd_rn((double)vg.xh[q], (double)vg.xl[q])
+                            : __dadd_rn((double)G.origin[q],
+                                        __dmul_rn(__dmul_rn((double)vg.xh[q], 0.5), (double)G.h));
+}
+
+// an FP32 distance d is re-decided when |d - gate| is within this bound: a few
+// thousand units of 2^-24 of the magnitudes it is formed from (world centre,
+// camera translation, camera depth times the largest pixel-ray slope)
+__device__ __forceinline__ float recheck_band(const TViewC& T, const VoxelGeom& vg,
+                                              const GridC& G, float pz) {
+    const ViewC& V = T.base;
+    const float slope = __fadd_rn(2.f, __fadd_rn(__fdiv_rn(fabsf(V.K[2]) + (float)V.W, fabsf(V.K[0])),
+                                                 __fdiv_rn(fabsf(V.K[3]) + (float)V.H, fabsf(V.K[1]))));
+    float mag = 1.f + fabsf(T.t[0]) + fabsf(T.t[1]) + fabsf(T.t[2]) + fabsf(pz) * slope;
+#pragma unroll
+    for (int q = 0; q < 3; ++q)
+        mag += G.contracted ? fabsf(vg.xh[q]) : fabsf(G.origin[q]) + fabsf(vg.xh[q]) * G.h;
+    return __fmul_rn(0x1p-15f, mag);
+}
+
+// squared world distance from the voxel centre x to pixel (px, py) unprojected
+// at planar depth d: R^T (p_c - t) - x, p_c = ((px + 1/2 - cx) / fx d,
+// (py + 1/2 - cy) / fy d, d)
+__device__ __forceinline__ double unproject_d2(const TViewC& T, int px, int py, float d,
+                                               const double* x) {
+    const ViewC& V = T.base;
+    const double dd = (double)d;
+    const double pc[3] = {
+        __dmul_rn(__ddiv_rn(__dsub_rn(__dadd_rn((double)px, 0.5), (double)V.K[2]), (double)V.K[0]), dd),
+        __dmul_rn(__ddiv_rn(__dsub_rn(__dadd_rn((double)py, 0.5), (double)V.K[3]), (double)V.K[1]), dd),
+        dd};
+    double s = 0.0;
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        const double w = __dadd_rn(__dadd_rn(__dmul_rn((double)T.R[r], __dsub_rn(pc[0], (double)T.t[0])),
+                                             __dmul_rn((double)T.R[3 + r], __dsub_rn(pc[1], (double)T.t[1]))),
+                                   __dmul_rn((double)T.R[6 + r], __dsub_rn(pc[2], (double)T.t[2])));
+        const double e = __dsub_rn(w, x[r]);
+        s = __dadd_rn(s, __dmul_rn(e, e));
+    }
+    return s;
 }
 
 // The same test as a threshold on n: with r = floor(sqrt(Q)), d^2 > Q and
@@ -267,6 +327,60 @@ __device__ __forceinline__ bool tuple_candidate(const TViewC& T, const VoxelGeom
     return true;
 }
 
+// One footprint pixel of the thin path: valid (the asymmetric, tightened
+// depth gate against its reference depth dq, d_med not below eps) and the
+// reference depth (d_min for a trusted front pixel, else d_med)
+__device__ __forceinline__ bool thin_pixel_valid(float qmed, float qmin, uint32_t nq, float mean,
+                                                 bool thr, uint32_t n_star, uint32_t A,
+                                                 unsigned long long S1, unsigned __int128 Q,
+                                                 const TViewC& T, const TupleC& TP, const FuseC& F,
+                                                 float pzh, float pzl, float t_full, float& dq) {
+    const float Eq = fmaxf(__fsub_rn((float)nq, mean), 0.f);
+    const float den = __fmaf_rn(TP.beta, Eq, 1.f);
+    const bool lay = thr ? nq >= n_star : layered_q(nq, A, S1, Q);
+    const bool fq = (lay || qmed > T.st_thr) && qmin <= qmed;
+    dq = fq ? qmin : qmed;
+    const float e = __fadd_rn(__fsub_rn(pzh, dq), pzl);
+    const float lhs = fq ? e : fabsf(e);
+    // lhs <= t_full / den, as lhs den <= t_full (den >= 1)
+    return !(qmed < F.eps) && __fmul_rn(lhs, den) <= t_full;
+}
+
+// "mask positive" (m > 1/2; logits l > 0) and the key of loaded mask bits
+template <int kMT>
+__device__ __forceinline__ bool thin_mask_key(const ViewC& V, uint32_t raw, float& key) {
+    if (mask_type_of<kMT>(V) == kMaskF16) {
+        key = __half2float(__ushort_as_half((unsigned short)raw));
+        return key > 0.5f;
+    }
+    key = __uint_as_float(raw);
+    return mask_type_of<kMT>(V) == kMaskLogit ? key > 0.f : key > 0.5f;
+}
+
+// The thin path's nearest squared distance in FP64 (unproject_d2 over the
+// valid mask-positive pixels of the box, the same per-pixel decisions as the
+// FP32 loop): the exact re-evaluation of a distance gate decision.
+template <int kMT>
+__device__ __noinline__ double thin_d2_exact(const TViewC& T, const FuseC& F, const TupleC& TP,
+                                             const double* x, int i0, int i1, int j0, int j1,
+                                             float mean, bool thr, uint32_t n_star, uint32_t A,
+                                             unsigned long long S1, unsigned __int128 Q, float pzh,
+                                             float pzl, float t_full) {
+    const ViewC& V = T.base;
+    double best = INFINITY;
+    for (int yy = j0; yy <= j1; ++yy)
+        for (int xx = i0; xx <= i1; ++xx) {
+            const int32_t q = yy * V.W + xx;
+            float dq, key;
+            const bool valid = thin_pixel_valid(__ldg(T.d_med + q), __ldg(V.depth + q),
+                                                __ldg(T.n_samp + q), mean, thr, n_star, A, S1, Q,
+                                                T, TP, F, pzh, pzl, t_full, dq);
+            if (valid && thin_mask_key<kMT>(V, mask_bits<kMT>(V, q), key))
+                best = fmin(best, unproject_d2(T, xx, yy, dq, x));
+        }
+    return best;
+}
+
 // One view of one voxel, in full: the centre pixel's candidates, the
 // footprint box from the centre's camera rows plus the corners' offsets, its
 // statistics from the integral images or, for views whose footprints are
@@ -276,8 +390,9 @@ __device__ __forceinline__ bool tuple_candidate(const TViewC& T, const VoxelGeom
 // The vote is returned, not added: kind 1 thick (x = m, y = w: W += m w,
 // Z += w), kind 2 thin (x = t: W += t, Z += 1), kind 0 none.
 template <bool kContracted, int kMT = -1>
-__device__ __forceinline__ void tuple_view(const TViewC& T, const VoxelGeom& vg, const FuseC& F,
-                                           const TupleC& TP, int& kind, float& x, float& y) {
+__device__ __forceinline__ void tuple_view(const TViewC& T, const VoxelGeom& vg, const GridC& G,
+                                           const FuseC& F, const TupleC& TP, int& kind, float& x,
+                                           float& y) {
     kind = 0;
     const ViewC& V = T.base;
     const float hv = vg.hv;                       // world edge h_v
@@ -425,25 +540,10 @@ __device__ __forceinline__ void tuple_view(const TViewC& T, const VoxelGeom& vg,
         }
 #pragma unroll
         for (int k = 0; k < kThinGroup; ++k) {
-            const float qmed = gmed[k], qmin = gmin[k];
-            const float Eq = fmaxf(__fsub_rn((float)gn[k], mean), 0.f);
-            const float den = __fmaf_rn(TP.beta, Eq, 1.f);
-            const bool lay = thr ? gn[k] >= n_star : layered_q(gn[k], A, S1, Q);
-            const bool fq = (lay || qmed > T.st_thr) && qmin <= qmed;
-            const float dq = fq ? qmin : qmed;
-            const float e = __fadd_rn(__fsub_rn(pzh, dq), pzl);
-            const float lhs = fq ? e : fabsf(e);
-            // lhs <= t_full / den, as lhs den <= t_full (den >= 1)
-            const bool valid = !(qmed < F.eps) && __fmul_rn(lhs, den) <= t_full;
-            float key;
-            bool hq;
-            if (mask_type_of<kMT>(V) == kMaskF16) {
-                key = __half2float(__ushort_as_half((unsigned short)gm[k]));
-                hq = key > 0.5f;
-            } else {
-                key = __uint_as_float(gm[k]);
-                hq = logit ? key > 0.f : key > 0.5f;
-            }
+            float dq, key;
+            const bool valid = thin_pixel_valid(gmed[k], gmin[k], gn[k], mean, thr, n_star, A, S1,
+                                                Q, T, TP, F, pzh, pzl, t_full, dq);
+            const bool hq = thin_mask_key<kMT>(V, gm[k], key);
             const float ax = __fmul_rn(__fsub_rn((float)gx[k] + 0.5f, V.K[2]), T.inv_fx);
             const float ay = __fmul_rn(__fsub_rn((float)gy[k] + 0.5f, V.K[3]), T.inv_fy);
             const float dx = __fsub_rn(__fmul_rn(ax, dq), px);
@@ -462,9 +562,20 @@ __device__ __forceinline__ void tuple_view(const TViewC& T, const VoxelGeom& vg,
         const float gate = __fmul_rn(TP.dist_gate, hv);
         // the probability of the peak key (the sigmoid is increasing)
         const float m_max = logit ? __frcp_rn(__fadd_rn(1.f, expf(-mkey))) : mkey;
-        if (d2 <= __fmul_rn(gate, gate) && m_max >= TP.tau_thin) {
-            kind = 2;
-            x = m_max;
+        if (m_max >= TP.tau_thin) {
+            bool inside = d2 <= __fmul_rn(gate, gate);
+            if (fabsf(__fsub_rn(__fsqrt_rn(d2), gate)) <=
+                recheck_band(T, vg, G, __fadd_rn(pzh, pzl))) {
+                double xw[3];
+                centre64(vg, G, xw);
+                const double g64 = __dmul_rn((double)TP.dist_gate, (double)hv);
+                inside = thin_d2_exact<kMT>(T, F, TP, xw, i0, i1, j0, j1, mean, thr, n_star, A, S1,
+                                            Q, pzh, pzl, t_full) <= __dmul_rn(g64, g64);
+            }
+            if (inside) {
+                kind = 2;
+                x = m_max;
+            }
         }
     }
 }
@@ -548,8 +659,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_tuple_heavy(
         float x = 0.f, y = 0.f;
         if (live && ((h.y >> l) & 1u)) {
             const VoxelGeom vg = voxel_geom<kContracted>(__ldg(active + h.x), G, F.gamma);
-            tuple_view<kContracted, kMT>(*reinterpret_cast<const TViewC*>(sv + l * kWords), vg, F, TP,
-                                         kind, x, y);
+            tuple_view<kContracted, kMT>(*reinterpret_cast<const TViewC*>(sv + l * kWords), vg, G, F,
+                                         TP, kind, x, y);
         }
         float Ws = 0.f, Zs = 0.f;
         uint32_t b = 0u;
@@ -1092,6 +1203,8 @@ divas_status divas_fuse_add_views_tuple_profiled(divas_ctx* c, const divas_tuple
             t.tile_dil = near ? tj.j[k0 + j].dil : nullptr;
             t.tiles_w = tj.j[k0 + j].tiles_w;
             t.key_thr = thin_key_threshold(v.mask_type, tp->tau_thin);
+            memcpy(t.R, v.cam.R, sizeof(t.R));
+            memcpy(t.t, v.cam.t, sizeof(t.t));
         }
         const int blocks = grid_for(c->cap, c->sm_count);
         const int32_t acc = c->n_views + k0 > 0 ? 1 : 0;

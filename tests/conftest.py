@@ -28,3 +28,31 @@ def pytest_collection_modifyitems(config, items):
     for item in items:
         if "gpu" in item.keywords:
             item.add_marker(skip)
+
+
+def pytest_terminal_summary(terminalreporter):
+    """Near-boundary counts of the parity checks that ran (oracle-flagged items
+    excluded from the exact comparisons), also written to
+    gpurun_out/parity_counts.json (or $DIVAS_PARITY_JSON)."""
+    try:
+        from tests import gpu_helpers
+    except Exception:
+        return
+    rows = gpu_helpers.PARITY
+    if not rows:
+        return
+    import json
+    tr = terminalreporter
+    tr.write_sep("-", "near-boundary items (flagged within 1e-6, excluded from exact checks)")
+    for r in rows:
+        tr.write_line(f"{r['check']}: {r['flagged']} of {r['items']} "
+                      f"({100.0 * r['flagged_frac']:.3f}%), mismatches outside them "
+                      f"{r['mismatches']}")
+    path = os.environ.get("DIVAS_PARITY_JSON",
+                          os.path.join(ROOT, "gpurun_out", "parity_counts.json"))
+    try:
+        os.makedirs(os.path.dirname(path), exist_ok=True)
+        with open(path, "w") as f:
+            json.dump(rows, f, indent=1)
+    except OSError:
+        pass

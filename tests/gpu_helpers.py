@@ -11,6 +11,27 @@ from paper_2601_04860_b300 import FusionParams, VoxelFusion, seg_bits_to_bool
 EXACT_FLAGS = 0xFFFFFFFF  # any near-boundary flag excludes a voxel from exact checks
 RTOL = 1e-5               # scores W, Z, P: relative tolerance in FP32
 
+# near-boundary counts of the parity checks of this session (printed and
+# written to a JSON file by the test session's terminal summary)
+PARITY: list[dict] = []
+
+
+def current_test() -> str:
+    """The running test's id (file::name[params])."""
+    import os
+    return os.environ.get("PYTEST_CURRENT_TEST", "?").split(" ")[0].split("/")[-1]
+
+
+def record(name: str, voxels: int, flagged: int, mismatches: int = 0, **extra) -> dict:
+    """Note one parity check: items compared, items the oracle flags as within
+    1e-6 of a boundary (excluded from the exact checks), mismatches outside
+    them (0 when the check passed)."""
+    row = {"check": name, "items": int(voxels), "flagged": int(flagged),
+           "flagged_frac": float(flagged) / max(1, int(voxels)), "mismatches": int(mismatches)}
+    row.update({k: (int(v) if isinstance(v, (np.integer, int)) else v) for k, v in extra.items()})
+    PARITY.append(row)
+    return row
+
 
 def to_params(p: oracle.Params) -> FusionParams:
     return FusionParams(p.tau_m, p.gamma, p.alpha1, p.tau_cons, p.eps, p.z_near)
@@ -70,10 +91,13 @@ def run_gpu(wl, params: oracle.Params, mode="oneshot", dev_inputs=None, want_pix
     return res
 
 
-def compare(wl, gpu: dict, params: oracle.Params, check_labels=True, sample=None):
+def compare(wl, gpu: dict, params: oracle.Params, check_labels=True, sample=None, name=None,
+            max_flagged=0.01):
     """Element-by-element comparison against the oracle; returns a summary dict.
 
-    ``sample``: optional indices into the active list to compare (full-size runs)."""
+    ``sample``: optional indices into the active list to compare (full-size runs);
+    ``max_flagged``: ceiling of the fraction of near-boundary voxels (flagged by
+    the oracle, excluded from the exact checks)."""
     lin = wl.active_linear()
     g = wl.grid.g
     act = gpu["active"].astype(np.int64)
@@ -87,6 +111,7 @@ def compare(wl, gpu: dict, params: oracle.Params, check_labels=True, sample=None
     ok = ~flagged
     summary = {"voxels": int(len(idx)), "flagged": int(flagged.sum()),
                "voted": int((o["Z"] > 0).sum())}
+    assert flagged.mean() <= max_flagged, ("near-boundary fraction", flagged.mean())
     if "pix" in gpu:
         gp = gpu["pix"][idx]
         assert (gp[ok] == o["pix"][ok]).all(), "voxel-to-pixel indices differ"
@@ -113,6 +138,8 @@ def compare(wl, gpu: dict, params: oracle.Params, check_labels=True, sample=None
         assert abs(gpu["n_seg"] - int(o["seg"].sum())) <= summary["flagged"]
     if check_labels and "labels" in gpu:
         summary.update(compare_labels(wl, gpu, o, lin, idx, flagged, sample))
+    record(name or current_test(), summary["voxels"], summary["flagged"],
+           **{k: v for k, v in summary.items() if k in ("points", "points_excluded")})
     return summary
 
 

@@ -58,7 +58,9 @@ def _gpu(nw, prm, npar, rho, splits=None, with_density=True):
     return out
 
 
-def _compare(nw, got, prm, npar, rho, min_ok=0.9, with_density=True):
+def _compare(nw, got, prm, npar, rho, max_flagged=0.015, with_density=True):
+    """Bits exact, W and Z within RTOL outside the oracle's near-boundary
+    voxels; max_flagged: ceiling of their fraction (1.5 x the measured one)."""
     lin = nw.active_linear()
     g = nw.grid.g
     act = got["active"].astype(np.int64)
@@ -67,7 +69,11 @@ def _compare(nw, got, prm, npar, rho, min_ok=0.9, with_density=True):
                            params=prm.f32(), nparams=npar.f32(),
                            rho=rho[lin].astype(np.float64) if with_density else None)
     ok = ref["flags"] == 0
-    assert ok.mean() > min_ok, ok.mean()
+    bad = ok & ((got["bits"] != ref["bits"]) |
+                ~np.isclose(got["W"], ref["W"], rtol=H.RTOL, atol=1e-30) |
+                ~np.isclose(got["Z"], ref["Z"], rtol=H.RTOL, atol=1e-30))
+    H.record(H.current_test(), len(lin), int((~ok).sum()), int(bad.sum()))
+    assert (~ok).mean() <= max_flagged, (~ok).mean()
     assert np.array_equal(got["bits"][ok], ref["bits"][ok]), "view bits differ"
     assert np.allclose(got["W"][ok], ref["W"][ok], rtol=H.RTOL, atol=1e-30), "W differs"
     assert np.allclose(got["Z"][ok], ref["Z"][ok], rtol=H.RTOL, atol=1e-30), "Z differs"
@@ -116,7 +122,7 @@ def test_nerf_contracted_and_many_views():
     nw, rho = synth.with_nerf_tuple(wl), synth.nerf_density(wl)
     prm, npar = oracle.Params(), oracle.NerfParams.mip360()
     one = _gpu(nw, prm, npar, rho)
-    thick, _ = _compare(nw, one, prm, npar, rho)
+    thick, _ = _compare(nw, one, prm, npar, rho, max_flagged=0.031)
     assert thick > 100
     split = _gpu(nw, prm, npar, rho, splits=[7, 13])
     for k in ("W", "Z", "bits", "score"):
@@ -156,7 +162,7 @@ def test_nerf_large_footprints():
     nw, rho = synth.with_nerf_tuple(wl), synth.nerf_density(wl)
     prm = oracle.Params()
     for npar in (oracle.NerfParams(), oracle.NerfParams(rho_cover=0.05, tau_thin=0.3)):
-        _compare(nw, _gpu(nw, prm, npar, rho), prm, npar, rho, min_ok=0.85)
+        _compare(nw, _gpu(nw, prm, npar, rho), prm, npar, rho, max_flagged=0.01)
 
 
 def test_density_floor_exact_and_ragged():

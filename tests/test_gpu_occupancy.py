@@ -99,7 +99,7 @@ def test_occupancy_feeds_the_fusion():
     d = H.upload(wl2)
     d["occ"] = occ  # the GPU's own occupancy
     got = H.run_gpu(wl2, oracle.Params(), dev_inputs=d, labels=False)
-    s = H.compare(wl2, got, oracle.Params(), check_labels=False)
+    s = H.compare(wl2, got, oracle.Params(), check_labels=False, max_flagged=0.03)
     assert s["voted"] > 100  # a coarse grid (h about 0.038): a few hundred voting voxels
 
 

@@ -34,9 +34,9 @@ def test_config1_full(tau_m):
 def test_config2_reduced():
     wl = synth.config2(g=128, W=504, H=378, n_ell=100, n_points=100_000)
     gpu = H.run_gpu(wl, P0, want_pix=True)
-    s = H.compare(wl, gpu, P0)
+    s = H.compare(wl, gpu, P0, max_flagged=0.0133)  # 1.5 x the measured 0.88%
     _report("config2 g=128", s)
-    assert s["voted"] > 500 and s["flagged"] < 0.02 * s["voxels"]
+    assert s["voted"] > 500
 
 
 def test_config2_soft_consensus():
@@ -50,9 +50,9 @@ def test_config3_reduced():
     wl = synth.config3(g=128, n_views=8, W=648, H=420, n_ell=300, n_occ=None,
                        n_points=100_000)
     gpu = H.run_gpu(wl, P0, want_pix=True)
-    s = H.compare(wl, gpu, P0)
+    s = H.compare(wl, gpu, P0, max_flagged=0.0263)  # 1.5 x the measured 1.75%
     _report("config3 g=128", s)
-    assert s["voted"] > 500 and s["flagged"] < 0.02 * s["voxels"]
+    assert s["voted"] > 500
 
 
 def test_config4_logits_reduced():
@@ -199,22 +199,24 @@ def test_invalid_arguments_are_rejected():
 # full sizes, in the launch configuration the benchmark times
 # ---------------------------------------------------------------------------
 def test_config2_full_size_sampled():
+    MAXF = 0.0285  # 1.5 x the measured 1.9%
     wl = synth.config2()
     gpu = H.run_gpu(wl, P0, want_pix=True)
     rng = np.random.Generator(np.random.PCG64(1))
     sample = np.sort(rng.choice(gpu["n_active"], size=min(150_000, gpu["n_active"]),
                                 replace=False))
-    s = H.compare(wl, gpu, P0, sample=sample)
+    s = H.compare(wl, gpu, P0, sample=sample, max_flagged=MAXF)
     _report("config2 full (sampled)", s)
     assert s["voted"] > 300
 
 
 def test_config3_full_size_sampled():
+    MAXF = 0.079  # 1.5 x the measured 5.2% (16 views: twice the pixel decisions)
     wl = synth.config3()
     gpu = H.run_gpu(wl, P0)
     rng = np.random.Generator(np.random.PCG64(1))
     sample = np.sort(rng.choice(gpu["n_active"], size=100_000, replace=False))
-    s = H.compare(wl, gpu, P0, sample=sample)
+    s = H.compare(wl, gpu, P0, sample=sample, max_flagged=MAXF)
     _report("config3 full (sampled)", s)
     assert s["voted"] > 1000
 

@@ -69,7 +69,9 @@ def test_surfel_labels_match_oracle(mask_type):
     got = _run(wl, mu, sc, q)
     ref = _oracle(wl, mu, sc, q)
     ok = ~ref["excluded"]
-    assert ok.mean() > 0.9, ok.mean()
+    bad = ok & ((got["f2"].astype(bool) != ref["F2"]) | (got["f"].astype(bool) != ref["F"]))
+    H.record(H.current_test(), len(mu), int(ref["excluded"].sum()), int(bad.sum()))
+    assert (~ok).mean() <= 0.011, (~ok).mean()  # 1.5 x the measured fraction
     assert ref["F1"][ok].sum() > 500 and ref["F"][ok].sum() > 100
     assert (ref["F2"][ok] < ref["F1"][ok]).sum() >= 3, "the needle cull removed nothing"
     assert (ref["F"][ok] < ref["F2"][ok]).sum() >= 3, "the coverage cull removed nothing"
@@ -113,7 +115,7 @@ def test_overlay_matches_oracle():
     flagged_cells[lin[o["flags"] != 0]] = True
     g, h = wl.grid.g, np.float64(np.float32(wl.grid.h))
     org = np.asarray(wl.grid.origin, np.float32).astype(np.float64)
-    total = ones = 0
+    total = ones = excluded = 0
     for k, cam in enumerate(wl.cams):
         got = fu.overlay(cam, d["depth"][k]).cpu().numpy()
         ref, fl = S.overlay(wl.grid, seg, cam, wl.depth[k])
@@ -132,6 +134,9 @@ def test_overlay_matches_oracle():
         cl = np.where(inside, (c[:, 2] * g + c[:, 1]) * g + c[:, 0], 0)
         bad = (fl.ravel() != 0) | (inside & flagged_cells[cl])
         ok = ~bad.reshape(Hh, Ww)
+        H.record(f"{H.current_test()} view {k}", Hh * Ww, int(bad.sum()),
+                 int((got[ok] != ref[ok]).sum()), pixels_near_cell_boundary=int((fl != 0).sum()))
+        assert bad.mean() <= 0.0082, bad.mean()  # 1.5 x the largest measured fraction
         assert np.array_equal(got[ok], ref[ok]), f"overlay differs in view {k}"
         total += ok.sum()
         ones += ref[ok].sum()

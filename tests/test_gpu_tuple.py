@@ -49,7 +49,9 @@ def _gpu(tw, prm, tp, splits=None):
     return out
 
 
-def _compare(tw, got, prm, tp, min_ok=0.9):
+def _compare(tw, got, prm, tp, max_flagged=0.026):
+    """Bits exact, W and Z within RTOL outside the oracle's near-boundary
+    voxels; max_flagged: ceiling of their fraction (1.5 x the measured one)."""
     lin = tw.active_linear()
     g = tw.grid.g
     act = got["active"].astype(np.int64)
@@ -57,7 +59,11 @@ def _compare(tw, got, prm, tp, min_ok=0.9):
     ref = oracle.fuse_tuple(tw.grid, lin, tw.cams, tw.tuple, tw.mask, tw.mask_type,
                             params=prm.f32(), tparams=tp.f32())
     ok = ref["flags"] == 0
-    assert ok.mean() > min_ok, ok.mean()
+    bad = ok & ((got["bits"] != ref["bits"]) |
+                ~np.isclose(got["W"], ref["W"], rtol=H.RTOL, atol=1e-30) |
+                ~np.isclose(got["Z"], ref["Z"], rtol=H.RTOL, atol=1e-30))
+    H.record(H.current_test(), len(lin), int((~ok).sum()), int(bad.sum()))
+    assert (~ok).mean() <= max_flagged, (~ok).mean()
     assert np.array_equal(got["bits"][ok], ref["bits"][ok]), "view bits differ"
     assert np.allclose(got["W"][ok], ref["W"][ok], rtol=H.RTOL, atol=1e-30), "W differs"
     assert np.allclose(got["Z"][ok], ref["Z"][ok], rtol=H.RTOL, atol=1e-30), "Z differs"
@@ -106,7 +112,7 @@ def test_tuple_contracted_and_many_views():
     tw = synth.with_tuple(wl, target=(0.0, 0.0, 0.5))
     prm, tp = oracle.Params(), oracle.TupleParams(n_abs=2.0)
     one = _gpu(tw, prm, tp)                 # 20 views: two launches of <= 16
-    thick, _ = _compare(tw, one, prm, tp)
+    thick, _ = _compare(tw, one, prm, tp, max_flagged=0.058)
     assert thick > 100
     split = _gpu(tw, prm, tp, splits=[7, 13])
     for k in ("W", "Z", "bits", "score"):
@@ -201,7 +207,7 @@ def test_tuple_large_footprints_and_wide_counts():
         tw.tuple["n_samp"][k] = np.where(hi, np.uint16(65535), n).astype(np.uint16)
     prm, tp = oracle.Params(), oracle.TupleParams(n_abs=4.0)
     # hundreds of pixels per footprint: more per-pixel gates near a tie
-    thick, thin = _compare(tw, _gpu(tw, prm, tp), prm, tp, min_ok=0.8)
+    thick, thin = _compare(tw, _gpu(tw, prm, tp), prm, tp, max_flagged=0.193)
     assert thick > 20 and thin > 20
 
 
@@ -211,7 +217,7 @@ def test_tuple_32_views_two_launches():
     tw = synth.with_tuple(wl)
     prm, tp = oracle.Params(), oracle.TupleParams(n_abs=2.0)
     got = _gpu(tw, prm, tp)
-    thick, _ = _compare(tw, got, prm, tp)
+    thick, _ = _compare(tw, got, prm, tp, max_flagged=0.056)
     assert thick > 100
     assert (got["bits"] >> 31).any(), "no voxel took a vote from view 31"
 
