@@ -91,6 +91,43 @@ def run_gpu(wl, params: oracle.Params, mode="oneshot", dev_inputs=None, want_pix
     return res
 
 
+def state_of(fu, score: torch.Tensor, labels: torch.Tensor | None = None) -> dict:
+    """A context's fused state in the form compare() takes: W, Z and view bits
+    exported, the given score buffer and point labels (e.g. written by a
+    batched finalize or the server), seg bits / view masks / the seg count from
+    a finalize into scratch buffers (it reads W and Z, it does not change them)."""
+    st = fu.export_state()
+    out = fu.finalize(score=False, seg_bits=True, vmask=True, count=True)
+    res = {"n_active": fu.n_active, "active": fu.active_coords().cpu().numpy(),
+           "score": score.cpu().numpy(),
+           "seg_dense": seg_bits_to_bool(out["seg_bits"], fu.n_cells).cpu().numpy(),
+           "vmask": out["vmask"].cpu().numpy().view(np.uint32), "n_seg": out["n_seg"],
+           "W": st["W"].cpu().numpy(), "Z": st["Z"].cpu().numpy(),
+           "bits": st["bits"].cpu().numpy().view(np.uint32)}
+    if labels is not None:
+        res["labels"] = labels.cpu().numpy()
+    return res
+
+
+def with_views(wl, order):
+    """A shallow copy of a workload whose views are wl's views in ``order``
+    (repeats allowed: a view folded twice votes twice)."""
+    import copy
+    w2 = copy.copy(wl)
+    w2.cams = [wl.cams[i] for i in order]
+    w2.depth = [wl.depth[i] for i in order]
+    w2.mask = [wl.mask[i] for i in order]
+    return w2
+
+
+def sample_of(n: int, k: int, seed: int = 1):
+    """Sorted random sample of k of n active-list positions (all when n <= k)."""
+    if n <= k:
+        return None
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return np.sort(rng.choice(n, size=k, replace=False))
+
+
 def compare(wl, gpu: dict, params: oracle.Params, check_labels=True, sample=None, name=None,
             max_flagged=0.01):
     """Element-by-element comparison against the oracle; returns a summary dict.

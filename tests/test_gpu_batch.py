@@ -98,3 +98,40 @@ def test_autotuner_picks_a_schedule_and_results_hold():
         r = _alone(wl, d)
         assert np.array_equal(fu.export_state()["W"].cpu().numpy(), r["W"])
         fu.close()
+
+
+# the config-5 session mix at full size: the largest dense grid (384^3), two
+# sparse contracted sets, small and mid dense grids; 2-6 views per session at
+# 640x480 .. 1297x840
+FULL_MIX = (3, 21, 49, 56, 9, 0)
+
+
+def test_batched_sessions_match_oracle():
+    """Every session folded by the batched persistent launch (and finalized
+    and labelled by the batched finalize) against the FP64 oracle on sampled
+    voxels: Eq. compact-fusion per session, whatever the mix around it."""
+    mix = synth.session_mix(n_sessions=64, scale=1.0)
+    sess = []
+    for i in FULL_MIX:
+        wl = synth.session_workload(mix[i])
+        sess.append((wl, H.upload(wl)))
+    assert any(wl.grid.contracted for wl, _ in sess) and max(wl.grid.g for wl, _ in sess) == 384
+    fus = [VoxelFusion(wl.grid, occ=d["occ"], coords=d["coords"], params=H.to_params(P0))
+           for wl, d in sess]
+    b = Batch(max_sessions=16, max_views=256)
+    for (wl, d), fu in zip(sess, fus):
+        b.queue(fu, wl.cams, d["depth"], d["mask"], mask_type=wl.mask_type)
+    b.fuse(Schedule(256, 1, 8, 4096))
+    scores = [torch.empty(f.n_cells if f.dense else f.n_active, device="cuda") for f in fus]
+    labs = [torch.empty(len(d["points"]), dtype=torch.uint8, device="cuda") for _, d in sess]
+    b.finalize(scores=scores, points=[d["points"] for _, d in sess], labels=labs)
+    torch.cuda.synchronize()
+    for (wl, d), fu, sc, lab in zip(sess, fus, scores, labs):
+        gpu = H.state_of(fu, sc, lab)
+        s = H.compare(wl, gpu, P0, sample=H.sample_of(fu.n_active, 20_000),
+                      name=f"{H.current_test()} {wl.name} g={wl.grid.g}"
+                           f"{' contracted' if wl.grid.contracted else ''}",
+                      max_flagged=0.06)
+        assert s["voted"] > 0
+        fu.close()
+    b.close()
