@@ -390,6 +390,24 @@ typedef struct {
 divas_status divas_depth_weight(divas_ctx* ctx, const divas_weight_view* views, int32_t n_views,
                                 int32_t mode, float* stats_out, void* stream);
 
+/* The depth-weighted masks of divas_depth_weight folded straight into the
+ * fusion (Sec. 3.4, the weight applied where the vote reads the mask, Eq.
+ * nerf-depthweight / Eqs. depthband, gs-bandpass, then Eqs. gs-depthweight
+ * and vmask): views as for divas_fuse_add_views (1..32, each view's depth
+ * raster D is also the depth the weight reads); every vote reads the mask
+ * probability m at its pixel, gates m~ = m w(D) >= tau_mask and votes with
+ * m~, w from the view's constants found by the same selection passes as
+ * divas_depth_weight.  No weighted raster is written; the accumulators are
+ * bitwise those of divas_depth_weight followed by divas_fuse_add_views of its
+ * FP32 outputs.  prompts (host, n_views entries; may be NULL for
+ * NERF_MINMAX): only n_prompts and prompt_xy are read (in frame of the
+ * view).  stats_out: as for divas_depth_weight.  Errors: DIVAS_E_INVALID
+ * before any launch (bad views, mode or prompts); DIVAS_E_STATE when the
+ * selection scratch would have to grow inside a stream capture. */
+divas_status divas_fuse_add_views_weighted(divas_ctx* ctx, const divas_view* views,
+                                           const divas_weight_view* prompts, int32_t n_views,
+                                           int32_t mode, float* stats_out, void* stream);
+
 /*
  * Occupancy construction from 2DGS surfels (Sec. 3.5 "Occupancy by Morton-
  * scattered opacity"; Appendix "Occupancy grid construction"):

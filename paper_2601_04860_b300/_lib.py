@@ -128,6 +128,9 @@ _SIGS = {
     "divas_default_tuple_params": (DivasTupleParams, []),
     "divas_depth_weight": (ctypes.c_int, [_P, ctypes.POINTER(DivasWeightView), ctypes.c_int32,
                                           ctypes.c_int32, _P, _P]),
+    "divas_fuse_add_views_weighted": (ctypes.c_int, [_P, ctypes.POINTER(DivasView),
+                                                     ctypes.POINTER(DivasWeightView),
+                                                     ctypes.c_int32, ctypes.c_int32, _P, _P]),
     "divas_default_occupancy_params": (DivasOccupancyParams, []),
     "divas_default_surfel_params": (DivasSurfelParams, []),
     "divas_overlay": (ctypes.c_int, [_P, ctypes.POINTER(DivasCamera), _P, _P, _P]),

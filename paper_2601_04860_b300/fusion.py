@@ -375,6 +375,43 @@ class VoxelFusion:
         self._check(self.lib.divas_depth_weight(self._h, arr, n, m, _ptr(st), _stream(stream)))
         return (out, st) if stats else out
 
+    def add_views_weighted(self, cams, depths=None, masks=None, mask_type: int | None = None,
+                           mode: str = "band", prompts=None, logits=False, stats: bool = False,
+                           stream=None):
+        """Fold views with the depth weight of ``depth_weight`` applied where
+        each vote reads the mask (``divas_fuse_add_views_weighted``: no
+        weighted raster is written).  ``cams``: cameras with ``depths`` and
+        ``masks``, or a PreparedViews of at most 32 views; ``mode`` "nerf" or
+        "band"; ``prompts``: per view a list of (x, y) pixels (band).  With
+        ``stats``, returns the (n, 4) float32 tensor of per-view constants."""
+        if isinstance(cams, PreparedViews):
+            if len(cams.chunks) != 1:
+                raise ValueError("add_views_weighted() takes up to 32 views")
+            arr, n = cams.chunks[0]
+            dev = cams._keep[0][0].device
+        else:
+            n = len(cams)
+            if n < 1 or n > L.MAX_VIEWS_PER_CALL:
+                raise ValueError("add_views_weighted() takes 1..32 views")
+            arr = (L.DivasView * n)()
+            for k in range(n):
+                arr[k] = view_c(cams[k], depths[k], masks[k], mask_type, logits)
+            dev = depths[0].device
+        m = {"nerf": L.WEIGHT_NERF_MINMAX, "band": L.WEIGHT_GS_BAND}[mode]
+        pr = (L.DivasWeightView * n)()
+        prompts = prompts if prompts is not None else [[] for _ in range(n)]
+        for k in range(n):
+            pk = list(prompts[k])
+            if len(pk) > L.MAX_PROMPTS:
+                raise ValueError("at most 15 prompts per view")
+            pr[k].n_prompts = len(pk)
+            for q, (x, y) in enumerate(pk):
+                pr[k].prompt_xy[2 * q], pr[k].prompt_xy[2 * q + 1] = int(x), int(y)
+        st = torch.empty((n, 4), dtype=torch.float32, device=dev) if stats else None
+        self._check(self.lib.divas_fuse_add_views_weighted(self._h, arr, pr, n, m, _ptr(st),
+                                                           _stream(stream)))
+        return st
+
     def overlay(self, cam, depth: torch.Tensor, out: torch.Tensor | None = None,
                 stream=None) -> torch.Tensor:
         """The back-projected overlay of a view (``divas_overlay``): uint8 (H,

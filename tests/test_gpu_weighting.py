@@ -183,3 +183,48 @@ def test_weight_rejects_bad_arguments():
     assert L.load().divas_depth_weight(fu.handle, arr, 1, 1, None, None) == 1  # NULL rasters
     assert L.load().divas_depth_weight(fu.handle, arr, 1, 3, None, None) == 1  # bad mode
     fu.close()
+
+
+@pytest.mark.parametrize("mode", ["nerf", "band"])
+@pytest.mark.parametrize("mask_type", [oracle.MASK_F16, oracle.MASK_F32, oracle.MASK_LOGIT_F32])
+def test_weighted_fusion_in_one_pass(mode, mask_type):
+    """The weight folded into the fusion's mask read: the accumulators equal
+    bitwise the two-pass path (weighted FP32 rasters, then add_views), and the
+    result equals the oracle's fusion of its own weighted masks outside the
+    flagged voxels (near-boundary decisions, or a sampled M~ within 1e-6 of the
+    mask gate)."""
+    wl = _wl(mask_type)
+    prm = oracle.Params()
+    pr = synth.prompts(wl)
+    d = H.upload(wl)
+    dm = [_dev_mask(m, mask_type) for m in wl.mask]
+    one = VoxelFusion(wl.grid, occ=d["occ"], params=H.to_params(prm))
+    st1 = one.add_views_weighted(wl.cams, d["depth"], dm, mask_type=mask_type, mode=mode,
+                                 prompts=pr, stats=True)
+    two = VoxelFusion(wl.grid, occ=d["occ"], params=H.to_params(prm))
+    wm, st2 = two.depth_weight(d["depth"], dm, mask_type, mode=mode, prompts=pr, stats=True)
+    two.add_views(wl.cams, d["depth"], wm, mask_type=oracle.MASK_F32)
+    a, b = one.export_state(), two.export_state()
+    for k in ("W", "Z", "bits"):
+        assert torch.equal(a[k], b[k]), k
+    assert torch.equal(st1.nan_to_num(-7.0), st2.nan_to_num(-7.0))
+    got = {k: a[k].cpu().numpy() for k in ("W", "Z")}
+    got["bits"] = a["bits"].cpu().numpy().view(np.uint32)
+    one.close()
+    two.close()
+    ref_m, _ = _oracle_weight(wl.depth, wl.mask, mask_type, mode, pr)
+    ref_m32 = [m.astype(np.float32) for m in ref_m]
+    lin = wl.active_linear()
+    o = oracle.fuse(wl.grid, lin, wl.cams, wl.depth, ref_m32, oracle.MASK_F32, prm, want_pix=True)
+    near = np.zeros(len(lin), bool)
+    for k in range(wl.n_views):
+        p = o["pix"][:, k]
+        v = np.where(p >= 0, ref_m[k].ravel()[np.maximum(p, 0)], 0.0)
+        near |= (p >= 0) & (np.abs(v - prm.tau_m) < 1e-6)
+    ok = (o["flags"] == 0) & ~near
+    bad = ok & ((got["bits"] != o["bits"]) |
+                (np.abs(got["W"].astype(np.float64) - o["W"]) > H.RTOL * np.abs(o["W"]) + 1e-30) |
+                (np.abs(got["Z"].astype(np.float64) - o["Z"]) > H.RTOL * np.abs(o["Z"]) + 1e-30))
+    H.record(H.current_test(), len(lin), int((~ok).sum()), int(bad.sum()))
+    assert (~ok).mean() <= 0.03 and (o["Z"][ok] > 0).sum() > 100
+    assert not bad.any()
