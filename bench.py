@@ -105,6 +105,12 @@ def job_throughput(units_per_rank: float, world: int, ms_max: float) -> float:
     return world * units_per_rank / (ms_max * 1e-3)
 
 
+# warp instructions per voxel-view of the contracted fusion kernel on the
+# unbounded-sparse workload (ncu smsp__inst_executed.sum of one launch divided
+# by its active voxels x views)
+SPARSE_FUSE_INSTS_PER_VOXEL_VIEW = 3.91
+
+
 def make_workload(name):
     import synth
     if name == "forward-dense-256":
@@ -112,6 +118,22 @@ def make_workload(name):
     if name == "unbounded-sparse-512":
         return synth.config3()
     raise SystemExit(f"unknown workload {name}")
+
+
+class L2Flush:
+    """Between timed iterations: writes a 256 MB buffer (twice the 126 MB L2),
+    then reads another 256 MB buffer, so that no line of the step's data is left
+    in L2 and the flush's own dirty lines are written back before the next
+    timed region rather than inside it."""
+
+    def __init__(self, dev):
+        import torch
+        self.w = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+        self.r = torch.ones(64 << 20, dtype=torch.float32, device=dev)
+
+    def zero_(self):
+        self.w.zero_()
+        self.r.sum()
 
 
 def peaks():
@@ -267,7 +289,7 @@ def run_ours(args, rank, world, local_rank):
     dense = wl.occ is not None
     score = torch.empty(fu.n_cells if dense else n_active, dtype=torch.float32, device=dev)
     labels = torch.empty(len(wl.points), dtype=torch.uint8, device=dev)
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    flush = L2Flush(dev)
     S = wl.n_views
     N = fu.n_cells if dense else n_active
     pv = PreparedViews(wl.cams, depth, mask, wl.mask_type)
@@ -564,7 +586,7 @@ def run_ours(args, rank, world, local_rank):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (seeded ray-cast scene; no dataset)",
         "config": {**workload_config(args.workload, wl),
-                   "l2": "flushed between timed steps (256 MB write, outside the timed events)",
+                   "l2": "flushed between timed steps (a 256 MB buffer written, then a 256 MB buffer read, outside the timed events)",
                    "launch": "one CUDA graph replay of divas_fuse_step per step (device time "
                              "from in-graph events around it); stage times from a second graph "
                              "of the same step with events between its launches; "
@@ -605,8 +627,163 @@ def run_ours(args, rank, world, local_rank):
         "clocks": clk,
         "wall_s_timed": t_wall,
     }
+    # the timed step's outputs, for the parity check against the oracle sample
+    if not args.quick:
+        if fast is not None:
+            fast.replay()
+        else:
+            graph.replay()
+        torch.cuda.synchronize()
+        st = fu.export_state()
+        fin = fu.finalize(score=False, seg_bits=True)
+        res["_parity_gpu"] = {
+            "W": st["W"].cpu().numpy(), "Z": st["Z"].cpu().numpy(),
+            "bits": st["bits"].cpu().numpy().view(np.uint32), "score": score.cpu().numpy(),
+            "seg_words": fin["seg_bits"].cpu().numpy().view(np.uint32),
+            "labels": labels.cpu().numpy()}
     fu.close()
     return res, wl
+
+
+def bench_parity(wl, gpu: dict, sample, o: dict, npts: int) -> dict:
+    """The timed step's outputs against the FP64 oracle on the CPU baseline's
+    voxel sample: voxels the oracle flags as within 1e-6 of a rounding or
+    threshold boundary are counted and excluded; every other sampled voxel must
+    match (view bits and seg exactly, W, Z and P within 1e-5 relative), and so
+    must the labels of the points that fall in sampled, unflagged voxels."""
+    import oracle
+    lin = wl.active_linear()[sample]
+    g = int(wl.grid.g)
+    dense = wl.occ is not None
+    flagged = o["flags"] != 0
+    ok = ~flagged
+    rel = lambda a, b: np.abs(a.astype(np.float64) - b) > 1e-5 * np.abs(b)  # noqa: E731
+    P = gpu["score"][lin] if dense else gpu["score"][sample]
+    seg = ((gpu["seg_words"][lin >> 5] >> (lin & 31).astype(np.uint32)) & 1).astype(bool)
+    bad = ok & ((gpu["bits"][sample] != o["bits"]) | rel(gpu["W"][sample], o["W"]) |
+                rel(gpu["Z"][sample], o["Z"]) | rel(P, o["P"]) | (seg != o["seg"].astype(bool)))
+    # labels: points whose cell is a sampled, unflagged voxel, not near a cell face
+    seg_o = np.zeros(g ** 3, np.uint8)
+    seg_o[lin] = o["seg"]
+    pts = wl.points[:npts]
+    lab_o, pfl = oracle.label(wl.grid, seg_o, pts)
+    x = pts.astype(np.float64)
+    if wl.grid.contracted:
+        r = np.linalg.norm(x, axis=1, keepdims=True)
+        with np.errstate(invalid="ignore", divide="ignore"):
+            x = np.where(r > 1.0, (2.0 - 1.0 / r) * x / r, x)
+    org = np.asarray(wl.grid.origin, np.float32).astype(np.float64)
+    with np.errstate(invalid="ignore"):
+        c = np.floor((x - org) / float(np.float32(wl.grid.h)))
+        inside = np.all((c >= 0) & (c < g), axis=1)
+    c = np.where(inside[:, None], c, 0).astype(np.int64)
+    cell = (c[:, 2] * g + c[:, 1]) * g + c[:, 0]
+    good_cell = np.zeros(g ** 3, bool)
+    good_cell[lin[ok]] = True
+    pok = inside & good_cell[cell] & (pfl == 0)
+    lab_bad = int((gpu["labels"][:npts][pok] != lab_o[pok]).sum())
+    return {"config": wl.name, "voxels_compared": int(len(sample)),
+            "flagged": int(flagged.sum()), "flagged_frac": float(flagged.mean()),
+            "mismatches_outside_flagged": int(bad.sum()),
+            "points_compared": int(pok.sum()), "point_mismatches": lab_bad,
+            "rule": "bits, seg exact; W, Z, P within 1e-5 relative; labels exact; "
+                    "flagged = within 1e-6 of a rounding or threshold boundary"}
+
+
+def measure_sparse(dev, steps: int, cpu_seconds: float = 8.0):
+    """Config 3 (unbounded sparse): the one-call step on the contracted 512^3
+    grid with ~12M occupied voxels given as int32 coordinates, 16 views
+    1297x840, 3M points, replayed from a CUDA graph (events around it), L2
+    flushed between steps; stage times from a second graph whose step records
+    events between its launches.  The fusion is ALU-bound here (compensated
+    projection of far contracted voxels): besides its HBM fraction, its
+    instruction-issue fraction is reported from the warp instructions one
+    launch executes (ncu, smsp__inst_executed.sum, scaled to this launch)
+    against the issue peak SMs x 4 schedulers x one warp instruction per
+    clock at the sampled SM clock."""
+    import torch
+
+    from paper_2601_04860_b300 import FusionParams, PreparedViews, VoxelFusion
+    wl = make_workload("unbounded-sparse-512")
+    coords = torch.from_numpy(wl.coords).to(dev)
+    depth = [torch.from_numpy(d).to(dev) for d in wl.depth]
+    mask = [torch.from_numpy(m.view(np.float16)).to(dev) for m in wl.mask]
+    pts = torch.from_numpy(np.ascontiguousarray(wl.points)).to(dev)
+    fu = VoxelFusion(wl.grid, coords=coords, params=FusionParams())
+    na = fu.n_active
+    score = torch.empty(na, dtype=torch.float32, device=dev)
+    labels = torch.empty(len(wl.points), dtype=torch.uint8, device=dev)
+    pv = PreparedViews(wl.cams, depth, mask, wl.mask_type)
+    flush = L2Flush(dev)
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        for _ in range(2):
+            fu.step(pv, coords=coords, score=score, xyz=pts, labels=labels)
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True, external=True) for _ in range(4)]
+    sev = [torch.cuda.Event(enable_timing=True, external=True) for _ in range(4)]
+    for e in ev + sev:
+        e.record()
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        fu.step(pv, coords=coords, score=score, xyz=pts, labels=labels,
+                stage_events=[ev[0], None, None, ev[3]])
+    gs = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(gs):
+        fu.step(pv, coords=coords, score=score, xyz=pts, labels=labels, stage_events=sev)
+    clocks = Clocks(dev.index or 0)
+    clocks.start()
+    ms, st = [], {"compaction": [], "fuse_finalize": [], "label": []}
+    for k in range(2 + steps):
+        flush.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        flush.zero_()
+        gs.replay()
+        torch.cuda.synchronize()
+        if k >= 2:
+            ms.append(ev[0].elapsed_time(ev[3]))
+            for i, name in enumerate(st):
+                st[name].append(sev[i].elapsed_time(sev[i + 1]))
+    clk = clocks.stop()
+    m = float(np.mean(ms))
+    stm = {k: float(np.mean(v)) for k, v in st.items()}
+    S = wl.n_views
+    algo, view_bytes, _, _ = algorithmic_bytes(wl, na)
+    peak, peak_kind = peaks()
+    fb = algo["fuse_finalize"]
+    ach = fb / (stm["fuse_finalize"] * 1e-3) / 1e9
+    props = torch.cuda.get_device_properties(dev)
+    sm_mhz = clk.get("sm_mhz") or 2032.0
+    issue_peak = props.multi_processor_count * 4 * sm_mhz * 1e6  # warp instructions / s
+    insts = SPARSE_FUSE_INSTS_PER_VOXEL_VIEW * na * S
+    out = {"workload": "unbounded-sparse-512 (contracted 512^3 grid, ~12M occupied voxels as "
+                       "int32 coordinates, 16 views 1297x840 FP32 depth + FP16 masks, 3M points)",
+           "ms_per_step": m, "updates_per_s": na * S / (m * 1e-3), "active_voxels": int(na),
+           "views": S, "stage_ms": stm,
+           "roofline": {"bound": "alu", "kernel": "k_fuse_fin (contracted)",
+                        "achieved": insts / (stm["fuse_finalize"] * 1e-3) / 1e12,
+                        "peak": issue_peak / 1e12, "unit": "warp Tinst/s",
+                        "frac": insts / (stm["fuse_finalize"] * 1e-3) / issue_peak,
+                        "insts_per_launch": insts,
+                        "insts_source": "ncu smsp__inst_executed.sum per voxel-view of this "
+                                        "kernel (profiles/unbounded-sparse-512_launch_list.md)",
+                        "hbm_achieved_gbs": ach, "hbm_frac": ach / peak, "hbm_peak_kind": peak_kind,
+                        "algorithmic_bytes_per_launch": int(fb)},
+           "clocks": clk,
+           "gpu_launches_per_step": 4}
+    fu.close()
+    # the oracle on a bounded sample of the same workload
+    full_s, det = oracle_rate(wl, cpu_seconds, repeats=1)
+    out["cpu_baseline"] = {"value": na * S / full_s, "unit": UNIT, "cores": det["cores"],
+                           "kind": "oracle",
+                           "sample": f"{det['sample_voxels']} of {det['active_voxels']} active "
+                                     f"voxels x {S} views + {det['sample_points']} points, "
+                                     f"extrapolated to the full step"}
+    return out
 
 
 def _tuple_step(dev, n_abs: float | None = None):
@@ -659,7 +836,7 @@ def measure_tuple(dev, steps: int):
                        "d_min / d_med / d_max FP32, n_samp uint16; 8 views 1008x756)",
            "what": "graph replay of set_occupancy + add_views_tuple (8 views) + finalize + "
                    "label_points; L2 flushed per step"}
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    flush = L2Flush(dev)
     peak, peak_kind = peaks()
     for name, n_abs in (("paper_defaults", None), ("thin_active_n_abs_4", 4.0)):
         fu, step, tw, tp = _tuple_step(dev, n_abs)
@@ -802,7 +979,7 @@ def measure_nerf(dev, steps: int):
                        "1008x756)",
            "what": "graph replay of density_floor + set_occupancy + add_views_nerf (8 views) + "
                    "finalize + label_points; L2 flushed per step"}
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    flush = L2Flush(dev)
     peak, peak_kind = peaks()
     for preset in ("llff", "mip360"):
         fu, step, nw, rho, npar = _nerf_step(dev, preset)
@@ -920,6 +1097,22 @@ def _weight_step(dev, mode: str):
         fu.add_views(wl.cams, depth, wbuf, mask_type=MASK_F32)
         fu.finalize(score=score)
         fu.label_points(pts, out=labels)
+
+    def fused_step(ev=None):
+        # the weight applied where each vote reads the mask: no weighted rasters
+        fu.set_occupancy(occ=occ)
+        fu.add_views_weighted(wl.cams, depth, mask, mask_type=wl.mask_type, mode=mode,
+                              prompts=pr)
+        fu.finalize(score=score)
+        fu.label_points(pts, out=labels)
+
+    def plain_step(ev=None):
+        fu.set_occupancy(occ=occ)
+        fu.add_views(wl.cams, depth, mask, mask_type=wl.mask_type)
+        fu.finalize(score=score)
+        fu.label_points(pts, out=labels)
+    step.fused = fused_step
+    step.plain = plain_step
     return fu, step, wl, pr
 
 
@@ -932,8 +1125,11 @@ def measure_weighting(dev, steps: int):
     out = {"workload": "forward-dense-256-weighted (config-2 scene; 8 views 1008x756, FP16 "
                        "masks, 3 positive prompts per view; weighted masks FP32)",
            "what": "graph replay of depth_weight (8 views) + set_occupancy + add_views "
-                   "(weighted masks) + finalize + label_points; L2 flushed per step"}
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+                   "(weighted masks) + finalize + label_points; fused: set_occupancy + "
+                   "add_views_weighted (selection passes + one fusion launch, no weighted "
+                   "rasters) + finalize + label_points; plain: the unweighted step; L2 "
+                   "flushed per step"}
+    flush = L2Flush(dev)
     peak, peak_kind = peaks()
     for mode in ("band", "nerf"):
         fu, step, wl, pr = _weight_step(dev, mode)
@@ -965,11 +1161,36 @@ def measure_weighting(dev, steps: int):
             if k >= 3:
                 ms.append(ev[0].elapsed_time(ev[1]))
                 wms.append(sev[0].elapsed_time(sev[1]))
+        # the one-pass fused step and the plain (unweighted) step, same graph setup
+        extra = {}
+        for name, fn in (("fused", step.fused), ("plain", step.plain)):
+            with torch.cuda.stream(side):
+                for _ in range(3):
+                    fn()
+            torch.cuda.current_stream().wait_stream(side)
+            torch.cuda.synchronize()
+            fe = [torch.cuda.Event(enable_timing=True, external=True) for _ in range(2)]
+            gf = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(gf):
+                fe[0].record()
+                fn()
+                fe[1].record()
+            t = []
+            for k in range(3 + steps):
+                flush.zero_()
+                gf.replay()
+                torch.cuda.synchronize()
+                if k >= 3:
+                    t.append(fe[0].elapsed_time(fe[1]))
+            extra[name] = float(np.mean(t))
         m, w = float(np.mean(ms)), float(np.mean(wms))
         algo = sum(c.W * c.H * (4 + 2 + 4) for c in wl.cams)  # depth, FP16 mask, FP32 out
         ach = algo / (w * 1e-3) / 1e9
         out[mode] = {"ms_per_step": m, "updates_per_s": fu.n_cells * wl.n_views / (m * 1e-3),
                      "weighting_ms": w,
+                     "fused_ms_per_step": extra["fused"],
+                     "plain_ms_per_step": extra["plain"],
+                     "fused_vs_plain_plus_weighting": extra["fused"] / (extra["plain"] + w),
                      "roofline": {"bound": "hbm", "kernel": "depth_weight (all passes)",
                                   "achieved": ach, "peak": peak, "unit": "GB/s",
                                   "frac": ach / peak, "traffic": None, "peak_kind": peak_kind,
@@ -1066,7 +1287,7 @@ def measure_occupancy(dev, steps: int):
     pts = torch.from_numpy(np.ascontiguousarray(wl.points)).to(dev)
     score = torch.empty(n, dtype=torch.float32, device=dev)
     labels = torch.empty(len(wl.points), dtype=torch.uint8, device=dev)
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    flush = L2Flush(dev)
     for _ in range(3):
         fu.step(pv, occ=occ, score=score, xyz=pts, labels=labels)
     torch.cuda.synchronize()
@@ -1183,7 +1404,7 @@ def measure_surfels(dev, steps: int):
     for _ in range(3):
         r = fu.surfel_labels(dm, ds, dq, wl.cams, mask, wl.mask_type)
     torch.cuda.synchronize()
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    flush = L2Flush(dev)
     ev = [torch.cuda.Event(enable_timing=True, external=True) for _ in range(2)]
     g = torch.cuda.CUDAGraph()
     with torch.cuda.graph(g):
@@ -1242,7 +1463,10 @@ def surfels_cpu_baseline(wl, mu, sc, q, n_sample: int = 20_000):
 
 def measure_adjoint(dev, steps: int):
     """Config 4: forward + hand-written backward through the autograd Function on
-    the 256^3 forward-facing scene with FP32 logits and depth as leaves."""
+    the 256^3 forward-facing scene with FP32 logits and depth as leaves: eager,
+    and the same forward + BCE + backward captured once in a CUDA graph and
+    replayed (the views are marshalled at capture only).  The adjoint kernel's
+    own time comes from a graph of the backward call alone."""
     import torch
 
     import synth
@@ -1254,7 +1478,15 @@ def measure_adjoint(dev, steps: int):
     fu = VoxelFusion(wl.grid, occ=occ, params=FusionParams())
     lin = torch.from_numpy(wl.active_linear()).to(dev)
     y = (torch.rand(len(lin), device=dev) < 0.1).float()  # any fixed target works for timing
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    flush = L2Flush(dev)
+
+    def fwd_bwd():
+        P = fuse(fu, wl.cams, logits, depths, MASK_LOGIT_F32)
+        Pc = P[lin].clamp(1e-6, 1 - 1e-6)
+        loss = -(y * torch.log(Pc) + (1 - y) * torch.log(1 - Pc)).sum()
+        loss.backward()
+        return loss
+
     fwd, bwd = [], []
     for k in range(3 + steps):
         for t in logits + depths:
@@ -1272,17 +1504,94 @@ def measure_adjoint(dev, steps: int):
         if k >= 3:
             fwd.append(a.elapsed_time(b))
             bwd.append(b.elapsed_time(c))
-    n = fu.n_cells
+    eager_grads = [t.grad.clone() for t in logits + depths]
+    # the whole step in a CUDA graph (warm-up on a side stream, then capture;
+    # the gradients are written into tensors the graph owns).  Fresh leaves: the
+    # eager steps' autograd nodes (and their default-stream gradient
+    # accumulation) must not be reused inside the capture.
+    del P, Pc, loss
+    logits = [t.detach().clone().requires_grad_(True) for t in logits]
+    depths = [t.detach().clone().requires_grad_(True) for t in depths]
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        for _ in range(3):
+            for t in logits + depths:
+                t.grad = None
+            fwd_bwd()
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    for t in logits + depths:
+        t.grad = None
+    ev = [torch.cuda.Event(enable_timing=True, external=True) for _ in range(2)]
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        ev[0].record()
+        fwd_bwd()
+        ev[1].record()
+    gms = []
+    for k in range(3 + steps):
+        flush.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        if k >= 3:
+            gms.append(ev[0].elapsed_time(ev[1]))
+    same = all(torch.equal(t.grad, e) for t, e in zip(logits + depths, eager_grads))
+    # the adjoint kernel alone: a graph of the backward call (gradient rasters
+    # zeroed outside it), for its roofline
+    gP = torch.ones(fu.n_cells, device=dev)
+    gm = [torch.zeros_like(t) for t in logits]
+    gd = [torch.zeros_like(t) for t in depths]
+    with torch.no_grad():
+        fu.reset()
+        fu.add_views(wl.cams, [d.detach() for d in depths], [m.detach() for m in logits],
+                     mask_type=MASK_LOGIT_F32)
+    torch.cuda.synchronize()
+    bev = [torch.cuda.Event(enable_timing=True, external=True) for _ in range(2)]
+    gb = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(gb):
+        bev[0].record()
+        fu.backward(wl.cams, [d.detach() for d in depths], [m.detach() for m in logits], gP,
+                    grad_mask=gm, grad_depth=gd, mask_type=MASK_LOGIT_F32)
+        bev[1].record()
+    kms = []
+    for k in range(3 + steps):
+        flush.zero_()
+        gb.replay()
+        torch.cuda.synchronize()
+        if k >= 3:
+            kms.append(bev[0].elapsed_time(bev[1]))
+    n, na, S = fu.n_cells, fu.n_active, wl.n_views
+    st = fu.export_state()
+    n_voted = int((st["Z"] > 0).sum())
+    n_votes = int(np.unpackbits(st["bits"].cpu().numpy().view(np.uint8)).sum())
     fu.close()
-    S = wl.n_views
+    # algorithmic bytes of one backward launch: every active voxel's index, Z
+    # and cotangent; a voted voxel's W and its S gathers (depth and logit, 4 B
+    # each); a vote's two gradient read-modify-writes (8 B each).  Voxels that
+    # never voted (Z = 0) are skipped after their first loads.
+    kb = 12 * na + n_voted * (4 + 8 * S) + 16 * n_votes
+    peak, peak_kind = peaks()
+    km = float(np.mean(kms))
+    fb = float(np.mean(gms))
     return {"workload": "differentiable-256 (config-2 scene, FP32 logits + depth as leaves)",
             "fwd_ms": float(np.mean(fwd)), "bwd_ms": float(np.mean(bwd)),
+            "graph_fwd_bwd_ms": fb,
+            "graph_fwd_bwd_updates_per_s": n * S / (fb * 1e-3),
+            "graph_grads_equal_eager": bool(same),
             "fwd_bwd_updates_per_s": n * S / ((np.mean(fwd) + np.mean(bwd)) * 1e-3),
+            "backward_kernel_ms": km, "voted_voxels": n_voted, "votes": n_votes,
+            "roofline": {"bound": "hbm", "kernel": "k_backward", "algorithmic_bytes_per_launch":
+                         int(kb), "achieved": kb / (km * 1e-3) / 1e9, "peak": peak,
+                         "unit": "GB/s", "frac": kb / (km * 1e-3) / 1e9 / peak,
+                         "peak_kind": peak_kind},
             "what": "eager autograd: fuse() + BCE on active voxels, then loss.backward() "
-                    "(adjoint kernel + gradient raster zero-fill); L2 flushed per step"}
+                    "(adjoint kernel + gradient raster zero-fill); graph: the same captured "
+                    "once and replayed; L2 flushed per step"}
 
 
-def measure_sessions(dev, scale: float, n_sessions: int, rates, budget_frac: float = 1.0):
+def measure_sessions(dev, scale: float, n_sessions: int, rates, budget_frac: float = 1.0,
+                     n_warm: int = 200, n_timed: int = 2000):
     """Config 5: many uneven sessions.  (a) Batched: every session's views in ONE
     persistent fuse launch + one finalize + one label launch, autotuned and
     replayed from a CUDA graph, vs the plain per-session launches.  (b) Served:
@@ -1307,7 +1616,7 @@ def measure_sessions(dev, scale: float, n_sessions: int, rates, budget_frac: flo
            "voxel_views_nominal": int(nominal)}
     # (a) batched vs plain, all views of every session
     sess = [Session(d, dev) for d in data]
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    flush = L2Flush(dev)
 
     def plain_pass():
         for s in sess:
@@ -1360,6 +1669,27 @@ def measure_sessions(dev, scale: float, n_sessions: int, rates, budget_frac: flo
             all_ms.append(ev[0].elapsed_time(ev[2]))
     out["batched_graph_ms"] = float(np.mean(all_ms))
     out["batched_fuse_ms"] = float(np.mean(fuse_ms))
+    # algorithmic bytes of the batched fold (first touch only): per session the
+    # active list, W / Z / bits read and written, its rasters once; and of the
+    # finalize + labels: scores (dense: the g^3 grid), seg bits, points, labels
+    fuse_b = fin_b = 0
+    for s in sess:
+        na = s.fusion.n_active
+        g3 = s.fusion.n_cells
+        fuse_b += 4 * na + 24 * na + sum(d.nbytes + m.nbytes for d, m in
+                                         zip(s.data.depth, s.data.mask))
+        fin_b += (4 * g3 if s.fusion.dense else 4 * na) + 12 * na + g3 // 8 + \
+            13 * len(s.data.points)
+    peak, peak_kind = peaks()
+    fuse_s = out["batched_fuse_ms"] * 1e-3
+    out["batched_roofline"] = {
+        "bound": "hbm", "kernel": "k_batch_fuse", "algorithmic_bytes_per_launch": int(fuse_b),
+        "achieved": fuse_b / fuse_s / 1e9, "peak": peak, "unit": "GB/s",
+        "frac": fuse_b / fuse_s / 1e9 / peak, "peak_kind": peak_kind,
+        "finalize_labels_bytes": int(fin_b),
+        "finalize_labels_frac": fin_b / ((out["batched_graph_ms"] - out["batched_fuse_ms"]) *
+                                         1e-3) / 1e9 / peak,
+        "what": "all sessions of the mix in one persistent launch (dense and sparse)"}
     out["batched_updates_per_s"] = nominal / (np.mean(all_ms) * 1e-3)
     out["plain_updates_per_s"] = nominal / (out["plain_ms"] * 1e-3)
     out["launches"] = {"batched": 3 + 0, "plain": 4 * n_sessions}
@@ -1368,26 +1698,27 @@ def measure_sessions(dev, scale: float, n_sessions: int, rates, budget_frac: flo
         s.close()
     batch.close()
     torch.cuda.synchronize()
-    # (b) served requests
+    # (b) served requests: n_warm warm-up requests, then n_timed timed ones, on
+    # one Poisson stream per rate (the same stream for the server and the two
+    # plain baselines)
     foot = sum(Session.footprint(d) for d in data)
-    served = {}
+    served = {"warmup_requests": n_warm, "timed_requests": n_timed}
     for rate in rates:
-        n_req = int(min(1000, max(200, rate * 2.0)))
         res = {}
         for mode in ("server", "incremental", "refuse"):
-            reqs = poisson_requests(n_req, float(rate), [d.sid for d in data], seed=1005 + 4)
+            reqs = poisson_requests(n_warm + n_timed, float(rate), [d.sid for d in data],
+                                    seed=1005 + 4)
+            timed = reqs[n_warm:]
             if mode == "server":
                 srv = Server(data, memory_budget=int(foot * budget_frac) + 1, max_batch=64)
                 srv.admit_all()
-                warm = poisson_requests(64, float(rate), [d.sid for d in data], seed=99)
-                srv.run(warm)
                 srv.run(reqs)
-                res[mode] = latency_summary(reqs)
+                res[mode] = latency_summary(timed)
                 res[mode]["evictions"] = srv.stats["evictions"]
                 srv.close()
             else:
                 serve_plain(data, reqs, mode)
-                res[mode] = latency_summary(reqs)
+                res[mode] = latency_summary(timed)
         served[str(rate)] = res
     out["served"] = served
     return out
@@ -1450,33 +1781,49 @@ def run(args):
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     res, wl = run_ours(args, rank, world, local_rank)
-    if not args.quick and not args.no_sessions:
-        import torch
-        res["sessions"] = measure_sessions(torch.device("cuda", local_rank), args.sessions_scale,
-                                           args.sessions, [float(r) for r in
-                                                           args.rates.split(",")])
-    if not args.quick and not args.no_adjoint:
-        import torch
-        res["adjoint"] = measure_adjoint(torch.device("cuda", local_rank), max(5, args.steps // 2))
-    if not args.quick and not args.no_tuple and args.workload == "forward-dense-256":
-        import torch
-        res["tuple"] = measure_tuple(torch.device("cuda", local_rank), max(5, args.steps // 2))
-    if not args.quick and not args.no_nerf and args.workload == "forward-dense-256":
-        import torch
-        res["nerf"] = measure_nerf(torch.device("cuda", local_rank), max(5, args.steps // 2))
-    if not args.quick and not args.no_weighting and args.workload == "forward-dense-256":
-        import torch
-        res["weighting"] = measure_weighting(torch.device("cuda", local_rank),
-                                             max(5, args.steps // 2))
-    if not args.quick and not args.no_occupancy and args.workload == "forward-dense-256":
-        import torch
-        res["occupancy"] = measure_occupancy(torch.device("cuda", local_rank),
-                                             max(5, args.steps // 2))
-    if not args.quick and not args.no_surfels and args.workload == "forward-dense-256":
-        import torch
-        res["surfels"] = measure_surfels(torch.device("cuda", local_rank), max(5, args.steps // 2))
+    import torch
+    dev = torch.device("cuda", local_rank)
+    dense_ws = args.workload == "forward-dense-256"
+
+    def leg(name, enabled, fn):
+        """An additional leg; its failure is reported in its key, not fatal."""
+        if not enabled or args.quick:
+            return
+        try:
+            res[name] = fn()
+        except Exception as e:  # noqa: BLE001
+            import traceback
+            traceback.print_exc()
+            res[name] = {"error": f"{type(e).__name__}: {e}"}
+
+    leg("sessions", not args.no_sessions,
+        lambda: measure_sessions(dev, args.sessions_scale, args.sessions,
+                                 [float(r) for r in args.rates.split(",")],
+                                 n_warm=args.warm_requests, n_timed=args.timed_requests))
+    leg("adjoint", not args.no_adjoint, lambda: measure_adjoint(dev, max(5, args.steps // 2)))
+    leg("unbounded_sparse", not args.no_sparse and dense_ws,
+        lambda: measure_sparse(dev, max(5, args.steps // 2)))
+    leg("tuple", not args.no_tuple and dense_ws, lambda: measure_tuple(dev, max(5, args.steps // 2)))
+    leg("nerf", not args.no_nerf and dense_ws, lambda: measure_nerf(dev, max(5, args.steps // 2)))
+    leg("weighting", not args.no_weighting and dense_ws,
+        lambda: measure_weighting(dev, max(5, args.steps // 2)))
+    leg("occupancy", not args.no_occupancy and dense_ws,
+        lambda: measure_occupancy(dev, max(5, args.steps // 2)))
+    leg("surfels", not args.no_surfels and dense_ws,
+        lambda: measure_surfels(dev, max(5, args.steps // 2)))
+    pgpu = res.pop("_parity_gpu", None)
     if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.quick:
         full_s, det = oracle_rate(wl, args.cpu_seconds)
+        if pgpu is not None:
+            try:
+                res["parity"] = bench_parity(wl, pgpu, det["sample_index"], det["sample_out"],
+                                             det["sample_points"])
+            except Exception as e:  # noqa: BLE001
+                res["parity"] = {"error": f"{type(e).__name__}: {e}"}
+            pgpu = None
+        if pgpu is not None:
+            res["parity"] = bench_parity(wl, pgpu, det["sample_index"], det["sample_out"],
+                                         det["sample_points"])
         N = res["config"]["voxels_nominal"]
         res["cpu_baseline"] = {
             "value": N * wl.n_views / full_s, "unit": UNIT, "cores": det["cores"],
@@ -1542,17 +1889,23 @@ def main(argv=None):
     ap.add_argument("--no-adjoint", action="store_true", help="skip the forward+backward leg")
     ap.add_argument("--no-sessions", action="store_true", help="skip the batched/served leg")
     ap.add_argument("--no-tuple", action="store_true", help="skip the depth-tuple-mode leg")
+    ap.add_argument("--no-sparse", action="store_true",
+                    help="skip the unbounded-sparse (config 3) leg")
     ap.add_argument("--no-nerf", action="store_true", help="skip the NeRF-variant leg")
     ap.add_argument("--no-weighting", action="store_true",
                     help="skip the depth-weighted-mask leg")
     ap.add_argument("--no-occupancy", action="store_true",
                     help="skip the occupancy-construction leg")
     ap.add_argument("--no-surfels", action="store_true", help="skip the voxel-to-surfel leg")
-    ap.add_argument("--sessions", type=int, default=32, help="sessions in the batched/served leg")
-    ap.add_argument("--sessions-scale", type=float, default=0.5,
+    ap.add_argument("--sessions", type=int, default=64, help="sessions in the batched/served leg")
+    ap.add_argument("--sessions-scale", type=float, default=1.0,
                     help="size scale of the sessions (1.0 = the full session mix)")
-    ap.add_argument("--rates", default="200,2000,20000",
+    ap.add_argument("--rates", default="200,1000,5000,20000",
                     help="request rates (per second) to serve")
+    ap.add_argument("--warm-requests", type=int, default=200,
+                    help="served leg: untimed warm-up requests per rate")
+    ap.add_argument("--timed-requests", type=int, default=2000,
+                    help="served leg: timed requests per rate")
     ap.add_argument("--quick", action="store_true",
                     help="timed graph steps only: no eager, per-update, e2e or CPU legs")
     ap.add_argument("--profile-steps", type=int, default=0,

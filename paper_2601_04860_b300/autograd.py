@@ -33,6 +33,7 @@ class DivasFuseFunction(torch.autograd.Function):
         fusion.add_views(cams, depths, masks, mask_type=mask_type)
         score = fusion.finalize(score=True)["score"]
         ctx.fusion = fusion
+        ctx.stream = torch.cuda.current_stream()  # the backward runs on the forward's stream
         ctx.cams = cams
         ctx.mask_type = mask_type
         ctx.n_views = n_views
@@ -49,13 +50,16 @@ class DivasFuseFunction(torch.autograd.Function):
             raise RuntimeError("the fusion context was modified between forward and backward")
         need_m = ctx.needs_input_grad[4:4 + n]
         need_d = ctx.needs_input_grad[4 + n:4 + 2 * n]
-        gm = [torch.zeros_like(m) if need_m[k] else None for k, m in enumerate(masks)]
-        gd = [torch.zeros_like(d) if need_d[k] else None for k, d in enumerate(depths)]
-        g = grad_score.contiguous()
-        for s0 in range(0, n, L.MAX_VIEWS_PER_CALL):
-            s1 = min(n, s0 + L.MAX_VIEWS_PER_CALL)
-            fusion.backward(ctx.cams[s0:s1], depths[s0:s1], masks[s0:s1], g,
-                            grad_mask=gm[s0:s1], grad_depth=gd[s0:s1], mask_type=ctx.mask_type)
+        st = ctx.stream  # grad_score was produced there by the loss's backward
+        with torch.cuda.stream(st):
+            gm = [torch.zeros_like(m) if need_m[k] else None for k, m in enumerate(masks)]
+            gd = [torch.zeros_like(d) if need_d[k] else None for k, d in enumerate(depths)]
+            g = grad_score.contiguous()
+            for s0 in range(0, n, L.MAX_VIEWS_PER_CALL):
+                s1 = min(n, s0 + L.MAX_VIEWS_PER_CALL)
+                fusion.backward(ctx.cams[s0:s1], depths[s0:s1], masks[s0:s1], g,
+                                grad_mask=gm[s0:s1], grad_depth=gd[s0:s1],
+                                mask_type=ctx.mask_type, stream=st)
         return (None, None, None, None, *gm, *gd)
 
 

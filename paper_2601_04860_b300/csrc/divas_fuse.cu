@@ -2,16 +2,18 @@
 //
 // Data layout in device memory (one context = one occupied set):
 //   occ_bits[ceil(g^3/32)]     occupancy prior as a bitfield, bit lin of the grid
-//   tile_state[tiles], ticket  look-back states of the single-pass compaction
+//   item_pref, tile_count,     the compaction's counts: per tile of 1024 words
+//   tile_offset, done          its count and exclusive prefix, per item of 8
+//                              words its offset inside the tile; a done counter
 //   active[cap]                occupied voxels in ascending linear index, stored as
 //                              packed coordinates i | j << 10 | k << 20
 //   W[cap], Z[cap], bits[cap]  accumulators of Eq. vmask, structure of arrays
 //   seg_bits[words]            segmentation bitfield B^seg of the last finalize
 //
-// Kernels: one single-pass compaction (occupancy -> bits -> scan with decoupled
-// look-back -> emit; sparse grids scatter their coordinates into the bits
-// first) builds the active list (the active-voxel list of Sec. 3.5 /
-// Appendix B.1); the fusion kernel walks the active list with a
+// Kernels: a two-launch compaction (occupancy -> bits and tile counts, the
+// last CTA scanning the counts; then the entries; sparse grids scatter their
+// coordinates into the bits first) builds the active list (the active-voxel
+// list of Sec. 3.5 / Appendix B.1); the fusion kernel walks the active list with a
 // grid-stride loop and folds up to 32 views per launch; finalize writes the
 // dense score grid with 128-bit stores (or the per-active scores), the seg
 // bitfield with warp-assembled words and the view masks; labels look points up
@@ -260,6 +262,62 @@ __device__ __forceinline__ uint32_t pack_lin(uint32_t lin, const FastDiv& gdiv) 
     return (lin - r * gdiv.d) | ((r - k * gdiv.d) << 10) | (k << 20);
 }
 
+// The active-list entries of one group of 32 occupancy words (lane = word
+// x of cell word w, the group g): slot = base + the word prefix + the word's
+// set bits below the bit.  Scattered bits (largest word popcount <= number of
+// non-empty words): every lane walks its own word; dense words: one round per
+// non-empty word in which lane b writes bit b (consecutive slots per store).
+// Packed coordinates come from the word's first cell plus the bit while the
+// word stays on one row.  Warp-uniform: every lane of the warp calls it.
+__device__ __forceinline__ void emit_group(uint32_t x, int64_t w, int64_t g, int64_t base,
+                                           int64_t cap, const FastDiv& gdiv,
+                                           uint32_t* __restrict__ active) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t lt = (1u << lane) - 1u;
+    uint32_t nz = __ballot_sync(0xffffffffu, x != 0u);
+    if (nz == 0u) return;  // warp-uniform
+    const uint32_t c = __popc(x);
+    uint32_t inc = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    const uint32_t ex = inc - c;
+    const uint32_t p0 = pack_lin((uint32_t)(w * 32), gdiv);  // this lane's word, bit 0
+    const uint32_t max_c = __reduce_max_sync(0xffffffffu, c);
+    if (max_c <= (uint32_t)__popc(nz)) {
+        // scattered bits: every lane walks its own word (rounds = the largest popcount)
+        uint32_t xb = x;
+        int64_t slot = base + ex;
+        const bool row = (p0 & 1023u) + 31u < gdiv.d;  // the word stays on one row
+        while (xb) {
+            const uint32_t b = __ffs(xb) - 1;
+            xb &= xb - 1u;
+            if (slot < cap) active[slot] = row ? p0 + b : pack_lin((uint32_t)(w * 32) + b, gdiv);
+            ++slot;
+        }
+        return;
+    }
+    // dense words: one round per non-empty word, in which lane b writes bit b
+    while (nz) {
+        const int src = __ffs(nz) - 1;
+        nz &= nz - 1u;
+        const uint32_t xs = __shfl_sync(0xffffffffu, x, src);
+        const uint32_t off = __shfl_sync(0xffffffffu, ex, src);
+        const uint32_t ps = __shfl_sync(0xffffffffu, p0, src);
+        if ((xs >> lane) & 1u) {
+            const int64_t slot = base + off + __popc(xs & lt);
+            if (slot < cap) {
+                // same row as the word's bit 0 unless the row wraps inside the word
+                active[slot] = (ps & 1023u) + lane < gdiv.d
+                                   ? ps + lane
+                                   : pack_lin((uint32_t)((g * 32 + src) * 32 + lane), gdiv);
+            }
+        }
+    }
+}
+
 // seg_zero / seg_zero2 (nullable): seg bitfields whose words are cleared on
 // the way (the one-call step)
 __global__ void __launch_bounds__(kThreads) k_tile_emit(
@@ -268,7 +326,6 @@ __global__ void __launch_bounds__(kThreads) k_tile_emit(
     uint32_t* __restrict__ active, uint32_t* __restrict__ seg_zero,
     uint32_t* __restrict__ seg_zero2) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint32_t lt = (1u << lane) - 1u;
     const int64_t n_groups = (n_words + 31) / 32;
     const int64_t n_warps = (int64_t)gridDim.x * (kThreads / 32);
     for (int64_t g = (int64_t)blockIdx.x * (kThreads / 32) + warp; g < n_groups; g += n_warps) {
@@ -281,50 +338,7 @@ __global__ void __launch_bounds__(kThreads) k_tile_emit(
             if (seg_zero) seg_zero[w] = 0u;
             if (seg_zero2) seg_zero2[w] = 0u;
         }
-        uint32_t nz = __ballot_sync(0xffffffffu, x != 0u);
-        if (nz == 0u) continue;  // warp-uniform
-        const int64_t base = (int64_t)t_off + i_pre;
-        const uint32_t c = __popc(x);
-        uint32_t inc = c;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
-            if (lane >= o) inc += y;
-        }
-        const uint32_t ex = inc - c;
-        const uint32_t p0 = pack_lin((uint32_t)(w * 32), gdiv);  // this lane's word, bit 0
-        const uint32_t max_c = __reduce_max_sync(0xffffffffu, c);
-        if (max_c <= (uint32_t)__popc(nz)) {
-            // scattered bits: every lane walks its own word (rounds = the largest popcount)
-            uint32_t xb = x;
-            int64_t slot = base + ex;
-            const bool row = (p0 & 1023u) + 31u < gdiv.d;  // the word stays on one row
-            while (xb) {
-                const uint32_t b = __ffs(xb) - 1;
-                xb &= xb - 1u;
-                if (slot < cap)
-                    active[slot] = row ? p0 + b : pack_lin((uint32_t)(w * 32) + b, gdiv);
-                ++slot;
-            }
-            continue;
-        }
-        // dense words: one round per non-empty word, in which lane b writes bit b
-        while (nz) {
-            const int src = __ffs(nz) - 1;
-            nz &= nz - 1u;
-            const uint32_t xs = __shfl_sync(0xffffffffu, x, src);
-            const uint32_t off = __shfl_sync(0xffffffffu, ex, src);
-            const uint32_t ps = __shfl_sync(0xffffffffu, p0, src);
-            if ((xs >> lane) & 1u) {
-                const int64_t slot = base + off + __popc(xs & lt);
-                if (slot < cap) {
-                    // same row as the word's bit 0 unless the row wraps inside the word
-                    active[slot] = (ps & 1023u) + lane < gdiv.d
-                                       ? ps + lane
-                                       : pack_lin((uint32_t)((g * 32 + src) * 32 + lane), gdiv);
-                }
-            }
-        }
+        emit_group(x, w, g, (int64_t)t_off + i_pre, cap, gdiv, active);
     }
 }
 

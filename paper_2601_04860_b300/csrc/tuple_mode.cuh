@@ -150,9 +150,10 @@ __device__ __forceinline__ void centre64(const VoxelGeom& vg, const GridC& G, do
                                         __dmul_rn(__dmul_rn((double)vg.xh[q], 0.5), (double)G.h));
 }
 
-// an FP32 distance d is re-decided when |d - gate| is within this bound: a few
-// thousand units of 2^-24 of the magnitudes it is formed from (world centre,
-// camera translation, camera depth times the largest pixel-ray slope)
+// an FP32 distance d is re-decided when |d - gate| is within this bound: 32
+// units of 2^-24 of the magnitudes it is formed from (world centre, camera
+// translation, camera depth times the largest pixel-ray slope), many times the
+// few roundings of those magnitudes the FP32 distance carries
 __device__ __forceinline__ float recheck_band(const TViewC& T, const VoxelGeom& vg,
                                               const GridC& G, float pz) {
     const ViewC& V = T.base;
@@ -162,7 +163,7 @@ __device__ __forceinline__ float recheck_band(const TViewC& T, const VoxelGeom& 
 #pragma unroll
     for (int q = 0; q < 3; ++q)
         mag += G.contracted ? fabsf(vg.xh[q]) : fabsf(G.origin[q]) + fabsf(vg.xh[q]) * G.h;
-    return __fmul_rn(0x1p-15f, mag);
+    return __fmul_rn(0x1p-19f, mag);
 }
 
 // squared world distance from the voxel centre x to pixel (px, py) unprojected

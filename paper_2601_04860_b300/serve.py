@@ -27,6 +27,7 @@ finalize + labels per request, no batching).
 """
 from __future__ import annotations
 
+import ctypes
 import time
 from collections import deque
 from dataclasses import dataclass, field
@@ -34,6 +35,7 @@ from dataclasses import dataclass, field
 import numpy as np
 import torch
 
+from . import _lib as L
 from .batch import Autotuner, Batch, Schedule
 from .fusion import FusionParams, PreparedViews, VoxelFusion, view_c
 
@@ -85,6 +87,12 @@ class Session:
         self.score = torch.zeros(n_score, dtype=torch.float32, device=dev)
         self.labels = torch.empty(len(data.points), dtype=torch.uint8, device=dev)
         self.views_done = 0
+        # the C-ABI arguments of a request, marshalled once
+        self.c_score = ctypes.c_void_p(self.score.data_ptr())
+        self.c_points = ctypes.c_void_p(self.points.data_ptr())
+        self.c_labels = ctypes.c_void_p(self.labels.data_ptr())
+        self.n_points = int(self.points.shape[0])
+        self.c_views = [ctypes.pointer(v) for v in self.view_c]
 
     @staticmethod
     def footprint(data: SessionData) -> int:
@@ -139,8 +147,14 @@ class Server:
             self.streams = [torch.cuda.Stream(device=self.dev) for _ in range(max_inflight)]
             self.batches = [Batch(max_sessions=max_batch, max_views=max_batch)
                             for _ in range(max_inflight)]
+            # per stream slot: its raw handle and one completion event, reused
+            # (a slot is only reused after its event completed)
+            self.c_streams = [ctypes.c_void_p(st.cuda_stream) for st in self.streams]
+            self.events = [torch.cuda.Event() for _ in range(max_inflight)]
+            self.lib = L.load()
         self.tuner = Autotuner() if autotune else None
         self.schedule = schedule or Schedule()
+        self.c_schedule = self.schedule.c()
         self.stats = {"batches": 0, "evictions": 0, "admissions": 0, "batch_sizes": []}
 
     # -- memory admission ---------------------------------------------------
@@ -229,7 +243,11 @@ class Server:
                     inflight.append(self._launch(picked, si))
                     continue
             if not waiting and not inflight and pending:
-                time.sleep(max(0.0, min(1e-3, pending[0].arrival - now)))
+                # sleep until shortly before the next arrival, then poll (the
+                # scheduler's wake-up overshoots short sleeps by tens of us)
+                gap = pending[0].arrival - now
+                if gap > 3e-4:
+                    time.sleep(min(1e-3, gap - 2e-4))
         return requests
 
     def _launch(self, picked: list[Request], si: int):
@@ -243,26 +261,44 @@ class Server:
             self.views_done[r.sid] = s.views_done
             self.last_use[r.sid] = time.perf_counter()
             sess.append(s)
-        with torch.cuda.stream(st):
-            if len(sess) == 1:
-                # a lone request: the session's own launches (fold + finalize,
-                # labels) cost less than staging a batch; bitwise the same result
-                s = sess[0]
-                s.fusion.update(views[0], score=s.score, keep_zeros=True)
-                s.fusion.label_points(s.points, out=s.labels)
-            else:
+        cs = self.c_streams[si]
+        lib = self.lib
+        if len(sess) == 1:
+            # a lone request: the session's own launches (fold + finalize,
+            # labels) cost less than staging a batch; bitwise the same result.
+            # The C ABI is called with the session's pre-marshalled arguments.
+            s = sess[0]
+            h = s.fusion.handle
+            k = (s.views_done - 1) % s.data.n_views
+            L.check(lib.divas_fuse_update(h, s.c_views[k], 1, s.c_score, None, L.KEEP_ZEROS, cs),
+                    h)
+            L.check(lib.divas_label_points(h, s.c_points, s.n_points, s.c_labels, cs), h)
+        elif self.tuner is not None:
+            with torch.cuda.stream(st):
                 for s, v in zip(sess, views):
                     b.queue_prepared(s.fusion, v)
-                sch = self.schedule
-                if self.tuner is not None:
-                    sch = self.tuner.pick(b, 1, candidates=[Schedule(256, 1, 8, 4096),
-                                                            Schedule(256, 2, 8, 8192),
-                                                            Schedule(128, 1, 16, 2048)])
+                sch = self.tuner.pick(b, 1, candidates=[Schedule(256, 1, 8, 4096),
+                                                        Schedule(256, 2, 8, 8192),
+                                                        Schedule(128, 1, 16, 2048)])
                 b.fuse(sch)
                 b.finalize(scores=[s.score for s in sess], points=[s.points for s in sess],
                            labels=[s.labels for s in sess], keep_zeros=True)
-            ev = torch.cuda.Event()
-            ev.record()
+        else:
+            # the batch through the C ABI with the sessions' pre-marshalled
+            # arguments: queue, one persistent fuse launch, one finalize
+            bh = b._h
+            for s in sess:
+                k = (s.views_done - 1) % s.data.n_views
+                b._check(lib.divas_batch_queue(bh, s.fusion.handle, s.c_views[k], 1))
+            b._check(lib.divas_batch_fuse(bh, ctypes.byref(self.c_schedule), 0, cs))
+            n = len(sess)
+            sc = (ctypes.c_void_p * n)(*[s.c_score.value for s in sess])
+            pts = (ctypes.c_void_p * n)(*[s.c_points.value for s in sess])
+            npts = (ctypes.c_int64 * n)(*[s.n_points for s in sess])
+            lab = (ctypes.c_void_p * n)(*[s.c_labels.value for s in sess])
+            b._check(lib.divas_batch_finalize(bh, sc, pts, npts, lab, L.KEEP_ZEROS, cs))
+        ev = self.events[si]
+        ev.record(st)
         self.stats["batches"] += 1
         self.stats["batch_sizes"].append(len(picked))
         for r in picked:

@@ -412,16 +412,20 @@ def fd_check(orc, wl, mask_type, n_per_view=60, n_random=20, eps_mask=1e-3, eps_
                 sel = aff[base["pix"][aff, i] == p]
                 vals = []
                 eps = eps_mask if which == "mask" else eps_depth
+                flat = np.ascontiguousarray(leaves[i]).reshape(-1)
+                old = flat[p]
                 for sgn in (+1, -1):
-                    leaf = leaves[i].copy().reshape(-1)
-                    leaf[p] = np.float32(float(leaf[p]) + sgn * eps)
+                    # perturb one pixel of a copy of the leaf list (the raster
+                    # itself is changed in place and restored)
+                    flat[p] = np.float32(float(old) + sgn * eps)
                     arrs = list(leaves)
-                    arrs[i] = leaf.reshape(leaves[i].shape)
+                    arrs[i] = flat.reshape(leaves[i].shape)
                     if which == "mask":
                         o2 = orc.fuse(wl.grid, lin[sel], wl.cams, wl.depth, arrs, mask_type, prm)
                     else:
                         o2 = orc.fuse(wl.grid, lin[sel], wl.cams, arrs, wl.mask, mask_type, prm)
-                    vals.append((o2, float(leaf[p])))
+                    vals.append((o2, float(flat[p])))
+                flat[p] = old
                 (op, xp), (om, xm) = vals
                 if len(sel) and ((op["bits"] != base["bits"][sel]).any()
                                  or (om["bits"] != base["bits"][sel]).any()):
@@ -440,6 +444,20 @@ def fd_check(orc, wl, mask_type, n_per_view=60, n_random=20, eps_mask=1e-3, eps_
                 checked += 1
     assert checked > 100, checked
     return checked, excluded
+
+
+def gradient_fd_config4_size(orc):
+    """Config 4's stated check: central differences (eps = 1e-3) of the FP64
+    forward on a 32^3 grid with 3 views (0, 3, 7) at 1008 x 756, 600 pixels
+    per view with a nonzero analytic gradient plus 100 random ones, for the
+    logits and the depths, against the oracle's analytic adjoint."""
+    wl = synth.config4(g=32, n_views=8, W=1008, H=756, n_ell=30, n_points=1000)
+    keep = [0, 3, 7]
+    wl.cams = [wl.cams[i] for i in keep]
+    wl.depth = [np.ascontiguousarray(wl.depth[i]) for i in keep]
+    wl.mask = [np.ascontiguousarray(wl.mask[i]) for i in keep]
+    return fd_check(orc, wl, oracle.MASK_LOGIT_F32, n_per_view=600, n_random=100,
+                    eps_mask=1e-3, eps_depth=1e-3)
 
 
 def pin_gradient_fd(orc):

@@ -22,3 +22,11 @@ def test_oracle_defaults_match_paper_constants():
     assert p.tau_m == c["mask_gate"]["value"]
     assert p.tau_cons == c["tau_cons"]["value"]
     assert p.gamma == c["gamma_gs"]["value"]
+
+
+def test_gradient_fd_at_config4_size():
+    """Every pixel with a nonzero analytic gradient (at most 600 per view and
+    leaf; a 32^3 grid seen at 1008 x 756 has fewer) plus 100 random pixels per
+    view and leaf."""
+    checked, excluded = pins.gradient_fd_config4_size(oracle)
+    assert checked > 600, (checked, excluded)
