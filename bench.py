@@ -1694,6 +1694,45 @@ def measure_sessions(dev, scale: float, n_sessions: int, rates, budget_frac: flo
     out["plain_updates_per_s"] = nominal / (out["plain_ms"] * 1e-3)
     out["launches"] = {"batched": 3 + 0, "plain": 4 * n_sessions}
     del graph
+    # the dense and the sparse (contracted) sessions as separate batches: the
+    # dense grids' fold against the HBM roofline, the contracted sets' fold
+    # (ALU-bound: compensated projections) for reference
+    for kind in ("dense", "sparse"):
+        part = [s for s in sess if s.fusion.dense == (kind == "dense")]
+        if not part:
+            continue
+        bp = Batch(max_sessions=len(part), max_views=sum(s.data.n_views for s in part))
+        for s in part:
+            s.fusion.reset()
+            bp.queue(s.fusion, s.data.cams, s.depth, s.mask, mask_type=s.data.mask_type)
+        pe = [torch.cuda.Event(enable_timing=True, external=True) for _ in range(2)]
+        gp = torch.cuda.CUDAGraph()
+        torch.cuda.synchronize()
+        with torch.cuda.graph(gp):
+            pe[0].record()
+            bp.fuse(sch)
+            pe[1].record()
+        pms = []
+        for k in range(6):
+            flush.zero_()
+            gp.replay()
+            torch.cuda.synchronize()
+            if k >= 2:
+                pms.append(pe[0].elapsed_time(pe[1]))
+        pb = sum(4 * s.fusion.n_active + 24 * s.fusion.n_active +
+                 sum(d.nbytes + m.nbytes for d, m in zip(s.data.depth, s.data.mask))
+                 for s in part)
+        act = sum(s.fusion.n_active * s.data.n_views for s in part)
+        t = float(np.mean(pms))
+        out[f"batched_fuse_{kind}"] = {
+            "sessions": len(part), "ms": t, "active_voxel_views": int(act),
+            "ns_per_active_voxel_view": t * 1e6 / max(1, act),
+            "roofline": {"bound": "hbm" if kind == "dense" else "alu",
+                         "algorithmic_bytes_per_launch": int(pb),
+                         "achieved_gbs": pb / (t * 1e-3) / 1e9,
+                         "hbm_frac": pb / (t * 1e-3) / 1e9 / peak, "peak_kind": peak_kind}}
+        del gp
+        bp.close()
     for s in sess:
         s.close()
     batch.close()

@@ -399,17 +399,28 @@ __device__ __forceinline__ void fold_views(const ViewBatch& VB, const VoxelGeom&
         for (int q = 0; q < kViewChunk; ++q)
             if (kF16Full || c * kViewChunk + q < VB.n)
                 load_raster<kMT>(VB.v[c * kViewChunk + q], pix[q], D[q], raw[q]);
+        // the chunk's gates as predicates, then one branch into the (rare) votes,
+        // added in view order
+        float e[kViewChunk];
+        uint32_t acc = 0u;
 #pragma unroll
         for (int q = 0; q < kViewChunk; ++q) {
             if (!kF16Full && c * kViewChunk + q >= VB.n) break;
-            const ViewC& V = VB.v[c * kViewChunk + q];
-            float e;
-            if (gates<kMT>(V, vg, F, pix[q], pzh[q], pzl[q], D[q], raw[q], e)) {
-                float m, w;
-                weight<kMT>(V, vg, F, raw[q], e, m, w);
-                W = __fmaf_rn(m, w, W);
-                Z = __fadd_rn(Z, w);
-                bits |= V.bit;
+            if (gates<kMT>(VB.v[c * kViewChunk + q], vg, F, pix[q], pzh[q], pzl[q], D[q], raw[q],
+                           e[q]))
+                acc |= 1u << q;
+        }
+        if (acc) {
+#pragma unroll
+            for (int q = 0; q < kViewChunk; ++q) {
+                if (acc & (1u << q)) {
+                    const ViewC& V = VB.v[c * kViewChunk + q];
+                    float m, w;
+                    weight<kMT>(V, vg, F, raw[q], e[q], m, w);
+                    W = __fmaf_rn(m, w, W);
+                    Z = __fadd_rn(Z, w);
+                    bits |= V.bit;
+                }
             }
         }
     }
