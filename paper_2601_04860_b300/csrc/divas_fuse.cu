@@ -24,6 +24,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <utility>
 #include <cmath>
 #include <cstddef>
 #include <cstdio>
@@ -109,6 +110,20 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* t
     return warp_off + x - v;
 }
 
+// Programmatic dependent launch within the one-call step: a kernel launched
+// with launch_dependent may start while its predecessor on the stream
+// finishes; it waits in wait_for_producer (which returns at once for a
+// kernel launched without the attribute) before it reads that kernel's
+// results, and a producer that lets its dependents start early says so with
+// allow_dependents.
+__device__ __forceinline__ void wait_for_producer() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
+__device__ __forceinline__ void allow_dependents() {
+    asm volatile("griddepcontrol.launch_dependents;" :::);
+}
+
 // ---------------------------------------------------------------------------
 // compaction in two launches, neither of which waits on another CTA.  A group
 // is 32 consecutive occupancy words (1024 cells), held one word per lane; an
@@ -157,6 +172,7 @@ __global__ void __launch_bounds__(kThreads) k_tile_count(
     uint32_t* __restrict__ tile_offset, uint32_t* __restrict__ done, int32_t n_tiles,
     int32_t* __restrict__ d_n, int64_t* __restrict__ d_total, int32_t* __restrict__ status) {
     __shared__ bool s_last;
+    allow_dependents();  // the emit may be scheduled now; it waits for this grid's end
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t g0 = (int64_t)blockIdx.x * kTileGroups + warp * kGroupsPerWarp;
     uint32_t word[kGroupsPerWarp];
@@ -325,6 +341,8 @@ __global__ void __launch_bounds__(kThreads) k_tile_emit(
     const uint32_t* __restrict__ item_pref, const uint32_t* __restrict__ tile_offset,
     uint32_t* __restrict__ active, uint32_t* __restrict__ seg_zero,
     uint32_t* __restrict__ seg_zero2) {
+    wait_for_producer();  // the counts and prefixes of k_tile_count
+    allow_dependents();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t n_groups = (n_words + 31) / 32;
     const int64_t n_warps = (int64_t)gridDim.x * (kThreads / 32);
@@ -506,6 +524,7 @@ __global__ void __launch_bounds__(kThreads, kContracted ? 4 : 6) k_fuse_fin(
     uint32_t* __restrict__ seg_bits, int32_t clear_bits, uint32_t* __restrict__ seg_out,
     int32_t clear_out, const uint32_t* __restrict__ occ_bits, int64_t n_words, int64_t n_cells,
     int32_t zero_unoccupied) {
+    wait_for_producer();  // the active list and its length
     const int lane = threadIdx.x & 31;
     const int32_t gw = (int32_t)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int32_t nw = (int32_t)((gridDim.x * blockDim.x) >> 5);
@@ -677,6 +696,7 @@ template <bool kPlainPow2>
 __global__ void __launch_bounds__(kThreads) k_label(const float* __restrict__ xyz, int64_t n,
                                                     GridC G, const uint32_t* __restrict__ seg_bits,
                                                     uint8_t* __restrict__ labels) {
+    wait_for_producer();  // the seg bitfield of the fusion
     const bool vec = (reinterpret_cast<uintptr_t>(xyz) & 15) == 0 &&
                      (reinterpret_cast<uintptr_t>(labels) & 3) == 0;
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; 4 * q < n;
@@ -884,6 +904,23 @@ int grid_for(int64_t items, int32_t sm_count, int per_sm = 16) {
 
 bool finite_pos(float x) { return x > 0.f && x <= FLT_MAX; }
 
+// launch with programmatic stream serialization (the kernel calls
+// wait_for_producer before reading its predecessor's results)
+template <typename... KArgs, typename... Args>
+cudaError_t launch_dependent(void (*f)(KArgs...), int blocks, cudaStream_t s, Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)blocks);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, f, std::forward<Args>(args)...);
+}
+
 // Argument checks shared by every entry point that takes a grid, fusion
 // parameters or a camera: nullptr when the argument is valid, else the reason.
 const char* grid_problem(const divas_grid* grid, int32_t g_max) {
@@ -1005,10 +1042,12 @@ cudaError_t launch_fuse_fin_chunks(int chunks, int blocks, cudaStream_t s, const
     bool f16_full = !kContracted && vb.n == kChunks * kViewChunk;
     for (int32_t i = 0; i < vb.n && f16_full; ++i) f16_full = vb.v[i].mask_type == kMaskF16;
 #define DIVAS_FUSE_FIN(F16)                                                                        \
-    k_fuse_fin<kAccumulate, kContracted, kChunks, F16><<<blocks, kThreads, 0, s>>>(                \
-        c->active, c->d_n, c->G, c->F, vb, c->W, c->Z, c->bits, c->grid.kind == 0 ? 1 : 0,         \
-        score_out, c->seg_bits, clear_bits ? 1 : 0, seg_out, clear_out ? 1 : 0, c->occ_bits,     \
-        c->n_words, c->n_cells, zero ? 1 : 0)
+    e = launch_dependent(k_fuse_fin<kAccumulate, kContracted, kChunks, F16>, blocks, s,           \
+        (const uint32_t*)c->active, (const int32_t*)c->d_n, c->G, c->F, vb, c->W, c->Z, c->bits,   \
+        (int32_t)(c->grid.kind == 0 ? 1 : 0), score_out, c->seg_bits,                              \
+        (int32_t)(clear_bits ? 1 : 0), seg_out, (int32_t)(clear_out ? 1 : 0),                      \
+        (const uint32_t*)c->occ_bits, c->n_words, c->n_cells, (int32_t)(zero ? 1 : 0))
+    cudaError_t e;
     if constexpr (!kContracted) {
         if (f16_full) DIVAS_FUSE_FIN(true);
         else DIVAS_FUSE_FIN(false);
@@ -1016,7 +1055,7 @@ cudaError_t launch_fuse_fin_chunks(int chunks, int blocks, cudaStream_t s, const
         DIVAS_FUSE_FIN(false);
     }
 #undef DIVAS_FUSE_FIN
-    return cudaGetLastError();
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 // zero: also write the zeros of a dense score_out's unoccupied cells
@@ -1075,9 +1114,12 @@ divas_status build_active(divas_ctx* c, const uint8_t* occ, const int32_t* coord
                           uint32_t* seg_zero2 = nullptr) {
     divas_status st = build_counts(c, occ, coords, n_coords, s);
     if (st != DIVAS_OK || !c->active) return st;
-    k_tile_emit<<<emit_blocks(c->n_words, c->sm_count), kThreads, 0, s>>>(
-        c->occ_bits, c->n_words, c->cap, c->gdiv, c->item_pref, c->tile_offset, c->active,
-        seg_zero, seg_zero2);
+    cudaError_t e = launch_dependent(k_tile_emit, emit_blocks(c->n_words, c->sm_count), s,
+                                     (const uint32_t*)c->occ_bits, c->n_words, c->cap, c->gdiv,
+                                     (const uint32_t*)c->item_pref,
+                                     (const uint32_t*)c->tile_offset, c->active, seg_zero,
+                                     seg_zero2);
+    if (e != cudaSuccess) return cuda_fail(c, e, "k_tile_emit");
     DIVAS_LAUNCHED(c, "k_tile_emit");
     return DIVAS_OK;
 }
@@ -1270,10 +1312,13 @@ static divas_status record_stage(divas_ctx* c, void* const* events, int k, cudaS
 static divas_status launch_label(divas_ctx* c, const float* xyz, int64_t n, uint8_t* labels_out,
                                  cudaStream_t s) {
     const int blocks = grid_for((n + 3) / 4, c->sm_count, 64);
-    if (!c->G.contracted && c->G.inv_h != 0.f)
-        k_label<true><<<blocks, kThreads, 0, s>>>(xyz, n, c->G, c->seg_bits, labels_out);
-    else
-        k_label<false><<<blocks, kThreads, 0, s>>>(xyz, n, c->G, c->seg_bits, labels_out);
+    const cudaError_t e =
+        !c->G.contracted && c->G.inv_h != 0.f
+            ? launch_dependent(k_label<true>, blocks, s, xyz, n, c->G,
+                               (const uint32_t*)c->seg_bits, labels_out)
+            : launch_dependent(k_label<false>, blocks, s, xyz, n, c->G,
+                               (const uint32_t*)c->seg_bits, labels_out);
+    if (e != cudaSuccess) return cuda_fail(c, e, "k_label");
     DIVAS_LAUNCHED(c, "k_label");
     return DIVAS_OK;
 }
