@@ -517,7 +517,7 @@ __global__ void __launch_bounds__(kThreads) k_finalize(
 // k_fuse followed by k_finalize.
 // ---------------------------------------------------------------------------
 template <bool kAccumulate, bool kContracted, int kChunks, bool kF16Full = false>
-__global__ void __launch_bounds__(kThreads, kContracted ? 4 : 6) k_fuse_fin(
+__global__ void __launch_bounds__(kThreads, kContracted ? 5 : 6) k_fuse_fin(
     const uint32_t* __restrict__ active, const int32_t* __restrict__ d_n, GridC G, FuseC F,
     const __grid_constant__ ViewBatch VB, float* __restrict__ W, float* __restrict__ Z,
     uint32_t* __restrict__ bits, int32_t dense, float* __restrict__ score_out,
@@ -965,13 +965,32 @@ divas_status check_camera(divas_ctx* c, const divas_camera* cam) {
 // T = R o + t, M = (h/2) R, each split into an exact hi part (multiples of a
 // power of two 2^q with |T| + sum |M| (2g - 1) < 2^(q+24), so that the device
 // FMA chain over hi parts is exact) and a lo remainder.
+// Contracted grids: the fusion's rows (folded = true) or the camera's R and t
+// as given (folded = false: the depth-tuple and NeRF modes, which form their
+// own rows and intrinsics).
 ViewC make_view(const divas_camera& cam, const GridC& G, const float* depth, const void* mask,
-                int32_t mask_type, int32_t index) {
+                int32_t mask_type, int32_t index, bool folded = true) {
     ViewC v;
     memset(&v, 0, sizeof(v));
-    if (G.contracted) {
+    if (G.contracted && !folded) {
         memcpy(v.A, cam.R, sizeof(cam.R));
         memcpy(v.C, cam.t, sizeof(cam.t));
+    } else if (G.contracted) {
+        // intrinsics folded into the pixel rows (in double, rounded once); the
+        // depth row as given
+        for (int j = 0; j < 3; ++j) {
+            v.A[j] = (float)((double)cam.fx * cam.R[j] + (double)cam.cx * cam.R[6 + j]);
+            v.A[3 + j] = (float)((double)cam.fy * cam.R[3 + j] + (double)cam.cy * cam.R[6 + j]);
+            v.A[6 + j] = cam.R[6 + j];
+        }
+        v.C[0] = (float)((double)cam.fx * cam.t[0] + (double)cam.cx * cam.t[2]);
+        v.C[1] = (float)((double)cam.fy * cam.t[1] + (double)cam.cy * cam.t[2]);
+        v.C[2] = cam.t[2];
+        // the depth screen's bound 2^-19 (max_j |R_zj| n1 + |t_z|): powers of two
+        // scale exactly; the coefficient is rounded up
+        const float rz = std::max(fabsf(cam.R[6]), std::max(fabsf(cam.R[7]), fabsf(cam.R[8])));
+        v.B[0] = nextafterf(ldexpf(rz, -19), INFINITY);
+        v.E = ldexpf(fabsf(cam.t[2]), -19);
     } else {
         // camera coordinates of the lattice point n: p = T + M n, T = R o + t,
         // M = (h / 2) R (in double)
@@ -1027,9 +1046,9 @@ float logit_threshold(float tau) {
     return (float)log((double)tau / (1.0 - (double)tau));
 }
 
-// launch k_fuse_fin with the chunk count as a compile-time constant; plain
-// grids whose views all carry binary16 masks and fill their chunks exactly take
-// the kF16Full instance
+// launch k_fuse_fin with the chunk count as a compile-time constant; batches
+// whose views all carry binary16 masks and fill their chunks exactly take the
+// kF16Full instance
 template <bool kAccumulate, bool kContracted, int kChunks = 1>
 cudaError_t launch_fuse_fin_chunks(int chunks, int blocks, cudaStream_t s, const divas_ctx* c,
                                    const ViewBatch& vb, float* score_out, bool clear_bits,
@@ -1039,7 +1058,7 @@ cudaError_t launch_fuse_fin_chunks(int chunks, int blocks, cudaStream_t s, const
             return launch_fuse_fin_chunks<kAccumulate, kContracted, kChunks + 1>(
                 chunks, blocks, s, c, vb, score_out, clear_bits, seg_out, clear_out, zero);
     }
-    bool f16_full = !kContracted && vb.n == kChunks * kViewChunk;
+    bool f16_full = vb.n == kChunks * kViewChunk;
     for (int32_t i = 0; i < vb.n && f16_full; ++i) f16_full = vb.v[i].mask_type == kMaskF16;
 #define DIVAS_FUSE_FIN(F16)                                                                        \
     e = launch_dependent(k_fuse_fin<kAccumulate, kContracted, kChunks, F16>, blocks, s,           \
@@ -1048,12 +1067,8 @@ cudaError_t launch_fuse_fin_chunks(int chunks, int blocks, cudaStream_t s, const
         (int32_t)(clear_bits ? 1 : 0), seg_out, (int32_t)(clear_out ? 1 : 0),                      \
         (const uint32_t*)c->occ_bits, c->n_words, c->n_cells, (int32_t)(zero ? 1 : 0))
     cudaError_t e;
-    if constexpr (!kContracted) {
-        if (f16_full) DIVAS_FUSE_FIN(true);
-        else DIVAS_FUSE_FIN(false);
-    } else {
-        DIVAS_FUSE_FIN(false);
-    }
+    if (f16_full) DIVAS_FUSE_FIN(true);
+    else DIVAS_FUSE_FIN(false);
 #undef DIVAS_FUSE_FIN
     return e != cudaSuccess ? e : cudaGetLastError();
 }

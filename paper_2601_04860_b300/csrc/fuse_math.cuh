@@ -32,11 +32,19 @@
 //    for the benchmark cameras, well inside the 1e-6-relative band within
 //    which a pixel decision counts as a tie.
 //
-//  * Contracted grids.  Centres are uncontracted in hi + lo pairs; the depth
-//    row is a compensated dot product (error-free products via FMA and
-//    error-free sums: Ogita, Rump and Oishi, "Accurate sum and dot product",
-//    SIAM J. Sci. Comput. 2005), the pixel rows plain FMA chains over the hi
-//    and lo parts (inside the same tie band as above).
+//  * Contracted grids.  Centres are uncontracted in hi + lo pairs; the three
+//    rows are plain FMA chains over the hi and lo parts, which place the
+//    pixel (inside the same tie band as above).  The depth gate first screens
+//    the plain depth: a bound on its error (x_s = fl(x_hi + x_lo) within 2^-24
+//    of |x_hi| + |x_lo| per coordinate, three roundings of partial sums below
+//    S = sum |R_zj| (|x_hi,j| + |x_lo,j|) + |t_z|: at most 2^-21.9 S)
+//    widened to 2^-19 S rejects |e| > Delta for certain.
+//    Only pairs that pass every other gate and the screen (about 0.1% of
+//    the voxel-views of an unbounded scene) form the depth as a compensated
+//    dot product (error-free products via FMA and error-free sums: Ogita,
+//    Rump and Oishi, "Accurate sum and dot product", SIAM J. Sci. Comput.
+//    2005) and decide on it, so decisions and weights are those of the
+//    compensated depth everywhere.
 //
 // In both, e = (p_z,hi - D) + p_z,lo, where p_z,hi - D is exact by
 // Sterbenz's lemma whenever the depth gate can pass.
@@ -89,8 +97,11 @@ __device__ __forceinline__ void dot3c(float a0, float a1, float a2, const float*
 //   contracted grid: A = R, C = t (B, E unused)
 // Per-view constants (112 bytes, so that a batch of 32 views stays within the
 // classic 4 KB kernel-parameter space).  Plain grids: A = (Ku, Kv, M_z hi),
-// B = M_z lo, C = (Tu, Tv, T_z hi), E = T_z lo.  Contracted grids: A = R,
-// C = t, K = (fx, fy, cx, cy); B and E are unused.
+// B = M_z lo, C = (Tu, Tv, T_z hi), E = T_z lo.  Contracted grids: A = (Ku,
+// Kv, R_z) with Ku = fx R_x + cx R_z, Kv = fy R_y + cy R_z, C = (fx t_x + cx
+// t_z, fy t_y + cy t_z, t_z); the depth screen's bound is
+// B[0] n1 + E >= 2^-19 S with B[0] >= 2^-19 max_j |R_zj| and E = 2^-19 |t_z|
+// (n1 = sum_j |x_hi,j| + |x_lo,j| per voxel); B[1], B[2] are unused.
 struct ViewC {
     float A[9];
     float B[3];
@@ -145,6 +156,11 @@ struct VoxelGeom {
     float xh[3], xl[3];  // plain grid: xh = n = 2 idx + 1, xl unused
     float Delta, invDelta;
     float hv;            // world edge h_v
+    // contracted grids: x_s = fl(x_hi + x_lo), the centre the plain rows use;
+    // for the depth screen n1 = sum_j |x_hi,j| + |x_lo,j| and
+    // Delta (1 + 2^-20), both rounded up
+    float xs[3];
+    float n1, DeltaS;
     bool ok;  // false: contracted centre with |c| >= 2 (no world position)
 };
 
@@ -250,6 +266,13 @@ __device__ __forceinline__ VoxelGeom voxel_geom(uint32_t pk, const GridC& G, flo
     vg.hv = hv;
     vg.Delta = __fmul_rn(gamma, hv);
     vg.invDelta = __frcp_rn(vg.Delta);
+    vg.n1 = 0.f;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        vg.xs[a] = __fadd_rn(vg.xh[a], vg.xl[a]);
+        vg.n1 = __fadd_ru(vg.n1, __fadd_ru(fabsf(vg.xh[a]), fabsf(vg.xl[a])));
+    }
+    vg.DeltaS = __fmul_ru(vg.Delta, 1.f + 0x1p-20f);
     return vg;
 }
 
@@ -294,21 +317,21 @@ __device__ __forceinline__ int32_t project(const ViewC& V, const VoxelGeom& vg, 
         v = __fmul_rn(pv, inv);
         return pixel_index(V, front, u, v);
     }
-    // depth compensated (hi + lo); the pixel rows in plain FMA chains over the
-    // centre's hi and lo parts: at most 6 ulp of sum |R_j x_j| + |t| (about
-    // 1e-4 at |x| = 256, i.e. < 5e-4 pixel for the benchmark cameras)
-    dot3c(V.A[6], V.A[7], V.A[8], vg.xh, vg.xl, V.C[2], pzh, pzl);
-    pz = pzh;
-    const float px = __fmaf_rn(V.A[0], vg.xh[0], __fmaf_rn(V.A[1], vg.xh[1], __fmaf_rn(
-        V.A[2], vg.xh[2], __fmaf_rn(V.A[0], vg.xl[0], __fmaf_rn(V.A[1], vg.xl[1], __fmaf_rn(
-        V.A[2], vg.xl[2], V.C[0]))))));
-    const float py = __fmaf_rn(V.A[3], vg.xh[0], __fmaf_rn(V.A[4], vg.xh[1], __fmaf_rn(
-        V.A[5], vg.xh[2], __fmaf_rn(V.A[3], vg.xl[0], __fmaf_rn(V.A[4], vg.xl[1], __fmaf_rn(
-        V.A[5], vg.xl[2], V.C[1]))))));
+    // the three rows in plain FMA chains over the rounded centre x_s: the
+    // depth row R_z x + t_z and the intrinsics-folded pixel rows
+    // u p_z = (fx R_x + cx R_z) x + (fx t_x + cx t_z) (and likewise v), each
+    // within 4 ulp of sum_j |row_j x_j| + |const| (about 1e-4 pixel at |x| = 256
+    // for the benchmark cameras); the depth is returned as (plain, 0) and made
+    // exact by depth_error only where the screen lets it pass
+    pz = __fmaf_rn(V.A[6], vg.xs[0], __fmaf_rn(V.A[7], vg.xs[1], __fmaf_rn(V.A[8], vg.xs[2], V.C[2])));
+    pzh = pz;
+    pzl = 0.f;
+    const float pu = __fmaf_rn(V.A[0], vg.xs[0], __fmaf_rn(V.A[1], vg.xs[1], __fmaf_rn(V.A[2], vg.xs[2], V.C[0])));
+    const float pv = __fmaf_rn(V.A[3], vg.xs[0], __fmaf_rn(V.A[4], vg.xs[1], __fmaf_rn(V.A[5], vg.xs[2], V.C[1])));
     const bool front = pz > z_near && pz <= FLT_MAX;
     const float inv = rcp_nr(front ? pz : 1.f);
-    u = __fmaf_rn(V.K[0], __fmul_rn(px, inv), V.K[2]);
-    v = __fmaf_rn(V.K[1], __fmul_rn(py, inv), V.K[3]);
+    u = __fmul_rn(pu, inv);
+    v = __fmul_rn(pv, inv);
     return pixel_index(V, front, u, v);
 }
 
@@ -336,14 +359,52 @@ __device__ __forceinline__ void load_raster(const ViewC& V, int32_t pix, float& 
 // ---------------------------------------------------------------------------
 // step 3: gates (predicates) and, for an accepted vote, the weight
 // ---------------------------------------------------------------------------
-template <int kMT = -1>
+// Contracted grids: false only where |e| > Delta for certain.  The plain depth
+// pz differs from the exact one by at most 2^-21.9 S; fl(pz - D) adds 2^-24
+// of itself; the exact e = fl(fl(p_z,hi - D) + p_z,lo) is within 2^-23 of
+// its own size of p_z - D.  So |e| <= Delta implies
+// |fl(pz - D)| <= Delta (1 + 2^-22) + 2^-21.2 S, which the threshold
+// Delta (1 + 2^-20) + 2^-19 S, summed rounding up, exceeds.  Plain grids:
+// true (their depth pair is already exact).
+template <bool kContracted>
+__device__ __forceinline__ bool depth_screen(const ViewC& V, const VoxelGeom& vg, float pzh,
+                                             float D) {
+    if (!kContracted) return true;
+    const float thr = __fadd_ru(vg.DeltaS, __fmaf_ru(V.B[0], vg.n1, V.E));
+    return fabsf(__fsub_rn(pzh, D)) <= thr;
+}
+
+// e = p_z - D from the exact depth: plain grids the pair of project(),
+// contracted grids the compensated dot product
+template <bool kContracted>
+__device__ __forceinline__ float depth_error(const ViewC& V, const VoxelGeom& vg, float pzh,
+                                             float pzl, float D) {
+    if (kContracted) dot3c(V.A[6], V.A[7], V.A[8], vg.xh, vg.xl, V.C[2], pzh, pzl);
+    return __fadd_rn(__fsub_rn(pzh, D), pzl);
+}
+
+// the gates before the depth gate: a pixel in frame, a surface there (+inf,
+// NaN or <= 0 depth: none), the mask gate; for contracted grids also the
+// depth screen
+template <bool kContracted, int kMT = -1>
+__device__ __forceinline__ bool pre_gates(const ViewC& V, const VoxelGeom& vg, const FuseC& F,
+                                          int32_t pix, float pzh, float D, float raw) {
+    const float thr = mask_type_of<kMT>(V) == kMaskLogit ? F.logit_tau : F.tau_m;
+    return pix >= 0 && D > 0.f && D <= FLT_MAX && raw >= thr &&
+           depth_screen<kContracted>(V, vg, pzh, D);
+}
+
+template <bool kContracted, int kMT = -1>
 __device__ __forceinline__ bool gates(const ViewC& V, const VoxelGeom& vg, const FuseC& F,
                                       int32_t pix, float pzh, float pzl, float D, float raw,
                                       float& e) {
-    e = __fadd_rn(__fsub_rn(pzh, D), pzl);
-    const float thr = mask_type_of<kMT>(V) == kMaskLogit ? F.logit_tau : F.tau_m;
-    // +inf, NaN or <= 0 depth: no surface; mask gate; depth gate
-    return pix >= 0 && D > 0.f && D <= FLT_MAX && raw >= thr && fabsf(e) <= vg.Delta;
+    if (!kContracted) {
+        e = depth_error<false>(V, vg, pzh, pzl, D);
+        return pre_gates<false, kMT>(V, vg, F, pix, pzh, D, raw) && fabsf(e) <= vg.Delta;
+    }
+    if (!pre_gates<true, kMT>(V, vg, F, pix, pzh, D, raw)) return false;
+    e = depth_error<true>(V, vg, pzh, pzl, D);
+    return fabsf(e) <= vg.Delta;
 }
 
 template <int kMT = -1>
@@ -366,7 +427,7 @@ __device__ __forceinline__ bool eval_vote(const ViewC& V, const VoxelGeom& vg, c
     float pzh, pzl, D, raw;
     const int32_t pix = project<kContracted>(V, vg, F.z_near, pzh, pzl);
     load_raster(V, pix, D, raw);
-    if (!gates(V, vg, F, pix, pzh, pzl, D, raw, out.e)) return false;
+    if (!gates<kContracted>(V, vg, F, pix, pzh, pzl, D, raw, out.e)) return false;
     weight(V, vg, F, raw, out.e, out.m, out.w);
     out.pix = pix;
     return true;
@@ -400,21 +461,28 @@ __device__ __forceinline__ void fold_views(const ViewBatch& VB, const VoxelGeom&
             if (kF16Full || c * kViewChunk + q < VB.n)
                 load_raster<kMT>(VB.v[c * kViewChunk + q], pix[q], D[q], raw[q]);
         // the chunk's gates as predicates, then one branch into the (rare) votes,
-        // added in view order
+        // added in view order (contracted grids: the screened candidates, whose
+        // exact depth decides there)
         float e[kViewChunk];
         uint32_t acc = 0u;
 #pragma unroll
         for (int q = 0; q < kViewChunk; ++q) {
             if (!kF16Full && c * kViewChunk + q >= VB.n) break;
-            if (gates<kMT>(VB.v[c * kViewChunk + q], vg, F, pix[q], pzh[q], pzl[q], D[q], raw[q],
-                           e[q]))
-                acc |= 1u << q;
+            const ViewC& V = VB.v[c * kViewChunk + q];
+            const bool pass =
+                kContracted ? pre_gates<true, kMT>(V, vg, F, pix[q], pzh[q], D[q], raw[q])
+                            : gates<false, kMT>(V, vg, F, pix[q], pzh[q], pzl[q], D[q], raw[q], e[q]);
+            if (pass) acc |= 1u << q;
         }
         if (acc) {
 #pragma unroll
             for (int q = 0; q < kViewChunk; ++q) {
                 if (acc & (1u << q)) {
                     const ViewC& V = VB.v[c * kViewChunk + q];
+                    if constexpr (kContracted) {
+                        e[q] = depth_error<true>(V, vg, pzh[q], pzl[q], D[q]);
+                        if (!(fabsf(e[q]) <= vg.Delta)) continue;
+                    }
                     float m, w;
                     weight<kMT>(V, vg, F, raw[q], e[q], m, w);
                     W = __fmaf_rn(m, w, W);
@@ -461,7 +529,8 @@ __device__ __forceinline__ void fold_views_multi(const ViewC* sv, int32_t n, con
                 if (v0 + q >= n) break;
                 const ViewC& V = sv[v0 + q];
                 float e;
-                if (gates(V, vg[j], F, pix[j][q], pzh[j][q], pzl[j][q], D[j][q], raw[j][q], e)) {
+                if (gates<kContracted>(V, vg[j], F, pix[j][q], pzh[j][q], pzl[j][q], D[j][q],
+                                       raw[j][q], e)) {
                     float m, w;
                     weight(V, vg[j], F, raw[j][q], e, m, w);
                     W[j] = __fmaf_rn(m, w, W[j]);

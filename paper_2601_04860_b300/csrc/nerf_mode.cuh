@@ -535,7 +535,8 @@ divas_status divas_fuse_add_views_nerf_profiled(divas_ctx* c, const divas_tuple_
         for (int32_t j = 0; j < tb.n; ++j) {
             const divas_tuple_view& v = views[k0 + j];
             TViewC& t = tb.v[j];
-            t.base = make_view(v.cam, c->G, v.d_min, v.mask, v.mask_type, c->n_views + k0 + j);
+            t.base = make_view(v.cam, c->G, v.d_min, v.mask, v.mask_type, c->n_views + k0 + j,
+                               false);
             memcpy(t.R, v.cam.R, sizeof(t.R));
             memcpy(t.t, v.cam.t, sizeof(t.t));
             t.d_med = v.d_med;  // d_exp

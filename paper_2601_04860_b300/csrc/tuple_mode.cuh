@@ -1175,7 +1175,8 @@ divas_status divas_fuse_add_views_tuple_profiled(divas_ctx* c, const divas_tuple
         for (int32_t j = 0; j < tb.n; ++j) {
             const divas_tuple_view& v = views[k0 + j];
             TViewC& t = tb.v[j];
-            t.base = make_view(v.cam, c->G, v.d_min, v.mask, v.mask_type, c->n_views + k0 + j);
+            t.base = make_view(v.cam, c->G, v.d_min, v.mask, v.mask_type, c->n_views + k0 + j,
+                               false);
             t.d_med = v.d_med;
             t.d_max = v.d_max;
             t.n_samp = v.n_samp;

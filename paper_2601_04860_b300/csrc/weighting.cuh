@@ -201,12 +201,14 @@ __global__ void __launch_bounds__(kThreads) k_fuse_weighted(
                     const int v = c * kViewChunk + q;
                     if (v >= VB.n) break;
                     const ViewC& V = VB.v[v];
-                    const float e = __fadd_rn(__fsub_rn(pzh[q], D[q]), pzl[q]);
+                    if (!(pix[q] >= 0 && D[q] > 0.f && D[q] <= FLT_MAX &&
+                          depth_screen<kContracted>(V, vg, pzh[q], D[q])))
+                        continue;
+                    const float e = depth_error<kContracted>(V, vg, pzh[q], pzl[q], D[q]);
                     const float m = V.mask_type == kMaskLogit
                                         ? __frcp_rn(__fadd_rn(1.f, expf(-raw[q])))
                                         : raw[q];
-                    if (pix[q] >= 0 && D[q] > 0.f && D[q] <= FLT_MAX && fabsf(e) <= vg.Delta &&
-                        !(m >= 0.f && m < F.tau_m)) {
+                    if (fabsf(e) <= vg.Delta && !(m >= 0.f && m < F.tau_m)) {
                         const float mt = __fmul_rn(m, weight_of(sc[v], D[q]));
                         if (mt >= F.tau_m) {
                             const float r = __fmul_rn(e, vg.invDelta);
