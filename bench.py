@@ -111,6 +111,29 @@ def job_throughput(units_per_rank: float, world: int, ms_max: float) -> float:
 SPARSE_FUSE_INSTS_PER_VOXEL_VIEW = 3.91
 
 
+def fusion_params(wl):
+    """Fusion constants for a workload: sparse priors on grids with a multiple
+    of 8 voxels per side keep their active list brick-major (warp-level view
+    culling; per-voxel results unchanged)."""
+    from paper_2601_04860_b300 import FusionParams
+    return FusionParams(brick_order=wl.coords is not None and wl.grid.g % 8 == 0)
+
+
+def linear_state(fu, st: dict, score, dense: bool) -> dict:
+    """W, Z, view bits (and a sparse score) of a context in ascending linear
+    order of their voxels, whatever the context's active order."""
+    out = {"W": st["W"].cpu().numpy(), "Z": st["Z"].cpu().numpy(),
+           "bits": st["bits"].cpu().numpy().view(np.uint32), "score": score.cpu().numpy()}
+    act = fu.active_coords().cpu().numpy().astype(np.int64)
+    g = fu.g
+    o = np.argsort((act[:, 2] * g + act[:, 1]) * g + act[:, 0], kind="stable")
+    for k in ("W", "Z", "bits"):
+        out[k] = out[k][o]
+    if not dense:
+        out["score"] = out["score"][o]
+    return out
+
+
 def make_workload(name):
     import synth
     if name == "forward-dense-256":
@@ -284,7 +307,7 @@ def run_ours(args, rank, world, local_rank):
     else:
         mask = [torch.from_numpy(m).to(dev) for m in wl.mask]
     pts = torch.from_numpy(np.ascontiguousarray(wl.points)).to(dev)
-    fu = VoxelFusion(wl.grid, occ=occ, coords=coords, params=FusionParams())
+    fu = VoxelFusion(wl.grid, occ=occ, coords=coords, params=fusion_params(wl))
     n_active = fu.n_active
     dense = wl.occ is not None
     score = torch.empty(fu.n_cells if dense else n_active, dtype=torch.float32, device=dev)
@@ -636,11 +659,9 @@ def run_ours(args, rank, world, local_rank):
         torch.cuda.synchronize()
         st = fu.export_state()
         fin = fu.finalize(score=False, seg_bits=True)
-        res["_parity_gpu"] = {
-            "W": st["W"].cpu().numpy(), "Z": st["Z"].cpu().numpy(),
-            "bits": st["bits"].cpu().numpy().view(np.uint32), "score": score.cpu().numpy(),
-            "seg_words": fin["seg_bits"].cpu().numpy().view(np.uint32),
-            "labels": labels.cpu().numpy()}
+        res["_parity_gpu"] = dict(linear_state(fu, st, score, dense),
+                                  seg_words=fin["seg_bits"].cpu().numpy().view(np.uint32),
+                                  labels=labels.cpu().numpy())
     fu.close()
     return res, wl
 
@@ -709,7 +730,7 @@ def measure_sparse(dev, steps: int, cpu_seconds: float = 8.0):
     depth = [torch.from_numpy(d).to(dev) for d in wl.depth]
     mask = [torch.from_numpy(m.view(np.float16)).to(dev) for m in wl.mask]
     pts = torch.from_numpy(np.ascontiguousarray(wl.points)).to(dev)
-    fu = VoxelFusion(wl.grid, coords=coords, params=FusionParams())
+    fu = VoxelFusion(wl.grid, coords=coords, params=fusion_params(wl))
     na = fu.n_active
     score = torch.empty(na, dtype=torch.float32, device=dev)
     labels = torch.empty(len(wl.points), dtype=torch.uint8, device=dev)
@@ -774,7 +795,16 @@ def measure_sparse(dev, steps: int, cpu_seconds: float = 8.0):
                         "hbm_achieved_gbs": ach, "hbm_frac": ach / peak, "hbm_peak_kind": peak_kind,
                         "algorithmic_bytes_per_launch": int(fb)},
            "clocks": clk,
-           "gpu_launches_per_step": 4}
+           "active_order": "brick-major (8^3 bricks; warp-level view culling)"
+                           if fu.params.brick_order else "linear",
+           "gpu_launches_per_step": 5 if fu.params.brick_order else 4}
+    # the timed step's outputs, for the parity check against the oracle sample
+    g.replay()
+    torch.cuda.synchronize()
+    fin = fu.finalize(score=False, seg_bits=True)
+    pgpu = dict(linear_state(fu, fu.export_state(), score, False),
+                seg_words=fin["seg_bits"].cpu().numpy().view(np.uint32),
+                labels=labels.cpu().numpy())
     fu.close()
     # the oracle on a bounded sample of the same workload
     full_s, det = oracle_rate(wl, cpu_seconds, repeats=1)
@@ -783,6 +813,11 @@ def measure_sparse(dev, steps: int, cpu_seconds: float = 8.0):
                            "sample": f"{det['sample_voxels']} of {det['active_voxels']} active "
                                      f"voxels x {S} views + {det['sample_points']} points, "
                                      f"extrapolated to the full step"}
+    try:
+        out["parity"] = bench_parity(wl, pgpu, det["sample_index"], det["sample_out"],
+                                     det["sample_points"])
+    except Exception as e:  # noqa: BLE001
+        out["parity"] = {"error": f"{type(e).__name__}: {e}"}
     return out
 
 
@@ -1779,7 +1814,7 @@ def profile_steps(args):
     mask = [torch.from_numpy(m.view(np.float16) if wl.mask_type == 1 else m).to(dev)
             for m in wl.mask]
     pts = torch.from_numpy(np.ascontiguousarray(wl.points)).to(dev)
-    fu = VoxelFusion(wl.grid, occ=occ, coords=coords, params=FusionParams())
+    fu = VoxelFusion(wl.grid, occ=occ, coords=coords, params=fusion_params(wl))
     score = torch.empty(fu.n_cells if occ is not None else fu.n_active, dtype=torch.float32,
                         device=dev)
     labels = torch.empty(len(wl.points), dtype=torch.uint8, device=dev)

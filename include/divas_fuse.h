@@ -85,8 +85,19 @@ typedef enum {
  * values), z_near 1e-6. */
 typedef struct {
     float tau_mask, gamma, alpha1, tau_cons, eps, z_near;
-    uint32_t flags; /* reserved, 0 */
+    uint32_t flags; /* 0 or DIVAS_ORDER_BRICKS */
 } divas_params;
+
+/* divas_params.flags: the active list in brick-major order instead of
+ * ascending linear index -- 8 x 8 x 8 bricks in linear brick order (x
+ * fastest), the cells of a brick in linear order (x fastest).  Sparse prior
+ * only, g a multiple of 8 (else DIVAS_E_INVALID).  Every per-voxel result is
+ * unchanged; only the order of the active list, and so of everything stored
+ * or returned in active-list order, differs.  Consecutive active voxels then
+ * lie close together in space, which lets the fusion skip, for a whole warp of
+ * voxels, a view whose mask gate none of them can pass (see
+ * divas_fuse_add_views). */
+#define DIVAS_ORDER_BRICKS 1u
 
 
 typedef struct {
@@ -123,7 +134,8 @@ void divas_default_params(divas_params* out);
  *           coords must be NULL.
  *   kind 1: coords = device n_coords x 3 int32 (i, j, k); duplicates are
  *           merged; occ_dense must be NULL.
- * The active list is ordered by ascending linear index.  Allocates device
+ * The active list is ordered by ascending linear index (brick-major with
+ * DIVAS_ORDER_BRICKS).  Allocates device
  * memory and synchronises `stream` once (to size the active arrays).
  */
 divas_status divas_fuse_init(divas_ctx** out, const divas_grid* grid, const uint8_t* occ_dense,

@@ -26,6 +26,9 @@ NERF_LLFF = 0
 NERF_MIP360 = 1
 
 
+ORDER_BRICKS = 1  # divas_params.flags: brick-major active list
+
+
 class DivasParams(ctypes.Structure):
     _fields_ = [("tau_mask", ctypes.c_float), ("gamma", ctypes.c_float),
                 ("alpha1", ctypes.c_float), ("tau_cons", ctypes.c_float),

@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 SRC_DIR = os.path.join(HERE, "csrc")
 SOURCES = ["divas_fuse.cu"]
-HEADERS = ["fuse_math.cuh", "tuple_mode.cuh", "weighting.cuh", "select.cuh", "occupancy.cuh", "surfels.cuh", "nerf_mode.cuh"]
+HEADERS = ["fuse_math.cuh", "tuple_mode.cuh", "weighting.cuh", "select.cuh", "occupancy.cuh", "surfels.cuh", "nerf_mode.cuh", "cull.cuh"]
 LIB = os.path.join(HERE, "libdivas_fuse.so")
 INCLUDE = os.path.join(ROOT, "include")
 

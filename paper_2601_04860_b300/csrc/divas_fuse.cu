@@ -35,6 +35,7 @@
 #include <vector>
 
 #include "fuse_math.cuh"
+#include "cull.cuh"
 
 using namespace divas;
 
@@ -52,10 +53,21 @@ struct BackPtrs {
 // ---------------------------------------------------------------------------
 // compaction
 // ---------------------------------------------------------------------------
-// sparse coordinates -> bitfield (atomic OR; duplicates merge).  Lanes take
-// consecutive coordinates and those that fall in the same 32-bit word OR their
-// bits together first, so a sorted (or spatially coherent) set costs one
-// atomic per word and warp instead of one per coordinate.
+// bit of cell (i, j, k) in the brick-major layout: 8^3 bricks in linear brick
+// order (x fastest), cells inside a brick in linear order (x fastest), so a
+// 32-bit word is an 8 x 4 patch of one brick slice (g a multiple of 8)
+__device__ __forceinline__ int64_t brick_bit(int32_t i, int32_t j, int32_t k, int32_t g) {
+    const int64_t nb = g >> 3;
+    const int64_t b = ((int64_t)(k >> 3) * nb + (j >> 3)) * nb + (i >> 3);
+    return b * 512 + (((k & 7) * 8 + (j & 7)) * 8 + (i & 7));
+}
+
+// sparse coordinates -> bitfield (atomic OR; duplicates merge), in linear or
+// brick-major layout.  Lanes take consecutive coordinates and those that fall
+// in the same 32-bit word OR their bits together first, so a sorted (or
+// spatially coherent) set costs one atomic per word and warp instead of one per
+// coordinate.
+template <bool kBrick>
 __global__ void __launch_bounds__(kThreads) k_scatter_coords(const int32_t* __restrict__ coords,
                                                              int64_t n, int32_t g,
                                                              uint32_t* __restrict__ bits,
@@ -72,7 +84,7 @@ __global__ void __launch_bounds__(kThreads) k_scatter_coords(const int32_t* __re
             if (i < 0 || j < 0 || k < 0 || i >= g || j >= g || k >= g) {
                 atomicOr(status, kStatusBadCoord);
             } else {
-                const int64_t lin = ((int64_t)k * g + j) * g + i;
+                const int64_t lin = kBrick ? brick_bit(i, j, k, g) : ((int64_t)k * g + j) * g + i;
                 word = (uint32_t)(lin >> 5);
                 bit = 1u << (lin & 31);
             }
@@ -108,20 +120,6 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* t
     if (total) *total = warp_sums[kThreads / 32 - 1];
     __syncthreads();
     return warp_off + x - v;
-}
-
-// Programmatic dependent launch within the one-call step: a kernel launched
-// with launch_dependent may start while its predecessor on the stream
-// finishes; it waits in wait_for_producer (which returns at once for a
-// kernel launched without the attribute) before it reads that kernel's
-// results, and a producer that lets its dependents start early says so with
-// allow_dependents.
-__device__ __forceinline__ void wait_for_producer() {
-    asm volatile("griddepcontrol.wait;" ::: "memory");
-}
-
-__device__ __forceinline__ void allow_dependents() {
-    asm volatile("griddepcontrol.launch_dependents;" :::);
 }
 
 // ---------------------------------------------------------------------------
@@ -285,6 +283,18 @@ __device__ __forceinline__ uint32_t pack_lin(uint32_t lin, const FastDiv& gdiv) 
 // non-empty word in which lane b writes bit b (consecutive slots per store).
 // Packed coordinates come from the word's first cell plus the bit while the
 // word stays on one row.  Warp-uniform: every lane of the warp calls it.
+//
+// Brick-major layout (kBrick; div divides by the bricks per side): word w is
+// rows 4 (w & 1) .. + 3 of slice (w & 15) >> 1 of brick w >> 4, bit b the
+// cell (b & 7, b >> 3) of that patch.
+__device__ __forceinline__ uint32_t brick_word_p0(uint32_t w, const FastDiv& bdiv) {
+    const uint32_t b = w >> 4, sl = w & 15u;
+    const uint32_t r = fast_div(b, bdiv), bk = fast_div(r, bdiv);
+    const uint32_t bi = b - r * bdiv.d, bj = r - bk * bdiv.d;
+    return (bi << 3) | (((bj << 3) + ((sl & 1u) << 2)) << 10) | (((bk << 3) + (sl >> 1)) << 20);
+}
+
+template <bool kBrick>
 __device__ __forceinline__ void emit_group(uint32_t x, int64_t w, int64_t g, int64_t base,
                                            int64_t cap, const FastDiv& gdiv,
                                            uint32_t* __restrict__ active) {
@@ -300,7 +310,8 @@ __device__ __forceinline__ void emit_group(uint32_t x, int64_t w, int64_t g, int
         if (lane >= o) inc += y;
     }
     const uint32_t ex = inc - c;
-    const uint32_t p0 = pack_lin((uint32_t)(w * 32), gdiv);  // this lane's word, bit 0
+    // this lane's word, bit 0
+    const uint32_t p0 = kBrick ? brick_word_p0((uint32_t)w, gdiv) : pack_lin((uint32_t)(w * 32), gdiv);
     const uint32_t max_c = __reduce_max_sync(0xffffffffu, c);
     if (max_c <= (uint32_t)__popc(nz)) {
         // scattered bits: every lane walks its own word (rounds = the largest popcount)
@@ -310,7 +321,9 @@ __device__ __forceinline__ void emit_group(uint32_t x, int64_t w, int64_t g, int
         while (xb) {
             const uint32_t b = __ffs(xb) - 1;
             xb &= xb - 1u;
-            if (slot < cap) active[slot] = row ? p0 + b : pack_lin((uint32_t)(w * 32) + b, gdiv);
+            if (slot < cap)
+                active[slot] = kBrick ? p0 + (b & 7u) + ((b >> 3) << 10)
+                                      : (row ? p0 + b : pack_lin((uint32_t)(w * 32) + b, gdiv));
             ++slot;
         }
         return;
@@ -326,7 +339,8 @@ __device__ __forceinline__ void emit_group(uint32_t x, int64_t w, int64_t g, int
             const int64_t slot = base + off + __popc(xs & lt);
             if (slot < cap) {
                 // same row as the word's bit 0 unless the row wraps inside the word
-                active[slot] = (ps & 1023u) + lane < gdiv.d
+                active[slot] = kBrick ? ps + (lane & 7) + ((uint32_t)(lane >> 3) << 10)
+                               : (ps & 1023u) + lane < gdiv.d
                                    ? ps + lane
                                    : pack_lin((uint32_t)((g * 32 + src) * 32 + lane), gdiv);
             }
@@ -336,6 +350,7 @@ __device__ __forceinline__ void emit_group(uint32_t x, int64_t w, int64_t g, int
 
 // seg_zero / seg_zero2 (nullable): seg bitfields whose words are cleared on
 // the way (the one-call step)
+template <bool kBrick>
 __global__ void __launch_bounds__(kThreads) k_tile_emit(
     const uint32_t* __restrict__ bits, int64_t n_words, int64_t cap, FastDiv gdiv,
     const uint32_t* __restrict__ item_pref, const uint32_t* __restrict__ tile_offset,
@@ -356,7 +371,7 @@ __global__ void __launch_bounds__(kThreads) k_tile_emit(
             if (seg_zero) seg_zero[w] = 0u;
             if (seg_zero2) seg_zero2[w] = 0u;
         }
-        emit_group(x, w, g, (int64_t)t_off + i_pre, cap, gdiv, active);
+        emit_group<kBrick>(x, w, g, (int64_t)t_off + i_pre, cap, gdiv, active);
     }
 }
 
@@ -563,6 +578,57 @@ __global__ void __launch_bounds__(kThreads, kContracted ? 5 : 6) k_fuse_fin(
     }
     if (zero_unoccupied)
         zero_unoccupied_groups(occ_bits, n_words, n_cells, score_out, gw, nw, x_first, true);
+}
+
+// ---------------------------------------------------------------------------
+// fusion + finalize with warp-level view culling (brick-ordered sparse sets):
+// per warp of 32 voxels, the views whose mask gate no voxel of the warp can
+// pass are skipped (cull_views); the kept views are folded in view order with
+// the arithmetic of k_fuse_fin, so every result is bitwise that of k_fuse_fin.
+// kMT: the batch's mask type when all views carry binary16 masks, else -1.
+// ---------------------------------------------------------------------------
+template <bool kAccumulate, bool kContracted, int kMT>
+__global__ void __launch_bounds__(kThreads, kContracted ? 5 : 6) k_fuse_fin_cull(
+    const uint32_t* __restrict__ active, const int32_t* __restrict__ d_n, GridC G, FuseC F,
+    const __grid_constant__ ViewBatch VB, const __grid_constant__ CullBatch CB,
+    float* __restrict__ W, float* __restrict__ Z, uint32_t* __restrict__ bits,
+    float* __restrict__ score_out, uint32_t* __restrict__ seg_bits, int32_t clear_bits,
+    uint32_t* __restrict__ seg_out, int32_t clear_out) {
+    __shared__ CullView sv[kMaxViews];
+    stage_cull_views(VB, CB, sv);  // kernel parameters only
+    wait_for_producer();           // the active list, its length and the mask pyramid
+    const int lane = threadIdx.x & 31;
+    const int32_t gw = (int32_t)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int32_t nw = (int32_t)((gridDim.x * blockDim.x) >> 5);
+    const int32_t n = *d_n;
+    for (int32_t base = gw * 32; base < n; base += nw * 32) {
+        const int32_t a = base + lane;
+        const bool live = a < n;
+        const uint32_t pk = live ? __ldg(active + a) : 0u;
+        const VoxelGeom vg = voxel_geom<kContracted>(pk, G, F.gamma);
+        const uint32_t keep = cull_views(sv, CB.pyr, VB.n, live && vg.ok,
+                                         kContracted ? vg.xs : vg.xh);
+        bool seg = false;
+        int64_t lin = 0;
+        if (live) {
+            float w = 0.f, z = 0.f;
+            uint32_t b = 0;
+            if (kAccumulate) {
+                w = W[a];
+                z = Z[a];
+                b = bits[a];
+            }
+            if (vg.ok) fold_views_kept<kContracted, kMT>(VB, keep, vg, F, w, z, b);
+            W[a] = w;
+            Z[a] = z;
+            bits[a] = b;
+            const float p = z > F.eps ? __fdiv_rn(w, z) : 0.f;
+            seg = p >= F.tau_cons;
+            lin = packed_lin(pk, G.g);
+            if (score_out) score_out[a] = p;
+        }
+        seg_epilogue(live, seg, lin, seg_bits, clear_bits != 0, seg_out, clear_out != 0);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -839,6 +905,10 @@ struct divas_ctx {
     uint32_t* seg_bits = nullptr;
     uint32_t* active = nullptr;
     FastDiv gdiv;  // division by g
+    bool brick = false;  // DIVAS_ORDER_BRICKS: brick-major bitfield and active list
+    FastDiv bdiv;        // division by g / 8 (brick order)
+    float* pyr = nullptr;  // brick order: mask max pyramids of a view batch
+    int64_t pyr_cap = 0;   // its capacity in floats
     void* sat = nullptr;   // tuple mode: integral-image scratch, grown on demand
     size_t sat_bytes = 0;
     void* wt = nullptr;    // depth weighting: selection state and histograms, grown on demand
@@ -932,12 +1002,25 @@ const char* grid_problem(const divas_grid* grid, int32_t g_max) {
     return nullptr;
 }
 
+// multiply-shift divider for d >= 1 (l = ceil(log2 d), m = 2^32 (2^l - d) / d + 1)
+FastDiv make_fast_div(uint32_t d) {
+    FastDiv f;
+    int32_t l = 0;
+    while ((1ull << l) < d) ++l;
+    f.d = d;
+    f.l = l;
+    f.m = (uint32_t)(((1ull << 32) * ((1ull << l) - d)) / d + 1);
+    f.pad = 0;
+    return f;
+}
+
 const char* params_problem(const divas_params* p) {
     if (!p) return "params is NULL";
     if (!(p->gamma > 0.f && p->gamma <= FLT_MAX) || !(p->alpha1 >= 0.f) ||
         !(p->alpha1 <= FLT_MAX) || !(p->eps >= 0.f) || !(p->tau_mask == p->tau_mask) ||
         !(p->tau_cons == p->tau_cons) || !(p->z_near == p->z_near))
         return "params out of range";
+    if (p->flags & ~DIVAS_ORDER_BRICKS) return "unknown params flags";
     return nullptr;
 }
 
@@ -1074,9 +1157,108 @@ cudaError_t launch_fuse_fin_chunks(int chunks, int blocks, cudaStream_t s, const
 }
 
 // zero: also write the zeros of a dense score_out's unoccupied cells
+// floats of one view's mask pyramid (levels kPyrL0 .. kPyrL0 + kPyrLevels - 1)
+int64_t pyramid_floats(int32_t W, int32_t H) {
+    int64_t f = 0;
+    for (int l = 0; l < kPyrLevels; ++l) {
+        const int L = kPyrL0 + l;
+        f += (int64_t)((W + (1 << L) - 1) >> L) * ((H + (1 << L) - 1) >> L);
+    }
+    return f;
+}
+
+// the cull constants of a view batch; false when the pyramids do not fit the
+// context's buffer (the batch is then fused without culling)
+bool make_cull(const divas_ctx* c, const ViewBatch& vb, CullBatch& cb) {
+    memset(&cb, 0, sizeof(cb));
+    cb.pyr = c->pyr;
+    cb.n = vb.n;
+    int64_t off = 0;
+    for (int32_t k = 0; k < vb.n; ++k) {
+        const ViewC& V = vb.v[k];
+        CullC& C = cb.v[k];
+        C.thr = V.mask_type == kMaskLogit ? c->F.logit_tau : c->F.tau_m;
+        // row magnitudes for the rectangle's error margin (rounded up)
+        float* sums[3] = {&C.su, &C.sv, &C.sz};
+        float* cons[3] = {&C.cu, &C.cv, &C.cz};
+        for (int r = 0; r < 3; ++r) {
+            double a = 0.0;
+            for (int j = 0; j < 3; ++j) a += fabs((double)V.A[3 * r + j]);
+            *sums[r] = nextafterf((float)(a * (1.0 + 1e-6)), INFINITY);
+            *cons[r] = fabsf(V.C[r]);
+        }
+        C.W = V.W;
+        C.H = V.H;
+        for (int l = 0; l < kPyrLevels; ++l) {
+            const int L = kPyrL0 + l;
+            C.lw[l] = (V.W + (1 << L) - 1) >> L;
+            C.lh[l] = (V.H + (1 << L) - 1) >> L;
+            C.off[l] = (int32_t)off;
+            off += (int64_t)C.lw[l] * C.lh[l];
+        }
+        if (off > c->pyr_cap) return false;
+    }
+    return true;
+}
+
+template <bool kAccumulate, bool kContracted>
+cudaError_t launch_fuse_fin_cull(const divas_ctx* c, const ViewBatch& vb, const CullBatch& cb,
+                                 int blocks, cudaStream_t s, float* score_out, bool clear_bits,
+                                 uint32_t* seg_out, bool clear_out) {
+    bool f16 = true;
+    for (int32_t i = 0; i < vb.n && f16; ++i) f16 = vb.v[i].mask_type == kMaskF16;
+#define DIVAS_FUSE_CULL(MT)                                                                       \
+    launch_dependent(k_fuse_fin_cull<kAccumulate, kContracted, MT>, blocks, s,                    \
+                     (const uint32_t*)c->active, (const int32_t*)c->d_n, c->G, c->F, vb, cb,      \
+                     c->W, c->Z, c->bits, score_out, c->seg_bits, (int32_t)(clear_bits ? 1 : 0), \
+                     seg_out, (int32_t)(clear_out ? 1 : 0))
+    const cudaError_t e = f16 ? DIVAS_FUSE_CULL(kMaskF16) : DIVAS_FUSE_CULL(-1);
+#undef DIVAS_FUSE_CULL
+    return e != cudaSuccess ? e : cudaGetLastError();
+}
+
+// the mask pyramids, then the culling fusion
+cudaError_t launch_culled(const divas_ctx* c, bool accumulate, const ViewBatch& vb,
+                          const CullBatch& cb, cudaStream_t s, float* score_out, bool clear_bits,
+                          uint32_t* seg_out, bool clear_out) {
+    int32_t wmax = 1, hmax = 1;
+    for (int32_t k = 0; k < vb.n; ++k) {
+        wmax = std::max(wmax, vb.v[k].W);
+        hmax = std::max(hmax, vb.v[k].H);
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)((wmax + kPyrTile - 1) / kPyrTile),
+                       (unsigned)((hmax + kPyrTile - 1) / kPyrTile), (unsigned)vb.n);
+    cfg.blockDim = dim3(256);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, k_mask_pyramid, vb, cb);
+    if (e != cudaSuccess) return e;
+    const int blocks = grid_for(c->cap, c->sm_count);
+    if (c->G.contracted)
+        return accumulate ? launch_fuse_fin_cull<true, true>(c, vb, cb, blocks, s, score_out,
+                                                             clear_bits, seg_out, clear_out)
+                          : launch_fuse_fin_cull<false, true>(c, vb, cb, blocks, s, score_out,
+                                                              clear_bits, seg_out, clear_out);
+    return accumulate ? launch_fuse_fin_cull<true, false>(c, vb, cb, blocks, s, score_out,
+                                                          clear_bits, seg_out, clear_out)
+                      : launch_fuse_fin_cull<false, false>(c, vb, cb, blocks, s, score_out,
+                                                           clear_bits, seg_out, clear_out);
+}
+
 cudaError_t launch_fuse_fin(const divas_ctx* c, bool accumulate, const ViewBatch& vb,
                             cudaStream_t s, float* score_out, bool clear_bits, uint32_t* seg_out,
                             bool clear_out, bool zero) {
+    if (c->brick && c->pyr && vb.n > 0) {
+        CullBatch cb;
+        if (make_cull(c, vb, cb))
+            return launch_culled(c, accumulate, vb, cb, s, score_out, clear_bits, seg_out,
+                                 clear_out);
+    }
     const int chunks = (vb.n + kViewChunk - 1) / kViewChunk;
     const int blocks = grid_for(zero ? std::max<int64_t>(c->cap, c->n_words) : c->cap, c->sm_count);
     if (c->G.contracted)
@@ -1110,8 +1292,12 @@ divas_status build_counts(divas_ctx* c, const uint8_t* occ, const int32_t* coord
     } else {
         DIVAS_CUDA(c, cudaMemsetAsync(c->occ_bits, 0, c->n_words * 4, s));
         if (n_coords > 0) {
-            k_scatter_coords<<<grid_for(n_coords, c->sm_count, 32), kThreads, 0, s>>>(
-                coords, n_coords, c->grid.g, c->occ_bits, c->d_status);
+            if (c->brick)
+                k_scatter_coords<true><<<grid_for(n_coords, c->sm_count, 32), kThreads, 0, s>>>(
+                    coords, n_coords, c->grid.g, c->occ_bits, c->d_status);
+            else
+                k_scatter_coords<false><<<grid_for(n_coords, c->sm_count, 32), kThreads, 0, s>>>(
+                    coords, n_coords, c->grid.g, c->occ_bits, c->d_status);
             DIVAS_LAUNCHED(c, "k_scatter_coords");
         }
         k_tile_count<true><<<c->n_tiles, kThreads, 0, s>>>(
@@ -1129,9 +1315,10 @@ divas_status build_active(divas_ctx* c, const uint8_t* occ, const int32_t* coord
                           uint32_t* seg_zero2 = nullptr) {
     divas_status st = build_counts(c, occ, coords, n_coords, s);
     if (st != DIVAS_OK || !c->active) return st;
-    cudaError_t e = launch_dependent(k_tile_emit, emit_blocks(c->n_words, c->sm_count), s,
-                                     (const uint32_t*)c->occ_bits, c->n_words, c->cap, c->gdiv,
-                                     (const uint32_t*)c->item_pref,
+    cudaError_t e = launch_dependent(c->brick ? k_tile_emit<true> : k_tile_emit<false>,
+                                     emit_blocks(c->n_words, c->sm_count), s,
+                                     (const uint32_t*)c->occ_bits, c->n_words, c->cap,
+                                     c->brick ? c->bdiv : c->gdiv, (const uint32_t*)c->item_pref,
                                      (const uint32_t*)c->tile_offset, c->active, seg_zero,
                                      seg_zero2);
     if (e != cudaSuccess) return cuda_fail(c, e, "k_tile_emit");
@@ -1159,6 +1346,7 @@ divas_status read_status(divas_ctx* c, cudaStream_t s) {
 void free_all(divas_ctx* c) {
     if (c->sat) cudaFree(c->sat);
     if (c->wt) cudaFree(c->wt);
+    if (c->pyr) cudaFree(c->pyr);
     void* ptrs[] = {c->occ_bits, c->item_pref, c->tile_count, c->tile_offset, c->done,
                     c->seg_bits, c->active,     c->W,          c->Z,           c->bits,
                     c->d_n,      c->d_status,   c->d_total,    c->d_nseg};
@@ -1198,6 +1386,8 @@ divas_status divas_fuse_init(divas_ctx** out, const divas_grid* grid, const uint
         return fail(nullptr, DIVAS_E_INVALID, "kind must be 0 (dense) or 1 (sparse)");
     }
     if (const char* why = params_problem(params)) return fail(nullptr, DIVAS_E_INVALID, why);
+    if ((params->flags & DIVAS_ORDER_BRICKS) && (grid->kind != 1 || grid->g % 8 != 0))
+        return fail(nullptr, DIVAS_E_INVALID, "brick order needs a sparse prior and g a multiple of 8");
 
     divas_ctx* c = new (std::nothrow) divas_ctx();
     if (!c) return fail(nullptr, DIVAS_E_OOM, "host allocation failed");
@@ -1223,15 +1413,9 @@ divas_status divas_fuse_init(divas_ctx** out, const divas_grid* grid, const uint
     c->F.eps = params->eps;
     c->F.tau_cons = params->tau_cons;
     c->F.pad = 0;
-    {  // multiply-shift divider for g (l = ceil(log2 g), m = 2^32 (2^l - g) / g + 1)
-        const uint32_t d = (uint32_t)grid->g;
-        int32_t l = 0;
-        while ((1ull << l) < d) ++l;
-        c->gdiv.d = d;
-        c->gdiv.l = l;
-        c->gdiv.m = (uint32_t)(((1ull << 32) * ((1ull << l) - d)) / d + 1);
-        c->gdiv.pad = 0;
-    }
+    c->gdiv = make_fast_div((uint32_t)grid->g);
+    c->brick = (params->flags & DIVAS_ORDER_BRICKS) != 0;
+    c->bdiv = make_fast_div((uint32_t)std::max(1, grid->g / 8));
     c->n_cells = (int64_t)grid->g * grid->g * grid->g;
     c->n_words = (c->n_cells + 31) / 32;
     c->n_tiles = (int32_t)((c->n_words + kTileSpan - 1) / kTileSpan);
@@ -1262,6 +1446,10 @@ divas_status divas_fuse_init(divas_ctx** out, const divas_grid* grid, const uint
     INIT_CUDA(cudaMalloc(&c->d_status, 4));
     INIT_CUDA(cudaMalloc(&c->d_total, 8));
     INIT_CUDA(cudaMalloc(&c->d_nseg, 8));
+    if (c->brick) {  // mask pyramids of up to 32 views of up to 2048 x 2048 pixels
+        c->pyr_cap = (int64_t)kMaxViews * pyramid_floats(2048, 2048);
+        INIT_CUDA(cudaMalloc(&c->pyr, c->pyr_cap * 4));
+    }
     INIT_CUDA(cudaMemsetAsync(c->d_status, 0, 4, s));
     INIT_CUDA(cudaMemsetAsync(c->seg_bits, 0, c->n_words * 4, s));
     c->cap = INT32_MAX;  // first pass only counts
@@ -2193,6 +2381,8 @@ extern "C" divas_status divas_fuse_dense_noalloc(const divas_grid* grid, const u
     if (n_views < 1 || n_views > kMaxViews)
         return noalloc_fail(DIVAS_E_INVALID, "n_views must be in 1..32");
     if (const char* why = params_problem(params)) return noalloc_fail(DIVAS_E_INVALID, why);
+    if (params->flags & DIVAS_ORDER_BRICKS)
+        return noalloc_fail(DIVAS_E_INVALID, "brick order needs a sparse prior");
     for (int32_t k = 0; k < n_views; ++k) {
         if (const char* why = camera_problem(&views[k].cam))
             return noalloc_fail(DIVAS_E_INVALID, why);
@@ -2290,7 +2480,7 @@ extern "C" divas_status divas_fuse_dense_noalloc(const divas_grid* grid, const u
                                                      item_pref, tile_count, tile_offset, done,
                                                      n_tiles, d_n, d_total, d_status);
     NA_CHECK("k_tile_count");
-    k_tile_emit<<<emit_blocks(n_words, sm_count), kThreads, 0, s>>>(
+    k_tile_emit<false><<<emit_blocks(n_words, sm_count), kThreads, 0, s>>>(
         occ_bits, n_words, cap, gdiv, item_pref, tile_offset, active, nullptr, nullptr);
     NA_CHECK("k_tile_emit");
     const int blocks = grid_for(n_cells, sm_count);

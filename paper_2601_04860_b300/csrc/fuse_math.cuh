@@ -57,6 +57,21 @@
 namespace divas {
 
 constexpr int kMaxViews = 32;
+
+// Programmatic dependent launch: a kernel launched with the programmatic
+// stream serialization attribute may start while its predecessor on the
+// stream finishes; it waits in wait_for_producer (which returns at once for a
+// kernel launched without the attribute) before it reads that kernel's
+// results, and a producer that lets its dependents start early says so with
+// allow_dependents.
+__device__ __forceinline__ void wait_for_producer() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
+__device__ __forceinline__ void allow_dependents() {
+    asm volatile("griddepcontrol.launch_dependents;" :::);
+}
+
 constexpr int kViewChunk = 4;  // views whose raster loads are issued together
 
 // ---------------------------------------------------------------------------

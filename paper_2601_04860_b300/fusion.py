@@ -31,10 +31,14 @@ class FusionParams:
     tau_cons: float = 0.5
     eps: float = 1e-12
     z_near: float = 1e-6
+    # sparse priors (g a multiple of 8): keep the active list in brick-major
+    # order (8^3 bricks), so that the fusion can skip whole warps' views that no
+    # voxel of the warp can vote in; per-voxel results are unchanged
+    brick_order: bool = False
 
     def c(self) -> L.DivasParams:
         return L.DivasParams(self.tau_mask, self.gamma, self.alpha1, self.tau_cons, self.eps,
-                             self.z_near, 0)
+                             self.z_near, L.ORDER_BRICKS if self.brick_order else 0)
 
 
 def _stream(stream=None) -> ctypes.c_void_p:

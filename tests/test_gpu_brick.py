@@ -1,0 +1,154 @@
+"""Brick-major active order (DIVAS_ORDER_BRICKS): the same per-voxel results as
+the linear order, bitwise, and the oracle's (GPU)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from paper_2601_04860_b300 import VoxelFusion, PreparedViews
+from tests import gpu_helpers as H
+
+pytestmark = pytest.mark.gpu
+
+P0 = oracle.Params()
+
+
+def brick_key(act: np.ndarray, g: int) -> np.ndarray:
+    """Position of each (i, j, k) in brick-major order: 8^3 bricks in linear
+    brick order, cells of a brick in linear order (x fastest in both)."""
+    a = act.astype(np.int64)
+    i, j, k = a[:, 0], a[:, 1], a[:, 2]
+    nb = g // 8
+    b = ((k // 8) * nb + (j // 8)) * nb + (i // 8)
+    return b * 512 + ((k % 8) * 8 + (j % 8)) * 8 + (i % 8)
+
+
+def to_linear(gpu: dict, g: int) -> dict:
+    """A sparse context's state with its active-list arrays permuted into
+    ascending linear order (the order compare() expects)."""
+    act = gpu["active"].astype(np.int64)
+    lin = (act[:, 2] * g + act[:, 1]) * g + act[:, 0]
+    o = np.argsort(lin, kind="stable")
+    out = dict(gpu)
+    for k in ("active", "W", "Z", "bits", "vmask", "score"):
+        out[k] = gpu[k][o]
+    return out
+
+
+def _plain_sparse():
+    """Config 1 (plain 64^3 grid) with its prior given as coordinates."""
+    import copy
+    wl = copy.copy(synth.config1())
+    lin = np.flatnonzero(wl.occ)
+    g = wl.grid.g
+    wl.coords = np.column_stack([lin % g, (lin // g) % g, lin // (g * g)]).astype(np.int32)
+    wl.occ = None
+    wl.name = "config1-sparse"
+    return wl
+
+
+def _small3():
+    return synth.config3(g=128, n_views=8, W=648, H=420, n_ell=300, n_occ=None,
+                         n_points=50_000)
+
+
+def _sparse_session():
+    mix = synth.session_mix(n_sessions=64, scale=0.25)
+    return next(synth.session_workload(r) for r in mix
+                if not r["dense"] and int(round(r["g"] * r.get("scale", 1.0))) % 8 == 0)
+
+
+# (workload builder, ceiling of its near-boundary fraction: 1.5 x the measured)
+WORKLOADS = [(_small3, 0.0263), (_plain_sparse, 0.0133), (_sparse_session, 0.06)]
+
+
+def _step(wl, d, brick: bool):
+    prm = H.to_params(P0)
+    prm.brick_order = brick
+    fu = VoxelFusion(wl.grid, coords=d["coords"], params=prm)
+    score = torch.empty(fu.n_active, dtype=torch.float32, device="cuda")
+    labels = torch.empty(len(d["points"]), dtype=torch.uint8, device="cuda")
+    views = PreparedViews(wl.cams, d["depth"], d["mask"], wl.mask_type)
+    fu.step(views, coords=d["coords"], score=score, xyz=d["points"], labels=labels)
+    torch.cuda.synchronize()
+    return fu, H.state_of(fu, score, labels)
+
+
+@pytest.mark.parametrize("which", [0, 1, 2])
+def test_brick_order_matches_linear_order_and_oracle(which):
+    build, max_flagged = WORKLOADS[which]
+    wl = build()
+    d = H.upload(wl)
+    fl, lin_state = _step(wl, d, brick=False)
+    fb, brick_state = _step(wl, d, brick=True)
+    g = wl.grid.g
+    key = brick_key(brick_state["active"], g)
+    assert (np.diff(key) > 0).all(), "active list not in brick-major order"
+    b = to_linear(brick_state, g)
+    for k in ("active", "W", "Z", "bits", "vmask", "score"):
+        assert np.array_equal(b[k], lin_state[k]), k
+    assert np.array_equal(b["seg_dense"], lin_state["seg_dense"])
+    assert np.array_equal(brick_state["labels"], lin_state["labels"])
+    s = H.compare(wl, b, P0, sample=H.sample_of(fb.n_active, 20_000),
+                  name=f"{H.current_test()} {wl.name} g={g}"
+                       f"{' contracted' if wl.grid.contracted else ''}",
+                  max_flagged=max_flagged)
+    assert s["voted"] > 0
+    fl.close()
+    fb.close()
+
+
+def test_brick_order_incremental_views():
+    """Views folded one call at a time onto a brick-ordered context give the
+    one-call result."""
+    wl = _small3()
+    d = H.upload(wl)
+    fb, ref = _step(wl, d, brick=True)
+    prm = H.to_params(P0)
+    prm.brick_order = True
+    fu = VoxelFusion(wl.grid, coords=d["coords"], params=prm)
+    h = wl.n_views // 2
+    fu.add_views(wl.cams[:h], d["depth"][:h], d["mask"][:h], mask_type=wl.mask_type)
+    fu.add_views(wl.cams[h:], d["depth"][h:], d["mask"][h:], mask_type=wl.mask_type)
+    score = torch.empty(fu.n_active, dtype=torch.float32, device="cuda")
+    fu.finalize(score=score)
+    st = H.state_of(fu, score)
+    for k in ("active", "W", "Z", "bits", "score"):
+        assert np.array_equal(st[k], ref[k]), k
+    fu.close()
+    fb.close()
+
+
+def test_brick_order_rejected_for_dense_priors():
+    wl = synth.config1()
+    d = H.upload(wl)
+    prm = H.to_params(P0)
+    prm.brick_order = True
+    with pytest.raises(Exception):
+        VoxelFusion(wl.grid, occ=d["occ"], params=prm)
+
+
+@pytest.mark.parametrize("mask_type", [oracle.MASK_F32, oracle.MASK_LOGIT_F32])
+def test_culling_with_f32_and_logit_masks(mask_type):
+    """The culled fusion on FP32 probability and logit masks (the per-view mask
+    type read at run time) gives the unculled linear-order result."""
+    import copy
+    wl = copy.copy(_small3())
+    prob = [m.view(np.float16).astype(np.float32) for m in wl.mask]
+    if mask_type == oracle.MASK_F32:
+        wl.mask = prob
+    else:
+        with np.errstate(divide="ignore"):
+            wl.mask = [np.log(p / (1.0 - p)).astype(np.float32) for p in prob]
+    wl.mask_type = mask_type
+    d = H.upload(wl)
+    fl, lin_state = _step(wl, d, brick=False)
+    fb, brick_state = _step(wl, d, brick=True)
+    b = to_linear(brick_state, wl.grid.g)
+    for k in ("active", "W", "Z", "bits", "vmask", "score"):
+        assert np.array_equal(b[k], lin_state[k]), k
+    assert np.array_equal(brick_state["labels"], lin_state["labels"])
+    assert (lin_state["Z"] > 0).any()
+    fl.close()
+    fb.close()
