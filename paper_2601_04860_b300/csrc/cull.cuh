@@ -68,6 +68,13 @@ __device__ __forceinline__ float from_ordered_key(int32_t k) {
     return __int_as_float(k ^ ((k >> 31) & 0x7fffffff));
 }
 
+// per-view constants the brick test reads with a lane-varying view index,
+// written to global memory by the pyramid kernel (one CTA per view)
+struct CullView {
+    float r[12];  // rows u (0..2), v (3..5), z (6..8) and constants (9..11)
+    CullC c;
+};
+
 // Max pyramid, levels 3..6, of one 64 x 64 pixel tile of one view per CTA
 // (grid: tiles x, tiles y, views; 256 threads).  Thread t reads column
 // t & 63 of rows 16 (t >> 6) .. + 15 (coalesced along rows), takes the max of
@@ -78,33 +85,47 @@ __device__ __forceinline__ float from_ordered_key(int32_t k) {
 // finishes; it waits for that kernel before it ends, so that a kernel waiting
 // for this one has also waited for the one before.
 __global__ void __launch_bounds__(256) k_mask_pyramid(const __grid_constant__ ViewBatch VB,
-                                                      const __grid_constant__ CullBatch CB) {
+                                                      const __grid_constant__ CullBatch CB,
+                                                      CullView* __restrict__ views_out) {
     __shared__ float l3[8][8];
     allow_dependents();
     const int v = blockIdx.z;
     const ViewC& V = VB.v[v];
     const CullC& C = CB.v[v];
     const int t = threadIdx.x, lane = t & 31;
+    if (blockIdx.x == 0 && blockIdx.y == 0 && t == 0) {
+        CullView cv;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) cv.r[k] = V.A[k];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) cv.r[9 + k] = V.C[k];
+        cv.c = C;
+        views_out[v] = cv;
+    }
     const int x = blockIdx.x * kPyrTile + (t & 63);
     const int yb = blockIdx.y * kPyrTile + 16 * (t >> 6);
-    // all 16 loads first (the mask type is uniform), then the maxima
+    // all 16 loads first, unconditional at clamped coordinates (the mask type
+    // is uniform), then the maxima over the pixels inside the raster
+    const int W = V.W, H = V.H;
+    const int xc = min(x, W - 1);
+    const bool xin = x < W;
     float val[16];
     if (V.mask_type == kMaskF16) {
-        const unsigned short* mp = reinterpret_cast<const unsigned short*>(V.mask);
+        const unsigned short* mp = reinterpret_cast<const unsigned short*>(V.mask) + xc;
+        unsigned short u[16];
 #pragma unroll
-        for (int r = 0; r < 16; ++r)
-            val[r] = x < V.W && yb + r < V.H
-                         ? __half2float(__ushort_as_half(__ldg(mp + (yb + r) * V.W + x)))
-                         : -INFINITY;
+        for (int r = 0; r < 16; ++r) u[r] = __ldg(mp + min(yb + r, H - 1) * W);
+#pragma unroll
+        for (int r = 0; r < 16; ++r) val[r] = __half2float(__ushort_as_half(u[r]));
     } else {
-        const float* mp = reinterpret_cast<const float*>(V.mask);
+        const float* mp = reinterpret_cast<const float*>(V.mask) + xc;
 #pragma unroll
-        for (int r = 0; r < 16; ++r)
-            val[r] = x < V.W && yb + r < V.H ? __ldg(mp + (yb + r) * V.W + x) : -INFINITY;
+        for (int r = 0; r < 16; ++r) val[r] = __ldg(mp + min(yb + r, H - 1) * W);
     }
     float m[2] = {-INFINITY, -INFINITY};
 #pragma unroll
-    for (int r = 0; r < 16; ++r) m[r >> 3] = fmaxf(m[r >> 3], val[r]);
+    for (int r = 0; r < 16; ++r)
+        if (xin && yb + r < H) m[r >> 3] = fmaxf(m[r >> 3], val[r]);
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
         float a = m[h];
@@ -141,143 +162,170 @@ __global__ void __launch_bounds__(256) k_mask_pyramid(const __grid_constant__ Vi
     wait_for_producer();
 }
 
-// per-view constants the cull reads with a lane-varying view index, staged in
-// shared memory once per CTA
-struct CullView {
-    float r[12];  // rows u (0..2), v (3..5), z (6..8) and constants (9..11)
-    CullC c;
-};
-
-// Stage the batch's cull constants (all threads of the CTA; ends with a
-// barrier).
-__device__ __forceinline__ void stage_cull_views(const ViewBatch& VB, const CullBatch& CB,
-                                                 CullView* sv) {
-    for (int v = threadIdx.x; v < VB.n; v += blockDim.x) {
-        const ViewC& V = VB.v[v];
+// Whether view V can see a voxel centre of the box [lo, hi] (projection
+// coordinates) in a pixel that passes its mask gate: false only when every
+// centre of the box is certain to project outside the raster or onto pixels
+// whose pyramid maximum is below the gate threshold.  One lane, eight corners.
+__device__ __forceinline__ bool box_may_vote(const CullView& cv, const float* pyr,
+                                             const float* lo, const float* hi) {
+    const float* r = cv.r;
+    const CullC& C = cv.c;
+    float umin = INFINITY, umax = -INFINITY, vmin = INFINITY, vmax = -INFINITY;
+    float zmin = INFINITY, xm = 0.f;
 #pragma unroll
-        for (int k = 0; k < 9; ++k) sv[v].r[k] = V.A[k];
+    for (int a = 0; a < 3; ++a) xm = fmaxf(xm, fmaxf(fabsf(lo[a]), fabsf(hi[a])));
 #pragma unroll
-        for (int k = 0; k < 3; ++k) sv[v].r[9 + k] = V.C[k];
-        sv[v].c = CB.v[v];
+    for (int corner = 0; corner < 8; ++corner) {
+        const float x0 = (corner & 1) ? hi[0] : lo[0];
+        const float x1 = (corner & 2) ? hi[1] : lo[1];
+        const float x2 = (corner & 4) ? hi[2] : lo[2];
+        const float pz = __fmaf_rn(r[6], x0, __fmaf_rn(r[7], x1, __fmaf_rn(r[8], x2, r[11])));
+        const float pu = __fmaf_rn(r[0], x0, __fmaf_rn(r[1], x1, __fmaf_rn(r[2], x2, r[9])));
+        const float pv = __fmaf_rn(r[3], x0, __fmaf_rn(r[4], x1, __fmaf_rn(r[5], x2, r[10])));
+        zmin = fminf(zmin, pz);
+        const float inv = rcp_nr(pz);
+        const float u = __fmul_rn(pu, inv), w = __fmul_rn(pv, inv);
+        umin = fminf(umin, u);
+        umax = fmaxf(umax, u);
+        vmin = fminf(vmin, w);
+        vmax = fmaxf(vmax, w);
     }
-    __syncthreads();
+    // S of each row over the box: sum_j |row_j| max_j |x_j| + |constant|
+    const float sz = __fmaf_ru(C.sz, xm, C.cz);
+    if (!(zmin > 0x1p-18f * sz)) return true;  // the box reaches too close to the camera plane
+    const float su = __fmaf_ru(C.su, xm, C.cu), sv = __fmaf_ru(C.sv, xm, C.cv);
+    const float au = fmaxf(fabsf(umin), fabsf(umax));
+    const float av = fmaxf(fabsf(vmin), fabsf(vmax));
+    // 1 / zmin within an ulp, taken up by one ulp more
+    const float iz = __fmul_ru(rcp_nr(zmin), 1.f + 0x1p-22f);
+    const float mu = __fmaf_ru(0x1p-18f, __fmaf_ru(__fmaf_ru(au, sz, su), iz, au), 2.f);
+    const float mv = __fmaf_ru(0x1p-18f, __fmaf_ru(__fmaf_ru(av, sz, sv), iz, av), 2.f);
+    const float fu0 = umin - mu, fu1 = umax + mu, fv0 = vmin - mv, fv1 = vmax + mv;
+    if (!(fu0 <= fu1 && fv0 <= fv1)) return true;  // NaN: no bound
+    if (fu1 < 0.f || fv1 < 0.f || fu0 >= (float)C.W || fv0 >= (float)C.H) return false;
+    const int32_t iu0 = (int32_t)floorf(fmaxf(fu0, 0.f));
+    const int32_t iu1 = (int32_t)floorf(fminf(fu1, (float)(C.W - 1)));
+    const int32_t iv0 = (int32_t)floorf(fmaxf(fv0, 0.f));
+    const int32_t iv1 = (int32_t)floorf(fminf(fv1, (float)(C.H - 1)));
+    const int32_t span = max(iu1 - iu0, iv1 - iv0) + 1;
+    const int32_t L = max(kPyrL0, (32 - __clz(span - 1)) - 1);
+    if (L >= kPyrL0 + kPyrLevels) return true;  // too wide for the pyramid
+    // the (at most 3 x 3) texels of the rectangle; indices past it are clamped
+    // to it (repeated texels do not change the maximum), so that all loads are
+    // issued before the first is used
+    const float* lev = pyr + C.off[L - kPyrL0];
+    const int32_t lw = C.lw[L - kPyrL0];
+    const int32_t tx0 = iu0 >> L, tx1 = iu1 >> L, ty0 = iv0 >> L, ty1 = iv1 >> L;
+    const int32_t xs[3] = {tx0, min(tx0 + 1, tx1), min(tx0 + 2, tx1)};
+    const int32_t ys[3] = {ty0, min(ty0 + 1, ty1), min(ty0 + 2, ty1)};
+    float t[9];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) t[3 * a + b] = __ldg(lev + ys[a] * lw + xs[b]);
+    float mx = -INFINITY;
+#pragma unroll
+    for (int a = 0; a < 9; ++a) mx = fmaxf(mx, t[a]);
+    return mx >= C.thr;
 }
 
-// Views [0, n) that some lane of the warp may vote in, as a bitmask (bit v).
-// live: this lane holds a voxel with a position (the rest are ignored); p: the
-// lane's projection coordinates.  Warp-uniform: every lane calls it.
-__device__ __forceinline__ uint32_t cull_views(const CullView* sv, const float* pyr, int32_t n,
-                                               bool live, const float* p) {
+// The voxel centres of brick (bi, bj, bk) (8^3 cells) as a box in projection
+// coordinates: lattice coordinates n = 2 idx + 1 on plain grids (exact); on
+// contracted grids, the contracted box of centres mapped by x = c s(|c|) with
+// s(rho) = 1 for rho <= 1 and 1 / (rho (2 - rho)) above (increasing in rho),
+// so x lies in the interval product of c's box and [s(rho_min), s(rho_max)].
+// FP32 with directed rounding (each bound rounded outwards), then widened by
+// 2^-18 of its magnitude to hold the FP32 centres of the voxels.  False when
+// the box reaches |c| >= 2 (no bound on the world positions).
+__device__ __forceinline__ bool brick_box(uint32_t bi, uint32_t bj, uint32_t bk, const GridC& G,
+                                          float* lo, float* hi) {
+    const uint32_t b3[3] = {bi, bj, bk};
+    if (!G.contracted) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            lo[a] = (float)(16 * b3[a] + 1);
+            hi[a] = (float)(16 * b3[a] + 15);
+        }
+        return true;
+    }
+    float clo[3], chi[3], r2min = 0.f, r2max = 0.f;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        clo[a] = __fmaf_rd((float)(8 * b3[a]) + 0.5f, G.h, G.origin[a]);
+        chi[a] = __fmaf_ru((float)(8 * b3[a]) + 7.5f, G.h, G.origin[a]);
+        const float near = clo[a] > 0.f ? clo[a] : (chi[a] < 0.f ? -chi[a] : 0.f);
+        const float far = fmaxf(fabsf(clo[a]), fabsf(chi[a]));
+        r2min = __fmaf_rd(near, near, r2min);
+        r2max = __fmaf_ru(far, far, r2max);
+    }
+    const float rmin = __fsqrt_rd(r2min), rmax = __fsqrt_ru(r2max);
+    if (!(rmax < 2.f)) return false;
+    // s(rmin) rounded down, s(rmax) rounded up
+    const float smin = rmin <= 1.f ? 1.f : __frcp_rd(__fmul_ru(rmin, __fsub_ru(2.f, rmin)));
+    const float smax = rmax <= 1.f ? 1.f : __frcp_ru(__fmul_rd(rmax, __fsub_rd(2.f, rmax)));
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float l = fminf(fminf(__fmul_rd(clo[a], smin), __fmul_rd(clo[a], smax)),
+                              fminf(__fmul_rd(chi[a], smin), __fmul_rd(chi[a], smax)));
+        const float h = fmaxf(fmaxf(__fmul_ru(clo[a], smin), __fmul_ru(clo[a], smax)),
+                              fmaxf(__fmul_ru(chi[a], smin), __fmul_ru(chi[a], smax)));
+        const float slack = __fmaf_ru(0x1p-18f, fmaxf(fabsf(l), fabsf(h)), 0x1p-100f);
+        lo[a] = __fsub_rd(l, slack);
+        hi[a] = __fadd_ru(h, slack);
+    }
+    return true;
+}
+
+// Per brick, the views (bit v) that some voxel of the brick may vote in; bricks
+// without an occupied cell (brick-major occupancy words all zero) get 0.  A
+// warp takes P = min(8, 32 / n) bricks at a time, lane l testing view l % n of
+// brick l / n.  Reads the compaction's bitfield, the pyramids and the views'
+// constants: waits for its predecessor first.
+//
+// wait_first: the predecessor is the pyramid kernel, waited for before any
+// read.  Otherwise the predecessor is the compaction's emit kernel, launched
+// after the count and pyramid kernels it waited for: both have completed when
+// this kernel starts, and it waits for the emit only before it ends (so that
+// a kernel waiting for this one has waited for the emit too).
+__global__ void __launch_bounds__(256) k_brick_views(const CullView* __restrict__ sv, int32_t n,
+                                                     const float* __restrict__ pyr, GridC G,
+                                                     FastDiv bdiv,
+                                                     const uint32_t* __restrict__ occ_bits,
+                                                     int64_t n_bricks,
+                                                     uint32_t* __restrict__ brick_keep,
+                                                     int32_t wait_first) {
+    if (wait_first) wait_for_producer();  // the views' constants and the pyramids
+    allow_dependents();
     const int lane = threadIdx.x & 31;
-    int32_t kmin[3], kmax[3];
+    const int P = min(8, 32 / n);
+    const int slot = lane / n, view = lane - slot * n;
+    const int64_t n_warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t b0 = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * P; b0 < n_bricks;
+         b0 += n_warps * P) {
+        // occupancy of the P bricks: lane l reads word l & 15 of brick 2 k + (l >> 4)
+        uint32_t occupied = 0u;  // bit p: brick b0 + p holds an occupied cell
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        const int32_t k = ordered_key(p[a]);
-        kmin[a] = __reduce_min_sync(0xffffffffu, live ? k : INT32_MAX);
-        kmax[a] = __reduce_max_sync(0xffffffffu, live ? k : INT32_MIN);
-    }
-    if (kmin[0] == INT32_MAX) return 0u;  // no voxel to vote for
-    float lo[3], hi[3], xm = 0.f;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        lo[a] = from_ordered_key(kmin[a]);
-        hi[a] = from_ordered_key(kmax[a]);
-        xm = fmaxf(xm, fmaxf(fabsf(lo[a]), fabsf(hi[a])));
-    }
-    const int half = lane & 1;
-    uint32_t keep_all = 0u;
-    for (int32_t v0 = 0; v0 < n; v0 += 16) {
-        const int32_t q = v0 + (lane >> 1);
-        const bool has = q < n;
-        float umin = INFINITY, umax = -INFINITY, vmin = INFINITY, vmax = -INFINITY;
-        float zmin = INFINITY;
-        if (has) {
-            const float* r = sv[q].r;
-#pragma unroll
-            for (int cc = 0; cc < 4; ++cc) {
-                const int corner = 4 * half + cc;
-                const float x0 = (corner & 1) ? hi[0] : lo[0];
-                const float x1 = (corner & 2) ? hi[1] : lo[1];
-                const float x2 = (corner & 4) ? hi[2] : lo[2];
-                const float pz = __fmaf_rn(r[6], x0, __fmaf_rn(r[7], x1, __fmaf_rn(r[8], x2, r[11])));
-                const float pu = __fmaf_rn(r[0], x0, __fmaf_rn(r[1], x1, __fmaf_rn(r[2], x2, r[9])));
-                const float pv = __fmaf_rn(r[3], x0, __fmaf_rn(r[4], x1, __fmaf_rn(r[5], x2, r[10])));
-                zmin = fminf(zmin, pz);
-                const float inv = rcp_nr(pz);
-                const float u = __fmul_rn(pu, inv), w = __fmul_rn(pv, inv);
-                umin = fminf(umin, u);
-                umax = fmaxf(umax, u);
-                vmin = fminf(vmin, w);
-                vmax = fmaxf(vmax, w);
-            }
+        for (int k = 0; k < 4; ++k) {
+            const int64_t b = b0 + 2 * k + (lane >> 4);
+            const uint32_t wv = (2 * k + (lane >> 4) < P && b < n_bricks)
+                                    ? __ldg(occ_bits + b * 16 + (lane & 15)) : 0u;
+            const uint32_t m = __ballot_sync(0xffffffffu, wv != 0u);
+            occupied |= ((m & 0xffffu) ? 1u : 0u) << (2 * k);
+            occupied |= ((m >> 16) ? 1u : 0u) << (2 * k + 1);
         }
-        // the partner lane holds the other four corners
-        umin = fminf(umin, __shfl_xor_sync(0xffffffffu, umin, 1));
-        umax = fmaxf(umax, __shfl_xor_sync(0xffffffffu, umax, 1));
-        vmin = fminf(vmin, __shfl_xor_sync(0xffffffffu, vmin, 1));
-        vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, 1));
-        zmin = fminf(zmin, __shfl_xor_sync(0xffffffffu, zmin, 1));
-        bool keep = false;
-        float mx = -INFINITY;
-        int32_t L = 0, tx0 = 0, tx1 = -1, ty0 = 0, ty1 = -1;
-        if (has) {
-            const CullC& C = sv[q].c;
-            // S of each row over the box: sum_j |row_j| max_j |x_j| + |constant|
-            const float sz = __fmaf_ru(C.sz, xm, C.cz);
-            if (!(zmin > 0x1p-18f * sz)) {
-                keep = true;  // the box reaches too close to (or behind) the camera plane
-            } else {
-                const float su = __fmaf_ru(C.su, xm, C.cu), sv_ = __fmaf_ru(C.sv, xm, C.cv);
-                const float au = fmaxf(fabsf(umin), fabsf(umax));
-                const float av = fmaxf(fabsf(vmin), fabsf(vmax));
-                // 1 / zmin within an ulp, taken up by one ulp more
-                const float iz = __fmul_ru(rcp_nr(zmin), 1.f + 0x1p-22f);
-                const float mu = __fmaf_ru(0x1p-18f, __fmaf_ru(__fmaf_ru(au, sz, su), iz, au), 2.f);
-                const float mv = __fmaf_ru(0x1p-18f, __fmaf_ru(__fmaf_ru(av, sz, sv_), iz, av), 2.f);
-                const float fu0 = umin - mu, fu1 = umax + mu, fv0 = vmin - mv, fv1 = vmax + mv;
-                if (!(fu0 <= fu1 && fv0 <= fv1)) {
-                    keep = true;  // NaN: no bound
-                } else if (fu1 < 0.f || fv1 < 0.f || fu0 >= (float)C.W || fv0 >= (float)C.H) {
-                    keep = false;  // every centre projects outside the raster
-                } else {
-                    const int32_t iu0 = (int32_t)floorf(fmaxf(fu0, 0.f));
-                    const int32_t iu1 = (int32_t)floorf(fminf(fu1, (float)(C.W - 1)));
-                    const int32_t iv0 = (int32_t)floorf(fmaxf(fv0, 0.f));
-                    const int32_t iv1 = (int32_t)floorf(fminf(fv1, (float)(C.H - 1)));
-                    const int32_t span = max(iu1 - iu0, iv1 - iv0) + 1;
-                    L = max(kPyrL0, (32 - __clz(span - 1)) - 1);
-                    if (L >= kPyrL0 + kPyrLevels) {
-                        keep = true;  // too wide for the pyramid
-                    } else {
-                        tx0 = iu0 >> L;
-                        tx1 = iu1 >> L;
-                        ty0 = iv0 >> L;
-                        ty1 = iv1 >> L;
-                    }
-                }
-            }
+        const int64_t b = b0 + slot;
+        bool vote = false;
+        if (slot < P && b < n_bricks && ((occupied >> slot) & 1u)) {
+            const uint32_t r = fast_div((uint32_t)b, bdiv), bk = fast_div(r, bdiv);
+            const uint32_t bi = (uint32_t)b - r * bdiv.d, bj = r - bk * bdiv.d;
+            float lo[3], hi[3];
+            vote = !brick_box(bi, bj, bk, G, lo, hi) || box_may_vote(sv[view], pyr, lo, hi);
         }
-        // the pair splits the (at most 3 x 3) texels: rows ty0, ty0 + 1 on the
-        // even lane, row ty0 + 2 on the odd one
-        if (tx1 >= tx0) {
-            const CullC& C = sv[q].c;
-            const float* lev = pyr + C.off[L - kPyrL0];
-            const int32_t lw = C.lw[L - kPyrL0];
-            const int32_t ya = half ? ty0 + 2 : ty0, yb = half ? ty0 + 2 : min(ty0 + 1, ty1);
-            for (int32_t y = ya; y <= min(yb, ty1); ++y)
-                for (int32_t xx = tx0; xx <= tx1; ++xx) mx = fmaxf(mx, __ldg(lev + y * lw + xx));
-        }
-        mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
-        if (has && tx1 >= tx0) keep = mx >= sv[q].c.thr;
-        // view q's verdict sits on lanes 2 (q - v0) and 2 (q - v0) + 1
-        uint32_t b = __ballot_sync(0xffffffffu, keep && half == 0) & 0x55555555u;
-        b = (b | (b >> 1)) & 0x33333333u;
-        b = (b | (b >> 2)) & 0x0f0f0f0fu;
-        b = (b | (b >> 4)) & 0x00ff00ffu;
-        b = (b | (b >> 8)) & 0x0000ffffu;
-        keep_all |= b << v0;
+        const uint32_t m = __ballot_sync(0xffffffffu, vote);
+        if (view == 0 && slot < P && b < n_bricks)
+            brick_keep[b] = n == 32 ? m : (m >> (slot * n)) & ((1u << n) - 1u);
     }
-    return keep_all;
+    if (!wait_first) wait_for_producer();
 }
 
 // Fold the views of `keep` (ascending view order, four at a time: the same

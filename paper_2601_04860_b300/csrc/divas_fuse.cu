@@ -163,18 +163,84 @@ __device__ __forceinline__ uint32_t bytes_nonzero16(uint4 v) {
     return r;
 }
 
-template <bool kFromBits>
+// 8 occupancy bytes -> 8 bits (bit t = byte t != 0)
+__device__ __forceinline__ uint32_t bytes_nonzero8(uint2 v) {
+    const uint32_t x[2] = {v.x, v.y};
+    uint32_t r = 0;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const uint32_t m = __vcmpne4(x[k], 0u) & 0x01010101u;
+        r |= ((m * 0x01020408u) >> 24) << (4 * k);
+    }
+    return r;
+}
+
+// The brick-major words of one tile (64 bricks of 8^3 cells, 1024 words) from
+// the uint8 prior (g a multiple of 8): thread t reads the 8-byte row segments
+// of slices 2 (t & 3) and 2 (t & 3) + 1 of brick t >> 2 (lanes 4 apart hold
+// neighbouring bricks, so a load instruction covers 64 contiguous bytes of 4
+// rows) and packs them into that brick's words 4 (t & 3) .. + 3, which it
+// writes to the bitfield and to sw (the tile's words in shared memory); with
+// score_zero, the cells' dense scores are zeroed on the way.
+__device__ __forceinline__ void brick_words_from_bytes(const uint8_t* __restrict__ occ, int32_t g,
+                                                       const FastDiv& bdiv, int64_t n_words,
+                                                       uint32_t* __restrict__ bits,
+                                                       float* __restrict__ score_zero,
+                                                       uint32_t* sw) {
+    const int t = threadIdx.x;
+    const int64_t b = (int64_t)blockIdx.x * 64 + (t >> 2);
+    const int rg = t & 3;
+    uint32_t wv[4] = {0u, 0u, 0u, 0u};
+    if ((b + 1) * 16 <= n_words) {
+        const uint32_t r = fast_div((uint32_t)b, bdiv), bk = fast_div(r, bdiv);
+        const uint32_t bi = (uint32_t)b - r * bdiv.d, bj = r - bk * bdiv.d;
+        uint2 raw[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {  // slice 2 rg + (q >> 3), row q & 7
+            const int64_t row = ((int64_t)(bk * 8 + 2 * rg + (q >> 3)) * g + (bj * 8 + (q & 7))) * g;
+            raw[q] = __ldcs(reinterpret_cast<const uint2*>(occ + row + bi * 8));
+        }
+#pragma unroll
+        for (int q = 0; q < 16; ++q) wv[q >> 2] |= bytes_nonzero8(raw[q]) << (8 * (q & 3));
+        if (score_zero) {
+            const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+                const int64_t row =
+                    ((int64_t)(bk * 8 + 2 * rg + (q >> 3)) * g + (bj * 8 + (q & 7))) * g + bi * 8;
+                __stcs(reinterpret_cast<float4*>(score_zero + row), z);
+                __stcs(reinterpret_cast<float4*>(score_zero + row) + 1, z);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) bits[b * 16 + 4 * rg + k] = wv[k];
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) sw[(t >> 2) * 16 + 4 * rg + k] = wv[k];
+    __syncthreads();
+}
+
+// kMode: 0 dense prior (linear words), 1 words already in the bitfield
+// (sparse, either layout), 2 dense prior into brick-major words
+template <int kMode>
 __global__ void __launch_bounds__(kThreads) k_tile_count(
     const uint8_t* __restrict__ occ, uint32_t* __restrict__ bits, int64_t n_cells, int64_t n_words,
     int64_t cap, uint32_t* __restrict__ item_pref, uint32_t* __restrict__ tile_count,
     uint32_t* __restrict__ tile_offset, uint32_t* __restrict__ done, int32_t n_tiles,
-    int32_t* __restrict__ d_n, int64_t* __restrict__ d_total, int32_t* __restrict__ status) {
+    int32_t* __restrict__ d_n, int64_t* __restrict__ d_total, int32_t* __restrict__ status,
+    int32_t g, FastDiv bdiv, float* __restrict__ score_zero) {
     __shared__ bool s_last;
+    __shared__ uint32_t sw[kMode == 2 ? kTileSpan : 1];
     allow_dependents();  // the emit may be scheduled now; it waits for this grid's end
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t g0 = (int64_t)blockIdx.x * kTileGroups + warp * kGroupsPerWarp;
     uint32_t word[kGroupsPerWarp];
-    if (kFromBits) {
+    if (kMode == 2) {
+        brick_words_from_bytes(occ, g, bdiv, n_words, bits, score_zero, sw);
+#pragma unroll
+        for (int q = 0; q < kGroupsPerWarp; ++q)
+            word[q] = sw[(warp * kGroupsPerWarp + q) * 32 + lane];
+    } else if (kMode == 1) {
 #pragma unroll
         for (int q = 0; q < kGroupsPerWarp; ++q) {
             const int64_t w = (g0 + q) * 32 + lane;
@@ -581,33 +647,47 @@ __global__ void __launch_bounds__(kThreads, kContracted ? 5 : 6) k_fuse_fin(
 }
 
 // ---------------------------------------------------------------------------
-// fusion + finalize with warp-level view culling (brick-ordered sparse sets):
-// per warp of 32 voxels, the views whose mask gate no voxel of the warp can
-// pass are skipped (cull_views); the kept views are folded in view order with
+// fusion + finalize with warp-level view culling (brick-ordered active lists):
+// per warp of 32 voxels, the views that no brick of the warp's voxels may vote
+// in (k_brick_views) are skipped; the kept views are folded in view order with
 // the arithmetic of k_fuse_fin, so every result is bitwise that of k_fuse_fin.
 // kMT: the batch's mask type when all views carry binary16 masks, else -1.
 // ---------------------------------------------------------------------------
 template <bool kAccumulate, bool kContracted, int kMT>
 __global__ void __launch_bounds__(kThreads, kContracted ? 5 : 6) k_fuse_fin_cull(
     const uint32_t* __restrict__ active, const int32_t* __restrict__ d_n, GridC G, FuseC F,
-    const __grid_constant__ ViewBatch VB, const __grid_constant__ CullBatch CB,
-    float* __restrict__ W, float* __restrict__ Z, uint32_t* __restrict__ bits,
-    float* __restrict__ score_out, uint32_t* __restrict__ seg_bits, int32_t clear_bits,
-    uint32_t* __restrict__ seg_out, int32_t clear_out) {
-    __shared__ CullView sv[kMaxViews];
-    stage_cull_views(VB, CB, sv);  // kernel parameters only
-    wait_for_producer();           // the active list, its length and the mask pyramid
+    const __grid_constant__ ViewBatch VB, const uint32_t* __restrict__ brick_keep,
+    float* __restrict__ W, float* __restrict__ Z, uint32_t* __restrict__ bits, int32_t dense,
+    float* __restrict__ score_out, int32_t score_zeroed, uint32_t* __restrict__ seg_bits,
+    int32_t clear_bits, uint32_t* __restrict__ seg_out, int32_t clear_out) {
+    wait_for_producer();  // the active list, its length and the bricks' kept views
     const int lane = threadIdx.x & 31;
     const int32_t gw = (int32_t)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int32_t nw = (int32_t)((gridDim.x * blockDim.x) >> 5);
     const int32_t n = *d_n;
+    const uint32_t nb = (uint32_t)G.g >> 3;
     for (int32_t base = gw * 32; base < n; base += nw * 32) {
         const int32_t a = base + lane;
         const bool live = a < n;
         const uint32_t pk = live ? __ldg(active + a) : 0u;
+        const uint32_t bk_index =
+            (((pk >> 23) * nb + ((pk >> 13) & 127u)) * nb + ((pk & 1023u) >> 3));
+        const uint32_t mine = live ? __ldg(brick_keep + bk_index) : 0u;
+        const uint32_t keep = __reduce_or_sync(0xffffffffu, mine);
+        if (!kAccumulate && keep == 0u && !clear_bits) {
+            // no view can vote for any voxel of the warp: zero accumulators and
+            // P = 0 (a zeroed score grid holds it already), no seg bit to set or
+            // clear
+            if (live) {
+                W[a] = 0.f;
+                Z[a] = 0.f;
+                bits[a] = 0u;
+                if (score_out && !score_zeroed)
+                    score_out[dense ? packed_lin(pk, G.g) : (int64_t)a] = 0.f;
+            }
+            continue;
+        }
         const VoxelGeom vg = voxel_geom<kContracted>(pk, G, F.gamma);
-        const uint32_t keep = cull_views(sv, CB.pyr, VB.n, live && vg.ok,
-                                         kContracted ? vg.xs : vg.xh);
         bool seg = false;
         int64_t lin = 0;
         if (live) {
@@ -625,7 +705,9 @@ __global__ void __launch_bounds__(kThreads, kContracted ? 5 : 6) k_fuse_fin_cull
             const float p = z > F.eps ? __fdiv_rn(w, z) : 0.f;
             seg = p >= F.tau_cons;
             lin = packed_lin(pk, G.g);
-            if (score_out) score_out[a] = p;
+            // a zeroed score grid keeps its +0 where P = +0
+            if (score_out && !(score_zeroed && __float_as_uint(p) == 0u))
+                score_out[dense ? lin : (int64_t)a] = p;
         }
         seg_epilogue(live, seg, lin, seg_bits, clear_bits != 0, seg_out, clear_out != 0);
     }
@@ -909,6 +991,8 @@ struct divas_ctx {
     FastDiv bdiv;        // division by g / 8 (brick order)
     float* pyr = nullptr;  // brick order: mask max pyramids of a view batch
     int64_t pyr_cap = 0;   // its capacity in floats
+    uint32_t* brick_keep = nullptr;  // brick order: per brick, the views it may vote in
+    CullView* cull_views = nullptr;  // brick order: the batch's views for the brick test
     void* sat = nullptr;   // tuple mode: integral-image scratch, grown on demand
     size_t sat_bytes = 0;
     void* wt = nullptr;    // depth weighting: selection state and histograms, grown on demand
@@ -1202,15 +1286,17 @@ bool make_cull(const divas_ctx* c, const ViewBatch& vb, CullBatch& cb) {
 }
 
 template <bool kAccumulate, bool kContracted>
-cudaError_t launch_fuse_fin_cull(const divas_ctx* c, const ViewBatch& vb, const CullBatch& cb,
-                                 int blocks, cudaStream_t s, float* score_out, bool clear_bits,
-                                 uint32_t* seg_out, bool clear_out) {
+cudaError_t launch_fuse_fin_cull(const divas_ctx* c, const ViewBatch& vb, int blocks,
+                                 cudaStream_t s, float* score_out, bool score_zeroed,
+                                 bool clear_bits, uint32_t* seg_out, bool clear_out) {
     bool f16 = true;
     for (int32_t i = 0; i < vb.n && f16; ++i) f16 = vb.v[i].mask_type == kMaskF16;
 #define DIVAS_FUSE_CULL(MT)                                                                       \
     launch_dependent(k_fuse_fin_cull<kAccumulate, kContracted, MT>, blocks, s,                    \
-                     (const uint32_t*)c->active, (const int32_t*)c->d_n, c->G, c->F, vb, cb,      \
-                     c->W, c->Z, c->bits, score_out, c->seg_bits, (int32_t)(clear_bits ? 1 : 0), \
+                     (const uint32_t*)c->active, (const int32_t*)c->d_n, c->G, c->F, vb,          \
+                     (const uint32_t*)c->brick_keep,                                               \
+                     c->W, c->Z, c->bits, (int32_t)(c->grid.kind == 0 ? 1 : 0), score_out,        \
+                     (int32_t)(score_zeroed ? 1 : 0), c->seg_bits, (int32_t)(clear_bits ? 1 : 0), \
                      seg_out, (int32_t)(clear_out ? 1 : 0))
     const cudaError_t e = f16 ? DIVAS_FUSE_CULL(kMaskF16) : DIVAS_FUSE_CULL(-1);
 #undef DIVAS_FUSE_CULL
@@ -1218,9 +1304,10 @@ cudaError_t launch_fuse_fin_cull(const divas_ctx* c, const ViewBatch& vb, const 
 }
 
 // the mask pyramids, then the culling fusion
-cudaError_t launch_culled(const divas_ctx* c, bool accumulate, const ViewBatch& vb,
-                          const CullBatch& cb, cudaStream_t s, float* score_out, bool clear_bits,
-                          uint32_t* seg_out, bool clear_out) {
+// the mask pyramids of a batch (programmatic dependent launch: the kernel reads
+// the masks only, and waits for its predecessor before it ends)
+cudaError_t launch_pyramid(const divas_ctx* c, const ViewBatch& vb, const CullBatch& cb,
+                           cudaStream_t s) {
     int32_t wmax = 1, hmax = 1;
     for (int32_t k = 0; k < vb.n; ++k) {
         wmax = std::max(wmax, vb.v[k].W);
@@ -1236,28 +1323,60 @@ cudaError_t launch_culled(const divas_ctx* c, bool accumulate, const ViewBatch& 
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    cudaError_t e = cudaLaunchKernelEx(&cfg, k_mask_pyramid, vb, cb);
-    if (e != cudaSuccess) return e;
-    const int blocks = grid_for(c->cap, c->sm_count);
-    if (c->G.contracted)
-        return accumulate ? launch_fuse_fin_cull<true, true>(c, vb, cb, blocks, s, score_out,
-                                                             clear_bits, seg_out, clear_out)
-                          : launch_fuse_fin_cull<false, true>(c, vb, cb, blocks, s, score_out,
-                                                              clear_bits, seg_out, clear_out);
-    return accumulate ? launch_fuse_fin_cull<true, false>(c, vb, cb, blocks, s, score_out,
-                                                          clear_bits, seg_out, clear_out)
-                      : launch_fuse_fin_cull<false, false>(c, vb, cb, blocks, s, score_out,
-                                                           clear_bits, seg_out, clear_out);
+    return cudaLaunchKernelEx(&cfg, k_mask_pyramid, vb, cb, c->cull_views);
 }
 
+// the bricks' kept views: several bricks per warp, one wave of CTAs
+cudaError_t launch_brick_views(const divas_ctx* c, const ViewBatch& vb, cudaStream_t s,
+                               bool wait_first) {
+    const int64_t n_bricks = c->n_words / 16;
+    const int64_t per_warp = std::min<int64_t>(8, 32 / std::max(1, vb.n));
+    const int64_t warps = (n_bricks + per_warp - 1) / per_warp;
+    return launch_dependent(
+        k_brick_views,
+        (int)std::max<int64_t>(1, std::min<int64_t>((warps + 7) / 8, (int64_t)c->sm_count * 8)),
+        s, (const CullView*)c->cull_views, vb.n, (const float*)c->pyr, c->G, c->bdiv,
+        (const uint32_t*)c->occ_bits, n_bricks, c->brick_keep, (int32_t)(wait_first ? 1 : 0));
+}
+
+// the culling fusion (the bricks' kept views are in place)
+cudaError_t launch_culled_fuse(const divas_ctx* c, bool accumulate, const ViewBatch& vb,
+                               cudaStream_t s, float* score_out, bool score_zeroed,
+                               bool clear_bits, uint32_t* seg_out, bool clear_out) {
+    const int blocks = grid_for(c->cap, c->sm_count);
+    if (c->G.contracted)
+        return accumulate ? launch_fuse_fin_cull<true, true>(
+                   c, vb, blocks, s, score_out, score_zeroed, clear_bits, seg_out, clear_out)
+                          : launch_fuse_fin_cull<false, true>(
+                   c, vb, blocks, s, score_out, score_zeroed, clear_bits, seg_out, clear_out);
+    return accumulate ? launch_fuse_fin_cull<true, false>(
+                   c, vb, blocks, s, score_out, score_zeroed, clear_bits, seg_out, clear_out)
+                      : launch_fuse_fin_cull<false, false>(
+                   c, vb, blocks, s, score_out, score_zeroed, clear_bits, seg_out, clear_out);
+}
+
+// whether a batch on this context is fused with culling (then cb holds its constants)
+bool culling(const divas_ctx* c, const ViewBatch& vb, CullBatch& cb) {
+    return c->brick && c->pyr && c->brick_keep && c->cull_views && vb.n > 0 && make_cull(c, vb, cb);
+}
+
+// score_zeroed: score_out holds +0 at every active voxel (brick contexts skip
+// storing a P of +0 there)
+// prepared: the batch's pyramids and the bricks' kept views were launched with
+// the compaction (one-call step)
 cudaError_t launch_fuse_fin(const divas_ctx* c, bool accumulate, const ViewBatch& vb,
                             cudaStream_t s, float* score_out, bool clear_bits, uint32_t* seg_out,
-                            bool clear_out, bool zero) {
-    if (c->brick && c->pyr && vb.n > 0) {
-        CullBatch cb;
-        if (make_cull(c, vb, cb))
-            return launch_culled(c, accumulate, vb, cb, s, score_out, clear_bits, seg_out,
-                                 clear_out);
+                            bool clear_out, bool zero, bool score_zeroed = false,
+                            bool prepared = false) {
+    CullBatch cb;
+    if (prepared || culling(c, vb, cb)) {
+        if (!prepared) {
+            cudaError_t e = launch_pyramid(c, vb, cb, s);
+            if (e == cudaSuccess) e = launch_brick_views(c, vb, s, true);
+            if (e != cudaSuccess) return e;
+        }
+        return launch_culled_fuse(c, accumulate, vb, s, score_out, score_zeroed, clear_bits,
+                                  seg_out, clear_out);
     }
     const int chunks = (vb.n + kViewChunk - 1) / kViewChunk;
     const int blocks = grid_for(zero ? std::max<int64_t>(c->cap, c->n_words) : c->cap, c->sm_count);
@@ -1283,11 +1402,20 @@ int emit_blocks(int64_t n_words, int32_t sm_count) {
 // occupancy -> bits -> tile counts -> active list (no allocation); seg_zero /
 // seg_zero2 (nullable) are seg bitfields to clear on the way
 divas_status build_counts(divas_ctx* c, const uint8_t* occ, const int32_t* coords,
-                          int64_t n_coords, cudaStream_t s) {
+                          int64_t n_coords, cudaStream_t s, float* score_zero = nullptr) {
     if (c->grid.kind == 0) {
-        k_tile_count<false><<<c->n_tiles, kThreads, 0, s>>>(
-            occ, c->occ_bits, c->n_cells, c->n_words, c->cap, c->item_pref, c->tile_count,
-            c->tile_offset, c->done, c->n_tiles, c->d_n, c->d_total, c->d_status);
+        if (c->brick && (reinterpret_cast<uintptr_t>(occ) & 7))
+            return fail(c, DIVAS_E_INVALID, "brick order needs an 8-byte aligned dense prior");
+        if (c->brick)
+            k_tile_count<2><<<c->n_tiles, kThreads, 0, s>>>(
+                occ, c->occ_bits, c->n_cells, c->n_words, c->cap, c->item_pref, c->tile_count,
+                c->tile_offset, c->done, c->n_tiles, c->d_n, c->d_total, c->d_status, c->grid.g,
+                c->bdiv, score_zero);
+        else
+            k_tile_count<0><<<c->n_tiles, kThreads, 0, s>>>(
+                occ, c->occ_bits, c->n_cells, c->n_words, c->cap, c->item_pref, c->tile_count,
+                c->tile_offset, c->done, c->n_tiles, c->d_n, c->d_total, c->d_status, c->grid.g,
+                c->bdiv, nullptr);
         DIVAS_LAUNCHED(c, "k_tile_count");
     } else {
         DIVAS_CUDA(c, cudaMemsetAsync(c->occ_bits, 0, c->n_words * 4, s));
@@ -1300,9 +1428,10 @@ divas_status build_counts(divas_ctx* c, const uint8_t* occ, const int32_t* coord
                     coords, n_coords, c->grid.g, c->occ_bits, c->d_status);
             DIVAS_LAUNCHED(c, "k_scatter_coords");
         }
-        k_tile_count<true><<<c->n_tiles, kThreads, 0, s>>>(
+        k_tile_count<1><<<c->n_tiles, kThreads, 0, s>>>(
             nullptr, c->occ_bits, c->n_cells, c->n_words, c->cap, c->item_pref, c->tile_count,
-            c->tile_offset, c->done, c->n_tiles, c->d_n, c->d_total, c->d_status);
+            c->tile_offset, c->done, c->n_tiles, c->d_n, c->d_total, c->d_status, c->grid.g,
+            c->bdiv, nullptr);
         DIVAS_LAUNCHED(c, "k_tile_count");
     }
     return DIVAS_OK;
@@ -1310,11 +1439,19 @@ divas_status build_counts(divas_ctx* c, const uint8_t* occ, const int32_t* coord
 
 // the full compaction: counts, then (when the active arrays exist) the list;
 // seg_zero / seg_zero2 (nullable) are seg bitfields to clear on the way
+// cull (nullable): a view batch whose pyramids are built while the counts
+// complete and whose bricks' kept views are tested while the entries are
+// emitted (the one-call step of a brick-ordered context)
 divas_status build_active(divas_ctx* c, const uint8_t* occ, const int32_t* coords, int64_t n_coords,
                           cudaStream_t s, uint32_t* seg_zero = nullptr,
-                          uint32_t* seg_zero2 = nullptr) {
-    divas_status st = build_counts(c, occ, coords, n_coords, s);
+                          uint32_t* seg_zero2 = nullptr, float* score_zero = nullptr,
+                          const ViewBatch* cull_vb = nullptr, const CullBatch* cull_cb = nullptr) {
+    divas_status st = build_counts(c, occ, coords, n_coords, s, score_zero);
     if (st != DIVAS_OK || !c->active) return st;
+    if (cull_vb) {
+        const cudaError_t e = launch_pyramid(c, *cull_vb, *cull_cb, s);
+        if (e != cudaSuccess) return cuda_fail(c, e, "k_mask_pyramid");
+    }
     cudaError_t e = launch_dependent(c->brick ? k_tile_emit<true> : k_tile_emit<false>,
                                      emit_blocks(c->n_words, c->sm_count), s,
                                      (const uint32_t*)c->occ_bits, c->n_words, c->cap,
@@ -1323,6 +1460,10 @@ divas_status build_active(divas_ctx* c, const uint8_t* occ, const int32_t* coord
                                      seg_zero2);
     if (e != cudaSuccess) return cuda_fail(c, e, "k_tile_emit");
     DIVAS_LAUNCHED(c, "k_tile_emit");
+    if (cull_vb) {
+        e = launch_brick_views(c, *cull_vb, s, false);
+        if (e != cudaSuccess) return cuda_fail(c, e, "k_brick_views");
+    }
     return DIVAS_OK;
 }
 
@@ -1347,6 +1488,8 @@ void free_all(divas_ctx* c) {
     if (c->sat) cudaFree(c->sat);
     if (c->wt) cudaFree(c->wt);
     if (c->pyr) cudaFree(c->pyr);
+    if (c->brick_keep) cudaFree(c->brick_keep);
+    if (c->cull_views) cudaFree(c->cull_views);
     void* ptrs[] = {c->occ_bits, c->item_pref, c->tile_count, c->tile_offset, c->done,
                     c->seg_bits, c->active,     c->W,          c->Z,           c->bits,
                     c->d_n,      c->d_status,   c->d_total,    c->d_nseg};
@@ -1386,8 +1529,8 @@ divas_status divas_fuse_init(divas_ctx** out, const divas_grid* grid, const uint
         return fail(nullptr, DIVAS_E_INVALID, "kind must be 0 (dense) or 1 (sparse)");
     }
     if (const char* why = params_problem(params)) return fail(nullptr, DIVAS_E_INVALID, why);
-    if ((params->flags & DIVAS_ORDER_BRICKS) && (grid->kind != 1 || grid->g % 8 != 0))
-        return fail(nullptr, DIVAS_E_INVALID, "brick order needs a sparse prior and g a multiple of 8");
+    if ((params->flags & DIVAS_ORDER_BRICKS) && grid->g % 8 != 0)
+        return fail(nullptr, DIVAS_E_INVALID, "brick order needs g a multiple of 8");
 
     divas_ctx* c = new (std::nothrow) divas_ctx();
     if (!c) return fail(nullptr, DIVAS_E_OOM, "host allocation failed");
@@ -1449,6 +1592,8 @@ divas_status divas_fuse_init(divas_ctx** out, const divas_grid* grid, const uint
     if (c->brick) {  // mask pyramids of up to 32 views of up to 2048 x 2048 pixels
         c->pyr_cap = (int64_t)kMaxViews * pyramid_floats(2048, 2048);
         INIT_CUDA(cudaMalloc(&c->pyr, c->pyr_cap * 4));
+        INIT_CUDA(cudaMalloc(&c->brick_keep, (c->n_words / 16) * 4));
+        INIT_CUDA(cudaMalloc(&c->cull_views, kMaxViews * sizeof(CullView)));
     }
     INIT_CUDA(cudaMemsetAsync(c->d_status, 0, 4, s));
     INIT_CUDA(cudaMemsetAsync(c->seg_bits, 0, c->n_words * 4, s));
@@ -1665,17 +1810,30 @@ divas_status divas_fuse_step_profiled(divas_ctx* c, const uint8_t* occ_dense,
     cudaStream_t s = S(stream);
     st = record_stage(c, stage_events, 0, s);
     if (st != DIVAS_OK) return st;
-    // occupancy gate + active list; the seg bitfields are cleared on the way
-    st = build_active(c, occ_dense, coords, n_coords, s, c->seg_bits, seg_bits_out);
+    // occupancy gate + active list; the seg bitfields are cleared on the way, and
+    // a brick-ordered dense context's count kernel zeroes the score grid (the
+    // fusion then writes the occupied cells' scores)
+    const bool dense = c->grid.kind == 0;
+    float* score_zero = dense && c->brick && score_out &&
+                                (reinterpret_cast<uintptr_t>(score_out) & 15) == 0
+                            ? score_out
+                            : nullptr;
+    if (dense && c->brick && score_out && !score_zero)
+        DIVAS_CUDA(c, cudaMemsetAsync(score_out, 0, c->n_cells * 4, s));
+    CullBatch cb;
+    const bool cull = culling(c, vb, cb);
+    st = build_active(c, occ_dense, coords, n_coords, s, c->seg_bits, seg_bits_out, score_zero,
+                      cull ? &vb : nullptr, cull ? &cb : nullptr);
     if (st != DIVAS_OK) return st;
     st = record_stage(c, stage_events, 1, s);
     if (st != DIVAS_OK) return st;
     c->n_views = 0;
     c->n_active = c->cap;  // upper bound until the next synchronising call
-    const bool zero = score_out && c->grid.kind == 0;
+    const bool zero = score_out && dense && !c->brick;
     // fusion of every view + finalize epilogue (both seg bitfields were
     // cleared) + the zeros of a dense score grid's unoccupied cells
-    cudaError_t e = launch_fuse_fin(c, false, vb, s, score_out, false, seg_bits_out, false, zero);
+    cudaError_t e = launch_fuse_fin(c, false, vb, s, score_out, false, seg_bits_out, false, zero,
+                                    dense && c->brick, cull);
     if (e != cudaSuccess) return cuda_fail(c, e, "k_fuse_fin");
     c->n_views = vb.n;
     st = record_stage(c, stage_events, 2, s);
@@ -1697,12 +1855,18 @@ divas_status divas_fuse_update(divas_ctx* c, const divas_view* views, int32_t n_
     if (st != DIVAS_OK) return st;
     cudaStream_t s = S(stream);
     const bool keep = (flags & DIVAS_KEEP_ZEROS) != 0;
-    const bool zero = !keep && score_out && c->grid.kind == 0;
+    bool zero = !keep && score_out && c->grid.kind == 0;
+    bool zeroed = false;
+    if (zero && c->brick) {  // the bitfield is brick-major: zero the whole grid first
+        DIVAS_CUDA(c, cudaMemsetAsync(score_out, 0, c->n_cells * 4, s));
+        zero = false;
+        zeroed = true;
+    }
     if (!keep && seg_bits_out) DIVAS_CUDA(c, cudaMemsetAsync(seg_bits_out, 0, c->n_words * 4, s));
     // the context's seg bitfield holds this occupied set's previous seg (or
     // zeros): set and clear in place; seg_bits_out likewise when kept
     cudaError_t e = launch_fuse_fin(c, c->n_views > 0, vb, s, score_out, true, seg_bits_out, keep,
-                                    zero);
+                                    zero, zeroed);
     if (e != cudaSuccess) return cuda_fail(c, e, "k_fuse_fin");
     c->n_views += vb.n;
     return DIVAS_OK;
@@ -2476,9 +2640,10 @@ extern "C" divas_status divas_fuse_dense_noalloc(const divas_grid* grid, const u
     if (e == cudaSuccess && seg_bits_out) e = cudaMemsetAsync(seg_bits_out, 0, n_words * 4, s);
     if (e != cudaSuccess)
         return noalloc_fail(DIVAS_E_CUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
-    k_tile_count<false><<<n_tiles, kThreads, 0, s>>>(occ_dense, occ_bits, n_cells, n_words, cap,
+    k_tile_count<0><<<n_tiles, kThreads, 0, s>>>(occ_dense, occ_bits, n_cells, n_words, cap,
                                                      item_pref, tile_count, tile_offset, done,
-                                                     n_tiles, d_n, d_total, d_status);
+                                                     n_tiles, d_n, d_total, d_status, grid->g,
+                                                     gdiv, nullptr);
     NA_CHECK("k_tile_count");
     k_tile_emit<false><<<emit_blocks(n_words, sm_count), kThreads, 0, s>>>(
         occ_bits, n_words, cap, gdiv, item_pref, tile_offset, active, nullptr, nullptr);

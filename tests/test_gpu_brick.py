@@ -120,13 +120,64 @@ def test_brick_order_incremental_views():
     fb.close()
 
 
-def test_brick_order_rejected_for_dense_priors():
-    wl = synth.config1()
+def test_brick_order_rejected_unless_g_multiple_of_8():
+    wl = synth.config1(g=60)
     d = H.upload(wl)
     prm = H.to_params(P0)
     prm.brick_order = True
     with pytest.raises(Exception):
         VoxelFusion(wl.grid, occ=d["occ"], params=prm)
+
+
+def _dense_state(fu, score, labels=None):
+    st = H.state_of(fu, score, labels)
+    return to_linear(dict(st, score=np.zeros(len(st["W"]), np.float32)), fu.g), st["score"]
+
+
+@pytest.mark.parametrize("build", [lambda: synth.config1(),
+                                   lambda: synth.config2(g=128, W=504, H=378)])
+def test_dense_brick_order_matches_linear_order_and_oracle(build):
+    """A dense prior in brick order (brick-major words built from the uint8
+    grid, the score grid zeroed by the count kernel, warp-level culling): the
+    one-call step, views folded one call at a time and an update with its
+    zero-fill give the linear-order results bitwise."""
+    wl = build()
+    d = H.upload(wl)
+    out = {}
+    for brick in (False, True):
+        prm = H.to_params(P0)
+        prm.brick_order = brick
+        fu = VoxelFusion(wl.grid, occ=d["occ"], params=prm)
+        score = torch.full((fu.n_cells,), 7.0, dtype=torch.float32, device="cuda")
+        labels = torch.empty(len(d["points"]), dtype=torch.uint8, device="cuda")
+        views = PreparedViews(wl.cams, d["depth"], d["mask"], wl.mask_type)
+        fu.step(views, occ=d["occ"], score=score, xyz=d["points"], labels=labels)
+        torch.cuda.synchronize()
+        lin_st, sc = _dense_state(fu, score, labels)
+        # the same views again through the incremental update (zero-fill path)
+        fu2 = VoxelFusion(wl.grid, occ=d["occ"], params=prm)
+        h = max(1, wl.n_views // 2)
+        fu2.add_views(wl.cams[:h], d["depth"][:h], d["mask"][:h], mask_type=wl.mask_type)
+        score2 = torch.full((fu2.n_cells,), 7.0, dtype=torch.float32, device="cuda")
+        fu2.update(PreparedViews(wl.cams[h:], d["depth"][h:], d["mask"][h:], wl.mask_type),
+                   score=score2)
+        torch.cuda.synchronize()
+        upd, sc2 = _dense_state(fu2, score2)
+        out[brick] = (lin_st, sc, upd, sc2, fu)
+        fu2.close()
+    a, b = out[False], out[True]
+    for k in ("active", "W", "Z", "bits", "vmask"):
+        assert np.array_equal(b[0][k], a[0][k]), k
+        assert np.array_equal(b[2][k], a[2][k]), ("update", k)
+    assert np.array_equal(b[1], a[1]) and np.array_equal(b[3], a[3]), "dense scores"
+    assert np.array_equal(b[0]["seg_dense"], a[0]["seg_dense"])
+    assert np.array_equal(b[0]["labels"], a[0]["labels"])
+    assert (a[0]["Z"] > 0).any()
+    lin_b = dict(b[0], score=b[1])
+    H.compare(wl, lin_b, P0, sample=H.sample_of(len(lin_b["W"]), 20_000),
+              name=f"{H.current_test()} {wl.name} g={wl.grid.g} dense brick", max_flagged=0.03)
+    for v in out.values():
+        v[4].close()
 
 
 @pytest.mark.parametrize("mask_type", [oracle.MASK_F32, oracle.MASK_LOGIT_F32])
