@@ -86,7 +86,8 @@ struct CullView {
 // for this one has also waited for the one before.
 __global__ void __launch_bounds__(256) k_mask_pyramid(const __grid_constant__ ViewBatch VB,
                                                       const __grid_constant__ CullBatch CB,
-                                                      CullView* __restrict__ views_out) {
+                                                      CullView* __restrict__ views_out,
+                                                      ViewC* __restrict__ fold_out) {
     __shared__ float l3[8][8];
     allow_dependents();
     const int v = blockIdx.z;
@@ -101,6 +102,7 @@ __global__ void __launch_bounds__(256) k_mask_pyramid(const __grid_constant__ Vi
         for (int k = 0; k < 3; ++k) cv.r[9 + k] = V.C[k];
         cv.c = C;
         views_out[v] = cv;
+        fold_out[v] = V;
     }
     const int x = blockIdx.x * kPyrTile + (t & 63);
     const int yb = blockIdx.y * kPyrTile + 16 * (t >> 6);
@@ -328,13 +330,29 @@ __global__ void __launch_bounds__(256) k_brick_views(const CullView* __restrict_
     if (!wait_first) wait_for_producer();
 }
 
+// A view's constants from a shared-memory copy of the batch (16-byte aligned):
+// seven 16-byte loads with a warp-uniform address.
+__device__ __forceinline__ ViewC view_from_shared(const ViewC* sv, int32_t v) {
+    const uint4* p = reinterpret_cast<const uint4*>(sv + v);
+    union {
+        uint4 w[sizeof(ViewC) / 16];
+        ViewC V;
+    } u;
+#pragma unroll
+    for (int k = 0; k < (int)(sizeof(ViewC) / 16); ++k) u.w[k] = p[k];
+    return u.V;
+}
+
 // Fold the views of `keep` (ascending view order, four at a time: the same
 // per-view arithmetic and order as fold_views over all views, which it matches
-// bitwise when the skipped views vote nowhere).  The view index is warp-uniform.
+// bitwise when the skipped views vote nowhere).  The view index is
+// warp-uniform; the views' constants come from the CTA's shared-memory copy
+// of the batch.
 template <bool kContracted, int kMT>
-__device__ __forceinline__ void fold_views_kept(const ViewBatch& VB, uint32_t keep,
+__device__ __forceinline__ void fold_views_kept(const ViewC* sv, uint32_t keep,
                                                 const VoxelGeom& vg, const FuseC& F, float& W,
                                                 float& Z, uint32_t& bits) {
+    static_assert(sizeof(ViewC) % 16 == 0, "views copy as 16-byte words");
     uint32_t rem = keep;
     while (rem) {
         int32_t vi[kViewChunk];
@@ -349,17 +367,23 @@ __device__ __forceinline__ void fold_views_kept(const ViewBatch& VB, uint32_t ke
         for (int q = 0; q < kViewChunk; ++q) {
             pix[q] = -1;
             pzh[q] = pzl[q] = 0.f;
-            if (vi[q] >= 0) pix[q] = project<kContracted>(VB.v[vi[q]], vg, F.z_near, pzh[q], pzl[q]);
+            if (vi[q] >= 0) {
+                const ViewC V = view_from_shared(sv, vi[q]);
+                pix[q] = project<kContracted>(V, vg, F.z_near, pzh[q], pzl[q]);
+            }
         }
 #pragma unroll
         for (int q = 0; q < kViewChunk; ++q)
-            if (vi[q] >= 0) load_raster<kMT>(VB.v[vi[q]], pix[q], D[q], raw[q]);
+            if (vi[q] >= 0) {
+                const ViewC V = view_from_shared(sv, vi[q]);
+                load_raster<kMT>(V, pix[q], D[q], raw[q]);
+            }
         float e[kViewChunk];
         uint32_t acc = 0u;
 #pragma unroll
         for (int q = 0; q < kViewChunk; ++q) {
             if (vi[q] < 0) break;
-            const ViewC& V = VB.v[vi[q]];
+            const ViewC V = view_from_shared(sv, vi[q]);
             const bool pass =
                 kContracted ? pre_gates<true, kMT>(V, vg, F, pix[q], pzh[q], D[q], raw[q])
                             : gates<false, kMT>(V, vg, F, pix[q], pzh[q], pzl[q], D[q], raw[q], e[q]);
@@ -369,7 +393,7 @@ __device__ __forceinline__ void fold_views_kept(const ViewBatch& VB, uint32_t ke
 #pragma unroll
             for (int q = 0; q < kViewChunk; ++q) {
                 if (acc & (1u << q)) {
-                    const ViewC& V = VB.v[vi[q]];
+                    const ViewC V = view_from_shared(sv, vi[q]);
                     if constexpr (kContracted) {
                         e[q] = depth_error<true>(V, vg, pzh[q], pzl[q], D[q]);
                         if (!(fabsf(e[q]) <= vg.Delta)) continue;

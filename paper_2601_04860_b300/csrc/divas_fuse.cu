@@ -656,11 +656,19 @@ __global__ void __launch_bounds__(kThreads, kContracted ? 5 : 6) k_fuse_fin(
 template <bool kAccumulate, bool kContracted, int kMT>
 __global__ void __launch_bounds__(kThreads, kContracted ? 5 : 6) k_fuse_fin_cull(
     const uint32_t* __restrict__ active, const int32_t* __restrict__ d_n, GridC G, FuseC F,
-    const __grid_constant__ ViewBatch VB, const uint32_t* __restrict__ brick_keep,
+    const ViewC* __restrict__ views, int32_t n_views, const uint32_t* __restrict__ brick_keep,
     float* __restrict__ W, float* __restrict__ Z, uint32_t* __restrict__ bits, int32_t dense,
     float* __restrict__ score_out, int32_t score_zeroed, uint32_t* __restrict__ seg_bits,
     int32_t clear_bits, uint32_t* __restrict__ seg_out, int32_t clear_out) {
-    wait_for_producer();  // the active list, its length and the bricks' kept views
+    __shared__ __align__(16) ViewC sv[kMaxViews];
+    wait_for_producer();  // the active list, its length, the views and the bricks' kept views
+    {  // the batch's view constants into shared memory (16-byte words)
+        const uint4* src = reinterpret_cast<const uint4*>(views);
+        uint4* dst = reinterpret_cast<uint4*>(sv);
+        for (int k = threadIdx.x; k < n_views * (int)(sizeof(ViewC) / 16); k += blockDim.x)
+            dst[k] = __ldg(src + k);
+        __syncthreads();
+    }
     const int lane = threadIdx.x & 31;
     const int32_t gw = (int32_t)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int32_t nw = (int32_t)((gridDim.x * blockDim.x) >> 5);
@@ -698,7 +706,7 @@ __global__ void __launch_bounds__(kThreads, kContracted ? 5 : 6) k_fuse_fin_cull
                 z = Z[a];
                 b = bits[a];
             }
-            if (vg.ok) fold_views_kept<kContracted, kMT>(VB, keep, vg, F, w, z, b);
+            if (vg.ok) fold_views_kept<kContracted, kMT>(sv, keep, vg, F, w, z, b);
             W[a] = w;
             Z[a] = z;
             bits[a] = b;
@@ -993,6 +1001,7 @@ struct divas_ctx {
     int64_t pyr_cap = 0;   // its capacity in floats
     uint32_t* brick_keep = nullptr;  // brick order: per brick, the views it may vote in
     CullView* cull_views = nullptr;  // brick order: the batch's views for the brick test
+    ViewC* fold_views = nullptr;     // brick order: the batch's views for the culled fusion
     void* sat = nullptr;   // tuple mode: integral-image scratch, grown on demand
     size_t sat_bytes = 0;
     void* wt = nullptr;    // depth weighting: selection state and histograms, grown on demand
@@ -1293,8 +1302,8 @@ cudaError_t launch_fuse_fin_cull(const divas_ctx* c, const ViewBatch& vb, int bl
     for (int32_t i = 0; i < vb.n && f16; ++i) f16 = vb.v[i].mask_type == kMaskF16;
 #define DIVAS_FUSE_CULL(MT)                                                                       \
     launch_dependent(k_fuse_fin_cull<kAccumulate, kContracted, MT>, blocks, s,                    \
-                     (const uint32_t*)c->active, (const int32_t*)c->d_n, c->G, c->F, vb,          \
-                     (const uint32_t*)c->brick_keep,                                               \
+                     (const uint32_t*)c->active, (const int32_t*)c->d_n, c->G, c->F,              \
+                     (const ViewC*)c->fold_views, vb.n, (const uint32_t*)c->brick_keep,            \
                      c->W, c->Z, c->bits, (int32_t)(c->grid.kind == 0 ? 1 : 0), score_out,        \
                      (int32_t)(score_zeroed ? 1 : 0), c->seg_bits, (int32_t)(clear_bits ? 1 : 0), \
                      seg_out, (int32_t)(clear_out ? 1 : 0))
@@ -1323,7 +1332,7 @@ cudaError_t launch_pyramid(const divas_ctx* c, const ViewBatch& vb, const CullBa
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_mask_pyramid, vb, cb, c->cull_views);
+    return cudaLaunchKernelEx(&cfg, k_mask_pyramid, vb, cb, c->cull_views, c->fold_views);
 }
 
 // the bricks' kept views: several bricks per warp, one wave of CTAs
@@ -1357,7 +1366,8 @@ cudaError_t launch_culled_fuse(const divas_ctx* c, bool accumulate, const ViewBa
 
 // whether a batch on this context is fused with culling (then cb holds its constants)
 bool culling(const divas_ctx* c, const ViewBatch& vb, CullBatch& cb) {
-    return c->brick && c->pyr && c->brick_keep && c->cull_views && vb.n > 0 && make_cull(c, vb, cb);
+    return c->brick && c->pyr && c->brick_keep && c->cull_views && c->fold_views && vb.n > 0 &&
+           make_cull(c, vb, cb);
 }
 
 // score_zeroed: score_out holds +0 at every active voxel (brick contexts skip
@@ -1490,6 +1500,7 @@ void free_all(divas_ctx* c) {
     if (c->pyr) cudaFree(c->pyr);
     if (c->brick_keep) cudaFree(c->brick_keep);
     if (c->cull_views) cudaFree(c->cull_views);
+    if (c->fold_views) cudaFree(c->fold_views);
     void* ptrs[] = {c->occ_bits, c->item_pref, c->tile_count, c->tile_offset, c->done,
                     c->seg_bits, c->active,     c->W,          c->Z,           c->bits,
                     c->d_n,      c->d_status,   c->d_total,    c->d_nseg};
@@ -1594,6 +1605,7 @@ divas_status divas_fuse_init(divas_ctx** out, const divas_grid* grid, const uint
         INIT_CUDA(cudaMalloc(&c->pyr, c->pyr_cap * 4));
         INIT_CUDA(cudaMalloc(&c->brick_keep, (c->n_words / 16) * 4));
         INIT_CUDA(cudaMalloc(&c->cull_views, kMaxViews * sizeof(CullView)));
+        INIT_CUDA(cudaMalloc(&c->fold_views, kMaxViews * sizeof(ViewC)));
     }
     INIT_CUDA(cudaMemsetAsync(c->d_status, 0, 4, s));
     INIT_CUDA(cudaMemsetAsync(c->seg_bits, 0, c->n_words * 4, s));
