@@ -107,8 +107,9 @@ def job_throughput(units_per_rank: float, world: int, ms_max: float) -> float:
 
 # warp instructions per voxel-view of the contracted fusion kernel on the
 # unbounded-sparse workload (ncu smsp__inst_executed.sum of one launch divided
-# by its active voxels x views)
-SPARSE_FUSE_INSTS_PER_VOXEL_VIEW = 3.91
+# by its 12M active voxels x 16 views), per active-list order: brick order runs
+# k_fuse_fin_cull (375,118,414 per launch), linear order k_fuse_fin (4.669e8)
+SPARSE_FUSE_INSTS_PER_VOXEL_VIEW = {"brick": 375_118_414 / 192e6, "linear": 466_900_000 / 192e6}
 
 
 ACTIVE_ORDER = "auto"  # --active-order
@@ -788,15 +789,21 @@ def measure_sparse(dev, steps: int, cpu_seconds: float = 8.0):
     props = torch.cuda.get_device_properties(dev)
     sm_mhz = clk.get("sm_mhz") or 2032.0
     issue_peak = props.multi_processor_count * 4 * sm_mhz * 1e6  # warp instructions / s
-    insts = SPARSE_FUSE_INSTS_PER_VOXEL_VIEW * na * S
+    order = "brick" if fu.params.brick_order else "linear"
+    ipv = SPARSE_FUSE_INSTS_PER_VOXEL_VIEW[order]
+    insts = None if ipv is None else ipv * na * S
     out = {"workload": "unbounded-sparse-512 (contracted 512^3 grid, ~12M occupied voxels as "
                        "int32 coordinates, 16 views 1297x840 FP32 depth + FP16 masks, 3M points)",
            "ms_per_step": m, "updates_per_s": na * S / (m * 1e-3), "active_voxels": int(na),
            "views": S, "stage_ms": stm,
-           "roofline": {"bound": "alu", "kernel": "k_fuse_fin (contracted)",
-                        "achieved": insts / (stm["fuse_finalize"] * 1e-3) / 1e12,
+           "roofline": {"bound": "alu",
+                        "kernel": "k_fuse_fin_cull (contracted)" if order == "brick"
+                                  else "k_fuse_fin (contracted)",
+                        "achieved": None if insts is None
+                                    else insts / (stm["fuse_finalize"] * 1e-3) / 1e12,
                         "peak": issue_peak / 1e12, "unit": "warp Tinst/s",
-                        "frac": insts / (stm["fuse_finalize"] * 1e-3) / issue_peak,
+                        "frac": None if insts is None
+                                else insts / (stm["fuse_finalize"] * 1e-3) / issue_peak,
                         "insts_per_launch": insts,
                         "insts_source": "ncu smsp__inst_executed.sum per voxel-view of this "
                                         "kernel (profiles/unbounded-sparse-512_launch_list.md)",
