@@ -64,10 +64,10 @@ def _env_int(k, d):
 STEP_SOURCES = ("paper_2601_04860_b300/csrc/divas_fuse.cu",
                 "paper_2601_04860_b300/csrc/fuse_math.cuh")
 TRAFFIC_CAPTURE = {
-    "source_sha1": "52d546d6924b58d9b870dfe7a127feb91d732abf",
-    "forward-dense-256": {"k_fuse_fin": 28_153_344 + 23_067_392,
-                          "k_tile_count": 16_799_488, "k_tile_emit": 2_368_768,
-                          "k_label": 13_339_648},
+    "source_sha1": "8737df8a9b38b915eb3717834b7e704f730205cf",
+    "forward-dense-256": {"k_fuse_fin": 28_176_896 + 22_810_624,
+                          "k_tile_count": 16_800_000, "k_tile_emit": 2_368_768,
+                          "k_label": 13_338_880},
 }
 
 
