@@ -1656,14 +1656,18 @@ def measure_sessions(dev, scale: float, n_sessions: int, rates, budget_frac: flo
                                              poisson_requests, serve_plain, session_data_from)
     t_gen = time.perf_counter()
     recipes = synth.session_mix(n_sessions=n_sessions, scale=scale)
-    data = [session_data_from(synth.session_workload(r), i) for i, r in enumerate(recipes)]
+    data = []
+    for i, r in enumerate(recipes):
+        wl = synth.session_workload(r)
+        data.append(session_data_from(wl, i, fusion_params(wl)))
     t_gen = time.perf_counter() - t_gen
     nominal = sum((int(d.grid.g) ** 3 if d.occ is not None else len(d.coords)) * d.n_views
                   for d in data)
     out = {"sessions": n_sessions, "scale": scale, "generation_s": t_gen,
            "dense": sum(d.occ is not None for d in data),
            "views_total": sum(d.n_views for d in data),
-           "voxel_views_nominal": int(nominal)}
+           "voxel_views_nominal": int(nominal),
+           "brick_ordered": sum(bool(d.params.brick_order) for d in data)}
     # (a) batched vs plain, all views of every session
     sess = [Session(d, dev) for d in data]
     flush = L2Flush(dev)

@@ -1364,10 +1364,15 @@ cudaError_t launch_culled_fuse(const divas_ctx* c, bool accumulate, const ViewBa
                    c, vb, blocks, s, score_out, score_zeroed, clear_bits, seg_out, clear_out);
 }
 
+// fewest views in a batch for which culling pays: below it the pyramid and brick
+// test launches cost more than the views they skip (measured on the served
+// session mix, where updates carry one view)
+constexpr int32_t kCullMinViews = 4;
+
 // whether a batch on this context is fused with culling (then cb holds its constants)
 bool culling(const divas_ctx* c, const ViewBatch& vb, CullBatch& cb) {
-    return c->brick && c->pyr && c->brick_keep && c->cull_views && c->fold_views && vb.n > 0 &&
-           make_cull(c, vb, cb);
+    return c->brick && c->pyr && c->brick_keep && c->cull_views && c->fold_views &&
+           vb.n >= kCullMinViews && make_cull(c, vb, cb);
 }
 
 // score_zeroed: score_out holds +0 at every active voxel (brick contexts skip
@@ -2040,6 +2045,9 @@ struct SessionDesc {
     GridC G;
     FuseC F;
     int32_t view_off, n_views, accumulate, dense;
+    // brick-ordered session fused with culling: per brick, the views it may vote
+    // in (null: every view)
+    const uint32_t* brick_keep;
     // finalize / labels (filled at finalize time)
     float* score_out;
     uint32_t* seg_bits;
@@ -2110,11 +2118,48 @@ __device__ __forceinline__ void batch_fuse_item(const SessionDesc& D, const View
     }
 }
 
-template <int kVPT>
+// a culled session's item: per group of 32 voxels the views some brick of
+// theirs may vote in (the session's brick masks), folded in view order with
+// the arithmetic of fold_views_multi (bitwise the full fold)
+template <bool kContracted>
+__device__ __forceinline__ void batch_fuse_item_cull(const SessionDesc& D, const ViewC* sv,
+                                                     int32_t a0, int32_t a1) {
+    const uint32_t nb = (uint32_t)D.G.g >> 3;
+    for (int32_t base = a0; base < a1; base += (int32_t)blockDim.x) {
+        const int32_t a = base + (int32_t)threadIdx.x;
+        const bool live = a < a1;
+        const uint32_t pk = __ldg(D.active + (live ? a : a0));
+        // (no brick masks: every view)
+        const uint32_t mine =
+            !live ? 0u
+            : D.brick_keep
+                ? __ldg(D.brick_keep +
+                        (((pk >> 23) * nb + ((pk >> 13) & 127u)) * nb + ((pk & 1023u) >> 3)))
+                : (D.n_views >= 32 ? 0xffffffffu : (1u << D.n_views) - 1u);
+        const uint32_t keep = __reduce_or_sync(0xffffffffu, mine);
+        const VoxelGeom vg = voxel_geom<kContracted>(pk, D.G, D.F.gamma);
+        if (!live) continue;
+        float W = 0.f, Z = 0.f;
+        uint32_t bits = 0u;
+        if (D.accumulate) {
+            W = D.W_in[a];
+            Z = D.Z_in[a];
+            bits = D.bits_in[a];
+        }
+        if (vg.ok) fold_views_kept<kContracted, -1>(sv, keep, vg, D.F, W, Z, bits);
+        D.W_out[a] = W;
+        D.Z_out[a] = Z;
+        D.bits_out[a] = bits;
+    }
+}
+
+// kCull: the work items are the culled sessions' (one voxel per thread), else
+// the other sessions' (kVPT voxels per thread)
+template <int kVPT, bool kCull = false>
 __global__ void __launch_bounds__(kThreads) k_batch_fuse(const SessionDesc* __restrict__ S, int32_t n_sessions,
                              const uint32_t* __restrict__ prefix, const ViewC* __restrict__ views,
                              int32_t tile, int32_t* __restrict__ counter) {
-    __shared__ ViewC sv[kMaxViews];
+    __shared__ __align__(16) ViewC sv[kMaxViews];  // read as 16-byte words by the culled fold
     uint32_t it;
     int32_t s;
     while (next_item(counter, prefix, n_sessions, it, s)) {
@@ -2131,10 +2176,17 @@ __global__ void __launch_bounds__(kThreads) k_batch_fuse(const SessionDesc* __re
         const int32_t a0 = (int32_t)(it - __ldg(prefix + s)) * tile;
         const int32_t a1 = min(a0 + tile, n);
         if (a0 < a1) {
-            if (D.G.contracted)
-                batch_fuse_item<true, kVPT>(D, sv, a0, a1);
-            else
-                batch_fuse_item<false, kVPT>(D, sv, a0, a1);
+            if constexpr (kCull) {
+                if (D.G.contracted)
+                    batch_fuse_item_cull<true>(D, sv, a0, a1);
+                else
+                    batch_fuse_item_cull<false>(D, sv, a0, a1);
+            } else {
+                if (D.G.contracted)
+                    batch_fuse_item<true, kVPT>(D, sv, a0, a1);
+                else
+                    batch_fuse_item<false, kVPT>(D, sv, a0, a1);
+            }
         }
     }
 }
@@ -2247,7 +2299,7 @@ divas_status divas_batch_create(divas_batch** out, int32_t max_sessions, int32_t
     auto align = [](size_t x) { return (x + 255) / 256 * 256; };
     b->off_views = align(sizeof(SessionDesc) * max_sessions);
     b->off_prefix = b->off_views + align(sizeof(ViewC) * max_views);
-    b->stage_bytes = b->off_prefix + align(sizeof(uint32_t) * 3 * (max_sessions + 1));
+    b->stage_bytes = b->off_prefix + align(sizeof(uint32_t) * 4 * (max_sessions + 1));
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->sm_count, cudaDevAttrMultiProcessorCount, dev);
@@ -2323,13 +2375,41 @@ divas_status divas_batch_fuse(divas_batch* b, const divas_schedule* sched, int32
         return bfail(b, DIVAS_E_INVALID, "bad schedule");
     cudaStream_t s = S(stream);
     SessionDesc* hs = stage_sessions(b);
-    // tile prefix over capacities (the device count bounds the real work)
+    // brick-ordered sessions: their views' mask pyramids and bricks' kept views,
+    // read by the culled fusion below
+    const ViewC* hv = stage_views(b);
+    // (an earlier copy of this staging buffer may still be pending on the stream
+    // when the batch is fused again, e.g. repeated dry runs: each field is
+    // written once, with its final value)
+    for (int32_t k = 0; k < ns; ++k) {
+        const divas_ctx* c = b->ctxs[k];
+        const uint32_t* keep = nullptr;
+        if (c->brick && hs[k].n_views >= 1 && hs[k].n_views <= kMaxViews) {
+            ViewBatch vb;
+            memset(&vb, 0, sizeof(vb));
+            vb.n = hs[k].n_views;
+            for (int32_t v = 0; v < vb.n; ++v) vb.v[v] = hv[hs[k].view_off + v];
+            CullBatch cb;
+            if (culling(c, vb, cb)) {
+                cudaError_t ce = launch_pyramid(c, vb, cb, s);
+                if (ce == cudaSuccess) ce = launch_brick_views(c, vb, s, true);
+                if (ce != cudaSuccess) return bfail(b, DIVAS_E_CUDA, cudaGetErrorString(ce));
+                keep = c->brick_keep;
+            }
+        }
+        hs[k].brick_keep = keep;
+    }
+    // tile prefixes over capacities (the device count bounds the real work): the
+    // culled sessions' items in prefix 3, the others' in prefix 0
     uint32_t* pf = stage_prefix(b, 0);
-    pf[0] = 0;
+    uint32_t* pc = stage_prefix(b, 3);
+    pf[0] = pc[0] = 0;
     int64_t total_cap = 0;
     for (int32_t k = 0; k < ns; ++k) {
         const int64_t cap = b->ctxs[k]->cap;
-        pf[k + 1] = pf[k] + (uint32_t)((cap + sched->tile - 1) / sched->tile);
+        const uint32_t tiles = (uint32_t)((cap + sched->tile - 1) / sched->tile);
+        pf[k + 1] = pf[k] + (hs[k].brick_keep ? 0u : tiles);
+        pc[k + 1] = pc[k] + (hs[k].brick_keep ? tiles : 0u);
         total_cap += cap;
     }
     if (dry_run) {  // outputs go to scratch: the contexts are left untouched
@@ -2365,16 +2445,24 @@ divas_status divas_batch_fuse(divas_batch* b, const divas_schedule* sched, int32
     cudaError_t e = cudaMemcpyAsync(b->d_stage, b->h_stage[b->cur], b->stage_bytes,
                                     cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess && !capturing(s)) e = cudaEventRecord(b->stage_done[b->cur], s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_counter, 0, 4, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_counter, 0, 16, s);
     if (e != cudaSuccess) return bfail(b, DIVAS_E_CUDA, cudaGetErrorString(e));
     const SessionDesc* dS = reinterpret_cast<const SessionDesc*>(b->d_stage);
     const ViewC* dV = reinterpret_cast<const ViewC*>(b->d_stage + b->off_views);
     const uint32_t* dP = reinterpret_cast<const uint32_t*>(b->d_stage + b->off_prefix);
-    const int grid = std::max(1, std::min<int>(b->sm_count * sched->ctas_per_sm, (int)pf[ns]));
-    switch (vpt) {
-        case 1: k_batch_fuse<1><<<grid, sched->threads, 0, s>>>(dS, ns, dP, dV, sched->tile, b->d_counter); break;
-        case 2: k_batch_fuse<2><<<grid, sched->threads, 0, s>>>(dS, ns, dP, dV, sched->tile, b->d_counter); break;
-        default: k_batch_fuse<4><<<grid, sched->threads, 0, s>>>(dS, ns, dP, dV, sched->tile, b->d_counter); break;
+    const uint32_t* dPc = dP + (size_t)3 * (b->max_sessions + 1);
+    if (pf[ns] > 0) {
+        const int grid = std::max(1, std::min<int>(b->sm_count * sched->ctas_per_sm, (int)pf[ns]));
+        switch (vpt) {
+            case 1: k_batch_fuse<1><<<grid, sched->threads, 0, s>>>(dS, ns, dP, dV, sched->tile, b->d_counter); break;
+            case 2: k_batch_fuse<2><<<grid, sched->threads, 0, s>>>(dS, ns, dP, dV, sched->tile, b->d_counter); break;
+            default: k_batch_fuse<4><<<grid, sched->threads, 0, s>>>(dS, ns, dP, dV, sched->tile, b->d_counter); break;
+        }
+    }
+    if (pc[ns] > 0) {
+        const int grid = std::max(1, std::min<int>(b->sm_count * sched->ctas_per_sm, (int)pc[ns]));
+        k_batch_fuse<1, true><<<grid, sched->threads, 0, s>>>(dS, ns, dPc, dV, sched->tile,
+                                                             b->d_counter + 3);
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return bfail(b, DIVAS_E_CUDA, std::string("k_batch_fuse: ") + cudaGetErrorString(e));

@@ -203,3 +203,40 @@ def test_culling_with_f32_and_logit_masks(mask_type):
     assert (lin_state["Z"] > 0).any()
     fl.close()
     fb.close()
+
+
+def test_batched_brick_sessions_match_linear_sessions_alone():
+    """Brick-ordered sessions in one batched launch (their views culled per
+    brick) give each session's linear-order result alone, bitwise."""
+    from paper_2601_04860_b300 import Batch, Schedule
+    mix = synth.session_mix(n_sessions=64, scale=0.25)
+    wls = [synth.session_workload(mix[i]) for i in (1, 3, 9, 21)]
+    ups = [H.upload(wl) for wl in wls]
+    ref = []
+    for wl, d in zip(wls, ups):
+        fu = VoxelFusion(wl.grid, occ=d["occ"], coords=d["coords"], params=H.to_params(P0))
+        fu.add_views(wl.cams, d["depth"], d["mask"], mask_type=wl.mask_type)
+        st = H.state_of(fu, torch.zeros(fu.n_cells if fu.dense else fu.n_active,
+                                        device="cuda"))
+        ref.append(st)
+        fu.close()
+    for sched in (Schedule(256, 1, 8, 4096), Schedule(128, 2, 4, 1024)):
+        fus = []
+        for wl, d in zip(wls, ups):
+            prm = H.to_params(P0)
+            prm.brick_order = wl.grid.g % 8 == 0
+            fus.append(VoxelFusion(wl.grid, occ=d["occ"], coords=d["coords"], params=prm))
+        b = Batch(max_sessions=8, max_views=256)
+        for (wl, d), fu in zip(zip(wls, ups), fus):
+            b.queue(fu, wl.cams, d["depth"], d["mask"], mask_type=wl.mask_type)
+        b.fuse(sched)
+        torch.cuda.synchronize()
+        for wl, fu, r in zip(wls, fus, ref):
+            st = to_linear(dict(H.state_of(fu, torch.zeros(fu.n_cells if fu.dense else fu.n_active,
+                                                           device="cuda")),
+                                score=np.zeros(fu.n_active, np.float32)), wl.grid.g)
+            rl = to_linear(dict(r, score=np.zeros(len(r["W"]), np.float32)), wl.grid.g)
+            for k in ("active", "W", "Z", "bits"):
+                assert np.array_equal(st[k], rl[k]), (wl.name, k)
+            fu.close()
+        b.close()
