@@ -53,20 +53,19 @@ struct BackPtrs {
 // ---------------------------------------------------------------------------
 // compaction
 // ---------------------------------------------------------------------------
-// bit of cell (i, j, k) in the brick-major layout: 8^3 bricks in linear brick
-// order (x fastest), cells inside a brick in linear order (x fastest), so a
-// 32-bit word is an 8 x 4 patch of one brick slice (g a multiple of 8)
-__device__ __forceinline__ int64_t brick_bit(int32_t i, int32_t j, int32_t k, int32_t g) {
-    const int64_t nb = g >> 3;
-    const int64_t b = ((int64_t)(k >> 3) * nb + (j >> 3)) * nb + (i >> 3);
-    return b * 512 + (((k & 7) * 8 + (j & 7)) * 8 + (i & 7));
-}
+// The brick-major layout: 8^3 bricks in linear brick order (x fastest), cells
+// inside a brick in linear order (x fastest), so a 32-bit word is an 8 x 4
+// patch of one brick slice (g a multiple of 8).
 
 // sparse coordinates -> bitfield (atomic OR; duplicates merge), in linear or
-// brick-major layout.  Lanes take consecutive coordinates and those that fall
-// in the same 32-bit word OR their bits together first, so a sorted (or
-// spatially coherent) set costs one atomic per word and warp instead of one per
-// coordinate.
+// brick-major layout.  Runs of consecutive lanes whose coordinates fall in the
+// same 32-bit word OR their bits together first (heads where a lane's word
+// differs from the previous lane's), so a sorted (or spatially coherent) set
+// costs one atomic per word and warp instead of one per coordinate.  Each
+// thread has the coordinates of kScatterUnroll grid-stride rounds loaded
+// before it handles the first.
+constexpr int kScatterUnroll = 4;
+
 template <bool kBrick>
 __global__ void __launch_bounds__(kThreads) k_scatter_coords(const int32_t* __restrict__ coords,
                                                              int64_t n, int32_t g,
@@ -74,24 +73,50 @@ __global__ void __launch_bounds__(kThreads) k_scatter_coords(const int32_t* __re
                                                              int32_t* __restrict__ status) {
     const int lane = threadIdx.x & 31;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const uint32_t ug = (uint32_t)g, nb = ug >> 3;
     for (int64_t base = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) & ~(int64_t)31; base < n;
-         base += stride) {
-        const int64_t a = base + lane;
-        uint32_t word = 0xffffffffu, bit = 0u;
-        if (a < n) {
-            const int32_t i = __ldg(coords + 3 * a), j = __ldg(coords + 3 * a + 1),
-                          k = __ldg(coords + 3 * a + 2);
-            if (i < 0 || j < 0 || k < 0 || i >= g || j >= g || k >= g) {
-                atomicOr(status, kStatusBadCoord);
-            } else {
-                const int64_t lin = kBrick ? brick_bit(i, j, k, g) : ((int64_t)k * g + j) * g + i;
-                word = (uint32_t)(lin >> 5);
-                bit = 1u << (lin & 31);
+         base += kScatterUnroll * stride) {
+        int32_t c[kScatterUnroll][3];
+#pragma unroll
+        for (int u = 0; u < kScatterUnroll; ++u) {
+            const int64_t a = base + u * stride + lane;
+            c[u][0] = c[u][1] = c[u][2] = -1;
+            if (a < n) {
+                c[u][0] = __ldcs(coords + 3 * a);
+                c[u][1] = __ldcs(coords + 3 * a + 1);
+                c[u][2] = __ldcs(coords + 3 * a + 2);
             }
         }
-        const uint32_t grp = __match_any_sync(0xffffffffu, word);
-        const uint32_t orv = __reduce_or_sync(grp, bit);
-        if (word != 0xffffffffu && lane == __ffs(grp) - 1) atomicOr(bits + word, orv);
+#pragma unroll
+        for (int u = 0; u < kScatterUnroll; ++u) {
+            if (base + u * stride >= n) break;  // warp-uniform
+            const bool live = base + u * stride + lane < n;
+            const uint32_t i = (uint32_t)c[u][0], j = (uint32_t)c[u][1], k = (uint32_t)c[u][2];
+            uint32_t word = 0xffffffffu, bit = 0u;
+            if (live) {
+                if (i >= ug || j >= ug || k >= ug) {  // negative values wrap above g
+                    atomicOr(status, kStatusBadCoord);
+                } else {
+                    // at most 2^30 cells: 32-bit positions
+                    const uint32_t lin =
+                        kBrick ? (((k >> 3) * nb + (j >> 3)) * nb + (i >> 3)) * 512u +
+                                     (((k & 7u) * 8u + (j & 7u)) * 8u + (i & 7u))
+                               : (k * ug + j) * ug + i;
+                    word = lin >> 5;
+                    bit = 1u << (lin & 31u);
+                }
+            }
+            // this lane's run of equal words among consecutive lanes
+            const uint32_t prev = __shfl_up_sync(0xffffffffu, word, 1);
+            const uint32_t heads = __ballot_sync(0xffffffffu, lane == 0 || prev != word);
+            const uint32_t upto = heads & (0xffffffffu >> (31 - lane));
+            const int first = 31 - __clz(upto);
+            const uint32_t after = heads & ~(0xffffffffu >> (31 - lane));
+            const int end = after ? __ffs(after) - 1 : 32;
+            const uint32_t grp = (end == 32 ? 0xffffffffu : (1u << end) - 1u) & ~((1u << first) - 1u);
+            const uint32_t orv = __reduce_or_sync(grp, bit);
+            if (word != 0xffffffffu && lane == first) atomicOr(bits + word, orv);
+        }
     }
 }
 
@@ -360,6 +385,21 @@ __device__ __forceinline__ uint32_t brick_word_p0(uint32_t w, const FastDiv& bdi
     return (bi << 3) | (((bj << 3) + ((sl & 1u) << 2)) << 10) | (((bk << 3) + (sl >> 1)) << 20);
 }
 
+// position of set bit number n (from 0) of v, for n < popc(v); always in [0, 31]
+__device__ __forceinline__ uint32_t nth_set_bit(uint32_t v, uint32_t n) {
+    uint32_t pos = 0;
+#pragma unroll
+    for (int w = 16; w >= 1; w >>= 1) {
+        const uint32_t lo = __popc(v & ((1u << w) - 1u));
+        if (n >= lo) {
+            n -= lo;
+            v >>= w;
+            pos += w;
+        }
+    }
+    return pos;
+}
+
 template <bool kBrick>
 __device__ __forceinline__ void emit_group(uint32_t x, int64_t w, int64_t g, int64_t base,
                                            int64_t cap, const FastDiv& gdiv,
@@ -379,6 +419,26 @@ __device__ __forceinline__ void emit_group(uint32_t x, int64_t w, int64_t g, int
     // this lane's word, bit 0
     const uint32_t p0 = kBrick ? brick_word_p0((uint32_t)w, gdiv) : pack_lin((uint32_t)(w * 32), gdiv);
     const uint32_t max_c = __reduce_max_sync(0xffffffffu, c);
+    if (kBrick && max_c <= (uint32_t)__popc(nz)) {
+        // scattered bits of brick words: rounds of 32 consecutive slots (coalesced
+        // stores); slot s belongs to the last lane o whose prefix ex_o <= s (its
+        // word holds it: ex_o + c_o > s) and is bit number s - ex_o of that word
+        const uint32_t total = __shfl_sync(0xffffffffu, inc, 31);
+        for (uint32_t s0 = 0; s0 < total; s0 += 32) {
+            const uint32_t sl = s0 + lane;
+            int o = 0;
+#pragma unroll
+            for (int step = 16; step >= 1; step >>= 1)
+                if (__shfl_sync(0xffffffffu, ex, o + step) <= sl) o += step;
+            const uint32_t xo = __shfl_sync(0xffffffffu, x, o);
+            const uint32_t eo = __shfl_sync(0xffffffffu, ex, o);
+            const uint32_t po = __shfl_sync(0xffffffffu, p0, o);
+            const uint32_t b = nth_set_bit(xo, sl - eo);
+            if (sl < total && base + sl < cap)
+                active[base + sl] = po + (b & 7u) + ((b >> 3) << 10);
+        }
+        return;
+    }
     if (max_c <= (uint32_t)__popc(nz)) {
         // scattered bits: every lane walks its own word (rounds = the largest popcount)
         uint32_t xb = x;
