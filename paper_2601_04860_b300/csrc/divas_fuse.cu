@@ -57,65 +57,114 @@ struct BackPtrs {
 // inside a brick in linear order (x fastest), so a 32-bit word is an 8 x 4
 // patch of one brick slice (g a multiple of 8).
 
-// sparse coordinates -> bitfield (atomic OR; duplicates merge), in linear or
-// brick-major layout.  Runs of consecutive lanes whose coordinates fall in the
-// same 32-bit word OR their bits together first (heads where a lane's word
-// differs from the previous lane's), so a sorted (or spatially coherent) set
-// costs one atomic per word and warp instead of one per coordinate.  Each
-// thread has the coordinates of kScatterUnroll grid-stride rounds loaded
-// before it handles the first.
-constexpr int kScatterUnroll = 4;
+// word and bit of coordinate (i, j, k) in the linear or brick-major layout
+// (at most 2^30 cells: 32-bit positions); word ~0u for a coordinate outside the
+// grid (negative values wrap above g), which also sets kStatusBadCoord
+template <bool kBrick>
+__device__ __forceinline__ void coord_bit(int32_t si, int32_t sj, int32_t sk, uint32_t ug,
+                                          int32_t* __restrict__ status, uint32_t& word,
+                                          uint32_t& bit) {
+    const uint32_t i = (uint32_t)si, j = (uint32_t)sj, k = (uint32_t)sk;
+    word = 0xffffffffu;
+    bit = 0u;
+    if (i >= ug || j >= ug || k >= ug) {
+        atomicOr(status, kStatusBadCoord);
+        return;
+    }
+    const uint32_t nb = ug >> 3;
+    const uint32_t lin = kBrick ? (((k >> 3) * nb + (j >> 3)) * nb + (i >> 3)) * 512u +
+                                      (((k & 7u) * 8u + (j & 7u)) * 8u + (i & 7u))
+                                : (k * ug + j) * ug + i;
+    word = lin >> 5;
+    bit = 1u << (lin & 31u);
+}
 
+// This lane's run of consecutive lanes holding the same word (from the last
+// head at or below the lane to the next head): its first lane and its end
+// (exclusive).  Warp-uniform call.
+__device__ __forceinline__ void word_run(uint32_t word, int& first, int& end) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t prev = __shfl_up_sync(0xffffffffu, word, 1);
+    const uint32_t heads = __ballot_sync(0xffffffffu, lane == 0 || prev != word);
+    first = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));
+    const uint32_t after = heads & ~(0xffffffffu >> (31 - lane));
+    end = after ? __ffs(after) - 1 : 32;
+}
+
+// OR of v over lanes [lane, end) by doubling steps (after the step of offset o
+// a lane holds the OR over [lane, min(lane + 2 o, end))), so a run's first lane
+// gets the run's OR: shuffles with the full mask, no per-run masks.
+// Warp-uniform call.
+__device__ __forceinline__ uint32_t run_suffix_or(uint32_t v, int end) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_down_sync(0xffffffffu, v, o);
+        if (lane + o < end) v |= y;
+    }
+    return v;
+}
+
+// OR of bit over this lane's run of equal words among consecutive lanes (valid
+// on the run's first lane), and whether the lane is the run's first.
+// Warp-uniform call.
+__device__ __forceinline__ uint32_t run_or(uint32_t word, uint32_t bit, bool& first_of_run) {
+    int first, end;
+    word_run(word, first, end);
+    first_of_run = (int)(threadIdx.x & 31) == first;
+    return run_suffix_or(bit, end);
+}
+
+// sparse coordinates -> bitfield (atomic OR; duplicates merge), in linear or
+// brick-major layout.  A warp takes 128 consecutive coordinates per round, 4
+// per lane (three 16-byte loads when the array is 16-byte aligned); a lane's
+// coordinates that fall in the same 32-bit word are OR-ed together, then the
+// lanes' k-th such runs that share a word with their neighbours' (one pass per
+// k), so a sorted or spatially coherent set costs about one atomic per word
+// and warp round instead of one per coordinate.
 template <bool kBrick>
 __global__ void __launch_bounds__(kThreads) k_scatter_coords(const int32_t* __restrict__ coords,
                                                              int64_t n, int32_t g,
                                                              uint32_t* __restrict__ bits,
                                                              int32_t* __restrict__ status) {
     const int lane = threadIdx.x & 31;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    const uint32_t ug = (uint32_t)g, nb = ug >> 3;
-    for (int64_t base = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) & ~(int64_t)31; base < n;
-         base += kScatterUnroll * stride) {
-        int32_t c[kScatterUnroll][3];
+    const uint32_t ug = (uint32_t)g;
+    const bool vec = (reinterpret_cast<uintptr_t>(coords) & 15) == 0;
+    const int64_t n_warps = (int64_t)gridDim.x * (blockDim.x / 32);
+    for (int64_t wb = ((int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5)) * 128; wb < n;
+         wb += n_warps * 128) {
+        const int64_t q0 = wb + 4 * lane;
+        int32_t v[12];
+        if (vec && q0 + 4 <= n) {
+            const uint4* p = reinterpret_cast<const uint4*>(coords + 3 * q0);
+            const uint4 a = __ldcs(p), b = __ldcs(p + 1), c = __ldcs(p + 2);
+            v[0] = (int32_t)a.x; v[1] = (int32_t)a.y; v[2] = (int32_t)a.z; v[3] = (int32_t)a.w;
+            v[4] = (int32_t)b.x; v[5] = (int32_t)b.y; v[6] = (int32_t)b.z; v[7] = (int32_t)b.w;
+            v[8] = (int32_t)c.x; v[9] = (int32_t)c.y; v[10] = (int32_t)c.z; v[11] = (int32_t)c.w;
+        } else {
 #pragma unroll
-        for (int u = 0; u < kScatterUnroll; ++u) {
-            const int64_t a = base + u * stride + lane;
-            c[u][0] = c[u][1] = c[u][2] = -1;
-            if (a < n) {
-                c[u][0] = __ldcs(coords + 3 * a);
-                c[u][1] = __ldcs(coords + 3 * a + 1);
-                c[u][2] = __ldcs(coords + 3 * a + 2);
+            for (int u = 0; u < 4; ++u) {
+                const bool in = q0 + u < n;
+#pragma unroll
+                for (int d = 0; d < 3; ++d) v[3 * u + d] = in ? __ldcs(coords + 3 * (q0 + u) + d) : 0;
             }
         }
+        uint32_t w[4], acc[4];
 #pragma unroll
-        for (int u = 0; u < kScatterUnroll; ++u) {
-            if (base + u * stride >= n) break;  // warp-uniform
-            const bool live = base + u * stride + lane < n;
-            const uint32_t i = (uint32_t)c[u][0], j = (uint32_t)c[u][1], k = (uint32_t)c[u][2];
-            uint32_t word = 0xffffffffu, bit = 0u;
-            if (live) {
-                if (i >= ug || j >= ug || k >= ug) {  // negative values wrap above g
-                    atomicOr(status, kStatusBadCoord);
-                } else {
-                    // at most 2^30 cells: 32-bit positions
-                    const uint32_t lin =
-                        kBrick ? (((k >> 3) * nb + (j >> 3)) * nb + (i >> 3)) * 512u +
-                                     (((k & 7u) * 8u + (j & 7u)) * 8u + (i & 7u))
-                               : (k * ug + j) * ug + i;
-                    word = lin >> 5;
-                    bit = 1u << (lin & 31u);
-                }
-            }
-            // this lane's run of equal words among consecutive lanes
-            const uint32_t prev = __shfl_up_sync(0xffffffffu, word, 1);
-            const uint32_t heads = __ballot_sync(0xffffffffu, lane == 0 || prev != word);
-            const uint32_t upto = heads & (0xffffffffu >> (31 - lane));
-            const int first = 31 - __clz(upto);
-            const uint32_t after = heads & ~(0xffffffffu >> (31 - lane));
-            const int end = after ? __ffs(after) - 1 : 32;
-            const uint32_t grp = (end == 32 ? 0xffffffffu : (1u << end) - 1u) & ~((1u << first) - 1u);
-            const uint32_t orv = __reduce_or_sync(grp, bit);
-            if (word != 0xffffffffu && lane == first) atomicOr(bits + word, orv);
+        for (int u = 0; u < 4; ++u) {
+            uint32_t bit = 0u;
+            w[u] = 0xffffffffu;
+            if (q0 + u < n) coord_bit<kBrick>(v[3 * u], v[3 * u + 1], v[3 * u + 2], ug, status, w[u], bit);
+            acc[u] = bit | (u > 0 && w[u] == w[u > 0 ? u - 1 : 0] ? acc[u > 0 ? u - 1 : 0] : 0u);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            // the lane's run ends at coordinate u: its word and bits take part in pass u
+            const bool ends = u == 3 || w[u] != w[u < 3 ? u + 1 : 3];
+            const uint32_t word = ends ? w[u] : 0xffffffffu;
+            bool first;
+            const uint32_t orv = run_or(word, ends ? acc[u] : 0u, first);
+            if (word != 0xffffffffu && first) atomicOr(bits + word, orv);
         }
     }
 }
@@ -592,16 +641,11 @@ __device__ __forceinline__ void seg_epilogue(bool live, bool seg, int64_t lin,
     const int lane = threadIdx.x & 31;
     const uint32_t word = live ? (uint32_t)(lin >> 5) : 0xffffffffu;
     const uint32_t bit = live ? 1u << (lin & 31) : 0u;
-    const uint32_t prev = __shfl_up_sync(0xffffffffu, word, 1);
-    const uint32_t heads = __ballot_sync(0xffffffffu, lane == 0 || prev != word);
-    // this lane's run: from the last head at or below it to the next head
-    const uint32_t upto = heads & (0xffffffffu >> (31 - lane));
-    const int first = 31 - __clz(upto);
-    const uint32_t after = heads & ~(0xffffffffu >> (31 - lane));
-    const int end = after ? __ffs(after) - 1 : 32;
-    const uint32_t grp = (end == 32 ? 0xffffffffu : (1u << end) - 1u) & ~((1u << first) - 1u);
-    const uint32_t set = __reduce_or_sync(grp, seg ? bit : 0u);
-    const uint32_t clr = __reduce_or_sync(grp, seg ? 0u : bit);
+    int first, end;
+    word_run(word, first, end);
+    const uint32_t set = run_suffix_or(seg ? bit : 0u, end);
+    const bool clearing = clear_bits || (seg_out && clear_out);  // warp-uniform
+    const uint32_t clr = clearing ? run_suffix_or(seg ? 0u : bit, end) : 0u;
     if (!live || lane != first) return;
     if (set) atomicOr(seg_bits + word, set);
     if (clr && clear_bits) atomicAnd(seg_bits + word, ~clr);
