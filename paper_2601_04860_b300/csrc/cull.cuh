@@ -282,21 +282,16 @@ __device__ __forceinline__ bool brick_box(uint32_t bi, uint32_t bj, uint32_t bk,
 // without an occupied cell (brick-major occupancy words all zero) get 0.  A
 // warp takes P = min(8, 32 / n) bricks at a time, lane l testing view l % n of
 // brick l / n.  Reads the compaction's bitfield, the pyramids and the views'
-// constants: waits for its predecessor first.
-//
-// wait_first: the predecessor is the pyramid kernel, waited for before any
-// read.  Otherwise the predecessor is the compaction's emit kernel, launched
-// after the count and pyramid kernels it waited for: both have completed when
-// this kernel starts, and it waits for the emit only before it ends (so that
-// a kernel waiting for this one has waited for the emit too).
+// constants: launched after the pyramid kernel (as its programmatic dependent,
+// or in plain stream order on a branch that has waited for the bitfield), it
+// waits for its predecessor before any read.
 __global__ void __launch_bounds__(256) k_brick_views(const CullView* __restrict__ sv, int32_t n,
                                                      const float* __restrict__ pyr, GridC G,
                                                      FastDiv bdiv,
                                                      const uint32_t* __restrict__ occ_bits,
                                                      int64_t n_bricks,
-                                                     uint32_t* __restrict__ brick_keep,
-                                                     int32_t wait_first) {
-    if (wait_first) wait_for_producer();  // the views' constants and the pyramids
+                                                     uint32_t* __restrict__ brick_keep) {
+    wait_for_producer();  // the views' constants and the pyramids
     allow_dependents();
     const int lane = threadIdx.x & 31;
     const int P = min(8, 32 / n);
@@ -327,7 +322,6 @@ __global__ void __launch_bounds__(256) k_brick_views(const CullView* __restrict_
         if (view == 0 && slot < P && b < n_bricks)
             brick_keep[b] = n == 32 ? m : (m >> (slot * n)) & ((1u << n) - 1u);
     }
-    if (!wait_first) wait_for_producer();
 }
 
 // A view's constants from a shared-memory copy of the batch (16-byte aligned):

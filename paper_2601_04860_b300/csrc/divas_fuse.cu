@@ -467,11 +467,11 @@ __device__ __forceinline__ void emit_group(uint32_t x, int64_t w, int64_t g, int
     const uint32_t ex = inc - c;
     // this lane's word, bit 0
     const uint32_t p0 = kBrick ? brick_word_p0((uint32_t)w, gdiv) : pack_lin((uint32_t)(w * 32), gdiv);
-    const uint32_t max_c = __reduce_max_sync(0xffffffffu, c);
-    if (kBrick && max_c <= (uint32_t)__popc(nz)) {
-        // scattered bits of brick words: rounds of 32 consecutive slots (coalesced
-        // stores); slot s belongs to the last lane o whose prefix ex_o <= s (its
-        // word holds it: ex_o + c_o > s) and is bit number s - ex_o of that word
+    if (kBrick) {
+        // brick words: rounds of 32 consecutive slots (coalesced stores, at most
+        // as many rounds as non-empty words); slot s belongs to the last lane o
+        // whose prefix ex_o <= s (its word holds it: ex_o + c_o > s) and is bit
+        // number s - ex_o of that word
         const uint32_t total = __shfl_sync(0xffffffffu, inc, 31);
         for (uint32_t s0 = 0; s0 < total; s0 += 32) {
             const uint32_t sl = s0 + lane;
@@ -488,6 +488,7 @@ __device__ __forceinline__ void emit_group(uint32_t x, int64_t w, int64_t g, int
         }
         return;
     }
+    const uint32_t max_c = __reduce_max_sync(0xffffffffu, c);
     if (max_c <= (uint32_t)__popc(nz)) {
         // scattered bits: every lane walks its own word (rounds = the largest popcount)
         uint32_t xb = x;
@@ -536,17 +537,32 @@ __global__ void __launch_bounds__(kThreads) k_tile_emit(
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t n_groups = (n_words + 31) / 32;
     const int64_t n_warps = (int64_t)gridDim.x * (kThreads / 32);
-    for (int64_t g = (int64_t)blockIdx.x * (kThreads / 32) + warp; g < n_groups; g += n_warps) {
+    // the group's slot base and words (one round trip), loaded for the next
+    // group of this warp while the current one is emitted
+    auto fetch = [&](int64_t g, uint32_t& base, uint32_t& x) {
+        base = 0u;
+        x = 0u;
+        if (g >= n_groups) return;
         const int64_t w = g * 32 + lane;
-        // the group's slot base is loaded with its words (one round trip)
-        const uint32_t t_off = __ldg(tile_offset + g / kTileGroups);
-        const uint32_t i_pre = __ldg(item_pref + g * (32 / kItemWords));
-        const uint32_t x = w < n_words ? __ldcg(bits + w) : 0u;
+        base = __ldg(tile_offset + g / kTileGroups) + __ldg(item_pref + g * (32 / kItemWords));
+        if (w < n_words) x = __ldcg(bits + w);
+    };
+    int64_t g = (int64_t)blockIdx.x * (kThreads / 32) + warp;
+    uint32_t base, x;
+    fetch(g, base, x);
+    while (g < n_groups) {
+        const int64_t gn = g + n_warps;
+        uint32_t base_n, x_n;
+        fetch(gn, base_n, x_n);
+        const int64_t w = g * 32 + lane;
         if (w < n_words) {
             if (seg_zero) seg_zero[w] = 0u;
             if (seg_zero2) seg_zero2[w] = 0u;
         }
-        emit_group<kBrick>(x, w, g, (int64_t)t_off + i_pre, cap, gdiv, active);
+        emit_group<kBrick>(x, w, g, (int64_t)base, cap, gdiv, active);
+        g = gn;
+        base = base_n;
+        x = x_n;
     }
 }
 
@@ -785,7 +801,9 @@ __global__ void __launch_bounds__(kThreads, kContracted ? 5 : 6) k_fuse_fin_cull
         const uint32_t bk_index =
             (((pk >> 23) * nb + ((pk >> 13) & 127u)) * nb + ((pk & 1023u) >> 3));
         const uint32_t mine = live ? __ldg(brick_keep + bk_index) : 0u;
-        const uint32_t keep = __reduce_or_sync(0xffffffffu, mine);
+        // only the batch's views, whatever the masks hold
+        const uint32_t keep = __reduce_or_sync(0xffffffffu, mine) &
+                              (n_views >= 32 ? 0xffffffffu : (1u << n_views) - 1u);
         if (!kAccumulate && keep == 0u && !clear_bits) {
             // no view can vote for any voxel of the warp: zero accumulators and
             // P = 0 (a zeroed score grid holds it already), no seg bit to set or
@@ -1106,6 +1124,8 @@ struct divas_ctx {
     uint32_t* brick_keep = nullptr;  // brick order: per brick, the views it may vote in
     CullView* cull_views = nullptr;  // brick order: the batch's views for the brick test
     ViewC* fold_views = nullptr;     // brick order: the batch's views for the culled fusion
+    cudaStream_t aux = nullptr;      // brick order: the culling kernels' branch of a step
+    cudaEvent_t fork[3] = {};        // brick order: start, occupancy bits ready, culling done
     void* sat = nullptr;   // tuple mode: integral-image scratch, grown on demand
     size_t sat_bytes = 0;
     void* wt = nullptr;    // depth weighting: selection state and histograms, grown on demand
@@ -1416,11 +1436,11 @@ cudaError_t launch_fuse_fin_cull(const divas_ctx* c, const ViewBatch& vb, int bl
     return e != cudaSuccess ? e : cudaGetLastError();
 }
 
-// the mask pyramids, then the culling fusion
-// the mask pyramids of a batch (programmatic dependent launch: the kernel reads
-// the masks only, and waits for its predecessor before it ends)
+// the mask pyramids of a batch (programmatic: a dependent launch -- the kernel
+// reads the masks only, and waits for its predecessor before it ends -- else
+// plain stream order)
 cudaError_t launch_pyramid(const divas_ctx* c, const ViewBatch& vb, const CullBatch& cb,
-                           cudaStream_t s) {
+                           cudaStream_t s, bool programmatic = true) {
     int32_t wmax = 1, hmax = 1;
     for (int32_t k = 0; k < vb.n; ++k) {
         wmax = std::max(wmax, vb.v[k].W);
@@ -1435,21 +1455,27 @@ cudaError_t launch_pyramid(const divas_ctx* c, const ViewBatch& vb, const CullBa
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = programmatic ? 1 : 0;
     return cudaLaunchKernelEx(&cfg, k_mask_pyramid, vb, cb, c->cull_views, c->fold_views);
 }
 
 // the bricks' kept views: several bricks per warp, one wave of CTAs
 cudaError_t launch_brick_views(const divas_ctx* c, const ViewBatch& vb, cudaStream_t s,
-                               bool wait_first) {
+                               bool programmatic = true) {
     const int64_t n_bricks = c->n_words / 16;
     const int64_t per_warp = std::min<int64_t>(8, 32 / std::max(1, vb.n));
     const int64_t warps = (n_bricks + per_warp - 1) / per_warp;
-    return launch_dependent(
-        k_brick_views,
-        (int)std::max<int64_t>(1, std::min<int64_t>((warps + 7) / 8, (int64_t)c->sm_count * 8)),
-        s, (const CullView*)c->cull_views, vb.n, (const float*)c->pyr, c->G, c->bdiv,
-        (const uint32_t*)c->occ_bits, n_bricks, c->brick_keep, (int32_t)(wait_first ? 1 : 0));
+    const int blocks =
+        (int)std::max<int64_t>(1, std::min<int64_t>((warps + 7) / 8, (int64_t)c->sm_count * 8));
+    if (!programmatic) {
+        k_brick_views<<<blocks, kThreads, 0, s>>>(
+            (const CullView*)c->cull_views, vb.n, (const float*)c->pyr, c->G, c->bdiv,
+            (const uint32_t*)c->occ_bits, n_bricks, c->brick_keep);
+        return cudaGetLastError();
+    }
+    return launch_dependent(k_brick_views, blocks, s, (const CullView*)c->cull_views, vb.n,
+                            (const float*)c->pyr, c->G, c->bdiv, (const uint32_t*)c->occ_bits,
+                            n_bricks, c->brick_keep);
 }
 
 // the culling fusion (the bricks' kept views are in place)
@@ -1475,7 +1501,7 @@ constexpr int32_t kCullMinViews = 4;
 
 // whether a batch on this context is fused with culling (then cb holds its constants)
 bool culling(const divas_ctx* c, const ViewBatch& vb, CullBatch& cb) {
-    return c->brick && c->pyr && c->brick_keep && c->cull_views && c->fold_views &&
+    return c->brick && c->pyr && c->brick_keep && c->cull_views && c->fold_views && c->aux &&
            vb.n >= kCullMinViews && make_cull(c, vb, cb);
 }
 
@@ -1491,7 +1517,7 @@ cudaError_t launch_fuse_fin(const divas_ctx* c, bool accumulate, const ViewBatch
     if (prepared || culling(c, vb, cb)) {
         if (!prepared) {
             cudaError_t e = launch_pyramid(c, vb, cb, s);
-            if (e == cudaSuccess) e = launch_brick_views(c, vb, s, true);
+            if (e == cudaSuccess) e = launch_brick_views(c, vb, s);
             if (e != cudaSuccess) return e;
         }
         return launch_culled_fuse(c, accumulate, vb, s, score_out, score_zeroed, clear_bits,
@@ -1520,8 +1546,21 @@ int emit_blocks(int64_t n_words, int32_t sm_count) {
 
 // occupancy -> bits -> tile counts -> active list (no allocation); seg_zero /
 // seg_zero2 (nullable) are seg bitfields to clear on the way
+// the culling branch of a brick-ordered one-call step: once the occupancy bits
+// are complete on s, the helper stream (which already builds the pyramids)
+// tests the bricks; fork[2] marks its end
+divas_status fork_brick_views(divas_ctx* c, const ViewBatch& vb, cudaStream_t s) {
+    DIVAS_CUDA(c, cudaEventRecord(c->fork[1], s));
+    DIVAS_CUDA(c, cudaStreamWaitEvent(c->aux, c->fork[1], 0));
+    const cudaError_t e = launch_brick_views(c, vb, c->aux, false);
+    if (e != cudaSuccess) return cuda_fail(c, e, "k_brick_views");
+    DIVAS_CUDA(c, cudaEventRecord(c->fork[2], c->aux));
+    return DIVAS_OK;
+}
+
 divas_status build_counts(divas_ctx* c, const uint8_t* occ, const int32_t* coords,
-                          int64_t n_coords, cudaStream_t s, float* score_zero = nullptr) {
+                          int64_t n_coords, cudaStream_t s, float* score_zero = nullptr,
+                          const ViewBatch* fork_vb = nullptr) {
     if (c->grid.kind == 0) {
         if (c->brick && (reinterpret_cast<uintptr_t>(occ) & 7))
             return fail(c, DIVAS_E_INVALID, "brick order needs an 8-byte aligned dense prior");
@@ -1536,6 +1575,7 @@ divas_status build_counts(divas_ctx* c, const uint8_t* occ, const int32_t* coord
                 c->tile_offset, c->done, c->n_tiles, c->d_n, c->d_total, c->d_status, c->grid.g,
                 c->bdiv, nullptr);
         DIVAS_LAUNCHED(c, "k_tile_count");
+        if (fork_vb) return fork_brick_views(c, *fork_vb, s);
     } else {
         DIVAS_CUDA(c, cudaMemsetAsync(c->occ_bits, 0, c->n_words * 4, s));
         if (n_coords > 0) {
@@ -1546,6 +1586,10 @@ divas_status build_counts(divas_ctx* c, const uint8_t* occ, const int32_t* coord
                 k_scatter_coords<false><<<grid_for(n_coords, c->sm_count, 32), kThreads, 0, s>>>(
                     coords, n_coords, c->grid.g, c->occ_bits, c->d_status);
             DIVAS_LAUNCHED(c, "k_scatter_coords");
+        }
+        if (fork_vb) {
+            const divas_status st = fork_brick_views(c, *fork_vb, s);
+            if (st != DIVAS_OK) return st;
         }
         k_tile_count<1><<<c->n_tiles, kThreads, 0, s>>>(
             nullptr, c->occ_bits, c->n_cells, c->n_words, c->cap, c->item_pref, c->tile_count,
@@ -1558,19 +1602,24 @@ divas_status build_counts(divas_ctx* c, const uint8_t* occ, const int32_t* coord
 
 // the full compaction: counts, then (when the active arrays exist) the list;
 // seg_zero / seg_zero2 (nullable) are seg bitfields to clear on the way
-// cull (nullable): a view batch whose pyramids are built while the counts
-// complete and whose bricks' kept views are tested while the entries are
-// emitted (the one-call step of a brick-ordered context)
+// cull (nullable): a view batch culled per brick (the one-call step of a
+// brick-ordered context).  The culling kernels run on the context's helper
+// stream, concurrently with the compaction: the pyramids from the start (they
+// read the masks only), the brick test once the occupancy bits are complete;
+// s waits for them after the emit.
 divas_status build_active(divas_ctx* c, const uint8_t* occ, const int32_t* coords, int64_t n_coords,
                           cudaStream_t s, uint32_t* seg_zero = nullptr,
                           uint32_t* seg_zero2 = nullptr, float* score_zero = nullptr,
                           const ViewBatch* cull_vb = nullptr, const CullBatch* cull_cb = nullptr) {
-    divas_status st = build_counts(c, occ, coords, n_coords, s, score_zero);
-    if (st != DIVAS_OK || !c->active) return st;
-    if (cull_vb) {
-        const cudaError_t e = launch_pyramid(c, *cull_vb, *cull_cb, s);
+    const bool fork = cull_vb && c->active;
+    if (fork) {
+        DIVAS_CUDA(c, cudaEventRecord(c->fork[0], s));
+        DIVAS_CUDA(c, cudaStreamWaitEvent(c->aux, c->fork[0], 0));
+        const cudaError_t e = launch_pyramid(c, *cull_vb, *cull_cb, c->aux, false);
         if (e != cudaSuccess) return cuda_fail(c, e, "k_mask_pyramid");
     }
+    divas_status st = build_counts(c, occ, coords, n_coords, s, score_zero, fork ? cull_vb : nullptr);
+    if (st != DIVAS_OK || !c->active) return st;
     cudaError_t e = launch_dependent(c->brick ? k_tile_emit<true> : k_tile_emit<false>,
                                      emit_blocks(c->n_words, c->sm_count), s,
                                      (const uint32_t*)c->occ_bits, c->n_words, c->cap,
@@ -1579,10 +1628,7 @@ divas_status build_active(divas_ctx* c, const uint8_t* occ, const int32_t* coord
                                      seg_zero2);
     if (e != cudaSuccess) return cuda_fail(c, e, "k_tile_emit");
     DIVAS_LAUNCHED(c, "k_tile_emit");
-    if (cull_vb) {
-        e = launch_brick_views(c, *cull_vb, s, false);
-        if (e != cudaSuccess) return cuda_fail(c, e, "k_brick_views");
-    }
+    if (fork) DIVAS_CUDA(c, cudaStreamWaitEvent(s, c->fork[2], 0));
     return DIVAS_OK;
 }
 
@@ -1610,6 +1656,9 @@ void free_all(divas_ctx* c) {
     if (c->brick_keep) cudaFree(c->brick_keep);
     if (c->cull_views) cudaFree(c->cull_views);
     if (c->fold_views) cudaFree(c->fold_views);
+    for (cudaEvent_t& ev : c->fork)
+        if (ev) cudaEventDestroy(ev);
+    if (c->aux) cudaStreamDestroy(c->aux);
     void* ptrs[] = {c->occ_bits, c->item_pref, c->tile_count, c->tile_offset, c->done,
                     c->seg_bits, c->active,     c->W,          c->Z,           c->bits,
                     c->d_n,      c->d_status,   c->d_total,    c->d_nseg};
@@ -1715,6 +1764,9 @@ divas_status divas_fuse_init(divas_ctx** out, const divas_grid* grid, const uint
         INIT_CUDA(cudaMalloc(&c->brick_keep, (c->n_words / 16) * 4));
         INIT_CUDA(cudaMalloc(&c->cull_views, kMaxViews * sizeof(CullView)));
         INIT_CUDA(cudaMalloc(&c->fold_views, kMaxViews * sizeof(ViewC)));
+        INIT_CUDA(cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking));
+        for (cudaEvent_t& ev : c->fork)
+            INIT_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
     }
     INIT_CUDA(cudaMemsetAsync(c->d_status, 0, 4, s));
     INIT_CUDA(cudaMemsetAsync(c->seg_bits, 0, c->n_words * 4, s));
@@ -2239,8 +2291,10 @@ __device__ __forceinline__ void batch_fuse_item_cull(const SessionDesc& D, const
             : D.brick_keep
                 ? __ldg(D.brick_keep +
                         (((pk >> 23) * nb + ((pk >> 13) & 127u)) * nb + ((pk & 1023u) >> 3)))
-                : (D.n_views >= 32 ? 0xffffffffu : (1u << D.n_views) - 1u);
-        const uint32_t keep = __reduce_or_sync(0xffffffffu, mine);
+                : 0xffffffffu;
+        // only the session's views, whatever the masks hold
+        const uint32_t keep = __reduce_or_sync(0xffffffffu, mine) &
+                              (D.n_views >= 32 ? 0xffffffffu : (1u << D.n_views) - 1u);
         const VoxelGeom vg = voxel_geom<kContracted>(pk, D.G, D.F.gamma);
         if (!live) continue;
         float W = 0.f, Z = 0.f;
@@ -2496,7 +2550,7 @@ divas_status divas_batch_fuse(divas_batch* b, const divas_schedule* sched, int32
             CullBatch cb;
             if (culling(c, vb, cb)) {
                 cudaError_t ce = launch_pyramid(c, vb, cb, s);
-                if (ce == cudaSuccess) ce = launch_brick_views(c, vb, s, true);
+                if (ce == cudaSuccess) ce = launch_brick_views(c, vb, s);
                 if (ce != cudaSuccess) return bfail(b, DIVAS_E_CUDA, cudaGetErrorString(ce));
                 keep = c->brick_keep;
             }
