@@ -372,28 +372,22 @@ __device__ __forceinline__ void fold_views_kept(const ViewC* sv, uint32_t keep,
                 const ViewC V = view_from_shared(sv, vi[q]);
                 load_raster<kMT>(V, pix[q], D[q], raw[q]);
             }
-        float e[kViewChunk];
         uint32_t acc = 0u;
 #pragma unroll
         for (int q = 0; q < kViewChunk; ++q) {
             if (vi[q] < 0) break;
             const ViewC V = view_from_shared(sv, vi[q]);
-            const bool pass =
-                kContracted ? pre_gates<true, kMT>(V, vg, F, pix[q], pzh[q], D[q], raw[q])
-                            : gates<false, kMT>(V, vg, F, pix[q], pzh[q], pzl[q], D[q], raw[q], e[q]);
-            if (pass) acc |= 1u << q;
+            if (pre_gates<kContracted, kMT>(V, vg, F, pix[q], pzh[q], D[q], raw[q])) acc |= 1u << q;
         }
         if (acc) {
 #pragma unroll
             for (int q = 0; q < kViewChunk; ++q) {
                 if (acc & (1u << q)) {
                     const ViewC V = view_from_shared(sv, vi[q]);
-                    if constexpr (kContracted) {
-                        e[q] = depth_error<true>(V, vg, pzh[q], pzl[q], D[q]);
-                        if (!(fabsf(e[q]) <= vg.Delta)) continue;
-                    }
+                    const float e = depth_error<kContracted>(V, vg, pzh[q], pzl[q], D[q]);
+                    if (!(fabsf(e) <= vg.Delta)) continue;
                     float m, w;
-                    weight<kMT>(V, vg, F, raw[q], e[q], m, w);
+                    weight<kMT>(V, vg, F, raw[q], e, m, w);
                     W = __fmaf_rn(m, w, W);
                     Z = __fadd_rn(Z, w);
                     bits |= V.bit;

@@ -1208,6 +1208,21 @@ cudaError_t launch_dependent(void (*f)(KArgs...), int blocks, cudaStream_t s, Ar
     return cudaLaunchKernelEx(&cfg, f, std::forward<Args>(args)...);
 }
 
+// A plain grid's depth tolerance Delta = fl(gamma h) and its derived
+// constants, as the kernels would round them: the single-precision product and
+// quotient here round to nearest like __fmul_rn and __frcp_rn; Delta (1 +
+// 2^-20) is exact in double and rounded up to float.
+void set_tolerances(GridC& G, float gamma) {
+    const float delta = gamma * G.h;
+    G.delta = delta;
+    G.inv_delta = 1.0f / delta;
+    const double ds = (double)delta * (1.0 + 0x1p-20);
+    float f = (float)ds;
+    if ((double)f < ds) f = nextafterf(f, INFINITY);
+    G.delta_s = f;
+    G.pad2 = 0;
+}
+
 // Argument checks shared by every entry point that takes a grid, fusion
 // parameters or a camera: nullptr when the argument is valid, else the reason.
 const char* grid_problem(const divas_grid* grid, int32_t g_max) {
@@ -1326,11 +1341,19 @@ ViewC make_view(const divas_camera& cam, const GridC& G, const float* depth, con
         }
         v.C[0] = (float)((double)cam.fx * T[0] + (double)cam.cx * T[2]);
         v.C[1] = (float)((double)cam.fy * T[1] + (double)cam.cy * T[2]);
+        if (folded) {
+            // the plain depth row (rounded to float) and the depth screen's
+            // slack 2^-20 b_max, rounded up
+            for (int j = 0; j < 3; ++j) v.K[j] = (float)M[2][j];
+            v.K[3] = nextafterf((float)ldexp(bmax, -20), INFINITY);
+        }
     }
-    v.K[0] = cam.fx;
-    v.K[1] = cam.fy;
-    v.K[2] = cam.cx;
-    v.K[3] = cam.cy;
+    if (G.contracted || !folded) {
+        v.K[0] = cam.fx;
+        v.K[1] = cam.fy;
+        v.K[2] = cam.cx;
+        v.K[3] = cam.cy;
+    }
     v.W = cam.W;
     v.H = cam.H;
     v.mask_type = mask_type;
@@ -1725,6 +1748,7 @@ divas_status divas_fuse_init(divas_ctx** out, const divas_grid* grid, const uint
     c->F.eps = params->eps;
     c->F.tau_cons = params->tau_cons;
     c->F.pad = 0;
+    set_tolerances(c->G, c->F.gamma);
     c->gdiv = make_fast_div((uint32_t)grid->g);
     c->brick = (params->flags & DIVAS_ORDER_BRICKS) != 0;
     c->bdiv = make_fast_div((uint32_t)std::max(1, grid->g / 8));
@@ -2863,6 +2887,7 @@ extern "C" divas_status divas_fuse_dense_noalloc(const divas_grid* grid, const u
     F.eps = params->eps;
     F.tau_cons = params->tau_cons;
     F.pad = 0;
+    set_tolerances(G, F.gamma);
     FastDiv gdiv;
     {
         const uint32_t d = (uint32_t)grid->g;

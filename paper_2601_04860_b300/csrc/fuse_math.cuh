@@ -112,7 +112,10 @@ __device__ __forceinline__ void dot3c(float a0, float a1, float a2, const float*
 //   contracted grid: A = R, C = t (B, E unused)
 // Per-view constants (112 bytes, so that a batch of 32 views stays within the
 // classic 4 KB kernel-parameter space).  Plain grids: A = (Ku, Kv, M_z hi),
-// B = M_z lo, C = (Tu, Tv, T_z hi), E = T_z lo.  Contracted grids: A = (Ku,
+// B = M_z lo, C = (Tu, Tv, T_z hi), E = T_z lo; K = (M_z rounded to float,
+// the depth screen's slack 2^-20 b_max rounded up, b_max = |T_z| + 2 g
+// sum_j |M_zj|) -- K holds the intrinsics (fx, fy, cx, cy) only for the
+// depth-tuple modes' unfolded views.  Contracted grids: A = (Ku,
 // Kv, R_z) with Ku = fx R_x + cx R_z, Kv = fy R_y + cy R_z, C = (fx t_x + cx
 // t_z, fy t_y + cy t_z, t_z); the depth screen's bound is
 // B[0] n1 + E >= 2^-19 S with B[0] >= 2^-19 max_j |R_zj| and E = 2^-19 |t_z|
@@ -155,6 +158,10 @@ struct GridC {
     int32_t contracted;
     float inv_h;  // 1/h when h is a power of two (exact), else 0
     int32_t pad;
+    // plain grids: Delta = fl(gamma h), 1 / Delta (rounded to nearest) and
+    // Delta (1 + 2^-20) rounded up, the same for every voxel
+    float delta, inv_delta, delta_s;
+    int32_t pad2;
 };
 
 struct FuseC {
@@ -171,9 +178,9 @@ struct VoxelGeom {
     float xh[3], xl[3];  // plain grid: xh = n = 2 idx + 1, xl unused
     float Delta, invDelta;
     float hv;            // world edge h_v
-    // contracted grids: x_s = fl(x_hi + x_lo), the centre the plain rows use;
-    // for the depth screen n1 = sum_j |x_hi,j| + |x_lo,j| and
-    // Delta (1 + 2^-20), both rounded up
+    // contracted grids: x_s = fl(x_hi + x_lo), the centre the plain rows use,
+    // and for the depth screen n1 = sum_j |x_hi,j| + |x_lo,j| (rounded up);
+    // both kinds: Delta (1 + 2^-20) rounded up
     float xs[3];
     float n1, DeltaS;
     bool ok;  // false: contracted centre with |c| >= 2 (no world position)
@@ -219,8 +226,9 @@ __device__ __forceinline__ VoxelGeom voxel_geom(uint32_t pk, const GridC& G, flo
         vg.xh[2] = (float)(2 * k + 1);
         vg.xl[0] = vg.xl[1] = vg.xl[2] = 0.f;
         vg.hv = G.h;
-        vg.Delta = __fmul_rn(gamma, G.h);
-        vg.invDelta = __frcp_rn(vg.Delta);
+        vg.Delta = G.delta;  // fl(gamma h), from the host
+        vg.invDelta = G.inv_delta;
+        vg.DeltaS = G.delta_s;
         return vg;
     }
     const float idx[3] = {(float)i, (float)j, (float)k};
@@ -317,11 +325,14 @@ __device__ __forceinline__ int32_t project(const ViewC& V, const VoxelGeom& vg, 
                                            float& pzh, float& pzl) {
     float pz, u, v;
     if (!kContracted) {
-        // depth exactly (hi + lo); the pixel rows u p_z = Ku n + Tu and
-        // v p_z = Kv n + Tv in plain FMA chains (a few ulp of |Ku n| + |Tu|:
-        // about 1e-4 pixel on the benchmark cameras)
-        lattice_row(V.A + 6, V.B, V.C[2], V.E, vg.xh, pzh, pzl);
-        pz = __fadd_rn(pzh, pzl);
+        // the depth in a plain FMA chain over the rounded row (within 2^-21.6
+        // b_max of the exact lattice depth; made exact by depth_error where the
+        // screen lets it pass), returned as (plain, 0); the pixel rows
+        // u p_z = Ku n + Tu and v p_z = Kv n + Tv likewise (a few ulp of
+        // |Ku n| + |Tu|: about 1e-4 pixel on the benchmark cameras)
+        pz = __fmaf_rn(V.K[0], vg.xh[0], __fmaf_rn(V.K[1], vg.xh[1], __fmaf_rn(V.K[2], vg.xh[2], V.C[2])));
+        pzh = pz;
+        pzl = 0.f;
         const float pu = __fmaf_rn(V.A[0], vg.xh[0],
                                    __fmaf_rn(V.A[1], vg.xh[1], __fmaf_rn(V.A[2], vg.xh[2], V.C[0])));
         const float pv = __fmaf_rn(V.A[3], vg.xh[0],
@@ -374,33 +385,38 @@ __device__ __forceinline__ void load_raster(const ViewC& V, int32_t pix, float& 
 // ---------------------------------------------------------------------------
 // step 3: gates (predicates) and, for an accepted vote, the weight
 // ---------------------------------------------------------------------------
-// Contracted grids: false only where |e| > Delta for certain.  The plain depth
+// False only where |e| > Delta for certain.  Contracted grids: the plain depth
 // pz differs from the exact one by at most 2^-21.9 S; fl(pz - D) adds 2^-24
 // of itself; the exact e = fl(fl(p_z,hi - D) + p_z,lo) is within 2^-23 of
 // its own size of p_z - D.  So |e| <= Delta implies
 // |fl(pz - D)| <= Delta (1 + 2^-22) + 2^-21.2 S, which the threshold
 // Delta (1 + 2^-20) + 2^-19 S, summed rounding up, exceeds.  Plain grids:
-// true (their depth pair is already exact).
+// the plain depth is within 5.2 2^-24 b_max of the exact pair (rounded row,
+// T_z's lo part left out, three FMAs), so |e| <= Delta implies
+// |fl(pz - D)| <= Delta (1 + 2^-21.9) + 5.3 2^-24 b_max, below the
+// threshold Delta (1 + 2^-20) + 2^-20 b_max summed rounding up.
 template <bool kContracted>
 __device__ __forceinline__ bool depth_screen(const ViewC& V, const VoxelGeom& vg, float pzh,
                                              float D) {
-    if (!kContracted) return true;
-    const float thr = __fadd_ru(vg.DeltaS, __fmaf_ru(V.B[0], vg.n1, V.E));
+    const float thr = kContracted ? __fadd_ru(vg.DeltaS, __fmaf_ru(V.B[0], vg.n1, V.E))
+                                  : __fadd_ru(vg.DeltaS, V.K[3]);
     return fabsf(__fsub_rn(pzh, D)) <= thr;
 }
 
-// e = p_z - D from the exact depth: plain grids the pair of project(),
-// contracted grids the compensated dot product
+// e = p_z - D from the exact depth: plain grids the lattice row as hi + lo
+// (the hi chain is exact), contracted grids the compensated dot product
 template <bool kContracted>
 __device__ __forceinline__ float depth_error(const ViewC& V, const VoxelGeom& vg, float pzh,
                                              float pzl, float D) {
-    if (kContracted) dot3c(V.A[6], V.A[7], V.A[8], vg.xh, vg.xl, V.C[2], pzh, pzl);
+    if (kContracted)
+        dot3c(V.A[6], V.A[7], V.A[8], vg.xh, vg.xl, V.C[2], pzh, pzl);
+    else
+        lattice_row(V.A + 6, V.B, V.C[2], V.E, vg.xh, pzh, pzl);
     return __fadd_rn(__fsub_rn(pzh, D), pzl);
 }
 
 // the gates before the depth gate: a pixel in frame, a surface there (+inf,
-// NaN or <= 0 depth: none), the mask gate; for contracted grids also the
-// depth screen
+// NaN or <= 0 depth: none), the mask gate and the depth screen
 template <bool kContracted, int kMT = -1>
 __device__ __forceinline__ bool pre_gates(const ViewC& V, const VoxelGeom& vg, const FuseC& F,
                                           int32_t pix, float pzh, float D, float raw) {
@@ -413,12 +429,8 @@ template <bool kContracted, int kMT = -1>
 __device__ __forceinline__ bool gates(const ViewC& V, const VoxelGeom& vg, const FuseC& F,
                                       int32_t pix, float pzh, float pzl, float D, float raw,
                                       float& e) {
-    if (!kContracted) {
-        e = depth_error<false>(V, vg, pzh, pzl, D);
-        return pre_gates<false, kMT>(V, vg, F, pix, pzh, D, raw) && fabsf(e) <= vg.Delta;
-    }
-    if (!pre_gates<true, kMT>(V, vg, F, pix, pzh, D, raw)) return false;
-    e = depth_error<true>(V, vg, pzh, pzl, D);
+    if (!pre_gates<kContracted, kMT>(V, vg, F, pix, pzh, D, raw)) return false;
+    e = depth_error<kContracted>(V, vg, pzh, pzl, D);
     return fabsf(e) <= vg.Delta;
 }
 
@@ -475,31 +487,25 @@ __device__ __forceinline__ void fold_views(const ViewBatch& VB, const VoxelGeom&
         for (int q = 0; q < kViewChunk; ++q)
             if (kF16Full || c * kViewChunk + q < VB.n)
                 load_raster<kMT>(VB.v[c * kViewChunk + q], pix[q], D[q], raw[q]);
-        // the chunk's gates as predicates, then one branch into the (rare) votes,
-        // added in view order (contracted grids: the screened candidates, whose
-        // exact depth decides there)
-        float e[kViewChunk];
+        // the chunk's gates up to the depth screen as predicates, then one
+        // branch into the (rare) candidates, whose exact depth decides and
+        // weighs, added in view order
         uint32_t acc = 0u;
 #pragma unroll
         for (int q = 0; q < kViewChunk; ++q) {
             if (!kF16Full && c * kViewChunk + q >= VB.n) break;
             const ViewC& V = VB.v[c * kViewChunk + q];
-            const bool pass =
-                kContracted ? pre_gates<true, kMT>(V, vg, F, pix[q], pzh[q], D[q], raw[q])
-                            : gates<false, kMT>(V, vg, F, pix[q], pzh[q], pzl[q], D[q], raw[q], e[q]);
-            if (pass) acc |= 1u << q;
+            if (pre_gates<kContracted, kMT>(V, vg, F, pix[q], pzh[q], D[q], raw[q])) acc |= 1u << q;
         }
         if (acc) {
 #pragma unroll
             for (int q = 0; q < kViewChunk; ++q) {
                 if (acc & (1u << q)) {
                     const ViewC& V = VB.v[c * kViewChunk + q];
-                    if constexpr (kContracted) {
-                        e[q] = depth_error<true>(V, vg, pzh[q], pzl[q], D[q]);
-                        if (!(fabsf(e[q]) <= vg.Delta)) continue;
-                    }
+                    const float e = depth_error<kContracted>(V, vg, pzh[q], pzl[q], D[q]);
+                    if (!(fabsf(e) <= vg.Delta)) continue;
                     float m, w;
-                    weight<kMT>(V, vg, F, raw[q], e[q], m, w);
+                    weight<kMT>(V, vg, F, raw[q], e, m, w);
                     W = __fmaf_rn(m, w, W);
                     Z = __fadd_rn(Z, w);
                     bits |= V.bit;
