@@ -64,10 +64,10 @@ def _env_int(k, d):
 STEP_SOURCES = ("paper_2601_04860_b300/csrc/divas_fuse.cu",
                 "paper_2601_04860_b300/csrc/fuse_math.cuh")
 TRAFFIC_CAPTURE = {
-    "source_sha1": "535f4caa37f9db814644d80ca6783d8040fa83db",
-    "forward-dense-256": {"k_fuse_fin": 28_215_808 + 20_422_400,
-                          "k_tile_count": 16_800_256, "k_tile_emit": 2_368_512,
-                          "k_label": 13_340_160 + 3_072},
+    "source_sha1": "651c34d77436ca2986c442242c1a7377a4941e7e",
+    "forward-dense-256": {"k_fuse_fin": 28_130_816 + 18_378_240,
+                          "k_tile_count": 16_800_512, "k_tile_emit": 2_373_376,
+                          "k_label": 13_338_112},
 }
 
 
@@ -108,8 +108,8 @@ def job_throughput(units_per_rank: float, world: int, ms_max: float) -> float:
 # warp instructions per voxel-view of the contracted fusion kernel on the
 # unbounded-sparse workload (ncu smsp__inst_executed.sum of one launch divided
 # by its 12M active voxels x 16 views), per active-list order: brick order runs
-# k_fuse_fin_cull (355,193,212 per launch), linear order k_fuse_fin (4.669e8)
-SPARSE_FUSE_INSTS_PER_VOXEL_VIEW = {"brick": 355_193_212 / 192e6, "linear": 466_900_000 / 192e6}
+# k_fuse_fin_cull (357,818,212 per launch), linear order k_fuse_fin (4.470e8)
+SPARSE_FUSE_INSTS_PER_VOXEL_VIEW = {"brick": 357_818_212 / 192e6, "linear": 447_009_000 / 192e6}
 
 
 ACTIVE_ORDER = "auto"  # --active-order
