@@ -506,35 +506,46 @@ def run_ours(args, rank, world, local_rank):
     # end to end through the public API: every step copies all of its inputs
     # (occupancy prior, rasters, points) from pinned host memory and its
     # outputs (the seg bitfield V_seg and the point labels) back to pinned host
-    # memory; the probability grid stays on the device.  Two device buffer
-    # sets and three streams (copy-in, kernels, copy-out) let step k + 1's
-    # copies overlap step k's kernels; the serial figure (one stream, a
-    # synchronisation per step) is reported beside it.
-    h_occ = None if occ is None else torch.from_numpy(wl.occ).pin_memory()
-    h_coords = None if coords is None else torch.from_numpy(wl.coords).pin_memory()
-    h_depth = [d.cpu().pin_memory() for d in depth]
-    h_mask = [m.cpu().pin_memory() for m in mask]
-    h_pts = pts.cpu().pin_memory()
+    # memory; the probability grid stays on the device.  The inputs of a step
+    # sit in one pinned host arena and move in one copy, its outputs in
+    # another (paper_2601_04860_b300.staging.Arena: a producer writes a step's
+    # inputs straight into the arena's host views).  Two arena sets and three
+    # streams (copy-in, kernels, copy-out) let step k + 1's copy overlap step
+    # k's kernels; the serial figure (one stream, a synchronisation per step)
+    # is reported beside it, and so is the same overlapped run with one copy
+    # per buffer (`per_buffer_ms_per_step`).
+    from paper_2601_04860_b300.staging import Arena
     n_seg_words = (fu.n_cells + 31) // 32
+    in_specs = []
+    if occ is not None:
+        in_specs.append(("occ", tuple(occ.shape), occ.dtype))
+    if coords is not None:
+        in_specs.append(("coords", tuple(coords.shape), coords.dtype))
+    in_specs += [(f"depth{k}", tuple(d.shape), d.dtype) for k, d in enumerate(depth)]
+    in_specs += [(f"mask{k}", tuple(m.shape), m.dtype) for k, m in enumerate(mask)]
+    in_specs.append(("pts", tuple(pts.shape), pts.dtype))
+    out_specs = [("seg", (n_seg_words,), torch.int32), ("labels", tuple(labels.shape), labels.dtype)]
     sets = []
     for _ in range(2):
-        st = {"occ": None if occ is None else torch.empty_like(occ),
-              "coords": None if coords is None else torch.empty_like(coords),
-              "depth": [torch.empty_like(d) for d in depth],
-              "mask": [torch.empty_like(m) for m in mask],
-              "pts": torch.empty_like(pts),
-              "seg": torch.empty(n_seg_words, dtype=torch.int32, device=dev),
-              "labels": torch.empty_like(labels),
-              "h_seg": torch.empty(n_seg_words, dtype=torch.int32).pin_memory(),
-              "h_labels": torch.empty(labels.shape, dtype=labels.dtype).pin_memory()}
-        st["pv"] = PreparedViews(wl.cams, st["depth"], st["mask"], wl.mask_type)
+        ai, ao = Arena(in_specs, dev), Arena(out_specs, dev)
+        if occ is not None:
+            ai.host["occ"].copy_(torch.from_numpy(wl.occ))
+        if coords is not None:
+            ai.host["coords"].copy_(torch.from_numpy(wl.coords))
+        for k, d in enumerate(depth):
+            ai.host[f"depth{k}"].copy_(d.cpu())
+        for k, m in enumerate(mask):
+            ai.host[f"mask{k}"].copy_(m.cpu())
+        ai.host["pts"].copy_(pts.cpu())
+        st = {"in": ai, "out": ao,
+              "pv": PreparedViews(wl.cams, [ai.device[f"depth{k}"] for k in range(len(depth))],
+                                  [ai.device[f"mask{k}"] for k in range(len(mask))], wl.mask_type)}
         sets.append(st)
-    h2d = sum(t.numel() * t.element_size() for t in
-              [x for x in (h_occ, h_coords) if x is not None] + h_depth + h_mask + [h_pts])
-    d2h = n_seg_words * 4 + labels.numel() * labels.element_size()
+    h2d = sets[0]["in"].payload_bytes()
+    d2h = sets[0]["out"].payload_bytes()
     s_in, s_k, s_out = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
 
-    def e2e_run(n_steps: int, overlap: bool) -> float:
+    def e2e_run(n_steps: int, overlap: bool, per_buffer: bool = False) -> float:
         """n_steps end-to-end steps; returns ms per step (device events from
         the first copy-in to the last copy-out)."""
         in_free = [None, None]   # kernels of the step that last read a set's inputs
@@ -545,38 +556,41 @@ def run_ours(args, rank, world, local_rank):
         for k in range(n_steps):
             st = sets[k % 2] if overlap else sets[0]
             j = k % 2 if overlap else 0
+            ai, ao = st["in"], st["out"]
             with torch.cuda.stream(s_in):
                 if in_free[j] is not None:
                     s_in.wait_event(in_free[j])
-                if st["occ"] is not None:
-                    st["occ"].copy_(h_occ, non_blocking=True)
-                if st["coords"] is not None:
-                    st["coords"].copy_(h_coords, non_blocking=True)
-                for a, b in zip(st["depth"], h_depth):
-                    a.copy_(b, non_blocking=True)
-                for a, b in zip(st["mask"], h_mask):
-                    a.copy_(b, non_blocking=True)
-                st["pts"].copy_(h_pts, non_blocking=True)
+                if per_buffer:
+                    for name in ai.host:
+                        ai.device[name].copy_(ai.host[name], non_blocking=True)
+                else:
+                    ai.upload(s_in)
                 e_in = torch.cuda.Event()
                 e_in.record(s_in)
             s_k.wait_event(e_in)
             if out_free[j] is not None:
                 s_k.wait_event(out_free[j])
+            d_occ = ai.device.get("occ")
+            d_coords = ai.device.get("coords")
             if len(st["pv"].chunks) == 1:
-                fu.step(st["pv"], occ=st["occ"], coords=st["coords"], score=score,
-                        seg_bits=st["seg"], xyz=st["pts"], labels=st["labels"], stream=s_k)
+                fu.step(st["pv"], occ=d_occ, coords=d_coords, score=score,
+                        seg_bits=ao.device["seg"], xyz=ai.device["pts"],
+                        labels=ao.device["labels"], stream=s_k)
             else:
-                fu.set_occupancy(occ=st["occ"], coords=st["coords"], stream=s_k)
+                fu.set_occupancy(occ=d_occ, coords=d_coords, stream=s_k)
                 fu.add_views(st["pv"], stream=s_k)
-                fu.finalize(score=score, seg_bits=st["seg"], stream=s_k)
-                fu.label_points(st["pts"], out=st["labels"], stream=s_k)
+                fu.finalize(score=score, seg_bits=ao.device["seg"], stream=s_k)
+                fu.label_points(ai.device["pts"], out=ao.device["labels"], stream=s_k)
             e_k = torch.cuda.Event()
             e_k.record(s_k)
             in_free[j] = e_k
             s_out.wait_event(e_k)
             with torch.cuda.stream(s_out):
-                st["h_seg"].copy_(st["seg"], non_blocking=True)
-                st["h_labels"].copy_(st["labels"], non_blocking=True)
+                if per_buffer:
+                    for name in ao.host:
+                        ao.host[name].copy_(ao.device[name], non_blocking=True)
+                else:
+                    ao.download(s_out)
                 e_o = torch.cuda.Event()
                 e_o.record(s_out)
                 out_free[j] = e_o
@@ -588,11 +602,13 @@ def run_ours(args, rank, world, local_rank):
 
     e2e_run(4, True)
     e2e_run(2, False)
+    e2e_run(2, True, per_buffer=True)
     e2e_steps = max(10, args.steps)
     e2e_ms = max_over_ranks(float(np.mean([e2e_run(e2e_steps, True) for _ in range(3)])), world, dev)
     e2e_serial_ms = float(np.mean([e2e_run(e2e_steps, False) for _ in range(2)]))
+    e2e_per_buffer_ms = float(np.mean([e2e_run(e2e_steps, True, per_buffer=True) for _ in range(2)]))
     # the labels read back (same inputs every step) equal the device result
-    if not torch.equal(sets[0]["h_labels"], labels.cpu()):
+    if not torch.equal(sets[0]["out"].host["labels"], labels.cpu()):
         raise RuntimeError("end-to-end read-back differs from the device labels")
 
     algo, view_bytes, _, _ = algorithmic_bytes(wl, n_active)
@@ -652,9 +668,11 @@ def run_ours(args, rank, world, local_rank):
                 "ms_per_step": e2e_ms, "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h),
                 "what": "VoxelFusion.step per step with every input copied in from pinned host "
-                        "memory and V_seg + point labels copied out; two buffer sets, copy-in / "
+                        "memory and V_seg + point labels copied out, each direction one copy of "
+                        "a pinned transfer arena (staging.Arena); two arena sets, copy-in / "
                         "kernel / copy-out streams",
-                "serial_ms_per_step": e2e_serial_ms},
+                "serial_ms_per_step": e2e_serial_ms,
+                "per_buffer_ms_per_step": e2e_per_buffer_ms},
         "gpu_launches": int(launches * args.steps),
         "clocks": clk,
         "wall_s_timed": t_wall,
