@@ -90,8 +90,9 @@ typedef struct {
 
 /* divas_params.flags: the active list in brick-major order instead of
  * ascending linear index -- 8 x 8 x 8 bricks in linear brick order (x
- * fastest), the cells of a brick in linear order (x fastest).  Sparse prior
- * only, g a multiple of 8 (else DIVAS_E_INVALID).  Every per-voxel result is
+ * fastest), the cells of a brick in linear order (x fastest).  Either prior
+ * kind (a dense prior 8-byte aligned), g a multiple of 8 (else
+ * DIVAS_E_INVALID).  Every per-voxel result is
  * unchanged; only the order of the active list, and so of everything stored
  * or returned in active-list order, differs.  Consecutive active voxels then
  * lie close together in space, which lets the fusion skip, for a whole warp of
@@ -198,12 +199,20 @@ divas_status divas_fuse_update(divas_ctx* ctx, const divas_view* views, int32_t 
  * The whole hot path in one call: divas_fuse_set_occupancy (A1), then
  * divas_fuse_add_views (views folded into fresh accumulators), then finalize
  * (score_out, seg_bits_out as in divas_fuse_finalize) and, when n_pts > 0,
- * divas_label_points, in four launches and no memset: the compaction clears
+ * divas_label_points, in four launches for a dense prior in linear order (a
+ * sparse prior adds the bitfield's memset and the coordinate scatter, view
+ * culling two more) and no memset of the outputs: the compaction clears
  * the seg bitfields, and the fusion launch also normalises and thresholds
  * each voxel and then writes the zeros of a dense score_out's unoccupied
  * cells.  Results (outputs and
  * context state) equal the separate calls; 1..DIVAS_MAX_VIEWS_PER_CALL views.
- * Capturable in a CUDA graph.  If the occupied set overflows the capacity
+ * Capturable in a CUDA graph.  A brick-ordered context fusing at least four
+ * views also launches its two culling kernels (mask pyramids, brick test) on
+ * a helper stream of its own, forked from `stream` at the call's start and
+ * joined back before the fusion by events (a captured step holds them as a
+ * parallel branch); the call's work is ordered after earlier work on
+ * `stream` and before later work on it, as for a single-stream call.  If the
+ * occupied set overflows the capacity
  * (DIVAS_E_CAPACITY at the next synchronising call), the dense scores of the
  * dropped voxels are unspecified.
  */
