@@ -508,7 +508,9 @@ class VoxelFusion:
     def step(self, views: "PreparedViews", occ=None, coords=None, score=None, seg_bits=None,
              xyz=None, labels=None, stage_events=None, stream=None):
         """The whole hot path in one call (occupancy gate, views, finalize,
-        labels) in four launches.  ``stage_events``: optional four
+        labels): four launches for a dense prior in linear order (a sparse
+        prior adds the coordinate scatter, view culling two launches on the
+        context's helper stream, joined back).  ``stage_events``: optional four
         ``torch.cuda.Event`` (timing enabled, already recorded once) marking
         before compaction / after compaction / after fusion / after labels."""
         if len(views.chunks) != 1:

@@ -240,3 +240,36 @@ def test_batched_brick_sessions_match_linear_sessions_alone():
                 assert np.array_equal(st[k], rl[k]), (wl.name, k)
             fu.close()
         b.close()
+
+
+def test_culled_step_in_a_cuda_graph():
+    """The brick-ordered one-call step with view culling (its culling kernels on
+    the context's helper stream, forked and joined by events) captured in a CUDA
+    graph and replayed: the eager step's results, bitwise."""
+    wl = _small3()
+    d = H.upload(wl)
+    fe, ref = _step(wl, d, brick=True)
+    prm = H.to_params(P0)
+    prm.brick_order = True
+    fu = VoxelFusion(wl.grid, coords=d["coords"], params=prm)
+    score = torch.empty(fu.n_active, dtype=torch.float32, device="cuda")
+    labels = torch.empty(len(d["points"]), dtype=torch.uint8, device="cuda")
+    views = PreparedViews(wl.cams, d["depth"], d["mask"], wl.mask_type)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        fu.step(views, coords=d["coords"], score=score, xyz=d["points"], labels=labels, stream=s)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        fu.step(views, coords=d["coords"], score=score, xyz=d["points"], labels=labels, stream=s)
+    score.fill_(7.0)
+    labels.fill_(9)
+    for _ in range(2):
+        g.replay()
+    torch.cuda.synchronize()
+    st = H.state_of(fu, score, labels)
+    for k in ("active", "W", "Z", "bits", "vmask", "score", "labels"):
+        assert np.array_equal(st[k], ref[k]), k
+    fu.close()
+    fe.close()
