@@ -25,8 +25,8 @@
 //
 // The mask test: a max pyramid of the raw mask values (levels 3..6: texels of
 // 8..64 pixels), built per batch of views; a rectangle of span s pixels is
-// covered by at most 3 x 3 texels of level max(3, ceil(log2 s) - 1); spans
-// above 128 pixels keep the view.  The maximum below the gate threshold (NaN
+// covered by at most 5 x 5 texels of level max(3, ceil(log2 s) - 2); spans
+// above 256 pixels keep the view.  The maximum below the gate threshold (NaN
 // pixels never pass the gate and never raise the maximum) culls the view.
 #pragma once
 
@@ -39,6 +39,7 @@ namespace divas {
 constexpr int kPyrL0 = 3;       // finest pyramid level (8-pixel texels)
 constexpr int kPyrLevels = 4;   // levels 3..6
 constexpr int kPyrTile = 64;    // pixels per side of a level-6 texel (one CTA)
+constexpr int kCullTexels = 5;  // pyramid texels per side that one brick test reads
 
 // per view: the gate threshold, the raster size and the pyramid's layout
 struct CullC {
@@ -210,24 +211,30 @@ __device__ __forceinline__ bool box_may_vote(const CullView& cv, const float* py
     const int32_t iv0 = (int32_t)floorf(fmaxf(fv0, 0.f));
     const int32_t iv1 = (int32_t)floorf(fminf(fv1, (float)(C.H - 1)));
     const int32_t span = max(iu1 - iu0, iv1 - iv0) + 1;
-    const int32_t L = max(kPyrL0, (32 - __clz(span - 1)) - 1);
+    // level: texels of at least span / 4 pixels, so the rectangle meets at most
+    // kCullTexels of them per side
+    const int32_t L = max(kPyrL0, (32 - __clz(span - 1)) - 2);
     if (L >= kPyrL0 + kPyrLevels) return true;  // too wide for the pyramid
-    // the (at most 3 x 3) texels of the rectangle; indices past it are clamped
-    // to it (repeated texels do not change the maximum), so that all loads are
-    // issued before the first is used
+    // the texels of the rectangle; indices past it are clamped to it (repeated
+    // texels do not change the maximum), so that all loads are issued before
+    // the first is used
     const float* lev = pyr + C.off[L - kPyrL0];
     const int32_t lw = C.lw[L - kPyrL0];
     const int32_t tx0 = iu0 >> L, tx1 = iu1 >> L, ty0 = iv0 >> L, ty1 = iv1 >> L;
-    const int32_t xs[3] = {tx0, min(tx0 + 1, tx1), min(tx0 + 2, tx1)};
-    const int32_t ys[3] = {ty0, min(ty0 + 1, ty1), min(ty0 + 2, ty1)};
-    float t[9];
+    int32_t xs[kCullTexels], ys[kCullTexels];
 #pragma unroll
-    for (int a = 0; a < 3; ++a)
+    for (int a = 0; a < kCullTexels; ++a) {
+        xs[a] = min(tx0 + a, tx1);
+        ys[a] = min(ty0 + a, ty1);
+    }
+    float t[kCullTexels * kCullTexels];
 #pragma unroll
-        for (int b = 0; b < 3; ++b) t[3 * a + b] = __ldg(lev + ys[a] * lw + xs[b]);
+    for (int a = 0; a < kCullTexels; ++a)
+#pragma unroll
+        for (int b = 0; b < kCullTexels; ++b) t[kCullTexels * a + b] = __ldg(lev + ys[a] * lw + xs[b]);
     float mx = -INFINITY;
 #pragma unroll
-    for (int a = 0; a < 9; ++a) mx = fmaxf(mx, t[a]);
+    for (int a = 0; a < kCullTexels * kCullTexels; ++a) mx = fmaxf(mx, t[a]);
     return mx >= C.thr;
 }
 
