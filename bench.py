@@ -108,8 +108,8 @@ def job_throughput(units_per_rank: float, world: int, ms_max: float) -> float:
 # warp instructions per voxel-view of the contracted fusion kernel on the
 # unbounded-sparse workload (ncu smsp__inst_executed.sum of one launch divided
 # by its 12M active voxels x 16 views), per active-list order: brick order runs
-# k_fuse_fin_cull (357,818,212 per launch), linear order k_fuse_fin (4.470e8)
-SPARSE_FUSE_INSTS_PER_VOXEL_VIEW = {"brick": 357_818_212 / 192e6, "linear": 447_009_000 / 192e6}
+# k_fuse_fin_cull (342,586,194 per launch), linear order k_fuse_fin (4.470e8)
+SPARSE_FUSE_INSTS_PER_VOXEL_VIEW = {"brick": 342_586_194 / 192e6, "linear": 447_009_000 / 192e6}
 
 
 ACTIVE_ORDER = "auto"  # --active-order
