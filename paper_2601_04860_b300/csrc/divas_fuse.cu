@@ -434,19 +434,38 @@ __device__ __forceinline__ uint32_t brick_word_p0(uint32_t w, const FastDiv& bdi
     return (bi << 3) | (((bj << 3) + ((sl & 1u) << 2)) << 10) | (((bk << 3) + (sl >> 1)) << 20);
 }
 
-// position of set bit number n (from 0) of v, for n < popc(v); always in [0, 31]
-__device__ __forceinline__ uint32_t nth_set_bit(uint32_t v, uint32_t n) {
-    uint32_t pos = 0;
-#pragma unroll
-    for (int w = 16; w >= 1; w >>= 1) {
-        const uint32_t lo = __popc(v & ((1u << w) - 1u));
-        if (n >= lo) {
-            n -= lo;
-            v >>= w;
-            pos += w;
-        }
+// position of set bit number k of a byte (0 past its last set bit), for every
+// byte and k < 8: entry 8 byte + k (built at compile time)
+struct NthBitTable {
+    uint8_t v[256 * 8];
+};
+constexpr NthBitTable make_nth_bit_table() {
+    NthBitTable t{};
+    for (int byte = 0; byte < 256; ++byte) {
+        int seen = 0;
+        for (int b = 0; b < 8; ++b)
+            if ((byte >> b) & 1) t.v[8 * byte + seen++] = (uint8_t)b;
     }
-    return pos;
+    return t;
+}
+__device__ const NthBitTable kNthBit = make_nth_bit_table();
+
+// position of set bit number n (from 0) of v, for n < popc(v); always in [0, 31]:
+// the byte that holds it by two popcount halvings, the bit inside that byte
+// from the table (a 2 KB global array, read through the L1 cache)
+__device__ __forceinline__ uint32_t nth_set_bit(uint32_t v, uint32_t n) {
+    uint32_t sh = 0;
+    const uint32_t lo16 = __popc(v & 0xffffu);
+    if (n >= lo16) {
+        n -= lo16;
+        sh = 16;
+    }
+    const uint32_t lo8 = __popc((v >> sh) & 0xffu);
+    if (n >= lo8) {
+        n -= lo8;
+        sh += 8;
+    }
+    return sh + __ldg(&kNthBit.v[(((v >> sh) & 0xffu) << 3) | (n & 7u)]);
 }
 
 template <bool kBrick>
