@@ -64,10 +64,10 @@ def _env_int(k, d):
 STEP_SOURCES = ("paper_2601_04860_b300/csrc/divas_fuse.cu",
                 "paper_2601_04860_b300/csrc/fuse_math.cuh")
 TRAFFIC_CAPTURE = {
-    "source_sha1": "651c34d77436ca2986c442242c1a7377a4941e7e",
-    "forward-dense-256": {"k_fuse_fin": 28_130_816 + 18_378_240,
-                          "k_tile_count": 16_800_512, "k_tile_emit": 2_373_376,
-                          "k_label": 13_338_112},
+    "source_sha1": "a691ef561e98b5cd0e61cd3092f59817023e1e9a",
+    "forward-dense-256": {"k_fuse_fin": 28_068_608 + 18_152_448,
+                          "k_tile_count": 16_800_256, "k_tile_emit": 2_369_536,
+                          "k_label": 13_338_368},
 }
 
 
