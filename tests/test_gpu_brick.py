@@ -273,3 +273,29 @@ def test_culled_step_in_a_cuda_graph():
         assert np.array_equal(st[k], ref[k]), k
     fu.close()
     fe.close()
+
+
+@pytest.mark.parametrize("brick", [False, True])
+def test_scatter_unaligned_and_ragged_coordinates(brick):
+    """Coordinates at a 4-byte (not 16-byte) aligned address, a count that is
+    not a multiple of four and repeated coordinates take the scatter's scalar
+    loads and merge: the occupied set of an aligned, de-duplicated copy."""
+    wl = _plain_sparse()
+    coords = torch.from_numpy(wl.coords).cuda()
+    n = coords.shape[0] - 3
+    buf = torch.empty(n * 3 + 3 + 1, dtype=torch.int32, device="cuda")
+    buf[1:1 + 3 * n].copy_(coords[:n].reshape(-1))
+    buf[1 + 3 * n:].copy_(coords[n // 2])  # one repeated coordinate
+    unaligned = buf[1:].view(n + 1, 3)
+    assert unaligned.data_ptr() % 16 != 0
+    prm = H.to_params(P0)
+    prm.brick_order = brick
+    fa = VoxelFusion(wl.grid, coords=unaligned, params=prm)
+    fb = VoxelFusion(wl.grid, coords=coords[:n].clone(), params=prm)
+    assert fa.n_active == fb.n_active == n
+    assert torch.equal(fa.active_coords(), fb.active_coords())
+    fa.set_occupancy(coords=unaligned)
+    fa.sync()
+    assert torch.equal(fa.active_coords(), fb.active_coords())
+    fa.close()
+    fb.close()
