@@ -226,17 +226,91 @@ __global__ void __launch_bounds__(kSurfThreads, 6) k_surfel_pass(
     }
 }
 
+// A box larger than kSliceArea pixels is cut into slices of whole rows (about
+// kSliceArea pixels each): the block that meets it takes the first slice and
+// queues the others for k_surfel_slices, their counts meeting in a split slot
+// whose last slice (remaining -> 0) decides the view.  When the queue or the
+// slots are full, the block takes the whole box itself.
+constexpr int64_t kSliceArea = 16384;
+constexpr int32_t kSplitCap = 1 << 16;  // split slots per call
+constexpr int32_t kSliceCap = 1 << 20;  // queued slices per call
+
+struct SplitSlot {
+    int32_t e, s;        // listed surfel, view
+    uint32_t tot, msk;   // counts of the slices done
+    int32_t remaining;   // slices not yet counted
+    int32_t pad;
+};
+
+struct SliceQueue {
+    SplitSlot* slots;
+    int32_t* n_slots;
+    uint2* slices;       // (slot, slice index)
+    int32_t* n_slices;
+};
+
+// rows per slice of a box of the given width
+__device__ __forceinline__ int32_t slice_rows(const SFoot& F) {
+    const int64_t w = (int64_t)(F.x1 - F.x0 + 1);
+    const int64_t r = kSliceArea / w;
+    return (int32_t)(r < 1 ? 1 : r);
+}
+
+// the view's fraction for listed surfel e into its accumulator (kappa: the
+// largest fraction, as non-negative float bits; y: some view reached tau_kappa)
+__device__ __forceinline__ void surfel_view_done(uint2* __restrict__ acc, int32_t e, uint32_t tot,
+                                                 uint32_t msk, float tau_kappa) {
+    const uint32_t den = max(tot, 1u);
+    atomicMax(&acc[e].x, __float_as_uint(__fdiv_rn((float)msk, (float)den)));
+    if ((double)msk >= (double)tau_kappa * (double)den) atomicOr(&acc[e].y, 1u);
+}
+
+// the box rows [ya, yb] of footprint F over the block (warps take rows, lanes
+// columns: consecutive mask words); the block's counts in (s_tot, s_msk)
+__device__ __forceinline__ void surfel_rows(const SView& V, const SFoot& F, int ya, int yb,
+                                            int32_t mask_type, float gate, uint32_t* s_tot,
+                                            uint32_t* s_msk) {
+    uint32_t tot = 0u, msk = 0u;
+    const int nwarps = (int)(blockDim.x >> 5), lane = (int)(threadIdx.x & 31);
+    for (int y = ya + (int)(threadIdx.x >> 5); y <= yb; y += nwarps)
+        for (int x = F.x0 + lane; x <= F.x1; x += 32)
+            surfel_pixel(V, F, x, y, mask_type, gate, tot, msk);
+    tot = __reduce_add_sync(0xffffffffu, tot);
+    msk = __reduce_add_sync(0xffffffffu, msk);
+    if (lane == 0) {
+        atomicAdd(s_tot, tot);
+        atomicAdd(s_msk, msk);
+    }
+}
+
+// a split slot's counts after one slice: the slice that finishes the box
+// decides the view
+__device__ __forceinline__ void slice_done(SplitSlot* slot, uint32_t tot, uint32_t msk,
+                                           uint2* __restrict__ acc, float tau_kappa) {
+    atomicAdd(&slot->tot, tot);
+    atomicAdd(&slot->msk, msk);
+    __threadfence();
+    if (atomicSub(&slot->remaining, 1) == 1) {
+        __threadfence();
+        const uint32_t t = atomicAdd(&slot->tot, 0u), m = atomicAdd(&slot->msk, 0u);
+        surfel_view_done(acc, slot->e, t, m, tau_kappa);
+    }
+}
+
 // The listed surfels: one block per (listed surfel, view) (blockIdx.y =
 // view); the footprint (one thread), then the box's pixels spread over the
-// block and the counts reduced; per surfel, the largest fraction (atomicMax
-// on its non-negative bits) and whether some view reached tau_kappa
-// (atomicOr) go to acc (zeroed).
+// block and the counts reduced (a box above kSliceArea pixels: its first
+// slice, the others queued); per surfel, the largest fraction (atomicMax on
+// its non-negative bits) and whether some view reached tau_kappa (atomicOr)
+// go to acc (zeroed).
 __global__ void __launch_bounds__(kSurfBigThreads) k_surfel_big(
     const float* __restrict__ mu, const float* __restrict__ scales, const float* __restrict__ quats,
     const uint2* __restrict__ big, const int32_t* __restrict__ n_big,
-    const __grid_constant__ SViews SV, float tau_kappa, float z_near, uint2* __restrict__ acc) {
+    const __grid_constant__ SViews SV, float tau_kappa, float z_near, uint2* __restrict__ acc,
+    SliceQueue Q) {
     __shared__ SFoot sF;
     __shared__ bool s_ok;
+    __shared__ int32_t s_slot, s_rows;
     __shared__ uint32_t s_tot, s_msk;
     const float gate = SV.mask_type == kMaskLogit ? SV.logit_m : SV.tau_m;
     const int32_t nb = *n_big;
@@ -251,30 +325,71 @@ __global__ void __launch_bounds__(kSurfBigThreads) k_surfel_big(
             s_ok = surfel_foot(SV.v[s], mm, t0, t1, z_near, sF);
             s_tot = 0u;
             s_msk = 0u;
-        }
-        __syncthreads();
-        if (s_ok) {
-            const SFoot F = sF;
-            uint32_t tot = 0u, msk = 0u;
-            // warps take rows, lanes take columns (consecutive mask words)
-            const int nwarps = (int)(blockDim.x >> 5), lane = (int)(threadIdx.x & 31);
-            if (F.any)
-                for (int y = F.y0 + (int)(threadIdx.x >> 5); y <= F.y1; y += nwarps)
-                    for (int x = F.x0 + lane; x <= F.x1; x += 32)
-                        surfel_pixel(SV.v[s], F, x, y, SV.mask_type, gate, tot, msk);
-            tot = __reduce_add_sync(0xffffffffu, tot);
-            msk = __reduce_add_sync(0xffffffffu, msk);
-            if ((threadIdx.x & 31) == 0) {
-                atomicAdd(&s_tot, tot);
-                atomicAdd(&s_msk, msk);
+            s_slot = -1;
+            s_rows = sF.y1 - sF.y0 + 1;
+            if (s_ok && sF.any && foot_area(sF) > kSliceArea) {
+                // queue slices 1 .. S - 1; slice 0 is this block's
+                const int32_t R = slice_rows(sF);
+                const int32_t S = (sF.y1 - sF.y0 + R) / R;
+                const int32_t slot = atomicAdd(Q.n_slots, 1);
+                const int32_t first = slot < kSplitCap ? atomicAdd(Q.n_slices, S - 1) : kSliceCap;
+                if (slot < kSplitCap && first + (S - 1) <= kSliceCap) {
+                    Q.slots[slot] = SplitSlot{e, s, 0u, 0u, S, 0};
+                    for (int32_t k = 1; k < S; ++k) Q.slices[first + k - 1] = make_uint2((uint32_t)slot, (uint32_t)k);
+                    s_slot = slot;
+                    s_rows = R;
+                } else {
+                    // no room: the whole box here; the part of the reservation
+                    // inside the queue is marked empty
+                    for (int32_t k = first; k < kSliceCap && k < first + (S - 1); ++k)
+                        Q.slices[k] = make_uint2(0xffffffffu, 0u);
+                }
             }
         }
         __syncthreads();
+        if (s_ok && sF.any)
+            surfel_rows(SV.v[s], sF, sF.y0, min(sF.y1, sF.y0 + s_rows - 1), SV.mask_type, gate,
+                        &s_tot, &s_msk);
+        __syncthreads();
         if (threadIdx.x == 0 && s_ok) {
-            const uint32_t den = max(s_tot, 1u);
-            atomicMax(&acc[e].x, __float_as_uint(__fdiv_rn((float)s_msk, (float)den)));
-            if ((double)s_msk >= (double)tau_kappa * (double)den) atomicOr(&acc[e].y, 1u);
+            if (s_slot >= 0) {
+                __threadfence();  // the slot's fields before the slices' counts
+                slice_done(Q.slots + s_slot, s_tot, s_msk, acc, tau_kappa);
+            } else {
+                surfel_view_done(acc, e, s_tot, s_msk, tau_kappa);
+            }
         }
+        __syncthreads();
+    }
+}
+
+// the queued slices of the split boxes, one at a time per block
+__global__ void __launch_bounds__(kSurfBigThreads) k_surfel_slices(
+    const float* __restrict__ mu, const float* __restrict__ scales, const float* __restrict__ quats,
+    const uint2* __restrict__ big, const __grid_constant__ SViews SV, float tau_kappa,
+    float z_near, uint2* __restrict__ acc, SliceQueue Q) {
+    __shared__ SFoot sF;
+    __shared__ uint32_t s_tot, s_msk;
+    const float gate = SV.mask_type == kMaskLogit ? SV.logit_m : SV.tau_m;
+    const int32_t n = min(*Q.n_slices, kSliceCap);
+    for (int32_t q = blockIdx.x; q < n; q += gridDim.x) {
+        const uint2 sl = Q.slices[q];
+        if (sl.x >= (uint32_t)kSplitCap) continue;  // an empty entry (block-uniform)
+        SplitSlot* slot = Q.slots + sl.x;
+        const int32_t e = slot->e, s = slot->s;
+        if (threadIdx.x == 0) {
+            float mm[3], t0[3], t1[3];
+            surfel_axes(mu, scales, quats, (int32_t)big[e].x, mm, t0, t1);
+            surfel_foot(SV.v[s], mm, t0, t1, z_near, sF);  // as when the box was split
+            s_tot = 0u;
+            s_msk = 0u;
+        }
+        __syncthreads();
+        const int32_t R = slice_rows(sF);
+        const int ya = sF.y0 + (int)sl.y * R;
+        surfel_rows(SV.v[s], sF, ya, min(sF.y1, ya + R - 1), SV.mask_type, gate, &s_tot, &s_msk);
+        __syncthreads();
+        if (threadIdx.x == 0) slice_done(slot, s_tot, s_msk, acc, tau_kappa);
         __syncthreads();
     }
 }
@@ -460,7 +575,8 @@ divas_status divas_surfel_labels(divas_ctx* c, const float* mu, const float* sca
     const int32_t n = (int32_t)m;
     const size_t arr = ((size_t)n * 4 + 255) / 256 * 256;
     const size_t lst = ((size_t)n * 16 + 256 + 255) / 256 * 256;  // list + accumulators
-    const size_t need = arr + lst + sel_scratch_bytes(1);
+    const size_t spl = (size_t)kSplitCap * sizeof(SplitSlot) + (size_t)kSliceCap * sizeof(uint2) + 256;
+    const size_t need = arr + lst + spl + sel_scratch_bytes(1);
     cudaStream_t s = S(stream);
     if (need > c->wt_bytes) {
         if (capturing(s))
@@ -476,8 +592,15 @@ divas_status divas_surfel_labels(divas_ctx* c, const float* mu, const float* sca
     int32_t* n_big = reinterpret_cast<int32_t*>(static_cast<unsigned char*>(c->wt) + arr);
     uint2* big = reinterpret_cast<uint2*>(static_cast<unsigned char*>(c->wt) + arr + 256);
     uint2* acc = big + n;
-    void* sel = static_cast<unsigned char*>(c->wt) + arr + lst;
+    unsigned char* sp = static_cast<unsigned char*>(c->wt) + arr + lst;
+    SliceQueue Q;
+    Q.n_slots = reinterpret_cast<int32_t*>(sp);
+    Q.n_slices = reinterpret_cast<int32_t*>(sp) + 1;
+    Q.slots = reinterpret_cast<SplitSlot*>(sp + 256);
+    Q.slices = reinterpret_cast<uint2*>(sp + 256 + (size_t)kSplitCap * sizeof(SplitSlot));
+    void* sel = static_cast<unsigned char*>(c->wt) + arr + lst + spl;
     DIVAS_CUDA(c, cudaMemsetAsync(n_big, 0, sizeof(int32_t), s));
+    DIVAS_CUDA(c, cudaMemsetAsync(sp, 0, 2 * sizeof(int32_t), s));
     DIVAS_CUDA(c, cudaMemsetAsync(acc, 0, (size_t)n * sizeof(uint2), s));
     const int blocks = (int)std::min<int64_t>((n + kSurfThreads - 1) / kSurfThreads, 16 * (int64_t)c->sm_count);
     k_surfel_aspect<<<blocks, kSurfThreads, 0, s>>>(scales, n, p->eps_aspect, aspect);
@@ -495,8 +618,12 @@ divas_status divas_surfel_labels(divas_ctx* c, const float* mu, const float* sca
     DIVAS_LAUNCHED(c, "k_surfel_pass");
     if (n_views > 0) {
         k_surfel_big<<<dim3(std::max(1, 4 * c->sm_count / n_views), n_views), kSurfBigThreads, 0, s>>>(
-            mu, scales, quats, big, n_big, SV, p->tau_kappa, c->F.z_near, acc);
+            mu, scales, quats, big, n_big, SV, p->tau_kappa, c->F.z_near, acc, Q);
         DIVAS_LAUNCHED(c, "k_surfel_big");
+        k_surfel_slices<<<4 * c->sm_count, kSurfBigThreads, 0, s>>>(mu, scales, quats, big, SV,
+                                                                   p->tau_kappa, c->F.z_near,
+                                                                   acc, Q);
+        DIVAS_LAUNCHED(c, "k_surfel_slices");
         k_surfel_big_out<<<c->sm_count, kSurfThreads, 0, s>>>(big, n_big, acc, f_out, kappa_out);
         DIVAS_LAUNCHED(c, "k_surfel_big_out");
     }
