@@ -142,3 +142,38 @@ def test_overlay_matches_oracle():
         ones += ref[ok].sum()
     assert ones > 100 and total > 0.95 * sum(c.W * c.H for c in wl.cams)
     fu.close()
+
+
+def test_large_footprints_cut_into_slices():
+    """Scored surfels scaled up 200 times (aspects unchanged) so that their
+    1-sigma boxes cover most of the 224 x 168 frame: boxes above 16,384 pixels
+    are counted in row slices by several blocks; Pass 2, the final indicator
+    and kappa equal the oracle's."""
+    wl, mu, sc, q = _setup(n_points=10_000, needles=False)
+    ref0 = _oracle(wl, mu, sc, q)
+    pick = np.flatnonzero(ref0["F2"] & ~ref0["excluded"])[:24]
+    mu, sc, q = mu[pick], (sc[pick] * np.float32(200.0)).astype(np.float32), q[pick]
+    got = _run(wl, mu, sc, q)
+    ref = _oracle(wl, mu, sc, q)
+    ok = ~ref["excluded"]
+    assert ref["F2"][ok].sum() >= 10
+    # boxes of the scored surfels above 16,384 pixels (clipped to the frame): the sliced path
+    n_large = 0
+    for i in np.flatnonzero(ref["F2"]):
+        R = S.quat_to_rot(q[i])
+        m = mu[i].astype(np.float64)
+        t0, t1 = float(sc[i, 0]) * R[:, 0], float(sc[i, 1]) * R[:, 1]
+        for cam in wl.cams:
+            pr = [S._project(cam, X) for X in (m, m + t0, m - t0, m + t1, m - t1)]
+            if not all(p[2] > 1e-6 for p, _ in pr):
+                continue
+            c = pr[0][1]
+            a0, a1 = 0.5 * (pr[1][1] - pr[2][1]), 0.5 * (pr[3][1] - pr[4][1])
+            ex, ey = max(abs(a0[0]), abs(a1[0])), max(abs(a0[1]), abs(a1[1]))
+            w = min(np.floor(c[0] + ex - 0.5), cam.W - 1) - max(np.ceil(c[0] - ex - 0.5), 0) + 1
+            h = min(np.floor(c[1] + ey - 0.5), cam.H - 1) - max(np.ceil(c[1] - ey - 0.5), 0) + 1
+            n_large += int(w > 0 and h > 0 and w * h > 16384)
+    assert n_large >= 10, n_large
+    assert np.array_equal(got["f2"][ok].astype(bool), ref["F2"][ok]), "Pass 2 differs"
+    assert np.array_equal(got["f"][ok].astype(bool), ref["F"][ok]), "final indicator differs"
+    assert np.allclose(got["kappa"][ok], ref["kappa"][ok], rtol=0, atol=1e-6), "kappa differs"
