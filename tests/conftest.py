@@ -32,8 +32,8 @@ def pytest_collection_modifyitems(config, items):
 
 def pytest_terminal_summary(terminalreporter):
     """Near-boundary counts of the parity checks that ran (oracle-flagged items
-    excluded from the exact comparisons), also written to
-    gpurun_out/parity_counts.json (or $DIVAS_PARITY_JSON)."""
+    excluded from the exact comparisons), also written as JSON to
+    $DIVAS_PARITY_JSON (default: parity_counts.json in the run-output folder)."""
     try:
         from tests import gpu_helpers
     except Exception:
