@@ -676,11 +676,18 @@ __device__ __forceinline__ void seg_epilogue(bool live, bool seg, int64_t lin,
     const int lane = threadIdx.x & 31;
     const uint32_t word = live ? (uint32_t)(lin >> 5) : 0xffffffffu;
     const uint32_t bit = live ? 1u << (lin & 31) : 0u;
+    const bool clearing = clear_bits || (seg_out && clear_out);  // warp-uniform
+    if (!clearing) {  // only bits to set: one atomic per seg voxel, no run merging
+        if (live && seg) {
+            atomicOr(seg_bits + word, bit);
+            if (seg_out) atomicOr(seg_out + word, bit);
+        }
+        return;
+    }
     int first, end;
     word_run(word, first, end);
     const uint32_t set = run_suffix_or(seg ? bit : 0u, end);
-    const bool clearing = clear_bits || (seg_out && clear_out);  // warp-uniform
-    const uint32_t clr = clearing ? run_suffix_or(seg ? 0u : bit, end) : 0u;
+    const uint32_t clr = run_suffix_or(seg ? 0u : bit, end);
     if (!live || lane != first) return;
     if (set) atomicOr(seg_bits + word, set);
     if (clr && clear_bits) atomicAnd(seg_bits + word, ~clr);
