@@ -64,10 +64,10 @@ def _env_int(k, d):
 STEP_SOURCES = ("paper_2601_04860_b300/csrc/divas_fuse.cu",
                 "paper_2601_04860_b300/csrc/fuse_math.cuh")
 TRAFFIC_CAPTURE = {
-    "source_sha1": "a691ef561e98b5cd0e61cd3092f59817023e1e9a",
-    "forward-dense-256": {"k_fuse_fin": 28_068_608 + 18_152_448,
-                          "k_tile_count": 16_800_256, "k_tile_emit": 2_369_536,
-                          "k_label": 13_338_368},
+    "source_sha1": "abdb534ab37e0be5707425b85e20d51b3e66dfe5",
+    "forward-dense-256": {"k_fuse_fin": 28_087_296 + 18_061_056,
+                          "k_tile_count": 16_800_256, "k_tile_emit": 2_369_280,
+                          "k_label": 13_339_136 + 1_280},
 }
 
 
@@ -108,8 +108,8 @@ def job_throughput(units_per_rank: float, world: int, ms_max: float) -> float:
 # warp instructions per voxel-view of the contracted fusion kernel on the
 # unbounded-sparse workload (ncu smsp__inst_executed.sum of one launch divided
 # by its 12M active voxels x 16 views), per active-list order: brick order runs
-# k_fuse_fin_cull (342,586,194 per launch), linear order k_fuse_fin (4.470e8)
-SPARSE_FUSE_INSTS_PER_VOXEL_VIEW = {"brick": 342_586_194 / 192e6, "linear": 447_009_000 / 192e6}
+# k_fuse_fin_cull (323,038,682 per launch), linear order k_fuse_fin (4.470e8)
+SPARSE_FUSE_INSTS_PER_VOXEL_VIEW = {"brick": 323_038_682 / 192e6, "linear": 447_009_000 / 192e6}
 
 
 ACTIVE_ORDER = "auto"  # --active-order
