@@ -214,6 +214,17 @@ __device__ __forceinline__ int64_t packed_lin(uint32_t pk, int32_t g) {
     return ((int64_t)k * g + j) * g + i;
 }
 
+// ---------------------------------------------------------------------------
+// reciprocal of a normal, positive float: the hardware approximation (relative
+// error below 2^-22) refined by one Newton-Raphson step r' = r + r (1 - x r),
+// which squares the error; the result is within one ulp of 1/x.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float rcp_nr(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return __fmaf_rn(r, __fmaf_rn(-x, r, 1.f), r);
+}
+
 template <bool kContracted>
 __device__ __forceinline__ VoxelGeom voxel_geom(uint32_t pk, const GridC& G, float gamma) {
     VoxelGeom vg;
@@ -262,7 +273,7 @@ __device__ __forceinline__ VoxelGeom voxel_geom(uint32_t pk, const GridC& G, flo
     } else if (!inner) {
         // rho = sqrt(n2) as hi + lo
         const float rh = __fsqrt_rn(n2h);
-        const float rl = __fdiv_rn(__fadd_rn(__fmaf_rn(-rh, rh, n2h), n2l), __fmul_rn(2.f, rh));
+        const float rl = __fmul_rn(__fadd_rn(__fmaf_rn(-rh, rh, n2h), n2l), rcp_nr(__fmul_rn(2.f, rh)));
         // d = 2 - rho (2 - rh is exact for rh in [1, 2])
         float dh, dl;
         two_sum(__fsub_rn(2.f, rh), -rl, dh, dl);
@@ -271,8 +282,8 @@ __device__ __forceinline__ VoxelGeom voxel_geom(uint32_t pk, const GridC& G, flo
         two_prod(rh, dh, qh, ql);
         ql = __fadd_rn(ql, __fadd_rn(__fmul_rn(rh, dl), __fmul_rn(rl, dh)));
         two_sum(qh, ql, qh, ql);
-        // sc = 1 / den
-        const float sh = __frcp_rn(qh);
+        // sc = 1 / den (the lo part corrects the hi reciprocal's error)
+        const float sh = rcp_nr(qh);
         const float res = __fsub_rn(__fmaf_rn(-sh, qh, 1.f), __fmul_rn(sh, ql));
         const float sl = __fmul_rn(sh, res);
         // x = c sc
@@ -284,11 +295,11 @@ __device__ __forceinline__ VoxelGeom voxel_geom(uint32_t pk, const GridC& G, flo
             two_sum(xh, xe, vg.xh[a], vg.xl[a]);
         }
         const float d = __fadd_rn(dh, dl);
-        hv = __fdiv_rn(G.h, __fmul_rn(d, d));  // largest stretch of the inverse contraction
+        hv = __fmul_rn(G.h, rcp_nr(__fmul_rn(d, d)));  // largest stretch of the inverse contraction
     }
     vg.hv = hv;
     vg.Delta = __fmul_rn(gamma, hv);
-    vg.invDelta = __frcp_rn(vg.Delta);
+    vg.invDelta = rcp_nr(vg.Delta);
     vg.n1 = 0.f;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
@@ -297,17 +308,6 @@ __device__ __forceinline__ VoxelGeom voxel_geom(uint32_t pk, const GridC& G, flo
     }
     vg.DeltaS = __fmul_ru(vg.Delta, 1.f + 0x1p-20f);
     return vg;
-}
-
-// ---------------------------------------------------------------------------
-// reciprocal of a normal, positive float: the hardware approximation (relative
-// error below 2^-22) refined by one Newton-Raphson step r' = r + r (1 - x r),
-// which squares the error; the result is within one ulp of 1/x.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ float rcp_nr(float x) {
-    float r;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-    return __fmaf_rn(r, __fmaf_rn(-x, r, 1.f), r);
 }
 
 // ---------------------------------------------------------------------------
