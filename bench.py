@@ -64,10 +64,10 @@ def _env_int(k, d):
 STEP_SOURCES = ("paper_2601_04860_b300/csrc/divas_fuse.cu",
                 "paper_2601_04860_b300/csrc/fuse_math.cuh")
 TRAFFIC_CAPTURE = {
-    "source_sha1": "abdb534ab37e0be5707425b85e20d51b3e66dfe5",
-    "forward-dense-256": {"k_fuse_fin": 28_087_296 + 18_061_056,
-                          "k_tile_count": 16_800_256, "k_tile_emit": 2_369_280,
-                          "k_label": 13_339_136 + 1_280},
+    "source_sha1": "f85cc2b98d0769c4b02d830db8d3249398a36aa3",
+    "forward-dense-256": {"k_fuse_fin": 28_112_384 + 18_184_448,
+                          "k_tile_count": 16_800_256 + 2_048, "k_tile_emit": 2_369_280,
+                          "k_label": 13_339_904},
 }
 
 
