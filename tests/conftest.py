@@ -33,7 +33,7 @@ def pytest_collection_modifyitems(config, items):
 def pytest_terminal_summary(terminalreporter):
     """Near-boundary counts of the parity checks that ran (oracle-flagged items
     excluded from the exact comparisons), also written as JSON to
-    $DIVAS_PARITY_JSON (default: parity_counts.json in the run-output folder)."""
+    the file that $DIVAS_PARITY_JSON names, when it is set."""
     try:
         from tests import gpu_helpers
     except Exception:
@@ -48,10 +48,11 @@ def pytest_terminal_summary(terminalreporter):
         tr.write_line(f"{r['check']}: {r['flagged']} of {r['items']} "
                       f"({100.0 * r['flagged_frac']:.3f}%), mismatches outside them "
                       f"{r['mismatches']}")
-    path = os.environ.get("DIVAS_PARITY_JSON",
-                          os.path.join(ROOT, "gpurun_out", "parity_counts.json"))
+    path = os.environ.get("DIVAS_PARITY_JSON")
+    if not path:
+        return
     try:
-        os.makedirs(os.path.dirname(path), exist_ok=True)
+        os.makedirs(os.path.dirname(os.path.abspath(path)), exist_ok=True)
         with open(path, "w") as f:
             json.dump(rows, f, indent=1)
     except OSError:
