@@ -108,8 +108,8 @@ def job_throughput(units_per_rank: float, world: int, ms_max: float) -> float:
 # warp instructions per voxel-view of the contracted fusion kernel on the
 # unbounded-sparse workload (ncu smsp__inst_executed.sum of one launch divided
 # by its 12M active voxels x 16 views), per active-list order: brick order runs
-# k_fuse_fin_cull (323,038,682 per launch), linear order k_fuse_fin (4.470e8)
-SPARSE_FUSE_INSTS_PER_VOXEL_VIEW = {"brick": 323_038_682 / 192e6, "linear": 447_009_000 / 192e6}
+# k_fuse_fin_cull (316,070,407 per launch), linear order k_fuse_fin (435,256,325)
+SPARSE_FUSE_INSTS_PER_VOXEL_VIEW = {"brick": 316_070_407 / 192e6, "linear": 435_256_325 / 192e6}
 
 
 ACTIVE_ORDER = "auto"  # --active-order
